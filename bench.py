@@ -1,0 +1,313 @@
+#!/usr/bin/env python
+"""Throughput of the adjoint-descent step on GB300.
+
+Metric: curve-point adjoint-gradient evaluations per second, i.e. interior
+curve points (M = N_s - 2 per curve) x descent steps / time.  One bench step is
+one full descent step of the workload curve: the row phase (f, residual,
+spatial adjoint, FP64 cost reductions), the s-phase with the descent update and
+|G|^2, and the s-phase D_t u of the new state (three kernels, plus the one-thread
+kernel that arms the step counter).
+
+Default workload: L = 22, N_x = 64, N_s = 1024 (the differentiation workload),
+FP32 storage and transforms with FP64 reductions.  The curve is far smaller
+than L2, so L2 is flushed (a 256 MiB write) before every timed step and each
+step is timed on its own with CUDA events on the curve's stream.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N > 1) every rank runs its own curve (independent replicas,
+weak scaling); rank 0 prints the JSON line with the max-over-ranks time.
+"""
+from __future__ import annotations
+
+import argparse
+import csv
+import io
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "curve-point adjoint-gradient evals/s"
+UNIT = "point-evals/s"
+FP32_LANES_PER_SM = 128
+N_SM = 152
+SM_MAX_MHZ = 2070.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the oracle CPU baseline")
+    ap.add_argument("--e2e-steps", type=int, default=100)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def workload_spec():
+    from paper_2301_11704_gb300 import gen
+    return gen.workload(1)[0]
+
+
+def workload_config(spec, precision):
+    return {"workload": "KSE curve L=%g N_x=%d N_s=%d (M=%d), S=%g, dtau=%g, %s storage, FP64 reductions"
+                        % (spec.L, spec.N, spec.Ns, spec.M, spec.S, spec.dtau, precision),
+            "L": spec.L, "N_x": spec.N, "N_s": spec.Ns, "S": spec.S, "dtau": spec.dtau,
+            "adjoint": "paper", "curves_per_gpu": 1,
+            "l2": "flushed before every timed step (256 MiB write); each step timed alone",
+            "parallelism": "independent replicas (one curve per GPU)"}
+
+
+# ---------------------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=10)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for row in csv.reader(io.StringIO(out)):
+            if len(row) < 9:
+                continue
+            try:
+                sm.append(float(row[1]))
+                smax.append(float(row[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, row[5:9]):
+                if val.strip().lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------- oracle (CPU)
+def oracle_steps(spec, budget_s, max_steps=None):
+    """Times the FP64 oracle's descent on the same curve until the budget is used."""
+    import oracle
+    from paper_2301_11704_gb300 import gen
+    up, um = gen.end_points(spec)
+    amps, vp = gen.perturbation(spec)
+    U = oracle.curve_init(spec.M, spec.S, up, um, s0=spec.s0, amps=amps, vp=vp)
+    oracle.curve_descend(U, spec.L, spec.S, 1, dtau=spec.dtau)          # build + warm caches
+    times = []
+    t_all = time.perf_counter()
+    while True:
+        t0 = time.perf_counter()
+        U, _, _, _ = oracle.curve_descend(U, spec.L, spec.S, 1, dtau=spec.dtau)
+        times.append(time.perf_counter() - t0)
+        if max_steps is not None and len(times) >= max_steps:
+            break
+        if max_steps is None and time.perf_counter() - t_all >= budget_s:
+            break
+    return times, oracle.num_threads()
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    spec = workload_spec()
+    import oracle
+    oracle.build()
+    # warm-up steps are untimed; each timed step is one full oracle descent step of the curve
+    oracle_steps(spec, 0.0, max_steps=max(1, min(args.warmup, 3)))
+    times, cores = oracle_steps(spec, 0.0, max_steps=args.steps)
+    total = sum(times)
+    value = spec.M * len(times) / total
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": len(times),
+            "warmup": args.warmup, "ms_per_step": 1e3 * total / len(times), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload_config(spec, "FP64"), "impl": "reference",
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": "%d full descent steps of the workload curve" % len(times)},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+# ---------------------------------------------------------------------------- GPU
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+    import torch.distributed as dist
+    from paper_2301_11704_gb300 import gen
+    from paper_2301_11704_gb300.curve import KSCurve
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    spec = workload_spec()
+    up, um = gen.end_points(spec)
+    amps, vp = gen.perturbation(spec)
+
+    def make_curve(precision):
+        c = KSCurve(spec.L, spec.N, spec.Ns, spec.S, up, um, s0=spec.s0, dtau=spec.dtau, precision=precision,
+                    device=dev)
+        c.init_trial(0.0, None, amps, vp)
+        return c
+
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    def timed_steps(c, K, W, profile=0):
+        for _ in range(W):
+            flush.fill_(1)
+            c.descend_async(1)
+        torch.cuda.synchronize(dev)
+        if profile:
+            c.profile(profile)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+        barrier()
+        torch.cuda.synchronize(dev)
+        for i in range(K):
+            flush.fill_(i & 255)
+            ev[i][0].record()
+            c.descend_async(1)
+            ev[i][1].record()
+        torch.cuda.synchronize(dev)
+        barrier()
+        ms = [a.elapsed_time(b) for a, b in ev]
+        prof = c.profile_read() if profile else None
+        if profile:
+            c.profile(0)
+        return ms, prof
+
+    curve = make_curve(args.precision)
+    K, W = args.steps, args.warmup
+    clocks = ClockSampler(local)
+    clocks.start()
+    step_ms, prof = timed_steps(curve, K, W, profile=min(K, 2000))
+    clk = clocks.stop()
+    total_ms = sum(step_ms)
+    t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    total_ms_max = float(t.item())
+    points = spec.M
+    value = world * points * K / (total_ms_max / 1e3)
+    sc = curve.scalars()
+
+    # ---- roofline of the dominant kernel (per-launch event times from inside the library)
+    b = 4 if args.precision == "fp32" else 8
+    field = spec.Ns * spec.N * b
+    avg = {k: v["ms"] / max(v["launches"], 1) for k, v in prof.items()}
+    dom = max(avg, key=avg.get)
+    flops_dt = 2.0 * spec.Ns * spec.Ns * spec.N
+    peak_alu = (N_SM * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12) if b == 4 else 1.25
+    peaks = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            peaks = json.load(f)
+    except OSError:
+        pass
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    if dom == "rows":
+        bytes_alg = 4 * field + spec.Ns * 32
+        ach = bytes_alg / (avg[dom] / 1e3) / 1e9
+        roof = {"bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s", "frac": ach / hbm_peak,
+                "traffic": None, "kernel": "k_rows", "algorithmic_bytes": bytes_alg}
+    else:
+        ach = flops_dt / (avg[dom] / 1e3) / 1e12
+        roof = {"bound": "alu", "achieved": ach, "peak": peak_alu, "unit": "TFLOP/s", "frac": ach / peak_alu,
+                "traffic": None, "kernel": "k_dt (%s)" % dom, "algorithmic_flops": flops_dt,
+                "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz" if b == 4 else
+                "nominal FP64 1.25 TFLOP/s"}
+    roof["phase_ms_per_launch"] = avg
+
+    # ---- end to end through the public API with host buffers
+    e2e = None
+    if rank == 0 or world > 1:
+        dt = curve.dtype
+        host_in = torch.empty((spec.Ns, spec.N), dtype=dt).pin_memory()
+        host_out = torch.empty((spec.Ns, spec.N), dtype=dt).pin_memory()
+        host_in.copy_(curve.get_state().cpu())
+        dev_in = torch.empty((spec.Ns, spec.N), dtype=dt, device=dev)
+        n_e2e = max(1, min(args.e2e_steps, K))
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        for _ in range(n_e2e):
+            dev_in.copy_(host_in, non_blocking=True)
+            curve.set_state(dev_in, 1.0, 0.0)
+            curve.descend(1)
+            host_out.copy_(curve.get_state(), non_blocking=True)
+            torch.cuda.synchronize(dev)
+        e2e_s = time.perf_counter() - t0
+        nb = spec.Ns * spec.N * b
+        e2e = {"value": points * n_e2e / e2e_s, "unit": UNIT, "h2d_bytes_per_step": nb,
+               "d2h_bytes_per_step": nb, "steps": n_e2e,
+               "path": "pinned host curve -> set_state -> descend(1) -> get_state -> pinned host"}
+
+    # ---- FP64 GPU path (context)
+    fp64 = None
+    if args.precision == "fp32":
+        c64 = make_curve("fp64")
+        k64 = max(3, min(50, K))
+        ms64, _ = timed_steps(c64, k64, 3)
+        fp64 = {"value": points * k64 / (sum(ms64) / 1e3), "unit": UNIT, "ms_per_step": sum(ms64) / k64,
+                "steps": k64}
+        c64.close()
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        times, cores = oracle_steps(spec, args.cpu_seconds)
+        cpu = {"value": points * len(times) / sum(times), "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": "%d full FP64 descent steps of the same curve (%.1f s)" % (len(times), sum(times))}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
+                "ms_per_step": total_ms_max / K, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "f64", "data": "synthetic",
+                "config": workload_config(spec, args.precision.upper()), "roofline": roof,
+                "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": 4 * K, "clocks": clk,
+                "fp64_gpu_path": fp64, "final_J": sc["J"], "final_J_arc": sc["J_arc"],
+                "step_ms_median": statistics.median(step_ms)}
+        print(json.dumps(line))
+    curve.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,222 @@
+/*
+ * ksconn.h -- C ABI of the GB300 (sm_103a) adjoint-descent library for
+ * connecting orbits of the Kuramoto-Sivashinsky equation (KSE), after
+ * Ashtari & Schneider, "Jacobian-Free Variational Method for Constructing
+ * Connecting Orbits in Nonlinear Dynamical Systems" (arXiv 2301.11704).
+ *
+ * One curve u(x, s) joins two equilibria u_- (s -> -inf) and u_+ (s -> +inf).
+ * It is discretised with N Fourier modes in x (Sec. V.C.1) and M + 2
+ * rational-Chebyshev sections in s (eq. t_grid; N_s = M + 2 counts both end
+ * sections).  One descent step evaluates, for every curve point at once,
+ *   f(u)           the KSE right-hand side            (eq. KSE, nu = 1)
+ *   r = f - l D_t u  the residual                      (eq. residual_definition, eq. KSE_residual)
+ *   G = -L^dagger(u; r) the adjoint descent direction  (eq. KSE_G)
+ *   J^2, J_arc     the cost and its arc-length form   (eq. cost_function_general, eq. J_arc)
+ * and advances u by semi-implicit Euler in fictitious time (Sec. V.C.3).
+ * l (lambda) scales the s-derivative; l = 1 is the published method.
+ *
+ * Conventions shared by every entry point
+ *  - All functions return ks_status; KS_OK is 0.  No function throws, exits or
+ *    prints.  On failure ks_last_error() returns a message for the calling
+ *    thread; outputs are then unspecified, and the curve stays usable unless
+ *    the status is KS_ECUDA (a failed CUDA call; the CUDA context may be lost).
+ *  - Device pointers ("_dev") point to memory of the current CUDA device,
+ *    allocated by the caller.  The library never allocates or frees device
+ *    memory itself: every buffer it uses lives in the caller's workspace.
+ *    Host pointers ("_host" or scalar outputs) are ordinary host memory.
+ *  - Physical curve arrays are row-major [N_s][N] in the storage type of the
+ *    curve (double for KS_FP64, float for KS_FP32); row m is section s_m,
+ *    row 0 is s = +inf (u_+), row N_s-1 is s = -inf (u_-); column n is x_n = n L / N.
+ *  - Work is issued on the caller's CUDA stream (cudaStream_t passed as void*;
+ *    NULL = legacy default stream).  Functions that return host scalars
+ *    synchronise that stream; the others are asynchronous.
+ *  - A curve handle is not thread safe; distinct handles are independent.
+ */
+#ifndef KSCONN_H
+#define KSCONN_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    KS_OK = 0,
+    KS_EINVAL = 1,            /* bad argument (sizes, null pointers, ranges) */
+    KS_ENOMEM = 2,            /* caller workspace smaller than ks_curve_workspace_bytes() */
+    KS_ECUDA = 3,             /* a CUDA runtime call failed */
+    KS_ETIMEOUT = 4,          /* a device-side bounded wait expired */
+    KS_ENONFINITE = 5,        /* J or G became NaN/Inf; the descent stopped */
+    KS_ENOTCONV = 6,          /* nsteps exhausted before the tolerance was met */
+    KS_ENOTEQUILIBRIUM = 7,   /* an end section is not an equilibrium (|f(u)| too large) */
+    KS_ENOTIMPL = 8
+} ks_status;
+
+typedef enum { KS_FP64 = 0, KS_FP32 = 1 } ks_precision;
+
+/* s-term of the adjoint (eq. KSE_G).
+ * KS_ADJ_PAPER:    +lambda D_t r, the continuous adjoint discretised, as published.
+ * KS_ADJ_DISCRETE: -lambda W^-1 D_t^T W r, the exact adjoint of the discretised
+ *                  residual under the quadrature inner product (W = diag(w_m)),
+ *                  so that G is exactly the negative W-gradient of J^2. */
+typedef enum { KS_ADJ_PAPER = 0, KS_ADJ_DISCRETE = 1 } ks_adjoint;
+
+/* Convergence measure compared with `tol` in ks_curve_descend.
+ * KS_CONV_JARC: J_arc (eq. J_arc; the published criterion is J_arc < 1e-12).
+ * KS_CONV_J:    J = sqrt(J^2).
+ * KS_CONV_JREL: J / |lambda D_t u|_W (scale-free; the FP32 criterion). */
+typedef enum { KS_CONV_JARC = 0, KS_CONV_J = 1, KS_CONV_JREL = 2 } ks_conv;
+
+typedef struct {
+    double L;            /* domain length, > 0 (Sec. V: x in [0, L)) */
+    int32_t nx;          /* N: Fourier modes = grid points per section; power of two, 8..256 */
+    int32_t ns;          /* N_s = M + 2 sections including both ends; 3 <= N_s <= 65536 */
+    double S;            /* map scale S > 0 (eq. Rational_domain) */
+    double s0;           /* map centre s0 (eq. Rational_domain) */
+    double lambda;       /* scale of the s-derivative; 1 = the published method */
+    int32_t lambda_free; /* 1: lambda descends along -dJ^2/dlambda with step dtau_lambda */
+    double dtau;         /* fictitious time step > 0 (Sec. V.C.3) */
+    double dtau_lambda;  /* step of the lambda update (used when lambda_free) */
+    int32_t precision;   /* ks_precision: storage and transform arithmetic; reductions are FP64 */
+    int32_t adjoint;     /* ks_adjoint */
+    int32_t conv;        /* ks_conv */
+    int32_t check_ends;  /* 1: ks_curve_create fails with KS_ENOTEQUILIBRIUM when an end
+                            section has |f(u)|_2 > 1e-8 (1 + |u|_2); 0: no check */
+    int32_t reserved;    /* must be 0 */
+} ks_params;
+
+/* Scalars of the state most recently evaluated (cost, gradient or descent). */
+typedef struct {
+    double J;            /* sqrt(J^2), J^2 = sum_m w_m |r_m|^2 (eq. cost_function_general) */
+    double J_arc;        /* eq. J_arc */
+    double dJ2_dlambda;  /* -2 sum_m w_m <D_t u_m, r_m> */
+    double G_norm;       /* |G|_W of the last gradient evaluated */
+    double Dnorm;        /* |lambda D_t u|_W, for J / Dnorm */
+    double lambda;       /* current lambda */
+    double tau;          /* fictitious time reached */
+    int64_t step;        /* descent steps applied since create / set_state */
+    int32_t converged;   /* 1 once the tolerance of the last descend was met */
+    int32_t status;      /* ks_status of the device-side checks (KS_OK or KS_ENONFINITE) */
+} ks_scalars;
+
+typedef struct ks_curve ks_curve;
+
+/* Thread-local message of the last failure on this thread ("" if none). */
+const char *ks_last_error(void);
+
+/* Library version, (major << 16) | minor. */
+int32_t ks_version(void);
+
+/* Bytes of device workspace a curve with these parameters needs (0 if the
+ * parameters are invalid; ks_last_error() says why).  The workspace holds the
+ * spectral state, its s-derivative, the residual, the adjoint, the
+ * rational-Chebyshev tables (O(N_s)), the Fourier tables and the FP64
+ * reduction buffers: about 6 N_s N storage words in total.  No O(N_s^2)
+ * matrix is stored: D_t is generated from an O(N_s) table on the fly. */
+size_t ks_curve_workspace_bytes(const ks_params *p);
+
+/* Creates a curve (Sec. V.C.1-2).
+ *  p            parameters (copied).
+ *  u_plus_host  [N] physical u_+ (s -> +inf), u_minus_host [N] physical u_- (s -> -inf).
+ *  u_init_dev   [N_s][N] physical initial curve in the storage type, or NULL
+ *               for the trial curve of eq. KSE_initial_curve with a = 0
+ *               (use ks_curve_init_trial for a != 0 or a perturbation).
+ *               Rows 0 and N_s-1 of u_init_dev are replaced by u_+ and u_-.
+ *  workspace_dev, workspace_bytes: caller memory, >= ks_curve_workspace_bytes(p),
+ *               256-byte aligned; owned by the caller, used until ks_curve_destroy.
+ *  stream       cudaStream_t for all work of this curve (may be changed with
+ *               ks_curve_set_stream).
+ *  out          receives the handle.
+ * Errors: KS_EINVAL, KS_ENOMEM, KS_ECUDA, KS_ENOTEQUILIBRIUM (check_ends = 1).
+ * Synchronises the stream. */
+ks_status ks_curve_create(const ks_params *p, const double *u_plus_host, const double *u_minus_host,
+                          const void *u_init_dev, void *workspace_dev, size_t workspace_bytes,
+                          void *stream, ks_curve **out);
+
+ks_status ks_curve_set_stream(ks_curve *c, void *stream);
+
+/* Re-initialises the interior sections with the trial curve (eq. KSE_initial_curve):
+ *   u0(x, s_m) = 1/2[(1 + tanh s_m) u_+ + (1 - tanh s_m) u_-] + a exp(-s_m^2) v(x)
+ *               + sum_{p=1}^{npert} amps[p-1] sin(p theta_m) vp[p-1](x).
+ * The last sum is a perturbation that vanishes at both ends (npert = 0 gives the
+ * published form).  v_host [N] may be NULL when a = 0; vp_host is [npert][N];
+ * npert <= 16.  Resets step, tau and lambda (to p->lambda).  Synchronises. */
+ks_status ks_curve_init_trial(ks_curve *c, double a, const double *v_host, int32_t npert,
+                              const double *amps_host, const double *vp_host);
+
+/* Residual r = f(u) - lambda D_t u of the current state, physical [N_s][N] in
+ * the storage type (eq. KSE_residual); rows 0 and N_s-1 are 0.  Also refreshes
+ * J, J_arc, dJ2_dlambda and Dnorm of ks_curve_scalars.  Asynchronous. */
+ks_status ks_curve_residual(ks_curve *c, void *r_dev);
+
+/* J^2 (eq. cost_function_general) and J_arc (eq. J_arc) of the current state
+ * into host doubles (either may be NULL).  Synchronises. */
+ks_status ks_curve_cost(ks_curve *c, double *J2, double *J_arc);
+
+/* Gradient of the current state into g_dev, physical [N_s][N], storage type.
+ *  euclidean = 0: the descent direction G = -L^dagger(u; r) of the curve's
+ *                 adjoint mode (eq. KSE_G); rows 0 and N_s-1 are 0.
+ *  euclidean = 1: dJ^2/du_{m,n} of the discretised cost J^2 = sum_m w_m |r_m|^2
+ *                 with respect to the interior grid values, = -2 dx w_m G_DISCRETE;
+ *                 rows 0 and N_s-1 are 0 (the end sections are fixed).
+ *  dJ2_dlambda (host, may be NULL) receives dJ^2/dlambda.  Synchronises when
+ *  dJ2_dlambda is not NULL. */
+ks_status ks_curve_gradient(ks_curve *c, int32_t euclidean, void *g_dev, double *dJ2_dlambda);
+
+/* Runs up to nsteps descent steps (Sec. III, Sec. V.C.3) on the device:
+ * each step evaluates r and G of the current state and applies
+ *   u <- [u + dtau (G + a_j^2 u)] / (1 + dtau a_j^2),  a_j = k_j^4 - k_j^2,
+ * to the interior sections (the term -A^2 u of G, A = d_xx + d_xxxx, implicit),
+ * and, when lambda_free, lambda <- lambda - dtau_lambda dJ^2/dlambda.
+ * Stops early once the convergence measure of p->conv falls below tol
+ * (tol <= 0: never).  steps_done, J, J_arc (host, may be NULL) receive the
+ * steps applied and the cost of the final state.  Returns KS_ENOTCONV when
+ * tol > 0 was not reached, KS_ENONFINITE if the cost became NaN/Inf.
+ * Synchronises. */
+ks_status ks_curve_descend(ks_curve *c, int64_t nsteps, double tol, int64_t *steps_done, double *J,
+                           double *J_arc);
+
+/* Enqueues `nsteps` descent steps without synchronising or checking the
+ * tolerance on the host (the device still stops at convergence to tol).
+ * For timing loops and CUDA-graph capture by the caller. */
+ks_status ks_curve_descend_async(ks_curve *c, int64_t nsteps, double tol);
+
+/* Host copy of the scalars of the most recent evaluation.  Synchronises. */
+ks_status ks_curve_scalars(ks_curve *c, ks_scalars *out);
+
+/* Current state, physical [N_s][N] in the storage type (may be NULL), plus
+ * lambda and tau (host, may be NULL).  Synchronises when lambda or tau is
+ * requested. */
+ks_status ks_curve_get_state(ks_curve *c, void *u_dev, double *lambda, double *tau);
+
+/* Replaces the state (all rows, including the end sections) from a physical
+ * [N_s][N] array in the storage type, with lambda and tau; step is reset to 0.
+ * Asynchronous. */
+ks_status ks_curve_set_state(ks_curve *c, const void *u_dev, double lambda, double tau);
+
+/* Per-phase device time of the descent steps, measured with CUDA events
+ * recorded on the curve's stream around each kernel of a step:
+ *   phase 0: row phase (f, residual, spatial adjoint, cost reductions)
+ *   phase 1: s-phase with the descent update (D_t r, G, u update, |G|^2)
+ *   phase 2: s-phase D_t u of the new state.
+ * ks_curve_profile(c, max_steps) starts recording for up to max_steps steps
+ * (max_steps = 0 stops and releases the events); ks_curve_profile_read
+ * synchronises and returns the accumulated milliseconds and launch counts. */
+typedef struct {
+    double ms[3];
+    int64_t launches[3];
+} ks_profile;
+
+ks_status ks_curve_profile(ks_curve *c, int32_t max_steps);
+ks_status ks_curve_profile_read(ks_curve *c, ks_profile *out);
+
+/* Releases the handle (host memory only; the workspace stays the caller's). */
+ks_status ks_curve_destroy(ks_curve *c);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* KSCONN_H */

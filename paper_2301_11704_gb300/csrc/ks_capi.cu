@@ -1,0 +1,491 @@
+// ks_capi.cu -- the C ABI declared in include/ksconn.h: argument checks,
+// workspace layout, and the order of kernel launches for each entry point.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/ksconn.h"
+#include "ks_internal.h"
+
+namespace ks {
+cudaError_t launch_set_ends(const CurveDev &c, void *X, cudaStream_t st);
+}
+
+struct ks_curve {
+    ks_params p;
+    ks::Layout lay;
+    ks::CurveDev d;
+    cudaStream_t st;
+    int device;
+    // profiling: events[2*(3*step + phase)] / [.. + 1] bracket one kernel
+    std::vector<cudaEvent_t> events;
+    int prof_cap = 0;      // steps that fit in `events`
+    int prof_used = 0;     // steps recorded so far
+};
+
+static thread_local char g_err[512];
+
+static ks_status fail(ks_status s, const char *fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+    return s;
+}
+
+#define KS_CUDA(call)                                                                           \
+    do {                                                                                        \
+        cudaError_t e_ = (call);                                                                \
+        if (e_ != cudaSuccess) return fail(KS_ECUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+    } while (0)
+
+namespace {
+
+// Restores the caller's current device on scope exit.
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = true;
+    explicit DeviceGuard(int dev)
+    {
+        if (cudaGetDevice(&prev) != cudaSuccess) { ok = false; return; }
+        if (prev != dev && cudaSetDevice(dev) != cudaSuccess) ok = false;
+    }
+    ~DeviceGuard()
+    {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+bool is_pow2(int x) { return x > 0 && (x & (x - 1)) == 0; }
+
+ks_status validate(const ks_params *p)
+{
+    if (!p) return fail(KS_EINVAL, "params is NULL");
+    if (!(p->L > 0) || !std::isfinite(p->L)) return fail(KS_EINVAL, "L must be finite and > 0 (got %g)", p->L);
+    if (!is_pow2(p->nx) || p->nx < 8 || p->nx > 256)
+        return fail(KS_EINVAL, "nx must be a power of two in [8, 256] (got %d)", p->nx);
+    if (p->ns < 3 || p->ns > 65536) return fail(KS_EINVAL, "ns must be in [3, 65536] (got %d)", p->ns);
+    if (!(p->S > 0) || !std::isfinite(p->S)) return fail(KS_EINVAL, "S must be finite and > 0 (got %g)", p->S);
+    if (!std::isfinite(p->s0)) return fail(KS_EINVAL, "s0 must be finite");
+    if (!std::isfinite(p->lambda)) return fail(KS_EINVAL, "lambda must be finite");
+    if (!(p->dtau > 0) || !std::isfinite(p->dtau)) return fail(KS_EINVAL, "dtau must be finite and > 0 (got %g)", p->dtau);
+    if (!(p->dtau_lambda >= 0) || !std::isfinite(p->dtau_lambda)) return fail(KS_EINVAL, "dtau_lambda must be finite and >= 0");
+    if (p->lambda_free != 0 && p->lambda_free != 1) return fail(KS_EINVAL, "lambda_free must be 0 or 1");
+    if (p->precision != KS_FP64 && p->precision != KS_FP32) return fail(KS_EINVAL, "precision must be KS_FP64 or KS_FP32");
+    if (p->adjoint != KS_ADJ_PAPER && p->adjoint != KS_ADJ_DISCRETE) return fail(KS_EINVAL, "adjoint must be KS_ADJ_PAPER or KS_ADJ_DISCRETE");
+    if (p->conv < KS_CONV_JARC || p->conv > KS_CONV_JREL) return fail(KS_EINVAL, "conv must be a ks_conv value");
+    if (p->check_ends != 0 && p->check_ends != 1) return fail(KS_EINVAL, "check_ends must be 0 or 1");
+    if (p->reserved != 0) return fail(KS_EINVAL, "reserved must be 0");
+    return KS_OK;
+}
+
+ks::CurveDev make_dev(const ks_params *p, const ks::Layout &l, void *ws)
+{
+    ks::CurveDev d{};
+    char *b = (char *)ws;
+    d.ns = p->ns;
+    d.nx = p->nx;
+    d.P = p->ns - 1;
+    d.prec = p->precision == KS_FP32 ? 1 : 0;
+    d.L = p->L;
+    d.S = p->S;
+    d.s0 = p->s0;
+    d.U = b + l.off_U;
+    d.D = b + l.off_D;
+    d.R = b + l.off_R;
+    d.A = b + l.off_A;
+    d.G = b + l.off_G;
+    d.X = b + l.off_X;
+    d.rowsc = (double *)(b + l.off_rowsc);
+    d.tile = (double *)(b + l.off_tile);
+    d.cot = b + l.off_cot;
+    d.sig = b + l.off_sig;
+    d.tau = b + l.off_tau;
+    d.sw = b + l.off_sw;
+    d.twr = b + l.off_twr;
+    d.w = (double *)(b + l.off_w);
+    d.twid = b + l.off_twid;
+    d.kj = b + l.off_kj;
+    d.aj = b + l.off_aj;
+    d.prec_imex = b + l.off_prec;
+    d.ends = (double *)(b + l.off_ends);
+    d.pert = (double *)(b + l.off_pert);
+    d.sc = (ks::DevScalars *)(b + l.off_sc);
+    return d;
+}
+
+ks_status check_handle(ks_curve *c)
+{
+    if (!c) return fail(KS_EINVAL, "curve handle is NULL");
+    return KS_OK;
+}
+
+// D_t u of the current state (kept in the workspace for the next evaluation).
+ks_status refresh_dt_u(ks_curve *c)
+{
+    KS_CUDA(ks::launch_dt(c->d, ks::GM_STORE, 0, 0, c->st));
+    return KS_OK;
+}
+
+ks_status read_scalars(ks_curve *c, ks::DevScalars *h)
+{
+    KS_CUDA(cudaMemcpyAsync(h, c->d.sc, sizeof(*h), cudaMemcpyDeviceToHost, c->st));
+    KS_CUDA(cudaStreamSynchronize(c->st));
+    return KS_OK;
+}
+
+ks_status enqueue_steps(ks_curve *c, int64_t nsteps, double tol)
+{
+    const int discrete = c->p.adjoint == KS_ADJ_DISCRETE;
+    KS_CUDA(ks::launch_set_limit(c->d, (long long)nsteps, tol, c->st));
+    for (int64_t s = 0; s < nsteps; ++s) {
+        const bool prof = c->prof_used < c->prof_cap;
+        cudaEvent_t *ev = prof ? &c->events[(size_t)6 * c->prof_used] : nullptr;
+        if (prof) KS_CUDA(cudaEventRecord(ev[0], c->st));
+        KS_CUDA(ks::launch_rows(c->d, ks::ROWS_STEP, c->st));
+        if (prof) KS_CUDA(cudaEventRecord(ev[1], c->st));
+        if (prof) KS_CUDA(cudaEventRecord(ev[2], c->st));
+        KS_CUDA(ks::launch_dt(c->d, ks::GM_UPDATE, discrete, 1, c->st));
+        if (prof) KS_CUDA(cudaEventRecord(ev[3], c->st));
+        if (prof) KS_CUDA(cudaEventRecord(ev[4], c->st));
+        KS_CUDA(ks::launch_dt(c->d, ks::GM_STORE, 0, 1, c->st));
+        if (prof) {
+            KS_CUDA(cudaEventRecord(ev[5], c->st));
+            c->prof_used++;
+        }
+    }
+    return KS_OK;
+}
+
+void release_events(ks_curve *c)
+{
+    for (cudaEvent_t e : c->events) cudaEventDestroy(e);
+    c->events.clear();
+    c->prof_cap = 0;
+    c->prof_used = 0;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *ks_last_error(void) { return g_err; }
+
+int32_t ks_version(void) { return (1 << 16) | 0; }
+
+size_t ks_curve_workspace_bytes(const ks_params *p)
+{
+    if (validate(p) != KS_OK) return 0;
+    return ks::make_layout(p->ns, p->nx, p->precision == KS_FP32).total;
+}
+
+ks_status ks_curve_create(const ks_params *p, const double *u_plus_host, const double *u_minus_host,
+                          const void *u_init_dev, void *workspace_dev, size_t workspace_bytes, void *stream,
+                          ks_curve **out)
+{
+    g_err[0] = 0;
+    ks_status s = validate(p);
+    if (s != KS_OK) return s;
+    if (!out) return fail(KS_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!u_plus_host || !u_minus_host) return fail(KS_EINVAL, "u_plus_host and u_minus_host are required");
+    if (!workspace_dev) return fail(KS_EINVAL, "workspace_dev is NULL");
+    if (((uintptr_t)workspace_dev) & 255) return fail(KS_EINVAL, "workspace_dev must be 256-byte aligned");
+    for (int n = 0; n < p->nx; ++n)
+        if (!std::isfinite(u_plus_host[n]) || !std::isfinite(u_minus_host[n]))
+            return fail(KS_EINVAL, "u_plus/u_minus contain non-finite values");
+    ks::Layout lay = ks::make_layout(p->ns, p->nx, p->precision == KS_FP32);
+    if (workspace_bytes < lay.total)
+        return fail(KS_ENOMEM, "workspace has %zu bytes, %zu needed", workspace_bytes, lay.total);
+
+    ks_curve *c = new (std::nothrow) ks_curve();
+    if (!c) return fail(KS_ENOMEM, "host allocation of the handle failed");
+    c->p = *p;
+    c->lay = lay;
+    c->d = make_dev(p, lay, workspace_dev);
+    c->st = (cudaStream_t)stream;
+    if (cudaGetDevice(&c->device) != cudaSuccess) {
+        delete c;
+        return fail(KS_ECUDA, "cudaGetDevice failed");
+    }
+    ks_status r = KS_OK;
+    do {
+        const size_t nb = (size_t)p->nx * sizeof(double);
+        if (cudaMemcpyAsync(c->d.ends, u_plus_host, nb, cudaMemcpyHostToDevice, c->st) != cudaSuccess ||
+            cudaMemcpyAsync(c->d.ends + p->nx, u_minus_host, nb, cudaMemcpyHostToDevice, c->st) != cudaSuccess ||
+            cudaMemsetAsync(c->d.pert, 0, (size_t)(p->nx + ks::MAX_PERT + ks::MAX_PERT * p->nx) * 8, c->st) != cudaSuccess) {
+            r = fail(KS_ECUDA, "copy of the end sections failed: %s", cudaGetErrorString(cudaGetLastError()));
+            break;
+        }
+        cudaError_t e = ks::launch_setup(c->d, p->dtau, c->st);
+        if (e == cudaSuccess)
+            e = ks::launch_scalars_init(c->d, p->lambda, p->lambda_free, p->dtau, p->dtau_lambda, p->conv, c->st);
+        if (e == cudaSuccess) {
+            if (u_init_dev) {
+                size_t bytes = (size_t)p->ns * p->nx * (p->precision == KS_FP32 ? 4 : 8);
+                e = cudaMemcpyAsync(c->d.X, u_init_dev, bytes, cudaMemcpyDeviceToDevice, c->st);
+                if (e == cudaSuccess) e = ks::launch_set_ends(c->d, c->d.X, c->st);
+            } else {
+                e = ks::launch_trial(c->d, 0.0, 0, 0, c->st);
+            }
+        }
+        if (e == cudaSuccess) e = ks::launch_row_fwd(c->d, c->d.X, c->d.U, 0, c->st);
+        if (e == cudaSuccess) e = ks::launch_dt(c->d, ks::GM_STORE, 0, 0, c->st);
+        if (e == cudaSuccess && p->check_ends) e = ks::launch_rows(c->d, ks::ROWS_EVAL, c->st);
+        if (e != cudaSuccess) {
+            r = fail(KS_ECUDA, "set-up kernels failed: %s", cudaGetErrorString(e));
+            break;
+        }
+        ks::DevScalars h;
+        r = read_scalars(c, &h);
+        if (r != KS_OK) break;
+        if (p->check_ends) {
+            double fp = std::sqrt(h.f2_plus), fm = std::sqrt(h.f2_minus);
+            double up = std::sqrt(h.u2_plus), um = std::sqrt(h.u2_minus);
+            if (fp > 1e-8 * (1.0 + up) || fm > 1e-8 * (1.0 + um)) {
+                r = fail(KS_ENOTEQUILIBRIUM, "end sections are not equilibria: |f(u_+)| = %.3e, |f(u_-)| = %.3e", fp, fm);
+                break;
+            }
+        }
+    } while (0);
+    if (r != KS_OK) {
+        delete c;
+        return r;
+    }
+    *out = c;
+    return KS_OK;
+}
+
+ks_status ks_curve_set_stream(ks_curve *c, void *stream)
+{
+    ks_status s = check_handle(c);
+    if (s != KS_OK) return s;
+    c->st = (cudaStream_t)stream;
+    return KS_OK;
+}
+
+ks_status ks_curve_init_trial(ks_curve *c, double a, const double *v_host, int32_t npert, const double *amps_host,
+                              const double *vp_host)
+{
+    ks_status s = check_handle(c);
+    if (s != KS_OK) return s;
+    if (npert < 0 || npert > ks::MAX_PERT) return fail(KS_EINVAL, "npert must be in [0, %d]", ks::MAX_PERT);
+    if (npert > 0 && (!amps_host || !vp_host)) return fail(KS_EINVAL, "amps_host and vp_host are required when npert > 0");
+    if (a != 0.0 && !v_host) return fail(KS_EINVAL, "v_host is required when a != 0");
+    if (!std::isfinite(a)) return fail(KS_EINVAL, "a must be finite");
+    DeviceGuard g(c->device);
+    if (!g.ok) return fail(KS_ECUDA, "cannot select the curve's device");
+    const int N = c->p.nx;
+    if (v_host) KS_CUDA(cudaMemcpyAsync(c->d.pert, v_host, N * 8, cudaMemcpyHostToDevice, c->st));
+    if (npert > 0) {
+        KS_CUDA(cudaMemcpyAsync(c->d.pert + N, amps_host, npert * 8, cudaMemcpyHostToDevice, c->st));
+        KS_CUDA(cudaMemcpyAsync(c->d.pert + N + ks::MAX_PERT, vp_host, (size_t)npert * N * 8, cudaMemcpyHostToDevice, c->st));
+    }
+    KS_CUDA(ks::launch_trial(c->d, a, v_host != nullptr && a != 0.0, npert, c->st));
+    KS_CUDA(ks::launch_row_fwd(c->d, c->d.X, c->d.U, 0, c->st));
+    s = refresh_dt_u(c);
+    if (s != KS_OK) return s;
+    KS_CUDA(ks::launch_scalars_init(c->d, c->p.lambda, c->p.lambda_free, c->p.dtau, c->p.dtau_lambda, c->p.conv, c->st));
+    KS_CUDA(cudaStreamSynchronize(c->st));
+    return KS_OK;
+}
+
+ks_status ks_curve_residual(ks_curve *c, void *r_dev)
+{
+    ks_status s = check_handle(c);
+    if (s != KS_OK) return s;
+    if (!r_dev) return fail(KS_EINVAL, "r_dev is NULL");
+    DeviceGuard g(c->device);
+    if (!g.ok) return fail(KS_ECUDA, "cannot select the curve's device");
+    KS_CUDA(ks::launch_rows(c->d, ks::ROWS_EVAL, c->st));
+    KS_CUDA(ks::launch_row_inv(c->d, c->d.R, r_dev, 0, c->st));
+    return KS_OK;
+}
+
+ks_status ks_curve_cost(ks_curve *c, double *J2, double *J_arc)
+{
+    ks_status s = check_handle(c);
+    if (s != KS_OK) return s;
+    DeviceGuard g(c->device);
+    if (!g.ok) return fail(KS_ECUDA, "cannot select the curve's device");
+    KS_CUDA(ks::launch_rows(c->d, ks::ROWS_EVAL, c->st));
+    ks::DevScalars h;
+    s = read_scalars(c, &h);
+    if (s != KS_OK) return s;
+    if (J2) *J2 = h.J2;
+    if (J_arc) *J_arc = h.Jarc;
+    return KS_OK;
+}
+
+ks_status ks_curve_gradient(ks_curve *c, int32_t euclidean, void *g_dev, double *dJ2_dlambda)
+{
+    ks_status s = check_handle(c);
+    if (s != KS_OK) return s;
+    if (!g_dev) return fail(KS_EINVAL, "g_dev is NULL");
+    if (euclidean != 0 && euclidean != 1) return fail(KS_EINVAL, "euclidean must be 0 or 1");
+    DeviceGuard g(c->device);
+    if (!g.ok) return fail(KS_ECUDA, "cannot select the curve's device");
+    const int discrete = euclidean ? 1 : (c->p.adjoint == KS_ADJ_DISCRETE);
+    KS_CUDA(ks::launch_rows(c->d, ks::ROWS_EVAL, c->st));
+    KS_CUDA(ks::launch_dt(c->d, ks::GM_GRAD, discrete, 0, c->st));
+    KS_CUDA(ks::launch_row_inv(c->d, c->d.G, g_dev, euclidean ? 1 : 0, c->st));
+    if (dJ2_dlambda) {
+        ks::DevScalars h;
+        s = read_scalars(c, &h);
+        if (s != KS_OK) return s;
+        *dJ2_dlambda = h.dJdl;
+    }
+    return KS_OK;
+}
+
+ks_status ks_curve_descend_async(ks_curve *c, int64_t nsteps, double tol)
+{
+    ks_status s = check_handle(c);
+    if (s != KS_OK) return s;
+    if (nsteps < 0) return fail(KS_EINVAL, "nsteps must be >= 0");
+    if (!std::isfinite(tol)) return fail(KS_EINVAL, "tol must be finite");
+    DeviceGuard g(c->device);
+    if (!g.ok) return fail(KS_ECUDA, "cannot select the curve's device");
+    return enqueue_steps(c, nsteps, tol);
+}
+
+ks_status ks_curve_descend(ks_curve *c, int64_t nsteps, double tol, int64_t *steps_done, double *J, double *J_arc)
+{
+    ks_status s = check_handle(c);
+    if (s != KS_OK) return s;
+    if (nsteps < 0) return fail(KS_EINVAL, "nsteps must be >= 0");
+    if (!std::isfinite(tol)) return fail(KS_EINVAL, "tol must be finite");
+    DeviceGuard g(c->device);
+    if (!g.ok) return fail(KS_ECUDA, "cannot select the curve's device");
+    ks::DevScalars h0;
+    s = read_scalars(c, &h0);
+    if (s != KS_OK) return s;
+    s = enqueue_steps(c, nsteps, tol);
+    if (s != KS_OK) return s;
+    KS_CUDA(ks::launch_rows(c->d, ks::ROWS_EVAL, c->st));
+    ks::DevScalars h;
+    s = read_scalars(c, &h);
+    if (s != KS_OK) return s;
+    if (steps_done) *steps_done = h.step - h0.step;
+    if (J) *J = std::sqrt(h.J2);
+    if (J_arc) *J_arc = h.Jarc;
+    if (h.status == KS_ENONFINITE || !std::isfinite(h.J2))
+        return fail(KS_ENONFINITE, "the cost became non-finite after %lld steps", (long long)(h.step - h0.step));
+    if (tol > 0 && !h.done) return fail(KS_ENOTCONV, "tolerance %.3e not reached in %lld steps", tol, (long long)nsteps);
+    return KS_OK;
+}
+
+ks_status ks_curve_scalars(ks_curve *c, ks_scalars *out)
+{
+    ks_status s = check_handle(c);
+    if (s != KS_OK) return s;
+    if (!out) return fail(KS_EINVAL, "out is NULL");
+    DeviceGuard g(c->device);
+    if (!g.ok) return fail(KS_ECUDA, "cannot select the curve's device");
+    ks::DevScalars h;
+    s = read_scalars(c, &h);
+    if (s != KS_OK) return s;
+    out->J = std::sqrt(h.J2);
+    out->J_arc = h.Jarc;
+    out->dJ2_dlambda = h.dJdl;
+    out->G_norm = std::sqrt(h.G2);
+    out->Dnorm = h.Dnorm;
+    out->lambda = h.lambda;
+    out->tau = h.tau;
+    out->step = h.step;
+    out->converged = h.done && h.status == 0;
+    out->status = h.status;
+    return KS_OK;
+}
+
+ks_status ks_curve_get_state(ks_curve *c, void *u_dev, double *lambda, double *tau)
+{
+    ks_status s = check_handle(c);
+    if (s != KS_OK) return s;
+    DeviceGuard g(c->device);
+    if (!g.ok) return fail(KS_ECUDA, "cannot select the curve's device");
+    if (u_dev) KS_CUDA(ks::launch_row_inv(c->d, c->d.U, u_dev, 0, c->st));
+    if (lambda || tau) {
+        ks::DevScalars h;
+        s = read_scalars(c, &h);
+        if (s != KS_OK) return s;
+        if (lambda) *lambda = h.lambda;
+        if (tau) *tau = h.tau;
+    }
+    return KS_OK;
+}
+
+ks_status ks_curve_set_state(ks_curve *c, const void *u_dev, double lambda, double tau)
+{
+    ks_status s = check_handle(c);
+    if (s != KS_OK) return s;
+    if (!u_dev) return fail(KS_EINVAL, "u_dev is NULL");
+    if (!std::isfinite(lambda) || !std::isfinite(tau)) return fail(KS_EINVAL, "lambda and tau must be finite");
+    DeviceGuard g(c->device);
+    if (!g.ok) return fail(KS_ECUDA, "cannot select the curve's device");
+    KS_CUDA(ks::launch_row_fwd(c->d, u_dev, c->d.U, 0, c->st));
+    s = refresh_dt_u(c);
+    if (s != KS_OK) return s;
+    KS_CUDA(ks::launch_set_lambda_tau(c->d, lambda, tau, c->st));
+    return KS_OK;
+}
+
+ks_status ks_curve_profile(ks_curve *c, int32_t max_steps)
+{
+    ks_status s = check_handle(c);
+    if (s != KS_OK) return s;
+    if (max_steps < 0 || max_steps > (1 << 20)) return fail(KS_EINVAL, "max_steps must be in [0, 2^20]");
+    DeviceGuard g(c->device);
+    if (!g.ok) return fail(KS_ECUDA, "cannot select the curve's device");
+    KS_CUDA(cudaStreamSynchronize(c->st));
+    release_events(c);
+    c->events.resize((size_t)6 * max_steps);
+    for (size_t i = 0; i < c->events.size(); ++i) {
+        if (cudaEventCreate(&c->events[i]) != cudaSuccess) {
+            c->events.resize(i);
+            release_events(c);
+            return fail(KS_ECUDA, "cudaEventCreate failed");
+        }
+    }
+    c->prof_cap = max_steps;
+    return KS_OK;
+}
+
+ks_status ks_curve_profile_read(ks_curve *c, ks_profile *out)
+{
+    ks_status s = check_handle(c);
+    if (s != KS_OK) return s;
+    if (!out) return fail(KS_EINVAL, "out is NULL");
+    DeviceGuard g(c->device);
+    if (!g.ok) return fail(KS_ECUDA, "cannot select the curve's device");
+    KS_CUDA(cudaStreamSynchronize(c->st));
+    for (int ph = 0; ph < 3; ++ph) {
+        out->ms[ph] = 0.0;
+        out->launches[ph] = 0;
+    }
+    for (int st = 0; st < c->prof_used; ++st)
+        for (int ph = 0; ph < 3; ++ph) {
+            float ms = 0.f;
+            KS_CUDA(cudaEventElapsedTime(&ms, c->events[(size_t)6 * st + 2 * ph], c->events[(size_t)6 * st + 2 * ph + 1]));
+            out->ms[ph] += ms;
+            out->launches[ph] += 1;
+        }
+    return KS_OK;
+}
+
+ks_status ks_curve_destroy(ks_curve *c)
+{
+    if (!c) return KS_OK;
+    {
+        DeviceGuard g(c->device);
+        release_events(c);
+    }
+    delete c;
+    return KS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,88 @@
+// ks_internal.h -- declarations shared by the kernels (ks_kernels.cu) and the
+// C-ABI host code (ks_capi.cu).  Not part of the public interface.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+namespace ks {
+
+// Tile of the structured s-direction contraction (D_t or D_t^T applied to the
+// columns of a curve).  BM output sections x BN real columns per CTA, BK
+// sections of the contraction per shared-memory stage.
+constexpr int GEMM_BM = 32;
+constexpr int GEMM_BN = 32;
+constexpr int GEMM_BK = 32;
+constexpr int GEMM_THREADS = 256;
+
+// Sections handled per CTA by the row (x-direction) kernels: two rows per warp,
+// packed into one complex FFT.
+constexpr int ROWS_WARPS = 4;
+constexpr int ROWS_PER_CTA = 2 * ROWS_WARPS;
+
+constexpr int MAX_PERT = 16;
+
+// Device-resident scalars of one curve.  Written only by device code during a
+// descent (single writer per field: the last CTA of a kernel), read by the host
+// after a stream synchronisation.
+struct DevScalars {
+    double J2, Jarc, dJdl, Dnorm, G2;   // of the last evaluated state
+    double lambda, lambda_next, tau;
+    double f2_plus, f2_minus;           // |f(u_+)|^2, |f(u_-)|^2 (spatial norm)
+    double u2_plus, u2_minus;           // |u_+|^2, |u_-|^2
+    double tol, dtau, dtau_lambda;
+    long long step, limit;
+    int done, active, status, conv;
+    int lambda_free, pad0;
+    unsigned int cnt_rows, cnt_gemm;    // arrival counters of the last-CTA reductions
+};
+
+// Gates of the kernels of one descent step:
+//   rows kernel:   skip when done or step >= limit (clears `active`)
+//   gemm kernels:  skip when !active
+enum RowsMode { ROWS_STEP = 0, ROWS_EVAL = 1 };
+enum GemmMode { GM_STORE = 0, GM_UPDATE = 1, GM_GRAD = 2 };
+
+// Pointers into the caller's workspace (typed as void* for the storage type).
+struct Layout {
+    size_t off_U, off_D, off_R, off_A, off_G, off_X;
+    size_t off_rowsc, off_tile, off_cot, off_sig, off_tau, off_sw, off_twr, off_w;
+    size_t off_twid, off_kj, off_aj, off_prec, off_ends, off_pert, off_sc;
+    size_t total;
+    int max_tiles;
+};
+
+struct CurveDev {
+    int ns, nx, P, prec;   // prec: 0 = double, 1 = float
+    double L, S, s0;
+    void *U, *D, *R, *A, *G, *X;
+    double *rowsc, *tile;
+    void *cot, *sig, *tau, *sw, *twr;
+    double *w;
+    void *twid, *kj, *aj, *prec_imex;
+    double *ends, *pert;
+    DevScalars *sc;
+};
+
+Layout make_layout(int ns, int nx, int prec);
+
+// ---- launchers (ks_kernels.cu); all enqueue on `st`, return the launch error
+cudaError_t launch_setup(const CurveDev &c, double dtau, cudaStream_t st);
+cudaError_t launch_scalars_init(const CurveDev &c, double lambda, int lambda_free, double dtau,
+                                double dtau_lambda, int conv, cudaStream_t st);
+cudaError_t launch_set_limit(const CurveDev &c, long long nsteps, double tol, cudaStream_t st);
+cudaError_t launch_set_lambda_tau(const CurveDev &c, double lambda, double tau, cudaStream_t st);
+cudaError_t launch_trial(const CurveDev &c, double a, int has_v, int npert, cudaStream_t st);
+cudaError_t launch_row_fwd(const CurveDev &c, const void *phys, void *spec, int keep_ends, cudaStream_t st);
+// spec -> phys; scale_mode 0: plain; 1: Euclidean gradient scaling -2 dx w_m
+// and zero end rows.
+cudaError_t launch_row_inv(const CurveDev &c, const void *spec, void *phys, int scale_mode, cudaStream_t st);
+cudaError_t launch_rows(const CurveDev &c, int mode, cudaStream_t st);
+// Structured contraction along s.  op 0: D_t (columns scaled by tau, rows by
+// sigma), op 1: W^-1 D_t^T W.  mode GM_STORE writes D_t U into D (gated when
+// `gate`), GM_UPDATE applies the descent update to U, GM_GRAD writes G.
+cudaError_t launch_dt(const CurveDev &c, int mode, int discrete, int gate, cudaStream_t st);
+
+}  // namespace ks

@@ -1,0 +1,850 @@
+// ks_kernels.cu -- sm_103a kernels of one adjoint-descent step for a curve of
+// KSE states (Ashtari & Schneider, arXiv 2301.11704).
+//
+// Data layout (every field): row-major [N_s][N] real words of the storage type T.
+// Row m holds section s_m spectrally: N/2 complex Fourier coefficients
+// u^_{m,j}, j = 0..N/2-1, interleaved (re, im); the Nyquist coefficient is not
+// stored (held at zero) and Im u^_{m,0} = 0.  Row 0 is s = +inf, row N_s-1 is
+// s = -inf (eq. t_grid).
+//
+// One descent step is three kernels:
+//   k_rows  (x-direction, one warp per pair of sections): f(u), r = f - l D_t u,
+//           the spatial adjoint (Df)^T r = u r_x - r_xx - r_xxxx, FP64 row sums,
+//           and in its last CTA the FP64 cost, J_arc, dJ^2/dl and the
+//           convergence decision.
+//   k_dt    (s-direction): e = l D_t r^ (or -l W^-1 D_t^T W r^), G = -(A + e)
+//           and the semi-implicit update of u, FP64 |G|^2; then
+//   k_dt    again: D_t u of the new state, kept for the next step.
+// D_t (eq. rational_diff_matrix) is never stored: its entries are
+//   D_{j,m} = sigma_j (cot[(j+m) mod 2P] + cot[(j-m) mod 2P]) tau_m,
+//   sigma_j = -(-1)^j sin^2(j pi/P) / (2S),  tau_m = (-1)^m / cbar_m,
+//   cot[t] = cot(pi t / (2P)), cot[0] = 0,  P = M + 1,
+// the closed form of the k-sum in eq. rational_diff_matrix, generated per tile
+// from an O(N_s) table.
+#include <cmath>
+#include <type_traits>
+
+#include "ks_internal.h"
+
+namespace ks {
+
+template <typename T>
+struct cpx {
+    T x, y;
+};
+
+template <typename T>
+__device__ __forceinline__ cpx<T> cmul(cpx<T> a, cpx<T> b)
+{
+    return {a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x};
+}
+
+// ---------------------------------------------------------------------------
+// Layout of the workspace
+// ---------------------------------------------------------------------------
+static size_t al256(size_t x) { return (x + 255) & ~size_t(255); }
+
+Layout make_layout(int ns, int nx, int prec)
+{
+    Layout l{};
+    size_t b = prec ? 4 : 8;
+    size_t field = al256((size_t)ns * nx * b);
+    size_t off = 0;
+    l.off_U = off; off += field;
+    l.off_D = off; off += field;
+    l.off_R = off; off += field;
+    l.off_A = off; off += field;
+    l.off_G = off; off += field;
+    l.off_X = off; off += field;
+    l.off_rowsc = off; off += al256((size_t)ns * 4 * 8);
+    l.max_tiles = ((ns + GEMM_BM - 1) / GEMM_BM) * ((nx + GEMM_BN - 1) / GEMM_BN);
+    l.off_tile = off; off += al256((size_t)l.max_tiles * 8);
+    int P = ns - 1;
+    l.off_cot = off; off += al256((size_t)2 * P * b);
+    l.off_sig = off; off += al256((size_t)ns * b);
+    l.off_tau = off; off += al256((size_t)ns * b);
+    l.off_sw = off; off += al256((size_t)ns * b);
+    l.off_twr = off; off += al256((size_t)ns * b);
+    l.off_w = off; off += al256((size_t)ns * 8);
+    l.off_twid = off; off += al256((size_t)nx * b);   // N/2 complex
+    l.off_kj = off; off += al256((size_t)(nx / 2) * b);
+    l.off_aj = off; off += al256((size_t)(nx / 2) * b);
+    l.off_prec = off; off += al256((size_t)(nx / 2) * b);
+    l.off_ends = off; off += al256((size_t)2 * nx * 8);
+    l.off_pert = off; off += al256((size_t)(nx + MAX_PERT + MAX_PERT * nx) * 8);
+    l.off_sc = off; off += al256(sizeof(DevScalars));
+    l.total = off;
+    return l;
+}
+
+// ---------------------------------------------------------------------------
+// Warp-level FFT on shared memory
+// ---------------------------------------------------------------------------
+// Stockham radix-2 FFT of length N by one warp: natural order in and out, no
+// bit reversal.  tw[t] = exp(-2 pi i t / N), t < N/2.  Forward uses exp(-...),
+// inverse exp(+...); neither scales.  Returns the buffer holding the result
+// (x or y); the other one is free scratch.
+template <typename T, int N>
+__device__ __forceinline__ cpx<T> *warp_fft(cpx<T> *x, cpx<T> *y, const cpx<T> *tw, bool inverse, int lane)
+{
+#pragma unroll
+    for (int ns = 1; ns < N; ns <<= 1) {
+#pragma unroll
+        for (int j = lane; j < N / 2; j += 32) {
+            int k = j & (ns - 1);
+            cpx<T> a = x[j], b = x[j + N / 2];
+            cpx<T> w = tw[k * (N / (2 * ns))];
+            if (inverse) w.y = -w.y;
+            b = cmul(b, w);
+            int o = ((j - k) << 1) + k;
+            y[o] = {a.x + b.x, a.y + b.y};
+            y[o + ns] = {a.x - b.x, a.y - b.y};
+        }
+        __syncwarp();
+        cpx<T> *t = x;
+        x = y;
+        y = t;
+    }
+    return x;
+}
+
+// Full spectrum of z = a + i b for two real sections given by their half spectra
+// (j = 0..N/2-1, Nyquist zero):  Z_j = A_j + i B_j,  Z_{N-j} = conj(A_j) + i conj(B_j).
+template <typename T, int N>
+__device__ __forceinline__ void put_pair(cpx<T> *Z, int j, cpx<T> A, cpx<T> B)
+{
+    Z[j] = {A.x - B.y, A.y + B.x};
+    if (j > 0) Z[N - j] = {A.x + B.y, B.x - A.y};
+}
+
+// Half spectra of two real sections from the FFT W of z = a + i b, with the
+// 1/N of the forward transform:  A_j = (W_j + conj W_{N-j}) / 2N,
+// B_j = (W_j - conj W_{N-j}) / 2iN.
+template <typename T, int N>
+__device__ __forceinline__ void get_pair(const cpx<T> *W, int j, cpx<T> &A, cpx<T> &B)
+{
+    cpx<T> wj = W[j], wn = W[(N - j) & (N - 1)];
+    const T h = T(0.5) / T(N);
+    A = {(wj.x + wn.x) * h, (wj.y - wn.y) * h};
+    B = {(wj.y + wn.y) * h, (wn.x - wj.x) * h};
+    if (j == 0) { A.y = 0; B.y = 0; }
+}
+
+template <typename T>
+__device__ __forceinline__ cpx<T> ld2(const T *p, int m, int N, int j)
+{
+    const T *q = p + (size_t)m * N + 2 * j;
+    return {q[0], j == 0 ? T(0) : q[1]};
+}
+
+template <typename T>
+__device__ __forceinline__ void st2(T *p, int m, int N, int j, cpx<T> v)
+{
+    T *q = p + (size_t)m * N + 2 * j;
+    q[0] = v.x;
+    q[1] = (j == 0) ? T(0) : v.y;
+}
+
+__device__ __forceinline__ double warp_sum(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Fixed-order block reduction (deterministic for a fixed blockDim).
+template <int NT>
+__device__ __forceinline__ double block_sum(double v, double *red)
+{
+    red[threadIdx.x] = v;
+    __syncthreads();
+#pragma unroll
+    for (int s = NT / 2; s > 0; s >>= 1) {
+        if ((int)threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+        __syncthreads();
+    }
+    double r = red[0];
+    __syncthreads();
+    return r;
+}
+
+// ---------------------------------------------------------------------------
+// Set-up: rational-Chebyshev tables (eq. t_grid, eq. c_bar, eq. rational_diff_matrix),
+// quadrature weights and Fourier tables, all evaluated in FP64 from integer indices.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void k_setup(CurveDev c, double dtau)
+{
+    const int P = c.P, ns = c.ns, H = c.nx / 2;
+    T *cot = (T *)c.cot, *sig = (T *)c.sig, *tau = (T *)c.tau, *sw = (T *)c.sw, *twr = (T *)c.twr;
+    cpx<T> *twid = (cpx<T> *)c.twid;
+    T *kj = (T *)c.kj, *aj = (T *)c.aj, *pr = (T *)c.prec_imex;
+    int total = max(2 * P, max(ns, H));
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
+        if (i < 2 * P) {
+            double v = 0.0;
+            if (i != 0) {
+                double s, co;
+                sincospi((double)i / (2.0 * P), &s, &co);
+                v = co / s;
+            }
+            cot[i] = (T)v;
+        }
+        if (i < ns) {
+            double s, co;
+            sincospi((double)i / (double)P, &s, &co);
+            double sn2 = s * s;
+            double sgn = (i & 1) ? -1.0 : 1.0;
+            bool end = (i == 0 || i == P);
+            double cb = end ? 2.0 : 1.0;
+            sig[i] = (T)(-sgn * sn2 / (2.0 * c.S));
+            tau[i] = (T)(sgn / cb);
+            c.w[i] = end ? 0.0 : (M_PI / (double)P) * c.S / sn2;
+            sw[i] = end ? T(0) : (T)(-sgn * M_PI / (2.0 * P));               // sigma_i w_i
+            twr[i] = end ? T(0) : (T)(sgn * sn2 * (double)P / (M_PI * c.S));  // tau_i / w_i
+        }
+        if (i < H) {
+            double s, co;
+            sincospi(2.0 * (double)i / (double)c.nx, &s, &co);
+            twid[i] = {(T)co, (T)(-s)};
+            double k = 2.0 * M_PI * (double)i / c.L;
+            double a = k * k * k * k - k * k;
+            kj[i] = (T)k;
+            aj[i] = (T)a;
+            pr[i] = (T)(1.0 / (1.0 + dtau * a * a));
+        }
+    }
+}
+
+__global__ void k_scalars_init(DevScalars *sc, double lambda, int lambda_free, double dtau,
+                               double dtau_lambda, int conv)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        DevScalars z{};
+        z.lambda = lambda;
+        z.lambda_next = lambda;
+        z.lambda_free = lambda_free;
+        z.dtau = dtau;
+        z.dtau_lambda = dtau_lambda;
+        z.conv = conv;
+        z.limit = 0;
+        *sc = z;
+    }
+}
+
+__global__ void k_set_limit(DevScalars *sc, long long nsteps, double tol)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        sc->limit = sc->step + nsteps;
+        sc->tol = tol;
+        sc->done = 0;
+        sc->status = 0;
+        sc->active = 0;
+    }
+}
+
+__global__ void k_set_lambda_tau(DevScalars *sc, double lambda, double tau)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        sc->lambda = lambda;
+        sc->lambda_next = lambda;
+        sc->tau = tau;
+        sc->step = 0;
+        sc->limit = 0;
+        sc->done = 0;
+        sc->status = 0;
+    }
+}
+
+// Trial curve (eq. KSE_initial_curve) on the grid, physical, into X:
+//   u0 = 1/2[(1 + tanh s_m) u_+ + (1 - tanh s_m) u_-] + a exp(-s_m^2) v
+//        + sum_p amps_p sin(p theta_m) vp_p ;   rows 0 and P are u_+ and u_-.
+template <typename T>
+__global__ void k_trial(CurveDev c, double a, int has_v, int npert)
+{
+    const int ns = c.ns, N = c.nx, P = c.P;
+    const double *up = c.ends, *um = c.ends + N;
+    const double *v = c.pert, *amps = c.pert + N, *vp = c.pert + N + MAX_PERT;
+    T *X = (T *)c.X;
+    size_t total = (size_t)ns * N;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+        int m = (int)(i / N), n = (int)(i % N);
+        double val;
+        if (m == 0) {
+            val = up[n];
+        } else if (m == P) {
+            val = um[n];
+        } else {
+            double s, co;
+            sincospi((double)m / (double)P, &s, &co);
+            double sm = c.s0 + c.S * co / s;
+            double t = tanh(sm);
+            val = 0.5 * ((1.0 + t) * up[n] + (1.0 - t) * um[n]);
+            if (has_v) val += a * exp(-sm * sm) * v[n];
+            for (int p = 0; p < npert; ++p) {
+                double sp, cp;
+                long long idx = ((long long)(p + 1) * m) % (2LL * P);
+                sincospi((double)idx / (double)P, &sp, &cp);
+                val += amps[p] * sp * vp[(size_t)p * N + n];
+            }
+        }
+        X[i] = (T)val;
+    }
+}
+
+// Replaces rows 0 and P of a physical curve with u_+ and u_-.
+template <typename T>
+__global__ void k_set_ends(CurveDev c, T *X)
+{
+    const int N = c.nx, P = c.P;
+    for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < N; n += gridDim.x * blockDim.x) {
+        X[n] = (T)c.ends[n];
+        X[(size_t)P * N + n] = (T)c.ends[N + n];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Row transforms (physical <-> spectral), two sections per warp
+// ---------------------------------------------------------------------------
+template <typename T, int N>
+__global__ void __launch_bounds__(ROWS_WARPS * 32) k_row_fwd(CurveDev c, const T *phys, T *spec, int keep_ends)
+{
+    constexpr int H = N / 2;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    cpx<T> *tw = (cpx<T> *)smem_raw;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    cpx<T> *B0 = tw + H + warp * 2 * N, *B1 = B0 + N;
+    for (int t = threadIdx.x; t < H; t += blockDim.x) tw[t] = ((const cpx<T> *)c.twid)[t];
+    __syncthreads();
+    const int ns = c.ns;
+    const int m0 = (blockIdx.x * ROWS_WARPS + warp) * 2, m1 = m0 + 1;
+    if (m0 >= ns) return;
+    const bool has1 = m1 < ns;
+    for (int n = lane; n < N; n += 32)
+        B0[n] = {phys[(size_t)m0 * N + n], has1 ? phys[(size_t)m1 * N + n] : T(0)};
+    __syncwarp();
+    cpx<T> *W = warp_fft<T, N>(B0, B1, tw, false, lane);
+    for (int j = lane; j < H; j += 32) {
+        cpx<T> A, B;
+        get_pair<T, N>(W, j, A, B);
+        if (!(keep_ends && (m0 == 0 || m0 == c.P))) st2(spec, m0, N, j, A);
+        if (has1 && !(keep_ends && m1 == c.P)) st2(spec, m1, N, j, B);
+    }
+}
+
+template <typename T, int N>
+__global__ void __launch_bounds__(ROWS_WARPS * 32) k_row_inv(CurveDev c, const T *spec, T *phys, int scale_mode)
+{
+    constexpr int H = N / 2;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    cpx<T> *tw = (cpx<T> *)smem_raw;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    cpx<T> *B0 = tw + H + warp * 2 * N, *B1 = B0 + N;
+    for (int t = threadIdx.x; t < H; t += blockDim.x) tw[t] = ((const cpx<T> *)c.twid)[t];
+    __syncthreads();
+    const int ns = c.ns, P = c.P;
+    const int m0 = (blockIdx.x * ROWS_WARPS + warp) * 2, m1 = m0 + 1;
+    if (m0 >= ns) return;
+    const bool has1 = m1 < ns;
+    for (int j = lane; j < H; j += 32) {
+        cpx<T> A = ld2(spec, m0, N, j);
+        cpx<T> B = has1 ? ld2(spec, m1, N, j) : cpx<T>{0, 0};
+        put_pair<T, N>(B0, j, A, B);
+    }
+    if (lane == 0) B0[H] = {0, 0};
+    __syncwarp();
+    cpx<T> *Z = warp_fft<T, N>(B0, B1, tw, true, lane);
+    T f0 = 1, f1 = 1;
+    if (scale_mode == 1) {   // Euclidean gradient: -2 dx w_m, zero on the end rows
+        const double dx = c.L / (double)N;
+        f0 = (m0 == 0 || m0 == P) ? T(0) : (T)(-2.0 * dx * c.w[m0]);
+        f1 = (!has1 || m1 == P) ? T(0) : (T)(-2.0 * dx * c.w[m1]);
+    }
+    for (int n = lane; n < N; n += 32) {
+        cpx<T> z = Z[n];
+        phys[(size_t)m0 * N + n] = f0 * z.x;
+        if (has1) phys[(size_t)m1 * N + n] = f1 * z.y;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Row phase of one evaluation
+// ---------------------------------------------------------------------------
+// Per section m (two per warp, packed as one complex FFT):
+//   u   = IDFT(u^)                      physical section
+//   w^  = DFT(u^2) / N
+//   f^  = -(1/2) i k w^ - a_j u^        (eq. KSE: -u u_x - u_xx - u_xxxx; a_j = k^4 - k^2)
+//   r^  = f^ - l d^                     (eq. KSE_residual; 0 on rows 0 and P)
+//   r_x = IDFT(i k r^)
+//   A^  = DFT(u r_x) / N - a_j r^       ((Df)^T r = u r_x - r_xx - r_xxxx, eq. KSE_G)
+// Row sums (Parseval, FP64): |r_m|^2, |d_m|^2, <d_m, r_m> (interior rows) and
+// |u_m|^2, |f_m|^2 (end rows).  The last CTA to finish reduces them over m in a
+// fixed order: J^2, J_arc, dJ^2/dl, |l d|_W, the end-section residuals, and
+// (step mode) the convergence decision and the next lambda.
+template <typename T, int N>
+__global__ void __launch_bounds__(ROWS_WARPS * 32) k_rows(CurveDev c, int mode)
+{
+    constexpr int H = N / 2;
+    constexpr int MPL = (H + 31) / 32;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    cpx<T> *tw = (cpx<T> *)smem_raw;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    cpx<T> *B0 = tw + H + warp * 3 * N, *B1 = B0 + N, *B2 = B1 + N;
+    __shared__ double red[ROWS_WARPS * 32];
+    __shared__ int am_last;
+    DevScalars *sc = c.sc;
+
+    if (mode == ROWS_STEP && (sc->done || sc->step >= sc->limit)) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) sc->active = 0;
+        return;
+    }
+    for (int t = threadIdx.x; t < H; t += blockDim.x) tw[t] = ((const cpx<T> *)c.twid)[t];
+    __syncthreads();
+
+    const int ns = c.ns, P = c.P;
+    const T lam = (T)sc->lambda;
+    const T *U = (const T *)c.U, *D = (const T *)c.D;
+    T *R = (T *)c.R, *A = (T *)c.A;
+    const T *kj = (const T *)c.kj, *aj = (const T *)c.aj;
+
+    const int m0 = (blockIdx.x * ROWS_WARPS + warp) * 2, m1 = m0 + 1;
+    if (m0 < ns) {
+        const bool has1 = m1 < ns;
+        const bool in0 = (m0 > 0 && m0 < P), in1 = has1 && (m1 > 0 && m1 < P);
+        cpx<T> ua[MPL], ub[MPL], ra[MPL], rb[MPL];
+        double s0[5] = {0, 0, 0, 0, 0}, s1[5] = {0, 0, 0, 0, 0};   // nr, nd, ndr, nu, nf
+        // spectrum of u_a + i u_b
+#pragma unroll
+        for (int i = 0; i < MPL; ++i) {
+            int j = lane + 32 * i;
+            if (j < H) {
+                ua[i] = ld2(U, m0, N, j);
+                ub[i] = has1 ? ld2(U, m1, N, j) : cpx<T>{0, 0};
+                put_pair<T, N>(B0, j, ua[i], ub[i]);
+            }
+        }
+        if (lane == 0) B0[H] = {0, 0};
+        __syncwarp();
+        cpx<T> *Zu = warp_fft<T, N>(B0, B1, tw, true, lane);     // u_a + i u_b on the grid
+        cpx<T> *Q = (Zu == B0) ? B1 : B0;
+        for (int n = lane; n < N; n += 32) {
+            cpx<T> z = Zu[n];
+            B2[n] = z;
+            Q[n] = {z.x * z.x, z.y * z.y};
+        }
+        __syncwarp();
+        cpx<T> *Wq = warp_fft<T, N>(Q, Zu, tw, false, lane);     // DFT of u_a^2 + i u_b^2
+#pragma unroll
+        for (int i = 0; i < MPL; ++i) {
+            int j = lane + 32 * i;
+            if (j < H) {
+                cpx<T> wa, wb;
+                get_pair<T, N>(Wq, j, wa, wb);
+                const T k = kj[j], a = aj[j], hk = T(0.5) * k;
+                cpx<T> fa = {hk * wa.y - a * ua[i].x, -hk * wa.x - a * ua[i].y};
+                cpx<T> fb = {hk * wb.y - a * ub[i].x, -hk * wb.x - a * ub[i].y};
+                cpx<T> da = ld2(D, m0, N, j);
+                cpx<T> db = has1 ? ld2(D, m1, N, j) : cpx<T>{0, 0};
+                ra[i] = in0 ? cpx<T>{fa.x - lam * da.x, fa.y - lam * da.y} : cpx<T>{0, 0};
+                rb[i] = in1 ? cpx<T>{fb.x - lam * db.x, fb.y - lam * db.y} : cpx<T>{0, 0};
+                if (j == 0) { ra[i].y = 0; rb[i].y = 0; fa.y = 0; fb.y = 0; }
+                const double cw = (j == 0) ? 1.0 : 2.0;
+                s0[0] += cw * ((double)ra[i].x * ra[i].x + (double)ra[i].y * ra[i].y);
+                s0[1] += cw * ((double)da.x * da.x + (double)da.y * da.y);
+                s0[2] += cw * ((double)da.x * ra[i].x + (double)da.y * ra[i].y);
+                s0[3] += cw * ((double)ua[i].x * ua[i].x + (double)ua[i].y * ua[i].y);
+                s0[4] += cw * ((double)fa.x * fa.x + (double)fa.y * fa.y);
+                s1[0] += cw * ((double)rb[i].x * rb[i].x + (double)rb[i].y * rb[i].y);
+                s1[1] += cw * ((double)db.x * db.x + (double)db.y * db.y);
+                s1[2] += cw * ((double)db.x * rb[i].x + (double)db.y * rb[i].y);
+                s1[3] += cw * ((double)ub[i].x * ub[i].x + (double)ub[i].y * ub[i].y);
+                s1[4] += cw * ((double)fb.x * fb.x + (double)fb.y * fb.y);
+            }
+        }
+        __syncwarp();
+        // spectrum of (i k r^_a) + i (i k r^_b) -> r_x on the grid
+        cpx<T> *X0 = Wq, *X1 = (Wq == B0) ? B1 : B0;
+#pragma unroll
+        for (int i = 0; i < MPL; ++i) {
+            int j = lane + 32 * i;
+            if (j < H) {
+                const T k = kj[j];
+                put_pair<T, N>(X0, j, cpx<T>{-k * ra[i].y, k * ra[i].x}, cpx<T>{-k * rb[i].y, k * rb[i].x});
+            }
+        }
+        if (lane == 0) X0[H] = {0, 0};
+        __syncwarp();
+        cpx<T> *Rx = warp_fft<T, N>(X0, X1, tw, true, lane);
+        cpx<T> *Y = (Rx == X0) ? X1 : X0;
+        for (int n = lane; n < N; n += 32) {
+            cpx<T> z = B2[n], q = Rx[n];
+            Y[n] = {z.x * q.x, z.y * q.y};
+        }
+        __syncwarp();
+        cpx<T> *Pp = warp_fft<T, N>(Y, Rx, tw, false, lane);     // DFT of u_a r_xa + i u_b r_xb
+#pragma unroll
+        for (int i = 0; i < MPL; ++i) {
+            int j = lane + 32 * i;
+            if (j < H) {
+                cpx<T> pa, pb;
+                get_pair<T, N>(Pp, j, pa, pb);
+                const T a = aj[j];
+                st2(R, m0, N, j, ra[i]);
+                st2(A, m0, N, j, cpx<T>{pa.x - a * ra[i].x, pa.y - a * ra[i].y});
+                if (has1) {
+                    st2(R, m1, N, j, rb[i]);
+                    st2(A, m1, N, j, cpx<T>{pb.x - a * rb[i].x, pb.y - a * rb[i].y});
+                }
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < 5; ++q) {
+            s0[q] = warp_sum(s0[q]);
+            s1[q] = warp_sum(s1[q]);
+        }
+        if (lane == 0) {
+            const double L = c.L;
+            double *rs = c.rowsc + (size_t)m0 * 4;
+            bool end0 = !in0;
+            rs[0] = L * (end0 ? s0[3] : s0[0]);
+            rs[1] = L * s0[1];
+            rs[2] = L * s0[2];
+            rs[3] = L * s0[4];
+            if (has1) {
+                double *rt = c.rowsc + (size_t)m1 * 4;
+                bool end1 = !in1;
+                rt[0] = L * (end1 ? s1[3] : s1[0]);
+                rt[1] = L * s1[1];
+                rt[2] = L * s1[2];
+                rt[3] = L * s1[4];
+            }
+        }
+    }
+
+    // ---- last CTA: FP64 reduction over the sections in a fixed order
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned prev = atomicAdd(&sc->cnt_rows, 1u);
+        am_last = (prev == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!am_last) return;
+    __threadfence();
+    const double lamd = sc->lambda, al = fabs(lamd);
+    double t_j2 = 0, t_num = 0, t_den = 0, t_dl = 0, t_d2 = 0;
+    for (int m = 1 + threadIdx.x; m < P; m += blockDim.x) {
+        const double nr = __ldcg(c.rowsc + 4 * (size_t)m), nd = __ldcg(c.rowsc + 4 * (size_t)m + 1);
+        const double ndr = __ldcg(c.rowsc + 4 * (size_t)m + 2);
+        const double w = c.w[m];
+        const double sd = sqrt(nd);
+        t_j2 += w * nr;
+        t_num += w * sqrt(nr) * al * sd;
+        t_den += w * al * sd;
+        t_dl += w * ndr;
+        t_d2 += w * lamd * lamd * nd;
+    }
+    t_j2 = block_sum<ROWS_WARPS * 32>(t_j2, red);
+    t_num = block_sum<ROWS_WARPS * 32>(t_num, red);
+    t_den = block_sum<ROWS_WARPS * 32>(t_den, red);
+    t_dl = block_sum<ROWS_WARPS * 32>(t_dl, red);
+    t_d2 = block_sum<ROWS_WARPS * 32>(t_d2, red);
+    if (threadIdx.x == 0) {
+        sc->J2 = t_j2;
+        sc->Jarc = t_den > 0 ? t_num / t_den : 0.0;
+        sc->dJdl = -2.0 * t_dl;
+        sc->Dnorm = sqrt(t_d2);
+        sc->u2_plus = __ldcg(c.rowsc + 0);
+        sc->f2_plus = __ldcg(c.rowsc + 3);
+        sc->u2_minus = __ldcg(c.rowsc + 4 * (size_t)P + 0);
+        sc->f2_minus = __ldcg(c.rowsc + 4 * (size_t)P + 3);
+        if (mode == ROWS_STEP) {
+            const double J = sqrt(t_j2);
+            const double crit = sc->conv == 0 ? sc->Jarc : (sc->conv == 1 ? J : (sc->Dnorm > 0 ? J / sc->Dnorm : J));
+            if (!isfinite(t_j2) || !isfinite(sc->Jarc)) {
+                sc->status = 5;
+                sc->done = 1;
+                sc->active = 0;
+            } else if (sc->tol > 0 && crit < sc->tol) {
+                sc->done = 1;
+                sc->active = 0;
+            } else {
+                sc->active = 1;
+            }
+            sc->lambda_next = sc->lambda_free ? lamd - sc->dtau_lambda * sc->dJdl : lamd;
+        }
+        sc->cnt_rows = 0;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// s-direction: structured contraction with D_t (or W^-1 D_t^T W)
+// ---------------------------------------------------------------------------
+// Y[j][col] = rowscale_j * sum_m (cot[(j+m) mod 2P] + tsign cot[(j-m) mod 2P]) colscale_m X[m][col]
+//   D_t:          colscale = tau, rowscale = sigma, tsign = +1
+//   W^-1 D_t^T W: colscale = sigma w, rowscale = tau / w, tsign = -1
+// Epilogues:
+//   GM_STORE:  D = Y                                  (D_t u of the new state)
+//   GM_UPDATE: e = +l Y (published adjoint) or -l Y (discrete adjoint),
+//              G = -(A^ + e) on interior rows, u += dtau G / (1 + dtau a_j^2)
+//              (the semi-implicit step of Sec. V.C.3 in its algebraically
+//              equivalent increment form), FP64 sum_m w_m |G_m|^2
+//   GM_GRAD:   as GM_UPDATE but G is written out instead of updating u.
+template <typename T>
+__global__ void __launch_bounds__(GEMM_THREADS) k_dt(CurveDev c, int mode, int discrete, int gate)
+{
+    constexpr int BM = GEMM_BM, BN = GEMM_BN, BK = GEMM_BK;
+    __shared__ T Ks[BM][BK + 1];
+    __shared__ T Xs[BK][BN];
+    __shared__ double red[GEMM_THREADS];
+    __shared__ int am_last;
+    DevScalars *sc = c.sc;
+    if (gate && !sc->active) return;
+
+    const int ns = c.ns, N = c.nx, P = c.P, twoP = 2 * P;
+    const T *X = (const T *)(mode == GM_STORE ? c.U : c.R);
+    const T *cot = (const T *)c.cot;
+    const T *colscale = (const T *)(discrete ? c.sw : c.tau);
+    const T *rowscale = (const T *)(discrete ? c.twr : c.sig);
+    const T tsign = discrete ? T(-1) : T(1);
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    const int j0 = blockIdx.y * BM, c0 = blockIdx.x * BN;
+    T acc[2][2] = {{0, 0}, {0, 0}};
+
+    for (int m0 = 0; m0 < ns; m0 += BK) {
+        for (int e = threadIdx.x; e < BK * BN; e += GEMM_THREADS) {
+            int kk = e / BN, cc = e % BN;
+            int m = m0 + kk, col = c0 + cc;
+            Xs[kk][cc] = (m < ns && col < N) ? colscale[m] * X[(size_t)m * N + col] : T(0);
+        }
+        for (int e = threadIdx.x; e < BM * BK; e += GEMM_THREADS) {
+            int jj = e / BK, kk = e % BK;
+            int j = j0 + jj, m = m0 + kk;
+            T v = 0;
+            if (j < ns && m < ns) {
+                int ip = j + m;
+                if (ip >= twoP) ip -= twoP;
+                int im = j - m;
+                if (im < 0) im += twoP;
+                v = cot[ip] + tsign * cot[im];
+            }
+            Ks[jj][kk] = v;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < BK; ++kk) {
+            const T a0 = Ks[2 * ty][kk], a1 = Ks[2 * ty + 1][kk];
+            const T b0 = Xs[kk][2 * tx], b1 = Xs[kk][2 * tx + 1];
+            acc[0][0] += a0 * b0;
+            acc[0][1] += a0 * b1;
+            acc[1][0] += a1 * b0;
+            acc[1][1] += a1 * b1;
+        }
+        __syncthreads();
+    }
+
+    if (mode == GM_STORE) {
+        T *Dout = (T *)c.D;
+#pragma unroll
+        for (int i = 0; i < 2; ++i)
+#pragma unroll
+            for (int l = 0; l < 2; ++l) {
+                int j = j0 + 2 * ty + i, col = c0 + 2 * tx + l;
+                if (j < ns && col < N) Dout[(size_t)j * N + col] = rowscale[j] * acc[i][l];
+            }
+        return;
+    }
+
+    const T lam = (T)sc->lambda, dtau = (T)sc->dtau;
+    const T *Ah = (const T *)c.A, *pr = (const T *)c.prec_imex;
+    T *U = (T *)c.U, *G = (T *)c.G;
+    double part = 0.0;
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int l = 0; l < 2; ++l) {
+            int j = j0 + 2 * ty + i, col = c0 + 2 * tx + l;
+            if (j >= ns || col >= N) continue;
+            const bool interior = (j > 0 && j < P);
+            T g = 0;
+            if (interior && col != 1) {
+                const T y = rowscale[j] * acc[i][l];
+                const T e = discrete ? -lam * y : lam * y;
+                g = -(Ah[(size_t)j * N + col] + e);
+                const double cw = (col < 2) ? 1.0 : 2.0;
+                part += c.w[j] * cw * (double)g * (double)g;
+            }
+            if (mode == GM_UPDATE) {
+                if (interior) U[(size_t)j * N + col] += dtau * pr[col >> 1] * g;
+            } else {
+                G[(size_t)j * N + col] = g;
+            }
+        }
+    part = block_sum<GEMM_THREADS>(part, red);
+    const int bid = blockIdx.y * gridDim.x + blockIdx.x, nb = gridDim.x * gridDim.y;
+    if (threadIdx.x == 0) c.tile[bid] = part;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned prev = atomicAdd(&sc->cnt_gemm, 1u);
+        am_last = (prev == (unsigned)nb - 1);
+    }
+    __syncthreads();
+    if (!am_last) return;
+    __threadfence();
+    double t = 0.0;
+    for (int b = threadIdx.x; b < nb; b += GEMM_THREADS) t += __ldcg(c.tile + b);
+    t = block_sum<GEMM_THREADS>(t, red);
+    if (threadIdx.x == 0) {
+        sc->G2 = c.L * t;
+        if (mode == GM_UPDATE) {
+            sc->step += 1;
+            sc->tau += sc->dtau;
+            sc->lambda = sc->lambda_next;
+        }
+        sc->cnt_gemm = 0;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Launchers
+// ---------------------------------------------------------------------------
+template <typename T>
+static size_t rows_smem(int N, int bufs)
+{
+    return (size_t)(N / 2 + ROWS_WARPS * bufs * N) * sizeof(cpx<T>);
+}
+
+template <typename K>
+static cudaError_t set_smem(K kern, size_t bytes)
+{
+    if (bytes <= 48 * 1024) return cudaSuccess;
+    return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+static int row_grid(int ns) { return (ns + ROWS_PER_CTA - 1) / ROWS_PER_CTA; }
+
+// Calls f(std::integral_constant<int, N>) for the supported section lengths.
+template <typename F>
+static cudaError_t dispatch_n(int n, F &&f)
+{
+    switch (n) {
+    case 8: return f(std::integral_constant<int, 8>{});
+    case 16: return f(std::integral_constant<int, 16>{});
+    case 32: return f(std::integral_constant<int, 32>{});
+    case 64: return f(std::integral_constant<int, 64>{});
+    case 128: return f(std::integral_constant<int, 128>{});
+    case 256: return f(std::integral_constant<int, 256>{});
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+template <typename T>
+static cudaError_t rows_t(const CurveDev &c, int mode, cudaStream_t st)
+{
+    return dispatch_n(c.nx, [&](auto nn) {
+        constexpr int NN = decltype(nn)::value;
+        size_t sm = rows_smem<T>(NN, 3);
+        cudaError_t e = set_smem(k_rows<T, NN>, sm);
+        if (e != cudaSuccess) return e;
+        k_rows<T, NN><<<row_grid(c.ns), ROWS_WARPS * 32, sm, st>>>(c, mode);
+        return cudaGetLastError();
+    });
+}
+
+template <typename T>
+static cudaError_t row_fwd_t(const CurveDev &c, const void *phys, void *spec, int keep_ends, cudaStream_t st)
+{
+    return dispatch_n(c.nx, [&](auto nn) {
+        constexpr int NN = decltype(nn)::value;
+        size_t sm = rows_smem<T>(NN, 2);
+        cudaError_t e = set_smem(k_row_fwd<T, NN>, sm);
+        if (e != cudaSuccess) return e;
+        k_row_fwd<T, NN><<<row_grid(c.ns), ROWS_WARPS * 32, sm, st>>>(c, (const T *)phys, (T *)spec, keep_ends);
+        return cudaGetLastError();
+    });
+}
+
+template <typename T>
+static cudaError_t row_inv_t(const CurveDev &c, const void *spec, void *phys, int scale_mode, cudaStream_t st)
+{
+    return dispatch_n(c.nx, [&](auto nn) {
+        constexpr int NN = decltype(nn)::value;
+        size_t sm = rows_smem<T>(NN, 2);
+        cudaError_t e = set_smem(k_row_inv<T, NN>, sm);
+        if (e != cudaSuccess) return e;
+        k_row_inv<T, NN><<<row_grid(c.ns), ROWS_WARPS * 32, sm, st>>>(c, (const T *)spec, (T *)phys, scale_mode);
+        return cudaGetLastError();
+    });
+}
+
+cudaError_t launch_setup(const CurveDev &c, double dtau, cudaStream_t st)
+{
+    int total = 2 * c.P > c.ns ? 2 * c.P : c.ns;
+    int grid = (total + 255) / 256;
+    if (c.prec) k_setup<float><<<grid, 256, 0, st>>>(c, dtau);
+    else k_setup<double><<<grid, 256, 0, st>>>(c, dtau);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scalars_init(const CurveDev &c, double lambda, int lambda_free, double dtau,
+                                double dtau_lambda, int conv, cudaStream_t st)
+{
+    k_scalars_init<<<1, 32, 0, st>>>(c.sc, lambda, lambda_free, dtau, dtau_lambda, conv);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_set_limit(const CurveDev &c, long long nsteps, double tol, cudaStream_t st)
+{
+    k_set_limit<<<1, 32, 0, st>>>(c.sc, nsteps, tol);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_set_lambda_tau(const CurveDev &c, double lambda, double tau, cudaStream_t st)
+{
+    k_set_lambda_tau<<<1, 32, 0, st>>>(c.sc, lambda, tau);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_trial(const CurveDev &c, double a, int has_v, int npert, cudaStream_t st)
+{
+    size_t total = (size_t)c.ns * c.nx;
+    int grid = (int)((total + 255) / 256);
+    if (grid > 4096) grid = 4096;
+    if (c.prec) k_trial<float><<<grid, 256, 0, st>>>(c, a, has_v, npert);
+    else k_trial<double><<<grid, 256, 0, st>>>(c, a, has_v, npert);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_set_ends(const CurveDev &c, void *X, cudaStream_t st)
+{
+    int grid = (c.nx + 255) / 256;
+    if (c.prec) k_set_ends<float><<<grid, 256, 0, st>>>(c, (float *)X);
+    else k_set_ends<double><<<grid, 256, 0, st>>>(c, (double *)X);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_row_fwd(const CurveDev &c, const void *phys, void *spec, int keep_ends, cudaStream_t st)
+{
+    return c.prec ? row_fwd_t<float>(c, phys, spec, keep_ends, st) : row_fwd_t<double>(c, phys, spec, keep_ends, st);
+}
+
+cudaError_t launch_row_inv(const CurveDev &c, const void *spec, void *phys, int scale_mode, cudaStream_t st)
+{
+    return c.prec ? row_inv_t<float>(c, spec, phys, scale_mode, st) : row_inv_t<double>(c, spec, phys, scale_mode, st);
+}
+
+cudaError_t launch_rows(const CurveDev &c, int mode, cudaStream_t st)
+{
+    return c.prec ? rows_t<float>(c, mode, st) : rows_t<double>(c, mode, st);
+}
+
+cudaError_t launch_dt(const CurveDev &c, int mode, int discrete, int gate, cudaStream_t st)
+{
+    dim3 grid((c.nx + GEMM_BN - 1) / GEMM_BN, (c.ns + GEMM_BM - 1) / GEMM_BM);
+    if (c.prec) k_dt<float><<<grid, GEMM_THREADS, 0, st>>>(c, mode, discrete, gate);
+    else k_dt<double><<<grid, GEMM_THREADS, 0, st>>>(c, mode, discrete, gate);
+    return cudaGetLastError();
+}
+
+}  // namespace ks

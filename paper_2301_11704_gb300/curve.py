@@ -1,0 +1,163 @@
+"""KSCurve: a curve of KSE states joining two equilibria, held on the GPU.
+
+PyTorch supplies the device memory (the workspace and the output tensors) and
+the CUDA stream; every step of the method runs in libksconn.so.
+"""
+from __future__ import annotations
+
+import ctypes
+from typing import Optional
+
+import numpy as np
+import torch
+
+from . import _native
+from ._native import KSParams, KSScalars, check, dptr
+
+_PREC = {"fp64": _native.KS_FP64, "fp32": _native.KS_FP32}
+_ADJ = {"paper": _native.KS_ADJ_PAPER, "discrete": _native.KS_ADJ_DISCRETE}
+_CONV = {"jarc": _native.KS_CONV_JARC, "j": _native.KS_CONV_J, "jrel": _native.KS_CONV_JREL}
+
+
+def _f64(a, n=None):
+    if a is None:
+        return None
+    a = np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+    if n is not None and a.size != n:
+        raise ValueError("expected %d values, got %d" % (n, a.size))
+    return a
+
+
+class KSCurve:
+    """One curve u(x_n, s_m), n < nx, m < ns (ns = M + 2 sections incl. both ends).
+
+    Physical arrays exchanged with the curve are torch tensors [ns, nx] on the
+    curve's device in its storage dtype (float64 for "fp64", float32 for "fp32").
+    Row 0 is s = +inf (u_plus), row ns-1 is s = -inf (u_minus).
+    """
+
+    def __init__(self, L: float, nx: int, ns: int, S: float, u_plus, u_minus=None, *, s0: float = 0.0,
+                 lam: float = 1.0, lambda_free: bool = False, dtau: float = 0.01, dtau_lambda: float = 0.0,
+                 precision: str = "fp64", adjoint: str = "paper", conv: str = "jarc", u_init=None,
+                 check_ends: bool = False, device=None, stream: Optional[torch.cuda.Stream] = None):
+        self.lib = _native.load()
+        self.device = torch.device(device if device is not None else "cuda")
+        self.dtype = torch.float64 if precision == "fp64" else torch.float32
+        self.nx, self.ns, self.L, self.S = int(nx), int(ns), float(L), float(S)
+        self.params = KSParams(L=L, nx=nx, ns=ns, S=S, s0=s0, lam=lam, lambda_free=int(bool(lambda_free)),
+                               dtau=dtau, dtau_lambda=dtau_lambda, precision=_PREC[precision],
+                               adjoint=_ADJ[adjoint], conv=_CONV[conv], check_ends=int(bool(check_ends)),
+                               reserved=0)
+        nbytes = self.lib.ks_curve_workspace_bytes(ctypes.byref(self.params))
+        if nbytes == 0:
+            raise _native.KSError(_native.KS_EINVAL, self.lib.ks_last_error().decode())
+        self.workspace_bytes = int(nbytes)
+        self._ws = torch.empty(self.workspace_bytes + 256, dtype=torch.uint8, device=self.device)
+        base = self._ws.data_ptr()
+        self._ws_ptr = (base + 255) & ~255
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        up = _f64(u_plus, nx)
+        um = _f64(u_minus, nx) if u_minus is not None else np.zeros(nx)
+        init_ptr = None
+        if u_init is not None:
+            u_init = self._as_curve_tensor(u_init)
+            init_ptr = u_init.data_ptr()
+        h = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            check(self.lib.ks_curve_create(ctypes.byref(self.params), dptr(up), dptr(um), init_ptr,
+                                           self._ws_ptr, self.workspace_bytes, self.stream.cuda_stream,
+                                           ctypes.byref(h)))
+        self.handle = h
+
+    # ------------------------------------------------------------------ helpers
+    def _as_curve_tensor(self, u):
+        u = torch.as_tensor(u, device=self.device, dtype=self.dtype).contiguous()
+        if tuple(u.shape) != (self.ns, self.nx):
+            raise ValueError("expected a [%d, %d] curve, got %s" % (self.ns, self.nx, tuple(u.shape)))
+        return u
+
+    def _new(self):
+        return torch.empty((self.ns, self.nx), dtype=self.dtype, device=self.device)
+
+    def _live(self):
+        if self.handle is None:
+            raise RuntimeError("curve is closed")
+        return self.handle
+
+    # ------------------------------------------------------------------ API
+    def init_trial(self, a: float = 0.0, v=None, amps=None, vp=None):
+        """Trial curve of eq. KSE_initial_curve plus sum_p amps[p] sin((p+1) theta) vp[p](x)."""
+        v = _f64(v, self.nx)
+        amps = _f64(amps)
+        npert = 0 if amps is None else int(amps.size)
+        vp = _f64(vp, npert * self.nx) if npert else None
+        check(self.lib.ks_curve_init_trial(self._live(), float(a), dptr(v), npert, dptr(amps), dptr(vp)))
+
+    def residual(self) -> torch.Tensor:
+        out = self._new()
+        check(self.lib.ks_curve_residual(self._live(), out.data_ptr()))
+        return out
+
+    def cost(self):
+        j2, ja = ctypes.c_double(), ctypes.c_double()
+        check(self.lib.ks_curve_cost(self._live(), ctypes.byref(j2), ctypes.byref(ja)))
+        return j2.value, ja.value
+
+    def gradient(self, euclidean: bool = False):
+        out = self._new()
+        dl = ctypes.c_double()
+        check(self.lib.ks_curve_gradient(self._live(), int(bool(euclidean)), out.data_ptr(), ctypes.byref(dl)))
+        return out, dl.value
+
+    def descend(self, nsteps: int, tol: float = 0.0, raise_on_notconv: bool = False):
+        steps, J, Ja = ctypes.c_int64(), ctypes.c_double(), ctypes.c_double()
+        st = self.lib.ks_curve_descend(self._live(), int(nsteps), float(tol), ctypes.byref(steps),
+                                       ctypes.byref(J), ctypes.byref(Ja))
+        allow = () if raise_on_notconv else (_native.KS_ENOTCONV,)
+        check(st, allow=allow)
+        return dict(steps=steps.value, J=J.value, J_arc=Ja.value, status=st)
+
+    def descend_async(self, nsteps: int, tol: float = 0.0):
+        check(self.lib.ks_curve_descend_async(self._live(), int(nsteps), float(tol)))
+
+    def scalars(self) -> dict:
+        s = KSScalars()
+        check(self.lib.ks_curve_scalars(self._live(), ctypes.byref(s)))
+        return s.as_dict()
+
+    def get_state(self) -> torch.Tensor:
+        out = self._new()
+        check(self.lib.ks_curve_get_state(self._live(), out.data_ptr(), None, None))
+        return out
+
+    def get_lambda_tau(self):
+        lam, tau = ctypes.c_double(), ctypes.c_double()
+        check(self.lib.ks_curve_get_state(self._live(), None, ctypes.byref(lam), ctypes.byref(tau)))
+        return lam.value, tau.value
+
+    def set_state(self, u, lam: float = 1.0, tau: float = 0.0):
+        u = self._as_curve_tensor(u)
+        check(self.lib.ks_curve_set_state(self._live(), u.data_ptr(), float(lam), float(tau)))
+        self.stream.synchronize()
+
+    def profile(self, max_steps: int):
+        """Start (max_steps > 0) or stop (0) per-phase event timing of descent steps."""
+        check(self.lib.ks_curve_profile(self._live(), int(max_steps)))
+
+    def profile_read(self) -> dict:
+        pr = _native.KSProfile()
+        check(self.lib.ks_curve_profile_read(self._live(), ctypes.byref(pr)))
+        names = ("rows", "dt_update", "dt_store")
+        return {n: dict(ms=pr.ms[i], launches=pr.launches[i]) for i, n in enumerate(names)}
+
+    def close(self):
+        if getattr(self, "handle", None) is not None:
+            self.stream.synchronize()
+            self.lib.ks_curve_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

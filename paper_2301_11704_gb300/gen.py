@@ -14,7 +14,9 @@ the top 53 bits and to normals with the Box-Muller transform.
 from __future__ import annotations
 
 import dataclasses
+import json
 import math
+import os
 from typing import List, Optional
 
 import numpy as np
@@ -162,3 +164,33 @@ def workload(cfg: int) -> List[CurveSpec]:
 def small_spec(L=22.0, N=8, Ns=16, S: Optional[float] = None, cfg=9, index=0) -> CurveSpec:
     """Tiny curve for brute-force checks (finite differences)."""
     return CurveSpec(cfg, index, L, N, Ns, S if S is not None else mapping_scale(Ns))
+
+
+_EQ = None
+
+
+def stored_equilibria() -> dict:
+    """The stored end-point equilibria, keyed by (cfg, index).  They were computed
+    once by the oracle's Newton solver (oracle/make_equilibria.py) and are read
+    here as plain input data."""
+    global _EQ
+    if _EQ is None:
+        path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "data", "equilibria.json")
+        with open(path) as f:
+            _EQ = {(e["cfg"], e["index"]): e for e in json.load(f)["entries"]}
+    return _EQ
+
+
+def end_points(spec: CurveSpec):
+    """(u_plus, u_minus) physical sections of a workload curve: u_+ from the
+    stored sine coefficients, u_- = 0."""
+    e = stored_equilibria()[(spec.cfg, spec.index)]
+    if e["N"] != spec.N or abs(e["L"] - spec.L) > 1e-12:
+        raise ValueError("stored equilibrium does not match the workload")
+    return _sine_series(np.array(e["b"]), spec.N, spec.L), np.zeros(spec.N)
+
+
+def perturbation(spec: CurveSpec):
+    """(amps, fields[npert, N]) of the trial-curve perturbation of a workload curve."""
+    v = perturbation_fields(spec.N, spec.L, spec.seed(), spec.npert)
+    return np.full(spec.npert, spec.amp), v

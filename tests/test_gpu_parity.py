@@ -1,0 +1,208 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle on the same
+seeded inputs.
+
+Tolerances: FP64 results within 1e-10 relative (max-norm error over max-norm of
+the oracle value, per field; plain relative error for scalars).  FP32 storage
+with FP64 reductions: J within 1e-5 relative, fields within 1e-5 relative in
+the 2-norm, both on the trial curve where J is far above the FP32 floor.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2301_11704_gb300 import gen
+from paper_2301_11704_gb300.curve import KSCurve
+from tests.curves import end_points, perturbation
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-10
+TOL32 = 1e-5
+
+
+def rel_max(a, b):
+    return float(np.abs(np.asarray(a) - np.asarray(b)).max() / max(np.abs(np.asarray(b)).max(), 1e-300))
+
+
+def rel_2(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(np.linalg.norm(np.asarray(b)), 1e-300))
+
+
+def make_pair(spec, precision="fp64", adjoint="paper", lam=1.0, lambda_free=False, dtau_lambda=0.0):
+    """GPU curve and oracle spectral curve of the same workload trial curve."""
+    up, um = end_points(spec)
+    amps, vp = perturbation(spec)
+    c = KSCurve(spec.L, spec.N, spec.Ns, spec.S, up, um, s0=spec.s0, lam=lam, lambda_free=lambda_free,
+                dtau=spec.dtau, dtau_lambda=dtau_lambda, precision=precision, adjoint=adjoint)
+    c.init_trial(0.0, None, amps, vp)
+    U = oracle.curve_init(spec.M, spec.S, up, um, s0=spec.s0, amps=amps, vp=vp)
+    return c, U
+
+
+def oracle_eval(U, spec, lam=1.0, mode=oracle.PAPER):
+    R, D = oracle.curve_residual(U, spec.L, spec.S, lam)
+    G, _ = oracle.curve_adjoint(U, R, spec.L, spec.S, lam, mode=mode)
+    sc = oracle.curve_scalars(R, D, spec.L, spec.S, lam, G=G)
+    return R, D, G, sc
+
+
+@pytest.fixture(scope="module")
+def cfg0():
+    return gen.workload(0)[0]
+
+
+@pytest.mark.parametrize("adjoint", ["paper", "discrete"])
+def test_single_evaluation_fp64(cfg0, adjoint):
+    spec = cfg0
+    mode = oracle.PAPER if adjoint == "paper" else oracle.DISCRETE
+    c, U = make_pair(spec, adjoint=adjoint)
+    assert rel_max(c.get_state().cpu().numpy(), oracle.curve_physical(U)) < 1e-13
+    R, D, G, sc = oracle_eval(U, spec, mode=mode)
+    r = c.residual().cpu().numpy()
+    assert rel_max(r, oracle.curve_physical(R)) < TOL64
+    J2, Ja = c.cost()
+    assert abs(J2 - sc["J2"]) < TOL64 * sc["J2"]
+    assert abs(Ja - sc["J_arc"]) < TOL64 * sc["J_arc"]
+    g, dl = c.gradient(euclidean=False)
+    assert rel_max(g.cpu().numpy(), oracle.curve_physical(G)) < TOL64
+    assert abs(dl - sc["dJ2_dlambda"]) < TOL64 * abs(sc["dJ2_dlambda"])
+    s = c.scalars()
+    assert abs(s["G_norm"] ** 2 - sc["G2"]) < TOL64 * sc["G2"]
+    assert abs(s["Dnorm"] - sc["Dnorm"]) < TOL64 * sc["Dnorm"]
+    c.close()
+
+
+def test_euclidean_gradient_fp64(cfg0):
+    spec = cfg0
+    c, U = make_pair(spec, adjoint="paper")
+    R, D = oracle.curve_residual(U, spec.L, spec.S)
+    Gd, _ = oracle.curve_adjoint(U, R, spec.L, spec.S, mode=oracle.DISCRETE)
+    _, _, w = oracle.grid(spec.M, spec.S)
+    ref = -2.0 * (spec.L / spec.N) * w[:, None] * oracle.curve_physical(Gd)
+    g, _ = c.gradient(euclidean=True)
+    assert rel_max(g.cpu().numpy(), ref) < TOL64
+    c.close()
+
+
+@pytest.mark.parametrize("adjoint", ["paper", "discrete"])
+def test_descent_2000_steps_fp64(cfg0, adjoint):
+    """cfg 0 end to end: 2000 semi-implicit descent steps from the same trial curve."""
+    spec = cfg0
+    mode = oracle.PAPER if adjoint == "paper" else oracle.DISCRETE
+    c, U = make_pair(spec, adjoint=adjoint)
+    Uo, steps_o, sco, _ = oracle.curve_descend(U, spec.L, spec.S, spec.steps, dtau=spec.dtau, mode=mode)
+    out = c.descend(spec.steps)
+    assert out["steps"] == steps_o == spec.steps
+    assert rel_max(c.get_state().cpu().numpy(), oracle.curve_physical(Uo)) < TOL64
+    assert abs(out["J"] - sco["J"]) < TOL64 * sco["J"]
+    assert abs(out["J_arc"] - sco["J_arc"]) < TOL64 * sco["J_arc"]
+    s = c.scalars()
+    assert abs(s["tau"] - spec.steps * spec.dtau) < 1e-9 and s["step"] == spec.steps
+    c.close()
+
+
+def test_descent_with_free_lambda_fp64(cfg0):
+    spec = cfg0
+    c, U = make_pair(spec, adjoint="discrete", lam=1.0, lambda_free=True, dtau_lambda=0.05)
+    Uo, _, sco, _ = oracle.curve_descend(U, spec.L, spec.S, 300, dtau=spec.dtau, lam=1.0, lambda_free=True,
+                                         dtau_lambda=0.05, mode=oracle.DISCRETE)
+    out = c.descend(300)
+    lam, _ = c.get_lambda_tau()
+    assert abs(lam - sco["lam"]) < TOL64 * abs(sco["lam"]) and abs(lam - 1.0) > 1e-6
+    assert rel_max(c.get_state().cpu().numpy(), oracle.curve_physical(Uo)) < TOL64
+    assert abs(out["J"] - sco["J"]) < TOL64 * sco["J"]
+    c.close()
+
+
+def test_descent_stops_at_tolerance(cfg0):
+    spec = cfg0
+    c, U = make_pair(spec)
+    _, _, _, hist = oracle.curve_descend(U, spec.L, spec.S, 60, dtau=spec.dtau, history=True)
+    tol = 0.5 * (hist[40, 3] + hist[41, 3])        # between J_arc after 40 and 41 steps
+    Uo, steps_o, sco, _ = oracle.curve_descend(U, spec.L, spec.S, 1000, dtau=spec.dtau, tol=tol)
+    out = c.descend(1000, tol=tol)
+    assert steps_o == 41 and out["steps"] == 41
+    assert abs(out["J_arc"] - sco["J_arc"]) < TOL64 * sco["J_arc"]
+    assert c.scalars()["converged"] == 1
+    c.close()
+
+
+def test_fp32_matches_fp64_oracle(cfg0):
+    spec = cfg0
+    c, U = make_pair(spec, precision="fp32")
+    R, D, G, sc = oracle_eval(U, spec)
+    J2, Ja = c.cost()
+    assert abs(np.sqrt(J2) - np.sqrt(sc["J2"])) < TOL32 * np.sqrt(sc["J2"])
+    assert abs(Ja - sc["J_arc"]) < TOL32 * sc["J_arc"]
+    assert rel_2(c.residual().double().cpu().numpy(), oracle.curve_physical(R)) < TOL32
+    g, _ = c.gradient()
+    assert rel_2(g.double().cpu().numpy(), oracle.curve_physical(G)) < TOL32
+    c.close()
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", TOL64), ("fp32", TOL32)])
+def test_config1_single_evaluation(precision, tol):
+    """N_x = 64, N_s = 1024 (the differentiation workload): one evaluation."""
+    spec = gen.workload(1)[0]
+    c, U = make_pair(spec, precision=precision)
+    R, D, G, sc = oracle_eval(U, spec)
+    J2, Ja = c.cost()
+    assert abs(np.sqrt(J2) - np.sqrt(sc["J2"])) < tol * np.sqrt(sc["J2"])
+    assert abs(Ja - sc["J_arc"]) < tol * sc["J_arc"]
+    cmp = rel_max if precision == "fp64" else rel_2
+    assert cmp(c.residual().double().cpu().numpy(), oracle.curve_physical(R)) < tol
+    g, _ = c.gradient()
+    assert cmp(g.double().cpu().numpy(), oracle.curve_physical(G)) < tol
+    c.close()
+
+
+@pytest.mark.parametrize("N,Ns", [(8, 3), (8, 16), (16, 37), (32, 33), (64, 65), (128, 31), (256, 20), (32, 129)])
+def test_edge_shapes_fp64(N, Ns):
+    """Smallest curve (one interior section), ragged N_s (odd, not a tile multiple),
+    every supported N_x, on a random smooth curve; includes 20 descent steps."""
+    L, S = 22.0 + N / 16.0, max(0.5, 0.1 * (Ns - 1))
+    rng = np.random.default_rng(N * 1000 + Ns)
+    X = np.zeros((Ns, N))
+    x = np.arange(N) * L / N
+    for m in range(Ns):
+        for j in range(1, min(5, N // 2)):
+            X[m] += 0.5 * rng.standard_normal() * np.sin(2 * np.pi * j * x / L + rng.uniform(0, 6.28))
+    c = KSCurve(L, N, Ns, S, X[0], X[-1], u_init=torch.from_numpy(X))
+    U = oracle.curve_spectral(X)
+    R, D, G, sc = oracle_eval(U, gen.CurveSpec(0, 0, L, N, Ns, S))
+    assert rel_max(c.residual().cpu().numpy(), oracle.curve_physical(R)) < TOL64
+    g, _ = c.gradient()
+    if Ns > 3 or np.abs(oracle.curve_physical(G)).max() > 0:
+        assert rel_max(g.cpu().numpy(), oracle.curve_physical(G)) < TOL64
+    Uo, _, sco, _ = oracle.curve_descend(U, L, S, 20, dtau=1e-3)
+    c2 = KSCurve(L, N, Ns, S, X[0], X[-1], u_init=torch.from_numpy(X), dtau=1e-3)
+    out = c2.descend(20)
+    assert rel_max(c2.get_state().cpu().numpy(), oracle.curve_physical(Uo)) < TOL64
+    assert abs(out["J"] - sco["J"]) < TOL64 * max(sco["J"], 1e-300)
+    c.close()
+    c2.close()
+
+
+def test_descent_is_deterministic_and_resumable(cfg0):
+    """Fixed reduction order: two identical runs agree bit for bit; a run resumed
+    from get_state/set_state (a physical round trip, exact to rounding) agrees
+    with the uninterrupted run to 1e-12."""
+    spec = cfg0
+    a, _ = make_pair(spec)
+    b, _ = make_pair(spec)
+    a.descend(80)
+    b.descend(80)
+    assert torch.equal(a.get_state(), b.get_state())
+    assert a.scalars()["J"] == b.scalars()["J"]
+    c, _ = make_pair(spec)
+    c.descend(50)
+    u = c.get_state().clone()
+    lam, tau = c.get_lambda_tau()
+    d, _ = make_pair(spec)
+    d.set_state(u, lam, tau)
+    d.descend(30)
+    assert rel_max(d.get_state().cpu().numpy(), a.get_state().cpu().numpy()) < 1e-12
+    assert abs(d.get_lambda_tau()[1] - 80 * spec.dtau) < 1e-12
+    for x in (a, b, c, d):
+        x.close()
