@@ -10,10 +10,6 @@
 #include "../../include/ksconn.h"
 #include "ks_internal.h"
 
-namespace ks {
-cudaError_t launch_set_ends(const CurveDev &c, void *X, cudaStream_t st);
-}
-
 struct ks_curve {
     ks_params p;
     ks::Layout lay;
@@ -109,6 +105,7 @@ ks::CurveDev make_dev(const ks_params *p, const ks::Layout &l, void *ws)
     d.twr = b + l.off_twr;
     d.w = (double *)(b + l.off_w);
     d.twid = b + l.off_twid;
+    d.twid64 = b + l.off_twid64;
     d.kj = b + l.off_kj;
     d.aj = b + l.off_aj;
     d.prec_imex = b + l.off_prec;
@@ -226,14 +223,13 @@ ks_status ks_curve_create(const ks_params *p, const double *u_plus_host, const d
             e = ks::launch_scalars_init(c->d, p->lambda, p->lambda_free, p->dtau, p->dtau_lambda, p->conv, c->st);
         if (e == cudaSuccess) {
             if (u_init_dev) {
-                size_t bytes = (size_t)p->ns * p->nx * (p->precision == KS_FP32 ? 4 : 8);
-                e = cudaMemcpyAsync(c->d.X, u_init_dev, bytes, cudaMemcpyDeviceToDevice, c->st);
-                if (e == cudaSuccess) e = ks::launch_set_ends(c->d, c->d.X, c->st);
+                e = ks::launch_widen(c->d, u_init_dev, c->st);
+                if (e == cudaSuccess) e = ks::launch_set_ends(c->d, c->st);
             } else {
                 e = ks::launch_trial(c->d, 0.0, 0, 0, c->st);
             }
         }
-        if (e == cudaSuccess) e = ks::launch_row_fwd(c->d, c->d.X, c->d.U, 0, c->st);
+        if (e == cudaSuccess) e = ks::launch_row_fwd_x(c->d, c->d.U, 0, c->st);
         if (e == cudaSuccess) e = ks::launch_dt(c->d, ks::GM_STORE, 0, 0, c->st);
         if (e == cudaSuccess && p->check_ends) e = ks::launch_rows(c->d, ks::ROWS_EVAL, c->st);
         if (e != cudaSuccess) {
@@ -286,7 +282,7 @@ ks_status ks_curve_init_trial(ks_curve *c, double a, const double *v_host, int32
         KS_CUDA(cudaMemcpyAsync(c->d.pert + N + ks::MAX_PERT, vp_host, (size_t)npert * N * 8, cudaMemcpyHostToDevice, c->st));
     }
     KS_CUDA(ks::launch_trial(c->d, a, v_host != nullptr && a != 0.0, npert, c->st));
-    KS_CUDA(ks::launch_row_fwd(c->d, c->d.X, c->d.U, 0, c->st));
+    KS_CUDA(ks::launch_row_fwd_x(c->d, c->d.U, 0, c->st));
     s = refresh_dt_u(c);
     if (s != KS_OK) return s;
     KS_CUDA(ks::launch_scalars_init(c->d, c->p.lambda, c->p.lambda_free, c->p.dtau, c->p.dtau_lambda, c->p.conv, c->st));
@@ -427,7 +423,8 @@ ks_status ks_curve_set_state(ks_curve *c, const void *u_dev, double lambda, doub
     if (!std::isfinite(lambda) || !std::isfinite(tau)) return fail(KS_EINVAL, "lambda and tau must be finite");
     DeviceGuard g(c->device);
     if (!g.ok) return fail(KS_ECUDA, "cannot select the curve's device");
-    KS_CUDA(ks::launch_row_fwd(c->d, u_dev, c->d.U, 0, c->st));
+    KS_CUDA(ks::launch_widen(c->d, u_dev, c->st));
+    KS_CUDA(ks::launch_row_fwd_x(c->d, c->d.U, 0, c->st));
     s = refresh_dt_u(c);
     if (s != KS_OK) return s;
     KS_CUDA(ks::launch_set_lambda_tau(c->d, lambda, tau, c->st));

@@ -49,7 +49,7 @@ enum GemmMode { GM_STORE = 0, GM_UPDATE = 1, GM_GRAD = 2 };
 struct Layout {
     size_t off_U, off_D, off_R, off_A, off_G, off_X;
     size_t off_rowsc, off_tile, off_cot, off_sig, off_tau, off_sw, off_twr, off_w;
-    size_t off_twid, off_kj, off_aj, off_prec, off_ends, off_pert, off_sc;
+    size_t off_twid, off_twid64, off_kj, off_aj, off_prec, off_ends, off_pert, off_sc;
     size_t total;
     int max_tiles;
 };
@@ -57,11 +57,12 @@ struct Layout {
 struct CurveDev {
     int ns, nx, P, prec;   // prec: 0 = double, 1 = float
     double L, S, s0;
-    void *U, *D, *R, *A, *G, *X;
+    void *U, *D, *R, *A, *G;
+    void *X;               // FP64 physical scratch [N_s][N]
     double *rowsc, *tile;
     void *cot, *sig, *tau, *sw, *twr;
     double *w;
-    void *twid, *kj, *aj, *prec_imex;
+    void *twid, *twid64, *kj, *aj, *prec_imex;
     double *ends, *pert;
     DevScalars *sc;
 };
@@ -74,8 +75,15 @@ cudaError_t launch_scalars_init(const CurveDev &c, double lambda, int lambda_fre
                                 double dtau_lambda, int conv, cudaStream_t st);
 cudaError_t launch_set_limit(const CurveDev &c, long long nsteps, double tol, cudaStream_t st);
 cudaError_t launch_set_lambda_tau(const CurveDev &c, double lambda, double tau, cudaStream_t st);
+// Trial curve (eq. KSE_initial_curve) into the FP64 scratch X.
 cudaError_t launch_trial(const CurveDev &c, double a, int has_v, int npert, cudaStream_t st);
-cudaError_t launch_row_fwd(const CurveDev &c, const void *phys, void *spec, int keep_ends, cudaStream_t st);
+// X = (double) in  (a physical curve in the storage type)
+cudaError_t launch_widen(const CurveDev &c, const void *in, cudaStream_t st);
+// rows 0 and P of X = u_+ and u_-
+cudaError_t launch_set_ends(const CurveDev &c, cudaStream_t st);
+// spectral state = forward transform of X, computed in FP64 and rounded per
+// coefficient to the storage type
+cudaError_t launch_row_fwd_x(const CurveDev &c, void *spec, int keep_ends, cudaStream_t st);
 // spec -> phys; scale_mode 0: plain; 1: Euclidean gradient scaling -2 dx w_m
 // and zero end rows.
 cudaError_t launch_row_inv(const CurveDev &c, const void *spec, void *phys, int scale_mode, cudaStream_t st);

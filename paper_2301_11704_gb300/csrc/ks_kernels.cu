@@ -55,7 +55,7 @@ Layout make_layout(int ns, int nx, int prec)
     l.off_R = off; off += field;
     l.off_A = off; off += field;
     l.off_G = off; off += field;
-    l.off_X = off; off += field;
+    l.off_X = off; off += al256((size_t)ns * nx * 8);   // physical scratch, always FP64
     l.off_rowsc = off; off += al256((size_t)ns * 4 * 8);
     l.max_tiles = ((ns + GEMM_BM - 1) / GEMM_BM) * ((nx + GEMM_BN - 1) / GEMM_BN);
     l.off_tile = off; off += al256((size_t)l.max_tiles * 8);
@@ -67,6 +67,7 @@ Layout make_layout(int ns, int nx, int prec)
     l.off_twr = off; off += al256((size_t)ns * b);
     l.off_w = off; off += al256((size_t)ns * 8);
     l.off_twid = off; off += al256((size_t)nx * b);   // N/2 complex
+    l.off_twid64 = off; off += al256((size_t)nx * 8); // N/2 complex, FP64
     l.off_kj = off; off += al256((size_t)(nx / 2) * b);
     l.off_aj = off; off += al256((size_t)(nx / 2) * b);
     l.off_prec = off; off += al256((size_t)(nx / 2) * b);
@@ -207,6 +208,7 @@ __global__ void k_setup(CurveDev c, double dtau)
             double s, co;
             sincospi(2.0 * (double)i / (double)c.nx, &s, &co);
             twid[i] = {(T)co, (T)(-s)};
+            ((cpx<double> *)c.twid64)[i] = {co, -s};
             double k = 2.0 * M_PI * (double)i / c.L;
             double a = k * k * k * k - k * k;
             kj[i] = (T)k;
@@ -265,7 +267,7 @@ __global__ void k_trial(CurveDev c, double a, int has_v, int npert)
     const int ns = c.ns, N = c.nx, P = c.P;
     const double *up = c.ends, *um = c.ends + N;
     const double *v = c.pert, *amps = c.pert + N, *vp = c.pert + N + MAX_PERT;
-    T *X = (T *)c.X;
+    double *X = (double *)c.X;
     size_t total = (size_t)ns * N;
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
         int m = (int)(i / N), n = (int)(i % N);
@@ -288,47 +290,60 @@ __global__ void k_trial(CurveDev c, double a, int has_v, int npert)
                 val += amps[p] * sp * vp[(size_t)p * N + n];
             }
         }
-        X[i] = (T)val;
+        X[i] = val;
     }
 }
 
-// Replaces rows 0 and P of a physical curve with u_+ and u_-.
+// X (FP64 physical scratch) = a physical curve given in the storage type.
 template <typename T>
-__global__ void k_set_ends(CurveDev c, T *X)
+__global__ void k_widen(CurveDev c, const T *in)
+{
+    size_t total = (size_t)c.ns * c.nx;
+    double *X = (double *)c.X;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x)
+        X[i] = (double)in[i];
+}
+
+// Replaces rows 0 and P of a physical curve with u_+ and u_-.
+__global__ void k_set_ends(CurveDev c)
 {
     const int N = c.nx, P = c.P;
+    double *X = (double *)c.X;
     for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < N; n += gridDim.x * blockDim.x) {
-        X[n] = (T)c.ends[n];
-        X[(size_t)P * N + n] = (T)c.ends[N + n];
+        X[n] = c.ends[n];
+        X[(size_t)P * N + n] = c.ends[N + n];
     }
 }
 
 // ---------------------------------------------------------------------------
 // Row transforms (physical <-> spectral), two sections per warp
 // ---------------------------------------------------------------------------
-template <typename T, int N>
-__global__ void __launch_bounds__(ROWS_WARPS * 32) k_row_fwd(CurveDev c, const T *phys, T *spec, int keep_ends)
+// Physical -> spectral in the compute type Tc (the type of the physical input;
+// FP64 for the scratch X), rounded to the storage type To per coefficient.
+template <typename Tc, typename To, int N>
+__global__ void __launch_bounds__(ROWS_WARPS * 32) k_row_fwd(CurveDev c, const Tc *phys, To *spec, int keep_ends)
 {
     constexpr int H = N / 2;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    cpx<T> *tw = (cpx<T> *)smem_raw;
+    cpx<Tc> *tw = (cpx<Tc> *)smem_raw;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    cpx<T> *B0 = tw + H + warp * 2 * N, *B1 = B0 + N;
-    for (int t = threadIdx.x; t < H; t += blockDim.x) tw[t] = ((const cpx<T> *)c.twid)[t];
+    cpx<Tc> *B0 = tw + H + warp * 2 * N, *B1 = B0 + N;
+    const cpx<Tc> *tsrc = (const cpx<Tc> *)(sizeof(Tc) == 8 ? c.twid64 : c.twid);
+    for (int t = threadIdx.x; t < H; t += blockDim.x) tw[t] = tsrc[t];
     __syncthreads();
     const int ns = c.ns;
     const int m0 = (blockIdx.x * ROWS_WARPS + warp) * 2, m1 = m0 + 1;
     if (m0 >= ns) return;
     const bool has1 = m1 < ns;
     for (int n = lane; n < N; n += 32)
-        B0[n] = {phys[(size_t)m0 * N + n], has1 ? phys[(size_t)m1 * N + n] : T(0)};
+        B0[n] = {phys[(size_t)m0 * N + n], has1 ? phys[(size_t)m1 * N + n] : Tc(0)};
     __syncwarp();
-    cpx<T> *W = warp_fft<T, N>(B0, B1, tw, false, lane);
+    cpx<Tc> *W = warp_fft<Tc, N>(B0, B1, tw, false, lane);
     for (int j = lane; j < H; j += 32) {
-        cpx<T> A, B;
-        get_pair<T, N>(W, j, A, B);
-        if (!(keep_ends && (m0 == 0 || m0 == c.P))) st2(spec, m0, N, j, A);
-        if (has1 && !(keep_ends && m1 == c.P)) st2(spec, m1, N, j, B);
+        cpx<Tc> A, B;
+        get_pair<Tc, N>(W, j, A, B);
+        if (!(keep_ends && (m0 == 0 || m0 == c.P))) st2(spec, m0, N, j, cpx<To>{(To)A.x, (To)A.y});
+        if (has1 && !(keep_ends && m1 == c.P)) st2(spec, m1, N, j, cpx<To>{(To)B.x, (To)B.y});
     }
 }
 
@@ -752,15 +767,15 @@ static cudaError_t rows_t(const CurveDev &c, int mode, cudaStream_t st)
     });
 }
 
-template <typename T>
+template <typename Tc, typename To>
 static cudaError_t row_fwd_t(const CurveDev &c, const void *phys, void *spec, int keep_ends, cudaStream_t st)
 {
     return dispatch_n(c.nx, [&](auto nn) {
         constexpr int NN = decltype(nn)::value;
-        size_t sm = rows_smem<T>(NN, 2);
-        cudaError_t e = set_smem(k_row_fwd<T, NN>, sm);
+        size_t sm = rows_smem<Tc>(NN, 2);
+        cudaError_t e = set_smem(k_row_fwd<Tc, To, NN>, sm);
         if (e != cudaSuccess) return e;
-        k_row_fwd<T, NN><<<row_grid(c.ns), ROWS_WARPS * 32, sm, st>>>(c, (const T *)phys, (T *)spec, keep_ends);
+        k_row_fwd<Tc, To, NN><<<row_grid(c.ns), ROWS_WARPS * 32, sm, st>>>(c, (const Tc *)phys, (To *)spec, keep_ends);
         return cudaGetLastError();
     });
 }
@@ -816,17 +831,27 @@ cudaError_t launch_trial(const CurveDev &c, double a, int has_v, int npert, cuda
     return cudaGetLastError();
 }
 
-cudaError_t launch_set_ends(const CurveDev &c, void *X, cudaStream_t st)
+cudaError_t launch_set_ends(const CurveDev &c, cudaStream_t st)
 {
     int grid = (c.nx + 255) / 256;
-    if (c.prec) k_set_ends<float><<<grid, 256, 0, st>>>(c, (float *)X);
-    else k_set_ends<double><<<grid, 256, 0, st>>>(c, (double *)X);
+    k_set_ends<<<grid, 256, 0, st>>>(c);
     return cudaGetLastError();
 }
 
-cudaError_t launch_row_fwd(const CurveDev &c, const void *phys, void *spec, int keep_ends, cudaStream_t st)
+cudaError_t launch_widen(const CurveDev &c, const void *in, cudaStream_t st)
 {
-    return c.prec ? row_fwd_t<float>(c, phys, spec, keep_ends, st) : row_fwd_t<double>(c, phys, spec, keep_ends, st);
+    size_t total = (size_t)c.ns * c.nx;
+    int grid = (int)((total + 255) / 256);
+    if (grid > 4096) grid = 4096;
+    if (c.prec) k_widen<float><<<grid, 256, 0, st>>>(c, (const float *)in);
+    else k_widen<double><<<grid, 256, 0, st>>>(c, (const double *)in);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_row_fwd_x(const CurveDev &c, void *spec, int keep_ends, cudaStream_t st)
+{
+    return c.prec ? row_fwd_t<double, float>(c, c.X, spec, keep_ends, st)
+                  : row_fwd_t<double, double>(c, c.X, spec, keep_ends, st);
 }
 
 cudaError_t launch_row_inv(const CurveDev &c, const void *spec, void *phys, int scale_mode, cudaStream_t st)
