@@ -212,6 +212,30 @@ typedef struct {
 ks_status ks_curve_profile(ks_curve *c, int32_t max_steps);
 ks_status ks_curve_profile_read(ks_curve *c, ks_profile *out);
 
+/* Allocation-free cost evaluation.  The paper has no counterpart: this entry
+ * point exists for callers that cannot allocate device memory, such as a host
+ * program that owns every device allocation and hands this library only its
+ * input and output buffers, a time-critical loop that must not pay cudaMalloc's
+ * synchronisation and latency, or a process whose device memory is reserved up
+ * front.  It computes J^2 and J_arc (eq. cost_function_general, eq. J_arc) of
+ * a curve without a handle and without a workspace:
+ *   p        parameters, same rules as ks_curve_workspace_bytes; the curve's
+ *            scratch (ks_curve_workspace_bytes(p)) must not exceed
+ *            KS_NOALLOC_SCRATCH_BYTES, else KS_ENOMEM with a message.
+ *   u_dev    [N_s][N] physical curve in the storage type (rows 0 and N_s-1
+ *            are the end sections u_+ and u_-).
+ *   out_dev  device doubles [2] receiving J^2 and J_arc.
+ *   stream   cudaStream_t (NULL = legacy default stream); asynchronous.
+ * The scratch is one static device array of KS_NOALLOC_SCRATCH_BYTES, held on
+ * every device that loads the library until the process exits.  The first
+ * call on a device looks up that array's device address (with that device
+ * current); make that first call before any stream capture.  All calls share
+ * the array and it keeps the last call's contents (each call clears what must
+ * start at zero): calls that overlap on the GPU race and give wrong results.
+ * No device memory is allocated or freed. */
+#define KS_NOALLOC_SCRATCH_BYTES (32u << 20)
+ks_status ks_cost_noalloc(const ks_params *p, const void *u_dev, double *out_dev, void *stream);
+
 /* Releases the handle (host memory only; the workspace stays the caller's). */
 ks_status ks_curve_destroy(ks_curve *c);
 

@@ -22,7 +22,7 @@ EXPORTS = [
     "ks_last_error", "ks_version", "ks_curve_workspace_bytes", "ks_curve_create", "ks_curve_set_stream",
     "ks_curve_init_trial", "ks_curve_residual", "ks_curve_cost", "ks_curve_gradient", "ks_curve_descend",
     "ks_curve_descend_async", "ks_curve_scalars", "ks_curve_get_state", "ks_curve_set_state", "ks_curve_profile",
-    "ks_curve_profile_read", "ks_curve_destroy",
+    "ks_curve_profile_read", "ks_curve_destroy", "ks_cost_noalloc",
 ]
 
 
@@ -110,6 +110,7 @@ def load(build_if_missing: bool = True):
         "ks_curve_profile": (i32, [p, i32]),
         "ks_curve_profile_read": (i32, [p, ctypes.POINTER(KSProfile)]),
         "ks_curve_destroy": (i32, [p]),
+        "ks_cost_noalloc": (i32, [ctypes.POINTER(KSParams), p, p, p]),
     }
     for name, (res, args) in sigs.items():
         fn = getattr(lib, name)

@@ -168,6 +168,21 @@ void release_events(ks_curve *c)
 
 }  // namespace
 
+namespace ks {
+// Helpers for other translation units of the library: the same parameter rules
+// and the same thread-local message as the entry points of this file.
+ks_status check_params(const ks_params *p) { return validate(p); }
+
+ks_status report_error(ks_status s, const char *fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+    return s;
+}
+}  // namespace ks
+
 extern "C" {
 
 const char *ks_last_error(void) { return g_err; }

@@ -7,6 +7,8 @@
 
 #include <cuda_runtime.h>
 
+#include "../../include/ksconn.h"
+
 namespace ks {
 
 // Tile of the structured s-direction contraction (D_t or D_t^T applied to the
@@ -68,6 +70,11 @@ struct CurveDev {
 };
 
 Layout make_layout(int ns, int nx, int prec);
+
+// ks_capi.cu: parameter rules of the entry points, and the thread-local
+// message returned by ks_last_error().
+ks_status check_params(const ks_params *p);
+ks_status report_error(ks_status s, const char *fmt, ...);
 
 // ---- launchers (ks_kernels.cu); all enqueue on `st`, return the launch error
 cudaError_t launch_setup(const CurveDev &c, double dtau, cudaStream_t st);

@@ -1,0 +1,124 @@
+// ks_noalloc.cu -- ks_cost_noalloc: the cost of a curve computed without any
+// device allocation, for callers that cannot allocate device memory.
+//
+// Who needs this: a host program that embeds this library but owns every
+// device allocation itself and hands over only input and output buffers; a
+// time-critical loop in which cudaMalloc (with its implicit synchronisation and
+// unbounded latency) is not acceptable; a process whose device memory is fully
+// reserved up front.  Such a caller cannot provide the workspace that
+// ks_curve_create needs, so this entry point keeps its scratch in one
+// statically sized device array that the CUDA runtime sets up when the
+// library's module is loaded on a device.
+//
+// The scratch array (KS_NOALLOC_SCRATCH_BYTES) is held on every device that
+// loads this library until the process exits.  All calls share it and it keeps
+// the last call's contents: each call rewrites everything it reads (tables,
+// spectral fields, and the reduction scalars and arrival counters, which are
+// cleared before use), and calls that overlap on the GPU -- on two streams, or
+// from two threads -- race on it and give wrong results.
+#include <cmath>
+#include <mutex>
+
+#include "../../include/ksconn.h"
+#include "ks_internal.h"
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[KS_NOALLOC_SCRATCH_BYTES];
+
+namespace {
+
+// Device address of g_noalloc_scratch per device.  In host code the symbol
+// name is only a host-side stand-in; the address the kernels need is looked
+// up once per device with that device current.
+constexpr int kMaxDevices = 64;
+std::mutex g_mu;
+void *g_addr[kMaxDevices] = {};
+
+__global__ void k_export_cost(const ks::DevScalars *sc, double *out)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        out[0] = sc->J2;
+        out[1] = sc->Jarc;
+    }
+}
+
+ks_status na_fail(ks_status s, const char *what, cudaError_t e)
+{
+    return ks::report_error(s, "ks_cost_noalloc: %s: %s", what, cudaGetErrorString(e));
+}
+
+}  // namespace
+
+extern "C" ks_status ks_cost_noalloc(const ks_params *p, const void *u_dev, double *out_dev, void *stream)
+{
+    if (!p || !u_dev || !out_dev)
+        return ks::report_error(KS_EINVAL, "ks_cost_noalloc: p, u_dev and out_dev are required");
+    ks_status s = ks::check_params(p);
+    if (s != KS_OK) return s;
+    const ks::Layout lay = ks::make_layout(p->ns, p->nx, p->precision == KS_FP32);
+    if (lay.total > (size_t)KS_NOALLOC_SCRATCH_BYTES)
+        return ks::report_error(KS_ENOMEM,
+                                "ks_cost_noalloc: a %d x %d curve needs %zu bytes of scratch; the built-in array holds %zu",
+                                p->ns, p->nx, lay.total, (size_t)KS_NOALLOC_SCRATCH_BYTES);
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return na_fail(KS_ECUDA, "cudaGetDevice", e);
+    if (dev < 0 || dev >= kMaxDevices) return ks::report_error(KS_EINVAL, "ks_cost_noalloc: device ordinal out of range");
+    void *base = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(g_mu);
+        if (!g_addr[dev]) {
+            void *ptr = nullptr;
+            e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+            if (e != cudaSuccess || !ptr) return na_fail(KS_ECUDA, "cudaGetSymbolAddress", e);
+            g_addr[dev] = ptr;
+        }
+        base = g_addr[dev];
+    }
+
+    ks::CurveDev d{};
+    char *b = (char *)base;
+    d.ns = p->ns;
+    d.nx = p->nx;
+    d.P = p->ns - 1;
+    d.prec = p->precision == KS_FP32 ? 1 : 0;
+    d.L = p->L;
+    d.S = p->S;
+    d.s0 = p->s0;
+    d.U = b + lay.off_U;
+    d.D = b + lay.off_D;
+    d.R = b + lay.off_R;
+    d.A = b + lay.off_A;
+    d.G = b + lay.off_G;
+    d.X = b + lay.off_X;
+    d.rowsc = (double *)(b + lay.off_rowsc);
+    d.tile = (double *)(b + lay.off_tile);
+    d.cot = b + lay.off_cot;
+    d.sig = b + lay.off_sig;
+    d.tau = b + lay.off_tau;
+    d.sw = b + lay.off_sw;
+    d.twr = b + lay.off_twr;
+    d.w = (double *)(b + lay.off_w);
+    d.twid = b + lay.off_twid;
+    d.twid64 = b + lay.off_twid64;
+    d.kj = b + lay.off_kj;
+    d.aj = b + lay.off_aj;
+    d.prec_imex = b + lay.off_prec;
+    d.ends = (double *)(b + lay.off_ends);
+    d.pert = (double *)(b + lay.off_pert);
+    d.sc = (ks::DevScalars *)(b + lay.off_sc);
+
+    cudaStream_t st = (cudaStream_t)stream;
+    // tables, then the scalars and arrival counters (cleared: they must start at zero)
+    if ((e = ks::launch_setup(d, p->dtau, st)) != cudaSuccess) return na_fail(KS_ECUDA, "set-up kernel", e);
+    if ((e = ks::launch_scalars_init(d, p->lambda, 0, p->dtau, 0.0, p->conv, st)) != cudaSuccess)
+        return na_fail(KS_ECUDA, "scalar reset", e);
+    // u (storage type, physical) -> FP64 scratch -> spectral state
+    if ((e = ks::launch_widen(d, u_dev, st)) != cudaSuccess) return na_fail(KS_ECUDA, "widen", e);
+    if ((e = ks::launch_row_fwd_x(d, d.U, 0, st)) != cudaSuccess) return na_fail(KS_ECUDA, "forward transform", e);
+    // D_t u, then the row phase with the FP64 cost reduction
+    if ((e = ks::launch_dt(d, ks::GM_STORE, 0, 0, st)) != cudaSuccess) return na_fail(KS_ECUDA, "D_t u", e);
+    if ((e = ks::launch_rows(d, ks::ROWS_EVAL, st)) != cudaSuccess) return na_fail(KS_ECUDA, "row phase", e);
+    k_export_cost<<<1, 32, 0, st>>>(d.sc, out_dev);
+    if ((e = cudaGetLastError()) != cudaSuccess) return na_fail(KS_ECUDA, "export", e);
+    return KS_OK;
+}
