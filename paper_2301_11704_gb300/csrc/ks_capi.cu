@@ -20,7 +20,13 @@ struct ks_curve {
     std::vector<cudaEvent_t> events;
     int prof_cap = 0;      // steps that fit in `events`
     int prof_used = 0;     // steps recorded so far
+    // CUDA graph of GRAPH_STEPS descent steps, captured once on a private stream
+    cudaGraphExec_t gexec = nullptr;
+    cudaStream_t gstream = nullptr;
+    int gdiscrete = -1;
 };
+
+static const int GRAPH_STEPS = 16;
 
 static thread_local char g_err[512];
 
@@ -79,41 +85,7 @@ ks_status validate(const ks_params *p)
     return KS_OK;
 }
 
-ks::CurveDev make_dev(const ks_params *p, const ks::Layout &l, void *ws)
-{
-    ks::CurveDev d{};
-    char *b = (char *)ws;
-    d.ns = p->ns;
-    d.nx = p->nx;
-    d.P = p->ns - 1;
-    d.prec = p->precision == KS_FP32 ? 1 : 0;
-    d.L = p->L;
-    d.S = p->S;
-    d.s0 = p->s0;
-    d.U = b + l.off_U;
-    d.D = b + l.off_D;
-    d.R = b + l.off_R;
-    d.A = b + l.off_A;
-    d.G = b + l.off_G;
-    d.X = b + l.off_X;
-    d.rowsc = (double *)(b + l.off_rowsc);
-    d.tile = (double *)(b + l.off_tile);
-    d.cot = b + l.off_cot;
-    d.sig = b + l.off_sig;
-    d.tau = b + l.off_tau;
-    d.sw = b + l.off_sw;
-    d.twr = b + l.off_twr;
-    d.w = (double *)(b + l.off_w);
-    d.twid = b + l.off_twid;
-    d.twid64 = b + l.off_twid64;
-    d.kj = b + l.off_kj;
-    d.aj = b + l.off_aj;
-    d.prec_imex = b + l.off_prec;
-    d.ends = (double *)(b + l.off_ends);
-    d.pert = (double *)(b + l.off_pert);
-    d.sc = (ks::DevScalars *)(b + l.off_sc);
-    return d;
-}
+ks::CurveDev make_dev(const ks_params *p, const ks::Layout &l, void *ws) { return ks::bind_layout(p, l, ws); }
 
 ks_status check_handle(ks_curve *c)
 {
@@ -135,10 +107,59 @@ ks_status read_scalars(ks_curve *c, ks::DevScalars *h)
     return KS_OK;
 }
 
+ks_status launch_step(ks_curve *c, int discrete, cudaStream_t st)
+{
+    KS_CUDA(ks::launch_rows(c->d, ks::ROWS_STEP, st));
+    KS_CUDA(ks::launch_dt(c->d, ks::GM_UPDATE, discrete, 1, st));
+    KS_CUDA(ks::launch_dt(c->d, ks::GM_STORE, 0, 1, st));
+    return KS_OK;
+}
+
+// Captures GRAPH_STEPS steps into an executable graph (once per curve and
+// adjoint mode).  Every kernel reads its gates from the device scalars, so the
+// same graph serves any step count and stops cleanly at convergence.
+ks_status ensure_graph(ks_curve *c, int discrete)
+{
+    if (c->gexec && c->gdiscrete == discrete) return KS_OK;
+    if (c->gexec) {
+        cudaGraphExecDestroy(c->gexec);
+        c->gexec = nullptr;
+    }
+    if (!c->gstream) KS_CUDA(cudaStreamCreateWithFlags(&c->gstream, cudaStreamNonBlocking));
+    KS_CUDA(cudaStreamBeginCapture(c->gstream, cudaStreamCaptureModeThreadLocal));
+    ks_status s = KS_OK;
+    for (int i = 0; i < GRAPH_STEPS && s == KS_OK; ++i) s = launch_step(c, discrete, c->gstream);
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamEndCapture(c->gstream, &graph);
+    if (s != KS_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return s;
+    }
+    if (e != cudaSuccess) return fail(KS_ECUDA, "graph capture failed: %s", cudaGetErrorString(e));
+    e = cudaGraphInstantiate(&c->gexec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+        c->gexec = nullptr;
+        return fail(KS_ECUDA, "graph instantiation failed: %s", cudaGetErrorString(e));
+    }
+    c->gdiscrete = discrete;
+    return KS_OK;
+}
+
 ks_status enqueue_steps(ks_curve *c, int64_t nsteps, double tol)
 {
     const int discrete = c->p.adjoint == KS_ADJ_DISCRETE;
     KS_CUDA(ks::launch_set_limit(c->d, (long long)nsteps, tol, c->st));
+    if (c->prof_used >= c->prof_cap && nsteps >= GRAPH_STEPS) {
+        ks_status s = ensure_graph(c, discrete);
+        if (s != KS_OK) return s;
+        for (int64_t g = 0; g < nsteps / GRAPH_STEPS; ++g) KS_CUDA(cudaGraphLaunch(c->gexec, c->st));
+        for (int64_t r = 0; r < nsteps % GRAPH_STEPS; ++r) {
+            s = launch_step(c, discrete, c->st);
+            if (s != KS_OK) return s;
+        }
+        return KS_OK;
+    }
     for (int64_t s = 0; s < nsteps; ++s) {
         const bool prof = c->prof_used < c->prof_cap;
         cudaEvent_t *ev = prof ? &c->events[(size_t)6 * c->prof_used] : nullptr;
@@ -495,6 +516,8 @@ ks_status ks_curve_destroy(ks_curve *c)
     {
         DeviceGuard g(c->device);
         release_events(c);
+        if (c->gexec) cudaGraphExecDestroy(c->gexec);
+        if (c->gstream) cudaStreamDestroy(c->gstream);
     }
     delete c;
     return KS_OK;

@@ -11,13 +11,16 @@
 
 namespace ks {
 
-// Tile of the structured s-direction contraction (D_t or D_t^T applied to the
-// columns of a curve).  BM output sections x BN real columns per CTA, BK
-// sections of the contraction per shared-memory stage.
-constexpr int GEMM_BM = 32;
-constexpr int GEMM_BN = 32;
-constexpr int GEMM_BK = 32;
-constexpr int GEMM_THREADS = 256;
+// Structured s-direction contraction (D_t or W^-1 D_t^T W applied to the
+// columns of a curve): DT_BM output sections x BN real columns per CTA, DT_BK
+// sections of the contraction per shared-memory stage, the contraction split
+// over `ksplit` CTAs when the tiles alone cannot fill the GPU.
+constexpr int DT_BM = 32;
+constexpr int DT_BK = 32;
+constexpr int DT_THREADS = 256;
+constexpr int DT_TARGET_CTAS = 256;   // split the contraction until about this many CTAs run
+constexpr int DT_MIN_KCHUNK = 64;     // but keep at least this many sections per split
+constexpr int DT_MAX_SPLIT = 8;       // the splits of one tile form one thread-block cluster
 
 // Sections handled per CTA by the row (x-direction) kernels: two rows per warp,
 // packed into one complex FFT.
@@ -47,13 +50,14 @@ struct DevScalars {
 enum RowsMode { ROWS_STEP = 0, ROWS_EVAL = 1 };
 enum GemmMode { GM_STORE = 0, GM_UPDATE = 1, GM_GRAD = 2 };
 
-// Pointers into the caller's workspace (typed as void* for the storage type).
+// Offsets into the caller's workspace.
 struct Layout {
     size_t off_U, off_D, off_R, off_A, off_G, off_X;
-    size_t off_rowsc, off_tile, off_cot, off_sig, off_tau, off_sw, off_twr, off_w;
+    size_t off_rowsc, off_bpart, off_tile, off_tcnt, off_part;
+    size_t off_cot, off_sig, off_tau, off_sw, off_twr, off_w;
     size_t off_twid, off_twid64, off_kj, off_aj, off_prec, off_ends, off_pert, off_sc;
     size_t total;
-    int max_tiles;
+    int bn, tiles_r, tiles_c, ksplit, kchunk, row_blocks;
 };
 
 struct CurveDev {
@@ -61,7 +65,12 @@ struct CurveDev {
     double L, S, s0;
     void *U, *D, *R, *A, *G;
     void *X;               // FP64 physical scratch [N_s][N]
-    double *rowsc, *tile;
+    double *rowsc;         // [N_s][4] row sums (end rows: |u|^2, |f|^2)
+    double *bpart;         // [row_blocks][5] per-CTA partial sums of the row phase
+    double *tile;          // [tiles] per-tile |G|^2 partials
+    unsigned *tcnt;        // [tiles] split arrival counters (zero between launches)
+    void *part;            // [ksplit][N_s][N] split partial sums (ksplit > 1)
+    int bn, tiles_r, tiles_c, ksplit, kchunk, row_blocks;
     void *cot, *sig, *tau, *sw, *twr;
     double *w;
     void *twid, *twid64, *kj, *aj, *prec_imex;
@@ -70,6 +79,8 @@ struct CurveDev {
 };
 
 Layout make_layout(int ns, int nx, int prec);
+// Pointers of a curve whose workspace starts at `base` (256-byte aligned).
+CurveDev bind_layout(const ks_params *p, const Layout &l, void *base);
 
 // ks_capi.cu: parameter rules of the entry points, and the thread-local
 // message returned by ks_last_error().
@@ -78,6 +89,7 @@ ks_status report_error(ks_status s, const char *fmt, ...);
 
 // ---- launchers (ks_kernels.cu); all enqueue on `st`, return the launch error
 cudaError_t launch_setup(const CurveDev &c, double dtau, cudaStream_t st);
+// Resets the scalars and the split arrival counters (which must start at zero).
 cudaError_t launch_scalars_init(const CurveDev &c, double lambda, int lambda_free, double dtau,
                                 double dtau_lambda, int conv, cudaStream_t st);
 cudaError_t launch_set_limit(const CurveDev &c, long long nsteps, double tol, cudaStream_t st);

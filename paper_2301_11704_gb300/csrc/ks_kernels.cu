@@ -24,6 +24,8 @@
 #include <cmath>
 #include <type_traits>
 
+#include <cooperative_groups.h>
+
 #include "ks_internal.h"
 
 namespace ks {
@@ -49,6 +51,21 @@ Layout make_layout(int ns, int nx, int prec)
     Layout l{};
     size_t b = prec ? 4 : 8;
     size_t field = al256((size_t)ns * nx * b);
+    // tiling and split of the s-contraction
+    l.bn = nx >= 64 ? 64 : 32;
+    l.tiles_r = (ns + DT_BM - 1) / DT_BM;
+    l.tiles_c = (nx + l.bn - 1) / l.bn;
+    int tiles = l.tiles_r * l.tiles_c;
+    int ks = tiles < DT_TARGET_CTAS ? DT_TARGET_CTAS / tiles : 1;
+    int kmax = ns / DT_MIN_KCHUNK;
+    if (ks > kmax) ks = kmax;
+    if (ks > DT_MAX_SPLIT) ks = DT_MAX_SPLIT;
+    if (ks < 1) ks = 1;
+    int kc = (ns + ks - 1) / ks;
+    kc = (kc + DT_BK - 1) / DT_BK * DT_BK;
+    l.kchunk = kc;
+    l.ksplit = (ns + kc - 1) / kc;
+    l.row_blocks = (ns + ROWS_PER_CTA - 1) / ROWS_PER_CTA;
     size_t off = 0;
     l.off_U = off; off += field;
     l.off_D = off; off += field;
@@ -57,8 +74,10 @@ Layout make_layout(int ns, int nx, int prec)
     l.off_G = off; off += field;
     l.off_X = off; off += al256((size_t)ns * nx * 8);   // physical scratch, always FP64
     l.off_rowsc = off; off += al256((size_t)ns * 4 * 8);
-    l.max_tiles = ((ns + GEMM_BM - 1) / GEMM_BM) * ((nx + GEMM_BN - 1) / GEMM_BN);
-    l.off_tile = off; off += al256((size_t)l.max_tiles * 8);
+    l.off_bpart = off; off += al256((size_t)l.row_blocks * 5 * 8);
+    l.off_tile = off; off += al256((size_t)tiles * l.ksplit * 8);
+    l.off_tcnt = off; off += al256((size_t)tiles * 4);
+    l.off_part = off;
     int P = ns - 1;
     l.off_cot = off; off += al256((size_t)2 * P * b);
     l.off_sig = off; off += al256((size_t)ns * b);
@@ -76,6 +95,51 @@ Layout make_layout(int ns, int nx, int prec)
     l.off_sc = off; off += al256(sizeof(DevScalars));
     l.total = off;
     return l;
+}
+
+CurveDev bind_layout(const ks_params *p, const Layout &l, void *base)
+{
+    CurveDev d{};
+    char *b = (char *)base;
+    d.ns = p->ns;
+    d.nx = p->nx;
+    d.P = p->ns - 1;
+    d.prec = p->precision == KS_FP32 ? 1 : 0;
+    d.L = p->L;
+    d.S = p->S;
+    d.s0 = p->s0;
+    d.U = b + l.off_U;
+    d.D = b + l.off_D;
+    d.R = b + l.off_R;
+    d.A = b + l.off_A;
+    d.G = b + l.off_G;
+    d.X = b + l.off_X;
+    d.rowsc = (double *)(b + l.off_rowsc);
+    d.bpart = (double *)(b + l.off_bpart);
+    d.tile = (double *)(b + l.off_tile);
+    d.tcnt = (unsigned *)(b + l.off_tcnt);
+    d.part = nullptr;
+    d.bn = l.bn;
+    d.tiles_r = l.tiles_r;
+    d.tiles_c = l.tiles_c;
+    d.ksplit = l.ksplit;
+    d.kchunk = l.kchunk;
+    d.row_blocks = l.row_blocks;
+    d.cot = b + l.off_cot;
+    d.sig = b + l.off_sig;
+    d.tau = b + l.off_tau;
+    d.sw = b + l.off_sw;
+    d.twr = b + l.off_twr;
+    d.w = (double *)(b + l.off_w);
+    d.twid = b + l.off_twid;
+    d.twid64 = b + l.off_twid64;
+    d.kj = b + l.off_kj;
+    d.aj = b + l.off_aj;
+    d.prec_imex = b + l.off_prec;
+    d.ends = (double *)(b + l.off_ends);
+    d.pert = (double *)(b + l.off_pert);
+    d.sc = (DevScalars *)(b + l.off_sc);
+    return d;
 }
 
 // ---------------------------------------------------------------------------
@@ -146,7 +210,8 @@ __device__ __forceinline__ void st2(T *p, int m, int N, int j, cpx<T> v)
     q[1] = (j == 0) ? T(0) : v.y;
 }
 
-__device__ __forceinline__ double warp_sum(double v)
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v)
 {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -218,9 +283,10 @@ __global__ void k_setup(CurveDev c, double dtau)
     }
 }
 
-__global__ void k_scalars_init(DevScalars *sc, double lambda, int lambda_free, double dtau,
-                               double dtau_lambda, int conv)
+__global__ void k_scalars_init(DevScalars *sc, unsigned *tcnt, int ntiles, double lambda, int lambda_free,
+                               double dtau, double dtau_lambda, int conv)
 {
+    for (int i = threadIdx.x; i < ntiles; i += blockDim.x) tcnt[i] = 0u;
     if (threadIdx.x == 0 && blockIdx.x == 0) {
         DevScalars z{};
         z.lambda = lambda;
@@ -405,7 +471,8 @@ __global__ void __launch_bounds__(ROWS_WARPS * 32) k_rows(CurveDev c, int mode)
     cpx<T> *tw = (cpx<T> *)smem_raw;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     cpx<T> *B0 = tw + H + warp * 3 * N, *B1 = B0 + N, *B2 = B1 + N;
-    __shared__ double red[ROWS_WARPS * 32];
+    __shared__ double red5[5][ROWS_WARPS * 32];
+    __shared__ double wpart[ROWS_WARPS][5];
     __shared__ int am_last;
     DevScalars *sc = c.sc;
 
@@ -427,7 +494,9 @@ __global__ void __launch_bounds__(ROWS_WARPS * 32) k_rows(CurveDev c, int mode)
         const bool has1 = m1 < ns;
         const bool in0 = (m0 > 0 && m0 < P), in1 = has1 && (m1 > 0 && m1 < P);
         cpx<T> ua[MPL], ub[MPL], ra[MPL], rb[MPL];
-        double s0[5] = {0, 0, 0, 0, 0}, s1[5] = {0, 0, 0, 0, 0};   // nr, nd, ndr, nu, nf
+        // sums over the modes of a section, in the storage type (N/2 <= 128 terms);
+        // sections are combined in FP64 below
+        T s0[5] = {0, 0, 0, 0, 0}, s1[5] = {0, 0, 0, 0, 0};   // nr, nd, ndr, nu, nf
         // spectrum of u_a + i u_b
 #pragma unroll
         for (int i = 0; i < MPL; ++i) {
@@ -463,17 +532,17 @@ __global__ void __launch_bounds__(ROWS_WARPS * 32) k_rows(CurveDev c, int mode)
                 ra[i] = in0 ? cpx<T>{fa.x - lam * da.x, fa.y - lam * da.y} : cpx<T>{0, 0};
                 rb[i] = in1 ? cpx<T>{fb.x - lam * db.x, fb.y - lam * db.y} : cpx<T>{0, 0};
                 if (j == 0) { ra[i].y = 0; rb[i].y = 0; fa.y = 0; fb.y = 0; }
-                const double cw = (j == 0) ? 1.0 : 2.0;
-                s0[0] += cw * ((double)ra[i].x * ra[i].x + (double)ra[i].y * ra[i].y);
-                s0[1] += cw * ((double)da.x * da.x + (double)da.y * da.y);
-                s0[2] += cw * ((double)da.x * ra[i].x + (double)da.y * ra[i].y);
-                s0[3] += cw * ((double)ua[i].x * ua[i].x + (double)ua[i].y * ua[i].y);
-                s0[4] += cw * ((double)fa.x * fa.x + (double)fa.y * fa.y);
-                s1[0] += cw * ((double)rb[i].x * rb[i].x + (double)rb[i].y * rb[i].y);
-                s1[1] += cw * ((double)db.x * db.x + (double)db.y * db.y);
-                s1[2] += cw * ((double)db.x * rb[i].x + (double)db.y * rb[i].y);
-                s1[3] += cw * ((double)ub[i].x * ub[i].x + (double)ub[i].y * ub[i].y);
-                s1[4] += cw * ((double)fb.x * fb.x + (double)fb.y * fb.y);
+                const T cw = (j == 0) ? T(1) : T(2);
+                s0[0] += cw * (ra[i].x * ra[i].x + ra[i].y * ra[i].y);
+                s0[1] += cw * (da.x * da.x + da.y * da.y);
+                s0[2] += cw * (da.x * ra[i].x + da.y * ra[i].y);
+                s0[3] += cw * (ua[i].x * ua[i].x + ua[i].y * ua[i].y);
+                s0[4] += cw * (fa.x * fa.x + fa.y * fa.y);
+                s1[0] += cw * (rb[i].x * rb[i].x + rb[i].y * rb[i].y);
+                s1[1] += cw * (db.x * db.x + db.y * db.y);
+                s1[2] += cw * (db.x * rb[i].x + db.y * rb[i].y);
+                s1[3] += cw * (ub[i].x * ub[i].x + ub[i].y * ub[i].y);
+                s1[4] += cw * (fb.x * fb.x + fb.y * fb.y);
             }
         }
         __syncwarp();
@@ -518,25 +587,47 @@ __global__ void __launch_bounds__(ROWS_WARPS * 32) k_rows(CurveDev c, int mode)
             s1[q] = warp_sum(s1[q]);
         }
         if (lane == 0) {
-            const double L = c.L;
-            double *rs = c.rowsc + (size_t)m0 * 4;
-            bool end0 = !in0;
-            rs[0] = L * (end0 ? s0[3] : s0[0]);
-            rs[1] = L * s0[1];
-            rs[2] = L * s0[2];
-            rs[3] = L * s0[4];
-            if (has1) {
-                double *rt = c.rowsc + (size_t)m1 * 4;
-                bool end1 = !in1;
-                rt[0] = L * (end1 ? s1[3] : s1[0]);
-                rt[1] = L * s1[1];
-                rt[2] = L * s1[2];
-                rt[3] = L * s1[4];
+            // per-section norms |q_m|^2 = L sum_j c_j |q^_j|^2 (FP64 from here on)
+            const double L = c.L, lamd = sc->lambda, al = fabs(lamd);
+            double v[5] = {0, 0, 0, 0, 0};
+            const int ms[2] = {m0, m1};
+            const bool ins[2] = {in0, in1};
+            // per-section terms in the storage type; their sum over sections in FP64
+            const T Lt = (T)L, alt = (T)al, l2 = (T)(lamd * lamd);
+            for (int q = 0; q < 2; ++q) {
+                if (q == 1 && !has1) break;
+                const T *sq = q ? s1 : s0;
+                const T nr = Lt * sq[0], nd = Lt * sq[1], ndr = Lt * sq[2];
+                double *rs = c.rowsc + (size_t)ms[q] * 4;
+                rs[0] = ins[q] ? (double)nr : (double)(Lt * sq[3]);
+                rs[1] = (double)nd;
+                rs[2] = (double)ndr;
+                rs[3] = (double)(Lt * sq[4]);
+                if (ins[q]) {
+                    const T w = (T)c.w[ms[q]], sd = sqrt(nd);
+                    v[0] += (double)(w * nr);                 // J^2
+                    v[1] += (double)(w * sqrt(nr) * alt * sd); // J_arc numerator
+                    v[2] += (double)(w * alt * sd);           // J_arc denominator
+                    v[3] += (double)(w * ndr);                // <d, r>_W
+                    v[4] += (double)(w * l2 * nd);            // |l d|_W^2
+                }
             }
+#pragma unroll
+            for (int q = 0; q < 5; ++q) wpart[warp][q] = v[q];
         }
+    } else if (lane == 0) {
+#pragma unroll
+        for (int q = 0; q < 5; ++q) wpart[warp][q] = 0.0;
+    }
+    __syncthreads();
+    if (threadIdx.x < 5) {
+        double t = 0.0;
+#pragma unroll
+        for (int w = 0; w < ROWS_WARPS; ++w) t += wpart[w][threadIdx.x];
+        c.bpart[(size_t)blockIdx.x * 5 + threadIdx.x] = t;
     }
 
-    // ---- last CTA: FP64 reduction over the sections in a fixed order
+    // ---- last CTA: FP64 reduction over the CTAs' partial sums in a fixed order
     __threadfence();
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -546,25 +637,22 @@ __global__ void __launch_bounds__(ROWS_WARPS * 32) k_rows(CurveDev c, int mode)
     __syncthreads();
     if (!am_last) return;
     __threadfence();
-    const double lamd = sc->lambda, al = fabs(lamd);
-    double t_j2 = 0, t_num = 0, t_den = 0, t_dl = 0, t_d2 = 0;
-    for (int m = 1 + threadIdx.x; m < P; m += blockDim.x) {
-        const double nr = __ldcg(c.rowsc + 4 * (size_t)m), nd = __ldcg(c.rowsc + 4 * (size_t)m + 1);
-        const double ndr = __ldcg(c.rowsc + 4 * (size_t)m + 2);
-        const double w = c.w[m];
-        const double sd = sqrt(nd);
-        t_j2 += w * nr;
-        t_num += w * sqrt(nr) * al * sd;
-        t_den += w * al * sd;
-        t_dl += w * ndr;
-        t_d2 += w * lamd * lamd * nd;
+    double t[5] = {0, 0, 0, 0, 0};
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x)
+#pragma unroll
+        for (int q = 0; q < 5; ++q) t[q] += __ldcg(c.bpart + (size_t)b * 5 + q);
+#pragma unroll
+    for (int q = 0; q < 5; ++q) red5[q][threadIdx.x] = t[q];
+    __syncthreads();
+    for (int sidx = ROWS_WARPS * 16; sidx > 0; sidx >>= 1) {
+        if ((int)threadIdx.x < sidx)
+#pragma unroll
+            for (int q = 0; q < 5; ++q) red5[q][threadIdx.x] += red5[q][threadIdx.x + sidx];
+        __syncthreads();
     }
-    t_j2 = block_sum<ROWS_WARPS * 32>(t_j2, red);
-    t_num = block_sum<ROWS_WARPS * 32>(t_num, red);
-    t_den = block_sum<ROWS_WARPS * 32>(t_den, red);
-    t_dl = block_sum<ROWS_WARPS * 32>(t_dl, red);
-    t_d2 = block_sum<ROWS_WARPS * 32>(t_d2, red);
     if (threadIdx.x == 0) {
+        const double lamd = sc->lambda;
+        const double t_j2 = red5[0][0], t_num = red5[1][0], t_den = red5[2][0], t_dl = red5[3][0], t_d2 = red5[4][0];
         sc->J2 = t_j2;
         sc->Jarc = t_den > 0 ? t_num / t_den : 0.0;
         sc->dJdl = -2.0 * t_dl;
@@ -598,20 +686,28 @@ __global__ void __launch_bounds__(ROWS_WARPS * 32) k_rows(CurveDev c, int mode)
 // Y[j][col] = rowscale_j * sum_m (cot[(j+m) mod 2P] + tsign cot[(j-m) mod 2P]) colscale_m X[m][col]
 //   D_t:          colscale = tau, rowscale = sigma, tsign = +1
 //   W^-1 D_t^T W: colscale = sigma w, rowscale = tau / w, tsign = -1
-// Epilogues:
+// CTA (tile_c, tile_r, ks) computes a DT_BM x BN output tile over the sections
+// [ks kchunk, (ks+1) kchunk).  Each DT_BK-stage builds its D_t tile in shared
+// memory from two contiguous windows of the cot table (one for j+m, one for
+// j-m).  With ksplit > 1 the partial tiles go to `part` and the last CTA of a
+// tile to arrive sums them in split order (deterministic) and runs the epilogue:
 //   GM_STORE:  D = Y                                  (D_t u of the new state)
 //   GM_UPDATE: e = +l Y (published adjoint) or -l Y (discrete adjoint),
 //              G = -(A^ + e) on interior rows, u += dtau G / (1 + dtau a_j^2)
 //              (the semi-implicit step of Sec. V.C.3 in its algebraically
 //              equivalent increment form), FP64 sum_m w_m |G_m|^2
 //   GM_GRAD:   as GM_UPDATE but G is written out instead of updating u.
-template <typename T>
-__global__ void __launch_bounds__(GEMM_THREADS) k_dt(CurveDev c, int mode, int discrete, int gate)
+template <typename T, int BN>
+__global__ void __launch_bounds__(DT_THREADS) k_dt(CurveDev c, int mode, int discrete, int gate)
 {
-    constexpr int BM = GEMM_BM, BN = GEMM_BN, BK = GEMM_BK;
-    __shared__ T Ks[BM][BK + 1];
-    __shared__ T Xs[BK][BN];
-    __shared__ double red[GEMM_THREADS];
+    namespace cg = cooperative_groups;
+    constexpr int BM = DT_BM, BK = DT_BK, TM = 2, TN = BN / 16, WIN = BM + BK - 1;
+    constexpr int XPT = BK * BN / DT_THREADS;   // X values per thread per stage
+    __shared__ __align__(16) T Ks[BK][BM];
+    __shared__ __align__(16) T Xs[BK][BN];
+    __shared__ __align__(16) T Pt[BM][BN];       // this split's partial tile (read by the cluster)
+    __shared__ T Wp[WIN + 1], Wm[WIN + 1];
+    __shared__ double red[DT_THREADS];
     __shared__ int am_last;
     DevScalars *sc = c.sc;
     if (gate && !sc->active) return;
@@ -623,81 +719,136 @@ __global__ void __launch_bounds__(GEMM_THREADS) k_dt(CurveDev c, int mode, int d
     const T *rowscale = (const T *)(discrete ? c.twr : c.sig);
     const T tsign = discrete ? T(-1) : T(1);
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-    const int j0 = blockIdx.y * BM, c0 = blockIdx.x * BN;
-    T acc[2][2] = {{0, 0}, {0, 0}};
+    const int tile_c = blockIdx.x, tile_r = blockIdx.y, ks = blockIdx.z;
+    const int j0 = tile_r * BM, c0 = tile_c * BN;
+    const int kbeg = ks * c.kchunk, kend = min(ns, kbeg + c.kchunk);
+    T acc[TM][TN];
+#pragma unroll
+    for (int i = 0; i < TM; ++i)
+#pragma unroll
+        for (int l = 0; l < TN; ++l) acc[i][l] = T(0);
 
-    for (int m0 = 0; m0 < ns; m0 += BK) {
-        for (int e = threadIdx.x; e < BK * BN; e += GEMM_THREADS) {
-            int kk = e / BN, cc = e % BN;
-            int m = m0 + kk, col = c0 + cc;
-            Xs[kk][cc] = (m < ns && col < N) ? colscale[m] * X[(size_t)m * N + col] : T(0);
+    // register-staged operands of one stage: scaled X values and the two cot windows
+    T xr[XPT], wpr = T(0), wmr = T(0);
+    auto fetch = [&](int m0) {
+#pragma unroll
+        for (int q = 0; q < XPT; ++q) {
+            const int e = threadIdx.x + q * DT_THREADS;
+            const int kk = e / BN, cc = e % BN, m = m0 + kk, col = c0 + cc;
+            xr[q] = (m < kend && col < N) ? colscale[m] * X[(size_t)m * N + col] : T(0);
         }
-        for (int e = threadIdx.x; e < BM * BK; e += GEMM_THREADS) {
-            int jj = e / BK, kk = e % BK;
-            int j = j0 + jj, m = m0 + kk;
-            T v = 0;
-            if (j < ns && m < ns) {
-                int ip = j + m;
-                if (ip >= twoP) ip -= twoP;
-                int im = j - m;
-                if (im < 0) im += twoP;
-                v = cot[ip] + tsign * cot[im];
-            }
-            Ks[jj][kk] = v;
+        if (threadIdx.x < WIN) {
+            int ip = (j0 + m0 + (int)threadIdx.x) % twoP;
+            int im = (j0 - m0 - BK + 1 + (int)threadIdx.x) % twoP;
+            if (im < 0) im += twoP;
+            wpr = cot[ip];
+            wmr = cot[im];
+        }
+    };
+    if (kbeg < kend) fetch(kbeg);
+    for (int m0 = kbeg; m0 < kend; m0 += BK) {
+#pragma unroll
+        for (int q = 0; q < XPT; ++q) {
+            const int e = threadIdx.x + q * DT_THREADS;
+            Xs[e / BN][e % BN] = xr[q];
+        }
+        if (threadIdx.x < WIN) {
+            Wp[threadIdx.x] = wpr;
+            Wm[threadIdx.x] = wmr;
         }
         __syncthreads();
-#pragma unroll
+        if (m0 + BK < kend) fetch(m0 + BK);      // next stage in flight while this one computes
+        // D_t tile, stored [kk][jj]: K(j0+jj, m0+kk) = Wp[jj+kk] + tsign Wm[jj-kk+BK-1]
+        for (int e = threadIdx.x; e < BK * BM; e += DT_THREADS) {
+            const int kk = e / BM, jj = e % BM;
+            Ks[kk][jj] = Wp[jj + kk] + tsign * Wm[jj - kk + BK - 1];
+        }
+        __syncthreads();
+#pragma unroll 8
         for (int kk = 0; kk < BK; ++kk) {
-            const T a0 = Ks[2 * ty][kk], a1 = Ks[2 * ty + 1][kk];
-            const T b0 = Xs[kk][2 * tx], b1 = Xs[kk][2 * tx + 1];
-            acc[0][0] += a0 * b0;
-            acc[0][1] += a0 * b1;
-            acc[1][0] += a1 * b0;
-            acc[1][1] += a1 * b1;
+            T a[TM], b[TN];
+#pragma unroll
+            for (int i = 0; i < TM; ++i) a[i] = Ks[kk][ty * TM + i];
+#pragma unroll
+            for (int l = 0; l < TN; ++l) b[l] = Xs[kk][tx * TN + l];
+#pragma unroll
+            for (int i = 0; i < TM; ++i)
+#pragma unroll
+                for (int l = 0; l < TN; ++l) acc[i][l] += a[i] * b[l];
         }
         __syncthreads();
     }
 
-    if (mode == GM_STORE) {
-        T *Dout = (T *)c.D;
+    // ---- sum of the splits of this tile inside the cluster (distributed shared memory)
+    const int ntiles = gridDim.x * gridDim.y;
+    const int nsplit = c.ksplit;
+    // outputs this CTA finishes: rows [r0, r1) of the tile, all columns
+    const int rows_per = (BM + nsplit - 1) / nsplit;
+    const int r0 = min(BM, ks * rows_per), r1 = min(BM, r0 + rows_per);
+    if (nsplit > 1) {
+        cg::cluster_group cluster = cg::this_cluster();
 #pragma unroll
-        for (int i = 0; i < 2; ++i)
+        for (int i = 0; i < TM; ++i)
 #pragma unroll
-            for (int l = 0; l < 2; ++l) {
-                int j = j0 + 2 * ty + i, col = c0 + 2 * tx + l;
-                if (j < ns && col < N) Dout[(size_t)j * N + col] = rowscale[j] * acc[i][l];
+            for (int l = 0; l < TN; ++l) Pt[ty * TM + i][tx * TN + l] = acc[i][l];
+        cluster.sync();
+        // this CTA's row band, read from every split in split order
+        for (int e = threadIdx.x; e < (r1 - r0) * BN; e += DT_THREADS) {
+            const int jj = r0 + e / BN, cc = e % BN;
+            T t = T(0);
+            for (int q = 0; q < nsplit; ++q) {
+                const T *rem = cluster.map_shared_rank(&Pt[0][0], q);
+                t += rem[jj * BN + cc];
             }
-        return;
+            ((T *)Ks)[e] = t;      // the band's sums, row-major with BN per row
+        }
+        cluster.sync();           // no CTA leaves while its partial tile may still be read
+        __syncthreads();
     }
 
+    // Epilogue over the outputs this CTA owns.  With splits: the band [r0, r1) held in
+    // Ks (row-major, BN per row); without: the thread's own accumulators.
+    T *Dout = (T *)c.D;
     const T lam = (T)sc->lambda, dtau = (T)sc->dtau;
     const T *Ah = (const T *)c.A, *pr = (const T *)c.prec_imex;
     T *U = (T *)c.U, *G = (T *)c.G;
-    double part = 0.0;
-#pragma unroll
-    for (int i = 0; i < 2; ++i)
-#pragma unroll
-        for (int l = 0; l < 2; ++l) {
-            int j = j0 + 2 * ty + i, col = c0 + 2 * tx + l;
-            if (j >= ns || col >= N) continue;
-            const bool interior = (j > 0 && j < P);
-            T g = 0;
-            if (interior && col != 1) {
-                const T y = rowscale[j] * acc[i][l];
-                const T e = discrete ? -lam * y : lam * y;
-                g = -(Ah[(size_t)j * N + col] + e);
-                const double cw = (col < 2) ? 1.0 : 2.0;
-                part += c.w[j] * cw * (double)g * (double)g;
-            }
-            if (mode == GM_UPDATE) {
-                if (interior) U[(size_t)j * N + col] += dtau * pr[col >> 1] * g;
-            } else {
-                G[(size_t)j * N + col] = g;
-            }
+    double partsum = 0.0;
+    auto emit = [&](int j, int col, T y0) {
+        if (j >= ns || col >= N) return;
+        const T y = rowscale[j] * y0;
+        if (mode == GM_STORE) {
+            Dout[(size_t)j * N + col] = y;
+            return;
         }
-    part = block_sum<GEMM_THREADS>(part, red);
-    const int bid = blockIdx.y * gridDim.x + blockIdx.x, nb = gridDim.x * gridDim.y;
-    if (threadIdx.x == 0) c.tile[bid] = part;
+        const bool interior = (j > 0 && j < P);
+        T g = 0;
+        if (interior && col != 1) {
+            const T e = discrete ? -lam * y : lam * y;
+            g = -(Ah[(size_t)j * N + col] + e);
+            const double cw = (col < 2) ? 1.0 : 2.0;
+            partsum += c.w[j] * cw * (double)g * (double)g;
+        }
+        if (mode == GM_UPDATE) {
+            if (interior) U[(size_t)j * N + col] += dtau * pr[col >> 1] * g;
+        } else {
+            G[(size_t)j * N + col] = g;
+        }
+    };
+    if (nsplit > 1) {
+        for (int e = threadIdx.x; e < (r1 - r0) * BN; e += DT_THREADS)
+            emit(j0 + r0 + e / BN, c0 + e % BN, ((T *)Ks)[e]);
+    } else {
+#pragma unroll
+        for (int i = 0; i < TM; ++i)
+#pragma unroll
+            for (int l = 0; l < TN; ++l) emit(j0 + ty * TM + i, c0 + tx * TN + l, acc[i][l]);
+    }
+    if (mode == GM_STORE) return;
+
+    // ---- FP64 |G|^2: per-CTA partial, last CTA of the grid sums them in a fixed order
+    partsum = block_sum<DT_THREADS>(partsum, red);
+    const int bid = (ks * gridDim.y + tile_r) * gridDim.x + tile_c, nb = ntiles * nsplit;
+    if (threadIdx.x == 0) c.tile[bid] = partsum;
     __threadfence();
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -708,8 +859,8 @@ __global__ void __launch_bounds__(GEMM_THREADS) k_dt(CurveDev c, int mode, int d
     if (!am_last) return;
     __threadfence();
     double t = 0.0;
-    for (int b = threadIdx.x; b < nb; b += GEMM_THREADS) t += __ldcg(c.tile + b);
-    t = block_sum<GEMM_THREADS>(t, red);
+    for (int b = threadIdx.x; b < nb; b += DT_THREADS) t += __ldcg(c.tile + b);
+    t = block_sum<DT_THREADS>(t, red);
     if (threadIdx.x == 0) {
         sc->G2 = c.L * t;
         if (mode == GM_UPDATE) {
@@ -805,7 +956,8 @@ cudaError_t launch_setup(const CurveDev &c, double dtau, cudaStream_t st)
 cudaError_t launch_scalars_init(const CurveDev &c, double lambda, int lambda_free, double dtau,
                                 double dtau_lambda, int conv, cudaStream_t st)
 {
-    k_scalars_init<<<1, 32, 0, st>>>(c.sc, lambda, lambda_free, dtau, dtau_lambda, conv);
+    k_scalars_init<<<1, 256, 0, st>>>(c.sc, c.tcnt, c.tiles_r * c.tiles_c, lambda, lambda_free, dtau, dtau_lambda,
+                                      conv);
     return cudaGetLastError();
 }
 
@@ -864,12 +1016,32 @@ cudaError_t launch_rows(const CurveDev &c, int mode, cudaStream_t st)
     return c.prec ? rows_t<float>(c, mode, st) : rows_t<double>(c, mode, st);
 }
 
+template <typename T, int BN>
+static cudaError_t launch_dt_t(const CurveDev &c, int mode, int discrete, int gate, cudaStream_t st)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(c.tiles_c, c.tiles_r, c.ksplit);
+    cfg.blockDim = dim3(DT_THREADS, 1, 1);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 1;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = c.ksplit;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaError_t e = cudaLaunchKernelEx(&cfg, k_dt<T, BN>, c, mode, discrete, gate);
+    if (e != cudaSuccess) return e;
+    return cudaGetLastError();
+}
+
 cudaError_t launch_dt(const CurveDev &c, int mode, int discrete, int gate, cudaStream_t st)
 {
-    dim3 grid((c.nx + GEMM_BN - 1) / GEMM_BN, (c.ns + GEMM_BM - 1) / GEMM_BM);
-    if (c.prec) k_dt<float><<<grid, GEMM_THREADS, 0, st>>>(c, mode, discrete, gate);
-    else k_dt<double><<<grid, GEMM_THREADS, 0, st>>>(c, mode, discrete, gate);
-    return cudaGetLastError();
+    if (c.bn == 64) return c.prec ? launch_dt_t<float, 64>(c, mode, discrete, gate, st)
+                                  : launch_dt_t<double, 64>(c, mode, discrete, gate, st);
+    return c.prec ? launch_dt_t<float, 32>(c, mode, discrete, gate, st)
+                  : launch_dt_t<double, 32>(c, mode, discrete, gate, st);
 }
 
 }  // namespace ks

@@ -75,37 +75,7 @@ extern "C" ks_status ks_cost_noalloc(const ks_params *p, const void *u_dev, doub
         base = g_addr[dev];
     }
 
-    ks::CurveDev d{};
-    char *b = (char *)base;
-    d.ns = p->ns;
-    d.nx = p->nx;
-    d.P = p->ns - 1;
-    d.prec = p->precision == KS_FP32 ? 1 : 0;
-    d.L = p->L;
-    d.S = p->S;
-    d.s0 = p->s0;
-    d.U = b + lay.off_U;
-    d.D = b + lay.off_D;
-    d.R = b + lay.off_R;
-    d.A = b + lay.off_A;
-    d.G = b + lay.off_G;
-    d.X = b + lay.off_X;
-    d.rowsc = (double *)(b + lay.off_rowsc);
-    d.tile = (double *)(b + lay.off_tile);
-    d.cot = b + lay.off_cot;
-    d.sig = b + lay.off_sig;
-    d.tau = b + lay.off_tau;
-    d.sw = b + lay.off_sw;
-    d.twr = b + lay.off_twr;
-    d.w = (double *)(b + lay.off_w);
-    d.twid = b + lay.off_twid;
-    d.twid64 = b + lay.off_twid64;
-    d.kj = b + lay.off_kj;
-    d.aj = b + lay.off_aj;
-    d.prec_imex = b + lay.off_prec;
-    d.ends = (double *)(b + lay.off_ends);
-    d.pert = (double *)(b + lay.off_pert);
-    d.sc = (ks::DevScalars *)(b + lay.off_sc);
+    const ks::CurveDev d = ks::bind_layout(p, lay, base);
 
     cudaStream_t st = (cudaStream_t)stream;
     // tables, then the scalars and arrival counters (cleared: they must start at zero)
