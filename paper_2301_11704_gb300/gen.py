@@ -194,3 +194,10 @@ def perturbation(spec: CurveSpec):
     """(amps, fields[npert, N]) of the trial-curve perturbation of a workload curve."""
     v = perturbation_fields(spec.N, spec.L, spec.seed(), spec.npert)
     return np.full(spec.npert, spec.amp), v
+
+
+def stored_equilibria_paper() -> dict:
+    """E1, E2, E3 at L = 22, N = 64 (stored Newton solutions), keyed by name."""
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "data", "equilibria.json")
+    with open(path) as f:
+        return json.load(f)["paper"]
