@@ -212,6 +212,50 @@ typedef struct {
 ks_status ks_curve_profile(ks_curve *c, int32_t max_steps);
 ks_status ks_curve_profile_read(ks_curve *c, ks_profile *out);
 
+/* ------------------------------------------------------------------------
+ * Batches: many independent curves (uneven N_s, N and L, one precision and
+ * one adjoint mode) descending together.  Each phase of a step is one launch
+ * over the (curve, block) work items of all curves, and the steps are
+ * replayed from a captured CUDA graph; every curve keeps its own gates,
+ * reductions and convergence test (the method of Sec. III applied per curve).
+ * Arrays indexed by curve have nb entries; u_plus_host / u_minus_host / vp_host
+ * concatenate the curves' sections in curve order.
+ * ------------------------------------------------------------------------ */
+typedef struct ks_batch ks_batch;
+
+/* Device workspace of a batch (0 for invalid parameters). */
+size_t ks_batch_workspace_bytes(int32_t nb, const ks_params *params);
+
+/* Creates a batch with the trial curves of eq. KSE_initial_curve (a = 0).
+ * Same conventions as ks_curve_create; synchronises the stream. */
+ks_status ks_batch_create(int32_t nb, const ks_params *params, const double *u_plus_host,
+                          const double *u_minus_host, void *workspace_dev, size_t workspace_bytes,
+                          void *stream, ks_batch **out);
+
+/* Trial curves with npert perturbation modes per curve (see ks_curve_init_trial):
+ * amps_host [nb][npert], vp_host the curves' [npert][N_i] fields concatenated. */
+ks_status ks_batch_init_trial(ks_batch *b, int32_t npert, const double *amps_host, const double *vp_host);
+
+/* Up to nsteps steps of every curve; a curve stops once its own convergence
+ * measure is below tol.  steps_done, J, J_arc (host, nb entries each, may be
+ * NULL).  KS_ENOTCONV if some curve missed tol > 0.  Synchronises. */
+ks_status ks_batch_descend(ks_batch *b, int64_t nsteps, double tol, int64_t *steps_done, double *J,
+                           double *J_arc);
+ks_status ks_batch_descend_async(ks_batch *b, int64_t nsteps, double tol);
+
+/* Scalars of every curve (out: nb entries).  Synchronises. */
+ks_status ks_batch_scalars(ks_batch *b, ks_scalars *out);
+
+/* Physical state of curve i, [N_s,i][N_i] in the storage type.  Asynchronous. */
+ks_status ks_batch_get_state(ks_batch *b, int32_t i, void *u_dev);
+
+/* Times `steps` descent steps of the batch for each candidate s-phase tile width
+ * (64 or 32 columns per CTA for curves with N >= 64) and keeps the faster one
+ * (*chosen, may be NULL).  The timed steps are real descent steps.  Synchronises. */
+ks_status ks_batch_autotune(ks_batch *b, int32_t steps, int32_t *chosen);
+
+ks_status ks_batch_destroy(ks_batch *b);
+
 /* Allocation-free cost evaluation.  The paper has no counterpart: this entry
  * point exists for callers that cannot allocate device memory, such as a host
  * program that owns every device allocation and hands this library only its

@@ -23,6 +23,8 @@ EXPORTS = [
     "ks_curve_init_trial", "ks_curve_residual", "ks_curve_cost", "ks_curve_gradient", "ks_curve_descend",
     "ks_curve_descend_async", "ks_curve_scalars", "ks_curve_get_state", "ks_curve_set_state", "ks_curve_profile",
     "ks_curve_profile_read", "ks_curve_destroy", "ks_cost_noalloc",
+    "ks_batch_workspace_bytes", "ks_batch_create", "ks_batch_init_trial", "ks_batch_descend",
+    "ks_batch_descend_async", "ks_batch_scalars", "ks_batch_get_state", "ks_batch_autotune", "ks_batch_destroy",
 ]
 
 
@@ -111,6 +113,15 @@ def load(build_if_missing: bool = True):
         "ks_curve_profile_read": (i32, [p, ctypes.POINTER(KSProfile)]),
         "ks_curve_destroy": (i32, [p]),
         "ks_cost_noalloc": (i32, [ctypes.POINTER(KSParams), p, p, p]),
+        "ks_batch_workspace_bytes": (sz, [i32, ctypes.POINTER(KSParams)]),
+        "ks_batch_create": (i32, [i32, ctypes.POINTER(KSParams), pd, pd, p, sz, p, ctypes.POINTER(p)]),
+        "ks_batch_init_trial": (i32, [p, i32, pd, pd]),
+        "ks_batch_descend": (i32, [p, i64, d, pi64, pd, pd]),
+        "ks_batch_descend_async": (i32, [p, i64, d]),
+        "ks_batch_scalars": (i32, [p, ctypes.POINTER(KSScalars)]),
+        "ks_batch_get_state": (i32, [p, i32, p]),
+        "ks_batch_autotune": (i32, [p, i32, ctypes.POINTER(i32)]),
+        "ks_batch_destroy": (i32, [p]),
     }
     for name, (res, args) in sigs.items():
         fn = getattr(lib, name)

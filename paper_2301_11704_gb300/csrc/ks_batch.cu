@@ -1,0 +1,419 @@
+// ks_batch.cu -- many independent curves (uneven N_s, N and L) descending
+// together: every phase of a step is one launch over the work items (curve,
+// block) of all curves, captured once into a CUDA graph and replayed.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <new>
+#include <vector>
+
+#include "../../include/ksconn.h"
+#include "ks_internal.h"
+
+namespace {
+
+const int BATCH_GRAPH_STEPS = 16;
+
+struct Group {
+    int key;              // N (rows) or tile width (s-phase)
+    size_t off;           // offset of the item list in the item area
+    int count;
+};
+
+}  // namespace
+
+struct ks_batch {
+    int nb = 0;
+    int prec = 0;
+    int discrete = 0;
+    cudaStream_t st = nullptr;
+    int device = 0;
+    std::vector<ks_params> p;
+    std::vector<size_t> off;            // per-curve workspace offsets
+    std::vector<ks::CurveDev> cv;       // host copy of the device curve array
+    ks::CurveDev *cv_dev = nullptr;
+    unsigned char *items_dev = nullptr; // item area
+    size_t items_cap = 0;
+    std::vector<Group> rows, dts;
+    int tile_pref = 0;                  // 0: per-curve default, 32 or 64: forced (autotuner)
+    cudaGraphExec_t gexec = nullptr;
+    cudaStream_t gstream = nullptr;
+};
+
+namespace {
+
+size_t al256(size_t x) { return (x + 255) & ~size_t(255); }
+
+// Bytes of the batch header: curve array and the largest item lists.
+void header_sizes(int nb, const ks_params *p, size_t *cv_bytes, size_t *items_bytes)
+{
+    size_t rows = 0, tiles = 0;
+    for (int i = 0; i < nb; ++i) {
+        rows += (p[i].ns + ks::ROWS_PER_CTA - 1) / ks::ROWS_PER_CTA;
+        tiles += (size_t)((p[i].ns + ks::DT_BM - 1) / ks::DT_BM) * ((p[i].nx + 31) / 32);
+    }
+    *cv_bytes = al256((size_t)nb * sizeof(ks::CurveDev));
+    *items_bytes = al256(rows * sizeof(int2)) + al256(tiles * sizeof(int4));
+}
+
+ks_status validate_batch(int nb, const ks_params *p)
+{
+    if (nb <= 0 || nb > 65536) return ks::report_error(KS_EINVAL, "batch size must be in [1, 65536]");
+    if (!p) return ks::report_error(KS_EINVAL, "params is NULL");
+    for (int i = 0; i < nb; ++i) {
+        ks_status s = ks::check_params(&p[i]);
+        if (s != KS_OK) return s;
+        if (p[i].precision != p[0].precision)
+            return ks::report_error(KS_EINVAL, "all curves of a batch must have the same precision");
+        if (p[i].adjoint != p[0].adjoint)
+            return ks::report_error(KS_EINVAL, "all curves of a batch must have the same adjoint mode");
+    }
+    return KS_OK;
+}
+
+// (Re)builds the curve array and the work-item lists for the current tile choice.
+ks_status build_items(ks_batch *b)
+{
+    std::map<int, std::vector<int2>> rows;
+    std::map<int, std::vector<int4>> dts;
+    for (int i = 0; i < b->nb; ++i) {
+        ks::CurveDev &c = b->cv[i];
+        const int bn = b->tile_pref ? (c.nx < 64 ? 32 : b->tile_pref) : (c.nx >= 64 ? 64 : 32);
+        c.bn = bn;
+        c.tiles_c = (c.nx + bn - 1) / bn;
+        for (int k = 0; k < c.row_blocks; ++k) rows[c.nx].push_back(make_int2(i, k));
+        for (int tr = 0; tr < c.tiles_r; ++tr)
+            for (int tc = 0; tc < c.tiles_c; ++tc) dts[bn].push_back(make_int4(i, tc, tr, 0));
+    }
+    size_t cvb, itb;
+    header_sizes(b->nb, b->p.data(), &cvb, &itb);
+    std::vector<unsigned char> host(itb, 0);
+    size_t o = 0;
+    b->rows.clear();
+    b->dts.clear();
+    for (auto &kv : rows) {
+        b->rows.push_back({kv.first, o, (int)kv.second.size()});
+        memcpy(host.data() + o, kv.second.data(), kv.second.size() * sizeof(int2));
+        o += kv.second.size() * sizeof(int2);
+    }
+    o = al256(o);
+    for (auto &kv : dts) {
+        b->dts.push_back({kv.first, o, (int)kv.second.size()});
+        memcpy(host.data() + o, kv.second.data(), kv.second.size() * sizeof(int4));
+        o += kv.second.size() * sizeof(int4);
+    }
+    if (o > itb) return ks::report_error(KS_ENOMEM, "batch item lists exceed their reserved space");
+    cudaError_t e = cudaMemcpyAsync(b->items_dev, host.data(), o, cudaMemcpyHostToDevice, b->st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b->cv_dev, b->cv.data(), b->nb * sizeof(ks::CurveDev), cudaMemcpyHostToDevice, b->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->st);   // host vectors die at return
+    if (e != cudaSuccess) return ks::report_error(KS_ECUDA, "batch item upload: %s", cudaGetErrorString(e));
+    if (b->gexec) {
+        cudaGraphExecDestroy(b->gexec);
+        b->gexec = nullptr;
+    }
+    return KS_OK;
+}
+
+ks_status launch_step(ks_batch *b, cudaStream_t st)
+{
+    cudaError_t e = cudaSuccess;
+    for (const Group &g : b->rows)
+        if (e == cudaSuccess)
+            e = ks::launch_rows_batch(b->prec, g.key, b->cv_dev, (const int2 *)(b->items_dev + g.off), g.count,
+                                      ks::ROWS_STEP, st);
+    for (const Group &g : b->dts)
+        if (e == cudaSuccess)
+            e = ks::launch_dt_batch(b->prec, g.key, b->cv_dev, (const int4 *)(b->items_dev + g.off), g.count,
+                                    ks::GM_UPDATE, b->discrete, 1, st);
+    for (const Group &g : b->dts)
+        if (e == cudaSuccess)
+            e = ks::launch_dt_batch(b->prec, g.key, b->cv_dev, (const int4 *)(b->items_dev + g.off), g.count,
+                                    ks::GM_STORE, 0, 1, st);
+    if (e != cudaSuccess) return ks::report_error(KS_ECUDA, "batched step launch: %s", cudaGetErrorString(e));
+    return KS_OK;
+}
+
+ks_status ensure_graph(ks_batch *b)
+{
+    if (b->gexec) return KS_OK;
+    cudaError_t e = cudaSuccess;
+    if (!b->gstream) e = cudaStreamCreateWithFlags(&b->gstream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamBeginCapture(b->gstream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return ks::report_error(KS_ECUDA, "graph capture: %s", cudaGetErrorString(e));
+    ks_status s = KS_OK;
+    for (int i = 0; i < BATCH_GRAPH_STEPS && s == KS_OK; ++i) s = launch_step(b, b->gstream);
+    cudaGraph_t graph = nullptr;
+    e = cudaStreamEndCapture(b->gstream, &graph);
+    if (s != KS_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return s;
+    }
+    if (e != cudaSuccess) return ks::report_error(KS_ECUDA, "graph capture: %s", cudaGetErrorString(e));
+    e = cudaGraphInstantiate(&b->gexec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+        b->gexec = nullptr;
+        return ks::report_error(KS_ECUDA, "graph instantiation: %s", cudaGetErrorString(e));
+    }
+    return KS_OK;
+}
+
+ks_status enqueue(ks_batch *b, int64_t nsteps, double tol)
+{
+    cudaError_t e = ks::launch_set_limit_batch(b->cv_dev, b->nb, (long long)nsteps, tol, b->st);
+    if (e != cudaSuccess) return ks::report_error(KS_ECUDA, "set limit: %s", cudaGetErrorString(e));
+    int64_t full = nsteps / BATCH_GRAPH_STEPS, rest = nsteps % BATCH_GRAPH_STEPS;
+    if (full > 0) {
+        ks_status s = ensure_graph(b);
+        if (s != KS_OK) return s;
+        for (int64_t g = 0; g < full; ++g) {
+            e = cudaGraphLaunch(b->gexec, b->st);
+            if (e != cudaSuccess) return ks::report_error(KS_ECUDA, "graph launch: %s", cudaGetErrorString(e));
+        }
+    }
+    for (int64_t r = 0; r < rest; ++r) {
+        ks_status s = launch_step(b, b->st);
+        if (s != KS_OK) return s;
+    }
+    return KS_OK;
+}
+
+ks_status read_all(ks_batch *b, std::vector<ks::DevScalars> &h)
+{
+    h.resize(b->nb);
+    for (int i = 0; i < b->nb; ++i) {
+        cudaError_t e = cudaMemcpyAsync(&h[i], b->cv[i].sc, sizeof(ks::DevScalars), cudaMemcpyDeviceToHost, b->st);
+        if (e != cudaSuccess) return ks::report_error(KS_ECUDA, "scalar read: %s", cudaGetErrorString(e));
+    }
+    cudaError_t e = cudaStreamSynchronize(b->st);
+    if (e != cudaSuccess) return ks::report_error(KS_ECUDA, "scalar read: %s", cudaGetErrorString(e));
+    return KS_OK;
+}
+
+ks_status eval_all(ks_batch *b)
+{
+    cudaError_t e = cudaSuccess;
+    for (const Group &g : b->rows)
+        if (e == cudaSuccess)
+            e = ks::launch_rows_batch(b->prec, g.key, b->cv_dev, (const int2 *)(b->items_dev + g.off), g.count,
+                                      ks::ROWS_EVAL, b->st);
+    if (e != cudaSuccess) return ks::report_error(KS_ECUDA, "batched evaluation: %s", cudaGetErrorString(e));
+    return KS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t ks_batch_workspace_bytes(int32_t nb, const ks_params *params)
+{
+    if (validate_batch(nb, params) != KS_OK) return 0;
+    size_t cvb, itb;
+    header_sizes(nb, params, &cvb, &itb);
+    size_t total = cvb + itb;
+    for (int i = 0; i < nb; ++i)
+        total += ks::make_layout(params[i].ns, params[i].nx, params[i].precision == KS_FP32, 0).total;
+    return total;
+}
+
+ks_status ks_batch_create(int32_t nb, const ks_params *params, const double *u_plus_host, const double *u_minus_host,
+                          void *workspace_dev, size_t workspace_bytes, void *stream, ks_batch **out)
+{
+    ks_status s = validate_batch(nb, params);
+    if (s != KS_OK) return s;
+    if (!out || !u_plus_host || !u_minus_host || !workspace_dev)
+        return ks::report_error(KS_EINVAL, "out, u_plus_host, u_minus_host and workspace_dev are required");
+    *out = nullptr;
+    if (((uintptr_t)workspace_dev) & 255) return ks::report_error(KS_EINVAL, "workspace_dev must be 256-byte aligned");
+    const size_t need = ks_batch_workspace_bytes(nb, params);
+    if (workspace_bytes < need)
+        return ks::report_error(KS_ENOMEM, "batch workspace has %zu bytes, %zu needed", workspace_bytes, need);
+    ks_batch *b = new (std::nothrow) ks_batch();
+    if (!b) return ks::report_error(KS_ENOMEM, "host allocation of the batch handle failed");
+    b->nb = nb;
+    b->prec = params[0].precision == KS_FP32 ? 1 : 0;
+    b->discrete = params[0].adjoint == KS_ADJ_DISCRETE;
+    b->st = (cudaStream_t)stream;
+    cudaGetDevice(&b->device);
+    b->p.assign(params, params + nb);
+    size_t cvb, itb;
+    header_sizes(nb, params, &cvb, &itb);
+    unsigned char *base = (unsigned char *)workspace_dev;
+    b->cv_dev = (ks::CurveDev *)base;
+    b->items_dev = base + cvb;
+    b->items_cap = itb;
+    size_t o = cvb + itb;
+    b->cv.resize(nb);
+    size_t xoff = 0;
+    for (int i = 0; i < nb; ++i) {
+        const ks::Layout l = ks::make_layout(params[i].ns, params[i].nx, b->prec, 0);
+        b->off.push_back(o);
+        b->cv[i] = ks::bind_layout(&params[i], l, base + o);
+        o += l.total;
+    }
+    s = KS_OK;
+    for (int i = 0; i < nb && s == KS_OK; ++i) {
+        const ks::CurveDev &c = b->cv[i];
+        const size_t nbytes = (size_t)c.nx * sizeof(double);
+        cudaError_t e = cudaMemcpyAsync(c.ends, u_plus_host + xoff, nbytes, cudaMemcpyHostToDevice, b->st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(c.ends + c.nx, u_minus_host + xoff, nbytes, cudaMemcpyHostToDevice, b->st);
+        if (e == cudaSuccess)
+            e = cudaMemsetAsync(c.pert, 0, (size_t)(c.nx + ks::MAX_PERT + ks::MAX_PERT * c.nx) * 8, b->st);
+        if (e == cudaSuccess) e = ks::launch_setup(c, params[i].dtau, b->st);
+        if (e == cudaSuccess)
+            e = ks::launch_scalars_init(c, params[i].lambda, params[i].lambda_free, params[i].dtau,
+                                        params[i].dtau_lambda, params[i].conv, b->st);
+        if (e == cudaSuccess) e = ks::launch_trial(c, 0.0, 0, 0, b->st);
+        if (e == cudaSuccess) e = ks::launch_row_fwd_x(c, c.U, 0, b->st);
+        if (e == cudaSuccess) e = ks::launch_dt(c, ks::GM_STORE, 0, 0, b->st);
+        if (e != cudaSuccess) s = ks::report_error(KS_ECUDA, "batch set-up of curve %d: %s", i, cudaGetErrorString(e));
+        xoff += c.nx;
+    }
+    if (s == KS_OK) s = build_items(b);
+    if (s != KS_OK) {
+        delete b;
+        return s;
+    }
+    *out = b;
+    return KS_OK;
+}
+
+ks_status ks_batch_init_trial(ks_batch *b, int32_t npert, const double *amps_host, const double *vp_host)
+{
+    if (!b) return ks::report_error(KS_EINVAL, "batch handle is NULL");
+    if (npert < 0 || npert > ks::MAX_PERT) return ks::report_error(KS_EINVAL, "npert must be in [0, %d]", ks::MAX_PERT);
+    if (npert > 0 && (!amps_host || !vp_host)) return ks::report_error(KS_EINVAL, "amps_host and vp_host are required");
+    size_t voff = 0;
+    for (int i = 0; i < b->nb; ++i) {
+        const ks::CurveDev &c = b->cv[i];
+        const ks_params &p = b->p[i];
+        cudaError_t e = cudaSuccess;
+        if (npert > 0) {
+            e = cudaMemcpyAsync(c.pert + c.nx, amps_host + (size_t)i * npert, npert * 8, cudaMemcpyHostToDevice, b->st);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(c.pert + c.nx + ks::MAX_PERT, vp_host + voff, (size_t)npert * c.nx * 8,
+                                    cudaMemcpyHostToDevice, b->st);
+        }
+        if (e == cudaSuccess) e = ks::launch_trial(c, 0.0, 0, npert, b->st);
+        if (e == cudaSuccess) e = ks::launch_row_fwd_x(c, c.U, 0, b->st);
+        if (e == cudaSuccess) e = ks::launch_dt(c, ks::GM_STORE, 0, 0, b->st);
+        if (e == cudaSuccess)
+            e = ks::launch_scalars_init(c, p.lambda, p.lambda_free, p.dtau, p.dtau_lambda, p.conv, b->st);
+        if (e != cudaSuccess) return ks::report_error(KS_ECUDA, "trial curve %d: %s", i, cudaGetErrorString(e));
+        voff += (size_t)npert * c.nx;
+    }
+    cudaError_t e = cudaStreamSynchronize(b->st);
+    if (e != cudaSuccess) return ks::report_error(KS_ECUDA, "trial curves: %s", cudaGetErrorString(e));
+    return KS_OK;
+}
+
+ks_status ks_batch_descend_async(ks_batch *b, int64_t nsteps, double tol)
+{
+    if (!b) return ks::report_error(KS_EINVAL, "batch handle is NULL");
+    if (nsteps < 0 || !std::isfinite(tol)) return ks::report_error(KS_EINVAL, "nsteps must be >= 0 and tol finite");
+    return enqueue(b, nsteps, tol);
+}
+
+ks_status ks_batch_descend(ks_batch *b, int64_t nsteps, double tol, int64_t *steps_done, double *J, double *J_arc)
+{
+    if (!b) return ks::report_error(KS_EINVAL, "batch handle is NULL");
+    if (nsteps < 0 || !std::isfinite(tol)) return ks::report_error(KS_EINVAL, "nsteps must be >= 0 and tol finite");
+    std::vector<ks::DevScalars> h0, h;
+    ks_status s = read_all(b, h0);
+    if (s == KS_OK) s = enqueue(b, nsteps, tol);
+    if (s == KS_OK) s = eval_all(b);
+    if (s == KS_OK) s = read_all(b, h);
+    if (s != KS_OK) return s;
+    bool nonfinite = false, all_done = true;
+    for (int i = 0; i < b->nb; ++i) {
+        if (steps_done) steps_done[i] = h[i].step - h0[i].step;
+        if (J) J[i] = std::sqrt(h[i].J2);
+        if (J_arc) J_arc[i] = h[i].Jarc;
+        if (h[i].status == KS_ENONFINITE || !std::isfinite(h[i].J2)) nonfinite = true;
+        if (!h[i].done) all_done = false;
+    }
+    if (nonfinite) return ks::report_error(KS_ENONFINITE, "a curve's cost became non-finite");
+    if (tol > 0 && !all_done) return ks::report_error(KS_ENOTCONV, "not every curve reached tolerance %.3e", tol);
+    return KS_OK;
+}
+
+ks_status ks_batch_scalars(ks_batch *b, ks_scalars *out)
+{
+    if (!b || !out) return ks::report_error(KS_EINVAL, "batch handle and out are required");
+    std::vector<ks::DevScalars> h;
+    ks_status s = read_all(b, h);
+    if (s != KS_OK) return s;
+    for (int i = 0; i < b->nb; ++i) {
+        out[i].J = std::sqrt(h[i].J2);
+        out[i].J_arc = h[i].Jarc;
+        out[i].dJ2_dlambda = h[i].dJdl;
+        out[i].G_norm = std::sqrt(h[i].G2);
+        out[i].Dnorm = h[i].Dnorm;
+        out[i].lambda = h[i].lambda;
+        out[i].tau = h[i].tau;
+        out[i].step = h[i].step;
+        out[i].converged = h[i].done && h[i].status == 0;
+        out[i].status = h[i].status;
+    }
+    return KS_OK;
+}
+
+ks_status ks_batch_get_state(ks_batch *b, int32_t i, void *u_dev)
+{
+    if (!b || !u_dev || i < 0 || i >= b->nb) return ks::report_error(KS_EINVAL, "bad batch handle, index or pointer");
+    cudaError_t e = ks::launch_row_inv(b->cv[i], b->cv[i].U, u_dev, 0, b->st);
+    if (e != cudaSuccess) return ks::report_error(KS_ECUDA, "get_state: %s", cudaGetErrorString(e));
+    return KS_OK;
+}
+
+ks_status ks_batch_autotune(ks_batch *b, int32_t steps, int32_t *chosen)
+{
+    if (!b || steps <= 0) return ks::report_error(KS_EINVAL, "batch handle required and steps > 0");
+    // candidates: the s-phase tile width of curves with N >= 64 (64 or 32 columns per CTA)
+    const int cand[2] = {64, 32};
+    float best = 1e30f;
+    int best_c = 64;
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+        return ks::report_error(KS_ECUDA, "autotune events");
+    // the timed trial steps are real descent steps of every curve (they count in
+    // each curve's step counter and tau)
+    ks_status s = KS_OK;
+    for (int k = 0; k < 2 && s == KS_OK; ++k) {
+        b->tile_pref = cand[k];
+        s = build_items(b);
+        if (s != KS_OK) break;
+        s = enqueue(b, 2, 0.0);                                      // warm-up
+        if (s != KS_OK) break;
+        cudaEventRecord(e0, b->st);
+        s = enqueue(b, steps, 0.0);
+        cudaEventRecord(e1, b->st);
+        cudaEventSynchronize(e1);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best) {
+            best = ms;
+            best_c = cand[k];
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (s != KS_OK) return s;
+    b->tile_pref = best_c;
+    s = build_items(b);
+    if (chosen) *chosen = best_c;
+    return s;
+}
+
+ks_status ks_batch_destroy(ks_batch *b)
+{
+    if (!b) return KS_OK;
+    if (b->gexec) cudaGraphExecDestroy(b->gexec);
+    if (b->gstream) cudaStreamDestroy(b->gstream);
+    delete b;
+    return KS_OK;
+}
+
+}  // extern "C"

@@ -78,7 +78,9 @@ struct CurveDev {
     DevScalars *sc;
 };
 
-Layout make_layout(int ns, int nx, int prec);
+// allow_split = 0 lays a curve out without split contractions (batched curves
+// get their parallelism from the batch); bn = 0 picks the column tile width.
+Layout make_layout(int ns, int nx, int prec, int allow_split = 1, int bn = 0);
 // Pointers of a curve whose workspace starts at `base` (256-byte aligned).
 CurveDev bind_layout(const ks_params *p, const Layout &l, void *base);
 
@@ -111,5 +113,12 @@ cudaError_t launch_rows(const CurveDev &c, int mode, cudaStream_t st);
 // sigma), op 1: W^-1 D_t^T W.  mode GM_STORE writes D_t U into D (gated when
 // `gate`), GM_UPDATE applies the descent update to U, GM_GRAD writes G.
 cudaError_t launch_dt(const CurveDev &c, int mode, int discrete, int gate, cudaStream_t st);
+
+// ---- batched launches over (curve, block) work items; cv is a device array of curves
+cudaError_t launch_rows_batch(int prec, int N, const CurveDev *cv, const int2 *items, int nitems, int mode,
+                              cudaStream_t st);
+cudaError_t launch_dt_batch(int prec, int bn, const CurveDev *cv, const int4 *items, int nitems, int mode,
+                            int discrete, int gate, cudaStream_t st);
+cudaError_t launch_set_limit_batch(const CurveDev *cv, int nb, long long nsteps, double tol, cudaStream_t st);
 
 }  // namespace ks

@@ -46,17 +46,18 @@ __device__ __forceinline__ cpx<T> cmul(cpx<T> a, cpx<T> b)
 // ---------------------------------------------------------------------------
 static size_t al256(size_t x) { return (x + 255) & ~size_t(255); }
 
-Layout make_layout(int ns, int nx, int prec)
+Layout make_layout(int ns, int nx, int prec, int allow_split, int bn)
 {
     Layout l{};
     size_t b = prec ? 4 : 8;
     size_t field = al256((size_t)ns * nx * b);
     // tiling and split of the s-contraction
-    l.bn = nx >= 64 ? 64 : 32;
+    l.bn = bn ? bn : (nx >= 64 ? 64 : 32);
     l.tiles_r = (ns + DT_BM - 1) / DT_BM;
     l.tiles_c = (nx + l.bn - 1) / l.bn;
     int tiles = l.tiles_r * l.tiles_c;
-    int ks = tiles < DT_TARGET_CTAS ? DT_TARGET_CTAS / tiles : 1;
+    int tiles_max = l.tiles_r * ((nx + 31) / 32);       // buffers sized for the narrowest tiles
+    int ks = (allow_split && tiles < DT_TARGET_CTAS) ? DT_TARGET_CTAS / tiles : 1;
     int kmax = ns / DT_MIN_KCHUNK;
     if (ks > kmax) ks = kmax;
     if (ks > DT_MAX_SPLIT) ks = DT_MAX_SPLIT;
@@ -75,8 +76,8 @@ Layout make_layout(int ns, int nx, int prec)
     l.off_X = off; off += al256((size_t)ns * nx * 8);   // physical scratch, always FP64
     l.off_rowsc = off; off += al256((size_t)ns * 4 * 8);
     l.off_bpart = off; off += al256((size_t)l.row_blocks * 5 * 8);
-    l.off_tile = off; off += al256((size_t)tiles * l.ksplit * 8);
-    l.off_tcnt = off; off += al256((size_t)tiles * 4);
+    l.off_tile = off; off += al256((size_t)tiles_max * l.ksplit * 8);
+    l.off_tcnt = off; off += al256((size_t)tiles_max * 4);
     l.off_part = off;
     int P = ns - 1;
     l.off_cot = off; off += al256((size_t)2 * P * b);
@@ -463,7 +464,7 @@ __global__ void __launch_bounds__(ROWS_WARPS * 32) k_row_inv(CurveDev c, const T
 // fixed order: J^2, J_arc, dJ^2/dl, |l d|_W, the end-section residuals, and
 // (step mode) the convergence decision and the next lambda.
 template <typename T, int N>
-__global__ void __launch_bounds__(ROWS_WARPS * 32) k_rows(CurveDev c, int mode)
+__device__ __forceinline__ void rows_body(const CurveDev &c, int mode, int blk, int nblk)
 {
     constexpr int H = N / 2;
     constexpr int MPL = (H + 31) / 32;
@@ -477,7 +478,7 @@ __global__ void __launch_bounds__(ROWS_WARPS * 32) k_rows(CurveDev c, int mode)
     DevScalars *sc = c.sc;
 
     if (mode == ROWS_STEP && (sc->done || sc->step >= sc->limit)) {
-        if (blockIdx.x == 0 && threadIdx.x == 0) sc->active = 0;
+        if (blk == 0 && threadIdx.x == 0) sc->active = 0;
         return;
     }
     for (int t = threadIdx.x; t < H; t += blockDim.x) tw[t] = ((const cpx<T> *)c.twid)[t];
@@ -489,7 +490,7 @@ __global__ void __launch_bounds__(ROWS_WARPS * 32) k_rows(CurveDev c, int mode)
     T *R = (T *)c.R, *A = (T *)c.A;
     const T *kj = (const T *)c.kj, *aj = (const T *)c.aj;
 
-    const int m0 = (blockIdx.x * ROWS_WARPS + warp) * 2, m1 = m0 + 1;
+    const int m0 = (blk * ROWS_WARPS + warp) * 2, m1 = m0 + 1;
     if (m0 < ns) {
         const bool has1 = m1 < ns;
         const bool in0 = (m0 > 0 && m0 < P), in1 = has1 && (m1 > 0 && m1 < P);
@@ -624,7 +625,7 @@ __global__ void __launch_bounds__(ROWS_WARPS * 32) k_rows(CurveDev c, int mode)
         double t = 0.0;
 #pragma unroll
         for (int w = 0; w < ROWS_WARPS; ++w) t += wpart[w][threadIdx.x];
-        c.bpart[(size_t)blockIdx.x * 5 + threadIdx.x] = t;
+        c.bpart[(size_t)blk * 5 + threadIdx.x] = t;
     }
 
     // ---- last CTA: FP64 reduction over the CTAs' partial sums in a fixed order
@@ -632,13 +633,13 @@ __global__ void __launch_bounds__(ROWS_WARPS * 32) k_rows(CurveDev c, int mode)
     __syncthreads();
     if (threadIdx.x == 0) {
         unsigned prev = atomicAdd(&sc->cnt_rows, 1u);
-        am_last = (prev == gridDim.x - 1);
+        am_last = (prev == (unsigned)nblk - 1);
     }
     __syncthreads();
     if (!am_last) return;
     __threadfence();
     double t[5] = {0, 0, 0, 0, 0};
-    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x)
+    for (int b = threadIdx.x; b < nblk; b += blockDim.x)
 #pragma unroll
         for (int q = 0; q < 5; ++q) t[q] += __ldcg(c.bpart + (size_t)b * 5 + q);
 #pragma unroll
@@ -680,6 +681,22 @@ __global__ void __launch_bounds__(ROWS_WARPS * 32) k_rows(CurveDev c, int mode)
     }
 }
 
+template <typename T, int N>
+__global__ void __launch_bounds__(ROWS_WARPS * 32) k_rows(CurveDev c, int mode)
+{
+    rows_body<T, N>(c, mode, blockIdx.x, gridDim.x);
+}
+
+// Batched row phase: work item (curve, row block) per CTA; every curve keeps its
+// own gates, counters and reductions.
+template <typename T, int N>
+__global__ void __launch_bounds__(ROWS_WARPS * 32) k_rows_batch(const CurveDev *cv, const int2 *items, int mode)
+{
+    const int2 it = items[blockIdx.x];
+    const CurveDev &c = cv[it.x];
+    rows_body<T, N>(c, mode, it.y, c.row_blocks);
+}
+
 // ---------------------------------------------------------------------------
 // s-direction: structured contraction with D_t (or W^-1 D_t^T W)
 // ---------------------------------------------------------------------------
@@ -698,7 +715,8 @@ __global__ void __launch_bounds__(ROWS_WARPS * 32) k_rows(CurveDev c, int mode)
 //              equivalent increment form), FP64 sum_m w_m |G_m|^2
 //   GM_GRAD:   as GM_UPDATE but G is written out instead of updating u.
 template <typename T, int BN>
-__global__ void __launch_bounds__(DT_THREADS) k_dt(CurveDev c, int mode, int discrete, int gate)
+__device__ __forceinline__ void dt_body(const CurveDev &c, int mode, int discrete, int gate, int tile_c, int tile_r,
+                                        int ks, int tiles_c, int tiles_r)
 {
     namespace cg = cooperative_groups;
     constexpr int BM = DT_BM, BK = DT_BK, TM = 2, TN = BN / 16, WIN = BM + BK - 1;
@@ -719,7 +737,6 @@ __global__ void __launch_bounds__(DT_THREADS) k_dt(CurveDev c, int mode, int dis
     const T *rowscale = (const T *)(discrete ? c.twr : c.sig);
     const T tsign = discrete ? T(-1) : T(1);
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-    const int tile_c = blockIdx.x, tile_r = blockIdx.y, ks = blockIdx.z;
     const int j0 = tile_r * BM, c0 = tile_c * BN;
     const int kbeg = ks * c.kchunk, kend = min(ns, kbeg + c.kchunk);
     T acc[TM][TN];
@@ -780,7 +797,7 @@ __global__ void __launch_bounds__(DT_THREADS) k_dt(CurveDev c, int mode, int dis
     }
 
     // ---- sum of the splits of this tile inside the cluster (distributed shared memory)
-    const int ntiles = gridDim.x * gridDim.y;
+    const int ntiles = tiles_c * tiles_r;
     const int nsplit = c.ksplit;
     // outputs this CTA finishes: rows [r0, r1) of the tile, all columns
     const int rows_per = (BM + nsplit - 1) / nsplit;
@@ -847,7 +864,7 @@ __global__ void __launch_bounds__(DT_THREADS) k_dt(CurveDev c, int mode, int dis
 
     // ---- FP64 |G|^2: per-CTA partial, last CTA of the grid sums them in a fixed order
     partsum = block_sum<DT_THREADS>(partsum, red);
-    const int bid = (ks * gridDim.y + tile_r) * gridDim.x + tile_c, nb = ntiles * nsplit;
+    const int bid = (ks * tiles_r + tile_r) * tiles_c + tile_c, nb = ntiles * nsplit;
     if (threadIdx.x == 0) c.tile[bid] = partsum;
     __threadfence();
     __syncthreads();
@@ -870,6 +887,23 @@ __global__ void __launch_bounds__(DT_THREADS) k_dt(CurveDev c, int mode, int dis
         }
         sc->cnt_gemm = 0;
     }
+}
+
+template <typename T, int BN>
+__global__ void __launch_bounds__(DT_THREADS) k_dt(CurveDev c, int mode, int discrete, int gate)
+{
+    dt_body<T, BN>(c, mode, discrete, gate, blockIdx.x, blockIdx.y, blockIdx.z, gridDim.x, gridDim.y);
+}
+
+// Batched s-phase: work item (curve, tile_c, tile_r) per CTA, curves laid out
+// without splits (ksplit = 1).
+template <typename T, int BN>
+__global__ void __launch_bounds__(DT_THREADS) k_dt_batch(const CurveDev *cv, const int4 *items, int mode,
+                                                          int discrete, int gate)
+{
+    const int4 it = items[blockIdx.x];
+    const CurveDev &c = cv[it.x];
+    dt_body<T, BN>(c, mode, discrete, gate, it.y, it.z, 0, c.tiles_c, c.tiles_r);
 }
 
 // ---------------------------------------------------------------------------
@@ -1042,6 +1076,58 @@ cudaError_t launch_dt(const CurveDev &c, int mode, int discrete, int gate, cudaS
                                   : launch_dt_t<double, 64>(c, mode, discrete, gate, st);
     return c.prec ? launch_dt_t<float, 32>(c, mode, discrete, gate, st)
                   : launch_dt_t<double, 32>(c, mode, discrete, gate, st);
+}
+
+template <typename T>
+static cudaError_t rows_batch_t(int N, const CurveDev *cv, const int2 *items, int nitems, int mode, cudaStream_t st)
+{
+    return dispatch_n(N, [&](auto nn) {
+        constexpr int NN = decltype(nn)::value;
+        size_t sm = rows_smem<T>(NN, 3);
+        cudaError_t e = set_smem(k_rows_batch<T, NN>, sm);
+        if (e != cudaSuccess) return e;
+        k_rows_batch<T, NN><<<nitems, ROWS_WARPS * 32, sm, st>>>(cv, items, mode);
+        return cudaGetLastError();
+    });
+}
+
+cudaError_t launch_rows_batch(int prec, int N, const CurveDev *cv, const int2 *items, int nitems, int mode,
+                              cudaStream_t st)
+{
+    if (nitems <= 0) return cudaSuccess;
+    return prec ? rows_batch_t<float>(N, cv, items, nitems, mode, st) : rows_batch_t<double>(N, cv, items, nitems, mode, st);
+}
+
+cudaError_t launch_dt_batch(int prec, int bn, const CurveDev *cv, const int4 *items, int nitems, int mode,
+                            int discrete, int gate, cudaStream_t st)
+{
+    if (nitems <= 0) return cudaSuccess;
+    if (bn == 64) {
+        if (prec) k_dt_batch<float, 64><<<nitems, DT_THREADS, 0, st>>>(cv, items, mode, discrete, gate);
+        else k_dt_batch<double, 64><<<nitems, DT_THREADS, 0, st>>>(cv, items, mode, discrete, gate);
+    } else {
+        if (prec) k_dt_batch<float, 32><<<nitems, DT_THREADS, 0, st>>>(cv, items, mode, discrete, gate);
+        else k_dt_batch<double, 32><<<nitems, DT_THREADS, 0, st>>>(cv, items, mode, discrete, gate);
+    }
+    return cudaGetLastError();
+}
+
+__global__ void k_set_limit_batch(const CurveDev *cv, int nb, long long nsteps, double tol)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nb; i += gridDim.x * blockDim.x) {
+        DevScalars *sc = cv[i].sc;
+        sc->limit = sc->step + nsteps;
+        sc->tol = tol;
+        sc->done = 0;
+        sc->status = 0;
+        sc->active = 0;
+    }
+}
+
+cudaError_t launch_set_limit_batch(const CurveDev *cv, int nb, long long nsteps, double tol, cudaStream_t st)
+{
+    k_set_limit_batch<<<(nb + 127) / 128, 128, 0, st>>>(cv, nb, nsteps, tol);
+    return cudaGetLastError();
 }
 
 }  // namespace ks

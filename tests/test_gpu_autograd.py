@@ -1,0 +1,111 @@
+"""KSCost / CurveCost (torch.autograd.Function over the C ABI) at the
+differentiation workload L = 22, N_x = 64, N_s = 1024:
+  * against central finite differences (h = 1e-6) of the same function along 64
+    seeded directions (FP64),
+  * against the oracle's exact gradient of the discretised J^2 (FP64 and FP32),
+  * dJ^2/dlambda, and the chain rule through ordinary torch operations.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2301_11704_gb300 import gen
+from paper_2301_11704_gb300.autograd import CurveCost
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def setup():
+    spec = gen.workload(1)[0]
+    up, um = gen.end_points(spec)
+    amps, vp = gen.perturbation(spec)
+    U = oracle.curve_init(spec.M, spec.S, up, um, amps=amps, vp=vp)
+    X = oracle.curve_physical(U)
+    return spec, up, um, U, X
+
+
+def _smooth_direction(rng, M, N, L):
+    """Seeded direction, smooth in x (mode amplitudes 0.7^j) and vanishing at the ends."""
+    x = np.arange(N) * L / N
+    d = np.zeros((M, N))
+    for m in range(M):
+        for j in range(1, 9):
+            d[m] += 0.7 ** j * (rng.normal() * np.cos(2 * np.pi * j * x / L) + rng.normal() * np.sin(2 * np.pi * j * x / L))
+    return d
+
+
+def _oracle_grad(U, spec, lam=1.0):
+    R, D = oracle.curve_residual(U, spec.L, spec.S, lam)
+    G, _ = oracle.curve_adjoint(U, R, spec.L, spec.S, lam, mode=oracle.DISCRETE)
+    _, _, w = oracle.grid(spec.M, spec.S)
+    sc = oracle.curve_scalars(R, D, spec.L, spec.S, lam)
+    return G, w, sc
+
+
+def _precond_rel(g_interior, G, w, spec):
+    """Relative max error of the gradient in the preconditioned norm the descent
+    applies (dtau / (1 + dtau a_j^2) per Fourier mode), after removing the
+    Euclidean weights -2 dx w_m."""
+    k = 2 * np.pi * np.arange(spec.N // 2) / spec.L
+    a = k ** 4 - k ** 2
+    pw = spec.dtau / (1 + spec.dtau * a * a)
+    gw = np.asarray(g_interior) / (-2.0 * spec.L / spec.N * w[1:-1, None])
+    gh = np.fft.rfft(gw, axis=1)[:, : spec.N // 2] / spec.N
+    ref = G[1:-1] * pw[None, :]
+    return np.abs(gh * pw[None, :] - ref).max() / np.abs(ref).max()
+
+
+def test_gradient_matches_finite_differences(setup):
+    spec, up, um, U, X = setup
+    cost = CurveCost(spec.L, spec.N, spec.Ns, spec.S, up, um)
+    u = torch.tensor(X[1:-1], dtype=torch.float64, device="cuda", requires_grad=True)
+    lam = torch.tensor(1.0, dtype=torch.float64, device="cuda", requires_grad=True)
+    J2 = cost(u, lam)
+    J2.backward()
+    g = u.grad.detach()
+    rng = gen.SplitMix64(gen.seed_for(1, 0) + 77)
+    h = 1e-6
+    gnorm = g.norm().item()
+    worst = 0.0
+    with torch.no_grad():
+        for _ in range(64):
+            d = torch.tensor(_smooth_direction(rng, spec.M, spec.N, spec.L), dtype=torch.float64, device="cuda")
+            fd = (cost(u + h * d, lam).item() - cost(u - h * d, lam).item()) / (2 * h)
+            an = torch.sum(g * d).item()
+            err = abs(fd - an) / (gnorm * d.norm().item())
+            worst = max(worst, err)
+        assert worst < 1e-7, worst
+        fdl = (cost(u, lam + h).item() - cost(u, lam - h).item()) / (2 * h)
+    assert abs(fdl - lam.grad.item()) <= 1e-7 * max(1.0, abs(lam.grad.item()))
+    cost.curve.close()
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-10), ("fp32", 1e-5)])
+def test_gradient_matches_the_oracle(setup, precision, tol):
+    spec, up, um, U, X = setup
+    G, w, sc = _oracle_grad(U, spec)
+    cost = CurveCost(spec.L, spec.N, spec.Ns, spec.S, up, um, precision=precision)
+    dt = torch.float64 if precision == "fp64" else torch.float32
+    u = torch.tensor(X[1:-1], dtype=dt, device="cuda", requires_grad=True)
+    lam = torch.tensor(1.0, dtype=torch.float64, device="cuda", requires_grad=True)
+    J2 = cost(u, lam)
+    assert abs(J2.item() - sc["J2"]) <= tol * sc["J2"]
+    J2.backward()
+    assert _precond_rel(u.grad.double().cpu().numpy(), G, w, spec) < tol
+    assert abs(lam.grad.item() - sc["dJ2_dlambda"]) <= tol * abs(sc["dJ2_dlambda"])
+    cost.curve.close()
+
+
+def test_chain_rule_through_torch_operations(setup):
+    spec, up, um, U, X = setup
+    cost = CurveCost(spec.L, spec.N, spec.Ns, spec.S, up, um)
+    base = torch.tensor(X[1:-1], dtype=torch.float64, device="cuda")
+    d = torch.tensor(_smooth_direction(gen.SplitMix64(5), spec.M, spec.N, spec.L), dtype=torch.float64, device="cuda")
+    alpha = torch.tensor(0.0, dtype=torch.float64, device="cuda", requires_grad=True)
+    (2.0 * cost(base + alpha * d)).backward()
+    u = base.clone().requires_grad_(True)
+    cost(u).backward()
+    assert abs(alpha.grad.item() - 2.0 * torch.sum(u.grad * d).item()) <= 1e-12 * max(1.0, abs(alpha.grad.item()))
+    cost.curve.close()

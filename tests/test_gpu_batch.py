@@ -1,0 +1,107 @@
+"""Batched descent (ks_batch_*): curves of uneven N_s, N and L in one set of
+launches must behave exactly like independent curves (each checked against a
+single-curve run and the oracle), stop independently at their own tolerance,
+and survive the tile autotuner; the 256-curve batch workload runs end to end."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2301_11704_gb300 import gen
+from paper_2301_11704_gb300.batch import KSBatch
+from paper_2301_11704_gb300.curve import KSCurve
+
+pytestmark = pytest.mark.gpu
+
+
+def _mixed_specs():
+    """Seven curves from the batch workload recipe, cut to small sizes (uneven
+    N_s, N, L; N_s ragged with respect to every tile size)."""
+    base = gen.workload(3)
+    picks = [0, 1, 2, 3, 5, 8, 13]
+    out = []
+    for k, i in enumerate(picks):
+        s = base[i]
+        Ns = [37, 130, 65, 200, 19, 96, 151][k]
+        out.append(gen.CurveSpec(3, i, s.L, s.N, Ns, gen.mapping_scale(Ns), dtau=0.002, steps=0))
+    return out
+
+
+def _inputs(spec):
+    up, um = gen.end_points(spec)
+    amps, vp = gen.perturbation(spec)
+    return up, um, amps, vp
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_batch_matches_independent_curves(precision):
+    specs = _mixed_specs()
+    ins = [_inputs(s) for s in specs]
+    b = KSBatch(specs, [i[0] for i in ins], [i[1] for i in ins], precision=precision, conv="jarc")
+    b.init_trial(np.array([i[2] for i in ins]), [i[3] for i in ins])
+    out = b.descend(40)
+    assert np.all(out["steps"] == 40)
+    tol = 1e-11 if precision == "fp64" else 2e-5
+    for k, s in enumerate(specs):
+        up, um, amps, vp = ins[k]
+        c = KSCurve(s.L, s.N, s.Ns, s.S, up, um, dtau=s.dtau, precision=precision)
+        c.init_trial(0.0, None, amps, vp)
+        ref = c.descend(40)
+        xb = b.get_state(k).double().cpu().numpy()
+        xc = c.get_state().double().cpu().numpy()
+        assert np.abs(xb - xc).max() <= tol * np.abs(xc).max(), (k, s)
+        assert abs(out["J"][k] - ref["J"]) <= tol * ref["J"]
+        c.close()
+    b.close()
+
+
+def test_batch_matches_the_oracle_fp64():
+    specs = _mixed_specs()[:3]
+    ins = [_inputs(s) for s in specs]
+    b = KSBatch(specs, [i[0] for i in ins], [i[1] for i in ins], precision="fp64", conv="jarc")
+    b.init_trial(np.array([i[2] for i in ins]), [i[3] for i in ins])
+    out = b.descend(25)
+    for k, s in enumerate(specs):
+        up, um, amps, vp = ins[k]
+        U = oracle.curve_init(s.M, s.S, up, um, amps=amps, vp=vp)
+        Uo, _, sco, _ = oracle.curve_descend(U, s.L, s.S, 25, dtau=s.dtau)
+        xo = oracle.curve_physical(Uo)
+        assert np.abs(b.get_state(k).cpu().numpy() - xo).max() <= 1e-10 * np.abs(xo).max()
+        assert abs(out["J_arc"][k] - sco["J_arc"]) <= 1e-10 * sco["J_arc"]
+    b.close()
+
+
+def test_curves_stop_at_their_own_tolerance_and_autotune_keeps_results():
+    specs = _mixed_specs()
+    ins = [_inputs(s) for s in specs]
+    b = KSBatch(specs, [i[0] for i in ins], [i[1] for i in ins], precision="fp64", conv="jarc")
+    b.init_trial(np.array([i[2] for i in ins]), [i[3] for i in ins])
+    first = b.descend(0)
+    tol = float(np.median(first["J_arc"]))          # about half of the curves are already below it
+    out = b.descend(30, tol)
+    below = first["J_arc"] < tol
+    assert np.all(out["steps"][below] == 0) and np.all(out["steps"][~below] > 0)
+    chosen = b.autotune(4)
+    assert chosen in (32, 64)
+    sc = b.scalars()
+    assert all(np.isfinite(x["J"]) for x in sc)
+    b.close()
+
+
+def test_batch_workload_256_curves_fp32():
+    specs = gen.workload(3)
+    ins = [_inputs(s) for s in specs]
+    b = KSBatch(specs, [i[0] for i in ins], [i[1] for i in ins], precision="fp32", conv="jrel")
+    b.init_trial(np.array([i[2] for i in ins]), [i[3] for i in ins])
+    j0 = b.descend(0)["J"]
+    # three curves' trial-curve cost against the FP64 oracle (J within 1e-5)
+    for k in (0, 100, 255):
+        s = specs[k]
+        up, um, amps, vp = ins[k]
+        R, D = oracle.curve_residual(oracle.curve_init(s.M, s.S, up, um, amps=amps, vp=vp), s.L, s.S)
+        J = np.sqrt(oracle.curve_scalars(R, D, s.L, s.S)["J2"])
+        assert abs(j0[k] - J) <= 1e-5 * J
+    out = b.descend(64)
+    assert np.all(np.isfinite(out["J"])) and np.all(out["steps"] == 64)
+    assert np.median(out["J"] / j0) < 1.0
+    b.close()
