@@ -476,25 +476,45 @@ __device__ __forceinline__ void rows_body(const CurveDev &c, int mode, int blk, 
     __shared__ double wpart[ROWS_WARPS][5];
     __shared__ int am_last;
     DevScalars *sc = c.sc;
-
-    if (mode == ROWS_STEP && (sc->done || sc->step >= sc->limit)) {
-        if (blk == 0 && threadIdx.x == 0) sc->active = 0;
-        return;
-    }
-    for (int t = threadIdx.x; t < H; t += blockDim.x) tw[t] = ((const cpx<T> *)c.twid)[t];
-    __syncthreads();
-
     const int ns = c.ns, P = c.P;
-    const T lam = (T)sc->lambda;
     const T *U = (const T *)c.U, *D = (const T *)c.D;
     T *R = (T *)c.R, *A = (T *)c.A;
     const T *kj = (const T *)c.kj, *aj = (const T *)c.aj;
-
     const int m0 = (blk * ROWS_WARPS + warp) * 2, m1 = m0 + 1;
-    if (m0 < ns) {
-        const bool has1 = m1 < ns;
+    const bool has0 = m0 < ns, has1 = m1 < ns;
+
+    // Every independent global load is issued before the first use (one memory
+    // round trip): the gate, lambda, the twiddles, both sections of u and D_t u,
+    // and the Fourier tables of the modes this lane owns.
+    const int g_done = sc->done;
+    const long long g_step = sc->step, g_limit = sc->limit;
+    const double lamd0 = sc->lambda;
+    const cpx<T> twv = ((int)threadIdx.x < H) ? ((const cpx<T> *)c.twid)[threadIdx.x] : cpx<T>{0, 0};
+    cpx<T> ua[MPL], ub[MPL], ra[MPL], rb[MPL], dva[MPL], dvb[MPL];
+    T kv[MPL], av[MPL];
+#pragma unroll
+    for (int i = 0; i < MPL; ++i) {
+        const int j = lane + 32 * i;
+        const bool ok = j < H;
+        ua[i] = (ok && has0) ? ld2(U, m0, N, j) : cpx<T>{0, 0};
+        ub[i] = (ok && has1) ? ld2(U, m1, N, j) : cpx<T>{0, 0};
+        dva[i] = (ok && has0) ? ld2(D, m0, N, j) : cpx<T>{0, 0};
+        dvb[i] = (ok && has1) ? ld2(D, m1, N, j) : cpx<T>{0, 0};
+        kv[i] = ok ? kj[j] : T(0);
+        av[i] = ok ? aj[j] : T(0);
+    }
+    for (int t = threadIdx.x + blockDim.x; t < H; t += blockDim.x) tw[t] = ((const cpx<T> *)c.twid)[t];
+
+    if (mode == ROWS_STEP && (g_done || g_step >= g_limit)) {
+        if (blk == 0 && threadIdx.x == 0) sc->active = 0;
+        return;
+    }
+    if ((int)threadIdx.x < H) tw[threadIdx.x] = twv;
+    __syncthreads();
+    const T lam = (T)lamd0;
+
+    if (has0) {
         const bool in0 = (m0 > 0 && m0 < P), in1 = has1 && (m1 > 0 && m1 < P);
-        cpx<T> ua[MPL], ub[MPL], ra[MPL], rb[MPL];
         // sums over the modes of a section, in the storage type (N/2 <= 128 terms);
         // sections are combined in FP64 below
         T s0[5] = {0, 0, 0, 0, 0}, s1[5] = {0, 0, 0, 0, 0};   // nr, nd, ndr, nu, nf
@@ -502,11 +522,7 @@ __device__ __forceinline__ void rows_body(const CurveDev &c, int mode, int blk, 
 #pragma unroll
         for (int i = 0; i < MPL; ++i) {
             int j = lane + 32 * i;
-            if (j < H) {
-                ua[i] = ld2(U, m0, N, j);
-                ub[i] = has1 ? ld2(U, m1, N, j) : cpx<T>{0, 0};
-                put_pair<T, N>(B0, j, ua[i], ub[i]);
-            }
+            if (j < H) put_pair<T, N>(B0, j, ua[i], ub[i]);
         }
         if (lane == 0) B0[H] = {0, 0};
         __syncwarp();
@@ -525,11 +541,10 @@ __device__ __forceinline__ void rows_body(const CurveDev &c, int mode, int blk, 
             if (j < H) {
                 cpx<T> wa, wb;
                 get_pair<T, N>(Wq, j, wa, wb);
-                const T k = kj[j], a = aj[j], hk = T(0.5) * k;
+                const T k = kv[i], a = av[i], hk = T(0.5) * k;
                 cpx<T> fa = {hk * wa.y - a * ua[i].x, -hk * wa.x - a * ua[i].y};
                 cpx<T> fb = {hk * wb.y - a * ub[i].x, -hk * wb.x - a * ub[i].y};
-                cpx<T> da = ld2(D, m0, N, j);
-                cpx<T> db = has1 ? ld2(D, m1, N, j) : cpx<T>{0, 0};
+                const cpx<T> da = dva[i], db = dvb[i];
                 ra[i] = in0 ? cpx<T>{fa.x - lam * da.x, fa.y - lam * da.y} : cpx<T>{0, 0};
                 rb[i] = in1 ? cpx<T>{fb.x - lam * db.x, fb.y - lam * db.y} : cpx<T>{0, 0};
                 if (j == 0) { ra[i].y = 0; rb[i].y = 0; fa.y = 0; fb.y = 0; }
@@ -553,7 +568,7 @@ __device__ __forceinline__ void rows_body(const CurveDev &c, int mode, int blk, 
         for (int i = 0; i < MPL; ++i) {
             int j = lane + 32 * i;
             if (j < H) {
-                const T k = kj[j];
+                const T k = kv[i];
                 put_pair<T, N>(X0, j, cpx<T>{-k * ra[i].y, k * ra[i].x}, cpx<T>{-k * rb[i].y, k * rb[i].x});
             }
         }
@@ -573,7 +588,7 @@ __device__ __forceinline__ void rows_body(const CurveDev &c, int mode, int blk, 
             if (j < H) {
                 cpx<T> pa, pb;
                 get_pair<T, N>(Pp, j, pa, pb);
-                const T a = aj[j];
+                const T a = av[i];
                 st2(R, m0, N, j, ra[i]);
                 st2(A, m0, N, j, cpx<T>{pa.x - a * ra[i].x, pa.y - a * ra[i].y});
                 if (has1) {
@@ -728,7 +743,8 @@ __device__ __forceinline__ void dt_body(const CurveDev &c, int mode, int discret
     __shared__ double red[DT_THREADS];
     __shared__ int am_last;
     DevScalars *sc = c.sc;
-    if (gate && !sc->active) return;
+    const int g_active = sc->active;
+    const double lam_d = sc->lambda, dtau_d = sc->dtau;
 
     const int ns = c.ns, N = c.nx, P = c.P, twoP = 2 * P;
     const T *X = (const T *)(mode == GM_STORE ? c.U : c.R);
@@ -763,6 +779,42 @@ __device__ __forceinline__ void dt_body(const CurveDev &c, int mode, int discret
         }
     };
     if (kbeg < kend) fetch(kbeg);
+
+    // Outputs this CTA finishes: with splits, the row band [r0, r1) of the tile
+    // (slot q = element threadIdx.x + q * DT_THREADS of the band); without, the
+    // thread's own accumulators.  Their epilogue operands are prefetched here,
+    // before the contraction, so their loads overlap it.
+    constexpr int EP = TM * TN;
+    const int nsplit = c.ksplit;
+    const int rows_per = (BM + nsplit - 1) / nsplit;
+    const int r0 = min(BM, ks * rows_per), r1 = min(BM, r0 + rows_per);
+    auto slot = [&](int q, int &j, int &col) -> bool {
+        if (nsplit > 1) {
+            const int e = threadIdx.x + q * DT_THREADS;
+            if (e >= (r1 - r0) * BN) return false;
+            j = j0 + r0 + e / BN;
+            col = c0 + e % BN;
+        } else {
+            j = j0 + ty * TM + q / TN;
+            col = c0 + tx * TN + q % TN;
+        }
+        return j < ns && col < N;
+    };
+    const T *Ah = (const T *)c.A, *pr = (const T *)c.prec_imex;
+    T pA[EP], pU[EP], pS[EP], pP[EP];
+    double pW[EP];
+#pragma unroll
+    for (int q = 0; q < EP; ++q) {
+        int j = 0, col = 0;
+        const bool ok = slot(q, j, col);
+        pS[q] = ok ? rowscale[j] : T(0);
+        pA[q] = (ok && mode != GM_STORE) ? Ah[(size_t)j * N + col] : T(0);
+        pU[q] = (ok && mode == GM_UPDATE) ? ((const T *)c.U)[(size_t)j * N + col] : T(0);
+        pP[q] = (ok && mode == GM_UPDATE) ? pr[col >> 1] : T(0);
+        pW[q] = (ok && mode != GM_STORE) ? c.w[j] : 0.0;
+    }
+    if (gate && !g_active) return;
+
     for (int m0 = kbeg; m0 < kend; m0 += BK) {
 #pragma unroll
         for (int q = 0; q < XPT; ++q) {
@@ -798,10 +850,6 @@ __device__ __forceinline__ void dt_body(const CurveDev &c, int mode, int discret
 
     // ---- sum of the splits of this tile inside the cluster (distributed shared memory)
     const int ntiles = tiles_c * tiles_r;
-    const int nsplit = c.ksplit;
-    // outputs this CTA finishes: rows [r0, r1) of the tile, all columns
-    const int rows_per = (BM + nsplit - 1) / nsplit;
-    const int r0 = min(BM, ks * rows_per), r1 = min(BM, r0 + rows_per);
     if (nsplit > 1) {
         cg::cluster_group cluster = cg::this_cluster();
 #pragma unroll
@@ -823,42 +871,34 @@ __device__ __forceinline__ void dt_body(const CurveDev &c, int mode, int discret
         __syncthreads();
     }
 
-    // Epilogue over the outputs this CTA owns.  With splits: the band [r0, r1) held in
-    // Ks (row-major, BN per row); without: the thread's own accumulators.
+    // ---- epilogue over the slots (operands prefetched above)
     T *Dout = (T *)c.D;
-    const T lam = (T)sc->lambda, dtau = (T)sc->dtau;
-    const T *Ah = (const T *)c.A, *pr = (const T *)c.prec_imex;
+    const T lam = (T)lam_d, dtau = (T)dtau_d;
     T *U = (T *)c.U, *G = (T *)c.G;
     double partsum = 0.0;
-    auto emit = [&](int j, int col, T y0) {
-        if (j >= ns || col >= N) return;
-        const T y = rowscale[j] * y0;
+#pragma unroll
+    for (int q = 0; q < EP; ++q) {
+        int j = 0, col = 0;
+        if (!slot(q, j, col)) continue;
+        const T y0 = (nsplit > 1) ? ((T *)Ks)[threadIdx.x + q * DT_THREADS] : acc[q / TN][q % TN];
+        const T y = pS[q] * y0;
         if (mode == GM_STORE) {
             Dout[(size_t)j * N + col] = y;
-            return;
+            continue;
         }
         const bool interior = (j > 0 && j < P);
         T g = 0;
         if (interior && col != 1) {
             const T e = discrete ? -lam * y : lam * y;
-            g = -(Ah[(size_t)j * N + col] + e);
+            g = -(pA[q] + e);
             const double cw = (col < 2) ? 1.0 : 2.0;
-            partsum += c.w[j] * cw * (double)g * (double)g;
+            partsum += pW[q] * cw * (double)g * (double)g;
         }
         if (mode == GM_UPDATE) {
-            if (interior) U[(size_t)j * N + col] += dtau * pr[col >> 1] * g;
+            if (interior) U[(size_t)j * N + col] = pU[q] + dtau * pP[q] * g;
         } else {
             G[(size_t)j * N + col] = g;
         }
-    };
-    if (nsplit > 1) {
-        for (int e = threadIdx.x; e < (r1 - r0) * BN; e += DT_THREADS)
-            emit(j0 + r0 + e / BN, c0 + e % BN, ((T *)Ks)[e]);
-    } else {
-#pragma unroll
-        for (int i = 0; i < TM; ++i)
-#pragma unroll
-            for (int l = 0; l < TN; ++l) emit(j0 + ty * TM + i, c0 + tx * TN + l, acc[i][l]);
     }
     if (mode == GM_STORE) return;
 
