@@ -84,7 +84,10 @@ typedef struct {
     int32_t conv;        /* ks_conv */
     int32_t check_ends;  /* 1: ks_curve_create fails with KS_ENOTEQUILIBRIUM when an end
                             section has |f(u)|_2 > 1e-8 (1 + |u|_2); 0: no check */
-    int32_t reserved;    /* must be 0 */
+    int32_t symmetry;    /* symmetric subspace held exactly (Sec. V.B; the dynamics preserves it):
+                            bit 0: every section odd, u(-x) = -u(x) (real parts of u^ zero);
+                            bit 1: every section L/2-periodic (odd Fourier modes zero);
+                            0 = none.  Values above 3 are invalid. */
 } ks_params;
 
 /* Scalars of the state most recently evaluated (cost, gradient or descent). */

@@ -62,6 +62,7 @@ def _load():
             "ko_dt_apply": (None, [i, d, p, p]),
             "ko_dtT_apply": (None, [i, d, p, p]),
             "ko_dt_matrix": (None, [i, d, p]),
+            "ko_dt_row": (None, [i, d, i, p]),
             "ko_curve_residual": (None, [i, i, d, d, d, p, p, p]),
             "ko_curve_rhs": (None, [i, i, d, p, p]),
             "ko_curve_linearised": (None, [i, i, d, d, d, p, p, p]),
@@ -170,6 +171,23 @@ def dtT_apply(y, S):
     out = np.empty(M + 2)
     _load().ko_dtT_apply(M, S, _ptr(y), _ptr(out))
     return out
+
+
+def dt_row(M, S, j):
+    """Row j of the D_t matrix, entry by entry from its explicit k-sum."""
+    out = np.empty(M + 2)
+    _load().ko_dt_row(M, S, int(j), _ptr(out))
+    return out
+
+
+def section_residual(U, j, L, S, lam=1.0):
+    """Residual of section j alone: f(u_j) - lam sum_m D_t[j, m] u_m, with the
+    row of D_t from its explicit sum (for sampled checks of large curves)."""
+    U = _c(U, np.complex128)
+    M, N = U.shape[0] - 2, 2 * U.shape[1]
+    if j == 0 or j == M + 1:
+        return np.zeros(N // 2, np.complex128)
+    return rhs(U[j], N, L) - lam * (dt_row(M, S, j) @ U)
 
 
 def dt_matrix(M, S):

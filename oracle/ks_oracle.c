@@ -287,6 +287,23 @@ void ko_dt_matrix(int M, double S, double *D)
     trig_free(tb);
 }
 
+/* Row j of the matrix of eq. rational_diff_matrix, each entry by its explicit
+ * k-sum (O(M^2) per row; used to check sampled sections of large curves). */
+void ko_dt_row(int M, double S, int j, double *row)
+{
+    int P = M + 1;
+    trig_tab tb = trig_table(P);
+    double sj = TS(tb, j);
+#pragma omp parallel for schedule(static)
+    for (int m = 0; m <= P; ++m) {
+        double acc = 0.0;
+        for (int k = 0; k <= P; ++k)
+            acc += (double)k / (cbar(m, P) * cbar(k, P)) * TC(tb, (long)m * k) * TS(tb, (long)k * j);
+        row[m] = 2.0 / (S * (double)P) * sj * sj * acc;
+    }
+    trig_free(tb);
+}
+
 /* Apply D_t (or D_t^T) to every real and imaginary column of a curve. */
 static void curve_dt(int M, int N, double S, const cplx *X, cplx *Y, int transpose)
 {

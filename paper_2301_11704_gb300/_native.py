@@ -43,7 +43,7 @@ class KSParams(ctypes.Structure):
         ("adjoint", ctypes.c_int32),
         ("conv", ctypes.c_int32),
         ("check_ends", ctypes.c_int32),
-        ("reserved", ctypes.c_int32),
+        ("symmetry", ctypes.c_int32),
     ]
 
 

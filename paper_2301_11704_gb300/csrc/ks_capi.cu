@@ -81,7 +81,7 @@ ks_status validate(const ks_params *p)
     if (p->adjoint != KS_ADJ_PAPER && p->adjoint != KS_ADJ_DISCRETE) return fail(KS_EINVAL, "adjoint must be KS_ADJ_PAPER or KS_ADJ_DISCRETE");
     if (p->conv < KS_CONV_JARC || p->conv > KS_CONV_JREL) return fail(KS_EINVAL, "conv must be a ks_conv value");
     if (p->check_ends != 0 && p->check_ends != 1) return fail(KS_EINVAL, "check_ends must be 0 or 1");
-    if (p->reserved != 0) return fail(KS_EINVAL, "reserved must be 0");
+    if (p->symmetry < 0 || p->symmetry > 3) return fail(KS_EINVAL, "symmetry must be in [0, 3]");
     return KS_OK;
 }
 

@@ -62,6 +62,7 @@ struct Layout {
 
 struct CurveDev {
     int ns, nx, P, prec;   // prec: 0 = double, 1 = float
+    int sym;               // symmetry bits of ks_params (coefficients held at zero)
     double L, S, s0;
     void *U, *D, *R, *A, *G;
     void *X;               // FP64 physical scratch [N_s][N]

@@ -106,6 +106,7 @@ CurveDev bind_layout(const ks_params *p, const Layout &l, void *base)
     d.nx = p->nx;
     d.P = p->ns - 1;
     d.prec = p->precision == KS_FP32 ? 1 : 0;
+    d.sym = p->symmetry;
     d.L = p->L;
     d.S = p->S;
     d.s0 = p->s0;
@@ -194,6 +195,23 @@ __device__ __forceinline__ void get_pair(const cpx<T> *W, int j, cpx<T> &A, cpx<
     A = {(wj.x + wn.x) * h, (wj.y - wn.y) * h};
     B = {(wj.y + wn.y) * h, (wn.x - wj.x) * h};
     if (j == 0) { A.y = 0; B.y = 0; }
+}
+
+// Symmetric subspaces (Sec. V.B): bit 0 = odd sections (real parts of every
+// coefficient zero), bit 1 = L/2-periodic sections (odd modes zero).
+template <typename T>
+__device__ __forceinline__ cpx<T> project(cpx<T> v, int j, int sym)
+{
+    if (sym & 1) v.x = T(0);
+    if ((sym & 2) && (j & 1)) v = cpx<T>{0, 0};
+    return v;
+}
+
+__device__ __forceinline__ bool col_allowed(int col, int sym)
+{
+    if ((sym & 1) && !(col & 1)) return false;
+    if ((sym & 2) && ((col >> 1) & 1)) return false;
+    return true;
 }
 
 template <typename T>
@@ -409,6 +427,8 @@ __global__ void __launch_bounds__(ROWS_WARPS * 32) k_row_fwd(CurveDev c, const T
     for (int j = lane; j < H; j += 32) {
         cpx<Tc> A, B;
         get_pair<Tc, N>(W, j, A, B);
+        A = project(A, j, c.sym);
+        B = project(B, j, c.sym);
         if (!(keep_ends && (m0 == 0 || m0 == c.P))) st2(spec, m0, N, j, cpx<To>{(To)A.x, (To)A.y});
         if (has1 && !(keep_ends && m1 == c.P)) st2(spec, m1, N, j, cpx<To>{(To)B.x, (To)B.y});
     }
@@ -545,8 +565,8 @@ __device__ __forceinline__ void rows_body(const CurveDev &c, int mode, int blk, 
                 cpx<T> fa = {hk * wa.y - a * ua[i].x, -hk * wa.x - a * ua[i].y};
                 cpx<T> fb = {hk * wb.y - a * ub[i].x, -hk * wb.x - a * ub[i].y};
                 const cpx<T> da = dva[i], db = dvb[i];
-                ra[i] = in0 ? cpx<T>{fa.x - lam * da.x, fa.y - lam * da.y} : cpx<T>{0, 0};
-                rb[i] = in1 ? cpx<T>{fb.x - lam * db.x, fb.y - lam * db.y} : cpx<T>{0, 0};
+                ra[i] = in0 ? project(cpx<T>{fa.x - lam * da.x, fa.y - lam * da.y}, j, c.sym) : cpx<T>{0, 0};
+                rb[i] = in1 ? project(cpx<T>{fb.x - lam * db.x, fb.y - lam * db.y}, j, c.sym) : cpx<T>{0, 0};
                 if (j == 0) { ra[i].y = 0; rb[i].y = 0; fa.y = 0; fb.y = 0; }
                 const T cw = (j == 0) ? T(1) : T(2);
                 s0[0] += cw * (ra[i].x * ra[i].x + ra[i].y * ra[i].y);
@@ -590,10 +610,10 @@ __device__ __forceinline__ void rows_body(const CurveDev &c, int mode, int blk, 
                 get_pair<T, N>(Pp, j, pa, pb);
                 const T a = av[i];
                 st2(R, m0, N, j, ra[i]);
-                st2(A, m0, N, j, cpx<T>{pa.x - a * ra[i].x, pa.y - a * ra[i].y});
+                st2(A, m0, N, j, project(cpx<T>{pa.x - a * ra[i].x, pa.y - a * ra[i].y}, j, c.sym));
                 if (has1) {
                     st2(R, m1, N, j, rb[i]);
-                    st2(A, m1, N, j, cpx<T>{pb.x - a * rb[i].x, pb.y - a * rb[i].y});
+                    st2(A, m1, N, j, project(cpx<T>{pb.x - a * rb[i].x, pb.y - a * rb[i].y}, j, c.sym));
                 }
             }
         }
@@ -888,7 +908,7 @@ __device__ __forceinline__ void dt_body(const CurveDev &c, int mode, int discret
         }
         const bool interior = (j > 0 && j < P);
         T g = 0;
-        if (interior && col != 1) {
+        if (interior && col != 1 && col_allowed(col, c.sym)) {
             const T e = discrete ? -lam * y : lam * y;
             g = -(pA[q] + e);
             const double cw = (col < 2) ? 1.0 : 2.0;

@@ -34,12 +34,15 @@ class KSCurve:
     Physical arrays exchanged with the curve are torch tensors [ns, nx] on the
     curve's device in its storage dtype (float64 for "fp64", float32 for "fp32").
     Row 0 is s = +inf (u_plus), row ns-1 is s = -inf (u_minus).
+    symmetry: 1 holds every section odd, 2 holds it L/2-periodic, 3 both (the
+    symmetric subspaces the descent preserves, Sec. V.B).
     """
 
     def __init__(self, L: float, nx: int, ns: int, S: float, u_plus, u_minus=None, *, s0: float = 0.0,
                  lam: float = 1.0, lambda_free: bool = False, dtau: float = 0.01, dtau_lambda: float = 0.0,
                  precision: str = "fp64", adjoint: str = "paper", conv: str = "jarc", u_init=None,
-                 check_ends: bool = False, device=None, stream: Optional[torch.cuda.Stream] = None):
+                 check_ends: bool = False, symmetry: int = 0, device=None,
+                 stream: Optional[torch.cuda.Stream] = None):
         self.lib = _native.load()
         self.device = torch.device(device if device is not None else "cuda")
         self.dtype = torch.float64 if precision == "fp64" else torch.float32
@@ -47,7 +50,7 @@ class KSCurve:
         self.params = KSParams(L=L, nx=nx, ns=ns, S=S, s0=s0, lam=lam, lambda_free=int(bool(lambda_free)),
                                dtau=dtau, dtau_lambda=dtau_lambda, precision=_PREC[precision],
                                adjoint=_ADJ[adjoint], conv=_CONV[conv], check_ends=int(bool(check_ends)),
-                               reserved=0)
+                               symmetry=int(symmetry))
         nbytes = self.lib.ks_curve_workspace_bytes(ctypes.byref(self.params))
         if nbytes == 0:
             raise _native.KSError(_native.KS_EINVAL, self.lib.ks_last_error().decode())

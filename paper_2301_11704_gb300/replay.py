@@ -69,8 +69,16 @@ def end_points(orbit: str):
     return equilibrium(a), equilibrium(b)
 
 
+def default_symmetry(orbit: str) -> int:
+    """The subspace the a = 0 trial curve lies in and the descent preserves
+    (Sec. V.B): every run is odd; E2 and gamma(1/4)E2 are also L/2-periodic, so
+    that search stays in the smaller subspace where, by Sec. V.D, no connection
+    exists."""
+    return 3 if orbit.startswith("E2-g14") else 1
+
+
 def run(orbit: str, precision: str = "fp64", tol: float = 1e-12, max_tau: float = 2.0e4,
-        record_every: int = 1000, device=None, log=None):
+        record_every: int = 1000, device=None, log=None, symmetry=None, save=None):
     """Descends the trial curve of `orbit` until J_arc < tol or tau >= max_tau.
 
     Returns a dict with the settings, the (tau, J, J_arc) history every
@@ -78,8 +86,9 @@ def run(orbit: str, precision: str = "fp64", tol: float = 1e-12, max_tau: float 
     from .curve import KSCurve
     M, S = ORBITS[orbit]
     um, up = end_points(orbit)
+    sym = default_symmetry(orbit) if symmetry is None else int(symmetry)
     c = KSCurve(L_PAPER, N_PAPER, M + 2, S, up, um, s0=0.0, dtau=DTAU_PAPER, precision=precision,
-                adjoint="paper", conv="jarc", check_ends=True, device=device)
+                adjoint="paper", conv="jarc", check_ends=True, symmetry=sym, device=device)
     J2, Ja = c.cost()
     hist = [(0.0, float(np.sqrt(J2)), float(Ja))]
     t0 = time.perf_counter()
@@ -100,8 +109,11 @@ def run(orbit: str, precision: str = "fp64", tol: float = 1e-12, max_tau: float 
         if not np.isfinite(out["J"]):
             break
     wall = time.perf_counter() - t0
+    if save:
+        np.save(save, c.get_state().double().cpu().numpy())
     c.close()
     return dict(orbit=orbit, M=M, S=S, N=N_PAPER, L=L_PAPER, dtau=DTAU_PAPER, precision=precision, tol=tol,
+                symmetry=sym,
                 steps=steps, tau=steps * DTAU_PAPER, J=hist[-1][1], J_arc=hist[-1][2], converged=converged,
                 seconds=wall, history=hist)
 
@@ -114,8 +126,11 @@ def main(argv=None):
     ap.add_argument("--max-tau", type=float, default=2.0e4)
     ap.add_argument("--record-every", type=int, default=1000)
     ap.add_argument("--history", action="store_true", help="print the full history")
+    ap.add_argument("--symmetry", type=int, default=None, help="0 none, 1 odd, 3 odd and L/2-periodic")
+    ap.add_argument("--save", default=None, help="write the final physical curve to this .npy file")
     args = ap.parse_args(argv)
-    res = run(args.orbit, args.precision, args.tol, args.max_tau, args.record_every, log=sys.stderr)
+    res = run(args.orbit, args.precision, args.tol, args.max_tau, args.record_every, log=sys.stderr,
+              symmetry=args.symmetry, save=args.save)
     if not args.history:
         h = res["history"]
         res["history"] = h[:: max(1, len(h) // 40)] + [h[-1]]

@@ -85,9 +85,14 @@ def test_gradient_matches_finite_differences(setup):
 @pytest.mark.parametrize("precision,tol", [("fp64", 1e-10), ("fp32", 1e-5)])
 def test_gradient_matches_the_oracle(setup, precision, tol):
     spec, up, um, U, X = setup
+    dt = torch.float64 if precision == "fp64" else torch.float32
+    if precision == "fp32":
+        # the same input on both sides: the curve as the FP32 tensor holds it
+        X = X.astype(np.float32).astype(np.float64)
+        U = oracle.curve_spectral(X)
+        up, um = X[0], X[-1]
     G, w, sc = _oracle_grad(U, spec)
     cost = CurveCost(spec.L, spec.N, spec.Ns, spec.S, up, um, precision=precision)
-    dt = torch.float64 if precision == "fp64" else torch.float32
     u = torch.tensor(X[1:-1], dtype=dt, device="cuda", requires_grad=True)
     lam = torch.tensor(1.0, dtype=torch.float64, device="cuda", requires_grad=True)
     J2 = cost(u, lam)

@@ -1,0 +1,92 @@
+"""Parity at the full sizes of the large workloads, where the oracle cannot run a
+whole evaluation: sampled sections of the residual are computed by the oracle
+one at a time (f of the section and its row of D_t from the explicit sum of
+eq. rational_diff_matrix), and properties that hold at any size are checked
+(cost of the FP32 path against the FP64 path; invariance of J under a grid shift).
+
+Workloads: L = 44, N_x = 128, N_s = 4096 (FP64 and FP32) and
+L = 100, N_x = 256, N_s = 16384 (FP32), trial curves of the seeded recipe.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2301_11704_gb300 import gen
+from paper_2301_11704_gb300.curve import KSCurve
+
+pytestmark = pytest.mark.gpu
+
+
+def _trial(spec):
+    up, um = gen.end_points(spec)
+    amps, vp = gen.perturbation(spec)
+    return up, um, amps, vp
+
+
+def _sampled_rows(spec, rows, U):
+    """Oracle residual of the sampled sections, physical [len(rows), N]."""
+    return np.stack([oracle.inv(oracle.section_residual(U, j, spec.L, spec.S), spec.N) for j in rows])
+
+
+def _rows(Ns):
+    return [1, 2, Ns // 7, Ns // 2 - 1, Ns // 2, (3 * Ns) // 4, Ns - 3, Ns - 2]
+
+
+@pytest.fixture(scope="module")
+def cfg2():
+    spec = gen.workload(2)[0]
+    up, um, amps, vp = _trial(spec)
+    U = oracle.curve_init(spec.M, spec.S, up, um, amps=amps, vp=vp)
+    rows = _rows(spec.Ns)
+    return spec, (up, um, amps, vp), rows, _sampled_rows(spec, rows, U)
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-10), ("fp32", 1e-5)])
+def test_large_curve_sampled_residual(cfg2, precision, tol):
+    spec, (up, um, amps, vp), rows, ref = cfg2
+    c = KSCurve(spec.L, spec.N, spec.Ns, spec.S, up, um, dtau=spec.dtau, precision=precision)
+    c.init_trial(0.0, None, amps, vp)
+    r = c.residual().double().cpu().numpy()[rows]
+    if precision == "fp64":
+        assert np.abs(r - ref).max() <= tol * np.abs(ref).max()
+    else:
+        assert np.linalg.norm(r - ref) <= tol * np.linalg.norm(ref)
+    c.close()
+
+
+def test_large_curve_fp32_cost_matches_fp64(cfg2):
+    spec, (up, um, amps, vp), rows, ref = cfg2
+    out = {}
+    for prec in ("fp64", "fp32"):
+        c = KSCurve(spec.L, spec.N, spec.Ns, spec.S, up, um, dtau=spec.dtau, precision=prec)
+        c.init_trial(0.0, None, amps, vp)
+        out[prec] = c.cost()
+        c.close()
+    (J2d, Jad), (J2s, Jas) = out["fp64"], out["fp32"]
+    assert abs(np.sqrt(J2s) - np.sqrt(J2d)) <= 1e-5 * np.sqrt(J2d)
+    assert abs(Jas - Jad) <= 1e-5 * Jad
+
+
+@pytest.fixture(scope="module")
+def cfg4():
+    spec = gen.workload(4)[0]
+    up, um, amps, vp = _trial(spec)
+    U = oracle.curve_init(spec.M, spec.S, up, um, amps=amps, vp=vp)
+    rows = _rows(spec.Ns)[::2]
+    return spec, (up, um, amps, vp), rows, _sampled_rows(spec, rows, U)
+
+
+def test_largest_curve_fp32_sampled_residual_and_shift_invariance(cfg4):
+    spec, (up, um, amps, vp), rows, ref = cfg4
+    c = KSCurve(spec.L, spec.N, spec.Ns, spec.S, up, um, dtau=spec.dtau, precision="fp32")
+    c.init_trial(0.0, None, amps, vp)
+    J2, Ja = c.cost()
+    r = c.residual().double().cpu().numpy()[rows]
+    assert np.linalg.norm(r - ref) <= 1e-5 * np.linalg.norm(ref)
+    # the same curve translated by 37 grid points has the same cost (Sec. V.B)
+    u = c.get_state()
+    c.set_state(torch.roll(u, shifts=37, dims=1), 1.0, 0.0)
+    J2s, Jas = c.cost()
+    assert abs(J2s - J2) <= 1e-5 * J2 and abs(Jas - Ja) <= 1e-5 * Ja
+    c.close()

@@ -245,3 +245,27 @@ def test_descent_is_deterministic_and_resumable(cfg0):
     assert abs(d.get_lambda_tau()[1] - 80 * spec.dtau) < 1e-12
     for x in (a, b, c, d):
         x.close()
+
+
+@pytest.mark.parametrize("sym", [1, 3])
+def test_symmetric_subspace_is_held_exactly(sym):
+    """Sections restricted to odd (and L/2-periodic) fields keep exactly zero
+    coefficients outside the subspace and agree with the oracle's unrestricted
+    descent, whose off-subspace coefficients stay at rounding level (Sec. V.B)."""
+    from paper_2301_11704_gb300 import replay
+    M, S, N, L = 60, 6.1, 32, 22.0
+    e2 = replay.equilibrium("E2", 64, L)[::2]          # E2 on the N = 32 grid
+    up, um = e2, np.zeros(N)
+    c = KSCurve(L, N, M + 2, S, up, um, symmetry=sym)
+    U = oracle.curve_init(M, S, up, um)
+    Uo, _, sco, _ = oracle.curve_descend(U, L, S, 100, dtau=0.01)
+    out = c.descend(100)
+    x = c.get_state().cpu().numpy()
+    h = np.fft.rfft(x, axis=1)[:, : N // 2]
+    assert np.abs(h.real).max() < 1e-12 * np.abs(h).max()         # odd: cosine parts vanish
+    if sym & 2:
+        assert np.abs(h[:, 1::2]).max() < 1e-12 * np.abs(h).max()  # L/2-periodic: odd modes vanish
+    xo = oracle.curve_physical(Uo)
+    assert np.abs(x - xo).max() <= 1e-10 * np.abs(xo).max()
+    assert abs(out["J_arc"] - sco["J_arc"]) <= 1e-10 * sco["J_arc"]
+    c.close()

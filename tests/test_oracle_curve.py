@@ -184,3 +184,10 @@ def test_trial_curve_end_rows_and_center():
     th = m * np.pi / (M + 1)
     ref = 0.5 * ((1 + t) * up + (1 - t) * um) + 0.1 * np.sin(th) * v[0] + 0.2 * np.sin(2 * th) * v[1]
     assert np.allclose(X[m], proj(ref), atol=1e-13)
+
+
+def test_single_section_residual_equals_the_curve_residual(small):
+    M, N, L, S, U = small
+    R, _ = oracle.curve_residual(U, L, S, 0.9)
+    for j in (0, 1, 6, M, M + 1):
+        assert np.abs(oracle.section_residual(U, j, L, S, 0.9) - R[j]).max() < 1e-13 * np.abs(R).max()

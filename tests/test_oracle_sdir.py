@@ -125,3 +125,10 @@ def test_two_sum_form_and_transpose_equal_the_matrix(M, S):
         x = rng.standard_normal(M + 2)
         assert np.abs(oracle.dt_apply(x, S) - D @ x).max() < 1e-12 * np.abs(D).max() * np.abs(x).sum()
         assert np.abs(oracle.dtT_apply(x, S) - D.T @ x).max() < 1e-12 * np.abs(D).max() * np.abs(x).sum()
+
+
+def test_single_rows_equal_the_explicit_matrix():
+    M, S = 41, 4.2
+    D = oracle.dt_matrix(M, S)
+    for j in (0, 1, 7, 20, M, M + 1):
+        assert np.abs(oracle.dt_row(M, S, j) - D[j]).max() < 1e-13 * np.abs(D).max()
