@@ -88,6 +88,10 @@ typedef struct {
                             bit 0: every section odd, u(-x) = -u(x) (real parts of u^ zero);
                             bit 1: every section L/2-periodic (odd Fourier modes zero);
                             0 = none.  Values above 3 are invalid. */
+    int32_t s_transform; /* how D_t is applied along s (same result to rounding):
+                            0 auto (FFT when available), 1 dense contraction generated from the
+                            O(N_s) cot table, 2 FFT convolution (N_s <= 2731 FP32 / 1366 FP64) */
+    int32_t reserved;    /* must be 0 */
 } ks_params;
 
 /* Scalars of the state most recently evaluated (cost, gradient or descent). */

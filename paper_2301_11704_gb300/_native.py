@@ -44,6 +44,8 @@ class KSParams(ctypes.Structure):
         ("conv", ctypes.c_int32),
         ("check_ends", ctypes.c_int32),
         ("symmetry", ctypes.c_int32),
+        ("s_transform", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
     ]
 
 

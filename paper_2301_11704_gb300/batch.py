@@ -14,6 +14,7 @@ from ._native import KSParams, KSScalars, check, dptr
 _PREC = {"fp64": _native.KS_FP64, "fp32": _native.KS_FP32}
 _ADJ = {"paper": _native.KS_ADJ_PAPER, "discrete": _native.KS_ADJ_DISCRETE}
 _CONV = {"jarc": _native.KS_CONV_JARC, "j": _native.KS_CONV_J, "jrel": _native.KS_CONV_JREL}
+_STR = {"auto": 0, "dense": 1, "fft": 2}
 
 
 class KSBatch:
@@ -21,7 +22,7 @@ class KSBatch:
     u_plus / u_minus: per-curve physical end sections."""
 
     def __init__(self, specs: Sequence, u_plus, u_minus, *, precision="fp32", adjoint="paper", conv="jrel",
-                 device=None, stream=None):
+                 s_transform="auto", device=None, stream=None):
         self.lib = _native.load()
         self.device = torch.device(device if device is not None else "cuda")
         self.dtype = torch.float64 if precision == "fp64" else torch.float32
@@ -31,7 +32,8 @@ class KSBatch:
         for i, s in enumerate(self.specs):
             arr[i] = KSParams(L=s.L, nx=s.N, ns=s.Ns, S=s.S, s0=getattr(s, "s0", 0.0), lam=1.0, lambda_free=0,
                               dtau=s.dtau, dtau_lambda=0.0, precision=_PREC[precision], adjoint=_ADJ[adjoint],
-                              conv=_CONV[conv], check_ends=0, symmetry=0)
+                              conv=_CONV[conv], check_ends=0, symmetry=0, s_transform=_STR[s_transform],
+                              reserved=0)
         self.params = arr
         nbytes = self.lib.ks_batch_workspace_bytes(self.nb, arr)
         if nbytes == 0:

@@ -76,3 +76,14 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
 
 if __name__ == "__main__":
     print(build(force="--force" in sys.argv, verbose=True))
+
+
+def fft_length(ns: int, fp32: bool) -> int:
+    """FFT length the library uses for the s-contraction of a curve with ns
+    sections (the smallest power of two >= 3 (ns - 1), at least 16), or 0 when
+    the curve is above the single-CTA limit (8192 in FP32, 4096 in FP64) and the
+    dense form is used."""
+    F = 16
+    while F < 3 * (ns - 1):
+        F <<= 1
+    return F if F <= (8192 if fp32 else 4096) else 0

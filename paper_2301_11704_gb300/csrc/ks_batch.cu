@@ -36,6 +36,7 @@ struct ks_batch {
     unsigned char *items_dev = nullptr; // item area
     size_t items_cap = 0;
     std::vector<Group> rows, dts;
+    Group fft{0, 0, 0};                 // (curve, mode) items of the FFT-form curves; key = largest F
     int tile_pref = 0;                  // 0: per-curve default, 32 or 64: forced (autotuner)
     cudaGraphExec_t gexec = nullptr;
     cudaStream_t gstream = nullptr;
@@ -48,13 +49,14 @@ size_t al256(size_t x) { return (x + 255) & ~size_t(255); }
 // Bytes of the batch header: curve array and the largest item lists.
 void header_sizes(int nb, const ks_params *p, size_t *cv_bytes, size_t *items_bytes)
 {
-    size_t rows = 0, tiles = 0;
+    size_t rows = 0, tiles = 0, modes = 0;
     for (int i = 0; i < nb; ++i) {
         rows += (p[i].ns + ks::ROWS_PER_CTA - 1) / ks::ROWS_PER_CTA;
         tiles += (size_t)((p[i].ns + ks::DT_BM - 1) / ks::DT_BM) * ((p[i].nx + 31) / 32);
+        modes += p[i].nx / 2;
     }
     *cv_bytes = al256((size_t)nb * sizeof(ks::CurveDev));
-    *items_bytes = al256(rows * sizeof(int2)) + al256(tiles * sizeof(int4));
+    *items_bytes = al256(rows * sizeof(int2)) + al256(tiles * sizeof(int4)) + al256(modes * sizeof(int2));
 }
 
 ks_status validate_batch(int nb, const ks_params *p)
@@ -77,12 +79,19 @@ ks_status build_items(ks_batch *b)
 {
     std::map<int, std::vector<int2>> rows;
     std::map<int, std::vector<int4>> dts;
+    std::vector<int2> fft;
+    int fmax = 0;
     for (int i = 0; i < b->nb; ++i) {
         ks::CurveDev &c = b->cv[i];
+        for (int k = 0; k < c.row_blocks; ++k) rows[c.nx].push_back(make_int2(i, k));
+        if (c.F > 0) {
+            for (int jm = 0; jm < c.nx / 2; ++jm) fft.push_back(make_int2(i, jm));
+            fmax = std::max(fmax, c.F);
+            continue;
+        }
         const int bn = b->tile_pref ? (c.nx < 64 ? 32 : b->tile_pref) : (c.nx >= 64 ? 64 : 32);
         c.bn = bn;
         c.tiles_c = (c.nx + bn - 1) / bn;
-        for (int k = 0; k < c.row_blocks; ++k) rows[c.nx].push_back(make_int2(i, k));
         for (int tr = 0; tr < c.tiles_r; ++tr)
             for (int tc = 0; tc < c.tiles_c; ++tc) dts[bn].push_back(make_int4(i, tc, tr, 0));
     }
@@ -103,6 +112,10 @@ ks_status build_items(ks_batch *b)
         memcpy(host.data() + o, kv.second.data(), kv.second.size() * sizeof(int4));
         o += kv.second.size() * sizeof(int4);
     }
+    o = al256(o);
+    b->fft = {fmax, o, (int)fft.size()};
+    if (!fft.empty()) memcpy(host.data() + o, fft.data(), fft.size() * sizeof(int2));
+    o += fft.size() * sizeof(int2);
     if (o > itb) return ks::report_error(KS_ENOMEM, "batch item lists exceed their reserved space");
     cudaError_t e = cudaMemcpyAsync(b->items_dev, host.data(), o, cudaMemcpyHostToDevice, b->st);
     if (e == cudaSuccess)
@@ -127,10 +140,16 @@ ks_status launch_step(ks_batch *b, cudaStream_t st)
         if (e == cudaSuccess)
             e = ks::launch_dt_batch(b->prec, g.key, b->cv_dev, (const int4 *)(b->items_dev + g.off), g.count,
                                     ks::GM_UPDATE, b->discrete, 1, st);
+    if (e == cudaSuccess && b->fft.count)
+        e = ks::launch_sconv_batch(b->prec, b->fft.key, b->cv_dev, (const int2 *)(b->items_dev + b->fft.off),
+                                   b->fft.count, ks::GM_UPDATE, b->discrete, 1, st);
     for (const Group &g : b->dts)
         if (e == cudaSuccess)
             e = ks::launch_dt_batch(b->prec, g.key, b->cv_dev, (const int4 *)(b->items_dev + g.off), g.count,
                                     ks::GM_STORE, 0, 1, st);
+    if (e == cudaSuccess && b->fft.count)
+        e = ks::launch_sconv_batch(b->prec, b->fft.key, b->cv_dev, (const int2 *)(b->items_dev + b->fft.off),
+                                   b->fft.count, ks::GM_STORE, 0, 1, st);
     if (e != cudaSuccess) return ks::report_error(KS_ECUDA, "batched step launch: %s", cudaGetErrorString(e));
     return KS_OK;
 }
@@ -214,7 +233,7 @@ size_t ks_batch_workspace_bytes(int32_t nb, const ks_params *params)
     header_sizes(nb, params, &cvb, &itb);
     size_t total = cvb + itb;
     for (int i = 0; i < nb; ++i)
-        total += ks::make_layout(params[i].ns, params[i].nx, params[i].precision == KS_FP32, 0).total;
+        total += ks::make_layout(params[i].ns, params[i].nx, params[i].precision == KS_FP32, 0, 0, params[i].s_transform).total;
     return total;
 }
 
@@ -248,7 +267,7 @@ ks_status ks_batch_create(int32_t nb, const ks_params *params, const double *u_p
     b->cv.resize(nb);
     size_t xoff = 0;
     for (int i = 0; i < nb; ++i) {
-        const ks::Layout l = ks::make_layout(params[i].ns, params[i].nx, b->prec, 0);
+        const ks::Layout l = ks::make_layout(params[i].ns, params[i].nx, b->prec, 0, 0, params[i].s_transform);
         b->off.push_back(o);
         b->cv[i] = ks::bind_layout(&params[i], l, base + o);
         o += l.total;

@@ -82,6 +82,11 @@ ks_status validate(const ks_params *p)
     if (p->conv < KS_CONV_JARC || p->conv > KS_CONV_JREL) return fail(KS_EINVAL, "conv must be a ks_conv value");
     if (p->check_ends != 0 && p->check_ends != 1) return fail(KS_EINVAL, "check_ends must be 0 or 1");
     if (p->symmetry < 0 || p->symmetry > 3) return fail(KS_EINVAL, "symmetry must be in [0, 3]");
+    if (p->s_transform < 0 || p->s_transform > 2) return fail(KS_EINVAL, "s_transform must be 0, 1 or 2");
+    if (p->reserved != 0) return fail(KS_EINVAL, "reserved must be 0");
+    if (p->s_transform == 2 && ks::fft_size(p->ns, p->precision == KS_FP32) == 0)
+        return fail(KS_EINVAL, "s_transform = FFT supports N_s <= %d at this precision",
+                    p->precision == KS_FP32 ? 2731 : 1366);
     return KS_OK;
 }
 
@@ -213,7 +218,7 @@ int32_t ks_version(void) { return (1 << 16) | 0; }
 size_t ks_curve_workspace_bytes(const ks_params *p)
 {
     if (validate(p) != KS_OK) return 0;
-    return ks::make_layout(p->ns, p->nx, p->precision == KS_FP32).total;
+    return ks::make_layout(p->ns, p->nx, p->precision == KS_FP32, 1, 0, p->s_transform).total;
 }
 
 ks_status ks_curve_create(const ks_params *p, const double *u_plus_host, const double *u_minus_host,
@@ -231,7 +236,7 @@ ks_status ks_curve_create(const ks_params *p, const double *u_plus_host, const d
     for (int n = 0; n < p->nx; ++n)
         if (!std::isfinite(u_plus_host[n]) || !std::isfinite(u_minus_host[n]))
             return fail(KS_EINVAL, "u_plus/u_minus contain non-finite values");
-    ks::Layout lay = ks::make_layout(p->ns, p->nx, p->precision == KS_FP32);
+    ks::Layout lay = ks::make_layout(p->ns, p->nx, p->precision == KS_FP32, 1, 0, p->s_transform);
     if (workspace_bytes < lay.total)
         return fail(KS_ENOMEM, "workspace has %zu bytes, %zu needed", workspace_bytes, lay.total);
 

@@ -22,6 +22,19 @@ constexpr int DT_TARGET_CTAS = 256;   // split the contraction until about this 
 constexpr int DT_MIN_KCHUNK = 64;     // but keep at least this many sections per split
 constexpr int DT_MAX_SPLIT = 8;       // the splits of one tile form one thread-block cluster
 
+// FFT form of the s-contraction: one CTA per Fourier mode (a column pair), the
+// convolution of length F (a power of two >= 3 (N_s - 1)) in shared memory.
+constexpr int SC_THREADS = 512;
+constexpr int SC_FMAX_F32 = 8192;
+constexpr int SC_FMAX_F64 = 4096;
+// FFT length for a curve, 0 if above the single-CTA limit of the precision.
+inline int fft_size(int ns, int prec)
+{
+    int F = 16;
+    while (F < 3 * (ns - 1)) F <<= 1;
+    return F <= (prec ? SC_FMAX_F32 : SC_FMAX_F64) ? F : 0;
+}
+
 // Sections handled per CTA by the row (x-direction) kernels: two rows per warp,
 // packed into one complex FFT.
 constexpr int ROWS_WARPS = 4;
@@ -52,6 +65,8 @@ enum GemmMode { GM_STORE = 0, GM_UPDATE = 1, GM_GRAD = 2 };
 
 // Offsets into the caller's workspace.
 struct Layout {
+    size_t off_chat, off_ftw;          // FFT form: kernel spectrum [F], twiddles [F/2] (complex)
+    int F;                             // 0: dense contraction
     size_t off_U, off_D, off_R, off_A, off_G, off_X;
     size_t off_rowsc, off_bpart, off_tile, off_tcnt, off_part;
     size_t off_cot, off_sig, off_tau, off_sw, off_twr, off_w;
@@ -72,6 +87,8 @@ struct CurveDev {
     unsigned *tcnt;        // [tiles] split arrival counters (zero between launches)
     void *part;            // [ksplit][N_s][N] split partial sums (ksplit > 1)
     int bn, tiles_r, tiles_c, ksplit, kchunk, row_blocks;
+    int F;                 // FFT length of the s-contraction (0: dense form)
+    void *chat, *ftw;      // FFT form: kernel spectrum / F and twiddles (complex, storage type)
     void *cot, *sig, *tau, *sw, *twr;
     double *w;
     void *twid, *twid64, *kj, *aj, *prec_imex;
@@ -81,7 +98,7 @@ struct CurveDev {
 
 // allow_split = 0 lays a curve out without split contractions (batched curves
 // get their parallelism from the batch); bn = 0 picks the column tile width.
-Layout make_layout(int ns, int nx, int prec, int allow_split = 1, int bn = 0);
+Layout make_layout(int ns, int nx, int prec, int allow_split = 1, int bn = 0, int s_transform = 0);
 // Pointers of a curve whose workspace starts at `base` (256-byte aligned).
 CurveDev bind_layout(const ks_params *p, const Layout &l, void *base);
 
@@ -121,5 +138,8 @@ cudaError_t launch_rows_batch(int prec, int N, const CurveDev *cv, const int2 *i
 cudaError_t launch_dt_batch(int prec, int bn, const CurveDev *cv, const int4 *items, int nitems, int mode,
                             int discrete, int gate, cudaStream_t st);
 cudaError_t launch_set_limit_batch(const CurveDev *cv, int nb, long long nsteps, double tol, cudaStream_t st);
+// FFT-form s-contraction over (curve, mode) items; smem sized for F_max
+cudaError_t launch_sconv_batch(int prec, int F_max, const CurveDev *cv, const int2 *items, int nitems, int mode,
+                               int discrete, int gate, cudaStream_t st);
 
 }  // namespace ks

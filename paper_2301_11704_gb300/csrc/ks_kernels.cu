@@ -46,10 +46,11 @@ __device__ __forceinline__ cpx<T> cmul(cpx<T> a, cpx<T> b)
 // ---------------------------------------------------------------------------
 static size_t al256(size_t x) { return (x + 255) & ~size_t(255); }
 
-Layout make_layout(int ns, int nx, int prec, int allow_split, int bn)
+Layout make_layout(int ns, int nx, int prec, int allow_split, int bn, int s_transform)
 {
     Layout l{};
     size_t b = prec ? 4 : 8;
+    l.F = (s_transform == 1) ? 0 : fft_size(ns, prec);
     size_t field = al256((size_t)ns * nx * b);
     // tiling and split of the s-contraction
     l.bn = bn ? bn : (nx >= 64 ? 64 : 32);
@@ -57,6 +58,7 @@ Layout make_layout(int ns, int nx, int prec, int allow_split, int bn)
     l.tiles_c = (nx + l.bn - 1) / l.bn;
     int tiles = l.tiles_r * l.tiles_c;
     int tiles_max = l.tiles_r * ((nx + 31) / 32);       // buffers sized for the narrowest tiles
+    if (tiles_max < nx / 2) tiles_max = nx / 2;          // the FFT form has one CTA per mode
     int ks = (allow_split && tiles < DT_TARGET_CTAS) ? DT_TARGET_CTAS / tiles : 1;
     int kmax = ns / DT_MIN_KCHUNK;
     if (ks > kmax) ks = kmax;
@@ -94,6 +96,8 @@ Layout make_layout(int ns, int nx, int prec, int allow_split, int bn)
     l.off_ends = off; off += al256((size_t)2 * nx * 8);
     l.off_pert = off; off += al256((size_t)(nx + MAX_PERT + MAX_PERT * nx) * 8);
     l.off_sc = off; off += al256(sizeof(DevScalars));
+    l.off_chat = off; off += l.F ? al256((size_t)l.F * 2 * b) : 0;
+    l.off_ftw = off; off += l.F ? al256((size_t)l.F * b) : 0;
     l.total = off;
     return l;
 }
@@ -127,6 +131,9 @@ CurveDev bind_layout(const ks_params *p, const Layout &l, void *base)
     d.ksplit = l.ksplit;
     d.kchunk = l.kchunk;
     d.row_blocks = l.row_blocks;
+    d.F = l.F;
+    d.chat = l.F ? (void *)(b + l.off_chat) : nullptr;
+    d.ftw = l.F ? (void *)(b + l.off_ftw) : nullptr;
     d.cot = b + l.off_cot;
     d.sig = b + l.off_sig;
     d.tau = b + l.off_tau;
@@ -967,6 +974,210 @@ __global__ void __launch_bounds__(DT_THREADS) k_dt_batch(const CurveDev *cv, con
 }
 
 // ---------------------------------------------------------------------------
+// s-direction, FFT form
+// ---------------------------------------------------------------------------
+// After the column scaling x'_m = colscale_m x_m, the contraction
+//   y_j = sum_{m=0}^{P} (cot[(j+m) mod 2P] + tsign cot[(j-m) mod 2P]) x'_m,  j = 0..P,
+// is the circular convolution of length 2P of the cot table with the extension
+//   z_0 = (1+tsign) x'_0, z_m = tsign x'_m (0<m<P), z_P = (1+tsign) x'_P, z_{2P-m} = x'_m,
+// and, as only j <= P is needed, equals the zero-padded circular convolution of
+// any length F >= 3P with c_F[t] = cot[t] (0 <= t <= P), c_F[F-t] = cot[2P-t]
+// (0 < t < 2P), 0 elsewhere.  With F a power of two:
+//   y = IFFT_F( FFT_F(c_F) / F * FFT_F(z) )[0..P],
+// two real columns (the real and imaginary parts of one Fourier mode) packed
+// into one complex transform (c_F is real).
+
+// Twiddles e^{-2 pi i t / F} (t < F/2) and the kernel spectrum FFT(c_F)/F, by a
+// direct DFT in FP64 over the 3P nonzero entries with integer-indexed phases.
+template <typename T>
+__global__ void k_setup_fft(CurveDev c)
+{
+    const int F = c.F, P = c.P;
+    cpx<T> *ftw = (cpx<T> *)c.ftw, *chat = (cpx<T> *)c.chat;
+    const T *cot = (const T *)c.cot;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < F; k += gridDim.x * blockDim.x) {
+        if (k < F / 2) {
+            double s, co;
+            sincospi(2.0 * (double)k / (double)F, &s, &co);
+            ftw[k] = {(T)co, (T)(-s)};
+        }
+        // cot values in FP64 again (the stored table is in the storage type)
+        double re = 0.0, im = 0.0;
+        for (int t = -(2 * P - 1); t <= P; ++t) {
+            const int u = (t % (2 * P) + 2 * P) % (2 * P);
+            if (u == 0) continue;
+            double sn, cs;
+            sincospi((double)u / (2.0 * P), &sn, &cs);
+            const double cv = cs / sn;
+            const int idx = t >= 0 ? t : F + t;
+            const long long ph = ((long long)k * idx) % F;
+            double ps, pc;
+            sincospi(2.0 * (double)ph / (double)F, &ps, &pc);
+            re += cv * pc;
+            im -= cv * ps;
+        }
+        chat[k] = {(T)(re / F), (T)(im / F)};
+    }
+    (void)cot;
+}
+
+// Radix-2 Stockham FFT of runtime length F by the whole CTA (natural order in
+// and out); tw[t] = e^{-2 pi i t / F}, t < F/2.  Returns the buffer holding the
+// result.
+template <typename T>
+__device__ cpx<T> *block_fft(cpx<T> *x, cpx<T> *y, const cpx<T> *tw, int F, bool inverse)
+{
+    for (int ns = 1; ns < F; ns <<= 1) {
+        const int step = F / (2 * ns);
+        for (int jj = threadIdx.x; jj < F / 2; jj += blockDim.x) {
+            const int k = jj & (ns - 1);
+            cpx<T> a = x[jj], b = x[jj + F / 2];
+            cpx<T> w = tw[k * step];
+            if (inverse) w.y = -w.y;
+            b = cmul(b, w);
+            const int o = ((jj - k) << 1) + k;
+            y[o] = {a.x + b.x, a.y + b.y};
+            y[o + ns] = {a.x - b.x, a.y - b.y};
+        }
+        __syncthreads();
+        cpx<T> *t = x;
+        x = y;
+        y = t;
+    }
+    return x;
+}
+
+template <typename T>
+__device__ __forceinline__ void sconv_body(const CurveDev &c, int mode, int discrete, int gate, int jm, int nmodes)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int F = c.F, P = c.P, N = c.nx, ns = c.ns;
+    cpx<T> *Z = (cpx<T> *)smem_raw, *Wb = Z + F, *tw = Wb + F;
+    __shared__ double red[SC_THREADS];
+    __shared__ int am_last;
+    DevScalars *sc = c.sc;
+    const int g_active = sc->active;
+    const double lam_d = sc->lambda, dtau_d = sc->dtau;
+    if (gate && !g_active) return;
+
+    const T *X = (const T *)(mode == GM_STORE ? c.U : c.R);
+    const T *colscale = (const T *)(discrete ? c.sw : c.tau);
+    const T *rowscale = (const T *)(discrete ? c.twr : c.sig);
+    const T s = discrete ? T(-1) : T(1);
+    const cpx<T> *ftw = (const cpx<T> *)c.ftw, *chat = (const cpx<T> *)c.chat;
+    const int ca = 2 * jm, cb = 2 * jm + 1;
+    const bool oka = col_allowed(ca, c.sym), okb = col_allowed(cb, c.sym) && jm != 0;
+
+    for (int t = threadIdx.x; t < F / 2; t += blockDim.x) tw[t] = ftw[t];
+    // z of the two columns, packed as za + i zb
+    for (int k = threadIdx.x; k < F; k += blockDim.x) {
+        cpx<T> v = {0, 0};
+        int m = -1;
+        T f = T(1);
+        if (k == 0) { m = 0; f = T(1) + s; }
+        else if (k < P) { m = k; f = s; }
+        else if (k == P) { m = P; f = T(1) + s; }
+        else if (k < 2 * P) { m = 2 * P - k; }
+        if (m >= 0 && f != T(0)) {
+            const T cs = colscale[m] * f;
+            const T *row = X + (size_t)m * N;
+            v.x = oka ? cs * row[ca] : T(0);
+            v.y = okb ? cs * row[cb] : T(0);
+        }
+        Z[k] = v;
+    }
+    __syncthreads();
+    cpx<T> *Y = block_fft<T>(Z, Wb, tw, F, false);
+    cpx<T> *O = (Y == Z) ? Wb : Z;
+    for (int k = threadIdx.x; k < F; k += blockDim.x) Y[k] = cmul(Y[k], chat[k]);
+    __syncthreads();
+    Y = block_fft<T>(Y, O, tw, F, true);
+
+    // epilogue over the sections j = 0..P of the two columns
+    T *Dout = (T *)c.D, *U = (T *)c.U, *G = (T *)c.G;
+    const T *Ah = (const T *)c.A;
+    const T lam = (T)lam_d, dtau = (T)dtau_d;
+    const T pr = ((const T *)c.prec_imex)[jm];
+    const double cw = (jm == 0) ? 1.0 : 2.0;
+    double partsum = 0.0;
+    for (int j = threadIdx.x; j < ns; j += blockDim.x) {
+        const T rs = rowscale[j];
+        const cpx<T> yv = {rs * Y[j].x, rs * Y[j].y};
+        T *drow = Dout + (size_t)j * N;
+        if (mode == GM_STORE) {
+            drow[ca] = oka ? yv.x : T(0);
+            drow[cb] = okb ? yv.y : T(0);
+            continue;
+        }
+        const bool interior = (j > 0 && j < P);
+        T ga = 0, gb = 0;
+        if (interior) {
+            const T *arow = Ah + (size_t)j * N;
+            if (oka) ga = -(arow[ca] + (discrete ? -lam * yv.x : lam * yv.x));
+            if (okb) gb = -(arow[cb] + (discrete ? -lam * yv.y : lam * yv.y));
+            partsum += c.w[j] * cw * ((double)ga * (double)ga + (double)gb * (double)gb);
+        }
+        if (mode == GM_UPDATE) {
+            if (interior) {
+                T *urow = U + (size_t)j * N;
+                urow[ca] += dtau * pr * ga;
+                urow[cb] += dtau * pr * gb;
+            }
+        } else {
+            T *grow = G + (size_t)j * N;
+            grow[ca] = ga;
+            grow[cb] = gb;
+        }
+    }
+    if (mode == GM_STORE) return;
+
+    partsum = block_sum<SC_THREADS>(partsum, red);
+    if (threadIdx.x == 0) c.tile[jm] = partsum;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned prev = atomicAdd(&sc->cnt_gemm, 1u);
+        am_last = (prev == (unsigned)nmodes - 1);
+    }
+    __syncthreads();
+    if (!am_last) return;
+    __threadfence();
+    double t = 0.0;
+    for (int b = threadIdx.x; b < nmodes; b += SC_THREADS) t += __ldcg(c.tile + b);
+    t = block_sum<SC_THREADS>(t, red);
+    if (threadIdx.x == 0) {
+        sc->G2 = c.L * t;
+        if (mode == GM_UPDATE) {
+            sc->step += 1;
+            sc->tau += sc->dtau;
+            sc->lambda = sc->lambda_next;
+        }
+        sc->cnt_gemm = 0;
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(SC_THREADS) k_sconv(CurveDev c, int mode, int discrete, int gate)
+{
+    sconv_body<T>(c, mode, discrete, gate, blockIdx.x, gridDim.x);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(SC_THREADS) k_sconv_batch(const CurveDev *cv, const int2 *items, int mode,
+                                                            int discrete, int gate)
+{
+    const int2 it = items[blockIdx.x];
+    const CurveDev &c = cv[it.x];
+    sconv_body<T>(c, mode, discrete, gate, it.y, c.nx / 2);
+}
+
+template <typename T>
+static size_t sconv_smem(int F)
+{
+    return (size_t)(2 * F + F / 2) * sizeof(cpx<T>);
+}
+
+// ---------------------------------------------------------------------------
 // Launchers
 // ---------------------------------------------------------------------------
 template <typename T>
@@ -1044,6 +1255,11 @@ cudaError_t launch_setup(const CurveDev &c, double dtau, cudaStream_t st)
     int grid = (total + 255) / 256;
     if (c.prec) k_setup<float><<<grid, 256, 0, st>>>(c, dtau);
     else k_setup<double><<<grid, 256, 0, st>>>(c, dtau);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess || c.F == 0) return e;
+    const int g2 = (c.F + 127) / 128;
+    if (c.prec) k_setup_fft<float><<<g2, 128, 0, st>>>(c);
+    else k_setup_fft<double><<<g2, 128, 0, st>>>(c);
     return cudaGetLastError();
 }
 
@@ -1130,8 +1346,37 @@ static cudaError_t launch_dt_t(const CurveDev &c, int mode, int discrete, int ga
     return cudaGetLastError();
 }
 
+template <typename T>
+static cudaError_t launch_sconv_t(const CurveDev &c, int mode, int discrete, int gate, cudaStream_t st)
+{
+    const size_t sm = sconv_smem<T>(c.F);
+    cudaError_t e = set_smem(k_sconv<T>, sm);
+    if (e != cudaSuccess) return e;
+    k_sconv<T><<<c.nx / 2, SC_THREADS, sm, st>>>(c, mode, discrete, gate);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sconv_batch(int prec, int F_max, const CurveDev *cv, const int2 *items, int nitems, int mode,
+                               int discrete, int gate, cudaStream_t st)
+{
+    if (nitems <= 0) return cudaSuccess;
+    cudaError_t e;
+    if (prec) {
+        const size_t sm = sconv_smem<float>(F_max);
+        if ((e = set_smem(k_sconv_batch<float>, sm)) != cudaSuccess) return e;
+        k_sconv_batch<float><<<nitems, SC_THREADS, sm, st>>>(cv, items, mode, discrete, gate);
+    } else {
+        const size_t sm = sconv_smem<double>(F_max);
+        if ((e = set_smem(k_sconv_batch<double>, sm)) != cudaSuccess) return e;
+        k_sconv_batch<double><<<nitems, SC_THREADS, sm, st>>>(cv, items, mode, discrete, gate);
+    }
+    return cudaGetLastError();
+}
+
 cudaError_t launch_dt(const CurveDev &c, int mode, int discrete, int gate, cudaStream_t st)
 {
+    if (c.F > 0) return c.prec ? launch_sconv_t<float>(c, mode, discrete, gate, st)
+                               : launch_sconv_t<double>(c, mode, discrete, gate, st);
     if (c.bn == 64) return c.prec ? launch_dt_t<float, 64>(c, mode, discrete, gate, st)
                                   : launch_dt_t<double, 64>(c, mode, discrete, gate, st);
     return c.prec ? launch_dt_t<float, 32>(c, mode, discrete, gate, st)

@@ -17,6 +17,7 @@ from ._native import KSParams, KSScalars, check, dptr
 _PREC = {"fp64": _native.KS_FP64, "fp32": _native.KS_FP32}
 _ADJ = {"paper": _native.KS_ADJ_PAPER, "discrete": _native.KS_ADJ_DISCRETE}
 _CONV = {"jarc": _native.KS_CONV_JARC, "j": _native.KS_CONV_J, "jrel": _native.KS_CONV_JREL}
+_STR = {"auto": 0, "dense": 1, "fft": 2}
 
 
 def _f64(a, n=None):
@@ -41,7 +42,7 @@ class KSCurve:
     def __init__(self, L: float, nx: int, ns: int, S: float, u_plus, u_minus=None, *, s0: float = 0.0,
                  lam: float = 1.0, lambda_free: bool = False, dtau: float = 0.01, dtau_lambda: float = 0.0,
                  precision: str = "fp64", adjoint: str = "paper", conv: str = "jarc", u_init=None,
-                 check_ends: bool = False, symmetry: int = 0, device=None,
+                 check_ends: bool = False, symmetry: int = 0, s_transform: str = "auto", device=None,
                  stream: Optional[torch.cuda.Stream] = None):
         self.lib = _native.load()
         self.device = torch.device(device if device is not None else "cuda")
@@ -50,7 +51,7 @@ class KSCurve:
         self.params = KSParams(L=L, nx=nx, ns=ns, S=S, s0=s0, lam=lam, lambda_free=int(bool(lambda_free)),
                                dtau=dtau, dtau_lambda=dtau_lambda, precision=_PREC[precision],
                                adjoint=_ADJ[adjoint], conv=_CONV[conv], check_ends=int(bool(check_ends)),
-                               symmetry=int(symmetry))
+                               symmetry=int(symmetry), s_transform=_STR[s_transform], reserved=0)
         nbytes = self.lib.ks_curve_workspace_bytes(ctypes.byref(self.params))
         if nbytes == 0:
             raise _native.KSError(_native.KS_EINVAL, self.lib.ks_last_error().decode())

@@ -29,12 +29,14 @@ def rel_2(a, b):
     return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(np.linalg.norm(np.asarray(b)), 1e-300))
 
 
-def make_pair(spec, precision="fp64", adjoint="paper", lam=1.0, lambda_free=False, dtau_lambda=0.0):
+def make_pair(spec, precision="fp64", adjoint="paper", lam=1.0, lambda_free=False, dtau_lambda=0.0,
+              s_transform="auto"):
     """GPU curve and oracle spectral curve of the same workload trial curve."""
     up, um = end_points(spec)
     amps, vp = perturbation(spec)
     c = KSCurve(spec.L, spec.N, spec.Ns, spec.S, up, um, s0=spec.s0, lam=lam, lambda_free=lambda_free,
-                dtau=spec.dtau, dtau_lambda=dtau_lambda, precision=precision, adjoint=adjoint)
+                dtau=spec.dtau, dtau_lambda=dtau_lambda, precision=precision, adjoint=adjoint,
+                s_transform=s_transform)
     c.init_trial(0.0, None, amps, vp)
     U = oracle.curve_init(spec.M, spec.S, up, um, s0=spec.s0, amps=amps, vp=vp)
     return c, U
@@ -85,11 +87,12 @@ def cfg0():
     return gen.workload(0)[0]
 
 
+@pytest.mark.parametrize("s_transform", ["dense", "fft"])
 @pytest.mark.parametrize("adjoint", ["paper", "discrete"])
-def test_single_evaluation_fp64(cfg0, adjoint):
+def test_single_evaluation_fp64(cfg0, adjoint, s_transform):
     spec = cfg0
     mode = oracle.PAPER if adjoint == "paper" else oracle.DISCRETE
-    c, U = make_pair(spec, adjoint=adjoint)
+    c, U = make_pair(spec, adjoint=adjoint, s_transform=s_transform)
     assert rel_max(c.get_state().cpu().numpy(), oracle.curve_physical(U)) < 1e-13
     R, D, G, sc = oracle_eval(U, spec, mode=mode)
     r = c.residual().cpu().numpy()
@@ -121,12 +124,12 @@ def test_euclidean_gradient_fp64(cfg0):
     c.close()
 
 
-@pytest.mark.parametrize("adjoint", ["paper", "discrete"])
-def test_descent_2000_steps_fp64(cfg0, adjoint):
+@pytest.mark.parametrize("adjoint,s_transform", [("paper", "dense"), ("paper", "fft"), ("discrete", "fft")])
+def test_descent_2000_steps_fp64(cfg0, adjoint, s_transform):
     """cfg 0 end to end: 2000 semi-implicit descent steps from the same trial curve."""
     spec = cfg0
     mode = oracle.PAPER if adjoint == "paper" else oracle.DISCRETE
-    c, U = make_pair(spec, adjoint=adjoint)
+    c, U = make_pair(spec, adjoint=adjoint, s_transform=s_transform)
     Uo, steps_o, sco, _ = oracle.curve_descend(U, spec.L, spec.S, spec.steps, dtau=spec.dtau, mode=mode)
     out = c.descend(spec.steps)
     assert out["steps"] == steps_o == spec.steps
@@ -164,9 +167,10 @@ def test_descent_stops_at_tolerance(cfg0):
     c.close()
 
 
-def test_fp32_matches_fp64_oracle(cfg0):
+@pytest.mark.parametrize("s_transform", ["dense", "fft"])
+def test_fp32_matches_fp64_oracle(cfg0, s_transform):
     spec = cfg0
-    c, U = make_pair(spec, precision="fp32")
+    c, U = make_pair(spec, precision="fp32", s_transform=s_transform)
     R, D, G, sc = oracle_eval(U, spec)
     J2, Ja = c.cost()
     assert abs(np.sqrt(J2) - np.sqrt(sc["J2"])) < TOL32 * np.sqrt(sc["J2"])
@@ -177,11 +181,12 @@ def test_fp32_matches_fp64_oracle(cfg0):
     c.close()
 
 
+@pytest.mark.parametrize("s_transform", ["dense", "fft"])
 @pytest.mark.parametrize("precision,tol", [("fp64", TOL64), ("fp32", TOL32)])
-def test_config1_single_evaluation(precision, tol):
+def test_config1_single_evaluation(precision, tol, s_transform):
     """N_x = 64, N_s = 1024 (the differentiation workload): one evaluation."""
     spec = gen.workload(1)[0]
-    c, U = make_pair(spec, precision=precision)
+    c, U = make_pair(spec, precision=precision, s_transform=s_transform)
     R, D, G, sc = oracle_eval(U, spec)
     J2, Ja = c.cost()
     assert abs(np.sqrt(J2) - np.sqrt(sc["J2"])) < tol * np.sqrt(sc["J2"])
@@ -196,8 +201,9 @@ def test_config1_single_evaluation(precision, tol):
     c.close()
 
 
+@pytest.mark.parametrize("s_transform", ["dense", "fft"])
 @pytest.mark.parametrize("N,Ns", [(8, 3), (8, 16), (16, 37), (32, 33), (64, 65), (128, 31), (256, 20), (32, 129)])
-def test_edge_shapes_fp64(N, Ns):
+def test_edge_shapes_fp64(N, Ns, s_transform):
     """Smallest curve (one interior section), ragged N_s (odd, not a tile multiple),
     every supported N_x, on a random smooth curve; includes 20 descent steps."""
     L, S = 22.0 + N / 16.0, max(0.5, 0.1 * (Ns - 1))
@@ -207,7 +213,7 @@ def test_edge_shapes_fp64(N, Ns):
     for m in range(Ns):
         for j in range(1, min(5, N // 2)):
             X[m] += 0.5 * rng.standard_normal() * np.sin(2 * np.pi * j * x / L + rng.uniform(0, 6.28))
-    c = KSCurve(L, N, Ns, S, X[0], X[-1], u_init=torch.from_numpy(X))
+    c = KSCurve(L, N, Ns, S, X[0], X[-1], u_init=torch.from_numpy(X), s_transform=s_transform)
     U = oracle.curve_spectral(X)
     spec = gen.CurveSpec(0, 0, L, N, Ns, S)
     R, D, G, sc = oracle_eval(U, spec)
@@ -215,7 +221,7 @@ def test_edge_shapes_fp64(N, Ns):
     g, _ = c.gradient()
     assert_grad_close(g.cpu().numpy(), G, U, spec, TOL64)
     Uo, _, sco, _ = oracle.curve_descend(U, L, S, 20, dtau=1e-3)
-    c2 = KSCurve(L, N, Ns, S, X[0], X[-1], u_init=torch.from_numpy(X), dtau=1e-3)
+    c2 = KSCurve(L, N, Ns, S, X[0], X[-1], u_init=torch.from_numpy(X), dtau=1e-3, s_transform=s_transform)
     out = c2.descend(20)
     assert rel_max(c2.get_state().cpu().numpy(), oracle.curve_physical(Uo)) < TOL64
     assert abs(out["J"] - sco["J"]) < TOL64 * max(sco["J"], 1e-300)
@@ -247,8 +253,9 @@ def test_descent_is_deterministic_and_resumable(cfg0):
         x.close()
 
 
+@pytest.mark.parametrize("s_transform", ["dense", "fft"])
 @pytest.mark.parametrize("sym", [1, 3])
-def test_symmetric_subspace_is_held_exactly(sym):
+def test_symmetric_subspace_is_held_exactly(sym, s_transform):
     """Sections restricted to odd (and L/2-periodic) fields keep exactly zero
     coefficients outside the subspace and agree with the oracle's unrestricted
     descent, whose off-subspace coefficients stay at rounding level (Sec. V.B)."""
@@ -256,7 +263,7 @@ def test_symmetric_subspace_is_held_exactly(sym):
     M, S, N, L = 60, 6.1, 32, 22.0
     e2 = replay.equilibrium("E2", 64, L)[::2]          # E2 on the N = 32 grid
     up, um = e2, np.zeros(N)
-    c = KSCurve(L, N, M + 2, S, up, um, symmetry=sym)
+    c = KSCurve(L, N, M + 2, S, up, um, symmetry=sym, s_transform=s_transform)
     U = oracle.curve_init(M, S, up, um)
     Uo, _, sco, _ = oracle.curve_descend(U, L, S, 100, dtau=0.01)
     out = c.descend(100)
