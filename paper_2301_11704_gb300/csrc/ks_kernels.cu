@@ -22,7 +22,9 @@
 // the closed form of the k-sum in eq. rational_diff_matrix, generated per tile
 // from an O(N_s) table.
 #include <cmath>
+#include <map>
 #include <type_traits>
+#include <utility>
 
 #include <cooperative_groups.h>
 
@@ -1186,11 +1188,21 @@ static size_t rows_smem(int N, int bufs)
     return (size_t)(N / 2 + ROWS_WARPS * bufs * N) * sizeof(cpx<T>);
 }
 
+// Opts a kernel into more than 48 KB of dynamic shared memory.  The attribute is
+// set to the largest size requested so far, once per size increase (per device:
+// kernels run on the device current at the call).
 template <typename K>
 static cudaError_t set_smem(K kern, size_t bytes)
 {
     if (bytes <= 48 * 1024) return cudaSuccess;
-    return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    static thread_local std::map<std::pair<int, const void *>, size_t> done;   // (device, kernel) -> bytes
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) dev = -1;
+    size_t &have = done[std::make_pair(dev, (const void *)kern)];
+    if (bytes <= have) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e == cudaSuccess) have = bytes;
+    return e;
 }
 
 static int row_grid(int ns) { return (ns + ROWS_PER_CTA - 1) / ROWS_PER_CTA; }
