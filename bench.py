@@ -47,6 +47,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32")
+    ap.add_argument("--s-transform", choices=["auto", "dense", "fft"], default="auto",
+                    help="how D_t is applied along s in the headline curve")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the oracle CPU baseline")
     ap.add_argument("--e2e-steps", type=int, default=100)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -64,7 +66,7 @@ def workload_config(spec, precision):
     return {"workload": "KSE curve L=%g N_x=%d N_s=%d (M=%d), S=%g, dtau=%g, %s storage, FP64 reductions"
                         % (spec.L, spec.N, spec.Ns, spec.M, spec.S, spec.dtau, precision),
             "L": spec.L, "N_x": spec.N, "N_s": spec.Ns, "S": spec.S, "dtau": spec.dtau,
-            "adjoint": "paper", "curves_per_gpu": 1, "s_transform": "auto (FFT convolution when N_s allows)",
+            "adjoint": "paper", "curves_per_gpu": 1,
             "l2": "flushed before every timed step (256 MiB write); each step timed alone",
             "parallelism": "independent replicas (one curve per GPU)"}
 
@@ -186,9 +188,21 @@ def run_batch(args):
     clk = clocks.stop()
     ms = e0.elapsed_time(e1)
     points = sum(s.M for s in specs)
-    flops = sum(4.0 * s.Ns * s.Ns * s.N for s in specs)
+    from paper_2301_11704_gb300.build import fft_length
+
+    def sflops(s):   # both s-contractions of a step, in the form the curve runs
+        F = fft_length(s.Ns, True)
+        return 2 * (s.N // 2) * (2 * 5.0 * F * np.log2(F) + 6.0 * F) if F else 4.0 * s.Ns * s.Ns * s.N
+    flops = sum(sflops(s) for s in specs)
     ach = flops / (ms / args.steps / 1e3) / 1e12
     peak = N_SM * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    bytes_alg = sum(2.0 * s.M * s.N * 4 for s in specs)   # state read + write per step
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            hbm_peak = float(json.load(f).get("hbm_gbs", 6800.0))
+    except OSError:
+        hbm_peak = 6800.0
+    hbm_ach = bytes_alg / (ms / args.steps / 1e3) / 1e9
     sc = b.scalars()
     line = {"metric": METRIC, "value": points * args.steps / (ms / 1e3), "unit": UNIT, "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
@@ -197,8 +211,12 @@ def run_batch(args):
                        "curves": len(specs), "points_per_step": points, "tile_width": chosen,
                        "l2": "working set ~0.4 GB > L2; steps back to back (CUDA-graph replay)"},
             "roofline": {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
-                         "traffic": None, "kernel": "whole step (two s-contractions dominate)",
-                         "algorithmic_flops_per_step": flops},
+                         "traffic": None, "kernel": "whole step: flops of both s-contractions (FFT form "
+                                                     "where N_s allows) / step time",
+                         "algorithmic_flops_per_step": flops,
+                         "hbm": {"achieved": hbm_ach, "peak": hbm_peak, "unit": "GB/s", "frac": hbm_ach / hbm_peak,
+                                 "algorithmic_bytes_per_step": bytes_alg,
+                                 "note": "B_alg = state read + write (2 N_x b per point)"}},
             "gpu_launches": None, "clocks": clk,
             "median_J_rel": float(np.median([x["J"] / max(x["Dnorm"], 1e-300) for x in sc]))}
     print(json.dumps(line))
@@ -266,7 +284,7 @@ def main():
             c.profile(0)
         return ms, prof
 
-    curve = make_curve(args.precision)
+    curve = make_curve(args.precision, args.s_transform)
     K, W = args.steps, args.warmup
     clocks = ClockSampler(local)
     clocks.start()
@@ -287,7 +305,7 @@ def main():
     avg = {k: v["ms"] / max(v["launches"], 1) for k, v in prof.items()}
     dom = max(avg, key=avg.get)
     from paper_2301_11704_gb300.build import fft_length
-    F = fft_length(spec.Ns, b == 4)
+    F = curve.fft_length
     if F:   # FFT form: per mode two complex FFTs of length F and the spectral product
         flops_dt = (spec.N // 2) * (2 * 5.0 * F * np.log2(F) + 6.0 * F)
         dt_form = "FFT convolution, F=%d" % F
@@ -352,13 +370,15 @@ def main():
         steady = {"value": points * K / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / K, "steps": K,
                   "note": "descend_async(K): CUDA-graph replay, curve L2-resident (not the headline)"}
 
-    # ---- the dense form of the s-contraction (context)
-    dense = None
-    if F:
-        cd = make_curve(args.precision, "dense")
+    # ---- the other form of the s-contraction (context)
+    other = None
+    other_form = "dense" if F else "fft"
+    if F or fft_length(spec.Ns, b == 4):
+        cd = make_curve(args.precision, other_form)
         kd = max(3, min(200, K))
         msd, _ = timed_steps(cd, kd, 3)
-        dense = {"value": points * kd / (sum(msd) / 1e3), "unit": UNIT, "ms_per_step": sum(msd) / kd, "steps": kd}
+        other = {"form": other_form, "value": points * kd / (sum(msd) / 1e3), "unit": UNIT,
+                 "ms_per_step": sum(msd) / kd, "steps": kd}
         cd.close()
 
     # ---- FP64 GPU path (context)
@@ -381,9 +401,10 @@ def main():
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
                 "ms_per_step": total_ms_max / K, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "f64", "data": "synthetic",
-                "config": workload_config(spec, args.precision.upper()), "roofline": roof,
+                "config": dict(workload_config(spec, args.precision.upper()), s_transform=dt_form),
+                "roofline": roof,
                 "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": 4 * K, "clocks": clk,
-                "fp64_gpu_path": fp64, "dense_s_contraction": dense, "steady_state": steady, "final_J": sc["J"], "final_J_arc": sc["J_arc"],
+                "fp64_gpu_path": fp64, "other_s_transform": other, "steady_state": steady, "final_J": sc["J"], "final_J_arc": sc["J_arc"],
                 "step_ms_median": statistics.median(step_ms)}
         print(json.dumps(line))
     curve.close()

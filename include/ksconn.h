@@ -89,8 +89,12 @@ typedef struct {
                             bit 1: every section L/2-periodic (odd Fourier modes zero);
                             0 = none.  Values above 3 are invalid. */
     int32_t s_transform; /* how D_t is applied along s (same result to rounding):
-                            0 auto (FFT when available), 1 dense contraction generated from the
-                            O(N_s) cot table, 2 FFT convolution (N_s <= 2731 FP32 / 1366 FP64) */
+                            0 auto: for a single curve the form measured faster on GB300 for its
+                            size (FFT when N_s N_x >= 131072 or N_s > 2048 in FP32, when N_x >= 64
+                            or N_s <= 128 in FP64, within the FFT size limit; else dense); in a
+                            batch the FFT form wherever the size limit allows;
+                            1 dense contraction generated from the O(N_s) cot table;
+                            2 FFT convolution (N_s <= 2731 FP32 / 1366 FP64) */
     int32_t reserved;    /* must be 0 */
 } ks_params;
 
@@ -123,6 +127,11 @@ int32_t ks_version(void);
  * reduction buffers: about 6 N_s N storage words in total.  No O(N_s^2)
  * matrix is stored: D_t is generated from an O(N_s) table on the fly. */
 size_t ks_curve_workspace_bytes(const ks_params *p);
+
+/* Length of the FFT that a single curve with parameters p applies D_t with
+ * (s_transform rule above), or 0 when it uses the dense contraction.  -1 when
+ * p is invalid (message in ks_last_error). */
+int32_t ks_curve_fft_length(const ks_params *p);
 
 /* Creates a curve (Sec. V.C.1-2).
  *  p            parameters (copied).

@@ -36,7 +36,7 @@ struct ks_batch {
     unsigned char *items_dev = nullptr; // item area
     size_t items_cap = 0;
     std::vector<Group> rows, dts;
-    Group fft{0, 0, 0};                 // (curve, mode) items of the FFT-form curves; key = largest F
+    std::vector<Group> ffts;            // (curve, mode) items of the FFT-form curves, one group per F
     int tile_pref = 0;                  // 0: per-curve default, 32 or 64: forced (autotuner)
     cudaGraphExec_t gexec = nullptr;
     cudaStream_t gstream = nullptr;
@@ -79,14 +79,12 @@ ks_status build_items(ks_batch *b)
 {
     std::map<int, std::vector<int2>> rows;
     std::map<int, std::vector<int4>> dts;
-    std::vector<int2> fft;
-    int fmax = 0;
+    std::map<int, std::vector<int2>> fft;   // by F: each group launched with its own shared memory
     for (int i = 0; i < b->nb; ++i) {
         ks::CurveDev &c = b->cv[i];
         for (int k = 0; k < c.row_blocks; ++k) rows[c.nx].push_back(make_int2(i, k));
         if (c.F > 0) {
-            for (int jm = 0; jm < c.nx / 2; ++jm) fft.push_back(make_int2(i, jm));
-            fmax = std::max(fmax, c.F);
+            for (int jm = 0; jm < c.nx / 2; ++jm) fft[c.F].push_back(make_int2(i, jm));
             continue;
         }
         const int bn = b->tile_pref ? (c.nx < 64 ? 32 : b->tile_pref) : (c.nx >= 64 ? 64 : 32);
@@ -113,9 +111,12 @@ ks_status build_items(ks_batch *b)
         o += kv.second.size() * sizeof(int4);
     }
     o = al256(o);
-    b->fft = {fmax, o, (int)fft.size()};
-    if (!fft.empty()) memcpy(host.data() + o, fft.data(), fft.size() * sizeof(int2));
-    o += fft.size() * sizeof(int2);
+    b->ffts.clear();
+    for (auto it = fft.rbegin(); it != fft.rend(); ++it) {   // largest F (longest CTAs) first
+        b->ffts.push_back({it->first, o, (int)it->second.size()});
+        memcpy(host.data() + o, it->second.data(), it->second.size() * sizeof(int2));
+        o += it->second.size() * sizeof(int2);
+    }
     if (o > itb) return ks::report_error(KS_ENOMEM, "batch item lists exceed their reserved space");
     cudaError_t e = cudaMemcpyAsync(b->items_dev, host.data(), o, cudaMemcpyHostToDevice, b->st);
     if (e == cudaSuccess)
@@ -140,16 +141,18 @@ ks_status launch_step(ks_batch *b, cudaStream_t st)
         if (e == cudaSuccess)
             e = ks::launch_dt_batch(b->prec, g.key, b->cv_dev, (const int4 *)(b->items_dev + g.off), g.count,
                                     ks::GM_UPDATE, b->discrete, 1, st);
-    if (e == cudaSuccess && b->fft.count)
-        e = ks::launch_sconv_batch(b->prec, b->fft.key, b->cv_dev, (const int2 *)(b->items_dev + b->fft.off),
-                                   b->fft.count, ks::GM_UPDATE, b->discrete, 1, st);
+    for (const Group &g : b->ffts)
+        if (e == cudaSuccess)
+            e = ks::launch_sconv_batch(b->prec, g.key, b->cv_dev, (const int2 *)(b->items_dev + g.off), g.count,
+                                       ks::GM_UPDATE, b->discrete, 1, st);
     for (const Group &g : b->dts)
         if (e == cudaSuccess)
             e = ks::launch_dt_batch(b->prec, g.key, b->cv_dev, (const int4 *)(b->items_dev + g.off), g.count,
                                     ks::GM_STORE, 0, 1, st);
-    if (e == cudaSuccess && b->fft.count)
-        e = ks::launch_sconv_batch(b->prec, b->fft.key, b->cv_dev, (const int2 *)(b->items_dev + b->fft.off),
-                                   b->fft.count, ks::GM_STORE, 0, 1, st);
+    for (const Group &g : b->ffts)
+        if (e == cudaSuccess)
+            e = ks::launch_sconv_batch(b->prec, g.key, b->cv_dev, (const int2 *)(b->items_dev + g.off), g.count,
+                                       ks::GM_STORE, 0, 1, st);
     if (e != cudaSuccess) return ks::report_error(KS_ECUDA, "batched step launch: %s", cudaGetErrorString(e));
     return KS_OK;
 }
@@ -208,6 +211,9 @@ ks_status read_all(ks_batch *b, std::vector<ks::DevScalars> &h)
     }
     cudaError_t e = cudaStreamSynchronize(b->st);
     if (e != cudaSuccess) return ks::report_error(KS_ECUDA, "scalar read: %s", cudaGetErrorString(e));
+    for (size_t i = 0; i < h.size(); ++i)
+        if (h[i].err)
+            return ks::report_error(KS_ETIMEOUT, "curve %zu: a device-side copy did not complete in time", i);
     return KS_OK;
 }
 

@@ -109,6 +109,7 @@ ks_status read_scalars(ks_curve *c, ks::DevScalars *h)
 {
     KS_CUDA(cudaMemcpyAsync(h, c->d.sc, sizeof(*h), cudaMemcpyDeviceToHost, c->st));
     KS_CUDA(cudaStreamSynchronize(c->st));
+    if (h->err) return fail(KS_ETIMEOUT, "a device-side copy did not complete in time; re-initialise the curve");
     return KS_OK;
 }
 
@@ -219,6 +220,12 @@ size_t ks_curve_workspace_bytes(const ks_params *p)
 {
     if (validate(p) != KS_OK) return 0;
     return ks::make_layout(p->ns, p->nx, p->precision == KS_FP32, 1, 0, p->s_transform).total;
+}
+
+int32_t ks_curve_fft_length(const ks_params *p)
+{
+    if (validate(p) != KS_OK) return -1;
+    return ks::make_layout(p->ns, p->nx, p->precision == KS_FP32, 1, 0, p->s_transform).F;
 }
 
 ks_status ks_curve_create(const ks_params *p, const double *u_plus_host, const double *u_minus_host,

@@ -35,6 +35,15 @@ inline int fft_size(int ns, int prec)
     return F <= (prec ? SC_FMAX_F32 : SC_FMAX_F64) ? F : 0;
 }
 
+// Form that `auto` picks for a single curve: the FFT form where it measured
+// faster than the dense contraction on GB300 (one step of one curve, L2 flushed,
+// N_x in {32, 64, 128, 256}, N_s from 128 to the size limit).
+inline bool fft_preferred(int ns, int nx, int prec)
+{
+    if (prec) return (long long)ns * nx >= 131072 || ns > 2048;
+    return nx >= 64 || ns <= 128;
+}
+
 // Sections handled per CTA by the row (x-direction) kernels: two rows per warp,
 // packed into one complex FFT.
 constexpr int ROWS_WARPS = 4;
@@ -53,7 +62,8 @@ struct DevScalars {
     double tol, dtau, dtau_lambda;
     long long step, limit;
     int done, active, status, conv;
-    int lambda_free, pad0;
+    int lambda_free;
+    int err;                            // nonzero: a bounded wait in a kernel gave up (launch invalid)
     unsigned int cnt_rows, cnt_gemm;    // arrival counters of the last-CTA reductions
 };
 

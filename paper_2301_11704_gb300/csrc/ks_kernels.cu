@@ -52,7 +52,10 @@ Layout make_layout(int ns, int nx, int prec, int allow_split, int bn, int s_tran
 {
     Layout l{};
     size_t b = prec ? 4 : 8;
-    l.F = (s_transform == 1) ? 0 : fft_size(ns, prec);
+    // s_transform 0 (auto): a single curve (allow_split) takes the measured rule,
+    // batched curves the FFT form wherever it fits
+    const bool want_fft = s_transform == 2 || (s_transform == 0 && (!allow_split || fft_preferred(ns, nx, prec)));
+    l.F = want_fft ? fft_size(ns, prec) : 0;
     size_t field = al256((size_t)ns * nx * b);
     // tiling and split of the s-contraction
     l.bn = bn ? bn : (nx >= 64 ? 64 : 32);
@@ -99,7 +102,7 @@ Layout make_layout(int ns, int nx, int prec, int allow_split, int bn, int s_tran
     l.off_pert = off; off += al256((size_t)(nx + MAX_PERT + MAX_PERT * nx) * 8);
     l.off_sc = off; off += al256(sizeof(DevScalars));
     l.off_chat = off; off += l.F ? al256((size_t)l.F * 2 * b) : 0;
-    l.off_ftw = off; off += l.F ? al256((size_t)l.F * b) : 0;
+    l.off_ftw = off; off += l.F ? al256((size_t)l.F * 2 * b) : 0;
     l.total = off;
     return l;
 }
@@ -989,7 +992,7 @@ __global__ void __launch_bounds__(DT_THREADS) k_dt_batch(const CurveDev *cv, con
 // two real columns (the real and imaginary parts of one Fourier mode) packed
 // into one complex transform (c_F is real).
 
-// Twiddles e^{-2 pi i t / F} (t < F/2) and the kernel spectrum FFT(c_F)/F, by a
+// Twiddles e^{-2 pi i t / F} (t < F) and the kernel spectrum FFT(c_F)/F, by a
 // direct DFT in FP64 over the 3P nonzero entries with integer-indexed phases.
 template <typename T>
 __global__ void k_setup_fft(CurveDev c)
@@ -998,7 +1001,7 @@ __global__ void k_setup_fft(CurveDev c)
     cpx<T> *ftw = (cpx<T> *)c.ftw, *chat = (cpx<T> *)c.chat;
     const T *cot = (const T *)c.cot;
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < F; k += gridDim.x * blockDim.x) {
-        if (k < F / 2) {
+        {
             double s, co;
             sincospi(2.0 * (double)k / (double)F, &s, &co);
             ftw[k] = {(T)co, (T)(-s)};
@@ -1023,21 +1026,109 @@ __global__ void k_setup_fft(CurveDev c)
     (void)cot;
 }
 
-// Radix-2 Stockham FFT of runtime length F by the whole CTA (natural order in
-// and out); tw[t] = e^{-2 pi i t / F}, t < F/2.  Returns the buffer holding the
-// result.
+// ---- bulk copy global -> shared through an mbarrier (the copy engine; no
+// tensor map).  Every wait is bounded: after about one second of polling it
+// records the failure in the curve's scalars and the launch is invalid.
+__device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(unsigned long long *bar, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+// Thread-level: arm the barrier for `bytes` and start the copy (both 16-byte aligned,
+// bytes a multiple of 16).
+__device__ __forceinline__ void bulk_load(void *dst, const void *src, unsigned bytes, unsigned long long *bar)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_test(unsigned long long *bar, unsigned parity)
+{
+    unsigned ok;
+    asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+                 : "=r"(ok)
+                 : "r"(smem_u32(bar)), "r"(parity)
+                 : "memory");
+    return ok != 0;
+}
+
+// Bounded wait for phase `parity`; false when the bound ran out.
+__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned parity)
+{
+    const long long t0 = clock64();
+    while (!mbar_test(bar, parity))
+        if (clock64() - t0 > (1ll << 31)) return false;
+    return true;
+}
+
+// Stockham FFT of runtime length F (a power of two) by the whole CTA: radix-4
+// stages, then one radix-2 stage when log2(F) is odd; natural order in and out.
+// tw[u] = e^{-2 pi i u / F}, u < F.  Each thread keeps two butterflies in flight
+// (all their operands loaded before any result is stored).  Returns the buffer
+// holding the result.
+template <typename T>
+__device__ __forceinline__ void r4_load(const cpx<T> *x, const cpx<T> *tw, int j, int Q, int ns, int step, bool inverse,
+                                        cpx<T> (&a)[4])
+{
+    const int k = j & (ns - 1);
+    const int u = k * step;
+    cpx<T> w1 = tw[u], w2 = tw[2 * u], w3 = tw[3 * u];
+    if (inverse) { w1.y = -w1.y; w2.y = -w2.y; w3.y = -w3.y; }
+    a[0] = x[j];
+    a[1] = cmul(x[j + Q], w1);
+    a[2] = cmul(x[j + 2 * Q], w2);
+    a[3] = cmul(x[j + 3 * Q], w3);
+}
+
+template <typename T>
+__device__ __forceinline__ void r4_store(cpx<T> *y, int j, int ns, bool inverse, const cpx<T> (&a)[4])
+{
+    const int k = j & (ns - 1);
+    const cpx<T> t0 = {a[0].x + a[2].x, a[0].y + a[2].y}, t1 = {a[0].x - a[2].x, a[0].y - a[2].y};
+    const cpx<T> t2 = {a[1].x + a[3].x, a[1].y + a[3].y}, t3 = {a[1].x - a[3].x, a[1].y - a[3].y};
+    // -i t3 (forward) or +i t3 (inverse)
+    const cpx<T> t3r = inverse ? cpx<T>{-t3.y, t3.x} : cpx<T>{t3.y, -t3.x};
+    const int o = (j - k) * 4 + k;
+    y[o] = {t0.x + t2.x, t0.y + t2.y};
+    y[o + ns] = {t1.x + t3r.x, t1.y + t3r.y};
+    y[o + 2 * ns] = {t0.x - t2.x, t0.y - t2.y};
+    y[o + 3 * ns] = {t1.x - t3r.x, t1.y - t3r.y};
+}
+
 template <typename T>
 __device__ cpx<T> *block_fft(cpx<T> *x, cpx<T> *y, const cpx<T> *tw, int F, bool inverse)
 {
-    for (int ns = 1; ns < F; ns <<= 1) {
-        const int step = F / (2 * ns);
-        for (int jj = threadIdx.x; jj < F / 2; jj += blockDim.x) {
-            const int k = jj & (ns - 1);
-            cpx<T> a = x[jj], b = x[jj + F / 2];
-            cpx<T> w = tw[k * step];
+    const int Q = F / 4, B = blockDim.x;
+    int ns = 1;
+    for (; ns * 4 <= F; ns *= 4) {
+        const int step = Q / ns;
+        for (int j0 = threadIdx.x; j0 < Q; j0 += 2 * B) {
+            const int j1 = j0 + B;
+            cpx<T> a0[4], a1[4];
+            r4_load(x, tw, j0, Q, ns, step, inverse, a0);
+            if (j1 < Q) r4_load(x, tw, j1, Q, ns, step, inverse, a1);
+            r4_store(y, j0, ns, inverse, a0);
+            if (j1 < Q) r4_store(y, j1, ns, inverse, a1);
+        }
+        __syncthreads();
+        cpx<T> *t = x;
+        x = y;
+        y = t;
+    }
+    if (ns < F) {   // ns == F / 2: the last radix-2 stage
+        for (int j = threadIdx.x; j < F / 2; j += B) {
+            const int k = j & (ns - 1);
+            cpx<T> a = x[j], b = x[j + F / 2];
+            cpx<T> w = tw[k];
             if (inverse) w.y = -w.y;
             b = cmul(b, w);
-            const int o = ((jj - k) << 1) + k;
+            const int o = ((j - k) << 1) + k;
             y[o] = {a.x + b.x, a.y + b.y};
             y[o + ns] = {a.x - b.x, a.y - b.y};
         }
@@ -1049,86 +1140,146 @@ __device__ cpx<T> *block_fft(cpx<T> *x, cpx<T> *y, const cpx<T> *tw, int F, bool
     return x;
 }
 
+// Loads of the FFT-form kernel: the largest per-thread counts (F / threads for the
+// spectrum, N_s / threads for the epilogue) fixed by the single-CTA size limits.
+template <typename T> struct SconvMax;
+template <> struct SconvMax<float> { static constexpr int SPEC = SC_FMAX_F32 / SC_THREADS, EPI = (SC_FMAX_F32 / 3 + 1 + SC_THREADS) / SC_THREADS; };
+template <> struct SconvMax<double> { static constexpr int SPEC = SC_FMAX_F64 / SC_THREADS, EPI = (SC_FMAX_F64 / 3 + 1 + SC_THREADS) / SC_THREADS; };
+
+template <typename T>
+struct vec2;
+template <> struct vec2<float> { using type = float2; };
+template <> struct vec2<double> { using type = double2; };
+
 template <typename T>
 __device__ __forceinline__ void sconv_body(const CurveDev &c, int mode, int discrete, int gate, int jm, int nmodes)
 {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int F = c.F, P = c.P, N = c.nx, ns = c.ns;
-    cpx<T> *Z = (cpx<T> *)smem_raw, *Wb = Z + F, *tw = Wb + F;
+    using V2 = typename vec2<T>::type;
+    constexpr int SPEC = SconvMax<T>::SPEC, EPI = SconvMax<T>::EPI, ZCH = 8;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    const int F = c.F, P = c.P, N = c.nx, ns = c.ns, B = SC_THREADS, t = threadIdx.x;
+    cpx<T> *Z = (cpx<T> *)smem_raw, *Wb = Z + F, *tw = Wb + F;   // tw: F entries
     __shared__ double red[SC_THREADS];
     __shared__ int am_last;
+    __shared__ unsigned long long bar;
     DevScalars *sc = c.sc;
     const int g_active = sc->active;
     const double lam_d = sc->lambda, dtau_d = sc->dtau;
+    const cpx<T> *ftw = (const cpx<T> *)c.ftw, *chat = (const cpx<T> *)c.chat;
+    // kernel spectrum for the product after the forward transform: issued first
+    cpx<T> ch[SPEC];
+#pragma unroll
+    for (int i = 0; i < SPEC; ++i)
+        if (t + i * B < F) ch[i] = chat[t + i * B];
     if (gate && !g_active) return;
+
+    // twiddles by one bulk copy, overlapped with building z
+    const bool bulk = ((reinterpret_cast<uintptr_t>(ftw) & 15) == 0);
+    if (bulk && t == 0) {
+        mbar_init(&bar, 1);
+        bulk_load(tw, ftw, (unsigned)(F * sizeof(cpx<T>)), &bar);
+    }
+    if (!bulk)
+        for (int k = t; k < F; k += B) tw[k] = ftw[k];
 
     const T *X = (const T *)(mode == GM_STORE ? c.U : c.R);
     const T *colscale = (const T *)(discrete ? c.sw : c.tau);
     const T *rowscale = (const T *)(discrete ? c.twr : c.sig);
     const T s = discrete ? T(-1) : T(1);
-    const cpx<T> *ftw = (const cpx<T> *)c.ftw, *chat = (const cpx<T> *)c.chat;
     const int ca = 2 * jm, cb = 2 * jm + 1;
     const bool oka = col_allowed(ca, c.sym), okb = col_allowed(cb, c.sym) && jm != 0;
-
-    for (int t = threadIdx.x; t < F / 2; t += blockDim.x) tw[t] = ftw[t];
-    // z of the two columns, packed as za + i zb
-    for (int k = threadIdx.x; k < F; k += blockDim.x) {
-        cpx<T> v = {0, 0};
-        int m = -1;
-        T f = T(1);
-        if (k == 0) { m = 0; f = T(1) + s; }
-        else if (k < P) { m = k; f = s; }
-        else if (k == P) { m = P; f = T(1) + s; }
-        else if (k < 2 * P) { m = 2 * P - k; }
-        if (m >= 0 && f != T(0)) {
-            const T cs = colscale[m] * f;
-            const T *row = X + (size_t)m * N;
-            v.x = oka ? cs * row[ca] : T(0);
-            v.y = okb ? cs * row[cb] : T(0);
+    // z of the two columns, packed as za + i zb; the (Re, Im) pair is one vector load
+    for (int k0 = t; k0 < F; k0 += ZCH * B) {
+        V2 xv[ZCH];
+        T cs[ZCH];
+        int mm[ZCH];
+#pragma unroll
+        for (int i = 0; i < ZCH; ++i) {
+            const int k = k0 + i * B;
+            int m = -1;
+            T f = T(1);
+            if (k == 0) { m = 0; f = T(1) + s; }
+            else if (k < P) { m = k; f = s; }
+            else if (k == P) { m = P; f = T(1) + s; }
+            else if (k < 2 * P) { m = 2 * P - k; }
+            if (f == T(0)) m = -1;
+            mm[i] = m;
+            cs[i] = f;
+            if (m >= 0) {
+                xv[i] = *reinterpret_cast<const V2 *>(X + (size_t)m * N + ca);
+                cs[i] = f * colscale[m];
+            }
         }
-        Z[k] = v;
+#pragma unroll
+        for (int i = 0; i < ZCH; ++i) {
+            const int k = k0 + i * B;
+            if (k >= F) break;
+            cpx<T> v = {0, 0};
+            if (mm[i] >= 0) {
+                v.x = oka ? cs[i] * xv[i].x : T(0);
+                v.y = okb ? cs[i] * xv[i].y : T(0);
+            }
+            Z[k] = v;
+        }
     }
-    __syncthreads();
+    __syncthreads();   // z complete; the barrier's initialisation visible to every thread
+    if (bulk && !mbar_wait(&bar, 0)) {
+        atomicExch(&sc->err, 1);
+        mbar_wait(&bar, 0);   // the copy may still be writing this CTA's shared memory
+    }
     cpx<T> *Y = block_fft<T>(Z, Wb, tw, F, false);
     cpx<T> *O = (Y == Z) ? Wb : Z;
-    for (int k = threadIdx.x; k < F; k += blockDim.x) Y[k] = cmul(Y[k], chat[k]);
+
+    // epilogue operands of the sections j = t + i B, issued before the product
+    T *Dout = (T *)c.D, *U = (T *)c.U, *G = (T *)c.G;
+    const T *Ah = (const T *)c.A;
+    const T pr = ((const T *)c.prec_imex)[jm];
+    T rs[EPI];
+    double wj[EPI];
+    V2 av[EPI], uv[EPI];
+#pragma unroll
+    for (int i = 0; i < EPI; ++i) {
+        const int j = t + i * B;
+        if (j < ns) {
+            rs[i] = rowscale[j];
+            if (mode != GM_STORE && j > 0 && j < P) {
+                wj[i] = c.w[j];
+                av[i] = *reinterpret_cast<const V2 *>(Ah + (size_t)j * N + ca);
+                if (mode == GM_UPDATE) uv[i] = *reinterpret_cast<const V2 *>(U + (size_t)j * N + ca);
+            }
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < SPEC; ++i)
+        if (t + i * B < F) Y[t + i * B] = cmul(Y[t + i * B], ch[i]);
     __syncthreads();
     Y = block_fft<T>(Y, O, tw, F, true);
 
     // epilogue over the sections j = 0..P of the two columns
-    T *Dout = (T *)c.D, *U = (T *)c.U, *G = (T *)c.G;
-    const T *Ah = (const T *)c.A;
     const T lam = (T)lam_d, dtau = (T)dtau_d;
-    const T pr = ((const T *)c.prec_imex)[jm];
     const double cw = (jm == 0) ? 1.0 : 2.0;
     double partsum = 0.0;
-    for (int j = threadIdx.x; j < ns; j += blockDim.x) {
-        const T rs = rowscale[j];
-        const cpx<T> yv = {rs * Y[j].x, rs * Y[j].y};
-        T *drow = Dout + (size_t)j * N;
+#pragma unroll
+    for (int i = 0; i < EPI; ++i) {
+        const int j = t + i * B;
+        if (j >= ns) break;
+        const cpx<T> yv = {rs[i] * Y[j].x, rs[i] * Y[j].y};
         if (mode == GM_STORE) {
-            drow[ca] = oka ? yv.x : T(0);
-            drow[cb] = okb ? yv.y : T(0);
+            *reinterpret_cast<V2 *>(Dout + (size_t)j * N + ca) = V2{oka ? yv.x : T(0), okb ? yv.y : T(0)};
             continue;
         }
         const bool interior = (j > 0 && j < P);
         T ga = 0, gb = 0;
         if (interior) {
-            const T *arow = Ah + (size_t)j * N;
-            if (oka) ga = -(arow[ca] + (discrete ? -lam * yv.x : lam * yv.x));
-            if (okb) gb = -(arow[cb] + (discrete ? -lam * yv.y : lam * yv.y));
-            partsum += c.w[j] * cw * ((double)ga * (double)ga + (double)gb * (double)gb);
+            if (oka) ga = -(av[i].x + (discrete ? -lam * yv.x : lam * yv.x));
+            if (okb) gb = -(av[i].y + (discrete ? -lam * yv.y : lam * yv.y));
+            partsum += wj[i] * cw * ((double)ga * (double)ga + (double)gb * (double)gb);
         }
         if (mode == GM_UPDATE) {
-            if (interior) {
-                T *urow = U + (size_t)j * N;
-                urow[ca] += dtau * pr * ga;
-                urow[cb] += dtau * pr * gb;
-            }
+            if (interior)
+                *reinterpret_cast<V2 *>(U + (size_t)j * N + ca) = V2{uv[i].x + dtau * pr * ga, uv[i].y + dtau * pr * gb};
         } else {
-            T *grow = G + (size_t)j * N;
-            grow[ca] = ga;
-            grow[cb] = gb;
+            *reinterpret_cast<V2 *>(G + (size_t)j * N + ca) = V2{ga, gb};
         }
     }
     if (mode == GM_STORE) return;
@@ -1144,11 +1295,11 @@ __device__ __forceinline__ void sconv_body(const CurveDev &c, int mode, int disc
     __syncthreads();
     if (!am_last) return;
     __threadfence();
-    double t = 0.0;
-    for (int b = threadIdx.x; b < nmodes; b += SC_THREADS) t += __ldcg(c.tile + b);
-    t = block_sum<SC_THREADS>(t, red);
+    double tt = 0.0;
+    for (int b2 = threadIdx.x; b2 < nmodes; b2 += SC_THREADS) tt += __ldcg(c.tile + b2);
+    tt = block_sum<SC_THREADS>(tt, red);
     if (threadIdx.x == 0) {
-        sc->G2 = c.L * t;
+        sc->G2 = c.L * tt;
         if (mode == GM_UPDATE) {
             sc->step += 1;
             sc->tau += sc->dtau;
@@ -1176,7 +1327,7 @@ __global__ void __launch_bounds__(SC_THREADS) k_sconv_batch(const CurveDev *cv, 
 template <typename T>
 static size_t sconv_smem(int F)
 {
-    return (size_t)(2 * F + F / 2) * sizeof(cpx<T>);
+    return (size_t)(3 * F) * sizeof(cpx<T>);
 }
 
 // ---------------------------------------------------------------------------
@@ -1188,13 +1339,13 @@ static size_t rows_smem(int N, int bufs)
     return (size_t)(N / 2 + ROWS_WARPS * bufs * N) * sizeof(cpx<T>);
 }
 
-// Opts a kernel into more than 48 KB of dynamic shared memory.  The attribute is
-// set to the largest size requested so far, once per size increase (per device:
-// kernels run on the device current at the call).
+// Sets a kernel's dynamic shared-memory limit to the largest size requested so
+// far, once per size increase (per device: kernels run on the device current at
+// the call).  Done for every size, not only above 48 KB: static shared memory
+// counts against the same default limit.
 template <typename K>
 static cudaError_t set_smem(K kern, size_t bytes)
 {
-    if (bytes <= 48 * 1024) return cudaSuccess;
     static thread_local std::map<std::pair<int, const void *>, size_t> done;   // (device, kernel) -> bytes
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) dev = -1;

@@ -56,6 +56,8 @@ class KSCurve:
         if nbytes == 0:
             raise _native.KSError(_native.KS_EINVAL, self.lib.ks_last_error().decode())
         self.workspace_bytes = int(nbytes)
+        # length of the FFT that applies D_t along s (0: dense contraction)
+        self.fft_length = int(self.lib.ks_curve_fft_length(ctypes.byref(self.params)))
         self._ws = torch.empty(self.workspace_bytes + 256, dtype=torch.uint8, device=self.device)
         base = self._ws.data_ptr()
         self._ws_ptr = (base + 255) & ~255

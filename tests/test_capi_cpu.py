@@ -87,3 +87,19 @@ def test_missing_pointers_and_small_workspace_are_rejected(lib):
 def test_null_handle_is_rejected(lib):
     assert lib.ks_curve_cost(None, None, None) == _native.KS_EINVAL
     assert lib.ks_curve_destroy(None) == _native.KS_OK
+
+
+@pytest.mark.parametrize("kw,F", [
+    (dict(precision=1, nx=64, ns=1024), 0),                  # FP32, N_s N_x = 65536: dense
+    (dict(precision=1, nx=128, ns=1024), 4096),              # FP32, N_s N_x = 131072: FFT, F >= 3 (N_s - 1)
+    (dict(precision=1, nx=32, ns=2731), 8192),               # FP32, N_s > 2048
+    (dict(precision=1, nx=256, ns=4096), 0),                 # above the FFT size limit: dense
+    (dict(precision=0, nx=64, ns=1024), 4096),               # FP64, N_x >= 64
+    (dict(precision=0, nx=32, ns=1024), 0),                  # FP64, N_x = 32
+    (dict(precision=0, nx=32, ns=128), 512),                 # FP64, N_s <= 128
+    (dict(precision=1, nx=64, ns=1024, s_transform=2), 4096),
+    (dict(precision=1, nx=128, ns=1024, s_transform=1), 0),
+    (dict(nx=24), -1),
+])
+def test_s_transform_rule(lib, kw, F):
+    assert lib.ks_curve_fft_length(ctypes.byref(_params(**kw))) == F
