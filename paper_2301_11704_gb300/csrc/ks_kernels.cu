@@ -43,6 +43,17 @@ __device__ __forceinline__ cpx<T> cmul(cpx<T> a, cpx<T> b)
     return {a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x};
 }
 
+// Programmatic dependent launch.  The step kernels are launched so that a kernel
+// is set up while its predecessor in the stream drains (its CTAs start as the
+// predecessor's CTAs exit, before the predecessor's completion is flushed):
+// before pdl_wait() a kernel reads only the tables written at curve set-up
+// (complete long before); pdl_wait() returns once the predecessor has completed
+// and its writes are visible; every gate and every field is read after it, and
+// no CTA leaves before it.  No kernel triggers its successor early: successor
+// CTAs parked on the SMs during a whole kernel slowed graph replay (measured).
+// A no-op for a kernel launched without the attribute.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 // ---------------------------------------------------------------------------
 // Layout of the workspace
 // ---------------------------------------------------------------------------
@@ -515,15 +526,24 @@ __device__ __forceinline__ void rows_body(const CurveDev &c, int mode, int blk, 
     const int m0 = (blk * ROWS_WARPS + warp) * 2, m1 = m0 + 1;
     const bool has0 = m0 < ns, has1 = m1 < ns;
 
-    // Every independent global load is issued before the first use (one memory
-    // round trip): the gate, lambda, the twiddles, both sections of u and D_t u,
-    // and the Fourier tables of the modes this lane owns.
-    const int g_done = sc->done;
-    const long long g_step = sc->step, g_limit = sc->limit;
-    const double lamd0 = sc->lambda;
+    // Every independent global load is issued before the first use: the
+    // twiddles and the Fourier tables of the modes this lane owns (before the
+    // predecessor has finished), then the gate, lambda and both sections of u and
+    // D_t u (one memory round trip).
     const cpx<T> twv = ((int)threadIdx.x < H) ? ((const cpx<T> *)c.twid)[threadIdx.x] : cpx<T>{0, 0};
     cpx<T> ua[MPL], ub[MPL], ra[MPL], rb[MPL], dva[MPL], dvb[MPL];
     T kv[MPL], av[MPL];
+#pragma unroll
+    for (int i = 0; i < MPL; ++i) {
+        const int j = lane + 32 * i;
+        kv[i] = (j < H) ? kj[j] : T(0);
+        av[i] = (j < H) ? aj[j] : T(0);
+    }
+    for (int t = threadIdx.x + blockDim.x; t < H; t += blockDim.x) tw[t] = ((const cpx<T> *)c.twid)[t];
+    pdl_wait();
+    const int g_done = sc->done;
+    const long long g_step = sc->step, g_limit = sc->limit;
+    const double lamd0 = sc->lambda;
 #pragma unroll
     for (int i = 0; i < MPL; ++i) {
         const int j = lane + 32 * i;
@@ -532,10 +552,7 @@ __device__ __forceinline__ void rows_body(const CurveDev &c, int mode, int blk, 
         ub[i] = (ok && has1) ? ld2(U, m1, N, j) : cpx<T>{0, 0};
         dva[i] = (ok && has0) ? ld2(D, m0, N, j) : cpx<T>{0, 0};
         dvb[i] = (ok && has1) ? ld2(D, m1, N, j) : cpx<T>{0, 0};
-        kv[i] = ok ? kj[j] : T(0);
-        av[i] = ok ? aj[j] : T(0);
     }
-    for (int t = threadIdx.x + blockDim.x; t < H; t += blockDim.x) tw[t] = ((const cpx<T> *)c.twid)[t];
 
     if (mode == ROWS_STEP && (g_done || g_step >= g_limit)) {
         if (blk == 0 && threadIdx.x == 0) sc->active = 0;
@@ -775,6 +792,7 @@ __device__ __forceinline__ void dt_body(const CurveDev &c, int mode, int discret
     __shared__ double red[DT_THREADS];
     __shared__ int am_last;
     DevScalars *sc = c.sc;
+    pdl_wait();
     const int g_active = sc->active;
     const double lam_d = sc->lambda, dtau_d = sc->dtau;
 
@@ -1156,24 +1174,20 @@ __device__ __forceinline__ void sconv_body(const CurveDev &c, int mode, int disc
 {
     using V2 = typename vec2<T>::type;
     constexpr int SPEC = SconvMax<T>::SPEC, EPI = SconvMax<T>::EPI, ZCH = 8;
-    extern __shared__ __align__(128) unsigned char smem_raw[];
+    extern __shared__ __align__(16) unsigned char smem_raw[];
     const int F = c.F, P = c.P, N = c.nx, ns = c.ns, B = SC_THREADS, t = threadIdx.x;
     cpx<T> *Z = (cpx<T> *)smem_raw, *Wb = Z + F, *tw = Wb + F;   // tw: F entries
     __shared__ double red[SC_THREADS];
     __shared__ int am_last;
     __shared__ unsigned long long bar;
     DevScalars *sc = c.sc;
-    const int g_active = sc->active;
-    const double lam_d = sc->lambda, dtau_d = sc->dtau;
     const cpx<T> *ftw = (const cpx<T> *)c.ftw, *chat = (const cpx<T> *)c.chat;
-    // kernel spectrum for the product after the forward transform: issued first
+    // tables first (written at set-up): the kernel spectrum for the product after
+    // the forward transform, and the twiddles by one bulk copy
     cpx<T> ch[SPEC];
 #pragma unroll
     for (int i = 0; i < SPEC; ++i)
         if (t + i * B < F) ch[i] = chat[t + i * B];
-    if (gate && !g_active) return;
-
-    // twiddles by one bulk copy, overlapped with building z
     const bool bulk = ((reinterpret_cast<uintptr_t>(ftw) & 15) == 0);
     if (bulk && t == 0) {
         mbar_init(&bar, 1);
@@ -1181,6 +1195,17 @@ __device__ __forceinline__ void sconv_body(const CurveDev &c, int mode, int disc
     }
     if (!bulk)
         for (int k = t; k < F; k += B) tw[k] = ftw[k];
+    pdl_wait();
+    const int g_active = sc->active;
+    const double lam_d = sc->lambda, dtau_d = sc->dtau;
+    if (gate && !g_active) {
+        // the thread that armed the barrier keeps the CTA alive until the copy has landed
+        if (bulk && t == 0 && !mbar_wait(&bar, 0)) {
+            atomicExch(&sc->err, 1);
+            mbar_wait(&bar, 0);
+        }
+        return;
+    }
 
     const T *X = (const T *)(mode == GM_STORE ? c.U : c.R);
     const T *colscale = (const T *)(discrete ? c.sw : c.tau);
@@ -1373,6 +1398,37 @@ static cudaError_t dispatch_n(int n, F &&f)
     }
 }
 
+// Launches a step kernel with programmatic stream serialization (it may start
+// while its predecessor finishes; see pdl_wait) and, for cluster_z > 0, thread-block
+// clusters of 1 x 1 x cluster_z CTAs.
+template <typename... KArgs, typename... Args>
+static cudaError_t launch_step_kernel(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                                      int cluster_z, Args... args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[2];
+    int n = 0;
+    attr[n].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[n].val.programmaticStreamSerializationAllowed = 1;
+    ++n;
+    if (cluster_z > 0) {
+        attr[n].id = cudaLaunchAttributeClusterDimension;
+        attr[n].val.clusterDim.x = 1;
+        attr[n].val.clusterDim.y = 1;
+        attr[n].val.clusterDim.z = cluster_z;
+        ++n;
+    }
+    cfg.attrs = attr;
+    cfg.numAttrs = n;
+    cudaError_t e = cudaLaunchKernelEx(&cfg, kern, args...);
+    if (e != cudaSuccess) return e;
+    return cudaGetLastError();
+}
+
 template <typename T>
 static cudaError_t rows_t(const CurveDev &c, int mode, cudaStream_t st)
 {
@@ -1381,8 +1437,7 @@ static cudaError_t rows_t(const CurveDev &c, int mode, cudaStream_t st)
         size_t sm = rows_smem<T>(NN, 3);
         cudaError_t e = set_smem(k_rows<T, NN>, sm);
         if (e != cudaSuccess) return e;
-        k_rows<T, NN><<<row_grid(c.ns), ROWS_WARPS * 32, sm, st>>>(c, mode);
-        return cudaGetLastError();
+        return launch_step_kernel(k_rows<T, NN>, dim3(row_grid(c.ns)), dim3(ROWS_WARPS * 32), sm, st, 0, c, mode);
     });
 }
 
@@ -1492,21 +1547,8 @@ cudaError_t launch_rows(const CurveDev &c, int mode, cudaStream_t st)
 template <typename T, int BN>
 static cudaError_t launch_dt_t(const CurveDev &c, int mode, int discrete, int gate, cudaStream_t st)
 {
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(c.tiles_c, c.tiles_r, c.ksplit);
-    cfg.blockDim = dim3(DT_THREADS, 1, 1);
-    cfg.dynamicSmemBytes = 0;
-    cfg.stream = st;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = 1;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = c.ksplit;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    cudaError_t e = cudaLaunchKernelEx(&cfg, k_dt<T, BN>, c, mode, discrete, gate);
-    if (e != cudaSuccess) return e;
-    return cudaGetLastError();
+    return launch_step_kernel(k_dt<T, BN>, dim3(c.tiles_c, c.tiles_r, c.ksplit), dim3(DT_THREADS), 0, st, c.ksplit, c,
+                              mode, discrete, gate);
 }
 
 template <typename T>
@@ -1515,8 +1557,7 @@ static cudaError_t launch_sconv_t(const CurveDev &c, int mode, int discrete, int
     const size_t sm = sconv_smem<T>(c.F);
     cudaError_t e = set_smem(k_sconv<T>, sm);
     if (e != cudaSuccess) return e;
-    k_sconv<T><<<c.nx / 2, SC_THREADS, sm, st>>>(c, mode, discrete, gate);
-    return cudaGetLastError();
+    return launch_step_kernel(k_sconv<T>, dim3(c.nx / 2), dim3(SC_THREADS), sm, st, 0, c, mode, discrete, gate);
 }
 
 cudaError_t launch_sconv_batch(int prec, int F_max, const CurveDev *cv, const int2 *items, int nitems, int mode,
@@ -1527,13 +1568,14 @@ cudaError_t launch_sconv_batch(int prec, int F_max, const CurveDev *cv, const in
     if (prec) {
         const size_t sm = sconv_smem<float>(F_max);
         if ((e = set_smem(k_sconv_batch<float>, sm)) != cudaSuccess) return e;
-        k_sconv_batch<float><<<nitems, SC_THREADS, sm, st>>>(cv, items, mode, discrete, gate);
+        return launch_step_kernel(k_sconv_batch<float>, dim3(nitems), dim3(SC_THREADS), sm, st, 0, cv, items, mode,
+                                  discrete, gate);
     } else {
         const size_t sm = sconv_smem<double>(F_max);
         if ((e = set_smem(k_sconv_batch<double>, sm)) != cudaSuccess) return e;
-        k_sconv_batch<double><<<nitems, SC_THREADS, sm, st>>>(cv, items, mode, discrete, gate);
+        return launch_step_kernel(k_sconv_batch<double>, dim3(nitems), dim3(SC_THREADS), sm, st, 0, cv, items, mode,
+                                  discrete, gate);
     }
-    return cudaGetLastError();
 }
 
 cudaError_t launch_dt(const CurveDev &c, int mode, int discrete, int gate, cudaStream_t st)
@@ -1554,8 +1596,7 @@ static cudaError_t rows_batch_t(int N, const CurveDev *cv, const int2 *items, in
         size_t sm = rows_smem<T>(NN, 3);
         cudaError_t e = set_smem(k_rows_batch<T, NN>, sm);
         if (e != cudaSuccess) return e;
-        k_rows_batch<T, NN><<<nitems, ROWS_WARPS * 32, sm, st>>>(cv, items, mode);
-        return cudaGetLastError();
+        return launch_step_kernel(k_rows_batch<T, NN>, dim3(nitems), dim3(ROWS_WARPS * 32), sm, st, 0, cv, items, mode);
     });
 }
 
@@ -1570,14 +1611,12 @@ cudaError_t launch_dt_batch(int prec, int bn, const CurveDev *cv, const int4 *it
                             int discrete, int gate, cudaStream_t st)
 {
     if (nitems <= 0) return cudaSuccess;
-    if (bn == 64) {
-        if (prec) k_dt_batch<float, 64><<<nitems, DT_THREADS, 0, st>>>(cv, items, mode, discrete, gate);
-        else k_dt_batch<double, 64><<<nitems, DT_THREADS, 0, st>>>(cv, items, mode, discrete, gate);
-    } else {
-        if (prec) k_dt_batch<float, 32><<<nitems, DT_THREADS, 0, st>>>(cv, items, mode, discrete, gate);
-        else k_dt_batch<double, 32><<<nitems, DT_THREADS, 0, st>>>(cv, items, mode, discrete, gate);
-    }
-    return cudaGetLastError();
+    const dim3 g(nitems), b(DT_THREADS);
+    if (bn == 64)
+        return prec ? launch_step_kernel(k_dt_batch<float, 64>, g, b, 0, st, 0, cv, items, mode, discrete, gate)
+                    : launch_step_kernel(k_dt_batch<double, 64>, g, b, 0, st, 0, cv, items, mode, discrete, gate);
+    return prec ? launch_step_kernel(k_dt_batch<float, 32>, g, b, 0, st, 0, cv, items, mode, discrete, gate)
+                : launch_step_kernel(k_dt_batch<double, 32>, g, b, 0, st, 0, cv, items, mode, discrete, gate);
 }
 
 __global__ void k_set_limit_batch(const CurveDev *cv, int nb, long long nsteps, double tol)
