@@ -95,7 +95,13 @@ typedef struct {
                             batch the FFT form wherever the size limit allows;
                             1 dense contraction generated from the O(N_s) cot table;
                             2 FFT convolution (N_s <= 2731 FP32 / 1366 FP64) */
-    int32_t reserved;    /* must be 0 */
+    int32_t launch;      /* how a single curve's descent steps are launched (same results):
+                            0 three kernels per step, chained by programmatic dependent
+                            launch and replayed from a CUDA graph;
+                            1 one persistent cooperative kernel for many steps, with
+                            grid-wide barriers between the phases of a step (dense form
+                            only, else as 0; measured slower than 0 on GB300).
+                            Batches ignore it. */
 } ks_params;
 
 /* Scalars of the state most recently evaluated (cost, gradient or descent). */
@@ -212,17 +218,23 @@ ks_status ks_curve_get_state(ks_curve *c, void *u_dev, double *lambda, double *t
  * Asynchronous. */
 ks_status ks_curve_set_state(ks_curve *c, const void *u_dev, double lambda, double tau);
 
-/* Per-phase device time of the descent steps, measured with CUDA events
- * recorded on the curve's stream around each kernel of a step:
+/* Device time of the descent steps, measured with CUDA events recorded on the
+ * curve's stream around each kernel.  Three-kernel steps (launch = 1, or the
+ * FFT form) are timed per phase:
  *   phase 0: row phase (f, residual, spatial adjoint, cost reductions)
  *   phase 1: s-phase with the descent update (D_t r, G, u update, |G|^2)
- *   phase 2: s-phase D_t u of the new state.
- * ks_curve_profile(c, max_steps) starts recording for up to max_steps steps
- * (max_steps = 0 stops and releases the events); ks_curve_profile_read
- * synchronises and returns the accumulated milliseconds and launch counts. */
+ *   phase 2: s-phase D_t u of the new state;
+ * launches of the persistent step kernel are timed whole (step_*).
+ * ks_curve_profile(c, max_steps) starts recording for up to max_steps steps or
+ * persistent launches (max_steps = 0 stops and releases the events);
+ * ks_curve_profile_read synchronises and returns the accumulated milliseconds
+ * and launch counts. */
 typedef struct {
-    double ms[3];
+    double ms[3];            /* three-kernel steps: milliseconds per phase */
     int64_t launches[3];
+    double step_ms;          /* persistent step kernel: milliseconds of its launches */
+    int64_t step_launches;   /* its launches */
+    int64_t step_steps;      /* steps those launches were asked to run */
 } ks_profile;
 
 ks_status ks_curve_profile(ks_curve *c, int32_t max_steps);

@@ -45,7 +45,7 @@ class KSParams(ctypes.Structure):
         ("check_ends", ctypes.c_int32),
         ("symmetry", ctypes.c_int32),
         ("s_transform", ctypes.c_int32),
-        ("reserved", ctypes.c_int32),
+        ("launch", ctypes.c_int32),
     ]
 
 
@@ -68,7 +68,8 @@ class KSScalars(ctypes.Structure):
 
 
 class KSProfile(ctypes.Structure):
-    _fields_ = [("ms", ctypes.c_double * 3), ("launches", ctypes.c_int64 * 3)]
+    _fields_ = [("ms", ctypes.c_double * 3), ("launches", ctypes.c_int64 * 3), ("step_ms", ctypes.c_double),
+                ("step_launches", ctypes.c_int64), ("step_steps", ctypes.c_int64)]
 
 
 class KSError(RuntimeError):

@@ -33,7 +33,7 @@ class KSBatch:
             arr[i] = KSParams(L=s.L, nx=s.N, ns=s.Ns, S=s.S, s0=getattr(s, "s0", 0.0), lam=1.0, lambda_free=0,
                               dtau=s.dtau, dtau_lambda=0.0, precision=_PREC[precision], adjoint=_ADJ[adjoint],
                               conv=_CONV[conv], check_ends=0, symmetry=0, s_transform=_STR[s_transform],
-                              reserved=0)
+                              launch=0)
         self.params = arr
         nbytes = self.lib.ks_batch_workspace_bytes(self.nb, arr)
         if nbytes == 0:

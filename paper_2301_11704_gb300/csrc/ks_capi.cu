@@ -1,5 +1,6 @@
 // ks_capi.cu -- the C ABI declared in include/ksconn.h: argument checks,
 // workspace layout, and the order of kernel launches for each entry point.
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -16,10 +17,13 @@ struct ks_curve {
     ks::CurveDev d;
     cudaStream_t st;
     int device;
-    // profiling: events[2*(3*step + phase)] / [.. + 1] bracket one kernel
+    // profiling: events[2*(3*entry + phase)] / [.. + 1] bracket one kernel; an
+    // entry is a three-kernel step (prof_steps = 0) or a persistent launch of
+    // prof_steps steps (phase 0 only)
     std::vector<cudaEvent_t> events;
-    int prof_cap = 0;      // steps that fit in `events`
-    int prof_used = 0;     // steps recorded so far
+    std::vector<int64_t> prof_steps;
+    int prof_cap = 0;      // entries that fit in `events`
+    int prof_used = 0;     // entries recorded so far
     // CUDA graph of GRAPH_STEPS descent steps, captured once on a private stream
     cudaGraphExec_t gexec = nullptr;
     cudaStream_t gstream = nullptr;
@@ -83,7 +87,7 @@ ks_status validate(const ks_params *p)
     if (p->check_ends != 0 && p->check_ends != 1) return fail(KS_EINVAL, "check_ends must be 0 or 1");
     if (p->symmetry < 0 || p->symmetry > 3) return fail(KS_EINVAL, "symmetry must be in [0, 3]");
     if (p->s_transform < 0 || p->s_transform > 2) return fail(KS_EINVAL, "s_transform must be 0, 1 or 2");
-    if (p->reserved != 0) return fail(KS_EINVAL, "reserved must be 0");
+    if (p->launch < 0 || p->launch > 1) return fail(KS_EINVAL, "launch must be 0 or 1");
     if (p->s_transform == 2 && ks::fft_size(p->ns, p->precision == KS_FP32) == 0)
         return fail(KS_EINVAL, "s_transform = FFT supports N_s <= %d at this precision",
                     p->precision == KS_FP32 ? 2731 : 1366);
@@ -152,10 +156,28 @@ ks_status ensure_graph(ks_curve *c, int discrete)
     return KS_OK;
 }
 
+// Steps per launch of the persistent kernel (a converged curve leaves early).
+static const int64_t PERSISTENT_STEPS = 1024;
+
 ks_status enqueue_steps(ks_curve *c, int64_t nsteps, double tol)
 {
     const int discrete = c->p.adjoint == KS_ADJ_DISCRETE;
     KS_CUDA(ks::launch_set_limit(c->d, (long long)nsteps, tol, c->st));
+    if (c->p.launch == 1 && c->d.part) {
+        for (int64_t done = 0; done < nsteps; done += PERSISTENT_STEPS) {
+            const int64_t n = std::min(PERSISTENT_STEPS, nsteps - done);
+            const bool prof = c->prof_used < c->prof_cap;
+            cudaEvent_t *ev = prof ? &c->events[(size_t)6 * c->prof_used] : nullptr;
+            if (prof) KS_CUDA(cudaEventRecord(ev[0], c->st));
+            KS_CUDA(ks::launch_step_persistent(c->d, discrete, (long long)n, c->st));
+            if (prof) {
+                KS_CUDA(cudaEventRecord(ev[1], c->st));
+                c->prof_steps[c->prof_used] = n;
+                c->prof_used++;
+            }
+        }
+        return KS_OK;
+    }
     if (c->prof_used >= c->prof_cap && nsteps >= GRAPH_STEPS) {
         ks_status s = ensure_graph(c, discrete);
         if (s != KS_OK) return s;
@@ -179,6 +201,7 @@ ks_status enqueue_steps(ks_curve *c, int64_t nsteps, double tol)
         KS_CUDA(ks::launch_dt(c->d, ks::GM_STORE, 0, 1, c->st));
         if (prof) {
             KS_CUDA(cudaEventRecord(ev[5], c->st));
+            c->prof_steps[c->prof_used] = 0;
             c->prof_used++;
         }
     }
@@ -189,6 +212,7 @@ void release_events(ks_curve *c)
 {
     for (cudaEvent_t e : c->events) cudaEventDestroy(e);
     c->events.clear();
+    c->prof_steps.clear();
     c->prof_cap = 0;
     c->prof_used = 0;
 }
@@ -219,7 +243,7 @@ int32_t ks_version(void) { return (1 << 16) | 0; }
 size_t ks_curve_workspace_bytes(const ks_params *p)
 {
     if (validate(p) != KS_OK) return 0;
-    return ks::make_layout(p->ns, p->nx, p->precision == KS_FP32, 1, 0, p->s_transform).total;
+    return ks::make_layout(p->ns, p->nx, p->precision == KS_FP32, 1, 0, p->s_transform, p->launch == 1).total;
 }
 
 int32_t ks_curve_fft_length(const ks_params *p)
@@ -243,7 +267,7 @@ ks_status ks_curve_create(const ks_params *p, const double *u_plus_host, const d
     for (int n = 0; n < p->nx; ++n)
         if (!std::isfinite(u_plus_host[n]) || !std::isfinite(u_minus_host[n]))
             return fail(KS_EINVAL, "u_plus/u_minus contain non-finite values");
-    ks::Layout lay = ks::make_layout(p->ns, p->nx, p->precision == KS_FP32, 1, 0, p->s_transform);
+    ks::Layout lay = ks::make_layout(p->ns, p->nx, p->precision == KS_FP32, 1, 0, p->s_transform, p->launch == 1);
     if (workspace_bytes < lay.total)
         return fail(KS_ENOMEM, "workspace has %zu bytes, %zu needed", workspace_bytes, lay.total);
 
@@ -496,6 +520,7 @@ ks_status ks_curve_profile(ks_curve *c, int32_t max_steps)
             return fail(KS_ECUDA, "cudaEventCreate failed");
         }
     }
+    c->prof_steps.assign((size_t)max_steps, 0);
     c->prof_cap = max_steps;
     return KS_OK;
 }
@@ -508,17 +533,23 @@ ks_status ks_curve_profile_read(ks_curve *c, ks_profile *out)
     DeviceGuard g(c->device);
     if (!g.ok) return fail(KS_ECUDA, "cannot select the curve's device");
     KS_CUDA(cudaStreamSynchronize(c->st));
-    for (int ph = 0; ph < 3; ++ph) {
-        out->ms[ph] = 0.0;
-        out->launches[ph] = 0;
-    }
-    for (int st = 0; st < c->prof_used; ++st)
+    *out = ks_profile{};
+    for (int st = 0; st < c->prof_used; ++st) {
+        if (c->prof_steps[st] > 0) {
+            float ms = 0.f;
+            KS_CUDA(cudaEventElapsedTime(&ms, c->events[(size_t)6 * st], c->events[(size_t)6 * st + 1]));
+            out->step_ms += ms;
+            out->step_launches += 1;
+            out->step_steps += c->prof_steps[st];
+            continue;
+        }
         for (int ph = 0; ph < 3; ++ph) {
             float ms = 0.f;
             KS_CUDA(cudaEventElapsedTime(&ms, c->events[(size_t)6 * st + 2 * ph], c->events[(size_t)6 * st + 2 * ph + 1]));
             out->ms[ph] += ms;
             out->launches[ph] += 1;
         }
+    }
     return KS_OK;
 }
 

@@ -51,6 +51,12 @@ constexpr int ROWS_PER_CTA = 2 * ROWS_WARPS;
 
 constexpr int MAX_PERT = 16;
 
+// Persistent descent step (one cooperative launch for many steps of a single
+// curve in the dense form): CTA size, warps per row unit, largest grid.
+constexpr int PS_THREADS = 256;
+constexpr int PS_WARPS = PS_THREADS / 32;
+constexpr int PS_MAX_CTAS = 1024;
+
 // Device-resident scalars of one curve.  Written only by device code during a
 // descent (single writer per field: the last CTA of a kernel), read by the host
 // after a stream synchronisation.
@@ -65,6 +71,7 @@ struct DevScalars {
     int lambda_free;
     int err;                            // nonzero: a bounded wait in a kernel gave up (launch invalid)
     unsigned int cnt_rows, cnt_gemm;    // arrival counters of the last-CTA reductions
+    unsigned long long bar;             // arrivals at the persistent step's grid barriers
 };
 
 // Gates of the kernels of one descent step:
@@ -78,7 +85,7 @@ struct Layout {
     size_t off_chat, off_ftw;          // FFT form: kernel spectrum [F], twiddles [F/2] (complex)
     int F;                             // 0: dense contraction
     size_t off_U, off_D, off_R, off_A, off_G, off_X;
-    size_t off_rowsc, off_bpart, off_tile, off_tcnt, off_part;
+    size_t off_rowsc, off_bpart, off_tile, off_tcnt, off_part, off_gpart;
     size_t off_cot, off_sig, off_tau, off_sw, off_twr, off_w;
     size_t off_twid, off_twid64, off_kj, off_aj, off_prec, off_ends, off_pert, off_sc;
     size_t total;
@@ -95,7 +102,8 @@ struct CurveDev {
     double *bpart;         // [row_blocks][5] per-CTA partial sums of the row phase
     double *tile;          // [tiles] per-tile |G|^2 partials
     unsigned *tcnt;        // [tiles] split arrival counters (zero between launches)
-    void *part;            // [ksplit][N_s][N] split partial sums (ksplit > 1)
+    void *part;            // persistent step: [ksplit][N_s][N] split partial sums (else null)
+    double *gpart;         // persistent step: [PS_MAX_CTAS] per-CTA |G|^2 partials
     int bn, tiles_r, tiles_c, ksplit, kchunk, row_blocks;
     int F;                 // FFT length of the s-contraction (0: dense form)
     void *chat, *ftw;      // FFT form: kernel spectrum / F and twiddles (complex, storage type)
@@ -108,7 +116,8 @@ struct CurveDev {
 
 // allow_split = 0 lays a curve out without split contractions (batched curves
 // get their parallelism from the batch); bn = 0 picks the column tile width.
-Layout make_layout(int ns, int nx, int prec, int allow_split = 1, int bn = 0, int s_transform = 0);
+Layout make_layout(int ns, int nx, int prec, int allow_split = 1, int bn = 0, int s_transform = 0,
+                   int persistent = 0);
 // Pointers of a curve whose workspace starts at `base` (256-byte aligned).
 CurveDev bind_layout(const ks_params *p, const Layout &l, void *base);
 
@@ -141,6 +150,9 @@ cudaError_t launch_rows(const CurveDev &c, int mode, cudaStream_t st);
 // sigma), op 1: W^-1 D_t^T W.  mode GM_STORE writes D_t U into D (gated when
 // `gate`), GM_UPDATE applies the descent update to U, GM_GRAD writes G.
 cudaError_t launch_dt(const CurveDev &c, int mode, int discrete, int gate, cudaStream_t st);
+// Persistent step (ks_step.cu): nsteps descent steps of a dense-form curve
+// (c.part set) in one cooperative launch; stops early with the curve's gates.
+cudaError_t launch_step_persistent(const CurveDev &c, int discrete, long long nsteps, cudaStream_t st);
 
 // ---- batched launches over (curve, block) work items; cv is a device array of curves
 cudaError_t launch_rows_batch(int prec, int N, const CurveDev *cv, const int2 *items, int nitems, int mode,

@@ -28,38 +28,16 @@
 
 #include <cooperative_groups.h>
 
-#include "ks_internal.h"
+#include "ks_device.cuh"
 
 namespace ks {
-
-template <typename T>
-struct cpx {
-    T x, y;
-};
-
-template <typename T>
-__device__ __forceinline__ cpx<T> cmul(cpx<T> a, cpx<T> b)
-{
-    return {a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x};
-}
-
-// Programmatic dependent launch.  The step kernels are launched so that a kernel
-// is set up while its predecessor in the stream drains (its CTAs start as the
-// predecessor's CTAs exit, before the predecessor's completion is flushed):
-// before pdl_wait() a kernel reads only the tables written at curve set-up
-// (complete long before); pdl_wait() returns once the predecessor has completed
-// and its writes are visible; every gate and every field is read after it, and
-// no CTA leaves before it.  No kernel triggers its successor early: successor
-// CTAs parked on the SMs during a whole kernel slowed graph replay (measured).
-// A no-op for a kernel launched without the attribute.
-__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 
 // ---------------------------------------------------------------------------
 // Layout of the workspace
 // ---------------------------------------------------------------------------
 static size_t al256(size_t x) { return (x + 255) & ~size_t(255); }
 
-Layout make_layout(int ns, int nx, int prec, int allow_split, int bn, int s_transform)
+Layout make_layout(int ns, int nx, int prec, int allow_split, int bn, int s_transform, int persistent)
 {
     Layout l{};
     size_t b = prec ? 4 : 8;
@@ -96,7 +74,11 @@ Layout make_layout(int ns, int nx, int prec, int allow_split, int bn, int s_tran
     l.off_bpart = off; off += al256((size_t)l.row_blocks * 5 * 8);
     l.off_tile = off; off += al256((size_t)tiles_max * l.ksplit * 8);
     l.off_tcnt = off; off += al256((size_t)tiles_max * 4);
-    l.off_part = off;
+    // the persistent step's split partials and per-CTA |G|^2 partials (single
+    // curves in the dense form that asked for it)
+    const bool persist = persistent && allow_split && l.F == 0;
+    l.off_part = off; off += persist ? al256((size_t)l.ksplit * ns * nx * b) : 0;
+    l.off_gpart = off; off += persist ? al256((size_t)PS_MAX_CTAS * 8) : 0;
     int P = ns - 1;
     l.off_cot = off; off += al256((size_t)2 * P * b);
     l.off_sig = off; off += al256((size_t)ns * b);
@@ -140,7 +122,8 @@ CurveDev bind_layout(const ks_params *p, const Layout &l, void *base)
     d.bpart = (double *)(b + l.off_bpart);
     d.tile = (double *)(b + l.off_tile);
     d.tcnt = (unsigned *)(b + l.off_tcnt);
-    d.part = nullptr;
+    d.part = l.off_gpart > l.off_part ? (void *)(b + l.off_part) : nullptr;
+    d.gpart = l.off_gpart > l.off_part ? (double *)(b + l.off_gpart) : nullptr;
     d.bn = l.bn;
     d.tiles_r = l.tiles_r;
     d.tiles_c = l.tiles_c;
@@ -165,115 +148,6 @@ CurveDev bind_layout(const ks_params *p, const Layout &l, void *base)
     d.pert = (double *)(b + l.off_pert);
     d.sc = (DevScalars *)(b + l.off_sc);
     return d;
-}
-
-// ---------------------------------------------------------------------------
-// Warp-level FFT on shared memory
-// ---------------------------------------------------------------------------
-// Stockham radix-2 FFT of length N by one warp: natural order in and out, no
-// bit reversal.  tw[t] = exp(-2 pi i t / N), t < N/2.  Forward uses exp(-...),
-// inverse exp(+...); neither scales.  Returns the buffer holding the result
-// (x or y); the other one is free scratch.
-template <typename T, int N>
-__device__ __forceinline__ cpx<T> *warp_fft(cpx<T> *x, cpx<T> *y, const cpx<T> *tw, bool inverse, int lane)
-{
-#pragma unroll
-    for (int ns = 1; ns < N; ns <<= 1) {
-#pragma unroll
-        for (int j = lane; j < N / 2; j += 32) {
-            int k = j & (ns - 1);
-            cpx<T> a = x[j], b = x[j + N / 2];
-            cpx<T> w = tw[k * (N / (2 * ns))];
-            if (inverse) w.y = -w.y;
-            b = cmul(b, w);
-            int o = ((j - k) << 1) + k;
-            y[o] = {a.x + b.x, a.y + b.y};
-            y[o + ns] = {a.x - b.x, a.y - b.y};
-        }
-        __syncwarp();
-        cpx<T> *t = x;
-        x = y;
-        y = t;
-    }
-    return x;
-}
-
-// Full spectrum of z = a + i b for two real sections given by their half spectra
-// (j = 0..N/2-1, Nyquist zero):  Z_j = A_j + i B_j,  Z_{N-j} = conj(A_j) + i conj(B_j).
-template <typename T, int N>
-__device__ __forceinline__ void put_pair(cpx<T> *Z, int j, cpx<T> A, cpx<T> B)
-{
-    Z[j] = {A.x - B.y, A.y + B.x};
-    if (j > 0) Z[N - j] = {A.x + B.y, B.x - A.y};
-}
-
-// Half spectra of two real sections from the FFT W of z = a + i b, with the
-// 1/N of the forward transform:  A_j = (W_j + conj W_{N-j}) / 2N,
-// B_j = (W_j - conj W_{N-j}) / 2iN.
-template <typename T, int N>
-__device__ __forceinline__ void get_pair(const cpx<T> *W, int j, cpx<T> &A, cpx<T> &B)
-{
-    cpx<T> wj = W[j], wn = W[(N - j) & (N - 1)];
-    const T h = T(0.5) / T(N);
-    A = {(wj.x + wn.x) * h, (wj.y - wn.y) * h};
-    B = {(wj.y + wn.y) * h, (wn.x - wj.x) * h};
-    if (j == 0) { A.y = 0; B.y = 0; }
-}
-
-// Symmetric subspaces (Sec. V.B): bit 0 = odd sections (real parts of every
-// coefficient zero), bit 1 = L/2-periodic sections (odd modes zero).
-template <typename T>
-__device__ __forceinline__ cpx<T> project(cpx<T> v, int j, int sym)
-{
-    if (sym & 1) v.x = T(0);
-    if ((sym & 2) && (j & 1)) v = cpx<T>{0, 0};
-    return v;
-}
-
-__device__ __forceinline__ bool col_allowed(int col, int sym)
-{
-    if ((sym & 1) && !(col & 1)) return false;
-    if ((sym & 2) && ((col >> 1) & 1)) return false;
-    return true;
-}
-
-template <typename T>
-__device__ __forceinline__ cpx<T> ld2(const T *p, int m, int N, int j)
-{
-    const T *q = p + (size_t)m * N + 2 * j;
-    return {q[0], j == 0 ? T(0) : q[1]};
-}
-
-template <typename T>
-__device__ __forceinline__ void st2(T *p, int m, int N, int j, cpx<T> v)
-{
-    T *q = p + (size_t)m * N + 2 * j;
-    q[0] = v.x;
-    q[1] = (j == 0) ? T(0) : v.y;
-}
-
-template <typename T>
-__device__ __forceinline__ T warp_sum(T v)
-{
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
-}
-
-// Fixed-order block reduction (deterministic for a fixed blockDim).
-template <int NT>
-__device__ __forceinline__ double block_sum(double v, double *red)
-{
-    red[threadIdx.x] = v;
-    __syncthreads();
-#pragma unroll
-    for (int s = NT / 2; s > 0; s >>= 1) {
-        if ((int)threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
-        __syncthreads();
-    }
-    double r = red[0];
-    __syncthreads();
-    return r;
 }
 
 // ---------------------------------------------------------------------------
@@ -492,259 +366,6 @@ __global__ void __launch_bounds__(ROWS_WARPS * 32) k_row_inv(CurveDev c, const T
     }
 }
 
-// ---------------------------------------------------------------------------
-// Row phase of one evaluation
-// ---------------------------------------------------------------------------
-// Per section m (two per warp, packed as one complex FFT):
-//   u   = IDFT(u^)                      physical section
-//   w^  = DFT(u^2) / N
-//   f^  = -(1/2) i k w^ - a_j u^        (eq. KSE: -u u_x - u_xx - u_xxxx; a_j = k^4 - k^2)
-//   r^  = f^ - l d^                     (eq. KSE_residual; 0 on rows 0 and P)
-//   r_x = IDFT(i k r^)
-//   A^  = DFT(u r_x) / N - a_j r^       ((Df)^T r = u r_x - r_xx - r_xxxx, eq. KSE_G)
-// Row sums (Parseval, FP64): |r_m|^2, |d_m|^2, <d_m, r_m> (interior rows) and
-// |u_m|^2, |f_m|^2 (end rows).  The last CTA to finish reduces them over m in a
-// fixed order: J^2, J_arc, dJ^2/dl, |l d|_W, the end-section residuals, and
-// (step mode) the convergence decision and the next lambda.
-template <typename T, int N>
-__device__ __forceinline__ void rows_body(const CurveDev &c, int mode, int blk, int nblk)
-{
-    constexpr int H = N / 2;
-    constexpr int MPL = (H + 31) / 32;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    cpx<T> *tw = (cpx<T> *)smem_raw;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    cpx<T> *B0 = tw + H + warp * 3 * N, *B1 = B0 + N, *B2 = B1 + N;
-    __shared__ double red5[5][ROWS_WARPS * 32];
-    __shared__ double wpart[ROWS_WARPS][5];
-    __shared__ int am_last;
-    DevScalars *sc = c.sc;
-    const int ns = c.ns, P = c.P;
-    const T *U = (const T *)c.U, *D = (const T *)c.D;
-    T *R = (T *)c.R, *A = (T *)c.A;
-    const T *kj = (const T *)c.kj, *aj = (const T *)c.aj;
-    const int m0 = (blk * ROWS_WARPS + warp) * 2, m1 = m0 + 1;
-    const bool has0 = m0 < ns, has1 = m1 < ns;
-
-    // Every independent global load is issued before the first use: the
-    // twiddles and the Fourier tables of the modes this lane owns (before the
-    // predecessor has finished), then the gate, lambda and both sections of u and
-    // D_t u (one memory round trip).
-    const cpx<T> twv = ((int)threadIdx.x < H) ? ((const cpx<T> *)c.twid)[threadIdx.x] : cpx<T>{0, 0};
-    cpx<T> ua[MPL], ub[MPL], ra[MPL], rb[MPL], dva[MPL], dvb[MPL];
-    T kv[MPL], av[MPL];
-#pragma unroll
-    for (int i = 0; i < MPL; ++i) {
-        const int j = lane + 32 * i;
-        kv[i] = (j < H) ? kj[j] : T(0);
-        av[i] = (j < H) ? aj[j] : T(0);
-    }
-    for (int t = threadIdx.x + blockDim.x; t < H; t += blockDim.x) tw[t] = ((const cpx<T> *)c.twid)[t];
-    pdl_wait();
-    const int g_done = sc->done;
-    const long long g_step = sc->step, g_limit = sc->limit;
-    const double lamd0 = sc->lambda;
-#pragma unroll
-    for (int i = 0; i < MPL; ++i) {
-        const int j = lane + 32 * i;
-        const bool ok = j < H;
-        ua[i] = (ok && has0) ? ld2(U, m0, N, j) : cpx<T>{0, 0};
-        ub[i] = (ok && has1) ? ld2(U, m1, N, j) : cpx<T>{0, 0};
-        dva[i] = (ok && has0) ? ld2(D, m0, N, j) : cpx<T>{0, 0};
-        dvb[i] = (ok && has1) ? ld2(D, m1, N, j) : cpx<T>{0, 0};
-    }
-
-    if (mode == ROWS_STEP && (g_done || g_step >= g_limit)) {
-        if (blk == 0 && threadIdx.x == 0) sc->active = 0;
-        return;
-    }
-    if ((int)threadIdx.x < H) tw[threadIdx.x] = twv;
-    __syncthreads();
-    const T lam = (T)lamd0;
-
-    if (has0) {
-        const bool in0 = (m0 > 0 && m0 < P), in1 = has1 && (m1 > 0 && m1 < P);
-        // sums over the modes of a section, in the storage type (N/2 <= 128 terms);
-        // sections are combined in FP64 below
-        T s0[5] = {0, 0, 0, 0, 0}, s1[5] = {0, 0, 0, 0, 0};   // nr, nd, ndr, nu, nf
-        // spectrum of u_a + i u_b
-#pragma unroll
-        for (int i = 0; i < MPL; ++i) {
-            int j = lane + 32 * i;
-            if (j < H) put_pair<T, N>(B0, j, ua[i], ub[i]);
-        }
-        if (lane == 0) B0[H] = {0, 0};
-        __syncwarp();
-        cpx<T> *Zu = warp_fft<T, N>(B0, B1, tw, true, lane);     // u_a + i u_b on the grid
-        cpx<T> *Q = (Zu == B0) ? B1 : B0;
-        for (int n = lane; n < N; n += 32) {
-            cpx<T> z = Zu[n];
-            B2[n] = z;
-            Q[n] = {z.x * z.x, z.y * z.y};
-        }
-        __syncwarp();
-        cpx<T> *Wq = warp_fft<T, N>(Q, Zu, tw, false, lane);     // DFT of u_a^2 + i u_b^2
-#pragma unroll
-        for (int i = 0; i < MPL; ++i) {
-            int j = lane + 32 * i;
-            if (j < H) {
-                cpx<T> wa, wb;
-                get_pair<T, N>(Wq, j, wa, wb);
-                const T k = kv[i], a = av[i], hk = T(0.5) * k;
-                cpx<T> fa = {hk * wa.y - a * ua[i].x, -hk * wa.x - a * ua[i].y};
-                cpx<T> fb = {hk * wb.y - a * ub[i].x, -hk * wb.x - a * ub[i].y};
-                const cpx<T> da = dva[i], db = dvb[i];
-                ra[i] = in0 ? project(cpx<T>{fa.x - lam * da.x, fa.y - lam * da.y}, j, c.sym) : cpx<T>{0, 0};
-                rb[i] = in1 ? project(cpx<T>{fb.x - lam * db.x, fb.y - lam * db.y}, j, c.sym) : cpx<T>{0, 0};
-                if (j == 0) { ra[i].y = 0; rb[i].y = 0; fa.y = 0; fb.y = 0; }
-                const T cw = (j == 0) ? T(1) : T(2);
-                s0[0] += cw * (ra[i].x * ra[i].x + ra[i].y * ra[i].y);
-                s0[1] += cw * (da.x * da.x + da.y * da.y);
-                s0[2] += cw * (da.x * ra[i].x + da.y * ra[i].y);
-                s0[3] += cw * (ua[i].x * ua[i].x + ua[i].y * ua[i].y);
-                s0[4] += cw * (fa.x * fa.x + fa.y * fa.y);
-                s1[0] += cw * (rb[i].x * rb[i].x + rb[i].y * rb[i].y);
-                s1[1] += cw * (db.x * db.x + db.y * db.y);
-                s1[2] += cw * (db.x * rb[i].x + db.y * rb[i].y);
-                s1[3] += cw * (ub[i].x * ub[i].x + ub[i].y * ub[i].y);
-                s1[4] += cw * (fb.x * fb.x + fb.y * fb.y);
-            }
-        }
-        __syncwarp();
-        // spectrum of (i k r^_a) + i (i k r^_b) -> r_x on the grid
-        cpx<T> *X0 = Wq, *X1 = (Wq == B0) ? B1 : B0;
-#pragma unroll
-        for (int i = 0; i < MPL; ++i) {
-            int j = lane + 32 * i;
-            if (j < H) {
-                const T k = kv[i];
-                put_pair<T, N>(X0, j, cpx<T>{-k * ra[i].y, k * ra[i].x}, cpx<T>{-k * rb[i].y, k * rb[i].x});
-            }
-        }
-        if (lane == 0) X0[H] = {0, 0};
-        __syncwarp();
-        cpx<T> *Rx = warp_fft<T, N>(X0, X1, tw, true, lane);
-        cpx<T> *Y = (Rx == X0) ? X1 : X0;
-        for (int n = lane; n < N; n += 32) {
-            cpx<T> z = B2[n], q = Rx[n];
-            Y[n] = {z.x * q.x, z.y * q.y};
-        }
-        __syncwarp();
-        cpx<T> *Pp = warp_fft<T, N>(Y, Rx, tw, false, lane);     // DFT of u_a r_xa + i u_b r_xb
-#pragma unroll
-        for (int i = 0; i < MPL; ++i) {
-            int j = lane + 32 * i;
-            if (j < H) {
-                cpx<T> pa, pb;
-                get_pair<T, N>(Pp, j, pa, pb);
-                const T a = av[i];
-                st2(R, m0, N, j, ra[i]);
-                st2(A, m0, N, j, project(cpx<T>{pa.x - a * ra[i].x, pa.y - a * ra[i].y}, j, c.sym));
-                if (has1) {
-                    st2(R, m1, N, j, rb[i]);
-                    st2(A, m1, N, j, project(cpx<T>{pb.x - a * rb[i].x, pb.y - a * rb[i].y}, j, c.sym));
-                }
-            }
-        }
-#pragma unroll
-        for (int q = 0; q < 5; ++q) {
-            s0[q] = warp_sum(s0[q]);
-            s1[q] = warp_sum(s1[q]);
-        }
-        if (lane == 0) {
-            // per-section norms |q_m|^2 = L sum_j c_j |q^_j|^2 (FP64 from here on)
-            const double L = c.L, lamd = sc->lambda, al = fabs(lamd);
-            double v[5] = {0, 0, 0, 0, 0};
-            const int ms[2] = {m0, m1};
-            const bool ins[2] = {in0, in1};
-            // per-section terms in the storage type; their sum over sections in FP64
-            const T Lt = (T)L, alt = (T)al, l2 = (T)(lamd * lamd);
-            for (int q = 0; q < 2; ++q) {
-                if (q == 1 && !has1) break;
-                const T *sq = q ? s1 : s0;
-                const T nr = Lt * sq[0], nd = Lt * sq[1], ndr = Lt * sq[2];
-                double *rs = c.rowsc + (size_t)ms[q] * 4;
-                rs[0] = ins[q] ? (double)nr : (double)(Lt * sq[3]);
-                rs[1] = (double)nd;
-                rs[2] = (double)ndr;
-                rs[3] = (double)(Lt * sq[4]);
-                if (ins[q]) {
-                    const T w = (T)c.w[ms[q]], sd = sqrt(nd);
-                    v[0] += (double)(w * nr);                 // J^2
-                    v[1] += (double)(w * sqrt(nr) * alt * sd); // J_arc numerator
-                    v[2] += (double)(w * alt * sd);           // J_arc denominator
-                    v[3] += (double)(w * ndr);                // <d, r>_W
-                    v[4] += (double)(w * l2 * nd);            // |l d|_W^2
-                }
-            }
-#pragma unroll
-            for (int q = 0; q < 5; ++q) wpart[warp][q] = v[q];
-        }
-    } else if (lane == 0) {
-#pragma unroll
-        for (int q = 0; q < 5; ++q) wpart[warp][q] = 0.0;
-    }
-    __syncthreads();
-    if (threadIdx.x < 5) {
-        double t = 0.0;
-#pragma unroll
-        for (int w = 0; w < ROWS_WARPS; ++w) t += wpart[w][threadIdx.x];
-        c.bpart[(size_t)blk * 5 + threadIdx.x] = t;
-    }
-
-    // ---- last CTA: FP64 reduction over the CTAs' partial sums in a fixed order
-    __threadfence();
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        unsigned prev = atomicAdd(&sc->cnt_rows, 1u);
-        am_last = (prev == (unsigned)nblk - 1);
-    }
-    __syncthreads();
-    if (!am_last) return;
-    __threadfence();
-    double t[5] = {0, 0, 0, 0, 0};
-    for (int b = threadIdx.x; b < nblk; b += blockDim.x)
-#pragma unroll
-        for (int q = 0; q < 5; ++q) t[q] += __ldcg(c.bpart + (size_t)b * 5 + q);
-#pragma unroll
-    for (int q = 0; q < 5; ++q) red5[q][threadIdx.x] = t[q];
-    __syncthreads();
-    for (int sidx = ROWS_WARPS * 16; sidx > 0; sidx >>= 1) {
-        if ((int)threadIdx.x < sidx)
-#pragma unroll
-            for (int q = 0; q < 5; ++q) red5[q][threadIdx.x] += red5[q][threadIdx.x + sidx];
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) {
-        const double lamd = sc->lambda;
-        const double t_j2 = red5[0][0], t_num = red5[1][0], t_den = red5[2][0], t_dl = red5[3][0], t_d2 = red5[4][0];
-        sc->J2 = t_j2;
-        sc->Jarc = t_den > 0 ? t_num / t_den : 0.0;
-        sc->dJdl = -2.0 * t_dl;
-        sc->Dnorm = sqrt(t_d2);
-        sc->u2_plus = __ldcg(c.rowsc + 0);
-        sc->f2_plus = __ldcg(c.rowsc + 3);
-        sc->u2_minus = __ldcg(c.rowsc + 4 * (size_t)P + 0);
-        sc->f2_minus = __ldcg(c.rowsc + 4 * (size_t)P + 3);
-        if (mode == ROWS_STEP) {
-            const double J = sqrt(t_j2);
-            const double crit = sc->conv == 0 ? sc->Jarc : (sc->conv == 1 ? J : (sc->Dnorm > 0 ? J / sc->Dnorm : J));
-            if (!isfinite(t_j2) || !isfinite(sc->Jarc)) {
-                sc->status = 5;
-                sc->done = 1;
-                sc->active = 0;
-            } else if (sc->tol > 0 && crit < sc->tol) {
-                sc->done = 1;
-                sc->active = 0;
-            } else {
-                sc->active = 1;
-            }
-            sc->lambda_next = sc->lambda_free ? lamd - sc->dtau_lambda * sc->dJdl : lamd;
-        }
-        sc->cnt_rows = 0;
-    }
-}
-
 template <typename T, int N>
 __global__ void __launch_bounds__(ROWS_WARPS * 32) k_rows(CurveDev c, int mode)
 {
@@ -768,10 +389,10 @@ __global__ void __launch_bounds__(ROWS_WARPS * 32) k_rows_batch(const CurveDev *
 //   D_t:          colscale = tau, rowscale = sigma, tsign = +1
 //   W^-1 D_t^T W: colscale = sigma w, rowscale = tau / w, tsign = -1
 // CTA (tile_c, tile_r, ks) computes a DT_BM x BN output tile over the sections
-// [ks kchunk, (ks+1) kchunk).  Each DT_BK-stage builds its D_t tile in shared
-// memory from two contiguous windows of the cot table (one for j+m, one for
-// j-m).  With ksplit > 1 the partial tiles go to `part` and the last CTA of a
-// tile to arrive sums them in split order (deterministic) and runs the epilogue:
+// [ks kchunk, (ks+1) kchunk) (DtContract).  With ksplit > 1 the splits of a tile
+// form one thread-block cluster: each CTA sums one row band of the tile over the
+// splits' partial tiles in split order (distributed shared memory;
+// deterministic) and runs the epilogue on it:
 //   GM_STORE:  D = Y                                  (D_t u of the new state)
 //   GM_UPDATE: e = +l Y (published adjoint) or -l Y (discrete adjoint),
 //              G = -(A^ + e) on interior rows, u += dtau G / (1 + dtau a_j^2)
@@ -783,12 +404,9 @@ __device__ __forceinline__ void dt_body(const CurveDev &c, int mode, int discret
                                         int ks, int tiles_c, int tiles_r)
 {
     namespace cg = cooperative_groups;
-    constexpr int BM = DT_BM, BK = DT_BK, TM = 2, TN = BN / 16, WIN = BM + BK - 1;
-    constexpr int XPT = BK * BN / DT_THREADS;   // X values per thread per stage
-    __shared__ __align__(16) T Ks[BK][BM];
-    __shared__ __align__(16) T Xs[BK][BN];
+    constexpr int BM = DT_BM, TM = 2, TN = BN / 16;
+    __shared__ DtTiles<T, BN> sm;
     __shared__ __align__(16) T Pt[BM][BN];       // this split's partial tile (read by the cluster)
-    __shared__ T Wp[WIN + 1], Wm[WIN + 1];
     __shared__ double red[DT_THREADS];
     __shared__ int am_last;
     DevScalars *sc = c.sc;
@@ -796,39 +414,27 @@ __device__ __forceinline__ void dt_body(const CurveDev &c, int mode, int discret
     const int g_active = sc->active;
     const double lam_d = sc->lambda, dtau_d = sc->dtau;
 
-    const int ns = c.ns, N = c.nx, P = c.P, twoP = 2 * P;
-    const T *X = (const T *)(mode == GM_STORE ? c.U : c.R);
-    const T *cot = (const T *)c.cot;
-    const T *colscale = (const T *)(discrete ? c.sw : c.tau);
+    const int ns = c.ns, N = c.nx, P = c.P;
     const T *rowscale = (const T *)(discrete ? c.twr : c.sig);
-    const T tsign = discrete ? T(-1) : T(1);
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
     const int j0 = tile_r * BM, c0 = tile_c * BN;
-    const int kbeg = ks * c.kchunk, kend = min(ns, kbeg + c.kchunk);
+    DtContract<T, BN> k;
+    k.X = (const T *)(mode == GM_STORE ? c.U : c.R);
+    k.cot = (const T *)c.cot;
+    k.colscale = (const T *)(discrete ? c.sw : c.tau);
+    k.tsign = discrete ? T(-1) : T(1);
+    k.N = N;
+    k.twoP = 2 * P;
+    k.j0 = j0;
+    k.c0 = c0;
+    k.kbeg = ks * c.kchunk;
+    k.kend = min(ns, k.kbeg + c.kchunk);
     T acc[TM][TN];
 #pragma unroll
     for (int i = 0; i < TM; ++i)
 #pragma unroll
         for (int l = 0; l < TN; ++l) acc[i][l] = T(0);
-
-    // register-staged operands of one stage: scaled X values and the two cot windows
-    T xr[XPT], wpr = T(0), wmr = T(0);
-    auto fetch = [&](int m0) {
-#pragma unroll
-        for (int q = 0; q < XPT; ++q) {
-            const int e = threadIdx.x + q * DT_THREADS;
-            const int kk = e / BN, cc = e % BN, m = m0 + kk, col = c0 + cc;
-            xr[q] = (m < kend && col < N) ? colscale[m] * X[(size_t)m * N + col] : T(0);
-        }
-        if (threadIdx.x < WIN) {
-            int ip = (j0 + m0 + (int)threadIdx.x) % twoP;
-            int im = (j0 - m0 - BK + 1 + (int)threadIdx.x) % twoP;
-            if (im < 0) im += twoP;
-            wpr = cot[ip];
-            wmr = cot[im];
-        }
-    };
-    if (kbeg < kend) fetch(kbeg);
+    if (k.kbeg < k.kend) k.fetch(k.kbeg);
 
     // Outputs this CTA finishes: with splits, the row band [r0, r1) of the tile
     // (slot q = element threadIdx.x + q * DT_THREADS of the band); without, the
@@ -864,39 +470,7 @@ __device__ __forceinline__ void dt_body(const CurveDev &c, int mode, int discret
         pW[q] = (ok && mode != GM_STORE) ? c.w[j] : 0.0;
     }
     if (gate && !g_active) return;
-
-    for (int m0 = kbeg; m0 < kend; m0 += BK) {
-#pragma unroll
-        for (int q = 0; q < XPT; ++q) {
-            const int e = threadIdx.x + q * DT_THREADS;
-            Xs[e / BN][e % BN] = xr[q];
-        }
-        if (threadIdx.x < WIN) {
-            Wp[threadIdx.x] = wpr;
-            Wm[threadIdx.x] = wmr;
-        }
-        __syncthreads();
-        if (m0 + BK < kend) fetch(m0 + BK);      // next stage in flight while this one computes
-        // D_t tile, stored [kk][jj]: K(j0+jj, m0+kk) = Wp[jj+kk] + tsign Wm[jj-kk+BK-1]
-        for (int e = threadIdx.x; e < BK * BM; e += DT_THREADS) {
-            const int kk = e / BM, jj = e % BM;
-            Ks[kk][jj] = Wp[jj + kk] + tsign * Wm[jj - kk + BK - 1];
-        }
-        __syncthreads();
-#pragma unroll 8
-        for (int kk = 0; kk < BK; ++kk) {
-            T a[TM], b[TN];
-#pragma unroll
-            for (int i = 0; i < TM; ++i) a[i] = Ks[kk][ty * TM + i];
-#pragma unroll
-            for (int l = 0; l < TN; ++l) b[l] = Xs[kk][tx * TN + l];
-#pragma unroll
-            for (int i = 0; i < TM; ++i)
-#pragma unroll
-                for (int l = 0; l < TN; ++l) acc[i][l] += a[i] * b[l];
-        }
-        __syncthreads();
-    }
+    k.run(sm, acc);
 
     // ---- sum of the splits of this tile inside the cluster (distributed shared memory)
     const int ntiles = tiles_c * tiles_r;
@@ -915,7 +489,7 @@ __device__ __forceinline__ void dt_body(const CurveDev &c, int mode, int discret
                 const T *rem = cluster.map_shared_rank(&Pt[0][0], q);
                 t += rem[jj * BN + cc];
             }
-            ((T *)Ks)[e] = t;      // the band's sums, row-major with BN per row
+            ((T *)sm.Ks)[e] = t;   // the band's sums, row-major with BN per row
         }
         cluster.sync();           // no CTA leaves while its partial tile may still be read
         __syncthreads();
@@ -930,7 +504,7 @@ __device__ __forceinline__ void dt_body(const CurveDev &c, int mode, int discret
     for (int q = 0; q < EP; ++q) {
         int j = 0, col = 0;
         if (!slot(q, j, col)) continue;
-        const T y0 = (nsplit > 1) ? ((T *)Ks)[threadIdx.x + q * DT_THREADS] : acc[q / TN][q % TN];
+        const T y0 = (nsplit > 1) ? ((T *)sm.Ks)[threadIdx.x + q * DT_THREADS] : acc[q / TN][q % TN];
         const T y = pS[q] * y0;
         if (mode == GM_STORE) {
             Dout[(size_t)j * N + col] = y;
@@ -1358,45 +932,10 @@ static size_t sconv_smem(int F)
 // ---------------------------------------------------------------------------
 // Launchers
 // ---------------------------------------------------------------------------
-template <typename T>
-static size_t rows_smem(int N, int bufs)
-{
-    return (size_t)(N / 2 + ROWS_WARPS * bufs * N) * sizeof(cpx<T>);
-}
 
-// Sets a kernel's dynamic shared-memory limit to the largest size requested so
-// far, once per size increase (per device: kernels run on the device current at
-// the call).  Done for every size, not only above 48 KB: static shared memory
-// counts against the same default limit.
-template <typename K>
-static cudaError_t set_smem(K kern, size_t bytes)
-{
-    static thread_local std::map<std::pair<int, const void *>, size_t> done;   // (device, kernel) -> bytes
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) dev = -1;
-    size_t &have = done[std::make_pair(dev, (const void *)kern)];
-    if (bytes <= have) return cudaSuccess;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-    if (e == cudaSuccess) have = bytes;
-    return e;
-}
 
 static int row_grid(int ns) { return (ns + ROWS_PER_CTA - 1) / ROWS_PER_CTA; }
 
-// Calls f(std::integral_constant<int, N>) for the supported section lengths.
-template <typename F>
-static cudaError_t dispatch_n(int n, F &&f)
-{
-    switch (n) {
-    case 8: return f(std::integral_constant<int, 8>{});
-    case 16: return f(std::integral_constant<int, 16>{});
-    case 32: return f(std::integral_constant<int, 32>{});
-    case 64: return f(std::integral_constant<int, 64>{});
-    case 128: return f(std::integral_constant<int, 128>{});
-    case 256: return f(std::integral_constant<int, 256>{});
-    default: return cudaErrorInvalidValue;
-    }
-}
 
 // Launches a step kernel with programmatic stream serialization (it may start
 // while its predecessor finishes; see pdl_wait) and, for cluster_z > 0, thread-block

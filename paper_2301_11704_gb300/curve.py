@@ -18,6 +18,7 @@ _PREC = {"fp64": _native.KS_FP64, "fp32": _native.KS_FP32}
 _ADJ = {"paper": _native.KS_ADJ_PAPER, "discrete": _native.KS_ADJ_DISCRETE}
 _CONV = {"jarc": _native.KS_CONV_JARC, "j": _native.KS_CONV_J, "jrel": _native.KS_CONV_JREL}
 _STR = {"auto": 0, "dense": 1, "fft": 2}
+_LAUNCH = {"auto": 0, "kernels": 0, "persistent": 1}
 
 
 def _f64(a, n=None):
@@ -37,13 +38,16 @@ class KSCurve:
     Row 0 is s = +inf (u_plus), row ns-1 is s = -inf (u_minus).
     symmetry: 1 holds every section odd, 2 holds it L/2-periodic, 3 both (the
     symmetric subspaces the descent preserves, Sec. V.B).
+    launch: "auto" / "kernels" run descent steps as three kernels per step,
+    "persistent" runs many steps of a dense-form curve in one cooperative kernel
+    (same results; slower on GB300 at the sizes measured).
     """
 
     def __init__(self, L: float, nx: int, ns: int, S: float, u_plus, u_minus=None, *, s0: float = 0.0,
                  lam: float = 1.0, lambda_free: bool = False, dtau: float = 0.01, dtau_lambda: float = 0.0,
                  precision: str = "fp64", adjoint: str = "paper", conv: str = "jarc", u_init=None,
-                 check_ends: bool = False, symmetry: int = 0, s_transform: str = "auto", device=None,
-                 stream: Optional[torch.cuda.Stream] = None):
+                 check_ends: bool = False, symmetry: int = 0, s_transform: str = "auto", launch: str = "auto",
+                 device=None, stream: Optional[torch.cuda.Stream] = None):
         self.lib = _native.load()
         self.device = torch.device(device if device is not None else "cuda")
         self.dtype = torch.float64 if precision == "fp64" else torch.float32
@@ -51,13 +55,16 @@ class KSCurve:
         self.params = KSParams(L=L, nx=nx, ns=ns, S=S, s0=s0, lam=lam, lambda_free=int(bool(lambda_free)),
                                dtau=dtau, dtau_lambda=dtau_lambda, precision=_PREC[precision],
                                adjoint=_ADJ[adjoint], conv=_CONV[conv], check_ends=int(bool(check_ends)),
-                               symmetry=int(symmetry), s_transform=_STR[s_transform], reserved=0)
+                               symmetry=int(symmetry), s_transform=_STR[s_transform],
+                               launch=_LAUNCH[launch])
         nbytes = self.lib.ks_curve_workspace_bytes(ctypes.byref(self.params))
         if nbytes == 0:
             raise _native.KSError(_native.KS_EINVAL, self.lib.ks_last_error().decode())
         self.workspace_bytes = int(nbytes)
         # length of the FFT that applies D_t along s (0: dense contraction)
         self.fft_length = int(self.lib.ks_curve_fft_length(ctypes.byref(self.params)))
+        # descent steps run as one persistent kernel (dense form) or as three kernels per step
+        self.persistent = self.fft_length == 0 and _LAUNCH[launch] == 1
         self._ws = torch.empty(self.workspace_bytes + 256, dtype=torch.uint8, device=self.device)
         base = self._ws.data_ptr()
         self._ws_ptr = (base + 255) & ~255
@@ -154,7 +161,10 @@ class KSCurve:
         pr = _native.KSProfile()
         check(self.lib.ks_curve_profile_read(self._live(), ctypes.byref(pr)))
         names = ("rows", "dt_update", "dt_store")
-        return {n: dict(ms=pr.ms[i], launches=pr.launches[i]) for i, n in enumerate(names)}
+        out = {n: dict(ms=pr.ms[i], launches=pr.launches[i]) for i, n in enumerate(names) if pr.launches[i]}
+        if pr.step_launches:
+            out["step"] = dict(ms=pr.step_ms, launches=pr.step_launches, steps=pr.step_steps)
+        return out
 
     def close(self):
         if getattr(self, "handle", None) is not None:

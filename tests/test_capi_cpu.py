@@ -41,7 +41,7 @@ def test_version(lib):
 
 def _params(**kw):
     base = dict(L=22.0, nx=32, ns=128, S=12.7, s0=0.0, lam=1.0, lambda_free=0, dtau=0.01, dtau_lambda=0.0,
-                precision=0, adjoint=0, conv=0, check_ends=0, symmetry=0, s_transform=0, reserved=0)
+                precision=0, adjoint=0, conv=0, check_ends=0, symmetry=0, s_transform=0, launch=0)
     base.update(kw)
     return KSParams(**base)
 
@@ -58,7 +58,7 @@ def test_workspace_size_scales_with_the_curve(lib):
 
 @pytest.mark.parametrize("bad", [dict(nx=24), dict(nx=4), dict(nx=512), dict(ns=2), dict(L=0.0), dict(S=-1.0),
                                  dict(dtau=0.0), dict(precision=7), dict(adjoint=3), dict(conv=9),
-                                 dict(symmetry=4), dict(s_transform=3), dict(reserved=1), dict(L=float("nan"))])
+                                 dict(symmetry=4), dict(s_transform=3), dict(launch=2), dict(L=float("nan"))])
 def test_invalid_parameters_are_rejected_on_the_host(lib, bad):
     p = _params(**bad)
     assert lib.ks_curve_workspace_bytes(ctypes.byref(p)) == 0

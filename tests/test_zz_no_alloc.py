@@ -69,7 +69,7 @@ def test_noalloc_cost_matches_the_workspace_entry_points(precision, tol):
 def test_noalloc_rejects_curves_larger_than_its_scratch():
     lib = _native.load()
     p = _native.KSParams(L=100.0, nx=256, ns=16384, S=1638.3, s0=0.0, lam=1.0, lambda_free=0, dtau=0.01,
-                         dtau_lambda=0.0, precision=1, adjoint=0, conv=0, check_ends=0, symmetry=0, s_transform=0, reserved=0)
+                         dtau_lambda=0.0, precision=1, adjoint=0, conv=0, check_ends=0, symmetry=0, s_transform=0, launch=0)
     dummy = torch.zeros(2, dtype=torch.float64, device="cuda")
     st = lib.ks_cost_noalloc(ctypes.byref(p), ctypes.c_void_p(dummy.data_ptr()), ctypes.c_void_p(dummy.data_ptr()),
                              None)
