@@ -589,33 +589,37 @@ __global__ void __launch_bounds__(DT_THREADS) k_dt_batch(const CurveDev *cv, con
 template <typename T>
 __global__ void k_setup_fft(CurveDev c)
 {
-    const int F = c.F, P = c.P;
-    cpx<T> *ftw = (cpx<T> *)c.ftw, *chat = (cpx<T> *)c.chat;
-    const T *cot = (const T *)c.cot;
-    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < F; k += gridDim.x * blockDim.x) {
-        {
-            double s, co;
-            sincospi(2.0 * (double)k / (double)F, &s, &co);
-            ftw[k] = {(T)co, (T)(-s)};
-        }
-        // cot values in FP64 again (the stored table is in the storage type)
-        double re = 0.0, im = 0.0;
-        for (int t = -(2 * P - 1); t <= P; ++t) {
-            const int u = (t % (2 * P) + 2 * P) % (2 * P);
-            if (u == 0) continue;
-            double sn, cs;
-            sincospi((double)u / (2.0 * P), &sn, &cs);
-            const double cv = cs / sn;
-            const int idx = t >= 0 ? t : F + t;
-            const long long ph = ((long long)k * idx) % F;
-            double ps, pc;
-            sincospi(2.0 * (double)ph / (double)F, &ps, &pc);
-            re += cv * pc;
-            im -= cv * ps;
-        }
-        chat[k] = {(T)(re / F), (T)(im / F)};
+    // FP64 tables per CTA: e^{-2 pi i p / F} (p < F) and cot(pi u / 2P) (u < 2P)
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int F = c.F, P = c.P, twoP = 2 * P;
+    double2 *w64 = (double2 *)smem_raw;
+    double *cot64 = (double *)(w64 + F);
+    for (int p = threadIdx.x; p < F; p += blockDim.x) {
+        double ps, pc;
+        sincospi(2.0 * (double)p / (double)F, &ps, &pc);
+        w64[p] = make_double2(pc, ps);
     }
-    (void)cot;
+    for (int u = threadIdx.x; u < twoP; u += blockDim.x) {
+        double sn, cs;
+        sincospi((double)u / (2.0 * P), &sn, &cs);
+        cot64[u] = u ? cs / sn : 0.0;
+    }
+    __syncthreads();
+    cpx<T> *ftw = (cpx<T> *)c.ftw, *chat = (cpx<T> *)c.chat;
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= F) return;
+    ftw[k] = {(T)w64[k].x, (T)(-w64[k].y)};
+    double re = 0.0, im = 0.0;
+    for (int t = -(twoP - 1); t <= P; ++t) {
+        const int u = (t % twoP + twoP) % twoP;
+        if (u == 0) continue;
+        const double cv = cot64[u];
+        const int idx = t >= 0 ? t : F + t;
+        const double2 wv = w64[(int)(((long long)k * idx) % F)];
+        re += cv * wv.x;
+        im -= cv * wv.y;
+    }
+    chat[k] = {(T)(re / F), (T)(im / F)};
 }
 
 // ---- bulk copy global -> shared through an mbarrier (the copy engine; no
@@ -1014,9 +1018,15 @@ cudaError_t launch_setup(const CurveDev &c, double dtau, cudaStream_t st)
     else k_setup<double><<<grid, 256, 0, st>>>(c, dtau);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess || c.F == 0) return e;
-    const int g2 = (c.F + 127) / 128;
-    if (c.prec) k_setup_fft<float><<<g2, 128, 0, st>>>(c);
-    else k_setup_fft<double><<<g2, 128, 0, st>>>(c);
+    const int g2 = (c.F + 255) / 256;
+    const size_t sm = (size_t)c.F * sizeof(double2) + (size_t)2 * c.P * sizeof(double);
+    if (c.prec) {
+        if ((e = set_smem(k_setup_fft<float>, sm)) != cudaSuccess) return e;
+        k_setup_fft<float><<<g2, 256, sm, st>>>(c);
+    } else {
+        if ((e = set_smem(k_setup_fft<double>, sm)) != cudaSuccess) return e;
+        k_setup_fft<double><<<g2, 256, sm, st>>>(c);
+    }
     return cudaGetLastError();
 }
 
