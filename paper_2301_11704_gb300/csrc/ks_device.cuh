@@ -158,37 +158,39 @@ __device__ __forceinline__ double block_sum(double v, double *red)
 // fixed order: J^2, J_arc, dJ^2/dl, |l d|_W, the end-section residuals, and
 // (step mode) the convergence decision and the next lambda.
 // FP64 reduction of the row phase over the per-unit partial sums c.bpart[0..nblk)
-// in a fixed order, the scalars derived from them (J^2, J_arc, dJ^2/dl, |l d|_W,
-// the end-section residuals) and, in step mode, the convergence decision and the
-// next lambda.  Called by every thread of a CTA of WARPS warps; thread 0 writes
-// the curve's scalars when `write`.  Returns to every thread 1 when the descent
-// goes on (always 1 in evaluation mode).
-template <int WARPS>
+// in a fixed order (strided per thread, then a shuffle tree per warp, then the
+// warps in order), the scalars derived from them (J^2, J_arc, dJ^2/dl, |l d|_W,
+// the end-section residuals) and, in step mode, the convergence decision and
+// the next lambda.  Called by every thread of a CTA of NT threads; thread 0
+// writes the curve's scalars when `write`.  Returns to every thread 1 when the
+// descent goes on (always 1 in evaluation mode).
+template <int NT>
 __device__ __forceinline__ int rows_finish(const CurveDev &c, int mode, int nblk, bool write)
 {
-    __shared__ double red5[5][WARPS * 32];
+    __shared__ double wred[NT / 32][5];
     __shared__ int go;
     DevScalars *sc = c.sc;
-    const int P = c.P;
+    const int P = c.P, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     double t[5] = {0, 0, 0, 0, 0};
-    for (int b = threadIdx.x; b < nblk; b += blockDim.x)
+    for (int b = threadIdx.x; b < nblk; b += NT)
 #pragma unroll
         for (int q = 0; q < 5; ++q) t[q] += __ldcg(c.bpart + (size_t)b * 5 + q);
 #pragma unroll
-    for (int q = 0; q < 5; ++q) red5[q][threadIdx.x] = t[q];
-    __syncthreads();
-    for (int sidx = WARPS * 16; sidx > 0; sidx >>= 1) {
-        if ((int)threadIdx.x < sidx)
-#pragma unroll
-            for (int q = 0; q < 5; ++q) red5[q][threadIdx.x] += red5[q][threadIdx.x + sidx];
-        __syncthreads();
+    for (int q = 0; q < 5; ++q) {
+        t[q] = warp_sum(t[q]);
+        if (lane == 0) wred[warp][q] = t[q];
     }
+    __syncthreads();
     if (threadIdx.x == 0) {
+        double r[5] = {0, 0, 0, 0, 0};
+        for (int w = 0; w < NT / 32; ++w)
+#pragma unroll
+            for (int q = 0; q < 5; ++q) r[q] += wred[w][q];
         const double lamd = sc->lambda, tol = sc->tol, dtl = sc->dtau_lambda;
         const int conv = sc->conv, lfree = sc->lambda_free;
         const double u2p = __ldcg(c.rowsc + 0), f2p = __ldcg(c.rowsc + 3);
         const double u2m = __ldcg(c.rowsc + 4 * (size_t)P + 0), f2m = __ldcg(c.rowsc + 4 * (size_t)P + 3);
-        const double t_j2 = red5[0][0], t_num = red5[1][0], t_den = red5[2][0], t_dl = red5[3][0], t_d2 = red5[4][0];
+        const double t_j2 = r[0], t_num = r[1], t_den = r[2], t_dl = r[3], t_d2 = r[4];
         const double Jarc = t_den > 0 ? t_num / t_den : 0.0, dJdl = -2.0 * t_dl, Dnorm = sqrt(t_d2);
         int active = 1;
         if (write) {
@@ -227,8 +229,8 @@ __device__ __forceinline__ int rows_finish(const CurveDev &c, int mode, int nblk
     return go;
 }
 
-template <typename T, int N, int WARPS = ROWS_WARPS, bool TAIL = true>
-__device__ __forceinline__ void rows_body(const CurveDev &c, int mode, int blk, int nblk)
+template <typename T, int N, int WARPS = ROWS_WARPS>
+__device__ __forceinline__ void rows_body(const CurveDev &c, int mode, int blk, int nblk, bool tail)
 {
     constexpr int H = N / 2;
     constexpr int MPL = (H + 31) / 32;
@@ -413,7 +415,7 @@ __device__ __forceinline__ void rows_body(const CurveDev &c, int mode, int blk, 
         c.bpart[(size_t)blk * 5 + threadIdx.x] = t;
     }
 
-    if (!TAIL) return;
+    if (!tail) return;
 
     // ---- last CTA: the FP64 reduction over the CTAs' partial sums
     __threadfence();
@@ -425,7 +427,7 @@ __device__ __forceinline__ void rows_body(const CurveDev &c, int mode, int blk, 
     __syncthreads();
     if (!am_last) return;
     __threadfence();
-    rows_finish<WARPS>(c, mode, nblk, true);
+    rows_finish<WARPS * 32>(c, mode, nblk, true);
 }
 
 // ---------------------------------------------------------------------------

@@ -369,7 +369,7 @@ __global__ void __launch_bounds__(ROWS_WARPS * 32) k_row_inv(CurveDev c, const T
 template <typename T, int N>
 __global__ void __launch_bounds__(ROWS_WARPS * 32) k_rows(CurveDev c, int mode)
 {
-    rows_body<T, N>(c, mode, blockIdx.x, gridDim.x);
+    rows_body<T, N>(c, mode, blockIdx.x, gridDim.x, true);
 }
 
 // Batched row phase: work item (curve, row block) per CTA; every curve keeps its
@@ -379,7 +379,7 @@ __global__ void __launch_bounds__(ROWS_WARPS * 32) k_rows_batch(const CurveDev *
 {
     const int2 it = items[blockIdx.x];
     const CurveDev &c = cv[it.x];
-    rows_body<T, N>(c, mode, it.y, c.row_blocks);
+    rows_body<T, N>(c, mode, it.y, c.row_blocks, true);
 }
 
 // ---------------------------------------------------------------------------

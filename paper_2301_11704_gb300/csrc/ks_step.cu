@@ -191,13 +191,13 @@ __global__ void __launch_bounds__(PS_THREADS) k_step(CurveDev c, int discrete, l
         __syncthreads();
         if (!gate_s) break;
         for (int u = blockIdx.x; u < nru; u += gridDim.x) {
-            rows_body<T, N, PS_WARPS, false>(c, ROWS_STEP, u, nru);
+            rows_body<T, N, PS_WARPS>(c, ROWS_STEP, u, nru, false);
             __syncthreads();
         }
         if (!gb.sync()) return;
         // every CTA reduces the units' partial sums in the same fixed order and
         // takes the same convergence decision; CTA 0 records the scalars
-        if (!rows_finish<PS_WARPS>(c, ROWS_STEP, nru, blockIdx.x == 0)) break;
+        if (!rows_finish<PS_THREADS>(c, ROWS_STEP, nru, blockIdx.x == 0)) break;
         const double lam = *(volatile double *)&sc->lambda, dtau = *(volatile double *)&sc->dtau;
 
         for (int u = blockIdx.x; u < ndt; u += gridDim.x) dt_partial<T, BN>(c, GM_UPDATE, discrete, u, sm);
