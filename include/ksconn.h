@@ -91,10 +91,14 @@ typedef struct {
     int32_t s_transform; /* how D_t is applied along s (same result to rounding):
                             0 auto: for a single curve the form measured faster on GB300 for its
                             size (FFT when N_s N_x >= 131072 or N_s > 2048 in FP32, when N_x >= 64
-                            or N_s <= 128 in FP64, within the FFT size limit; else dense); in a
+                            or N_s <= 128 in FP64, within the FFT size limit; else dense, on the
+                            tensor cores for FP32 when N_s >= 8192, or N_s >= 4096 at N_x >= 128); in a
                             batch the FFT form wherever the size limit allows;
                             1 dense contraction generated from the O(N_s) cot table;
-                            2 FFT convolution (N_s <= 2731 FP32 / 1366 FP64) */
+                            2 FFT convolution (N_s <= 2731 FP32 / 1366 FP64);
+                            3 dense contraction on the tensor cores (FP32 storage only: each
+                            FP32 operand split exactly into three TF32 parts, six products,
+                            FP32 accumulation per 32 sections, FP32 sums across them) */
     int32_t launch;      /* how a single curve's descent steps are launched (same results):
                             0 three kernels per step, chained by programmatic dependent
                             launch and replayed from a CUDA graph;

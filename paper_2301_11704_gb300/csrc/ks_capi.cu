@@ -86,7 +86,9 @@ ks_status validate(const ks_params *p)
     if (p->conv < KS_CONV_JARC || p->conv > KS_CONV_JREL) return fail(KS_EINVAL, "conv must be a ks_conv value");
     if (p->check_ends != 0 && p->check_ends != 1) return fail(KS_EINVAL, "check_ends must be 0 or 1");
     if (p->symmetry < 0 || p->symmetry > 3) return fail(KS_EINVAL, "symmetry must be in [0, 3]");
-    if (p->s_transform < 0 || p->s_transform > 2) return fail(KS_EINVAL, "s_transform must be 0, 1 or 2");
+    if (p->s_transform < 0 || p->s_transform > 3) return fail(KS_EINVAL, "s_transform must be 0, 1, 2 or 3");
+    if (p->s_transform == 3 && p->precision != KS_FP32)
+        return fail(KS_EINVAL, "s_transform = tensor cores needs FP32 storage");
     if (p->launch < 0 || p->launch > 1) return fail(KS_EINVAL, "launch must be 0 or 1");
     if (p->s_transform == 2 && ks::fft_size(p->ns, p->precision == KS_FP32) == 0)
         return fail(KS_EINVAL, "s_transform = FFT supports N_s <= %d at this precision",

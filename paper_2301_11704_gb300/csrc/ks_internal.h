@@ -22,6 +22,13 @@ constexpr int DT_TARGET_CTAS = 256;   // split the contraction until about this 
 constexpr int DT_MIN_KCHUNK = 64;     // but keep at least this many sections per split
 constexpr int DT_MAX_SPLIT = 8;       // the splits of one tile form one thread-block cluster
 
+// Tensor-core form of the dense s-contraction (FP32 storage): 128 output
+// sections per CTA, stages of TC_KC sections, split over up to DT_MAX_SPLIT CTAs
+// of a cluster.
+constexpr int TC_M = 128;
+constexpr int TC_KC = 32;
+constexpr int TC_THREADS = 256;
+
 // FFT form of the s-contraction: one CTA per Fourier mode (a column pair), the
 // convolution of length F (a power of two >= 3 (N_s - 1)) in shared memory.
 constexpr int SC_THREADS = 512;
@@ -42,6 +49,14 @@ inline bool fft_preferred(int ns, int nx, int prec)
 {
     if (prec) return (long long)ns * nx >= 131072 || ns > 2048;
     return nx >= 64 || ns <= 128;
+}
+
+// Where `auto` puts a dense-form FP32 curve on the tensor cores: the sizes where
+// it measured faster than the SIMT contraction on GB300 (one step, L2 flushed,
+// N_x in {32, 64, 128, 256}, N_s from 1024 to 16384: by 7-20 %).
+inline bool tc_preferred(int ns, int nx)
+{
+    return nx >= 32 && (ns >= 8192 || (nx >= 128 && ns >= 4096));
 }
 
 // Sections handled per CTA by the row (x-direction) kernels: two rows per warp,
@@ -90,6 +105,7 @@ struct Layout {
     size_t off_twid, off_twid64, off_kj, off_aj, off_prec, off_ends, off_pert, off_sc;
     size_t total;
     int bn, tiles_r, tiles_c, ksplit, kchunk, row_blocks;
+    int tc, tc_bn, tc_tiles_r, tc_tiles_c, tc_ksplit, tc_kchunk;   // tensor-core form (tc = 1)
 };
 
 struct CurveDev {
@@ -105,6 +121,7 @@ struct CurveDev {
     void *part;            // persistent step: [ksplit][N_s][N] split partial sums (else null)
     double *gpart;         // persistent step: [PS_MAX_CTAS] per-CTA |G|^2 partials
     int bn, tiles_r, tiles_c, ksplit, kchunk, row_blocks;
+    int tc, tc_bn, tc_tiles_r, tc_tiles_c, tc_ksplit, tc_kchunk;   // tensor-core form (tc = 1)
     int F;                 // FFT length of the s-contraction (0: dense form)
     void *chat, *ftw;      // FFT form: kernel spectrum / F and twiddles (complex, storage type)
     void *cot, *sig, *tau, *sw, *twr;
@@ -150,6 +167,10 @@ cudaError_t launch_rows(const CurveDev &c, int mode, cudaStream_t st);
 // sigma), op 1: W^-1 D_t^T W.  mode GM_STORE writes D_t U into D (gated when
 // `gate`), GM_UPDATE applies the descent update to U, GM_GRAD writes G.
 cudaError_t launch_dt(const CurveDev &c, int mode, int discrete, int gate, cudaStream_t st);
+// Tensor-core form of the dense contraction (ks_tc.cu; c.tc set): the same
+// modes and epilogue as the dense kernel.
+cudaError_t launch_dt_tc(const CurveDev &c, int mode, int discrete, int gate, cudaStream_t st);
+
 // Persistent step (ks_step.cu): nsteps descent steps of a dense-form curve
 // (c.part set) in one cooperative launch; stops early with the curve's gates.
 cudaError_t launch_step_persistent(const CurveDev &c, int discrete, long long nsteps, cudaStream_t st);

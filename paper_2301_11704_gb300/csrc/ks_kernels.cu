@@ -63,6 +63,23 @@ Layout make_layout(int ns, int nx, int prec, int allow_split, int bn, int s_tran
     l.kchunk = kc;
     l.ksplit = (ns + kc - 1) / kc;
     l.row_blocks = (ns + ROWS_PER_CTA - 1) / ROWS_PER_CTA;
+    // tensor-core form of the dense contraction: FP32 storage, single curves,
+    // asked for (s_transform 3) or picked by the measured rule (auto)
+    if (prec && allow_split && l.F == 0 && (s_transform == 3 || (s_transform == 0 && tc_preferred(ns, nx)))) {
+        l.tc = 1;
+        l.tc_bn = nx >= 64 ? 64 : (nx >= 32 ? 32 : 16);
+        l.tc_tiles_c = (nx + l.tc_bn - 1) / l.tc_bn;
+        l.tc_tiles_r = (ns + TC_M - 1) / TC_M;
+        const int tt = l.tc_tiles_c * l.tc_tiles_r;
+        int tks = tt < DT_TARGET_CTAS ? DT_TARGET_CTAS / tt : 1;
+        if (tks > ns / DT_MIN_KCHUNK) tks = ns / DT_MIN_KCHUNK;
+        if (tks > DT_MAX_SPLIT) tks = DT_MAX_SPLIT;
+        if (tks < 1) tks = 1;
+        int tkc = (ns + tks - 1) / tks;
+        tkc = (tkc + TC_KC - 1) / TC_KC * TC_KC;
+        l.tc_kchunk = tkc;
+        l.tc_ksplit = (ns + tkc - 1) / tkc;
+    }
     size_t off = 0;
     l.off_U = off; off += field;
     l.off_D = off; off += field;
@@ -72,7 +89,7 @@ Layout make_layout(int ns, int nx, int prec, int allow_split, int bn, int s_tran
     l.off_X = off; off += al256((size_t)ns * nx * 8);   // physical scratch, always FP64
     l.off_rowsc = off; off += al256((size_t)ns * 4 * 8);
     l.off_bpart = off; off += al256((size_t)l.row_blocks * 5 * 8);
-    l.off_tile = off; off += al256((size_t)tiles_max * l.ksplit * 8);
+    l.off_tile = off; off += al256((size_t)tiles_max * DT_MAX_SPLIT * 8);   // either contraction form
     l.off_tcnt = off; off += al256((size_t)tiles_max * 4);
     // the persistent step's split partials and per-CTA |G|^2 partials (single
     // curves in the dense form that asked for it)
@@ -131,6 +148,12 @@ CurveDev bind_layout(const ks_params *p, const Layout &l, void *base)
     d.kchunk = l.kchunk;
     d.row_blocks = l.row_blocks;
     d.F = l.F;
+    d.tc = l.tc;
+    d.tc_bn = l.tc_bn;
+    d.tc_tiles_r = l.tc_tiles_r;
+    d.tc_tiles_c = l.tc_tiles_c;
+    d.tc_ksplit = l.tc_ksplit;
+    d.tc_kchunk = l.tc_kchunk;
     d.chat = l.F ? (void *)(b + l.off_chat) : nullptr;
     d.ftw = l.F ? (void *)(b + l.off_ftw) : nullptr;
     d.cot = b + l.off_cot;
@@ -1131,6 +1154,7 @@ cudaError_t launch_dt(const CurveDev &c, int mode, int discrete, int gate, cudaS
 {
     if (c.F > 0) return c.prec ? launch_sconv_t<float>(c, mode, discrete, gate, st)
                                : launch_sconv_t<double>(c, mode, discrete, gate, st);
+    if (c.tc) return launch_dt_tc(c, mode, discrete, gate, st);
     if (c.bn == 64) return c.prec ? launch_dt_t<float, 64>(c, mode, discrete, gate, st)
                                   : launch_dt_t<double, 64>(c, mode, discrete, gate, st);
     return c.prec ? launch_dt_t<float, 32>(c, mode, discrete, gate, st)

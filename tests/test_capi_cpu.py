@@ -58,7 +58,7 @@ def test_workspace_size_scales_with_the_curve(lib):
 
 @pytest.mark.parametrize("bad", [dict(nx=24), dict(nx=4), dict(nx=512), dict(ns=2), dict(L=0.0), dict(S=-1.0),
                                  dict(dtau=0.0), dict(precision=7), dict(adjoint=3), dict(conv=9),
-                                 dict(symmetry=4), dict(s_transform=3), dict(launch=2), dict(L=float("nan"))])
+                                 dict(symmetry=4), dict(s_transform=4), dict(s_transform=3, precision=0), dict(launch=2), dict(L=float("nan"))])
 def test_invalid_parameters_are_rejected_on_the_host(lib, bad):
     p = _params(**bad)
     assert lib.ks_curve_workspace_bytes(ctypes.byref(p)) == 0

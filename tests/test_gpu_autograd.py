@@ -82,8 +82,11 @@ def test_gradient_matches_finite_differences(setup):
     cost.curve.close()
 
 
-@pytest.mark.parametrize("precision,tol", [("fp64", 1e-10), ("fp32", 1e-5)])
-def test_gradient_matches_the_oracle(setup, precision, tol):
+# J within 1e-5 in FP32; the FP32 gradient, compared in the preconditioned norm,
+# within 5e-5 (about 400 FP32 ulps: its floor depends on the contraction form,
+# 3e-6 to 2e-5 measured at this size for the SIMT, FFT and tensor-core forms)
+@pytest.mark.parametrize("precision,tol,gtol", [("fp64", 1e-10, 1e-10), ("fp32", 1e-5, 5e-5)])
+def test_gradient_matches_the_oracle(setup, precision, tol, gtol):
     spec, up, um, U, X = setup
     dt = torch.float64 if precision == "fp64" else torch.float32
     if precision == "fp32":
@@ -98,7 +101,7 @@ def test_gradient_matches_the_oracle(setup, precision, tol):
     J2 = cost(u, lam)
     assert abs(J2.item() - sc["J2"]) <= tol * sc["J2"]
     J2.backward()
-    assert _precond_rel(u.grad.double().cpu().numpy(), G, w, spec) < tol
+    assert _precond_rel(u.grad.double().cpu().numpy(), G, w, spec) < gtol
     assert abs(lam.grad.item() - sc["dJ2_dlambda"]) <= tol * abs(sc["dJ2_dlambda"])
     cost.curve.close()
 
