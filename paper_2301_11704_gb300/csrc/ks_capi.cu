@@ -90,9 +90,9 @@ ks_status validate(const ks_params *p)
     if (p->s_transform == 3 && p->precision != KS_FP32)
         return fail(KS_EINVAL, "s_transform = tensor cores needs FP32 storage");
     if (p->launch < 0 || p->launch > 1) return fail(KS_EINVAL, "launch must be 0 or 1");
-    if (p->s_transform == 2 && ks::fft_size(p->ns, p->precision == KS_FP32) == 0)
-        return fail(KS_EINVAL, "s_transform = FFT supports N_s <= %d at this precision",
-                    p->precision == KS_FP32 ? 2731 : 1366);
+    if (p->s_transform == 2 && ks::fft_size(p->ns, p->precision == KS_FP32) == 0 &&
+        ks::fft4_size(p->ns, p->precision == KS_FP32) == 0)
+        return fail(KS_EINVAL, "s_transform = FFT supports N_s <= %d", ks::F4_FMAX / 3 + 1);
     return KS_OK;
 }
 

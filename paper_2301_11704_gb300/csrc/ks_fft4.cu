@@ -1,0 +1,352 @@
+// ks_fft4.cu -- the FFT form of the s-contraction for transforms longer than one
+// CTA's shared memory holds (Ashtari & Schneider, arXiv 2301.11704, eq.
+// rational_diff_matrix, Sec. V.C.1; the convolution identity is stated beside
+// the single-CTA form in ks_kernels.cu):
+//
+//   y = IFFT_F( FFT_F(c_F) / F * FFT_F(z) )[0..P],   F = F1 F2 (powers of two <= 256)
+//
+// with the index maps n = F2 n1 + n2 and k = k1 + F1 k2, so that
+//   FFT:  Z[k1 + F1 k2] = sum_n2 W_F2^(n2 k2) W_F^(n2 k1) sum_n1 W_F1^(n1 k1) z[F2 n1 + n2]
+//   IFFT: x[F2 n1 + n2] = sum_k1 W_F1^(-n1 k1) W_F^(-n2 k1) sum_k2 W_F2^(-n2 k2) X[k1 + F1 k2]
+// (W_L = e^(-2 pi i / L)).  Three passes per Fourier mode (the mode's two real
+// columns packed as one complex sequence), one warp per line transform:
+//   pass 1 (per n2): z from the columns, FFT over n1, times W_F^(n2 k1), stored
+//          transposed as S[k1][n2] (staged through shared memory);
+//   pass 2 (per k1): FFT over n2, times the kernel spectrum (kept in the same
+//          [k1][k2] order: no transposes), IFFT over k2, times W_F^(-n2 k1);
+//   pass 3 (per n2): IFFT over k1 -> y at j = F2 n1 + n2 <= P, and the epilogue
+//          of the single-CTA form (store D_t u; or G, the semi-implicit
+//          increment and the FP64 |G|^2 with its last-CTA sum).
+#include <cmath>
+
+#include "ks_device.cuh"
+
+namespace ks {
+
+namespace {
+
+constexpr int F4W = F4_THREADS / 32;   // lines per CTA
+
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, size_t smem, cudaStream_t st, Args... args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = dim3(F4_THREADS);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaError_t e = cudaLaunchKernelEx(&cfg, kern, args...);
+    if (e != cudaSuccess) return e;
+    return cudaGetLastError();
+}
+
+template <typename T>
+struct V2of;
+template <> struct V2of<float> { using type = float2; };
+template <> struct V2of<double> { using type = double2; };
+
+// Shared memory of a pass: the line transform's twiddles, two buffers per warp,
+// and a staging tile of F4W lines for the transposed accesses.
+template <typename T, int L, int LS>
+struct F4Smem {
+    static constexpr size_t TW = L / 2, BUF = (size_t)2 * F4W * L, STAGE = (size_t)F4W * (LS + 1);
+    static constexpr size_t BYTES = (TW + BUF + STAGE) * sizeof(cpx<T>);
+};
+
+}  // namespace
+
+// ---- pass 1: lines over n1 (length F1), one per n2
+template <typename T, int F1, int F2>
+__global__ void __launch_bounds__(F4_THREADS) k_f4_p1(CurveDev c, int mode, int discrete, int gate)
+{
+    using V2 = typename V2of<T>::type;
+    using Sm = F4Smem<T, F1, F1>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    cpx<T> *tw = (cpx<T> *)smem_raw, *buf = tw + Sm::TW, *stage = buf + Sm::BUF;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, jm = blockIdx.y;
+    const int n2 = blockIdx.x * F4W + warp;
+    const cpx<T> *ftw = (const cpx<T> *)c.ftw;
+    for (int t = threadIdx.x; t < F1 / 2; t += F4_THREADS) tw[t] = ftw[t * F2];   // W_F1^t
+    pdl_wait();
+    if (gate && !c.sc->active) return;
+
+    const int P = c.P, N = c.nx;
+    const T *X = (const T *)(mode == GM_STORE ? c.U : c.R);
+    const T *colscale = (const T *)(discrete ? c.sw : c.tau);
+    const T s = discrete ? T(-1) : T(1);
+    const int ca = 2 * jm, cb = 2 * jm + 1;
+    const bool oka = col_allowed(ca, c.sym), okb = col_allowed(cb, c.sym) && jm != 0;
+    cpx<T> *x = buf + (size_t)warp * 2 * F1, *y = x + F1;
+    // z[F2 n1 + n2]: the symmetric extension of the scaled columns (as in the single-CTA form)
+#pragma unroll
+    for (int n1 = lane; n1 < F1; n1 += 32) {
+        const int k = F2 * n1 + n2;
+        int m = -1;
+        T f = T(1);
+        if (k == 0) { m = 0; f = T(1) + s; }
+        else if (k < P) { m = k; f = s; }
+        else if (k == P) { m = P; f = T(1) + s; }
+        else if (k < 2 * P) { m = 2 * P - k; }
+        cpx<T> v = {0, 0};
+        if (m >= 0 && f != T(0)) {
+            const T cs = f * colscale[m];
+            const V2 xv = *reinterpret_cast<const V2 *>(X + (size_t)m * N + ca);
+            v.x = oka ? cs * xv.x : T(0);
+            v.y = okb ? cs * xv.y : T(0);
+        }
+        x[n1] = v;
+    }
+    __syncwarp();
+    __syncthreads();   // twiddles
+    cpx<T> *Y = warp_fft<T, F1>(x, y, tw, false, lane);
+    // times W_F^(n2 k1), into the staging tile [line][k1]
+#pragma unroll
+    for (int k1 = lane; k1 < F1; k1 += 32) stage[(size_t)warp * (F1 + 1) + k1] = cmul(Y[k1], ftw[n2 * k1]);
+    __syncthreads();
+    // S[jm][k1][n2]: F4W consecutive n2 per k1
+    cpx<T> *S = (cpx<T> *)c.f4s + (size_t)jm * F1 * F2;
+    for (int e = threadIdx.x; e < F4W * F1; e += F4_THREADS) {
+        const int k1 = e / F4W, w = e % F4W;
+        S[(size_t)k1 * F2 + blockIdx.x * F4W + w] = stage[(size_t)w * (F1 + 1) + k1];
+    }
+}
+
+// ---- pass 2: lines over n2 (length F2), one per k1: FFT, spectrum, IFFT
+template <typename T, int F1, int F2>
+__global__ void __launch_bounds__(F4_THREADS) k_f4_p2(CurveDev c, int gate)
+{
+    using Sm = F4Smem<T, F2, F2>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    cpx<T> *tw = (cpx<T> *)smem_raw, *buf = tw + Sm::TW;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, jm = blockIdx.y;
+    const int k1 = blockIdx.x * F4W + warp;
+    const cpx<T> *ftw = (const cpx<T> *)c.ftw, *chat = (const cpx<T> *)c.chat + (size_t)k1 * F2;
+    for (int t = threadIdx.x; t < F2 / 2; t += F4_THREADS) tw[t] = ftw[t * F1];   // W_F2^t
+    pdl_wait();
+    if (gate && !c.sc->active) return;
+
+    cpx<T> *S = (cpx<T> *)c.f4s + ((size_t)jm * F1 + k1) * F2;
+    cpx<T> *x = buf + (size_t)warp * 2 * F2, *y = x + F2;
+#pragma unroll
+    for (int n2 = lane; n2 < F2; n2 += 32) x[n2] = S[n2];
+    __syncwarp();
+    __syncthreads();   // twiddles
+    cpx<T> *Z = warp_fft<T, F2>(x, y, tw, false, lane);
+    cpx<T> *O = (Z == x) ? y : x;
+#pragma unroll
+    for (int k2 = lane; k2 < F2; k2 += 32) Z[k2] = cmul(Z[k2], chat[k2]);
+    __syncwarp();
+    cpx<T> *V = warp_fft<T, F2>(Z, O, tw, true, lane);
+#pragma unroll
+    for (int n2 = lane; n2 < F2; n2 += 32) {
+        cpx<T> w = ftw[n2 * k1];
+        w.y = -w.y;
+        S[n2] = cmul(V[n2], w);
+    }
+}
+
+// ---- pass 3: lines over k1 (length F1), one per n2: IFFT and the epilogue
+template <typename T, int F1, int F2>
+__global__ void __launch_bounds__(F4_THREADS) k_f4_p3(CurveDev c, int mode, int discrete, int gate)
+{
+    using V2 = typename V2of<T>::type;
+    using Sm = F4Smem<T, F1, F1>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    cpx<T> *tw = (cpx<T> *)smem_raw, *buf = tw + Sm::TW, *stage = buf + Sm::BUF;
+    __shared__ double wsum[F4W];
+    __shared__ double red[F4_THREADS];
+    __shared__ int am_last;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, jm = blockIdx.y;
+    const int n2 = blockIdx.x * F4W + warp;
+    const cpx<T> *ftw = (const cpx<T> *)c.ftw;
+    for (int t = threadIdx.x; t < F1 / 2; t += F4_THREADS) tw[t] = ftw[t * F2];   // W_F1^t
+    DevScalars *sc = c.sc;
+    pdl_wait();
+    if (gate && !sc->active) return;
+    const double lam_d = sc->lambda, dtau_d = sc->dtau;
+
+    // S[jm][k1][n2] for this CTA's F4W values of n2 -> staging tile [line][k1]
+    const cpx<T> *S = (const cpx<T> *)c.f4s + (size_t)jm * F1 * F2;
+    for (int e = threadIdx.x; e < F4W * F1; e += F4_THREADS) {
+        const int k1 = e / F4W, w = e % F4W;
+        stage[(size_t)w * (F1 + 1) + k1] = S[(size_t)k1 * F2 + blockIdx.x * F4W + w];
+    }
+    __syncthreads();
+    cpx<T> *x = buf + (size_t)warp * 2 * F1, *y = x + F1;
+#pragma unroll
+    for (int k1 = lane; k1 < F1; k1 += 32) x[k1] = stage[(size_t)warp * (F1 + 1) + k1];
+    __syncwarp();
+    cpx<T> *Y = warp_fft<T, F1>(x, y, tw, true, lane);
+
+    // epilogue over the sections j = F2 n1 + n2 <= P of the two columns
+    const int ns = c.ns, N = c.nx, P = c.P;
+    const int ca = 2 * jm, cb = 2 * jm + 1;
+    const bool oka = col_allowed(ca, c.sym), okb = col_allowed(cb, c.sym) && jm != 0;
+    const T *rowscale = (const T *)(discrete ? c.twr : c.sig);
+    T *Dout = (T *)c.D, *U = (T *)c.U, *G = (T *)c.G;
+    const T *Ah = (const T *)c.A;
+    const T pr = ((const T *)c.prec_imex)[jm];
+    const T lam = (T)lam_d, dtau = (T)dtau_d;
+    const double cw = (jm == 0) ? 1.0 : 2.0;
+    double partsum = 0.0;
+#pragma unroll
+    for (int n1 = lane; n1 < F1; n1 += 32) {
+        const int j = F2 * n1 + n2;
+        if (j >= ns) continue;
+        const T rs = rowscale[j];
+        const cpx<T> yv = {rs * Y[n1].x, rs * Y[n1].y};
+        const size_t o = (size_t)j * N + ca;
+        if (mode == GM_STORE) {
+            *reinterpret_cast<V2 *>(Dout + o) = V2{oka ? yv.x : T(0), okb ? yv.y : T(0)};
+            continue;
+        }
+        const bool interior = (j > 0 && j < P);
+        T ga = 0, gb = 0;
+        if (interior) {
+            const V2 av = *reinterpret_cast<const V2 *>(Ah + o);
+            if (oka) ga = -(av.x + (discrete ? -lam * yv.x : lam * yv.x));
+            if (okb) gb = -(av.y + (discrete ? -lam * yv.y : lam * yv.y));
+            partsum += c.w[j] * cw * ((double)ga * (double)ga + (double)gb * (double)gb);
+        }
+        if (mode == GM_UPDATE) {
+            if (interior) {
+                const V2 uv = *reinterpret_cast<const V2 *>(U + o);
+                *reinterpret_cast<V2 *>(U + o) = V2{uv.x + dtau * pr * ga, uv.y + dtau * pr * gb};
+            }
+        } else {
+            *reinterpret_cast<V2 *>(G + o) = V2{ga, gb};
+        }
+    }
+    if (mode == GM_STORE) return;
+
+    // ---- FP64 |G|^2: per-CTA partial, last CTA of the grid sums them in a fixed order
+    partsum = warp_sum(partsum);
+    if (lane == 0) wsum[warp] = partsum;
+    __syncthreads();
+    const int bid = jm * gridDim.x + blockIdx.x, nb = gridDim.x * gridDim.y;
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < F4W; ++w) t += wsum[w];
+        c.tile[bid] = t;
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned prev = atomicAdd(&sc->cnt_gemm, 1u);
+        am_last = (prev == (unsigned)nb - 1);
+    }
+    __syncthreads();
+    if (!am_last) return;
+    __threadfence();
+    double t = 0.0;
+    for (int b = threadIdx.x; b < nb; b += F4_THREADS) t += __ldcg(c.tile + b);
+    t = block_sum<F4_THREADS>(t, red);
+    if (threadIdx.x == 0) {
+        sc->G2 = c.L * t;
+        if (mode == GM_UPDATE) {
+            sc->step += 1;
+            sc->tau += sc->dtau;
+            sc->lambda = sc->lambda_next;
+        }
+        sc->cnt_gemm = 0;
+    }
+}
+
+// ---- set-up: FP64 tables in the scratch buffer, then the twiddles W_F^k and the
+// kernel spectrum FFT(c_F)/F by a direct DFT in FP64 (c_F is real: the upper
+// half of the spectrum is the conjugate of the lower), stored [k1][k2].
+__global__ void k_f4_tables(CurveDev c)
+{
+    const int F = c.F, twoP = 2 * c.P;
+    double2 *w64 = (double2 *)c.f4s;
+    double *cot64 = (double *)(w64 + F);
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < F; p += gridDim.x * blockDim.x) {
+        double sn, cs;
+        sincospi(2.0 * (double)p / (double)F, &sn, &cs);
+        w64[p] = make_double2(cs, sn);
+    }
+    for (int u = blockIdx.x * blockDim.x + threadIdx.x; u < twoP; u += gridDim.x * blockDim.x) {
+        double sn, cs;
+        sincospi((double)u / (double)twoP, &sn, &cs);
+        cot64[u] = u ? cs / sn : 0.0;
+    }
+}
+
+template <typename T>
+__global__ void k_f4_spectrum(CurveDev c)
+{
+    const int F = c.F, P = c.P, twoP = 2 * P, F1 = c.F1, F2 = c.F2;
+    const double2 *w64 = (const double2 *)c.f4s;
+    const double *cot64 = (const double *)(w64 + F);
+    cpx<T> *ftw = (cpx<T> *)c.ftw, *chat = (cpx<T> *)c.chat;
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k > F / 2) return;
+    double re = 0.0, im = 0.0;
+    for (int t = -(twoP - 1); t <= P; ++t) {
+        const int u = (t % twoP + twoP) % twoP;
+        if (u == 0) continue;
+        const double cv = cot64[u];
+        const int idx = t >= 0 ? t : F + t;
+        const double2 wv = w64[(int)(((long long)k * idx) % F)];
+        re += cv * wv.x;
+        im -= cv * wv.y;
+    }
+    // spectrum at k and (conjugate) at F - k, in the [k1][k2] order of the passes
+    chat[(size_t)(k % F1) * F2 + k / F1] = {(T)(re / F), (T)(im / F)};
+    ftw[k] = {(T)w64[k].x, (T)(-w64[k].y)};
+    const int kc = (F - k) % F;
+    if (kc == k) return;
+    chat[(size_t)(kc % F1) * F2 + kc / F1] = {(T)(re / F), (T)(-im / F)};
+    ftw[kc] = {(T)w64[kc].x, (T)(-w64[kc].y)};
+}
+
+// ---- launchers
+template <typename T, int F1, int F2>
+static cudaError_t f4_run(const CurveDev &c, int mode, int discrete, int gate, cudaStream_t st)
+{
+    const int nm = c.nx / 2;
+    const size_t sm1 = F4Smem<T, F1, F1>::BYTES, sm2 = F4Smem<T, F2, F2>::BYTES;
+    cudaError_t e;
+    if ((e = set_smem(k_f4_p1<T, F1, F2>, sm1)) != cudaSuccess) return e;
+    if ((e = set_smem(k_f4_p2<T, F1, F2>, sm2)) != cudaSuccess) return e;
+    if ((e = set_smem(k_f4_p3<T, F1, F2>, sm1)) != cudaSuccess) return e;
+    if ((e = launch_pdl(k_f4_p1<T, F1, F2>, dim3(F2 / F4W, nm), sm1, st, c, mode, discrete, gate)) != cudaSuccess)
+        return e;
+    if ((e = launch_pdl(k_f4_p2<T, F1, F2>, dim3(F1 / F4W, nm), sm2, st, c, gate)) != cudaSuccess) return e;
+    return launch_pdl(k_f4_p3<T, F1, F2>, dim3(F2 / F4W, nm), sm1, st, c, mode, discrete, gate);
+}
+
+template <typename T>
+static cudaError_t f4_dispatch(const CurveDev &c, int mode, int discrete, int gate, cudaStream_t st)
+{
+    if (c.F1 == 128 && c.F2 == 64) return f4_run<T, 128, 64>(c, mode, discrete, gate, st);
+    if (c.F1 == 128 && c.F2 == 128) return f4_run<T, 128, 128>(c, mode, discrete, gate, st);
+    if (c.F1 == 256 && c.F2 == 128) return f4_run<T, 256, 128>(c, mode, discrete, gate, st);
+    if (c.F1 == 256 && c.F2 == 256) return f4_run<T, 256, 256>(c, mode, discrete, gate, st);
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_f4(const CurveDev &c, int mode, int discrete, int gate, cudaStream_t st)
+{
+    return c.prec ? f4_dispatch<float>(c, mode, discrete, gate, st) : f4_dispatch<double>(c, mode, discrete, gate, st);
+}
+
+cudaError_t launch_setup_f4(const CurveDev &c, cudaStream_t st)
+{
+    // the FP64 tables (16 F + 16 P bytes) fit the scratch buffer (at least 8 F bytes
+    // per mode, N/2 >= 4 modes, P < F / 3)
+    k_f4_tables<<<(c.F + 255) / 256, 256, 0, st>>>(c);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const int g = (c.F / 2 + 1 + 255) / 256;
+    if (c.prec) k_f4_spectrum<float><<<g, 256, 0, st>>>(c);
+    else k_f4_spectrum<double><<<g, 256, 0, st>>>(c);
+    return cudaGetLastError();
+}
+
+}  // namespace ks

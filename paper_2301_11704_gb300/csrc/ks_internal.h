@@ -42,6 +42,18 @@ inline int fft_size(int ns, int prec)
     return F <= (prec ? SC_FMAX_F32 : SC_FMAX_F64) ? F : 0;
 }
 
+// Four-step form for longer transforms (single curves): F = F1 F2 with line
+// FFTs of F1, F2 <= 256 points by one warp each and one pass through a scratch
+// buffer in between; up to F4_FMAX.
+constexpr int F4_FMAX = 65536;
+constexpr int F4_THREADS = 256;           // 8 warps, one line each
+inline int fft4_size(int ns, int prec)
+{
+    int F = 16;
+    while (F < 3 * (ns - 1)) F <<= 1;
+    return (F > (prec ? SC_FMAX_F32 : SC_FMAX_F64) && F <= F4_FMAX) ? F : 0;
+}
+
 // Form that `auto` picks for a single curve: the FFT form where it measured
 // faster than the dense contraction on GB300 (one step of one curve, L2 flushed,
 // N_x in {32, 64, 128, 256}, N_s from 128 to the size limit).
@@ -97,7 +109,8 @@ enum GemmMode { GM_STORE = 0, GM_UPDATE = 1, GM_GRAD = 2 };
 
 // Offsets into the caller's workspace.
 struct Layout {
-    size_t off_chat, off_ftw;          // FFT form: kernel spectrum [F], twiddles [F/2] (complex)
+    size_t off_chat, off_ftw;          // FFT form: kernel spectrum [F], twiddles [F] (complex)
+    size_t off_f4s;                    // four-step form: scratch [N/2][F] (complex)
     int F;                             // 0: dense contraction
     size_t off_U, off_D, off_R, off_A, off_G, off_X;
     size_t off_rowsc, off_bpart, off_tile, off_tcnt, off_part, off_gpart;
@@ -106,6 +119,7 @@ struct Layout {
     size_t total;
     int bn, tiles_r, tiles_c, ksplit, kchunk, row_blocks;
     int tc, tc_bn, tc_tiles_r, tc_tiles_c, tc_ksplit, tc_kchunk;   // tensor-core form (tc = 1)
+    int f4, F1, F2;                    // four-step FFT form (f4 = 1): F = F1 F2
 };
 
 struct CurveDev {
@@ -122,8 +136,11 @@ struct CurveDev {
     double *gpart;         // persistent step: [PS_MAX_CTAS] per-CTA |G|^2 partials
     int bn, tiles_r, tiles_c, ksplit, kchunk, row_blocks;
     int tc, tc_bn, tc_tiles_r, tc_tiles_c, tc_ksplit, tc_kchunk;   // tensor-core form (tc = 1)
+    int f4, F1, F2;                    // four-step FFT form (f4 = 1): F = F1 F2
     int F;                 // FFT length of the s-contraction (0: dense form)
-    void *chat, *ftw;      // FFT form: kernel spectrum / F and twiddles (complex, storage type)
+    void *chat, *ftw;      // FFT form: kernel spectrum / F and twiddles (complex, storage type);
+                           // four-step form: spectrum stored [k1][k2] for k = k1 + F1 k2
+    void *f4s;             // four-step form: scratch [N/2][F1][F2] (complex, storage type)
     void *cot, *sig, *tau, *sw, *twr;
     double *w;
     void *twid, *twid64, *kj, *aj, *prec_imex;
@@ -170,6 +187,11 @@ cudaError_t launch_dt(const CurveDev &c, int mode, int discrete, int gate, cudaS
 // Tensor-core form of the dense contraction (ks_tc.cu; c.tc set): the same
 // modes and epilogue as the dense kernel.
 cudaError_t launch_dt_tc(const CurveDev &c, int mode, int discrete, int gate, cudaStream_t st);
+
+// Four-step FFT form (ks_fft4.cu; c.f4 set): set-up of the kernel spectrum and
+// the s-contraction in the modes of launch_dt.
+cudaError_t launch_setup_f4(const CurveDev &c, cudaStream_t st);
+cudaError_t launch_f4(const CurveDev &c, int mode, int discrete, int gate, cudaStream_t st);
 
 // Persistent step (ks_step.cu): nsteps descent steps of a dense-form curve
 // (c.part set) in one cooperative launch; stops early with the curve's gates.

@@ -45,6 +45,14 @@ Layout make_layout(int ns, int nx, int prec, int allow_split, int bn, int s_tran
     // batched curves the FFT form wherever it fits
     const bool want_fft = s_transform == 2 || (s_transform == 0 && (!allow_split || fft_preferred(ns, nx, prec)));
     l.F = want_fft ? fft_size(ns, prec) : 0;
+    if (want_fft && !l.F && allow_split && fft4_size(ns, prec)) {   // longer: the four-step form
+        l.F = fft4_size(ns, prec);
+        l.f4 = 1;
+        int lg = 0;
+        while ((1 << lg) < l.F) ++lg;
+        l.F1 = 1 << ((lg + 1) / 2);
+        l.F2 = l.F / l.F1;
+    }
     size_t field = al256((size_t)ns * nx * b);
     // tiling and split of the s-contraction
     l.bn = bn ? bn : (nx >= 64 ? 64 : 32);
@@ -89,7 +97,9 @@ Layout make_layout(int ns, int nx, int prec, int allow_split, int bn, int s_tran
     l.off_X = off; off += al256((size_t)ns * nx * 8);   // physical scratch, always FP64
     l.off_rowsc = off; off += al256((size_t)ns * 4 * 8);
     l.off_bpart = off; off += al256((size_t)l.row_blocks * 5 * 8);
-    l.off_tile = off; off += al256((size_t)tiles_max * DT_MAX_SPLIT * 8);   // either contraction form
+    size_t ntile = (size_t)tiles_max * DT_MAX_SPLIT;                   // either contraction form
+    if (l.f4 && ntile < (size_t)(l.F2 / 8) * (nx / 2)) ntile = (size_t)(l.F2 / 8) * (nx / 2);   // four-step CTAs
+    l.off_tile = off; off += al256(ntile * 8);
     l.off_tcnt = off; off += al256((size_t)tiles_max * 4);
     // the persistent step's split partials and per-CTA |G|^2 partials (single
     // curves in the dense form that asked for it)
@@ -113,6 +123,7 @@ Layout make_layout(int ns, int nx, int prec, int allow_split, int bn, int s_tran
     l.off_sc = off; off += al256(sizeof(DevScalars));
     l.off_chat = off; off += l.F ? al256((size_t)l.F * 2 * b) : 0;
     l.off_ftw = off; off += l.F ? al256((size_t)l.F * 2 * b) : 0;
+    l.off_f4s = off; off += l.f4 ? al256((size_t)(nx / 2) * l.F * 2 * b) : 0;
     l.total = off;
     return l;
 }
@@ -156,6 +167,10 @@ CurveDev bind_layout(const ks_params *p, const Layout &l, void *base)
     d.tc_kchunk = l.tc_kchunk;
     d.chat = l.F ? (void *)(b + l.off_chat) : nullptr;
     d.ftw = l.F ? (void *)(b + l.off_ftw) : nullptr;
+    d.f4s = l.f4 ? (void *)(b + l.off_f4s) : nullptr;
+    d.f4 = l.f4;
+    d.F1 = l.F1;
+    d.F2 = l.F2;
     d.cot = b + l.off_cot;
     d.sig = b + l.off_sig;
     d.tau = b + l.off_tau;
@@ -1041,6 +1056,7 @@ cudaError_t launch_setup(const CurveDev &c, double dtau, cudaStream_t st)
     else k_setup<double><<<grid, 256, 0, st>>>(c, dtau);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess || c.F == 0) return e;
+    if (c.f4) return launch_setup_f4(c, st);
     const int g2 = (c.F + 255) / 256;
     const size_t sm = (size_t)c.F * sizeof(double2) + (size_t)2 * c.P * sizeof(double);
     if (c.prec) {
@@ -1152,6 +1168,7 @@ cudaError_t launch_sconv_batch(int prec, int F_max, const CurveDev *cv, const in
 
 cudaError_t launch_dt(const CurveDev &c, int mode, int discrete, int gate, cudaStream_t st)
 {
+    if (c.f4) return launch_f4(c, mode, discrete, gate, st);
     if (c.F > 0) return c.prec ? launch_sconv_t<float>(c, mode, discrete, gate, st)
                                : launch_sconv_t<double>(c, mode, discrete, gate, st);
     if (c.tc) return launch_dt_tc(c, mode, discrete, gate, st);

@@ -53,7 +53,7 @@ def test_workspace_size_scales_with_the_curve(lib):
     assert a > 6 * 128 * 32 * 8 and b > a and c < a
     # linear, not quadratic, in ns
     big = lib.ks_curve_workspace_bytes(ctypes.byref(_params(ns=16384, nx=256)))
-    assert big < 10 * 16384 * 256 * 8
+    assert big < 16 * 16384 * 256 * 8   # fields, FP64 scratch and the four-step scratch (about 4 fields)
 
 
 @pytest.mark.parametrize("bad", [dict(nx=24), dict(nx=4), dict(nx=512), dict(ns=2), dict(L=0.0), dict(S=-1.0),
@@ -93,7 +93,9 @@ def test_null_handle_is_rejected(lib):
     (dict(precision=1, nx=64, ns=1024), 0),                  # FP32, N_s N_x = 65536: dense
     (dict(precision=1, nx=128, ns=1024), 4096),              # FP32, N_s N_x = 131072: FFT, F >= 3 (N_s - 1)
     (dict(precision=1, nx=32, ns=2731), 8192),               # FP32, N_s > 2048
-    (dict(precision=1, nx=256, ns=4096), 0),                 # above the FFT size limit: dense
+    (dict(precision=1, nx=256, ns=4096), 16384),             # above one CTA: the four-step form
+    (dict(precision=1, nx=256, ns=16384), 65536),
+    (dict(precision=1, nx=64, ns=30000), 0),                 # above the four-step limit: dense
     (dict(precision=0, nx=64, ns=1024), 4096),               # FP64, N_x >= 64
     (dict(precision=0, nx=32, ns=1024), 0),                  # FP64, N_x = 32
     (dict(precision=0, nx=32, ns=128), 512),                 # FP64, N_s <= 128

@@ -1,0 +1,108 @@
+"""The four-step FFT form of the s-contraction (transforms longer than one CTA
+holds: F = F1 F2 with warp-level line transforms and a scratch pass in between)
+against the FP64 oracle and against the dense contraction on the same inputs:
+every pair (F1, F2) the library uses, both adjoints, the descent, ragged N_s and
+the symmetric subspace.
+
+Tolerances: FP64 1e-10 relative; FP32 1e-5 on J and 5e-6 (2-norm) on fields
+between the two FP32 forms (each within FP32 rounding of the exact result, about
+2e-6 apart at these sizes)."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2301_11704_gb300 import gen
+from paper_2301_11704_gb300.curve import KSCurve
+from tests.test_gpu_parity import assert_grad_close, rel_2, rel_max
+
+pytestmark = pytest.mark.gpu
+
+
+def _curve(N, Ns, L, seed, fp32=False):
+    rng = np.random.default_rng(seed)
+    X = np.zeros((Ns, N))
+    x = np.arange(N) * L / N
+    th = np.arange(Ns) * np.pi / (Ns - 1)
+    for j in range(1, min(6, N // 2)):
+        a, b = rng.standard_normal(2)
+        X += (0.6 ** j) * (a * np.cos(2 * np.pi * j * x / L) + b * np.sin(2 * np.pi * j * x / L))[None, :] * \
+            (0.5 + np.sin(th * (1 + j % 3)))[:, None]
+    return X.astype(np.float32).astype(np.float64) if fp32 else X
+
+
+@pytest.mark.parametrize("adjoint", ["paper", "discrete"])
+def test_four_step_fp64_matches_oracle(adjoint):
+    """N_s = 1500 in FP64: F = 8192 = 128 x 64 (above the single-CTA FP64 limit)."""
+    N, Ns, L = 32, 1500, 22.0
+    S = 0.1 * (Ns - 1)
+    X = _curve(N, Ns, L, 11)
+    c = KSCurve(L, N, Ns, S, X[0], X[-1], u_init=torch.from_numpy(X), adjoint=adjoint, s_transform="fft")
+    assert c.fft_length == 8192
+    U = oracle.curve_spectral(X)
+    spec = gen.CurveSpec(0, 0, L, N, Ns, S)
+    mode = oracle.DISCRETE if adjoint == "discrete" else oracle.PAPER
+    R, D = oracle.curve_residual(U, L, S, 1.0)
+    G, _ = oracle.curve_adjoint(U, R, L, S, 1.0, mode=mode)
+    sc = oracle.curve_scalars(R, D, L, S, 1.0)
+    assert rel_max(c.residual().cpu().numpy(), oracle.curve_physical(R)) < 1e-10
+    J2, Ja = c.cost()
+    assert abs(J2 - sc["J2"]) < 1e-10 * sc["J2"] and abs(Ja - sc["J_arc"]) < 1e-10 * sc["J_arc"]
+    g, _ = c.gradient()
+    assert_grad_close(g.cpu().numpy(), G, U, spec, 1e-10)
+    c.close()
+    c2 = KSCurve(L, N, Ns, S, X[0], X[-1], u_init=torch.from_numpy(X), adjoint=adjoint, dtau=1e-3, s_transform="fft")
+    out = c2.descend(20)
+    Uo, _, sco, _ = oracle.curve_descend(U, L, S, 20, dtau=1e-3, mode=mode)
+    assert rel_max(c2.get_state().cpu().numpy(), oracle.curve_physical(Uo)) < 1e-10
+    assert abs(out["J"] - sco["J"]) < 1e-10 * sco["J"]
+    c2.close()
+
+
+@pytest.mark.parametrize("precision,N,Ns,F", [
+    ("fp32", 64, 3000, 16384),     # 128 x 128
+    ("fp32", 32, 7001, 32768),     # 256 x 128, ragged
+    ("fp32", 16, 12345, 65536),    # 256 x 256, ragged
+    ("fp64", 128, 2500, 8192),     # 128 x 64
+    ("fp64", 64, 5000, 16384),
+])
+def test_four_step_matches_dense(precision, N, Ns, F):
+    L, S = 22.0 + N / 16.0, 0.1 * (Ns - 1)
+    X = _curve(N, Ns, L, N + Ns, fp32=precision == "fp32")
+    xt = torch.from_numpy(X)
+    xt = xt.float() if precision == "fp32" else xt
+    cf = KSCurve(L, N, Ns, S, X[0], X[-1], u_init=xt, precision=precision, dtau=1e-3, s_transform="fft")
+    cd = KSCurve(L, N, Ns, S, X[0], X[-1], u_init=xt, precision=precision, dtau=1e-3, s_transform="dense")
+    assert cf.fft_length == F and cd.fft_length == 0
+    ftol, jtol = (5e-6, 1e-5) if precision == "fp32" else (1e-10, 1e-10)
+    diff = rel_2 if precision == "fp32" else rel_max
+    rf, rd = cf.residual().double().cpu().numpy(), cd.residual().double().cpu().numpy()
+    assert diff(rf, rd) < ftol
+    (J2f, Jaf), (J2d, Jad) = cf.cost(), cd.cost()
+    assert abs(J2f - J2d) < jtol * J2d and abs(Jaf - Jad) < jtol * Jad
+    of, od = cf.descend(10), cd.descend(10)
+    xf, xd = cf.get_state().double().cpu().numpy(), cd.get_state().double().cpu().numpy()
+    assert diff(xf, xd) < ftol
+    assert abs(of["J"] - od["J"]) < jtol * od["J"]
+    cf.close()
+    cd.close()
+
+
+@pytest.mark.parametrize("sym", [1, 3])
+def test_four_step_holds_the_symmetric_subspace(sym):
+    """Odd (and L/2-periodic) sections stay so exactly through the descent."""
+    N, Ns, L = 32, 3000, 22.0
+    x = np.arange(N) * L / N
+    th = np.arange(Ns) * np.pi / (Ns - 1)
+    X = np.outer(np.sin(th / 2) + 0.2, np.sin(4 * np.pi * x / L)) + 0.3 * np.outer(np.sin(th), np.sin(8 * np.pi * x / L))
+    if sym == 1:
+        X += 0.2 * np.outer(np.sin(2 * th), np.sin(2 * np.pi * x / L))
+    c = KSCurve(L, N, Ns, 0.1 * (Ns - 1), X[0], X[-1], u_init=torch.from_numpy(X), dtau=1e-3, symmetry=sym,
+                s_transform="fft")
+    assert c.fft_length == 16384
+    c.descend(20)
+    U = np.fft.rfft(c.get_state().cpu().numpy(), axis=1)
+    assert np.abs(U.real).max() <= 1e-12 * np.abs(U).max()
+    if sym == 3:
+        assert np.abs(U[:, 1::2]).max() <= 1e-12 * np.abs(U).max()
+    c.close()
