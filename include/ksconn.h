@@ -89,16 +89,23 @@ typedef struct {
                             bit 1: every section L/2-periodic (odd Fourier modes zero);
                             0 = none.  Values above 3 are invalid. */
     int32_t s_transform; /* how D_t is applied along s (same result to rounding):
-                            0 auto: for a single curve the form measured faster on GB300 for its
-                            size (FFT when N_s N_x >= 131072 or N_s > 2048 in FP32, when N_x >= 64
-                            or N_s <= 128 in FP64, within the FFT size limit; else dense, on the
-                            tensor cores for FP32 when N_s >= 8192, or N_s >= 4096 at N_x >= 128); in a
-                            batch the FFT form wherever the size limit allows;
+                            0 auto: for a single curve the form measured fastest on GB300 for its
+                            size: at N_x >= 256 the one-CTA FFT form where it fits; the four-step
+                            FFT form for 683 < N_s <= 21846 in FP64, and in FP32 from N_s >= 1366
+                            (N_s >= 1024 at N_x >= 128); below that the one-CTA FFT form when
+                            N_s N_x >= 131072 (FP32) or N_x >= 64 or N_s <= 128 (FP64); else dense
+                            (on the tensor cores for FP32 when N_s >= 8192, or N_s >= 4096 at
+                            N_x >= 128: above the four-step limit); in a batch the one-CTA FFT
+                            form wherever it fits;
                             1 dense contraction generated from the O(N_s) cot table;
-                            2 FFT convolution (N_s <= 2731 FP32 / 1366 FP64);
+                            2 FFT convolution (N_s <= 21846; one CTA per mode up to N_s = 2731
+                            FP32 / 1366 FP64, the four-step form above);
                             3 dense contraction on the tensor cores (FP32 storage only: each
                             FP32 operand split exactly into three TF32 parts, six products,
-                            FP32 accumulation per 32 sections, FP32 sums across them) */
+                            FP32 accumulation per 32 sections, FP32 sums across them);
+                            4 FFT convolution in the four-step form (transform length F = F1 F2
+                            from 4096 to 65536: 684 <= N_s <= 21846), which 2 and auto use
+                            above one CTA's limit */
     int32_t launch;      /* how a single curve's descent steps are launched (same results):
                             0 three kernels per step, chained by programmatic dependent
                             launch and replayed from a CUDA graph;

@@ -86,7 +86,10 @@ ks_status validate(const ks_params *p)
     if (p->conv < KS_CONV_JARC || p->conv > KS_CONV_JREL) return fail(KS_EINVAL, "conv must be a ks_conv value");
     if (p->check_ends != 0 && p->check_ends != 1) return fail(KS_EINVAL, "check_ends must be 0 or 1");
     if (p->symmetry < 0 || p->symmetry > 3) return fail(KS_EINVAL, "symmetry must be in [0, 3]");
-    if (p->s_transform < 0 || p->s_transform > 3) return fail(KS_EINVAL, "s_transform must be 0, 1, 2 or 3");
+    if (p->s_transform < 0 || p->s_transform > 4) return fail(KS_EINVAL, "s_transform must be in [0, 4]");
+    if (p->s_transform == 4 && ks::fft4_size(p->ns, p->precision == KS_FP32, 1) == 0)
+        return fail(KS_EINVAL, "s_transform = four-step FFT needs %d <= 3 (N_s - 1) <= %d (rounded up to a power of two)",
+                    ks::F4_FMIN / 2 + 1, ks::F4_FMAX);
     if (p->s_transform == 3 && p->precision != KS_FP32)
         return fail(KS_EINVAL, "s_transform = tensor cores needs FP32 storage");
     if (p->launch < 0 || p->launch > 1) return fail(KS_EINVAL, "launch must be 0 or 1");

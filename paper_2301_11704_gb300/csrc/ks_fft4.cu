@@ -324,6 +324,7 @@ static cudaError_t f4_run(const CurveDev &c, int mode, int discrete, int gate, c
 template <typename T>
 static cudaError_t f4_dispatch(const CurveDev &c, int mode, int discrete, int gate, cudaStream_t st)
 {
+    if (c.F1 == 64 && c.F2 == 64) return f4_run<T, 64, 64>(c, mode, discrete, gate, st);
     if (c.F1 == 128 && c.F2 == 64) return f4_run<T, 128, 64>(c, mode, discrete, gate, st);
     if (c.F1 == 128 && c.F2 == 128) return f4_run<T, 128, 128>(c, mode, discrete, gate, st);
     if (c.F1 == 256 && c.F2 == 128) return f4_run<T, 256, 128>(c, mode, discrete, gate, st);

@@ -46,21 +46,32 @@ inline int fft_size(int ns, int prec)
 // FFTs of F1, F2 <= 256 points by one warp each and one pass through a scratch
 // buffer in between; up to F4_FMAX.
 constexpr int F4_FMAX = 65536;
+constexpr int F4_FMIN = 4096;             // 64 x 64
 constexpr int F4_THREADS = 256;           // 8 warps, one line each
-inline int fft4_size(int ns, int prec)
+// Four-step length for a curve: above the single-CTA limit, or from F4_FMIN on
+// when asked for (any = 1); 0 outside the range.
+inline int fft4_size(int ns, int prec, int any = 0)
 {
     int F = 16;
     while (F < 3 * (ns - 1)) F <<= 1;
-    return (F > (prec ? SC_FMAX_F32 : SC_FMAX_F64) && F <= F4_FMAX) ? F : 0;
+    const int lo = any ? F4_FMIN : 2 * (prec ? SC_FMAX_F32 : SC_FMAX_F64);
+    return (F >= lo && F <= F4_FMAX) ? F : 0;
 }
 
-// Form that `auto` picks for a single curve: the FFT form where it measured
-// faster than the dense contraction on GB300 (one step of one curve, L2 flushed,
-// N_x in {32, 64, 128, 256}, N_s from 128 to the size limit).
-inline bool fft_preferred(int ns, int nx, int prec)
+// Form of the s-contraction: dense, FFT with one CTA per mode, four-step FFT.
+enum SForm { SF_DENSE = 0, SF_FFT1 = 1, SF_FFT4 = 2 };
+
+// Form that `auto` picks for a single curve: the fastest measured on GB300 (one
+// step, L2 flushed, N_x in {32, 64, 128, 256}, N_s from 128 to 16384).  The
+// four-step form runs many more CTAs than the one-CTA-per-mode form and wins
+// wherever it applies, except at N_x = 256 where the modes alone fill the GPU.
+inline int auto_form(int ns, int nx, int prec)
 {
-    if (prec) return (long long)ns * nx >= 131072 || ns > 2048;
-    return nx >= 64 || ns <= 128;
+    const bool f1 = fft_size(ns, prec) > 0, f4 = fft4_size(ns, prec, 1) > 0;
+    if (nx >= 256 && f1) return SF_FFT1;
+    if (f4 && (ns >= 1366 || (nx >= 128 && ns >= 1024) || !prec || nx >= 256)) return SF_FFT4;
+    if (f1 && (prec ? (long long)ns * nx >= 131072 : (nx >= 64 || ns <= 128))) return SF_FFT1;
+    return SF_DENSE;
 }
 
 // Where `auto` puts a dense-form FP32 curve on the tensor cores: the sizes where

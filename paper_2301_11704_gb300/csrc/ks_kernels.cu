@@ -42,11 +42,15 @@ Layout make_layout(int ns, int nx, int prec, int allow_split, int bn, int s_tran
     Layout l{};
     size_t b = prec ? 4 : 8;
     // s_transform 0 (auto): a single curve (allow_split) takes the measured rule,
-    // batched curves the FFT form wherever it fits
-    const bool want_fft = s_transform == 2 || (s_transform == 0 && (!allow_split || fft_preferred(ns, nx, prec)));
-    l.F = want_fft ? fft_size(ns, prec) : 0;
-    if (want_fft && !l.F && allow_split && fft4_size(ns, prec)) {   // longer: the four-step form
-        l.F = fft4_size(ns, prec);
+    // batched curves the one-CTA FFT form wherever it fits
+    int form = SF_DENSE;
+    if (!allow_split) form = (s_transform == 0 || s_transform == 2) && fft_size(ns, prec) ? SF_FFT1 : SF_DENSE;
+    else if (s_transform == 0) form = auto_form(ns, nx, prec);
+    else if (s_transform == 2) form = fft_size(ns, prec) ? SF_FFT1 : (fft4_size(ns, prec) ? SF_FFT4 : SF_DENSE);
+    else if (s_transform == 4) form = fft4_size(ns, prec, 1) ? SF_FFT4 : SF_DENSE;
+    if (form == SF_FFT1) l.F = fft_size(ns, prec);
+    if (form == SF_FFT4) {   // the four-step form
+        l.F = fft4_size(ns, prec, 1);
         l.f4 = 1;
         int lg = 0;
         while ((1 << lg) < l.F) ++lg;

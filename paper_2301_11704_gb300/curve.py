@@ -17,7 +17,7 @@ from ._native import KSParams, KSScalars, check, dptr
 _PREC = {"fp64": _native.KS_FP64, "fp32": _native.KS_FP32}
 _ADJ = {"paper": _native.KS_ADJ_PAPER, "discrete": _native.KS_ADJ_DISCRETE}
 _CONV = {"jarc": _native.KS_CONV_JARC, "j": _native.KS_CONV_J, "jrel": _native.KS_CONV_JREL}
-_STR = {"auto": 0, "dense": 1, "fft": 2, "dense_tc": 3}
+_STR = {"auto": 0, "dense": 1, "fft": 2, "dense_tc": 3, "fft4": 4}
 _LAUNCH = {"auto": 0, "kernels": 0, "persistent": 1}
 
 

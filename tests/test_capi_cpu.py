@@ -58,7 +58,7 @@ def test_workspace_size_scales_with_the_curve(lib):
 
 @pytest.mark.parametrize("bad", [dict(nx=24), dict(nx=4), dict(nx=512), dict(ns=2), dict(L=0.0), dict(S=-1.0),
                                  dict(dtau=0.0), dict(precision=7), dict(adjoint=3), dict(conv=9),
-                                 dict(symmetry=4), dict(s_transform=4), dict(s_transform=3, precision=0), dict(launch=2), dict(L=float("nan"))])
+                                 dict(symmetry=4), dict(s_transform=5), dict(s_transform=4, ns=500), dict(s_transform=3, precision=0), dict(launch=2), dict(L=float("nan"))])
 def test_invalid_parameters_are_rejected_on_the_host(lib, bad):
     p = _params(**bad)
     assert lib.ks_curve_workspace_bytes(ctypes.byref(p)) == 0
@@ -97,7 +97,8 @@ def test_null_handle_is_rejected(lib):
     (dict(precision=1, nx=256, ns=16384), 65536),
     (dict(precision=1, nx=64, ns=30000), 0),                 # above the four-step limit: dense
     (dict(precision=0, nx=64, ns=1024), 4096),               # FP64, N_x >= 64
-    (dict(precision=0, nx=32, ns=1024), 0),                  # FP64, N_x = 32
+    (dict(precision=0, nx=32, ns=1024), 4096),               # FP64, N_s >= 684: four-step
+    (dict(precision=0, nx=32, ns=600), 0),                   # FP64, N_x = 32, small
     (dict(precision=0, nx=32, ns=128), 512),                 # FP64, N_s <= 128
     (dict(precision=1, nx=64, ns=1024, s_transform=2), 4096),
     (dict(precision=1, nx=128, ns=1024, s_transform=1), 0),

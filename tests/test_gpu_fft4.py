@@ -59,19 +59,21 @@ def test_four_step_fp64_matches_oracle(adjoint):
     c2.close()
 
 
-@pytest.mark.parametrize("precision,N,Ns,F", [
-    ("fp32", 64, 3000, 16384),     # 128 x 128
-    ("fp32", 32, 7001, 32768),     # 256 x 128, ragged
-    ("fp32", 16, 12345, 65536),    # 256 x 256, ragged
-    ("fp64", 128, 2500, 8192),     # 128 x 64
-    ("fp64", 64, 5000, 16384),
+@pytest.mark.parametrize("precision,N,Ns,F,form", [
+    ("fp32", 64, 3000, 16384, "fft"),     # 128 x 128
+    ("fp32", 32, 7001, 32768, "fft"),     # 256 x 128, ragged
+    ("fp32", 16, 12345, 65536, "fft"),    # 256 x 256, ragged
+    ("fp64", 128, 2500, 8192, "fft"),     # 128 x 64
+    ("fp64", 64, 5000, 16384, "fft"),
+    ("fp32", 64, 1024, 4096, "fft4"),     # 64 x 64, where one CTA would also hold it
+    ("fp64", 256, 700, 4096, "fft4"),
 ])
-def test_four_step_matches_dense(precision, N, Ns, F):
+def test_four_step_matches_dense(precision, N, Ns, F, form):
     L, S = 22.0 + N / 16.0, 0.1 * (Ns - 1)
     X = _curve(N, Ns, L, N + Ns, fp32=precision == "fp32")
     xt = torch.from_numpy(X)
     xt = xt.float() if precision == "fp32" else xt
-    cf = KSCurve(L, N, Ns, S, X[0], X[-1], u_init=xt, precision=precision, dtau=1e-3, s_transform="fft")
+    cf = KSCurve(L, N, Ns, S, X[0], X[-1], u_init=xt, precision=precision, dtau=1e-3, s_transform=form)
     cd = KSCurve(L, N, Ns, S, X[0], X[-1], u_init=xt, precision=precision, dtau=1e-3, s_transform="dense")
     assert cf.fft_length == F and cd.fft_length == 0
     ftol, jtol = (5e-6, 1e-5) if precision == "fp32" else (1e-10, 1e-10)
