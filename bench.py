@@ -393,6 +393,24 @@ def main():
                 "steps": k64}
         c64.close()
 
+    # ---- the larger workloads (context): L=44, N_x=128, N_s=4096 and L=100, N_x=256,
+    # N_s=16384, FP32 storage, the form auto picks, L2 flushed before each step
+    large = []
+    if rank == 0 and args.precision == "fp32":
+        for cfg in (2, 4):
+            sp = gen.workload(cfg)[0]
+            upl, uml = gen.end_points(sp)
+            ampl, vpl = gen.perturbation(sp)
+            cl = KSCurve(sp.L, sp.N, sp.Ns, sp.S, upl, uml, s0=sp.s0, dtau=sp.dtau, precision="fp32", device=dev)
+            cl.init_trial(0.0, None, ampl, vpl)
+            kl = max(3, min(50, K))
+            msl, _ = timed_steps(cl, kl, 3)
+            large.append({"workload": "L=%g N_x=%d N_s=%d FP32" % (sp.L, sp.N, sp.Ns),
+                          "value": sp.M * kl / (sum(msl) / 1e3), "unit": UNIT, "ms_per_step": sum(msl) / kl,
+                          "steps": kl, "s_transform": ("FFT convolution, F=%d" % cl.fft_length) if cl.fft_length
+                          else "dense contraction"})
+            cl.close()
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         times, cores = oracle_steps(spec, args.cpu_seconds)
@@ -406,7 +424,7 @@ def main():
                 "config": dict(workload_config(spec, args.precision.upper()), s_transform=dt_form),
                 "roofline": roof,
                 "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": 4 * K, "clocks": clk,
-                "fp64_gpu_path": fp64, "other_s_transform": other, "steady_state": steady, "final_J": sc["J"], "final_J_arc": sc["J_arc"],
+                "fp64_gpu_path": fp64, "larger_workloads": large, "other_s_transform": other, "steady_state": steady, "final_J": sc["J"], "final_J_arc": sc["J_arc"],
                 "step_ms_median": statistics.median(step_ms)}
         print(json.dumps(line))
     curve.close()
