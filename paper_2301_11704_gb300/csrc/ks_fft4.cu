@@ -257,52 +257,77 @@ __global__ void __launch_bounds__(F4_THREADS) k_f4_p3(CurveDev c, int mode, int 
     }
 }
 
-// ---- set-up: FP64 tables in the scratch buffer, then the twiddles W_F^k and the
-// kernel spectrum FFT(c_F)/F by a direct DFT in FP64 (c_F is real: the upper
-// half of the spectrum is the conjugate of the lower), stored [k1][k2].
-__global__ void k_f4_tables(CurveDev c)
+// ---- set-up: the twiddles W_F^k (storage type) and the kernel spectrum
+// FFT(c_F)/F in the [k1][k2] order of the passes, by the forward half of the same
+// decomposition in FP64: c_F[t] = cot(pi t / 2P) for 0 <= t <= P, c_F[F - t] =
+// cot(pi (2P - t) / 2P) for 0 < t < 2P, 0 elsewhere (cot 0 = 0).  FP64 tables
+// W_F^p and the intermediate S64[k1][n2] live in the scratch buffer (32 F bytes;
+// it holds at least 8 F bytes per mode and N/2 >= 4 modes).
+__device__ __forceinline__ double cot_kernel(int n, int F, int P)
 {
-    const int F = c.F, twoP = 2 * c.P;
-    double2 *w64 = (double2 *)c.f4s;
-    double *cot64 = (double *)(w64 + F);
+    int u = -1;
+    if (n <= P) u = n;
+    else if (n > F - 2 * P) u = 2 * P - (F - n);
+    if (u <= 0) return 0.0;
+    double sn, cs;
+    sincospi((double)u / (double)(2 * P), &sn, &cs);
+    return cs / sn;
+}
+
+__global__ void k_f4_twiddles(CurveDev c)
+{
+    const int F = c.F;
+    double2 *w64 = (double2 *)c.f4s;   // e^{-2 pi i p / F} as (cos, -sin)
     for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < F; p += gridDim.x * blockDim.x) {
         double sn, cs;
         sincospi(2.0 * (double)p / (double)F, &sn, &cs);
-        w64[p] = make_double2(cs, sn);
-    }
-    for (int u = blockIdx.x * blockDim.x + threadIdx.x; u < twoP; u += gridDim.x * blockDim.x) {
-        double sn, cs;
-        sincospi((double)u / (double)twoP, &sn, &cs);
-        cot64[u] = u ? cs / sn : 0.0;
+        w64[p] = make_double2(cs, -sn);
     }
 }
 
-template <typename T>
-__global__ void k_f4_spectrum(CurveDev c)
+// pass A (per n2): FFT over n1 of c_F[F2 n1 + n2], times W_F^(n2 k1) -> S64[k1][n2]
+template <int F1, int F2>
+__global__ void __launch_bounds__(F4_THREADS) k_f4_specA(CurveDev c)
 {
-    const int F = c.F, P = c.P, twoP = 2 * P, F1 = c.F1, F2 = c.F2;
-    const double2 *w64 = (const double2 *)c.f4s;
-    const double *cot64 = (const double *)(w64 + F);
-    cpx<T> *ftw = (cpx<T> *)c.ftw, *chat = (cpx<T> *)c.chat;
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k > F / 2) return;
-    double re = 0.0, im = 0.0;
-    for (int t = -(twoP - 1); t <= P; ++t) {
-        const int u = (t % twoP + twoP) % twoP;
-        if (u == 0) continue;
-        const double cv = cot64[u];
-        const int idx = t >= 0 ? t : F + t;
-        const double2 wv = w64[(int)(((long long)k * idx) % F)];
-        re += cv * wv.x;
-        im -= cv * wv.y;
+    using Sm = F4Smem<double, F1, F1>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    cpx<double> *tw = (cpx<double> *)smem_raw, *buf = tw + Sm::TW, *stage = buf + Sm::BUF;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, F = F1 * F2;
+    const int n2 = blockIdx.x * F4W + warp;
+    const cpx<double> *w64 = (const cpx<double> *)c.f4s;
+    cpx<double> *S = (cpx<double> *)c.f4s + F;
+    for (int t = threadIdx.x; t < F1 / 2; t += F4_THREADS) tw[t] = w64[t * F2];
+    cpx<double> *x = buf + (size_t)warp * 2 * F1, *y = x + F1;
+    for (int n1 = lane; n1 < F1; n1 += 32) x[n1] = {cot_kernel(F2 * n1 + n2, F, c.P), 0.0};
+    __syncthreads();
+    cpx<double> *Y = warp_fft<double, F1>(x, y, tw, false, lane);
+    for (int k1 = lane; k1 < F1; k1 += 32) stage[(size_t)warp * (F1 + 1) + k1] = cmul(Y[k1], w64[n2 * k1]);
+    __syncthreads();
+    for (int e = threadIdx.x; e < F4W * F1; e += F4_THREADS) {
+        const int k1 = e / F4W, w = e % F4W;
+        S[(size_t)k1 * F2 + blockIdx.x * F4W + w] = stage[(size_t)w * (F1 + 1) + k1];
     }
-    // spectrum at k and (conjugate) at F - k, in the [k1][k2] order of the passes
-    chat[(size_t)(k % F1) * F2 + k / F1] = {(T)(re / F), (T)(im / F)};
-    ftw[k] = {(T)w64[k].x, (T)(-w64[k].y)};
-    const int kc = (F - k) % F;
-    if (kc == k) return;
-    chat[(size_t)(kc % F1) * F2 + kc / F1] = {(T)(re / F), (T)(-im / F)};
-    ftw[kc] = {(T)w64[kc].x, (T)(-w64[kc].y)};
+}
+
+// pass B (per k1): FFT over n2 -> spectrum[k1][k2] / F in the storage type; twiddles
+template <typename T, int F1, int F2>
+__global__ void __launch_bounds__(F4_THREADS) k_f4_specB(CurveDev c)
+{
+    using Sm = F4Smem<double, F2, F2>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    cpx<double> *tw = (cpx<double> *)smem_raw, *buf = tw + Sm::TW;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, F = F1 * F2;
+    const int k1 = blockIdx.x * F4W + warp;
+    const cpx<double> *w64 = (const cpx<double> *)c.f4s;
+    const cpx<double> *S = (const cpx<double> *)c.f4s + F + (size_t)k1 * F2;
+    for (int t = threadIdx.x; t < F2 / 2; t += F4_THREADS) tw[t] = w64[t * F1];
+    cpx<double> *x = buf + (size_t)warp * 2 * F2, *y = x + F2;
+    for (int n2 = lane; n2 < F2; n2 += 32) x[n2] = S[n2];
+    __syncthreads();
+    cpx<double> *Z = warp_fft<double, F2>(x, y, tw, false, lane);
+    cpx<T> *chat = (cpx<T> *)c.chat + (size_t)k1 * F2, *ftw = (cpx<T> *)c.ftw;
+    for (int k2 = lane; k2 < F2; k2 += 32) chat[k2] = {(T)(Z[k2].x / F), (T)(Z[k2].y / F)};
+    for (int p = k1 * F2 + lane; p < (k1 + 1) * F2; p += 32) ftw[p] = {(T)w64[p].x, (T)w64[p].y};
 }
 
 // ---- launchers
@@ -337,17 +362,33 @@ cudaError_t launch_f4(const CurveDev &c, int mode, int discrete, int gate, cudaS
     return c.prec ? f4_dispatch<float>(c, mode, discrete, gate, st) : f4_dispatch<double>(c, mode, discrete, gate, st);
 }
 
+template <typename T, int F1, int F2>
+static cudaError_t setup_run(const CurveDev &c, cudaStream_t st)
+{
+    const size_t smA = F4Smem<double, F1, F1>::BYTES, smB = F4Smem<double, F2, F2>::BYTES;
+    cudaError_t e;
+    if ((e = set_smem(k_f4_specA<F1, F2>, smA)) != cudaSuccess) return e;
+    if ((e = set_smem(k_f4_specB<T, F1, F2>, smB)) != cudaSuccess) return e;
+    k_f4_twiddles<<<(c.F + 255) / 256, 256, 0, st>>>(c);
+    k_f4_specA<F1, F2><<<F2 / F4W, F4_THREADS, smA, st>>>(c);
+    k_f4_specB<T, F1, F2><<<F1 / F4W, F4_THREADS, smB, st>>>(c);
+    return cudaGetLastError();
+}
+
+template <typename T>
+static cudaError_t setup_dispatch(const CurveDev &c, cudaStream_t st)
+{
+    if (c.F1 == 64 && c.F2 == 64) return setup_run<T, 64, 64>(c, st);
+    if (c.F1 == 128 && c.F2 == 64) return setup_run<T, 128, 64>(c, st);
+    if (c.F1 == 128 && c.F2 == 128) return setup_run<T, 128, 128>(c, st);
+    if (c.F1 == 256 && c.F2 == 128) return setup_run<T, 256, 128>(c, st);
+    if (c.F1 == 256 && c.F2 == 256) return setup_run<T, 256, 256>(c, st);
+    return cudaErrorInvalidValue;
+}
+
 cudaError_t launch_setup_f4(const CurveDev &c, cudaStream_t st)
 {
-    // the FP64 tables (16 F + 16 P bytes) fit the scratch buffer (at least 8 F bytes
-    // per mode, N/2 >= 4 modes, P < F / 3)
-    k_f4_tables<<<(c.F + 255) / 256, 256, 0, st>>>(c);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    const int g = (c.F / 2 + 1 + 255) / 256;
-    if (c.prec) k_f4_spectrum<float><<<g, 256, 0, st>>>(c);
-    else k_f4_spectrum<double><<<g, 256, 0, st>>>(c);
-    return cudaGetLastError();
+    return c.prec ? setup_dispatch<float>(c, st) : setup_dispatch<double>(c, st);
 }
 
 }  // namespace ks
