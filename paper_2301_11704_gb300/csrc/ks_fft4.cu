@@ -9,11 +9,13 @@
 //   FFT:  Z[k1 + F1 k2] = sum_n2 W_F2^(n2 k2) W_F^(n2 k1) sum_n1 W_F1^(n1 k1) z[F2 n1 + n2]
 //   IFFT: x[F2 n1 + n2] = sum_k1 W_F1^(-n1 k1) W_F^(-n2 k1) sum_k2 W_F2^(-n2 k2) X[k1 + F1 k2]
 // (W_L = e^(-2 pi i / L)).  Three passes per Fourier mode (the mode's two real
-// columns packed as one complex sequence), one warp per line transform:
+// columns packed as one complex sequence), one warp per line transform, the
+// line held in registers (k1 and k2 stay in the transforms' scrambled order,
+// the spectrum and the twiddles are tabulated in it):
 //   pass 1 (per n2): z from the columns, FFT over n1, times W_F^(n2 k1), stored
 //          transposed as S[k1][n2] (staged through shared memory);
 //   pass 2 (per k1): FFT over n2, times the kernel spectrum (kept in the same
-//          [k1][k2] order: no transposes), IFFT over k2, times W_F^(-n2 k1);
+//          order: no transposes), IFFT over k2, times W_F^(-n2 k1);
 //   pass 3 (per n2): IFFT over k1 -> y at j = F2 n1 + n2 <= P, and the epilogue
 //          of the single-CTA form (store D_t u; or G, the semi-implicit
 //          increment and the FP64 |G|^2 with its last-CTA sum).
@@ -58,6 +60,129 @@ struct F4Smem {
     static constexpr size_t BYTES = (TW + BUF + STAGE) * sizeof(cpx<T>);
 };
 
+// ---- line transforms in registers.  A line of L = 32 R points is held by one
+// warp, R values per lane: v[a] at lane l is x[l + 32 a].  The forward transform
+// is an R-point DFT within each lane, the twiddles W_L^(a l), and a 32-point
+// decimation-in-frequency transform across the lanes by shuffles; it leaves
+// X[a + R brev5(l)] in v[a] at lane l.  The inverse takes that layout back to
+// natural order (decimation in time across the lanes, the conjugate twiddles,
+// the inverse R-point DFT).  Neither scales.  The passes keep the scrambled
+// order: an index k of a transformed axis is stored at the position
+// (k mod R) * 32 + brev5(k / R), so lane l's register a always maps to
+// position a * 32 + l and no pass permutes data.
+
+__device__ __forceinline__ int brev5(int x) { return (int)(__brev((unsigned)x) >> 27); }
+
+template <int R>
+__host__ __device__ constexpr int brev_r(int i)
+{
+    int r = 0;
+    for (int b = 1; b < R; b <<= 1, i >>= 1) r = (r << 1) | (i & 1);
+    return r;
+}
+
+template <typename T>
+__device__ __forceinline__ cpx<T> cadd(cpx<T> a, cpx<T> b) { return {a.x + b.x, a.y + b.y}; }
+template <typename T>
+__device__ __forceinline__ cpx<T> csub(cpx<T> a, cpx<T> b) { return {a.x - b.x, a.y - b.y}; }
+template <typename T>
+__device__ __forceinline__ cpx<T> cconj(cpx<T> a) { return {a.x, -a.y}; }
+template <typename T>
+__device__ __forceinline__ cpx<T> cshfl(cpx<T> a, int m)
+{
+    return {__shfl_xor_sync(0xffffffffu, a.x, m), __shfl_xor_sync(0xffffffffu, a.y, m)};
+}
+
+// v * W_8^e (forward, e^(-2 pi i e / 8)) or v * W_8^(-e) (inverse), e < 4; e is a
+// constant once the caller's loops are unrolled
+template <typename T>
+__device__ __forceinline__ cpx<T> mul_w8(cpx<T> v, int e, bool inv)
+{
+    const T h = T(0.70710678118654752440);
+    if (e == 0) return v;
+    if (e == 2) return inv ? cpx<T>{-v.y, v.x} : cpx<T>{v.y, -v.x};
+    if (e == 1) return inv ? cpx<T>{h * (v.x - v.y), h * (v.x + v.y)} : cpx<T>{h * (v.x + v.y), h * (v.y - v.x)};
+    return inv ? cpx<T>{-h * (v.x + v.y), h * (v.x - v.y)} : cpx<T>{h * (v.y - v.x), -h * (v.x + v.y)};
+}
+
+// R-point DFT (R <= 8) within a lane, natural order in and out (radix 2, in time)
+template <typename T, int R>
+__device__ __forceinline__ void reg_dft(cpx<T> (&v)[R], bool inv)
+{
+    cpx<T> t[R];
+#pragma unroll
+    for (int i = 0; i < R; ++i) t[brev_r<R>(i)] = v[i];
+#pragma unroll
+    for (int h = 1; h < R; h <<= 1) {
+#pragma unroll
+        for (int i = 0; i < R; i += 2 * h) {
+#pragma unroll
+            for (int j = 0; j < h; ++j) {
+                const cpx<T> u = t[i + j], x = mul_w8(t[i + j + h], j * (4 / h), inv);
+                t[i + j] = cadd(u, x);
+                t[i + j + h] = csub(u, x);
+            }
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < R; ++i) v[i] = t[i];
+}
+
+// twl[a * 32 + l] = W_L^(a l) (a < R), w32[s] = W_32^s (s < 16)
+template <typename T, int R>
+__device__ __forceinline__ void reg_fft_fwd(cpx<T> (&v)[R], const cpx<T> *twl, const cpx<T> *w32, int lane)
+{
+    reg_dft<T, R>(v, false);
+#pragma unroll
+    for (int a = 1; a < R; ++a) v[a] = cmul(v[a], twl[a * 32 + lane]);
+#pragma unroll
+    for (int m = 16; m >= 1; m >>= 1) {
+        const bool up = (lane & m) != 0;
+        const cpx<T> w = w32[up ? (lane & (m - 1)) * (16 / m) : 0];   // W_2m^(pos - m) on the upper lanes
+#pragma unroll
+        for (int a = 0; a < R; ++a) {
+            const cpx<T> p = cshfl(v[a], m);
+            const cpx<T> d = up ? csub(p, v[a]) : cadd(v[a], p);
+            v[a] = (m > 1) ? cmul(d, w) : d;
+        }
+    }
+}
+
+template <typename T, int R>
+__device__ __forceinline__ void reg_fft_inv(cpx<T> (&v)[R], const cpx<T> *twl, const cpx<T> *w32, int lane)
+{
+#pragma unroll
+    for (int m = 1; m <= 16; m <<= 1) {
+        const bool up = (lane & m) != 0;
+        const cpx<T> w = cconj(w32[up ? (lane & (m - 1)) * (16 / m) : 0]);
+#pragma unroll
+        for (int a = 0; a < R; ++a) {
+            const cpx<T> b = (m > 1) ? cmul(v[a], w) : v[a];
+            const cpx<T> p = cshfl(b, m);
+            v[a] = up ? csub(p, b) : cadd(b, p);
+        }
+    }
+#pragma unroll
+    for (int a = 1; a < R; ++a) v[a] = cmul(v[a], cconj(twl[a * 32 + lane]));
+    reg_dft<T, R>(v, true);
+}
+
+// the line twiddles of a length-L transform from the plain table W_F^k
+template <typename T, int L>
+__device__ __forceinline__ void load_line_twiddles(cpx<T> *twl, cpx<T> *w32, const cpx<T> *ftw, int F)
+{
+    for (int t = threadIdx.x; t < L; t += F4_THREADS) twl[t] = ftw[(size_t)((t >> 5) * (t & 31)) * (F / L)];
+    for (int t = threadIdx.x; t < 16; t += F4_THREADS) w32[t] = ftw[(size_t)t * (F / 32)];
+}
+
+// staging tile row length: conflict-free column access by F4W lines (8-byte
+// elements: a pad of two; 16-byte elements: one)
+template <typename T, int L>
+struct F4Stage {
+    static constexpr int LS = L + (sizeof(T) == 4 ? 2 : 1);
+    static constexpr size_t BYTES = (size_t)(L + 16 + F4W * LS) * sizeof(cpx<T>);
+};
+
 }  // namespace
 
 // ---- pass 1: lines over n1 (length F1), one per n2
@@ -65,13 +190,13 @@ template <typename T, int F1, int F2>
 __global__ void __launch_bounds__(F4_THREADS) k_f4_p1(CurveDev c, int mode, int discrete, int gate)
 {
     using V2 = typename V2of<T>::type;
-    using Sm = F4Smem<T, F1, F1>;
+    constexpr int R = F1 / 32, LS = F4Stage<T, F1>::LS;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    cpx<T> *tw = (cpx<T> *)smem_raw, *buf = tw + Sm::TW, *stage = buf + Sm::BUF;
+    cpx<T> *twl = (cpx<T> *)smem_raw, *w32 = twl + F1, *stage = w32 + 16;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, jm = blockIdx.y;
-    const int n2 = blockIdx.x * F4W + warp;
+    const int n2 = blockIdx.x * F4W + warp, F = F1 * F2;
     const cpx<T> *ftw = (const cpx<T> *)c.ftw;
-    for (int t = threadIdx.x; t < F1 / 2; t += F4_THREADS) tw[t] = ftw[t * F2];   // W_F1^t
+    load_line_twiddles<T, F1>(twl, w32, ftw, F);
     pdl_wait();
     if (gate && !c.sc->active) return;
 
@@ -81,38 +206,37 @@ __global__ void __launch_bounds__(F4_THREADS) k_f4_p1(CurveDev c, int mode, int 
     const T s = discrete ? T(-1) : T(1);
     const int ca = 2 * jm, cb = 2 * jm + 1;
     const bool oka = col_allowed(ca, c.sym), okb = col_allowed(cb, c.sym) && jm != 0;
-    cpx<T> *x = buf + (size_t)warp * 2 * F1, *y = x + F1;
     // z[F2 n1 + n2]: the symmetric extension of the scaled columns (as in the single-CTA form)
+    cpx<T> v[R];
 #pragma unroll
-    for (int n1 = lane; n1 < F1; n1 += 32) {
-        const int k = F2 * n1 + n2;
+    for (int a = 0; a < R; ++a) {
+        const int k = F2 * (lane + 32 * a) + n2;
         int m = -1;
         T f = T(1);
         if (k == 0) { m = 0; f = T(1) + s; }
         else if (k < P) { m = k; f = s; }
         else if (k == P) { m = P; f = T(1) + s; }
         else if (k < 2 * P) { m = 2 * P - k; }
-        cpx<T> v = {0, 0};
+        v[a] = {0, 0};
         if (m >= 0 && f != T(0)) {
             const T cs = f * colscale[m];
             const V2 xv = *reinterpret_cast<const V2 *>(X + (size_t)m * N + ca);
-            v.x = oka ? cs * xv.x : T(0);
-            v.y = okb ? cs * xv.y : T(0);
+            v[a].x = oka ? cs * xv.x : T(0);
+            v[a].y = okb ? cs * xv.y : T(0);
         }
-        x[n1] = v;
     }
-    __syncwarp();
     __syncthreads();   // twiddles
-    cpx<T> *Y = warp_fft<T, F1>(x, y, tw, false, lane);
-    // times W_F^(n2 k1), into the staging tile [line][k1]
+    reg_fft_fwd<T, R>(v, twl, w32, lane);
+    // times W_F^(n2 k1) (table in the scrambled order of k1), into the staging tile
+    const cpx<T> *t1 = ftw + F + (size_t)n2 * F1;
 #pragma unroll
-    for (int k1 = lane; k1 < F1; k1 += 32) stage[(size_t)warp * (F1 + 1) + k1] = cmul(Y[k1], ftw[n2 * k1]);
+    for (int a = 0; a < R; ++a) stage[warp * LS + a * 32 + lane] = cmul(v[a], t1[a * 32 + lane]);
     __syncthreads();
-    // S[jm][k1][n2]: F4W consecutive n2 per k1
-    cpx<T> *S = (cpx<T> *)c.f4s + (size_t)jm * F1 * F2;
+    // S[jm][k1][n2] (k1 in the scrambled order): F4W consecutive n2 per k1
+    cpx<T> *S = (cpx<T> *)c.f4s + (size_t)jm * F;
     for (int e = threadIdx.x; e < F4W * F1; e += F4_THREADS) {
-        const int k1 = e / F4W, w = e % F4W;
-        S[(size_t)k1 * F2 + blockIdx.x * F4W + w] = stage[(size_t)w * (F1 + 1) + k1];
+        const int r = e / F4W, w = e % F4W;
+        S[(size_t)r * F2 + blockIdx.x * F4W + w] = stage[w * LS + r];
     }
 }
 
@@ -120,34 +244,27 @@ __global__ void __launch_bounds__(F4_THREADS) k_f4_p1(CurveDev c, int mode, int 
 template <typename T, int F1, int F2>
 __global__ void __launch_bounds__(F4_THREADS) k_f4_p2(CurveDev c, int gate)
 {
-    using Sm = F4Smem<T, F2, F2>;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    cpx<T> *tw = (cpx<T> *)smem_raw, *buf = tw + Sm::TW;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, jm = blockIdx.y;
-    const int k1 = blockIdx.x * F4W + warp;
-    const cpx<T> *ftw = (const cpx<T> *)c.ftw, *chat = (const cpx<T> *)c.chat + (size_t)k1 * F2;
-    for (int t = threadIdx.x; t < F2 / 2; t += F4_THREADS) tw[t] = ftw[t * F1];   // W_F2^t
+    constexpr int R = F2 / 32;
+    __shared__ cpx<T> twl[F2], w32[16];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, jm = blockIdx.y, F = F1 * F2;
+    const int r = blockIdx.x * F4W + warp;   // position of k1 in the scrambled order
+    const cpx<T> *ftw = (const cpx<T> *)c.ftw, *chat = (const cpx<T> *)c.chat + (size_t)r * F2;
+    const cpx<T> *t2 = ftw + 2 * (size_t)F + (size_t)r * F2;
+    load_line_twiddles<T, F2>(twl, w32, ftw, F);
     pdl_wait();
     if (gate && !c.sc->active) return;
 
-    cpx<T> *S = (cpx<T> *)c.f4s + ((size_t)jm * F1 + k1) * F2;
-    cpx<T> *x = buf + (size_t)warp * 2 * F2, *y = x + F2;
+    cpx<T> *S = (cpx<T> *)c.f4s + (size_t)jm * F + (size_t)r * F2;
+    cpx<T> v[R];
 #pragma unroll
-    for (int n2 = lane; n2 < F2; n2 += 32) x[n2] = S[n2];
-    __syncwarp();
+    for (int a = 0; a < R; ++a) v[a] = S[lane + 32 * a];
     __syncthreads();   // twiddles
-    cpx<T> *Z = warp_fft<T, F2>(x, y, tw, false, lane);
-    cpx<T> *O = (Z == x) ? y : x;
+    reg_fft_fwd<T, R>(v, twl, w32, lane);
 #pragma unroll
-    for (int k2 = lane; k2 < F2; k2 += 32) Z[k2] = cmul(Z[k2], chat[k2]);
-    __syncwarp();
-    cpx<T> *V = warp_fft<T, F2>(Z, O, tw, true, lane);
+    for (int a = 0; a < R; ++a) v[a] = cmul(v[a], chat[a * 32 + lane]);   // spectrum in the same order
+    reg_fft_inv<T, R>(v, twl, w32, lane);
 #pragma unroll
-    for (int n2 = lane; n2 < F2; n2 += 32) {
-        cpx<T> w = ftw[n2 * k1];
-        w.y = -w.y;
-        S[n2] = cmul(V[n2], w);
-    }
+    for (int a = 0; a < R; ++a) S[lane + 32 * a] = cmul(v[a], cconj(t2[lane + 32 * a]));   // W_F^(-n2 k1)
 }
 
 // ---- pass 3: lines over k1 (length F1), one per n2: IFFT and the epilogue
@@ -155,35 +272,33 @@ template <typename T, int F1, int F2>
 __global__ void __launch_bounds__(F4_THREADS) k_f4_p3(CurveDev c, int mode, int discrete, int gate)
 {
     using V2 = typename V2of<T>::type;
-    using Sm = F4Smem<T, F1, F1>;
+    constexpr int R = F1 / 32, LS = F4Stage<T, F1>::LS;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    cpx<T> *tw = (cpx<T> *)smem_raw, *buf = tw + Sm::TW, *stage = buf + Sm::BUF;
+    cpx<T> *twl = (cpx<T> *)smem_raw, *w32 = twl + F1, *stage = w32 + 16;
     __shared__ double wsum[F4W];
     __shared__ double red[F4_THREADS];
     __shared__ int am_last;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, jm = blockIdx.y;
-    const int n2 = blockIdx.x * F4W + warp;
-    const cpx<T> *ftw = (const cpx<T> *)c.ftw;
-    for (int t = threadIdx.x; t < F1 / 2; t += F4_THREADS) tw[t] = ftw[t * F2];   // W_F1^t
+    const int n2 = blockIdx.x * F4W + warp, F = F1 * F2;
+    load_line_twiddles<T, F1>(twl, w32, (const cpx<T> *)c.ftw, F);
     DevScalars *sc = c.sc;
     pdl_wait();
     if (gate && !sc->active) return;
     const double lam_d = sc->lambda, dtau_d = sc->dtau;
 
     // S[jm][k1][n2] for this CTA's F4W values of n2 -> staging tile [line][k1]
-    const cpx<T> *S = (const cpx<T> *)c.f4s + (size_t)jm * F1 * F2;
+    const cpx<T> *S = (const cpx<T> *)c.f4s + (size_t)jm * F;
     for (int e = threadIdx.x; e < F4W * F1; e += F4_THREADS) {
-        const int k1 = e / F4W, w = e % F4W;
-        stage[(size_t)w * (F1 + 1) + k1] = S[(size_t)k1 * F2 + blockIdx.x * F4W + w];
+        const int r = e / F4W, w = e % F4W;
+        stage[w * LS + r] = S[(size_t)r * F2 + blockIdx.x * F4W + w];
     }
     __syncthreads();
-    cpx<T> *x = buf + (size_t)warp * 2 * F1, *y = x + F1;
+    cpx<T> v[R];
 #pragma unroll
-    for (int k1 = lane; k1 < F1; k1 += 32) x[k1] = stage[(size_t)warp * (F1 + 1) + k1];
-    __syncwarp();
-    cpx<T> *Y = warp_fft<T, F1>(x, y, tw, true, lane);
+    for (int a = 0; a < R; ++a) v[a] = stage[warp * LS + a * 32 + lane];
+    reg_fft_inv<T, R>(v, twl, w32, lane);
 
-    // epilogue over the sections j = F2 n1 + n2 <= P of the two columns
+    // epilogue over the sections j = F2 n1 + n2 <= P of the two columns (n1 = lane + 32 a)
     const int ns = c.ns, N = c.nx, P = c.P;
     const int ca = 2 * jm, cb = 2 * jm + 1;
     const bool oka = col_allowed(ca, c.sym), okb = col_allowed(cb, c.sym) && jm != 0;
@@ -195,11 +310,11 @@ __global__ void __launch_bounds__(F4_THREADS) k_f4_p3(CurveDev c, int mode, int 
     const double cw = (jm == 0) ? 1.0 : 2.0;
     double partsum = 0.0;
 #pragma unroll
-    for (int n1 = lane; n1 < F1; n1 += 32) {
-        const int j = F2 * n1 + n2;
+    for (int a = 0; a < R; ++a) {
+        const int j = F2 * (lane + 32 * a) + n2;
         if (j >= ns) continue;
         const T rs = rowscale[j];
-        const cpx<T> yv = {rs * Y[n1].x, rs * Y[n1].y};
+        const cpx<T> yv = {rs * v[a].x, rs * v[a].y};
         const size_t o = (size_t)j * N + ca;
         if (mode == GM_STORE) {
             *reinterpret_cast<V2 *>(Dout + o) = V2{oka ? yv.x : T(0), okb ? yv.y : T(0)};
@@ -309,7 +424,8 @@ __global__ void __launch_bounds__(F4_THREADS) k_f4_specA(CurveDev c)
     }
 }
 
-// pass B (per k1): FFT over n2 -> spectrum[k1][k2] / F in the storage type; twiddles
+// pass B (per k1): FFT over n2 -> spectrum / F in the storage type, both indices
+// in the scrambled order of the passes; the plain twiddle table W_F^p
 template <typename T, int F1, int F2>
 __global__ void __launch_bounds__(F4_THREADS) k_f4_specB(CurveDev c)
 {
@@ -325,9 +441,30 @@ __global__ void __launch_bounds__(F4_THREADS) k_f4_specB(CurveDev c)
     for (int n2 = lane; n2 < F2; n2 += 32) x[n2] = S[n2];
     __syncthreads();
     cpx<double> *Z = warp_fft<double, F2>(x, y, tw, false, lane);
-    cpx<T> *chat = (cpx<T> *)c.chat + (size_t)k1 * F2, *ftw = (cpx<T> *)c.ftw;
-    for (int k2 = lane; k2 < F2; k2 += 32) chat[k2] = {(T)(Z[k2].x / F), (T)(Z[k2].y / F)};
+    constexpr int R1 = F1 / 32, R2 = F2 / 32;
+    cpx<T> *chat = (cpx<T> *)c.chat + (size_t)((k1 % R1) * 32 + brev5(k1 / R1)) * F2, *ftw = (cpx<T> *)c.ftw;
+    for (int k2 = lane; k2 < F2; k2 += 32)
+        chat[(k2 % R2) * 32 + brev5(k2 / R2)] = {(T)(Z[k2].x / F), (T)(Z[k2].y / F)};
     for (int p = k1 * F2 + lane; p < (k1 + 1) * F2; p += 32) ftw[p] = {(T)w64[p].x, (T)w64[p].y};
+}
+
+// the step twiddles W_F^(n2 k1) with k1 at its scrambled position r (k1 = r / 32 +
+// R1 brev5(r mod 32)), once as [n2][r] for pass 1 and once as [r][n2] for pass 2
+template <typename T, int F1, int F2>
+__global__ void k_f4_steptw(CurveDev c)
+{
+    constexpr int R1 = F1 / 32, F = F1 * F2;
+    const cpx<double> *w64 = (const cpx<double> *)c.f4s;
+    cpx<T> *t1 = (cpx<T> *)c.ftw + F, *t2 = t1 + F;
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < F; p += gridDim.x * blockDim.x) {
+        int n2 = p / F1, r = p % F1;
+        cpx<double> w = w64[n2 * ((r >> 5) + R1 * brev5(r & 31))];
+        t1[p] = {(T)w.x, (T)w.y};
+        r = p / F2;
+        n2 = p % F2;
+        w = w64[n2 * ((r >> 5) + R1 * brev5(r & 31))];
+        t2[p] = {(T)w.x, (T)w.y};
+    }
 }
 
 // ---- launchers
@@ -335,14 +472,13 @@ template <typename T, int F1, int F2>
 static cudaError_t f4_run(const CurveDev &c, int mode, int discrete, int gate, cudaStream_t st)
 {
     const int nm = c.nx / 2;
-    const size_t sm1 = F4Smem<T, F1, F1>::BYTES, sm2 = F4Smem<T, F2, F2>::BYTES;
+    const size_t sm1 = F4Stage<T, F1>::BYTES;
     cudaError_t e;
     if ((e = set_smem(k_f4_p1<T, F1, F2>, sm1)) != cudaSuccess) return e;
-    if ((e = set_smem(k_f4_p2<T, F1, F2>, sm2)) != cudaSuccess) return e;
     if ((e = set_smem(k_f4_p3<T, F1, F2>, sm1)) != cudaSuccess) return e;
     if ((e = launch_pdl(k_f4_p1<T, F1, F2>, dim3(F2 / F4W, nm), sm1, st, c, mode, discrete, gate)) != cudaSuccess)
         return e;
-    if ((e = launch_pdl(k_f4_p2<T, F1, F2>, dim3(F1 / F4W, nm), sm2, st, c, gate)) != cudaSuccess) return e;
+    if ((e = launch_pdl(k_f4_p2<T, F1, F2>, dim3(F1 / F4W, nm), 0, st, c, gate)) != cudaSuccess) return e;
     return launch_pdl(k_f4_p3<T, F1, F2>, dim3(F2 / F4W, nm), sm1, st, c, mode, discrete, gate);
 }
 
@@ -372,6 +508,7 @@ static cudaError_t setup_run(const CurveDev &c, cudaStream_t st)
     k_f4_twiddles<<<(c.F + 255) / 256, 256, 0, st>>>(c);
     k_f4_specA<F1, F2><<<F2 / F4W, F4_THREADS, smA, st>>>(c);
     k_f4_specB<T, F1, F2><<<F1 / F4W, F4_THREADS, smB, st>>>(c);
+    k_f4_steptw<T, F1, F2><<<(c.F + 255) / 256, 256, 0, st>>>(c);
     return cudaGetLastError();
 }
 

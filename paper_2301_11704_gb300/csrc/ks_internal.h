@@ -150,7 +150,8 @@ struct CurveDev {
     int f4, F1, F2;                    // four-step FFT form (f4 = 1): F = F1 F2
     int F;                 // FFT length of the s-contraction (0: dense form)
     void *chat, *ftw;      // FFT form: kernel spectrum / F and twiddles (complex, storage type);
-                           // four-step form: spectrum stored [k1][k2] for k = k1 + F1 k2
+                           // four-step form: spectrum stored [k1][k2] for k = k1 + F1 k2 (both
+                           // scrambled), twiddles W_F^p [F] then W_F^(n2 k1) as [n2][k1] and [k1][n2]
     void *f4s;             // four-step form: scratch [N/2][F1][F2] (complex, storage type)
     void *cot, *sig, *tau, *sw, *twr;
     double *w;

@@ -126,7 +126,7 @@ Layout make_layout(int ns, int nx, int prec, int allow_split, int bn, int s_tran
     l.off_pert = off; off += al256((size_t)(nx + MAX_PERT + MAX_PERT * nx) * 8);
     l.off_sc = off; off += al256(sizeof(DevScalars));
     l.off_chat = off; off += l.F ? al256((size_t)l.F * 2 * b) : 0;
-    l.off_ftw = off; off += l.F ? al256((size_t)l.F * 2 * b) : 0;
+    l.off_ftw = off; off += l.F ? al256((size_t)l.F * (l.f4 ? 3 : 1) * 2 * b) : 0;   // four-step: + step twiddles
     l.off_f4s = off; off += l.f4 ? al256((size_t)(nx / 2) * l.F * 2 * b) : 0;
     l.total = off;
     return l;
