@@ -4,9 +4,13 @@ against the FP64 oracle and against the dense contraction on the same inputs:
 every pair (F1, F2) the library uses, both adjoints, the descent, ragged N_s and
 the symmetric subspace.
 
-Tolerances: FP64 1e-10 relative; FP32 1e-5 on J and 5e-6 (2-norm) on fields
+Tolerances: FP64 1e-10 relative; FP32 5e-6 (2-norm) on fields and 1e-5 on J
 between the two FP32 forms (each within FP32 rounding of the exact result, about
-2e-6 apart at these sizes)."""
+2e-6 apart at these sizes).  J_arc, a variance of |D_t u| over the sections,
+amplifies the FP32 rounding of D_t u about tenfold; the rounding of a length-F
+FFT convolution grows with log2 F and the size of the cot kernel (up to 2P/pi),
+so J_arc of the FP32 FFT form is held to 3e-5 relative (measured: 1e-5 at
+F = 65536 against the FP64 oracle)."""
 import numpy as np
 import pytest
 import torch
@@ -76,18 +80,35 @@ def test_four_step_matches_dense(precision, N, Ns, F, form):
     cf = KSCurve(L, N, Ns, S, X[0], X[-1], u_init=xt, precision=precision, dtau=1e-3, s_transform=form)
     cd = KSCurve(L, N, Ns, S, X[0], X[-1], u_init=xt, precision=precision, dtau=1e-3, s_transform="dense")
     assert cf.fft_length == F and cd.fft_length == 0
-    ftol, jtol = (5e-6, 1e-5) if precision == "fp32" else (1e-10, 1e-10)
+    ftol, jtol, atol = (5e-6, 1e-5, 3e-5) if precision == "fp32" else (1e-10, 1e-10, 1e-10)
     diff = rel_2 if precision == "fp32" else rel_max
     rf, rd = cf.residual().double().cpu().numpy(), cd.residual().double().cpu().numpy()
     assert diff(rf, rd) < ftol
     (J2f, Jaf), (J2d, Jad) = cf.cost(), cd.cost()
-    assert abs(J2f - J2d) < jtol * J2d and abs(Jaf - Jad) < jtol * Jad
+    assert abs(J2f - J2d) < jtol * J2d and abs(Jaf - Jad) < atol * Jad
     of, od = cf.descend(10), cd.descend(10)
     xf, xd = cf.get_state().double().cpu().numpy(), cd.get_state().double().cpu().numpy()
     assert diff(xf, xd) < ftol
     assert abs(of["J"] - od["J"]) < jtol * od["J"]
     cf.close()
     cd.close()
+
+
+def test_four_step_fp32_matches_oracle():
+    """F = 65536 = 256 x 256 in FP32 against the FP64 oracle on the same (FP32) curve."""
+    N, Ns = 16, 12345
+    L, S = 22.0 + N / 16.0, 0.1 * (Ns - 1)
+    X = _curve(N, Ns, L, N + Ns, fp32=True)
+    c = KSCurve(L, N, Ns, S, X[0], X[-1], u_init=torch.from_numpy(X).float(), precision="fp32", s_transform="fft")
+    assert c.fft_length == 65536
+    U = oracle.curve_spectral(X)
+    R, D = oracle.curve_residual(U, L, S, 1.0)
+    sc = oracle.curve_scalars(R, D, L, S, 1.0)
+    assert rel_2(c.residual().double().cpu().numpy(), oracle.curve_physical(R)) < 2e-6
+    J2, Ja = c.cost()
+    assert abs(J2 - sc["J2"]) < 1e-5 * sc["J2"]
+    assert abs(Ja - sc["J_arc"]) < 3e-5 * sc["J_arc"]
+    c.close()
 
 
 @pytest.mark.parametrize("sym", [1, 3])
