@@ -28,6 +28,7 @@ namespace ks {
 namespace {
 
 constexpr int F4W = F4_THREADS / 32;   // lines per CTA
+static_assert(F4_THREADS / F4W == 32, "passes 1 and 3 map a CTA's threads to F4W lines x 32 positions");
 
 template <typename... KArgs, typename... Args>
 cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, size_t smem, cudaStream_t st, Args... args)
@@ -175,26 +176,67 @@ __device__ __forceinline__ void load_line_twiddles(cpx<T> *twl, cpx<T> *w32, con
     for (int t = threadIdx.x; t < 16; t += F4_THREADS) w32[t] = ftw[(size_t)t * (F / 32)];
 }
 
-// staging tile row length: conflict-free column access by F4W lines (8-byte
-// elements: a pad of two; 16-byte elements: one)
+// Passes 1 and 3 work on MPC modes at once, so that a section row is read and
+// written in whole 32-byte sectors (its columns 2 jm0 .. 2 jm0 + 2 MPC - 1), with
+// F4W lines each: a tile [mode][line][position] in shared memory holds their
+// values between the row accesses, the line transforms and the scratch.  Row
+// length LS pads the line so that the column accesses (F4W lines, one or two
+// positions) fall in distinct banks: 8-byte elements pad two, 16-byte one.
+template <typename T>
+struct F4Sector {
+    static constexpr int MPC = 32 / (2 * (int)sizeof(T));   // 4 (FP32) or 2 (FP64)
+    static constexpr int NV = 2 * MPC;                      // values of a row sector
+};
+
 template <typename T, int L>
 struct F4Stage {
     static constexpr int LS = L + (sizeof(T) == 4 ? 2 : 1);
-    static constexpr size_t BYTES = (size_t)(L + 16 + F4W * LS) * sizeof(cpx<T>);
+    static constexpr int TS = F4W * LS;   // tile stride of a mode
+    static constexpr size_t BYTES = (size_t)(L + 16 + F4Sector<T>::MPC * TS) * sizeof(cpx<T>);
 };
+
+__device__ __forceinline__ void ld_sector(const float *p, float (&x)[8])
+{
+    const float4 a = reinterpret_cast<const float4 *>(p)[0], b = reinterpret_cast<const float4 *>(p)[1];
+    x[0] = a.x; x[1] = a.y; x[2] = a.z; x[3] = a.w; x[4] = b.x; x[5] = b.y; x[6] = b.z; x[7] = b.w;
+}
+__device__ __forceinline__ void ld_sector(const double *p, double (&x)[4])
+{
+    const double2 a = reinterpret_cast<const double2 *>(p)[0], b = reinterpret_cast<const double2 *>(p)[1];
+    x[0] = a.x; x[1] = a.y; x[2] = b.x; x[3] = b.y;
+}
+__device__ __forceinline__ void st_sector(float *p, const float (&x)[8])
+{
+    reinterpret_cast<float4 *>(p)[0] = make_float4(x[0], x[1], x[2], x[3]);
+    reinterpret_cast<float4 *>(p)[1] = make_float4(x[4], x[5], x[6], x[7]);
+}
+__device__ __forceinline__ void st_sector(double *p, const double (&x)[4])
+{
+    reinterpret_cast<double2 *>(p)[0] = make_double2(x[0], x[1]);
+    reinterpret_cast<double2 *>(p)[1] = make_double2(x[2], x[3]);
+}
+
+// the columns 2 jm0 + i of a row sector that the subspace keeps (column 1, the
+// imaginary part of the mean, never)
+__device__ __forceinline__ bool sector_col_ok(int jm0, int i, int sym)
+{
+    const int col = 2 * jm0 + i;
+    return col != 1 && col_allowed(col, sym);
+}
 
 }  // namespace
 
-// ---- pass 1: lines over n1 (length F1), one per n2
+// ---- pass 1: lines over n1 (length F1), one per (n2, mode)
 template <typename T, int F1, int F2>
 __global__ void __launch_bounds__(F4_THREADS) k_f4_p1(CurveDev c, int mode, int discrete, int gate)
 {
-    using V2 = typename V2of<T>::type;
-    constexpr int R = F1 / 32, LS = F4Stage<T, F1>::LS;
+    using Sec = F4Sector<T>;
+    using St = F4Stage<T, F1>;
+    constexpr int R = F1 / 32, LS = St::LS, TS = St::TS, MPC = Sec::MPC, NV = Sec::NV;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    cpx<T> *twl = (cpx<T> *)smem_raw, *w32 = twl + F1, *stage = w32 + 16;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, jm = blockIdx.y;
-    const int n2 = blockIdx.x * F4W + warp, F = F1 * F2;
+    cpx<T> *twl = (cpx<T> *)smem_raw, *w32 = twl + F1, *tile = w32 + 16;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int n2_0 = blockIdx.y * F4W, jm0 = blockIdx.x * MPC, F = F1 * F2;
     const cpx<T> *ftw = (const cpx<T> *)c.ftw;
     load_line_twiddles<T, F1>(twl, w32, ftw, F);
     pdl_wait();
@@ -204,39 +246,61 @@ __global__ void __launch_bounds__(F4_THREADS) k_f4_p1(CurveDev c, int mode, int 
     const T *X = (const T *)(mode == GM_STORE ? c.U : c.R);
     const T *colscale = (const T *)(discrete ? c.sw : c.tau);
     const T s = discrete ? T(-1) : T(1);
-    const int ca = 2 * jm, cb = 2 * jm + 1;
-    const bool oka = col_allowed(ca, c.sym), okb = col_allowed(cb, c.sym) && jm != 0;
-    // z[F2 n1 + n2]: the symmetric extension of the scaled columns (as in the single-CTA form)
-    cpx<T> v[R];
+    // z[F2 n1 + n2] of the MPC modes (the symmetric extension of the scaled
+    // columns, as in the single-CTA form): thread -> line n2_0 + tn, n1 = t / F4W + 32 i.
+    // Rows are fetched two at a time, both loads issued before either is used.
+    const int tn = threadIdx.x % F4W;
 #pragma unroll
-    for (int a = 0; a < R; ++a) {
-        const int k = F2 * (lane + 32 * a) + n2;
-        int m = -1;
-        T f = T(1);
-        if (k == 0) { m = 0; f = T(1) + s; }
-        else if (k < P) { m = k; f = s; }
-        else if (k == P) { m = P; f = T(1) + s; }
-        else if (k < 2 * P) { m = 2 * P - k; }
-        v[a] = {0, 0};
-        if (m >= 0 && f != T(0)) {
-            const T cs = f * colscale[m];
-            const V2 xv = *reinterpret_cast<const V2 *>(X + (size_t)m * N + ca);
-            v[a].x = oka ? cs * xv.x : T(0);
-            v[a].y = okb ? cs * xv.y : T(0);
+    for (int i0 = 0; i0 < R; i0 += 2) {
+        T x[2][NV], cs[2];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int k = F2 * (threadIdx.x / F4W + 32 * (i0 + h)) + n2_0 + tn;
+            int m = -1;
+            T f = T(1);
+            if (k == 0) { m = 0; f = T(1) + s; }
+            else if (k < P) { m = k; f = s; }
+            else if (k == P) { m = P; f = T(1) + s; }
+            else if (k < 2 * P) { m = 2 * P - k; }
+            cs[h] = T(0);
+#pragma unroll
+            for (int q = 0; q < NV; ++q) x[h][q] = T(0);
+            if (m >= 0 && f != T(0)) {
+                cs[h] = f * colscale[m];
+                ld_sector(X + (size_t)m * N + 2 * jm0, x[h]);
+            }
+        }
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int n1 = threadIdx.x / F4W + 32 * (i0 + h);
+#pragma unroll
+            for (int q = 0; q < MPC; ++q)
+                tile[q * TS + tn * LS + n1] = {sector_col_ok(jm0, 2 * q, c.sym) ? cs[h] * x[h][2 * q] : T(0),
+                                               sector_col_ok(jm0, 2 * q + 1, c.sym) ? cs[h] * x[h][2 * q + 1] : T(0)};
         }
     }
-    __syncthreads();   // twiddles
-    reg_fft_fwd<T, R>(v, twl, w32, lane);
-    // times W_F^(n2 k1) (table in the scrambled order of k1), into the staging tile
-    const cpx<T> *t1 = ftw + F + (size_t)n2 * F1;
+    // the step twiddles W_F^(n2 k1) of this warp's line (scrambled order of k1)
+    const cpx<T> *t1 = ftw + F + (size_t)(n2_0 + warp) * F1;
+    cpx<T> tw1[R];
 #pragma unroll
-    for (int a = 0; a < R; ++a) stage[warp * LS + a * 32 + lane] = cmul(v[a], t1[a * 32 + lane]);
+    for (int a = 0; a < R; ++a) tw1[a] = t1[a * 32 + lane];
     __syncthreads();
-    // S[jm][k1][n2] (k1 in the scrambled order): F4W consecutive n2 per k1
-    cpx<T> *S = (cpx<T> *)c.f4s + (size_t)jm * F;
-    for (int e = threadIdx.x; e < F4W * F1; e += F4_THREADS) {
-        const int r = e / F4W, w = e % F4W;
-        S[(size_t)r * F2 + blockIdx.x * F4W + w] = stage[w * LS + r];
+    for (int q = 0; q < MPC; ++q) {
+        cpx<T> *line = tile + q * TS + warp * LS;
+        cpx<T> v[R];
+#pragma unroll
+        for (int a = 0; a < R; ++a) v[a] = line[lane + 32 * a];
+        __syncwarp();
+        reg_fft_fwd<T, R>(v, twl, w32, lane);
+#pragma unroll
+        for (int a = 0; a < R; ++a) line[a * 32 + lane] = cmul(v[a], tw1[a]);
+    }
+    __syncthreads();
+    // S[jm][k1][n2] (k1 in the scrambled order): F4W consecutive n2 per (mode, k1)
+    cpx<T> *S = (cpx<T> *)c.f4s;
+    for (int e = threadIdx.x; e < MPC * F1 * F4W; e += F4_THREADS) {
+        const int w = e % F4W, r = (e / F4W) % F1, q = e / (F4W * F1);
+        S[((size_t)(jm0 + q) * F1 + r) * F2 + n2_0 + w] = tile[q * TS + w * LS + r];
     }
 }
 
@@ -267,74 +331,108 @@ __global__ void __launch_bounds__(F4_THREADS) k_f4_p2(CurveDev c, int gate)
     for (int a = 0; a < R; ++a) S[lane + 32 * a] = cmul(v[a], cconj(t2[lane + 32 * a]));   // W_F^(-n2 k1)
 }
 
-// ---- pass 3: lines over k1 (length F1), one per n2: IFFT and the epilogue
+// ---- pass 3: lines over k1 (length F1), one per (n2, mode): IFFT and the epilogue
 template <typename T, int F1, int F2>
 __global__ void __launch_bounds__(F4_THREADS) k_f4_p3(CurveDev c, int mode, int discrete, int gate)
 {
-    using V2 = typename V2of<T>::type;
-    constexpr int R = F1 / 32, LS = F4Stage<T, F1>::LS;
+    using Sec = F4Sector<T>;
+    using St = F4Stage<T, F1>;
+    constexpr int R = F1 / 32, LS = St::LS, TS = St::TS, MPC = Sec::MPC, NV = Sec::NV;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    cpx<T> *twl = (cpx<T> *)smem_raw, *w32 = twl + F1, *stage = w32 + 16;
+    cpx<T> *twl = (cpx<T> *)smem_raw, *w32 = twl + F1, *tile = w32 + 16;
     __shared__ double wsum[F4W];
     __shared__ double red[F4_THREADS];
     __shared__ int am_last;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, jm = blockIdx.y;
-    const int n2 = blockIdx.x * F4W + warp, F = F1 * F2;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int n2_0 = blockIdx.y * F4W, jm0 = blockIdx.x * MPC, F = F1 * F2;
     load_line_twiddles<T, F1>(twl, w32, (const cpx<T> *)c.ftw, F);
     DevScalars *sc = c.sc;
     pdl_wait();
     if (gate && !sc->active) return;
     const double lam_d = sc->lambda, dtau_d = sc->dtau;
 
-    // S[jm][k1][n2] for this CTA's F4W values of n2 -> staging tile [line][k1]
-    const cpx<T> *S = (const cpx<T> *)c.f4s + (size_t)jm * F;
-    for (int e = threadIdx.x; e < F4W * F1; e += F4_THREADS) {
-        const int r = e / F4W, w = e % F4W;
-        stage[w * LS + r] = S[(size_t)r * F2 + blockIdx.x * F4W + w];
+    // S[jm][k1][n2] of this CTA's lines and modes -> tile
+    const cpx<T> *S = (const cpx<T> *)c.f4s;
+    for (int e = threadIdx.x; e < MPC * F1 * F4W; e += F4_THREADS) {
+        const int w = e % F4W, r = (e / F4W) % F1, q = e / (F4W * F1);
+        tile[q * TS + w * LS + r] = S[((size_t)(jm0 + q) * F1 + r) * F2 + n2_0 + w];
     }
     __syncthreads();
-    cpx<T> v[R];
+    for (int q = 0; q < MPC; ++q) {
+        cpx<T> *line = tile + q * TS + warp * LS;
+        cpx<T> v[R];
 #pragma unroll
-    for (int a = 0; a < R; ++a) v[a] = stage[warp * LS + a * 32 + lane];
-    reg_fft_inv<T, R>(v, twl, w32, lane);
+        for (int a = 0; a < R; ++a) v[a] = line[a * 32 + lane];
+        __syncwarp();
+        reg_fft_inv<T, R>(v, twl, w32, lane);
+#pragma unroll
+        for (int a = 0; a < R; ++a) line[lane + 32 * a] = v[a];
+    }
+    __syncthreads();
 
-    // epilogue over the sections j = F2 n1 + n2 <= P of the two columns (n1 = lane + 32 a)
-    const int ns = c.ns, N = c.nx, P = c.P;
-    const int ca = 2 * jm, cb = 2 * jm + 1;
-    const bool oka = col_allowed(ca, c.sym), okb = col_allowed(cb, c.sym) && jm != 0;
+    // epilogue over the sections j = F2 n1 + n2 < N_s: thread -> line n2_0 + tn,
+    // n1 = t / F4W + 32 i; the MPC modes' columns of row j as one sector.  Two rows
+    // at a time, all their loads issued before the arithmetic.
+    const int ns = c.ns, N = c.nx, P = c.P, sym = c.sym;
     const T *rowscale = (const T *)(discrete ? c.twr : c.sig);
     T *Dout = (T *)c.D, *U = (T *)c.U, *G = (T *)c.G;
     const T *Ah = (const T *)c.A;
-    const T pr = ((const T *)c.prec_imex)[jm];
+    const T *prec = (const T *)c.prec_imex + jm0;
     const T lam = (T)lam_d, dtau = (T)dtau_d;
-    const double cw = (jm == 0) ? 1.0 : 2.0;
+    const int tn = threadIdx.x % F4W;
     double partsum = 0.0;
 #pragma unroll
-    for (int a = 0; a < R; ++a) {
-        const int j = F2 * (lane + 32 * a) + n2;
-        if (j >= ns) continue;
-        const T rs = rowscale[j];
-        const cpx<T> yv = {rs * v[a].x, rs * v[a].y};
-        const size_t o = (size_t)j * N + ca;
-        if (mode == GM_STORE) {
-            *reinterpret_cast<V2 *>(Dout + o) = V2{oka ? yv.x : T(0), okb ? yv.y : T(0)};
-            continue;
-        }
-        const bool interior = (j > 0 && j < P);
-        T ga = 0, gb = 0;
-        if (interior) {
-            const V2 av = *reinterpret_cast<const V2 *>(Ah + o);
-            if (oka) ga = -(av.x + (discrete ? -lam * yv.x : lam * yv.x));
-            if (okb) gb = -(av.y + (discrete ? -lam * yv.y : lam * yv.y));
-            partsum += c.w[j] * cw * ((double)ga * (double)ga + (double)gb * (double)gb);
-        }
-        if (mode == GM_UPDATE) {
-            if (interior) {
-                const V2 uv = *reinterpret_cast<const V2 *>(U + o);
-                *reinterpret_cast<V2 *>(U + o) = V2{uv.x + dtau * pr * ga, uv.y + dtau * pr * gb};
+    for (int i0 = 0; i0 < R; i0 += 2) {
+        int jv[2];
+        T rsv[2], av[2][NV], uv[2][NV];
+        double wv[2] = {0.0, 0.0};
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int j = F2 * (threadIdx.x / F4W + 32 * (i0 + h)) + n2_0 + tn;
+            jv[h] = j;
+            rsv[h] = rowscale[j < ns ? j : 0];
+            if (mode != GM_STORE && j > 0 && j < P) {
+                const size_t o = (size_t)j * N + 2 * jm0;
+                ld_sector(Ah + o, av[h]);
+                if (mode == GM_UPDATE) ld_sector(U + o, uv[h]);
+                wv[h] = c.w[j];
             }
-        } else {
-            *reinterpret_cast<V2 *>(G + o) = V2{ga, gb};
+        }
+        if (jv[0] >= ns) break;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int j = jv[h], n1 = threadIdx.x / F4W + 32 * (i0 + h);
+            if (j >= ns) break;
+            T y[NV];
+#pragma unroll
+            for (int q = 0; q < MPC; ++q) {
+                const cpx<T> t = tile[q * TS + tn * LS + n1];
+                y[2 * q] = sector_col_ok(jm0, 2 * q, sym) ? rsv[h] * t.x : T(0);
+                y[2 * q + 1] = sector_col_ok(jm0, 2 * q + 1, sym) ? rsv[h] * t.y : T(0);
+            }
+            const size_t o = (size_t)j * N + 2 * jm0;
+            if (mode == GM_STORE) {
+                st_sector(Dout + o, y);
+                continue;
+            }
+            T g[NV];
+            if (j > 0 && j < P) {
+#pragma unroll
+                for (int q = 0; q < NV; ++q) {
+                    g[q] = sector_col_ok(jm0, q, sym) ? -(av[h][q] + (discrete ? -lam * y[q] : lam * y[q])) : T(0);
+                    const double cw = (jm0 + q / 2 == 0) ? 1.0 : 2.0;
+                    partsum += wv[h] * cw * ((double)g[q] * (double)g[q]);
+                }
+                if (mode == GM_UPDATE) {
+#pragma unroll
+                    for (int q = 0; q < NV; ++q) uv[h][q] += dtau * prec[q / 2] * g[q];
+                    st_sector(U + o, uv[h]);
+                }
+            } else {
+#pragma unroll
+                for (int q = 0; q < NV; ++q) g[q] = T(0);
+            }
+            if (mode == GM_GRAD) st_sector(G + o, g);
         }
     }
     if (mode == GM_STORE) return;
@@ -343,7 +441,7 @@ __global__ void __launch_bounds__(F4_THREADS) k_f4_p3(CurveDev c, int mode, int 
     partsum = warp_sum(partsum);
     if (lane == 0) wsum[warp] = partsum;
     __syncthreads();
-    const int bid = jm * gridDim.x + blockIdx.x, nb = gridDim.x * gridDim.y;
+    const int bid = blockIdx.y * gridDim.x + blockIdx.x, nb = gridDim.x * gridDim.y;
     if (threadIdx.x == 0) {
         double t = 0.0;
         for (int w = 0; w < F4W; ++w) t += wsum[w];
@@ -473,13 +571,14 @@ static cudaError_t f4_run(const CurveDev &c, int mode, int discrete, int gate, c
 {
     const int nm = c.nx / 2;
     const size_t sm1 = F4Stage<T, F1>::BYTES;
+    const int nmb = c.nx / 2 / F4Sector<T>::MPC;
     cudaError_t e;
     if ((e = set_smem(k_f4_p1<T, F1, F2>, sm1)) != cudaSuccess) return e;
     if ((e = set_smem(k_f4_p3<T, F1, F2>, sm1)) != cudaSuccess) return e;
-    if ((e = launch_pdl(k_f4_p1<T, F1, F2>, dim3(F2 / F4W, nm), sm1, st, c, mode, discrete, gate)) != cudaSuccess)
+    if ((e = launch_pdl(k_f4_p1<T, F1, F2>, dim3(nmb, F2 / F4W), sm1, st, c, mode, discrete, gate)) != cudaSuccess)
         return e;
     if ((e = launch_pdl(k_f4_p2<T, F1, F2>, dim3(F1 / F4W, nm), 0, st, c, gate)) != cudaSuccess) return e;
-    return launch_pdl(k_f4_p3<T, F1, F2>, dim3(F2 / F4W, nm), sm1, st, c, mode, discrete, gate);
+    return launch_pdl(k_f4_p3<T, F1, F2>, dim3(nmb, F2 / F4W), sm1, st, c, mode, discrete, gate);
 }
 
 template <typename T>

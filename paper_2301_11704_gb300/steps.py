@@ -20,6 +20,8 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=2)
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--s-transform", default="auto", choices=["auto", "dense", "fft", "dense_tc", "fft4"])
+    ap.add_argument("--phases", action="store_true",
+                    help="after the timed steps, time the phases of --steps more steps (rows, the two contractions)")
     args = ap.parse_args(argv)
 
     import torch
@@ -41,10 +43,20 @@ def main(argv=None):
         e1.record()
         torch.cuda.synchronize()
         ms.append(e0.elapsed_time(e1))
+    phases = None
+    if args.phases:
+        c.profile(args.steps)
+        c.descend_async(args.steps)
+        torch.cuda.synchronize()
+        phases = {k: v["ms"] / max(1, v["launches"]) for k, v in c.profile_read().items() if "launches" in v}
+        c.profile(0)
     sc = c.scalars()
     c.close()
-    print(json.dumps({"L": sp.L, "N_x": sp.N, "N_s": sp.Ns, "precision": args.precision,
-                      "fft_length": c.fft_length, "ms_per_step": ms, "J": sc["J"]}))
+    out = {"L": sp.L, "N_x": sp.N, "N_s": sp.Ns, "precision": args.precision,
+           "fft_length": c.fft_length, "ms_per_step": ms, "J": sc["J"]}
+    if phases is not None:
+        out["ms_per_phase_launch"] = phases
+    print(json.dumps(out))
     return 0
 
 
