@@ -5,8 +5,9 @@ Metric: curve-point adjoint-gradient evaluations per second, i.e. interior
 curve points (M = N_s - 2 per curve) x descent steps / time.  One bench step is
 one full descent step of the workload curve: the row phase (f, residual,
 spatial adjoint, FP64 cost reductions), the s-phase with the descent update and
-|G|^2, and the s-phase D_t u of the new state (three kernels, plus the one-thread
-kernel that arms the step counter).
+|G|^2, and the s-phase D_t u of the new state (one kernel each, three each in
+the three-launch four-step form, plus the one-thread kernel that arms the step
+counter).
 
 Default workload: L = 22, N_x = 64, N_s = 1024 (the differentiation workload),
 FP32 storage and transforms with FP64 reductions.  The curve is far smaller
@@ -47,7 +48,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32")
-    ap.add_argument("--s-transform", choices=["auto", "dense", "fft"], default="auto",
+    ap.add_argument("--s-transform", choices=["auto", "dense", "fft", "dense_tc", "fft4", "fft4c"], default="auto",
                     help="how D_t is applied along s in the headline curve")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the oracle CPU baseline")
     ap.add_argument("--e2e-steps", type=int, default=100)
@@ -308,12 +309,17 @@ def main():
     dom = max(avg, key=avg.get)
     from paper_2301_11704_gb300.build import fft_length
     F = curve.fft_length
+    form_name = {"dense": "dense contraction", "dense_tc": "dense contraction on the tensor cores",
+                 "fft": "FFT convolution, one CTA per mode", "fft4": "four-step FFT convolution, three launches",
+                 "fft4c": "four-step FFT convolution, one clustered launch"}[curve.s_form]
     if F:   # FFT form: per mode two complex FFTs of length F and the spectral product
         flops_dt = (spec.N // 2) * (2 * 5.0 * F * np.log2(F) + 6.0 * F)
-        dt_form = "FFT convolution, F=%d" % F
+        dt_form = "%s, F=%d" % (form_name, F)
     else:
         flops_dt = 2.0 * spec.Ns * spec.Ns * spec.N
-        dt_form = "dense contraction"
+        dt_form = form_name
+    # kernels per step: the step-limit kernel, the row phase, two s-contractions
+    launches_per_step = 2 + 2 * (3 if curve.s_form == "fft4" else 1)
     peak_alu = (N_SM * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12) if b == 4 else 1.25
     peaks = {}
     try:
@@ -407,8 +413,8 @@ def main():
             msl, _ = timed_steps(cl, kl, 3)
             large.append({"workload": "L=%g N_x=%d N_s=%d FP32" % (sp.L, sp.N, sp.Ns),
                           "value": sp.M * kl / (sum(msl) / 1e3), "unit": UNIT, "ms_per_step": sum(msl) / kl,
-                          "steps": kl, "s_transform": ("FFT convolution, F=%d" % cl.fft_length) if cl.fft_length
-                          else "dense contraction"})
+                          "steps": kl, "s_transform": "%s%s" % (cl.s_form, (", F=%d" % cl.fft_length) if cl.fft_length
+                                                                else "")})
             cl.close()
 
     cpu = None
@@ -423,7 +429,7 @@ def main():
                 "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "f64", "data": "synthetic",
                 "config": dict(workload_config(spec, args.precision.upper()), s_transform=dt_form),
                 "roofline": roof,
-                "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": 4 * K, "clocks": clk,
+                "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches_per_step * K, "clocks": clk,
                 "fp64_gpu_path": fp64, "larger_workloads": large, "other_s_transform": other, "steady_state": steady, "final_J": sc["J"], "final_J_arc": sc["J_arc"],
                 "step_ms_median": statistics.median(step_ms)}
         print(json.dumps(line))

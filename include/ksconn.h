@@ -90,13 +90,15 @@ typedef struct {
                             0 = none.  Values above 3 are invalid. */
     int32_t s_transform; /* how D_t is applied along s (same result to rounding):
                             0 auto: for a single curve the form measured fastest on GB300 for its
-                            size: at N_x >= 256 the one-CTA FFT form where it fits; the four-step
-                            FFT form for 683 < N_s <= 21846 in FP64, and in FP32 from N_s >= 1366
-                            (N_s >= 1024 at N_x >= 128); below that the one-CTA FFT form when
-                            N_s N_x >= 131072 (FP32) or N_x >= 64 or N_s <= 128 (FP64); else dense
-                            (on the tensor cores for FP32 when N_s >= 8192, or N_s >= 4096 at
-                            N_x >= 128: above the four-step limit); in a batch the one-CTA FFT
-                            form wherever it fits;
+                            size: from N_s = 684 on (FFT length >= 4096) a four-step FFT form:
+                            in FP32 the clustered one (5) at N_x <= 64 up to N_s = 5462 and at
+                            N_x = 128 up to N_s = 2731, else the three-launch one (4); in FP64
+                            the clustered one at N_x <= 16 up to N_s = 1366, the one-CTA form
+                            at N_x = 256 while it fits (N_s <= 1366), else the three-launch one;
+                            below N_s = 684 dense, or in FP64 the one-CTA FFT form at N_x >= 64
+                            or N_s <= 128; above the four-step limit dense (on the tensor cores
+                            for FP32 when N_s >= 8192, or N_s >= 4096 at N_x >= 128); in a
+                            batch the one-CTA FFT form wherever it fits;
                             1 dense contraction generated from the O(N_s) cot table;
                             2 FFT convolution (N_s <= 21846; one CTA per mode up to N_s = 2731
                             FP32 / 1366 FP64, the four-step form above);
@@ -105,7 +107,11 @@ typedef struct {
                             FP32 accumulation per 32 sections, FP32 sums across them);
                             4 FFT convolution in the four-step form (transform length F = F1 F2
                             from 4096 to 65536: 684 <= N_s <= 21846), which 2 and auto use
-                            above one CTA's limit */
+                            above one CTA's limit: three launches through a scratch array;
+                            5 the same four-step form in one launch: a cluster of 8 CTAs per
+                            one or two Fourier modes holds their intermediate array in
+                            distributed shared memory (same N_s range as 4, in FP64 up to
+                            N_s = 10923: F <= 32768) */
     int32_t launch;      /* how a single curve's descent steps are launched (same results):
                             0 three kernels per step, chained by programmatic dependent
                             launch and replayed from a CUDA graph;
@@ -149,6 +155,12 @@ size_t ks_curve_workspace_bytes(const ks_params *p);
  * (s_transform rule above), or 0 when it uses the dense contraction.  -1 when
  * p is invalid (message in ks_last_error). */
 int32_t ks_curve_fft_length(const ks_params *p);
+
+/* The form a single curve with parameters p applies D_t in, as an s_transform
+ * code with `auto` resolved: 1 dense, 2 FFT with one CTA per mode, 3 dense on the
+ * tensor cores, 4 four-step FFT in three launches, 5 four-step FFT in one
+ * clustered launch.  -1 when p is invalid (message in ks_last_error). */
+int32_t ks_curve_s_form(const ks_params *p);
 
 /* Creates a curve (Sec. V.C.1-2).
  *  p            parameters (copied).

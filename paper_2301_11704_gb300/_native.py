@@ -19,7 +19,7 @@ KS_CONV_JARC, KS_CONV_J, KS_CONV_JREL = 0, 1, 2
 
 # Every symbol include/ksconn.h declares.
 EXPORTS = [
-    "ks_last_error", "ks_version", "ks_curve_workspace_bytes", "ks_curve_fft_length", "ks_curve_create", "ks_curve_set_stream",
+    "ks_last_error", "ks_version", "ks_curve_workspace_bytes", "ks_curve_fft_length", "ks_curve_s_form", "ks_curve_create", "ks_curve_set_stream",
     "ks_curve_init_trial", "ks_curve_residual", "ks_curve_cost", "ks_curve_gradient", "ks_curve_descend",
     "ks_curve_descend_async", "ks_curve_scalars", "ks_curve_get_state", "ks_curve_set_state", "ks_curve_profile",
     "ks_curve_profile_read", "ks_curve_destroy", "ks_cost_noalloc",
@@ -102,6 +102,7 @@ def load(build_if_missing: bool = True):
         "ks_version": (i32, []),
         "ks_curve_workspace_bytes": (sz, [ctypes.POINTER(KSParams)]),
         "ks_curve_fft_length": (i32, [ctypes.POINTER(KSParams)]),
+        "ks_curve_s_form": (i32, [ctypes.POINTER(KSParams)]),
         "ks_curve_create": (i32, [ctypes.POINTER(KSParams), pd, pd, p, p, sz, p, ctypes.POINTER(p)]),
         "ks_curve_set_stream": (i32, [p, p]),
         "ks_curve_init_trial": (i32, [p, d, pd, i32, pd, pd]),

@@ -86,10 +86,16 @@ ks_status validate(const ks_params *p)
     if (p->conv < KS_CONV_JARC || p->conv > KS_CONV_JREL) return fail(KS_EINVAL, "conv must be a ks_conv value");
     if (p->check_ends != 0 && p->check_ends != 1) return fail(KS_EINVAL, "check_ends must be 0 or 1");
     if (p->symmetry < 0 || p->symmetry > 3) return fail(KS_EINVAL, "symmetry must be in [0, 3]");
-    if (p->s_transform < 0 || p->s_transform > 4) return fail(KS_EINVAL, "s_transform must be in [0, 4]");
-    if (p->s_transform == 4 && ks::fft4_size(p->ns, p->precision == KS_FP32, 1) == 0)
+    if (p->s_transform < 0 || p->s_transform > 5) return fail(KS_EINVAL, "s_transform must be in [0, 5]");
+    if ((p->s_transform == 4 || p->s_transform == 5) && ks::fft4_size(p->ns, p->precision == KS_FP32, 1) == 0)
         return fail(KS_EINVAL, "s_transform = four-step FFT needs %d <= 3 (N_s - 1) <= %d (rounded up to a power of two)",
                     ks::F4_FMIN / 2 + 1, ks::F4_FMAX);
+    if (p->s_transform == 5) {
+        int F1 = 0, F2 = 0;
+        ks::f4_split(ks::fft4_size(p->ns, p->precision == KS_FP32, 1), F1, F2);
+        if (!ks::f4c_fits(p->precision == KS_FP32, F1, F2))
+            return fail(KS_EINVAL, "s_transform = clustered four-step FFT holds F <= 32768 in FP64 (N_s <= 10923)");
+    }
     if (p->s_transform == 3 && p->precision != KS_FP32)
         return fail(KS_EINVAL, "s_transform = tensor cores needs FP32 storage");
     if (p->launch < 0 || p->launch > 1) return fail(KS_EINVAL, "launch must be 0 or 1");
@@ -255,6 +261,15 @@ int32_t ks_curve_fft_length(const ks_params *p)
 {
     if (validate(p) != KS_OK) return -1;
     return ks::make_layout(p->ns, p->nx, p->precision == KS_FP32, 1, 0, p->s_transform).F;
+}
+
+int32_t ks_curve_s_form(const ks_params *p)
+{
+    if (validate(p) != KS_OK) return -1;
+    const ks::Layout l = ks::make_layout(p->ns, p->nx, p->precision == KS_FP32, 1, 0, p->s_transform);
+    if (l.f4) return l.f4c ? 5 : 4;
+    if (l.F) return 2;
+    return l.tc ? 3 : 1;
 }
 
 ks_status ks_curve_create(const ks_params *p, const double *u_plus_host, const double *u_minus_host,

@@ -21,6 +21,8 @@
 //          increment and the FP64 |G|^2 with its last-CTA sum).
 #include <cmath>
 
+#include <cooperative_groups.h>
+
 #include "ks_device.cuh"
 
 namespace ks {
@@ -129,22 +131,50 @@ __device__ __forceinline__ void reg_dft(cpx<T> (&v)[R], bool inv)
     for (int i = 0; i < R; ++i) v[i] = t[i];
 }
 
+// The cross-lane stages come in two forms.  FP32 (latency-bound): each lane
+// fetches its partner's value and computes its half of the butterfly (the lower
+// lanes multiply by 1).  FP64 (bound by GB300's FP64 rate): on the register pair
+// (a, a + 1) lanes l and l ^ m first swap one value each, so that the lower lane
+// holds both inputs of register a's butterfly and the upper lane both of register
+// a + 1's; each lane does a whole butterfly and a second swap restores the
+// layout: the same shuffles, half the arithmetic.
+template <typename T>
+__device__ __forceinline__ void lane_swap(cpx<T> &v0, cpx<T> &v1, bool up, int m)
+{
+    const cpx<T> r = cshfl(up ? v0 : v1, m);
+    if (up) v0 = r;
+    else v1 = r;
+}
+
 // twl[a * 32 + l] = W_L^(a l) (a < R), w32[s] = W_32^s (s < 16)
 template <typename T, int R>
 __device__ __forceinline__ void reg_fft_fwd(cpx<T> (&v)[R], const cpx<T> *twl, const cpx<T> *w32, int lane)
 {
+    static_assert(R % 2 == 0, "register pairs");
     reg_dft<T, R>(v, false);
 #pragma unroll
     for (int a = 1; a < R; ++a) v[a] = cmul(v[a], twl[a * 32 + lane]);
 #pragma unroll
     for (int m = 16; m >= 1; m >>= 1) {
         const bool up = (lane & m) != 0;
-        const cpx<T> w = w32[up ? (lane & (m - 1)) * (16 / m) : 0];   // W_2m^(pos - m) on the upper lanes
+        if constexpr (sizeof(T) == 8) {
+            const cpx<T> w = w32[(lane & (m - 1)) * (16 / m)];   // W_2m^(position within the half)
 #pragma unroll
-        for (int a = 0; a < R; ++a) {
-            const cpx<T> p = cshfl(v[a], m);
-            const cpx<T> d = up ? csub(p, v[a]) : cadd(v[a], p);
-            v[a] = (m > 1) ? cmul(d, w) : d;
+            for (int a = 0; a < R; a += 2) {
+                lane_swap(v[a], v[a + 1], up, m);
+                const cpx<T> x = v[a], y = v[a + 1];
+                v[a] = cadd(x, y);
+                v[a + 1] = (m > 1) ? cmul(csub(x, y), w) : csub(x, y);
+                lane_swap(v[a], v[a + 1], up, m);
+            }
+        } else {
+            const cpx<T> w = w32[up ? (lane & (m - 1)) * (16 / m) : 0];   // 1 on the lower lanes
+#pragma unroll
+            for (int a = 0; a < R; ++a) {
+                const cpx<T> p = cshfl(v[a], m);
+                const cpx<T> d = up ? csub(p, v[a]) : cadd(v[a], p);
+                v[a] = (m > 1) ? cmul(d, w) : d;
+            }
         }
     }
 }
@@ -152,15 +182,28 @@ __device__ __forceinline__ void reg_fft_fwd(cpx<T> (&v)[R], const cpx<T> *twl, c
 template <typename T, int R>
 __device__ __forceinline__ void reg_fft_inv(cpx<T> (&v)[R], const cpx<T> *twl, const cpx<T> *w32, int lane)
 {
+    static_assert(R % 2 == 0, "register pairs");
 #pragma unroll
     for (int m = 1; m <= 16; m <<= 1) {
         const bool up = (lane & m) != 0;
-        const cpx<T> w = cconj(w32[up ? (lane & (m - 1)) * (16 / m) : 0]);
+        if constexpr (sizeof(T) == 8) {
+            const cpx<T> w = cconj(w32[(lane & (m - 1)) * (16 / m)]);
 #pragma unroll
-        for (int a = 0; a < R; ++a) {
-            const cpx<T> b = (m > 1) ? cmul(v[a], w) : v[a];
-            const cpx<T> p = cshfl(b, m);
-            v[a] = up ? csub(p, b) : cadd(b, p);
+            for (int a = 0; a < R; a += 2) {
+                lane_swap(v[a], v[a + 1], up, m);
+                const cpx<T> x = v[a], y = (m > 1) ? cmul(v[a + 1], w) : v[a + 1];
+                v[a] = cadd(x, y);
+                v[a + 1] = csub(x, y);
+                lane_swap(v[a], v[a + 1], up, m);
+            }
+        } else {
+            const cpx<T> w = cconj(w32[up ? (lane & (m - 1)) * (16 / m) : 0]);
+#pragma unroll
+            for (int a = 0; a < R; ++a) {
+                const cpx<T> b = (m > 1) ? cmul(v[a], w) : v[a];
+                const cpx<T> p = cshfl(b, m);
+                v[a] = up ? csub(p, b) : cadd(b, p);
+            }
         }
     }
 #pragma unroll
@@ -470,6 +513,296 @@ __global__ void __launch_bounds__(F4_THREADS) k_f4_p3(CurveDev c, int mode, int 
     }
 }
 
+// ---- the clustered form: the three passes of MPC modes in one launch, by a
+// cluster of CS CTAs that holds the modes' whole intermediate array in
+// distributed shared memory.  CTA `rank` owns the scrambled rows r of k1 in
+// [rank F1/CS, (rank + 1) F1/CS) (all n2) and the lines n2 in [rank F2/CS, ...):
+//   pass 1: FFT over n1 of its lines into a local tile [mode][line][r], then each
+//           row's run of its lines copied to the row's owner in 16-byte chunks;
+//   pass 2: FFT, spectrum, IFFT over n2 of its own rows, in place;
+//   pass 3: its lines' runs copied back from the rows' owners into the tile,
+//           IFFT over k1, epilogue.
+// Remote shared memory is only moved in contiguous 16-byte chunks (scattered
+// 8-byte remote accesses cost several cycles each, measured).  Cluster
+// barriers order the passes (release / acquire) and keep every CTA resident
+// until its rows have been read; they are hardware barriers of one cluster,
+// whose CTAs run together.
+__device__ __forceinline__ void cluster_arrive_relaxed() { asm volatile("barrier.cluster.arrive.relaxed.aligned;" ::: "memory"); }
+__device__ __forceinline__ void cluster_arrive() { asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory"); }
+__device__ __forceinline__ void cluster_wait() { asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory"); }
+
+template <typename T, int NV>
+struct RowVec;   // NV values of a section row: 8 or 16 bytes
+template <> struct RowVec<float, 2> {
+    static __device__ __forceinline__ void ld(const float *p, float (&x)[2]) { const float2 v = *reinterpret_cast<const float2 *>(p); x[0] = v.x; x[1] = v.y; }
+    static __device__ __forceinline__ void st(float *p, const float (&x)[2]) { *reinterpret_cast<float2 *>(p) = make_float2(x[0], x[1]); }
+};
+template <> struct RowVec<float, 4> {
+    static __device__ __forceinline__ void ld(const float *p, float (&x)[4]) { const float4 v = *reinterpret_cast<const float4 *>(p); x[0] = v.x; x[1] = v.y; x[2] = v.z; x[3] = v.w; }
+    static __device__ __forceinline__ void st(float *p, const float (&x)[4]) { *reinterpret_cast<float4 *>(p) = make_float4(x[0], x[1], x[2], x[3]); }
+};
+template <> struct RowVec<double, 2> {
+    static __device__ __forceinline__ void ld(const double *p, double (&x)[2]) { const double2 v = *reinterpret_cast<const double2 *>(p); x[0] = v.x; x[1] = v.y; }
+    static __device__ __forceinline__ void st(double *p, const double (&x)[2]) { *reinterpret_cast<double2 *>(p) = make_double2(x[0], x[1]); }
+};
+
+// one 16-byte chunk of complex values (two FP32 or one FP64)
+__device__ __forceinline__ void st_chunk(cpx<float> *p, const cpx<float> (&v)[2])
+{
+    *reinterpret_cast<float4 *>(p) = make_float4(v[0].x, v[0].y, v[1].x, v[1].y);
+}
+__device__ __forceinline__ void st_chunk(cpx<double> *p, const cpx<double> (&v)[1])
+{
+    *reinterpret_cast<double2 *>(p) = make_double2(v[0].x, v[0].y);
+}
+__device__ __forceinline__ void ld_chunk(const cpx<float> *p, cpx<float> (&v)[2])
+{
+    const float4 t = *reinterpret_cast<const float4 *>(p);
+    v[0] = {t.x, t.y};
+    v[1] = {t.z, t.w};
+}
+__device__ __forceinline__ void ld_chunk(const cpx<double> *p, cpx<double> (&v)[1])
+{
+    const double2 t = *reinterpret_cast<const double2 *>(p);
+    v[0] = {t.x, t.y};
+}
+
+// Shared memory of the clustered form: line twiddles, the rows this CTA owns
+// B[mode][row][F2] and the tile of its lines L[mode][line][F1 + pad].
+template <typename T, int F1, int F2, int MPC>
+struct F4C {
+    static constexpr int CV = 16 / (int)sizeof(cpx<T>);          // complex values per 16-byte chunk
+    static constexpr int LT = F1 + (sizeof(T) == 4 ? 2 : 1);    // tile row: conflict-free column access
+    static size_t bytes(int cs)
+    {
+        return ((size_t)F1 + F2 + 16 + (size_t)MPC * (F1 / cs) * F2 + (size_t)MPC * (F2 / cs) * LT) * sizeof(cpx<T>);
+    }
+};
+
+template <typename T, int F1, int F2, int MPC>
+__global__ void __launch_bounds__(F4_THREADS) k_f4c(CurveDev c, int mode, int discrete, int gate)
+{
+    namespace cg = cooperative_groups;
+    using Cfg = F4C<T, F1, F2, MPC>;
+    constexpr int R1 = F1 / 32, R2 = F2 / 32, NV = 2 * MPC, CV = Cfg::CV, LT = Cfg::LT;
+    using RV = RowVec<T, NV>;
+    cg::cluster_group cluster = cg::this_cluster();
+    const int CS = (int)cluster.num_blocks(), rank = (int)cluster.block_rank();
+    const int RPC = F1 / CS, LPC = F2 / CS, CPS = LPC / CV;   // rows, lines, chunks of a row's run
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    cpx<T> *tw1 = (cpx<T> *)smem_raw, *tw2 = tw1 + F1, *w32 = tw2 + F2;
+    cpx<T> *B = w32 + 16, *Lt = B + (size_t)MPC * RPC * F2;
+    __shared__ double wsum[F4W];
+    __shared__ double red[F4_THREADS];
+    __shared__ int am_last;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, jm0 = blockIdx.y * MPC, F = F1 * F2;
+    const cpx<T> *ftw = (const cpx<T> *)c.ftw;
+    load_line_twiddles<T, F2>(tw2, w32, ftw, F);
+    for (int t = threadIdx.x; t < F1; t += F4_THREADS) tw1[t] = ftw[(size_t)((t >> 5) * (t & 31)) * (F / F1)];
+    DevScalars *sc = c.sc;
+    pdl_wait();
+    if (gate && !sc->active) return;   // the whole cluster leaves together
+    cluster_arrive_relaxed();          // every CTA of the cluster has started (before the first copy)
+    const double lam_d = sc->lambda, dtau_d = sc->dtau;
+    const int P = c.P, N = c.nx, ns = c.ns, sym = c.sym;
+    __syncthreads();   // twiddles
+
+    // ---- pass 1: lines n2 of this CTA, MPC modes each, into the tile
+    {
+        const T *X = (const T *)(mode == GM_STORE ? c.U : c.R);
+        const T *colscale = (const T *)(discrete ? c.sw : c.tau);
+        const T s = discrete ? T(-1) : T(1);
+        for (int li = warp; li < LPC; li += F4W) {
+            const int n2 = rank * LPC + li;
+            T x[R1][NV], cs[R1];
+            cpx<T> t1[R1];
+#pragma unroll
+            for (int a = 0; a < R1; ++a) {
+                const int k = F2 * (lane + 32 * a) + n2;
+                int m = -1;
+                T f = T(1);
+                if (k == 0) { m = 0; f = T(1) + s; }
+                else if (k < P) { m = k; f = s; }
+                else if (k == P) { m = P; f = T(1) + s; }
+                else if (k < 2 * P) { m = 2 * P - k; }
+                cs[a] = T(0);
+#pragma unroll
+                for (int q = 0; q < NV; ++q) x[a][q] = T(0);
+                if (m >= 0 && f != T(0)) {
+                    cs[a] = f * colscale[m];
+                    RV::ld(X + (size_t)m * N + 2 * jm0, x[a]);
+                }
+                t1[a] = ftw[F + (size_t)n2 * F1 + 32 * a + lane];
+            }
+#pragma unroll
+            for (int q = 0; q < MPC; ++q) {
+                cpx<T> v[R1];
+#pragma unroll
+                for (int a = 0; a < R1; ++a)
+                    v[a] = {sector_col_ok(jm0, 2 * q, sym) ? cs[a] * x[a][2 * q] : T(0),
+                            sector_col_ok(jm0, 2 * q + 1, sym) ? cs[a] * x[a][2 * q + 1] : T(0)};
+                reg_fft_fwd<T, R1>(v, tw1, w32, lane);
+                cpx<T> *lt = Lt + ((size_t)q * LPC + li) * LT;
+#pragma unroll
+                for (int a = 0; a < R1; ++a) lt[32 * a + lane] = cmul(v[a], t1[a]);
+            }
+        }
+    }
+    __syncthreads();
+    cluster_wait();   // every CTA has started
+    // each row r's run of this CTA's lines -> the row's owner, columns [rank LPC, rank LPC + LPC)
+    for (int e = threadIdx.x; e < MPC * F1 * CPS; e += F4_THREADS) {
+        const int ch = e % CPS, r = (e / CPS) % F1, q = e / (CPS * F1), owner = r / RPC;
+        cpx<T> vals[CV];
+#pragma unroll
+        for (int i = 0; i < CV; ++i) vals[i] = Lt[((size_t)q * LPC + ch * CV + i) * LT + r];
+        cpx<T> *dst = cluster.map_shared_rank(B, owner) + ((size_t)q * RPC + (r - owner * RPC)) * F2 + rank * LPC + ch * CV;
+        st_chunk(dst, vals);
+    }
+    cluster_arrive();
+    cluster_wait();
+
+    // ---- pass 2: this CTA's rows, in place
+    for (int rl = warp; rl < MPC * RPC; rl += F4W) {
+        const int r = rank * RPC + rl % RPC;
+        cpx<T> *row = B + (size_t)rl * F2;
+        const cpx<T> *chp = (const cpx<T> *)c.chat + (size_t)r * F2, *t2 = ftw + 2 * (size_t)F + (size_t)r * F2;
+        cpx<T> v[R2], chv[R2], t2v[R2];
+#pragma unroll
+        for (int a = 0; a < R2; ++a) {
+            v[a] = row[lane + 32 * a];
+            chv[a] = chp[32 * a + lane];
+            t2v[a] = t2[lane + 32 * a];
+        }
+        reg_fft_fwd<T, R2>(v, tw2, w32, lane);
+#pragma unroll
+        for (int a = 0; a < R2; ++a) v[a] = cmul(v[a], chv[a]);
+        reg_fft_inv<T, R2>(v, tw2, w32, lane);
+#pragma unroll
+        for (int a = 0; a < R2; ++a) row[lane + 32 * a] = cmul(v[a], cconj(t2v[a]));
+    }
+    cluster_arrive();
+    cluster_wait();
+
+    // ---- pass 3: this CTA's lines copied back into the tile, IFFT over k1, epilogue
+    for (int e = threadIdx.x; e < MPC * F1 * CPS; e += F4_THREADS) {
+        const int ch = e % CPS, r = (e / CPS) % F1, q = e / (CPS * F1), owner = r / RPC;
+        const cpx<T> *src = cluster.map_shared_rank(B, owner) + ((size_t)q * RPC + (r - owner * RPC)) * F2 + rank * LPC + ch * CV;
+        cpx<T> vals[CV];
+        ld_chunk(src, vals);
+#pragma unroll
+        for (int i = 0; i < CV; ++i) Lt[((size_t)q * LPC + ch * CV + i) * LT + r] = vals[i];
+    }
+    cluster_arrive();   // this CTA's rows may be freed once every CTA has copied its runs
+    __syncthreads();
+
+    // epilogue on the sections j = F2 n1 + n2 < N_s (n1 = lane + 32 a; rows two
+    // at a time, their loads issued first)
+    const T *rowscale = (const T *)(discrete ? c.twr : c.sig);
+    T *Dout = (T *)c.D, *U = (T *)c.U, *G = (T *)c.G;
+    const T *Ah = (const T *)c.A;
+    const T *prec = (const T *)c.prec_imex + jm0;
+    const T lam = (T)lam_d, dtau = (T)dtau_d;
+    double partsum = 0.0;
+    for (int li = warp; li < LPC; li += F4W) {
+        const int n2 = rank * LPC + li;
+        cpx<T> y[MPC][R1];
+#pragma unroll
+        for (int q = 0; q < MPC; ++q) {
+            const cpx<T> *lt = Lt + ((size_t)q * LPC + li) * LT;
+#pragma unroll
+            for (int a = 0; a < R1; ++a) y[q][a] = lt[32 * a + lane];
+            reg_fft_inv<T, R1>(y[q], tw1, w32, lane);
+        }
+#pragma unroll
+        for (int a0 = 0; a0 < R1; a0 += 2) {
+            int jv[2];
+            T rsv[2], av[2][NV], uv[2][NV];
+            double wv[2] = {0.0, 0.0};
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int j = F2 * (lane + 32 * (a0 + h)) + n2;
+                jv[h] = j;
+                rsv[h] = rowscale[j < ns ? j : 0];
+                if (mode != GM_STORE && j > 0 && j < P) {
+                    const size_t o = (size_t)j * N + 2 * jm0;
+                    RV::ld(Ah + o, av[h]);
+                    if (mode == GM_UPDATE) RV::ld(U + o, uv[h]);
+                    wv[h] = c.w[j];
+                }
+            }
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int j = jv[h];
+                if (j >= ns) continue;
+                T yv[NV];
+#pragma unroll
+                for (int q = 0; q < MPC; ++q) {
+                    yv[2 * q] = sector_col_ok(jm0, 2 * q, sym) ? rsv[h] * y[q][a0 + h].x : T(0);
+                    yv[2 * q + 1] = sector_col_ok(jm0, 2 * q + 1, sym) ? rsv[h] * y[q][a0 + h].y : T(0);
+                }
+                const size_t o = (size_t)j * N + 2 * jm0;
+                if (mode == GM_STORE) {
+                    RV::st(Dout + o, yv);
+                    continue;
+                }
+                T g[NV];
+                if (j > 0 && j < P) {
+#pragma unroll
+                    for (int q = 0; q < NV; ++q) {
+                        g[q] = sector_col_ok(jm0, q, sym) ? -(av[h][q] + (discrete ? -lam * yv[q] : lam * yv[q])) : T(0);
+                        const double cw = (jm0 + q / 2 == 0) ? 1.0 : 2.0;
+                        partsum += wv[h] * cw * ((double)g[q] * (double)g[q]);
+                    }
+                    if (mode == GM_UPDATE) {
+#pragma unroll
+                        for (int q = 0; q < NV; ++q) uv[h][q] += dtau * prec[q / 2] * g[q];
+                        RV::st(U + o, uv[h]);
+                    }
+                } else {
+#pragma unroll
+                    for (int q = 0; q < NV; ++q) g[q] = T(0);
+                }
+                if (mode == GM_GRAD) RV::st(G + o, g);
+            }
+        }
+    }
+    cluster_wait();
+    if (mode == GM_STORE) return;
+
+    // ---- FP64 |G|^2: per-CTA partial, last CTA of the grid sums them in a fixed order
+    partsum = warp_sum(partsum);
+    if (lane == 0) wsum[warp] = partsum;
+    __syncthreads();
+    const int bid = blockIdx.y * gridDim.x + blockIdx.x, nb = gridDim.x * gridDim.y;
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < F4W; ++w) t += wsum[w];
+        c.tile[bid] = t;
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned prev = atomicAdd(&sc->cnt_gemm, 1u);
+        am_last = (prev == (unsigned)nb - 1);
+    }
+    __syncthreads();
+    if (!am_last) return;
+    __threadfence();
+    double t = 0.0;
+    for (int b = threadIdx.x; b < nb; b += F4_THREADS) t += __ldcg(c.tile + b);
+    t = block_sum<F4_THREADS>(t, red);
+    if (threadIdx.x == 0) {
+        sc->G2 = c.L * t;
+        if (mode == GM_UPDATE) {
+            sc->step += 1;
+            sc->tau += sc->dtau;
+            sc->lambda = sc->lambda_next;
+        }
+        sc->cnt_gemm = 0;
+    }
+}
+
 // ---- set-up: the twiddles W_F^k (storage type) and the kernel spectrum
 // FFT(c_F)/F in the [k1][k2] order of the passes, by the forward half of the same
 // decomposition in FP64: c_F[t] = cot(pi t / 2P) for 0 <= t <= P, c_F[F - t] =
@@ -592,8 +925,49 @@ static cudaError_t f4_dispatch(const CurveDev &c, int mode, int discrete, int ga
     return cudaErrorInvalidValue;
 }
 
+template <typename T, int F1, int F2, int MPC>
+static cudaError_t f4c_run(const CurveDev &c, int mode, int discrete, int gate, cudaStream_t st)
+{
+    const size_t sm = F4C<T, F1, F2, MPC>::bytes(c.f4c);
+    cudaError_t e = set_smem(k_f4c<T, F1, F2, MPC>, sm);
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(c.f4c, c.nx / 2 / MPC);
+    cfg.blockDim = dim3(F4_THREADS);
+    cfg.dynamicSmemBytes = sm;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[2];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    attr[1].id = cudaLaunchAttributeClusterDimension;
+    attr[1].val.clusterDim.x = c.f4c;
+    attr[1].val.clusterDim.y = 1;
+    attr[1].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 2;
+    e = cudaLaunchKernelEx(&cfg, k_f4c<T, F1, F2, MPC>, c, mode, discrete, gate);
+    if (e != cudaSuccess) return e;
+    return cudaGetLastError();
+}
+
+template <typename T, int MPC>
+static cudaError_t f4c_dispatch(const CurveDev &c, int mode, int discrete, int gate, cudaStream_t st)
+{
+    if (c.F1 == 64 && c.F2 == 64) return f4c_run<T, 64, 64, MPC>(c, mode, discrete, gate, st);
+    if (c.F1 == 128 && c.F2 == 64) return f4c_run<T, 128, 64, MPC>(c, mode, discrete, gate, st);
+    if (c.F1 == 128 && c.F2 == 128) return f4c_run<T, 128, 128, MPC>(c, mode, discrete, gate, st);
+    if (c.F1 == 256 && c.F2 == 128) return f4c_run<T, 256, 128, MPC>(c, mode, discrete, gate, st);
+    if (c.F1 == 256 && c.F2 == 256) return f4c_run<T, 256, 256, MPC>(c, mode, discrete, gate, st);
+    return cudaErrorInvalidValue;
+}
+
 cudaError_t launch_f4(const CurveDev &c, int mode, int discrete, int gate, cudaStream_t st)
 {
+    if (c.f4c) {
+        if (!c.prec) return f4c_dispatch<double, 1>(c, mode, discrete, gate, st);
+        return f4c_mpc(c.prec, c.nx, c.F1, c.F2) == 2 ? f4c_dispatch<float, 2>(c, mode, discrete, gate, st)
+                                          : f4c_dispatch<float, 1>(c, mode, discrete, gate, st);
+    }
     return c.prec ? f4_dispatch<float>(c, mode, discrete, gate, st) : f4_dispatch<double>(c, mode, discrete, gate, st);
 }
 

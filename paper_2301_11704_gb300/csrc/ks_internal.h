@@ -48,6 +48,31 @@ inline int fft_size(int ns, int prec)
 constexpr int F4_FMAX = 65536;
 constexpr int F4_FMIN = 4096;             // 64 x 64
 constexpr int F4_THREADS = 256;           // 8 warps, one line each
+constexpr int F4C_CS = 8;                 // clustered four-step form: CTAs per cluster (portable size)
+constexpr size_t F4C_SMEM_MAX = 224 * 1024;   // its dynamic shared memory per CTA (of 227 KB)
+// F = F1 F2 with F1 = F2 or 2 F2
+inline void f4_split(int F, int &F1, int &F2)
+{
+    int lg = 0;
+    while ((1 << lg) < F) ++lg;
+    F1 = 1 << ((lg + 1) / 2);
+    F2 = F / F1;
+}
+// dynamic shared memory of the clustered form: line twiddles, the CTA's rows
+// [mpc][F1/cs][F2] and its tile [mpc][F2/cs][F1 + pad] (complex values)
+inline size_t f4c_bytes(int prec, int F1, int F2, int mpc, int cs)
+{
+    const size_t cb = prec ? 8 : 16;
+    const size_t lt = (size_t)F1 + (prec ? 2 : 1);
+    return ((size_t)F1 + F2 + 16 + (size_t)mpc * (F1 / cs) * F2 + (size_t)mpc * (F2 / cs) * lt) * cb;
+}
+inline bool f4c_fits(int prec, int F1, int F2) { return f4c_bytes(prec, F1, F2, 1, F4C_CS) <= F4C_SMEM_MAX; }
+// modes per cluster: two FP32 modes (16-byte row segments) once there are enough
+// modes to fill the GPU and their rows fit, else one
+inline int f4c_mpc(int prec, int nx, int F1, int F2)
+{
+    return (prec && nx >= 128 && f4c_bytes(prec, F1, F2, 2, F4C_CS) <= F4C_SMEM_MAX) ? 2 : 1;
+}
 // Four-step length for a curve: above the single-CTA limit, or from F4_FMIN on
 // when asked for (any = 1); 0 outside the range.
 inline int fft4_size(int ns, int prec, int any = 0)
@@ -58,19 +83,32 @@ inline int fft4_size(int ns, int prec, int any = 0)
     return (F >= lo && F <= F4_FMAX) ? F : 0;
 }
 
-// Form of the s-contraction: dense, FFT with one CTA per mode, four-step FFT.
-enum SForm { SF_DENSE = 0, SF_FFT1 = 1, SF_FFT4 = 2 };
+// Form of the s-contraction: dense, FFT with one CTA per mode, four-step FFT in
+// three launches, four-step FFT in one clustered launch.
+enum SForm { SF_DENSE = 0, SF_FFT1 = 1, SF_FFT4 = 2, SF_FFT4C = 3 };
 
-// Form that `auto` picks for a single curve: the fastest measured on GB300 (one
-// step, L2 flushed, N_x in {32, 64, 128, 256}, N_s from 128 to 16384).  The
-// four-step form runs many more CTAs than the one-CTA-per-mode form and wins
-// wherever it applies, except at N_x = 256 where the modes alone fill the GPU.
+// Form that `auto` picks for a single curve: the fastest measured on GB300 (20
+// graph-replayed steps, N_x from 8 to 256, N_s from 256 to 16384).  From
+// N_s = 684 on (F >= 4096) a four-step form wins: in FP32 the clustered one-launch
+// form up to F = 16384 at N_x <= 64 and up to F = 8192 at N_x = 128 (15-30 %
+// ahead: fewer launches and no scratch), the three-launch form elsewhere; in FP64,
+// where the transforms' arithmetic dominates, the clustered form only at
+// F = 4096, N_x <= 16, and the one-CTA form at N_x = 256 while it fits.  Below
+// N_s = 684 the dense form, except the one-CTA FFT form in FP64 at N_x >= 64 or
+// N_s <= 128.
 inline int auto_form(int ns, int nx, int prec)
 {
-    const bool f1 = fft_size(ns, prec) > 0, f4 = fft4_size(ns, prec, 1) > 0;
-    if (nx >= 256 && f1) return SF_FFT1;
-    if (f4 && (ns >= 1366 || (nx >= 128 && ns >= 1024) || !prec || nx >= 256)) return SF_FFT4;
-    if (f1 && (prec ? (long long)ns * nx >= 131072 : (nx >= 64 || ns <= 128))) return SF_FFT1;
+    const bool f1 = fft_size(ns, prec) > 0;
+    const int F = fft4_size(ns, prec, 1);
+    if (F) {
+        int F1 = 0, F2 = 0;
+        f4_split(F, F1, F2);
+        const bool cl = prec ? ((nx <= 64 && F <= 16384) || (nx <= 128 && F <= 8192)) : (nx <= 16 && F <= 4096);
+        if (cl && f4c_fits(prec, F1, F2)) return SF_FFT4C;
+        if (!prec && nx >= 256 && f1) return SF_FFT1;
+        return SF_FFT4;
+    }
+    if (!prec && f1 && (nx >= 64 || ns <= 128)) return SF_FFT1;
     return SF_DENSE;
 }
 
@@ -131,6 +169,7 @@ struct Layout {
     int bn, tiles_r, tiles_c, ksplit, kchunk, row_blocks;
     int tc, tc_bn, tc_tiles_r, tc_tiles_c, tc_ksplit, tc_kchunk;   // tensor-core form (tc = 1)
     int f4, F1, F2;                    // four-step FFT form (f4 = 1): F = F1 F2
+    int f4c;                           // its clustered one-launch variant: cluster size (0: three passes)
 };
 
 struct CurveDev {
@@ -148,6 +187,7 @@ struct CurveDev {
     int bn, tiles_r, tiles_c, ksplit, kchunk, row_blocks;
     int tc, tc_bn, tc_tiles_r, tc_tiles_c, tc_ksplit, tc_kchunk;   // tensor-core form (tc = 1)
     int f4, F1, F2;                    // four-step FFT form (f4 = 1): F = F1 F2
+    int f4c;                           // its clustered one-launch variant: cluster size (0: three passes)
     int F;                 // FFT length of the s-contraction (0: dense form)
     void *chat, *ftw;      // FFT form: kernel spectrum / F and twiddles (complex, storage type);
                            // four-step form: spectrum stored [k1][k2] for k = k1 + F1 k2 (both

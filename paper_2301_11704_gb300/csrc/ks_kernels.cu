@@ -48,14 +48,13 @@ Layout make_layout(int ns, int nx, int prec, int allow_split, int bn, int s_tran
     else if (s_transform == 0) form = auto_form(ns, nx, prec);
     else if (s_transform == 2) form = fft_size(ns, prec) ? SF_FFT1 : (fft4_size(ns, prec) ? SF_FFT4 : SF_DENSE);
     else if (s_transform == 4) form = fft4_size(ns, prec, 1) ? SF_FFT4 : SF_DENSE;
+    else if (s_transform == 5) form = fft4_size(ns, prec, 1) ? SF_FFT4C : SF_DENSE;
     if (form == SF_FFT1) l.F = fft_size(ns, prec);
-    if (form == SF_FFT4) {   // the four-step form
+    if (form == SF_FFT4 || form == SF_FFT4C) {   // the four-step form
         l.F = fft4_size(ns, prec, 1);
         l.f4 = 1;
-        int lg = 0;
-        while ((1 << lg) < l.F) ++lg;
-        l.F1 = 1 << ((lg + 1) / 2);
-        l.F2 = l.F / l.F1;
+        f4_split(l.F, l.F1, l.F2);
+        l.f4c = (form == SF_FFT4C && f4c_fits(prec, l.F1, l.F2)) ? F4C_CS : 0;
     }
     size_t field = al256((size_t)ns * nx * b);
     // tiling and split of the s-contraction
@@ -175,6 +174,7 @@ CurveDev bind_layout(const ks_params *p, const Layout &l, void *base)
     d.f4 = l.f4;
     d.F1 = l.F1;
     d.F2 = l.F2;
+    d.f4c = l.f4c;
     d.cot = b + l.off_cot;
     d.sig = b + l.off_sig;
     d.tau = b + l.off_tau;

@@ -17,7 +17,8 @@ from ._native import KSParams, KSScalars, check, dptr
 _PREC = {"fp64": _native.KS_FP64, "fp32": _native.KS_FP32}
 _ADJ = {"paper": _native.KS_ADJ_PAPER, "discrete": _native.KS_ADJ_DISCRETE}
 _CONV = {"jarc": _native.KS_CONV_JARC, "j": _native.KS_CONV_J, "jrel": _native.KS_CONV_JREL}
-_STR = {"auto": 0, "dense": 1, "fft": 2, "dense_tc": 3, "fft4": 4}
+_STR = {"auto": 0, "dense": 1, "fft": 2, "dense_tc": 3, "fft4": 4, "fft4c": 5}
+_FORM_NAME = {1: "dense", 2: "fft", 3: "dense_tc", 4: "fft4", 5: "fft4c"}
 _LAUNCH = {"auto": 0, "kernels": 0, "persistent": 1}
 
 
@@ -63,6 +64,7 @@ class KSCurve:
         self.workspace_bytes = int(nbytes)
         # length of the FFT that applies D_t along s (0: dense contraction)
         self.fft_length = int(self.lib.ks_curve_fft_length(ctypes.byref(self.params)))
+        self.s_form = _FORM_NAME.get(int(self.lib.ks_curve_s_form(ctypes.byref(self.params))))
         # descent steps run as one persistent kernel (dense form) or as three kernels per step
         self.persistent = self.fft_length == 0 and _LAUNCH[launch] == 1
         self._ws = torch.empty(self.workspace_bytes + 256, dtype=torch.uint8, device=self.device)

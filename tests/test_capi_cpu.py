@@ -58,7 +58,7 @@ def test_workspace_size_scales_with_the_curve(lib):
 
 @pytest.mark.parametrize("bad", [dict(nx=24), dict(nx=4), dict(nx=512), dict(ns=2), dict(L=0.0), dict(S=-1.0),
                                  dict(dtau=0.0), dict(precision=7), dict(adjoint=3), dict(conv=9),
-                                 dict(symmetry=4), dict(s_transform=5), dict(s_transform=4, ns=500), dict(s_transform=3, precision=0), dict(launch=2), dict(L=float("nan"))])
+                                 dict(symmetry=4), dict(s_transform=6), dict(s_transform=4, ns=500), dict(s_transform=5, ns=500), dict(s_transform=5, ns=12000, precision=0), dict(s_transform=3, precision=0), dict(launch=2), dict(L=float("nan"))])
 def test_invalid_parameters_are_rejected_on_the_host(lib, bad):
     p = _params(**bad)
     assert lib.ks_curve_workspace_bytes(ctypes.byref(p)) == 0
@@ -89,20 +89,29 @@ def test_null_handle_is_rejected(lib):
     assert lib.ks_curve_destroy(None) == _native.KS_OK
 
 
-@pytest.mark.parametrize("kw,F", [
-    (dict(precision=1, nx=64, ns=1024), 0),                  # FP32, N_s N_x = 65536: dense
-    (dict(precision=1, nx=128, ns=1024), 4096),              # FP32, N_s N_x = 131072: FFT, F >= 3 (N_s - 1)
-    (dict(precision=1, nx=32, ns=2731), 8192),               # FP32, N_s > 2048
-    (dict(precision=1, nx=256, ns=4096), 16384),             # above one CTA: the four-step form
-    (dict(precision=1, nx=256, ns=16384), 65536),
-    (dict(precision=1, nx=64, ns=30000), 0),                 # above the four-step limit: dense
-    (dict(precision=0, nx=64, ns=1024), 4096),               # FP64, N_x >= 64
-    (dict(precision=0, nx=32, ns=1024), 4096),               # FP64, N_s >= 684: four-step
-    (dict(precision=0, nx=32, ns=600), 0),                   # FP64, N_x = 32, small
-    (dict(precision=0, nx=32, ns=128), 512),                 # FP64, N_s <= 128
-    (dict(precision=1, nx=64, ns=1024, s_transform=2), 4096),
-    (dict(precision=1, nx=128, ns=1024, s_transform=1), 0),
-    (dict(nx=24), -1),
+@pytest.mark.parametrize("kw,F,form", [
+    (dict(precision=1, nx=64, ns=600), 0, 1),                # FP32 below N_s = 684: dense
+    (dict(precision=1, nx=64, ns=1024), 4096, 5),            # FP32 from N_s = 684: clustered four-step
+    (dict(precision=1, nx=64, ns=5462), 16384, 5),           # N_x <= 64 up to F = 16384
+    (dict(precision=1, nx=64, ns=5463), 32768, 4),
+    (dict(precision=1, nx=128, ns=2731), 8192, 5),           # N_x = 128 up to F = 8192
+    (dict(precision=1, nx=128, ns=2732), 16384, 4),
+    (dict(precision=1, nx=256, ns=700), 4096, 4),            # N_x = 256: three-launch four-step
+    (dict(precision=1, nx=256, ns=16384), 65536, 4),
+    (dict(precision=1, nx=64, ns=30000), 0, 3),              # above the four-step limit: tensor-core dense
+    (dict(precision=0, nx=16, ns=1366), 4096, 5),            # FP64 clustered at F = 4096, N_x <= 16
+    (dict(precision=0, nx=32, ns=1024), 4096, 4),            # FP64 N_s >= 684: four-step
+    (dict(precision=0, nx=256, ns=1024), 4096, 2),           # FP64 N_x = 256: one CTA per mode while it fits
+    (dict(precision=0, nx=256, ns=2048), 8192, 4),
+    (dict(precision=0, nx=64, ns=600), 2048, 2),             # FP64 below N_s = 684, N_x >= 64: one-CTA FFT
+    (dict(precision=0, nx=32, ns=600), 0, 1),                # FP64, N_x = 32, small: dense
+    (dict(precision=0, nx=32, ns=128), 512, 2),              # FP64, N_s <= 128
+    (dict(precision=1, nx=64, ns=1024, s_transform=2), 4096, 2),
+    (dict(precision=1, nx=64, ns=1024, s_transform=4), 4096, 4),
+    (dict(precision=1, nx=128, ns=1024, s_transform=1), 0, 1),
+    (dict(precision=1, nx=128, ns=1024, s_transform=3), 0, 3),
+    (dict(nx=24), -1, -1),
 ])
-def test_s_transform_rule(lib, kw, F):
+def test_s_transform_rule(lib, kw, F, form):
     assert lib.ks_curve_fft_length(ctypes.byref(_params(**kw))) == F
+    assert lib.ks_curve_s_form(ctypes.byref(_params(**kw))) == form

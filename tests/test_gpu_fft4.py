@@ -35,13 +35,15 @@ def _curve(N, Ns, L, seed, fp32=False):
     return X.astype(np.float32).astype(np.float64) if fp32 else X
 
 
+@pytest.mark.parametrize("form", ["fft", "fft4c"])
 @pytest.mark.parametrize("adjoint", ["paper", "discrete"])
-def test_four_step_fp64_matches_oracle(adjoint):
-    """N_s = 1500 in FP64: F = 8192 = 128 x 64 (above the single-CTA FP64 limit)."""
+def test_four_step_fp64_matches_oracle(adjoint, form):
+    """N_s = 1500 in FP64: F = 8192 = 128 x 64 (above the single-CTA FP64 limit);
+    the three-launch form and the clustered one-launch form."""
     N, Ns, L = 32, 1500, 22.0
     S = 0.1 * (Ns - 1)
     X = _curve(N, Ns, L, 11)
-    c = KSCurve(L, N, Ns, S, X[0], X[-1], u_init=torch.from_numpy(X), adjoint=adjoint, s_transform="fft")
+    c = KSCurve(L, N, Ns, S, X[0], X[-1], u_init=torch.from_numpy(X), adjoint=adjoint, s_transform=form)
     assert c.fft_length == 8192
     U = oracle.curve_spectral(X)
     spec = gen.CurveSpec(0, 0, L, N, Ns, S)
@@ -55,7 +57,7 @@ def test_four_step_fp64_matches_oracle(adjoint):
     g, _ = c.gradient()
     assert_grad_close(g.cpu().numpy(), G, U, spec, 1e-10)
     c.close()
-    c2 = KSCurve(L, N, Ns, S, X[0], X[-1], u_init=torch.from_numpy(X), adjoint=adjoint, dtau=1e-3, s_transform="fft")
+    c2 = KSCurve(L, N, Ns, S, X[0], X[-1], u_init=torch.from_numpy(X), adjoint=adjoint, dtau=1e-3, s_transform=form)
     out = c2.descend(20)
     Uo, _, sco, _ = oracle.curve_descend(U, L, S, 20, dtau=1e-3, mode=mode)
     assert rel_max(c2.get_state().cpu().numpy(), oracle.curve_physical(Uo)) < 1e-10
@@ -71,6 +73,14 @@ def test_four_step_fp64_matches_oracle(adjoint):
     ("fp64", 64, 5000, 16384, "fft"),
     ("fp32", 64, 1024, 4096, "fft4"),     # 64 x 64, where one CTA would also hold it
     ("fp64", 256, 700, 4096, "fft4"),
+    # the clustered one-launch form: every (F1, F2), one and two FP32 modes per cluster
+    ("fp32", 64, 1024, 4096, "fft4c"),
+    ("fp32", 128, 2000, 8192, "fft4c"),   # 128 x 64, two modes per cluster
+    ("fp32", 256, 3000, 16384, "fft4c"),  # 128 x 128
+    ("fp32", 32, 7001, 32768, "fft4c"),   # 256 x 128, ragged
+    ("fp32", 16, 12345, 65536, "fft4c"),  # 256 x 256, ragged
+    ("fp64", 128, 2500, 8192, "fft4c"),
+    ("fp64", 8, 10923, 32768, "fft4c"),   # the largest FP64 N_s of this form, the smallest N_x
 ])
 def test_four_step_matches_dense(precision, N, Ns, F, form):
     L, S = 22.0 + N / 16.0, 0.1 * (Ns - 1)
@@ -111,8 +121,9 @@ def test_four_step_fp32_matches_oracle():
     c.close()
 
 
+@pytest.mark.parametrize("form", ["fft", "fft4c"])
 @pytest.mark.parametrize("sym", [1, 3])
-def test_four_step_holds_the_symmetric_subspace(sym):
+def test_four_step_holds_the_symmetric_subspace(sym, form):
     """Odd (and L/2-periodic) sections stay so exactly through the descent."""
     N, Ns, L = 32, 3000, 22.0
     x = np.arange(N) * L / N
@@ -121,7 +132,7 @@ def test_four_step_holds_the_symmetric_subspace(sym):
     if sym == 1:
         X += 0.2 * np.outer(np.sin(2 * th), np.sin(2 * np.pi * x / L))
     c = KSCurve(L, N, Ns, 0.1 * (Ns - 1), X[0], X[-1], u_init=torch.from_numpy(X), dtau=1e-3, symmetry=sym,
-                s_transform="fft")
+                s_transform=form)
     assert c.fft_length == 16384
     c.descend(20)
     U = np.fft.rfft(c.get_state().cpu().numpy(), axis=1)
