@@ -596,56 +596,128 @@ __global__ void __launch_bounds__(F4_THREADS) k_f4c(CurveDev c, int mode, int di
     __shared__ double red[F4_THREADS];
     __shared__ int am_last;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, jm0 = blockIdx.y * MPC, F = F1 * F2;
+    const int P = c.P, N = c.nx, ns = c.ns, sym = c.sym;
     const cpx<T> *ftw = (const cpx<T> *)c.ftw;
+    const T *X = (const T *)(mode == GM_STORE ? c.U : c.R);
+    const T *colscale = (const T *)(discrete ? c.sw : c.tau);
+    const T *rowscale = (const T *)(discrete ? c.twr : c.sig);
+    T *Dout = (T *)c.D, *U = (T *)c.U, *G = (T *)c.G;
+    const T *Ah = (const T *)c.A;
+    const T s = discrete ? T(-1) : T(1);
+
+    // Inputs of one item of each pass.  The set-up tables of every warp's first
+    // item are loaded before the programmatic wait, its field values right after
+    // it, so that their latency overlaps the predecessor's tail and the passes.
+    // pass 1, line n2: source rows m (-1: zero), scale, step twiddles; the rows' values
+    auto p1_tables = [&](int n2, int (&m)[R1], T (&cs)[R1], cpx<T> (&t1)[R1]) {
+#pragma unroll
+        for (int a = 0; a < R1; ++a) {
+            const int k = F2 * (lane + 32 * a) + n2;
+            int mm = -1;
+            T f = T(1);
+            if (k == 0) { mm = 0; f = T(1) + s; }
+            else if (k < P) { mm = k; f = s; }
+            else if (k == P) { mm = P; f = T(1) + s; }
+            else if (k < 2 * P) { mm = 2 * P - k; }
+            if (f == T(0)) mm = -1;
+            m[a] = mm;
+            cs[a] = mm >= 0 ? f * colscale[mm] : T(0);
+            t1[a] = ftw[F + (size_t)n2 * F1 + 32 * a + lane];
+        }
+    };
+    auto p1_rows = [&](const int (&m)[R1], T (&x)[R1][NV]) {
+#pragma unroll
+        for (int a = 0; a < R1; ++a) {
+#pragma unroll
+            for (int q = 0; q < NV; ++q) x[a][q] = T(0);
+            if (m[a] >= 0) RV::ld(X + (size_t)m[a] * N + 2 * jm0, x[a]);
+        }
+    };
+    // pass 2, row r: kernel spectrum and step twiddles
+    auto p2_tables = [&](int r, cpx<T> (&chv)[R2], cpx<T> (&t2v)[R2]) {
+        const cpx<T> *chp = (const cpx<T> *)c.chat + (size_t)r * F2, *t2 = ftw + 2 * (size_t)F + (size_t)r * F2;
+#pragma unroll
+        for (int a = 0; a < R2; ++a) {
+            chv[a] = chp[32 * a + lane];
+            t2v[a] = t2[lane + 32 * a];
+        }
+    };
+    // pass 3, line n2, rows a0 and a0 + 1: row scale and quadrature weight; A and u
+    auto p3_tables = [&](int n2, int a0, int (&jv)[2], T (&rsv)[2], double (&wv)[2]) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int j = F2 * (lane + 32 * (a0 + h)) + n2;
+            jv[h] = j;
+            rsv[h] = rowscale[j < ns ? j : 0];
+            wv[h] = (j > 0 && j < P) ? c.w[j] : 0.0;
+        }
+    };
+    auto p3_rows = [&](const int (&jv)[2], T (&av)[2][NV], T (&uv)[2][NV]) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int j = jv[h];
+            if (mode != GM_STORE && j > 0 && j < P) {
+                const size_t o = (size_t)j * N + 2 * jm0;
+                RV::ld(Ah + o, av[h]);
+                if (mode == GM_UPDATE) RV::ld(U + o, uv[h]);
+            }
+        }
+    };
+
     load_line_twiddles<T, F2>(tw2, w32, ftw, F);
     for (int t = threadIdx.x; t < F1; t += F4_THREADS) tw1[t] = ftw[(size_t)((t >> 5) * (t & 31)) * (F / F1)];
+    int m1f[R1];
+    T cs1f[R1];
+    cpx<T> t1f[R1], ch2f[R2], t22f[R2];
+    int j3f[2];
+    T rs3f[2];
+    double w3f[2];
+    if (warp < LPC) {
+        p1_tables(rank * LPC + warp, m1f, cs1f, t1f);
+        p3_tables(rank * LPC + warp, 0, j3f, rs3f, w3f);
+    }
+    if (warp < MPC * RPC) p2_tables(rank * RPC + warp % RPC, ch2f, t22f);
     DevScalars *sc = c.sc;
     pdl_wait();
     if (gate && !sc->active) return;   // the whole cluster leaves together
     cluster_arrive_relaxed();          // every CTA of the cluster has started (before the first copy)
+    T x1f[R1][NV], a3f[2][NV], u3f[2][NV];
+    if (warp < LPC) {
+        p1_rows(m1f, x1f);
+        p3_rows(j3f, a3f, u3f);
+    }
     const double lam_d = sc->lambda, dtau_d = sc->dtau;
-    const int P = c.P, N = c.nx, ns = c.ns, sym = c.sym;
     __syncthreads();   // twiddles
 
     // ---- pass 1: lines n2 of this CTA, MPC modes each, into the tile
-    {
-        const T *X = (const T *)(mode == GM_STORE ? c.U : c.R);
-        const T *colscale = (const T *)(discrete ? c.sw : c.tau);
-        const T s = discrete ? T(-1) : T(1);
-        for (int li = warp; li < LPC; li += F4W) {
-            const int n2 = rank * LPC + li;
-            T x[R1][NV], cs[R1];
-            cpx<T> t1[R1];
+    for (int li = warp; li < LPC; li += F4W) {
+        const int n2 = rank * LPC + li;
+        int m[R1];
+        T x[R1][NV], cs[R1];
+        cpx<T> t1[R1];
+        if (li == warp) {
 #pragma unroll
             for (int a = 0; a < R1; ++a) {
-                const int k = F2 * (lane + 32 * a) + n2;
-                int m = -1;
-                T f = T(1);
-                if (k == 0) { m = 0; f = T(1) + s; }
-                else if (k < P) { m = k; f = s; }
-                else if (k == P) { m = P; f = T(1) + s; }
-                else if (k < 2 * P) { m = 2 * P - k; }
-                cs[a] = T(0);
+                cs[a] = cs1f[a];
+                t1[a] = t1f[a];
 #pragma unroll
-                for (int q = 0; q < NV; ++q) x[a][q] = T(0);
-                if (m >= 0 && f != T(0)) {
-                    cs[a] = f * colscale[m];
-                    RV::ld(X + (size_t)m * N + 2 * jm0, x[a]);
-                }
-                t1[a] = ftw[F + (size_t)n2 * F1 + 32 * a + lane];
+                for (int q = 0; q < NV; ++q) x[a][q] = x1f[a][q];
             }
+        } else {
+            p1_tables(n2, m, cs, t1);
+            p1_rows(m, x);
+        }
 #pragma unroll
-            for (int q = 0; q < MPC; ++q) {
-                cpx<T> v[R1];
+        for (int q = 0; q < MPC; ++q) {
+            cpx<T> v[R1];
 #pragma unroll
-                for (int a = 0; a < R1; ++a)
-                    v[a] = {sector_col_ok(jm0, 2 * q, sym) ? cs[a] * x[a][2 * q] : T(0),
-                            sector_col_ok(jm0, 2 * q + 1, sym) ? cs[a] * x[a][2 * q + 1] : T(0)};
-                reg_fft_fwd<T, R1>(v, tw1, w32, lane);
-                cpx<T> *lt = Lt + ((size_t)q * LPC + li) * LT;
+            for (int a = 0; a < R1; ++a)
+                v[a] = {sector_col_ok(jm0, 2 * q, sym) ? cs[a] * x[a][2 * q] : T(0),
+                        sector_col_ok(jm0, 2 * q + 1, sym) ? cs[a] * x[a][2 * q + 1] : T(0)};
+            reg_fft_fwd<T, R1>(v, tw1, w32, lane);
+            cpx<T> *lt = Lt + ((size_t)q * LPC + li) * LT;
 #pragma unroll
-                for (int a = 0; a < R1; ++a) lt[32 * a + lane] = cmul(v[a], t1[a]);
-            }
+            for (int a = 0; a < R1; ++a) lt[32 * a + lane] = cmul(v[a], t1[a]);
         }
     }
     __syncthreads();
@@ -664,16 +736,19 @@ __global__ void __launch_bounds__(F4_THREADS) k_f4c(CurveDev c, int mode, int di
 
     // ---- pass 2: this CTA's rows, in place
     for (int rl = warp; rl < MPC * RPC; rl += F4W) {
-        const int r = rank * RPC + rl % RPC;
         cpx<T> *row = B + (size_t)rl * F2;
-        const cpx<T> *chp = (const cpx<T> *)c.chat + (size_t)r * F2, *t2 = ftw + 2 * (size_t)F + (size_t)r * F2;
         cpx<T> v[R2], chv[R2], t2v[R2];
+        if (rl == warp) {
 #pragma unroll
-        for (int a = 0; a < R2; ++a) {
-            v[a] = row[lane + 32 * a];
-            chv[a] = chp[32 * a + lane];
-            t2v[a] = t2[lane + 32 * a];
+            for (int a = 0; a < R2; ++a) {
+                chv[a] = ch2f[a];
+                t2v[a] = t22f[a];
+            }
+        } else {
+            p2_tables(rank * RPC + rl % RPC, chv, t2v);
         }
+#pragma unroll
+        for (int a = 0; a < R2; ++a) v[a] = row[lane + 32 * a];
         reg_fft_fwd<T, R2>(v, tw2, w32, lane);
 #pragma unroll
         for (int a = 0; a < R2; ++a) v[a] = cmul(v[a], chv[a]);
@@ -693,14 +768,13 @@ __global__ void __launch_bounds__(F4_THREADS) k_f4c(CurveDev c, int mode, int di
 #pragma unroll
         for (int i = 0; i < CV; ++i) Lt[((size_t)q * LPC + ch * CV + i) * LT + r] = vals[i];
     }
-    cluster_arrive();   // this CTA's rows may be freed once every CTA has copied its runs
+    // this CTA's rows may be freed once every CTA has copied its runs (the copies
+    // have completed: their values are in the tile), so no release is needed
+    cluster_arrive_relaxed();
     __syncthreads();
 
     // epilogue on the sections j = F2 n1 + n2 < N_s (n1 = lane + 32 a; rows two
     // at a time, their loads issued first)
-    const T *rowscale = (const T *)(discrete ? c.twr : c.sig);
-    T *Dout = (T *)c.D, *U = (T *)c.U, *G = (T *)c.G;
-    const T *Ah = (const T *)c.A;
     const T *prec = (const T *)c.prec_imex + jm0;
     const T lam = (T)lam_d, dtau = (T)dtau_d;
     double partsum = 0.0;
@@ -718,19 +792,24 @@ __global__ void __launch_bounds__(F4_THREADS) k_f4c(CurveDev c, int mode, int di
         for (int a0 = 0; a0 < R1; a0 += 2) {
             int jv[2];
             T rsv[2], av[2][NV], uv[2][NV];
-            double wv[2] = {0.0, 0.0};
+            double wv[2];
+            if (li == warp && a0 == 0) {
 #pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const int j = F2 * (lane + 32 * (a0 + h)) + n2;
-                jv[h] = j;
-                rsv[h] = rowscale[j < ns ? j : 0];
-                if (mode != GM_STORE && j > 0 && j < P) {
-                    const size_t o = (size_t)j * N + 2 * jm0;
-                    RV::ld(Ah + o, av[h]);
-                    if (mode == GM_UPDATE) RV::ld(U + o, uv[h]);
-                    wv[h] = c.w[j];
+                for (int h = 0; h < 2; ++h) {
+                    jv[h] = j3f[h];
+                    rsv[h] = rs3f[h];
+                    wv[h] = w3f[h];
+#pragma unroll
+                    for (int q = 0; q < NV; ++q) {
+                        av[h][q] = a3f[h][q];
+                        uv[h][q] = u3f[h][q];
+                    }
                 }
+            } else {
+                p3_tables(n2, a0, jv, rsv, wv);
+                p3_rows(jv, av, uv);
             }
+            if (jv[0] >= ns) break;
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
                 const int j = jv[h];
