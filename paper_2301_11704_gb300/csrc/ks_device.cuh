@@ -34,6 +34,23 @@ __device__ __forceinline__ cpx<T> cmul(cpx<T> a, cpx<T> b)
 // A no-op for a kernel launched without the attribute.
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 
+// Arrival of a CTA at a grid-wide last-CTA reduction, after the CTA has written
+// its partials: a CTA barrier, then one acquire-release atomic add at GPU scope
+// by thread 0 (its release covers the CTA's writes ordered before the barrier,
+// its acquire makes every earlier arrival's partials visible to the last CTA).
+// True in every thread of the CTA that arrives last.
+__device__ __forceinline__ bool last_cta_arrive(unsigned *cnt, unsigned n, int &flag)
+{
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned prev;
+        asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], 1;" : "=r"(prev) : "l"(cnt) : "memory");
+        flag = (prev == n - 1);
+    }
+    __syncthreads();
+    return flag != 0;
+}
+
 // ---------------------------------------------------------------------------
 // Warp-level FFT on shared memory
 // ---------------------------------------------------------------------------
@@ -171,6 +188,20 @@ __device__ __forceinline__ int rows_finish(const CurveDev &c, int mode, int nblk
     __shared__ int go;
     DevScalars *sc = c.sc;
     const int P = c.P, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    // thread 0's scalars and end-row sums, loaded together with the partials
+    double lamd = 0, tol = 0, dtl = 0, u2p = 0, f2p = 0, u2m = 0, f2m = 0;
+    int conv = 0, lfree = 0;
+    if (threadIdx.x == 0) {
+        lamd = sc->lambda;
+        tol = sc->tol;
+        dtl = sc->dtau_lambda;
+        conv = sc->conv;
+        lfree = sc->lambda_free;
+        u2p = __ldcg(c.rowsc + 0);
+        f2p = __ldcg(c.rowsc + 3);
+        u2m = __ldcg(c.rowsc + 4 * (size_t)P + 0);
+        f2m = __ldcg(c.rowsc + 4 * (size_t)P + 3);
+    }
     double t[5] = {0, 0, 0, 0, 0};
     for (int b = threadIdx.x; b < nblk; b += NT)
 #pragma unroll
@@ -186,10 +217,6 @@ __device__ __forceinline__ int rows_finish(const CurveDev &c, int mode, int nblk
         for (int w = 0; w < NT / 32; ++w)
 #pragma unroll
             for (int q = 0; q < 5; ++q) r[q] += wred[w][q];
-        const double lamd = sc->lambda, tol = sc->tol, dtl = sc->dtau_lambda;
-        const int conv = sc->conv, lfree = sc->lambda_free;
-        const double u2p = __ldcg(c.rowsc + 0), f2p = __ldcg(c.rowsc + 3);
-        const double u2m = __ldcg(c.rowsc + 4 * (size_t)P + 0), f2m = __ldcg(c.rowsc + 4 * (size_t)P + 3);
         const double t_j2 = r[0], t_num = r[1], t_den = r[2], t_dl = r[3], t_d2 = r[4];
         const double Jarc = t_den > 0 ? t_num / t_den : 0.0, dJdl = -2.0 * t_dl, Dnorm = sqrt(t_d2);
         int active = 1;
@@ -418,15 +445,7 @@ __device__ __forceinline__ void rows_body(const CurveDev &c, int mode, int blk, 
     if (!tail) return;
 
     // ---- last CTA: the FP64 reduction over the CTAs' partial sums
-    __threadfence();
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        unsigned prev = atomicAdd(&sc->cnt_rows, 1u);
-        am_last = (prev == (unsigned)nblk - 1);
-    }
-    __syncthreads();
-    if (!am_last) return;
-    __threadfence();
+    if (!last_cta_arrive(&sc->cnt_rows, (unsigned)nblk, am_last)) return;
     rows_finish<WARPS * 32>(c, mode, nblk, true);
 }
 

@@ -490,15 +490,7 @@ __global__ void __launch_bounds__(F4_THREADS) k_f4_p3(CurveDev c, int mode, int 
         for (int w = 0; w < F4W; ++w) t += wsum[w];
         c.tile[bid] = t;
     }
-    __threadfence();
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        unsigned prev = atomicAdd(&sc->cnt_gemm, 1u);
-        am_last = (prev == (unsigned)nb - 1);
-    }
-    __syncthreads();
-    if (!am_last) return;
-    __threadfence();
+    if (!last_cta_arrive(&sc->cnt_gemm, (unsigned)nb, am_last)) return;
     double t = 0.0;
     for (int b = threadIdx.x; b < nb; b += F4_THREADS) t += __ldcg(c.tile + b);
     t = block_sum<F4_THREADS>(t, red);
@@ -859,15 +851,7 @@ __global__ void __launch_bounds__(F4_THREADS) k_f4c(CurveDev c, int mode, int di
         for (int w = 0; w < F4W; ++w) t += wsum[w];
         c.tile[bid] = t;
     }
-    __threadfence();
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        unsigned prev = atomicAdd(&sc->cnt_gemm, 1u);
-        am_last = (prev == (unsigned)nb - 1);
-    }
-    __syncthreads();
-    if (!am_last) return;
-    __threadfence();
+    if (!last_cta_arrive(&sc->cnt_gemm, (unsigned)nb, am_last)) return;
     double t = 0.0;
     for (int b = threadIdx.x; b < nb; b += F4_THREADS) t += __ldcg(c.tile + b);
     t = block_sum<F4_THREADS>(t, red);

@@ -572,15 +572,7 @@ __device__ __forceinline__ void dt_body(const CurveDev &c, int mode, int discret
     partsum = block_sum<DT_THREADS>(partsum, red);
     const int bid = (ks * tiles_r + tile_r) * tiles_c + tile_c, nb = ntiles * nsplit;
     if (threadIdx.x == 0) c.tile[bid] = partsum;
-    __threadfence();
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        unsigned prev = atomicAdd(&sc->cnt_gemm, 1u);
-        am_last = (prev == (unsigned)nb - 1);
-    }
-    __syncthreads();
-    if (!am_last) return;
-    __threadfence();
+    if (!last_cta_arrive(&sc->cnt_gemm, (unsigned)nb, am_last)) return;
     double t = 0.0;
     for (int b = threadIdx.x; b < nb; b += DT_THREADS) t += __ldcg(c.tile + b);
     t = block_sum<DT_THREADS>(t, red);
@@ -931,15 +923,7 @@ __device__ __forceinline__ void sconv_body(const CurveDev &c, int mode, int disc
 
     partsum = block_sum<SC_THREADS>(partsum, red);
     if (threadIdx.x == 0) c.tile[jm] = partsum;
-    __threadfence();
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        unsigned prev = atomicAdd(&sc->cnt_gemm, 1u);
-        am_last = (prev == (unsigned)nmodes - 1);
-    }
-    __syncthreads();
-    if (!am_last) return;
-    __threadfence();
+    if (!last_cta_arrive(&sc->cnt_gemm, (unsigned)nmodes, am_last)) return;
     double tt = 0.0;
     for (int b2 = threadIdx.x; b2 < nmodes; b2 += SC_THREADS) tt += __ldcg(c.tile + b2);
     tt = block_sum<SC_THREADS>(tt, red);

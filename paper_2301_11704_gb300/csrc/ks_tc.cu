@@ -385,15 +385,7 @@ __global__ void __launch_bounds__(TC_THREADS) k_dt_tc(CurveDev c, int mode, int 
     partsum = block_sum<TC_THREADS>(partsum, red);
     const int bid = (ks * tiles_r + tile_r) * tiles_c + tile_c, nb = tiles_c * tiles_r * nsplit;
     if (tid == 0) c.tile[bid] = partsum;
-    __threadfence();
-    __syncthreads();
-    if (tid == 0) {
-        unsigned prev = atomicAdd(&sc->cnt_gemm, 1u);
-        am_last = (prev == (unsigned)nb - 1);
-    }
-    __syncthreads();
-    if (!am_last) return;
-    __threadfence();
+    if (!last_cta_arrive(&sc->cnt_gemm, (unsigned)nb, am_last)) return;
     double t = 0.0;
     for (int b = tid; b < nb; b += TC_THREADS) t += __ldcg(c.tile + b);
     t = block_sum<TC_THREADS>(t, red);
