@@ -253,7 +253,9 @@ ks_status ks_curve_set_state(ks_curve *c, const void *u_dev, double lambda, doub
  * ks_curve_profile_read synchronises and returns the accumulated milliseconds
  * and launch counts. */
 typedef struct {
-    double ms[3];            /* three-kernel steps: milliseconds per phase */
+    double ms[3];            /* kernel-per-phase steps: milliseconds per phase (rows, update,
+                                D_t u); the clustered four-step form applies D_t u inside the
+                                update launch and reports no third phase */
     int64_t launches[3];
     double step_ms;          /* persistent step kernel: milliseconds of its launches */
     int64_t step_launches;   /* its launches */

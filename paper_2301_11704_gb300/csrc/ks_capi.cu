@@ -128,9 +128,17 @@ ks_status read_scalars(ks_curve *c, ks::DevScalars *h)
     return KS_OK;
 }
 
+// The clustered four-step form applies the update and D_t u of the updated state
+// in one launch (GM_STEP) at the sizes of f4c_fused; every other form in two.
+static bool fused_step(const ks_curve *c) { return c->d.f4c != 0 && ks::f4c_fused(c->d.prec, c->d.nx, c->d.F); }
+
 ks_status launch_step(ks_curve *c, int discrete, cudaStream_t st)
 {
     KS_CUDA(ks::launch_rows(c->d, ks::ROWS_STEP, st));
+    if (fused_step(c)) {
+        KS_CUDA(ks::launch_dt(c->d, ks::GM_STEP, discrete, 1, st));
+        return KS_OK;
+    }
     KS_CUDA(ks::launch_dt(c->d, ks::GM_UPDATE, discrete, 1, st));
     KS_CUDA(ks::launch_dt(c->d, ks::GM_STORE, 0, 1, st));
     return KS_OK;
@@ -206,10 +214,10 @@ ks_status enqueue_steps(ks_curve *c, int64_t nsteps, double tol)
         KS_CUDA(ks::launch_rows(c->d, ks::ROWS_STEP, c->st));
         if (prof) KS_CUDA(cudaEventRecord(ev[1], c->st));
         if (prof) KS_CUDA(cudaEventRecord(ev[2], c->st));
-        KS_CUDA(ks::launch_dt(c->d, ks::GM_UPDATE, discrete, 1, c->st));
+        KS_CUDA(ks::launch_dt(c->d, fused_step(c) ? ks::GM_STEP : ks::GM_UPDATE, discrete, 1, c->st));
         if (prof) KS_CUDA(cudaEventRecord(ev[3], c->st));
         if (prof) KS_CUDA(cudaEventRecord(ev[4], c->st));
-        KS_CUDA(ks::launch_dt(c->d, ks::GM_STORE, 0, 1, c->st));
+        if (!fused_step(c)) KS_CUDA(ks::launch_dt(c->d, ks::GM_STORE, 0, 1, c->st));
         if (prof) {
             KS_CUDA(cudaEventRecord(ev[5], c->st));
             c->prof_steps[c->prof_used] = 0;
@@ -564,6 +572,7 @@ ks_status ks_curve_profile_read(ks_curve *c, ks_profile *out)
             continue;
         }
         for (int ph = 0; ph < 3; ++ph) {
+            if (ph == 2 && fused_step(c)) continue;   // D_t u ran inside the update launch
             float ms = 0.f;
             KS_CUDA(cudaEventElapsedTime(&ms, c->events[(size_t)6 * st + 2 * ph], c->events[(size_t)6 * st + 2 * ph + 1]));
             out->ms[ph] += ms;

@@ -527,14 +527,17 @@ template <typename T, int NV>
 struct RowVec;   // NV values of a section row: 8 or 16 bytes
 template <> struct RowVec<float, 2> {
     static __device__ __forceinline__ void ld(const float *p, float (&x)[2]) { const float2 v = *reinterpret_cast<const float2 *>(p); x[0] = v.x; x[1] = v.y; }
+    static __device__ __forceinline__ void ldcg(const float *p, float (&x)[2]) { const float2 v = __ldcg(reinterpret_cast<const float2 *>(p)); x[0] = v.x; x[1] = v.y; }
     static __device__ __forceinline__ void st(float *p, const float (&x)[2]) { *reinterpret_cast<float2 *>(p) = make_float2(x[0], x[1]); }
 };
 template <> struct RowVec<float, 4> {
     static __device__ __forceinline__ void ld(const float *p, float (&x)[4]) { const float4 v = *reinterpret_cast<const float4 *>(p); x[0] = v.x; x[1] = v.y; x[2] = v.z; x[3] = v.w; }
+    static __device__ __forceinline__ void ldcg(const float *p, float (&x)[4]) { const float4 v = __ldcg(reinterpret_cast<const float4 *>(p)); x[0] = v.x; x[1] = v.y; x[2] = v.z; x[3] = v.w; }
     static __device__ __forceinline__ void st(float *p, const float (&x)[4]) { *reinterpret_cast<float4 *>(p) = make_float4(x[0], x[1], x[2], x[3]); }
 };
 template <> struct RowVec<double, 2> {
     static __device__ __forceinline__ void ld(const double *p, double (&x)[2]) { const double2 v = *reinterpret_cast<const double2 *>(p); x[0] = v.x; x[1] = v.y; }
+    static __device__ __forceinline__ void ldcg(const double *p, double (&x)[2]) { const double2 v = __ldcg(reinterpret_cast<const double2 *>(p)); x[0] = v.x; x[1] = v.y; }
     static __device__ __forceinline__ void st(double *p, const double (&x)[2]) { *reinterpret_cast<double2 *>(p) = make_double2(x[0], x[1]); }
 };
 
@@ -571,9 +574,12 @@ struct F4C {
     }
 };
 
-template <typename T, int F1, int F2, int MPC>
+template <typename T, int F1, int F2, int MPC, bool STEP>
 __global__ void __launch_bounds__(F4_THREADS) k_f4c(CurveDev c, int mode, int discrete, int gate)
 {
+    // STEP: the fused descent step (mode GM_STEP, two contractions); otherwise one
+    // contraction (GM_STORE / GM_UPDATE / GM_GRAD)
+    constexpr int NCT = STEP ? 2 : 1;
     namespace cg = cooperative_groups;
     using Cfg = F4C<T, F1, F2, MPC>;
     constexpr int R1 = F1 / 32, R2 = F2 / 32, NV = 2 * MPC, CV = Cfg::CV, LT = Cfg::LT;
@@ -590,12 +596,15 @@ __global__ void __launch_bounds__(F4_THREADS) k_f4c(CurveDev c, int mode, int di
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, jm0 = blockIdx.y * MPC, F = F1 * F2;
     const int P = c.P, N = c.nx, ns = c.ns, sym = c.sym;
     const cpx<T> *ftw = (const cpx<T> *)c.ftw;
-    const T *X = (const T *)(mode == GM_STORE ? c.U : c.R);
-    const T *colscale = (const T *)(discrete ? c.sw : c.tau);
-    const T *rowscale = (const T *)(discrete ? c.twr : c.sig);
+    // the contraction being applied: GM_STEP runs the update (adjoint mode
+    // `discrete`), then D_t u of the updated state (cmode, cdisc switch between them)
+    int cmode = STEP ? GM_UPDATE : mode, cdisc = discrete;
+    const T *X = (const T *)(cmode == GM_STORE ? c.U : c.R);
+    const T *colscale = (const T *)(cdisc ? c.sw : c.tau);
+    const T *rowscale = (const T *)(cdisc ? c.twr : c.sig);
     T *Dout = (T *)c.D, *U = (T *)c.U, *G = (T *)c.G;
     const T *Ah = (const T *)c.A;
-    const T s = discrete ? T(-1) : T(1);
+    T s = cdisc ? T(-1) : T(1);
 
     // Inputs of one item of each pass.  The set-up tables of every warp's first
     // item are loaded before the programmatic wait, its field values right after
@@ -622,7 +631,7 @@ __global__ void __launch_bounds__(F4_THREADS) k_f4c(CurveDev c, int mode, int di
         for (int a = 0; a < R1; ++a) {
 #pragma unroll
             for (int q = 0; q < NV; ++q) x[a][q] = T(0);
-            if (m[a] >= 0) RV::ld(X + (size_t)m[a] * N + 2 * jm0, x[a]);
+            if (m[a] >= 0) RV::ldcg(X + (size_t)m[a] * N + 2 * jm0, x[a]);
         }
     };
     // pass 2, row r: kernel spectrum and step twiddles
@@ -648,10 +657,10 @@ __global__ void __launch_bounds__(F4_THREADS) k_f4c(CurveDev c, int mode, int di
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
             const int j = jv[h];
-            if (mode != GM_STORE && j > 0 && j < P) {
+            if (cmode != GM_STORE && j > 0 && j < P) {
                 const size_t o = (size_t)j * N + 2 * jm0;
                 RV::ld(Ah + o, av[h]);
-                if (mode == GM_UPDATE) RV::ld(U + o, uv[h]);
+                if (cmode == GM_UPDATE) RV::ld(U + o, uv[h]);
             }
         }
     };
@@ -679,7 +688,21 @@ __global__ void __launch_bounds__(F4_THREADS) k_f4c(CurveDev c, int mode, int di
         p3_rows(j3f, a3f, u3f);
     }
     const double lam_d = sc->lambda, dtau_d = sc->dtau;
+    const T *prec = (const T *)c.prec_imex + jm0;
+    const T lam = (T)lam_d, dtau = (T)dtau_d;
+    double partsum = 0.0;
     __syncthreads();   // twiddles
+
+    for (int ct = 0; ct < NCT; ++ct) {
+    const bool pf = (ct == 0);   // the prefetched first items belong to the first contraction
+    if (ct == 1) {
+        cmode = GM_STORE;
+        cdisc = 0;
+        X = (const T *)c.U;
+        colscale = (const T *)c.tau;
+        rowscale = (const T *)c.sig;
+        s = T(1);
+    }
 
     // ---- pass 1: lines n2 of this CTA, MPC modes each, into the tile
     for (int li = warp; li < LPC; li += F4W) {
@@ -687,7 +710,7 @@ __global__ void __launch_bounds__(F4_THREADS) k_f4c(CurveDev c, int mode, int di
         int m[R1];
         T x[R1][NV], cs[R1];
         cpx<T> t1[R1];
-        if (li == warp) {
+        if (pf && li == warp) {
 #pragma unroll
             for (int a = 0; a < R1; ++a) {
                 cs[a] = cs1f[a];
@@ -713,7 +736,7 @@ __global__ void __launch_bounds__(F4_THREADS) k_f4c(CurveDev c, int mode, int di
         }
     }
     __syncthreads();
-    cluster_wait();   // every CTA has started
+    if (pf) cluster_wait();   // every CTA has started
     // each row r's run of this CTA's lines -> the row's owner, columns [rank LPC, rank LPC + LPC)
     for (int e = threadIdx.x; e < MPC * F1 * CPS; e += F4_THREADS) {
         const int ch = e % CPS, r = (e / CPS) % F1, q = e / (CPS * F1), owner = r / RPC;
@@ -730,7 +753,7 @@ __global__ void __launch_bounds__(F4_THREADS) k_f4c(CurveDev c, int mode, int di
     for (int rl = warp; rl < MPC * RPC; rl += F4W) {
         cpx<T> *row = B + (size_t)rl * F2;
         cpx<T> v[R2], chv[R2], t2v[R2];
-        if (rl == warp) {
+        if (pf && rl == warp) {
 #pragma unroll
             for (int a = 0; a < R2; ++a) {
                 chv[a] = ch2f[a];
@@ -760,16 +783,17 @@ __global__ void __launch_bounds__(F4_THREADS) k_f4c(CurveDev c, int mode, int di
 #pragma unroll
         for (int i = 0; i < CV; ++i) Lt[((size_t)q * LPC + ch * CV + i) * LT + r] = vals[i];
     }
-    // this CTA's rows may be freed once every CTA has copied its runs (the copies
-    // have completed: their values are in the tile), so no release is needed
-    cluster_arrive_relaxed();
+    // The last contraction: this CTA's rows may be freed once every CTA has
+    // copied its runs (the copies have completed: their values are in the tile),
+    // so no release is needed.  Before a second contraction the barrier comes
+    // after the epilogue instead (release / acquire of the updated state, and the
+    // rows are free to be pushed into again).
+    const bool last = (ct + 1 == NCT);
+    if (last) cluster_arrive_relaxed();
     __syncthreads();
 
     // epilogue on the sections j = F2 n1 + n2 < N_s (n1 = lane + 32 a; rows two
     // at a time, their loads issued first)
-    const T *prec = (const T *)c.prec_imex + jm0;
-    const T lam = (T)lam_d, dtau = (T)dtau_d;
-    double partsum = 0.0;
     for (int li = warp; li < LPC; li += F4W) {
         const int n2 = rank * LPC + li;
         cpx<T> y[MPC][R1];
@@ -785,7 +809,7 @@ __global__ void __launch_bounds__(F4_THREADS) k_f4c(CurveDev c, int mode, int di
             int jv[2];
             T rsv[2], av[2][NV], uv[2][NV];
             double wv[2];
-            if (li == warp && a0 == 0) {
+            if (pf && li == warp && a0 == 0) {
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
                     jv[h] = j3f[h];
@@ -813,7 +837,7 @@ __global__ void __launch_bounds__(F4_THREADS) k_f4c(CurveDev c, int mode, int di
                     yv[2 * q + 1] = sector_col_ok(jm0, 2 * q + 1, sym) ? rsv[h] * y[q][a0 + h].y : T(0);
                 }
                 const size_t o = (size_t)j * N + 2 * jm0;
-                if (mode == GM_STORE) {
+                if (cmode == GM_STORE) {
                     RV::st(Dout + o, yv);
                     continue;
                 }
@@ -821,11 +845,11 @@ __global__ void __launch_bounds__(F4_THREADS) k_f4c(CurveDev c, int mode, int di
                 if (j > 0 && j < P) {
 #pragma unroll
                     for (int q = 0; q < NV; ++q) {
-                        g[q] = sector_col_ok(jm0, q, sym) ? -(av[h][q] + (discrete ? -lam * yv[q] : lam * yv[q])) : T(0);
+                        g[q] = sector_col_ok(jm0, q, sym) ? -(av[h][q] + (cdisc ? -lam * yv[q] : lam * yv[q])) : T(0);
                         const double cw = (jm0 + q / 2 == 0) ? 1.0 : 2.0;
                         partsum += wv[h] * cw * ((double)g[q] * (double)g[q]);
                     }
-                    if (mode == GM_UPDATE) {
+                    if (cmode == GM_UPDATE) {
 #pragma unroll
                         for (int q = 0; q < NV; ++q) uv[h][q] += dtau * prec[q / 2] * g[q];
                         RV::st(U + o, uv[h]);
@@ -834,11 +858,13 @@ __global__ void __launch_bounds__(F4_THREADS) k_f4c(CurveDev c, int mode, int di
 #pragma unroll
                     for (int q = 0; q < NV; ++q) g[q] = T(0);
                 }
-                if (mode == GM_GRAD) RV::st(G + o, g);
+                if (cmode == GM_GRAD) RV::st(G + o, g);
             }
         }
     }
+    if (!last) cluster_arrive();
     cluster_wait();
+    }   // contractions
     if (mode == GM_STORE) return;
 
     // ---- FP64 |G|^2: per-CTA partial, last CTA of the grid sums them in a fixed order
@@ -857,7 +883,7 @@ __global__ void __launch_bounds__(F4_THREADS) k_f4c(CurveDev c, int mode, int di
     t = block_sum<F4_THREADS>(t, red);
     if (threadIdx.x == 0) {
         sc->G2 = c.L * t;
-        if (mode == GM_UPDATE) {
+        if (STEP || mode == GM_UPDATE) {
             sc->step += 1;
             sc->tau += sc->dtau;
             sc->lambda = sc->lambda_next;
@@ -988,11 +1014,11 @@ static cudaError_t f4_dispatch(const CurveDev &c, int mode, int discrete, int ga
     return cudaErrorInvalidValue;
 }
 
-template <typename T, int F1, int F2, int MPC>
+template <typename T, int F1, int F2, int MPC, bool STEP>
 static cudaError_t f4c_run(const CurveDev &c, int mode, int discrete, int gate, cudaStream_t st)
 {
     const size_t sm = F4C<T, F1, F2, MPC>::bytes(c.f4c);
-    cudaError_t e = set_smem(k_f4c<T, F1, F2, MPC>, sm);
+    cudaError_t e = set_smem(k_f4c<T, F1, F2, MPC, STEP>, sm);
     if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(c.f4c, c.nx / 2 / MPC);
@@ -1008,7 +1034,7 @@ static cudaError_t f4c_run(const CurveDev &c, int mode, int discrete, int gate, 
     attr[1].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 2;
-    e = cudaLaunchKernelEx(&cfg, k_f4c<T, F1, F2, MPC>, c, mode, discrete, gate);
+    e = cudaLaunchKernelEx(&cfg, k_f4c<T, F1, F2, MPC, STEP>, c, mode, discrete, gate);
     if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
@@ -1016,16 +1042,26 @@ static cudaError_t f4c_run(const CurveDev &c, int mode, int discrete, int gate, 
 template <typename T, int MPC>
 static cudaError_t f4c_dispatch(const CurveDev &c, int mode, int discrete, int gate, cudaStream_t st)
 {
-    if (c.F1 == 64 && c.F2 == 64) return f4c_run<T, 64, 64, MPC>(c, mode, discrete, gate, st);
-    if (c.F1 == 128 && c.F2 == 64) return f4c_run<T, 128, 64, MPC>(c, mode, discrete, gate, st);
-    if (c.F1 == 128 && c.F2 == 128) return f4c_run<T, 128, 128, MPC>(c, mode, discrete, gate, st);
-    if (c.F1 == 256 && c.F2 == 128) return f4c_run<T, 256, 128, MPC>(c, mode, discrete, gate, st);
-    if (c.F1 == 256 && c.F2 == 256) return f4c_run<T, 256, 256, MPC>(c, mode, discrete, gate, st);
+    if (mode == GM_STEP) {   // the fused step exists for the sizes of f4c_fused
+        if (!f4c_fused(c.prec, c.nx, c.F)) return cudaErrorInvalidValue;
+        if (c.F1 == 64 && c.F2 == 64) return f4c_run<T, 64, 64, MPC, true>(c, mode, discrete, gate, st);
+        if constexpr (sizeof(T) == 4) {
+            if (c.F1 == 128 && c.F2 == 64) return f4c_run<T, 128, 64, MPC, true>(c, mode, discrete, gate, st);
+            if (c.F1 == 128 && c.F2 == 128) return f4c_run<T, 128, 128, MPC, true>(c, mode, discrete, gate, st);
+        }
+        return cudaErrorInvalidValue;
+    }
+    if (c.F1 == 64 && c.F2 == 64) return f4c_run<T, 64, 64, MPC, false>(c, mode, discrete, gate, st);
+    if (c.F1 == 128 && c.F2 == 64) return f4c_run<T, 128, 64, MPC, false>(c, mode, discrete, gate, st);
+    if (c.F1 == 128 && c.F2 == 128) return f4c_run<T, 128, 128, MPC, false>(c, mode, discrete, gate, st);
+    if (c.F1 == 256 && c.F2 == 128) return f4c_run<T, 256, 128, MPC, false>(c, mode, discrete, gate, st);
+    if (c.F1 == 256 && c.F2 == 256) return f4c_run<T, 256, 256, MPC, false>(c, mode, discrete, gate, st);
     return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_f4(const CurveDev &c, int mode, int discrete, int gate, cudaStream_t st)
 {
+    if (mode == GM_STEP && !c.f4c) return cudaErrorInvalidValue;
     if (c.f4c) {
         if (!c.prec) return f4c_dispatch<double, 1>(c, mode, discrete, gate, st);
         return f4c_mpc(c.prec, c.nx, c.F1, c.F2) == 2 ? f4c_dispatch<float, 2>(c, mode, discrete, gate, st)

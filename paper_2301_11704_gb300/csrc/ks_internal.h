@@ -67,6 +67,14 @@ inline size_t f4c_bytes(int prec, int F1, int F2, int mpc, int cs)
     return ((size_t)F1 + F2 + 16 + (size_t)mpc * (F1 / cs) * F2 + (size_t)mpc * (F2 / cs) * lt) * cb;
 }
 inline bool f4c_fits(int prec, int F1, int F2) { return f4c_bytes(prec, F1, F2, 1, F4C_CS) <= F4C_SMEM_MAX; }
+// The sizes where the clustered form is the fastest measured on GB300 (FP32:
+// N_x <= 64 up to F = 16384, N_x = 128 up to F = 8192; FP64: N_x <= 16 at
+// F = 4096).  Descent steps there apply the update and D_t u in one launch; the
+// fused kernel's registers allow one wave of clusters at these sizes only.
+inline bool f4c_fused(int prec, int nx, int F)
+{
+    return prec ? ((nx <= 64 && F <= 16384) || (nx <= 128 && F <= 8192)) : (nx <= 16 && F == 4096);
+}
 // modes per cluster: two FP32 modes (16-byte row segments) once there are enough
 // modes to fill the GPU and their rows fit, else one
 inline int f4c_mpc(int prec, int nx, int F1, int F2)
@@ -103,8 +111,7 @@ inline int auto_form(int ns, int nx, int prec)
     if (F) {
         int F1 = 0, F2 = 0;
         f4_split(F, F1, F2);
-        const bool cl = prec ? ((nx <= 64 && F <= 16384) || (nx <= 128 && F <= 8192)) : (nx <= 16 && F <= 4096);
-        if (cl && f4c_fits(prec, F1, F2)) return SF_FFT4C;
+        if (f4c_fused(prec, nx, F) && f4c_fits(prec, F1, F2)) return SF_FFT4C;
         if (!prec && nx >= 256 && f1) return SF_FFT1;
         return SF_FFT4;
     }
@@ -154,7 +161,9 @@ struct DevScalars {
 //   rows kernel:   skip when done or step >= limit (clears `active`)
 //   gemm kernels:  skip when !active
 enum RowsMode { ROWS_STEP = 0, ROWS_EVAL = 1 };
-enum GemmMode { GM_STORE = 0, GM_UPDATE = 1, GM_GRAD = 2 };
+// GM_STEP (clustered four-step form only): GM_UPDATE, then GM_STORE of the
+// updated state in the same launch.
+enum GemmMode { GM_STORE = 0, GM_UPDATE = 1, GM_GRAD = 2, GM_STEP = 3 };
 
 // Offsets into the caller's workspace.
 struct Layout {

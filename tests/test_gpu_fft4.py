@@ -65,6 +65,27 @@ def test_four_step_fp64_matches_oracle(adjoint, form):
     c2.close()
 
 
+@pytest.mark.parametrize("adjoint", ["paper", "discrete"])
+def test_fused_step_fp64_matches_oracle(adjoint):
+    """N_x = 16, N_s = 1000 in FP64 (F = 4096): the clustered form, whose descent
+    steps apply the update and D_t u of the updated state in one launch."""
+    N, Ns, L = 16, 1000, 22.0
+    S = 0.1 * (Ns - 1)
+    X = _curve(N, Ns, L, 7)
+    U = oracle.curve_spectral(X)
+    mode = oracle.DISCRETE if adjoint == "discrete" else oracle.PAPER
+    c = KSCurve(L, N, Ns, S, X[0], X[-1], u_init=torch.from_numpy(X), adjoint=adjoint, dtau=1e-3, s_transform="auto")
+    assert c.s_form == "fft4c" and c.fft_length == 4096
+    out = c.descend(20)
+    Uo, _, sco, _ = oracle.curve_descend(U, L, S, 20, dtau=1e-3, mode=mode)
+    assert out["steps"] == 20
+    assert rel_max(c.get_state().cpu().numpy(), oracle.curve_physical(Uo)) < 1e-10
+    assert abs(out["J"] - sco["J"]) < 1e-10 * sco["J"]
+    R, D = oracle.curve_residual(Uo, L, S, 1.0)
+    assert rel_max(c.residual().cpu().numpy(), oracle.curve_physical(R)) < 1e-10
+    c.close()
+
+
 @pytest.mark.parametrize("precision,N,Ns,F,form", [
     ("fp32", 64, 3000, 16384, "fft"),     # 128 x 128
     ("fp32", 32, 7001, 32768, "fft"),     # 256 x 128, ragged
