@@ -39,6 +39,11 @@ UNIT = "point-evals/s"
 FP32_LANES_PER_SM = 128
 N_SM = 152
 SM_MAX_MHZ = 2070.0
+# DRAM bytes (read + write) per launch of the dominant kernel, from one
+# `ncu --set full` capture of `bench.py --steps 30 --warmup 3` (caches flushed by
+# ncu between its passes), keyed by (form, F, N_x, precision, fused step); other
+# configurations report null, and an entry is dropped when its kernel changes.
+NCU_TRAFFIC = {("fft4c", 4096, 64, "fp32", True): 960512}
 
 
 def parse():
@@ -348,6 +353,8 @@ def main():
                 "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz" if b == 4 else
                 "nominal FP64 1.25 TFLOP/s"}
     roof["phase_ms_per_launch"] = avg
+    if dom != "rows":
+        roof["traffic"] = NCU_TRAFFIC.get((curve.s_form, F, spec.N, args.precision, fused))
 
     # ---- end to end through the public API with host buffers
     e2e = None
