@@ -323,13 +323,13 @@ def main():
     else:
         flops_dt = 2.0 * spec.Ns * spec.Ns * spec.N
         dt_form = form_name
-    # kernels per step: the step-limit kernel, the row phase, two s-contractions
-    # (three launches each in the three-launch four-step form, both in one launch
-    # in the clustered form)
+    # kernels per timed step (one descend call of one step, whose row phase arms
+    # the step limit): the row phase and two s-contractions (three launches each
+    # in the three-launch four-step form, both in one launch in the clustered form)
     n_x = spec.N
     fused = curve.s_form == "fft4c" and ((n_x <= 64 and F <= 16384) or (n_x <= 128 and F <= 8192) if b == 4
                                          else n_x <= 16 and F == 4096)
-    launches_per_step = 3 if fused else (8 if curve.s_form == "fft4" else 4)
+    launches_per_step = 2 if fused else (7 if curve.s_form == "fft4" else 3)
     if fused:   # the update launch applies both contractions
         flops_dt *= 2
         dt_form += "; update and D_t u in one launch"

@@ -181,8 +181,12 @@ static const int64_t PERSISTENT_STEPS = 1024;
 ks_status enqueue_steps(ks_curve *c, int64_t nsteps, double tol)
 {
     const int discrete = c->p.adjoint == KS_ADJ_DISCRETE;
-    KS_CUDA(ks::launch_set_limit(c->d, (long long)nsteps, tol, c->st));
-    if (c->p.launch == 1 && c->d.part) {
+    const bool persistent = c->p.launch == 1 && c->d.part;
+    const bool graph = !persistent && c->prof_used >= c->prof_cap && nsteps >= GRAPH_STEPS;
+    // the kernel-per-phase loop arms the step limit in its first row phase; the
+    // persistent kernel and the graph replay read it as set by k_set_limit
+    if (persistent || graph || nsteps <= 0) KS_CUDA(ks::launch_set_limit(c->d, (long long)nsteps, tol, c->st));
+    if (persistent) {
         for (int64_t done = 0; done < nsteps; done += PERSISTENT_STEPS) {
             const int64_t n = std::min(PERSISTENT_STEPS, nsteps - done);
             const bool prof = c->prof_used < c->prof_cap;
@@ -197,7 +201,7 @@ ks_status enqueue_steps(ks_curve *c, int64_t nsteps, double tol)
         }
         return KS_OK;
     }
-    if (c->prof_used >= c->prof_cap && nsteps >= GRAPH_STEPS) {
+    if (graph) {
         ks_status s = ensure_graph(c, discrete);
         if (s != KS_OK) return s;
         for (int64_t g = 0; g < nsteps / GRAPH_STEPS; ++g) KS_CUDA(cudaGraphLaunch(c->gexec, c->st));
@@ -211,7 +215,8 @@ ks_status enqueue_steps(ks_curve *c, int64_t nsteps, double tol)
         const bool prof = c->prof_used < c->prof_cap;
         cudaEvent_t *ev = prof ? &c->events[(size_t)6 * c->prof_used] : nullptr;
         if (prof) KS_CUDA(cudaEventRecord(ev[0], c->st));
-        KS_CUDA(ks::launch_rows(c->d, ks::ROWS_STEP, c->st));
+        const ks::StepArm arm = {(long long)nsteps, tol, s == 0 ? 1 : 0};
+        KS_CUDA(ks::launch_rows(c->d, ks::ROWS_STEP, c->st, arm));
         if (prof) KS_CUDA(cudaEventRecord(ev[1], c->st));
         if (prof) KS_CUDA(cudaEventRecord(ev[2], c->st));
         KS_CUDA(ks::launch_dt(c->d, fused_step(c) ? ks::GM_STEP : ks::GM_UPDATE, discrete, 1, c->st));

@@ -182,7 +182,8 @@ __device__ __forceinline__ double block_sum(double v, double *red)
 // writes the curve's scalars when `write`.  Returns to every thread 1 when the
 // descent goes on (always 1 in evaluation mode).
 template <int NT>
-__device__ __forceinline__ int rows_finish(const CurveDev &c, int mode, int nblk, bool write)
+__device__ __forceinline__ int rows_finish(const CurveDev &c, int mode, int nblk, bool write,
+                                           StepArm arm = StepArm{0, 0.0, 0})
 {
     __shared__ double wred[NT / 32][5];
     __shared__ int go;
@@ -193,7 +194,7 @@ __device__ __forceinline__ int rows_finish(const CurveDev &c, int mode, int nblk
     int conv = 0, lfree = 0;
     if (threadIdx.x == 0) {
         lamd = sc->lambda;
-        tol = sc->tol;
+        tol = arm.on ? arm.tol : sc->tol;
         dtl = sc->dtau_lambda;
         conv = sc->conv;
         lfree = sc->lambda_free;
@@ -257,7 +258,8 @@ __device__ __forceinline__ int rows_finish(const CurveDev &c, int mode, int nblk
 }
 
 template <typename T, int N, int WARPS = ROWS_WARPS>
-__device__ __forceinline__ void rows_body(const CurveDev &c, int mode, int blk, int nblk, bool tail)
+__device__ __forceinline__ void rows_body(const CurveDev &c, int mode, int blk, int nblk, bool tail,
+                                          StepArm arm = StepArm{0, 0.0, 0})
 {
     constexpr int H = N / 2;
     constexpr int MPL = (H + 31) / 32;
@@ -291,9 +293,18 @@ __device__ __forceinline__ void rows_body(const CurveDev &c, int mode, int blk, 
     const T wm0 = has0 ? (T)c.w[m0] : T(0), wm1 = has1 ? (T)c.w[m1] : T(0);   // quadrature weights
     for (int t = threadIdx.x + blockDim.x; t < H; t += blockDim.x) tw[t] = ((const cpx<T> *)c.twid)[t];
     pdl_wait();
-    const int g_done = sc->done;
-    const long long g_step = sc->step, g_limit = sc->limit;
+    // an armed call starts from the current step with `done` cleared; block 0
+    // records the limit for the later kernels before its arrival at the
+    // reduction, which orders these writes before the last CTA's
+    const int g_done = arm.on ? 0 : sc->done;
+    const long long g_step = sc->step, g_limit = arm.on ? g_step + arm.nsteps : sc->limit;
     const double lamd0 = sc->lambda;
+    if (arm.on && blk == 0 && threadIdx.x == 0) {
+        sc->limit = g_limit;
+        sc->tol = arm.tol;
+        sc->done = 0;
+        sc->status = 0;
+    }
 #pragma unroll
     for (int i = 0; i < MPL; ++i) {
         const int j = lane + 32 * i;
@@ -446,7 +457,7 @@ __device__ __forceinline__ void rows_body(const CurveDev &c, int mode, int blk, 
 
     // ---- last CTA: the FP64 reduction over the CTAs' partial sums
     if (!last_cta_arrive(&sc->cnt_rows, (unsigned)nblk, am_last)) return;
-    rows_finish<WARPS * 32>(c, mode, nblk, true);
+    rows_finish<WARPS * 32>(c, mode, nblk, true, arm);
 }
 
 // ---------------------------------------------------------------------------

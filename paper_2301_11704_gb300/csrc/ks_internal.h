@@ -240,7 +240,15 @@ cudaError_t launch_row_fwd_x(const CurveDev &c, void *spec, int keep_ends, cudaS
 // spec -> phys; scale_mode 0: plain; 1: Euclidean gradient scaling -2 dx w_m
 // and zero end rows.
 cudaError_t launch_row_inv(const CurveDev &c, const void *spec, void *phys, int scale_mode, cudaStream_t st);
-cudaError_t launch_rows(const CurveDev &c, int mode, cudaStream_t st);
+// Arming of the step limit by the first row phase of a descent call (instead of a
+// separate kernel): limit = step + nsteps, the convergence tolerance, done and
+// status cleared; `on` = 0 reads them from the scalars as set before.
+struct StepArm {
+    long long nsteps;
+    double tol;
+    int on;
+};
+cudaError_t launch_rows(const CurveDev &c, int mode, cudaStream_t st, StepArm arm = StepArm{0, 0.0, 0});
 // Structured contraction along s.  op 0: D_t (columns scaled by tau, rows by
 // sigma), op 1: W^-1 D_t^T W.  mode GM_STORE writes D_t U into D (gated when
 // `gate`), GM_UPDATE applies the descent update to U, GM_GRAD writes G.

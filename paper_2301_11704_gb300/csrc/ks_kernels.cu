@@ -409,9 +409,9 @@ __global__ void __launch_bounds__(ROWS_WARPS * 32) k_row_inv(CurveDev c, const T
 }
 
 template <typename T, int N>
-__global__ void __launch_bounds__(ROWS_WARPS * 32) k_rows(CurveDev c, int mode)
+__global__ void __launch_bounds__(ROWS_WARPS * 32) k_rows(CurveDev c, int mode, StepArm arm)
 {
-    rows_body<T, N>(c, mode, blockIdx.x, gridDim.x, true);
+    rows_body<T, N>(c, mode, blockIdx.x, gridDim.x, true, arm);
 }
 
 // Batched row phase: work item (curve, row block) per CTA; every curve keeps its
@@ -999,14 +999,14 @@ static cudaError_t launch_step_kernel(void (*kern)(KArgs...), dim3 grid, dim3 bl
 }
 
 template <typename T>
-static cudaError_t rows_t(const CurveDev &c, int mode, cudaStream_t st)
+static cudaError_t rows_t(const CurveDev &c, int mode, cudaStream_t st, StepArm arm)
 {
     return dispatch_n(c.nx, [&](auto nn) {
         constexpr int NN = decltype(nn)::value;
         size_t sm = rows_smem<T>(NN, 3);
         cudaError_t e = set_smem(k_rows<T, NN>, sm);
         if (e != cudaSuccess) return e;
-        return launch_step_kernel(k_rows<T, NN>, dim3(row_grid(c.ns)), dim3(ROWS_WARPS * 32), sm, st, 0, c, mode);
+        return launch_step_kernel(k_rows<T, NN>, dim3(row_grid(c.ns)), dim3(ROWS_WARPS * 32), sm, st, 0, c, mode, arm);
     });
 }
 
@@ -1115,9 +1115,9 @@ cudaError_t launch_row_inv(const CurveDev &c, const void *spec, void *phys, int 
     return c.prec ? row_inv_t<float>(c, spec, phys, scale_mode, st) : row_inv_t<double>(c, spec, phys, scale_mode, st);
 }
 
-cudaError_t launch_rows(const CurveDev &c, int mode, cudaStream_t st)
+cudaError_t launch_rows(const CurveDev &c, int mode, cudaStream_t st, StepArm arm)
 {
-    return c.prec ? rows_t<float>(c, mode, st) : rows_t<double>(c, mode, st);
+    return c.prec ? rows_t<float>(c, mode, st, arm) : rows_t<double>(c, mode, st, arm);
 }
 
 template <typename T, int BN>
