@@ -6,8 +6,8 @@ curve points (M = N_s - 2 per curve) x descent steps / time.  One bench step is
 one full descent step of the workload curve: the row phase (f, residual,
 spatial adjoint, FP64 cost reductions), the s-phase with the descent update and
 |G|^2, and the s-phase D_t u of the new state (one kernel each, three each in
-the three-launch four-step form, plus the one-thread kernel that arms the step
-counter).
+the three-launch four-step form; one launch for both s-phases in the clustered
+form, the bench workload's).
 
 Default workload: L = 22, N_x = 64, N_s = 1024 (the differentiation workload),
 FP32 storage and transforms with FP64 reductions.  The curve is far smaller
