@@ -144,6 +144,35 @@ __device__ __forceinline__ T warp_sum(T v)
     return v;
 }
 
+// Sums of five FP64 values over a warp with few FP64 instructions (GB300 issues
+// a warp's FP64 instruction at a small fraction of the FP32 rate, whatever the
+// number of active lanes): the values (padded to eight) are halved at each of the
+// first three butterfly levels, each lane keeping the half its lane bit selects,
+// so every lane adds 4 + 2 + 1 values there and then 1 + 1 (9 additions instead
+// of 25).  Lane l ends with the total of value (l >> 2) & 7 (same in its four
+// lanes).  Fixed order: deterministic.
+__device__ __forceinline__ double warp_sum5(const double (&t)[5], int lane)
+{
+    double v8[8] = {t[0], t[1], t[2], t[3], t[4], 0.0, 0.0, 0.0};
+    double v4[4], v2[2];
+    const bool b4 = (lane & 16) != 0, b3 = (lane & 8) != 0, b2 = (lane & 4) != 0;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const double keep = b4 ? v8[4 + i] : v8[i], give = b4 ? v8[i] : v8[4 + i];
+        v4[i] = keep + __shfl_xor_sync(0xffffffffu, give, 16);
+    }
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        const double keep = b3 ? v4[2 + i] : v4[i], give = b3 ? v4[i] : v4[2 + i];
+        v2[i] = keep + __shfl_xor_sync(0xffffffffu, give, 8);
+    }
+    const double keep = b2 ? v2[1] : v2[0], give = b2 ? v2[0] : v2[1];
+    double v = keep + __shfl_xor_sync(0xffffffffu, give, 4);
+    v += __shfl_xor_sync(0xffffffffu, v, 2);
+    v += __shfl_xor_sync(0xffffffffu, v, 1);
+    return v;
+}
+
 // Fixed-order block reduction (deterministic for a fixed blockDim).
 template <int NT>
 __device__ __forceinline__ double block_sum(double v, double *red)
@@ -207,19 +236,27 @@ __device__ __forceinline__ int rows_finish(const CurveDev &c, int mode, int nblk
     for (int b = threadIdx.x; b < nblk; b += NT)
 #pragma unroll
         for (int q = 0; q < 5; ++q) t[q] += __ldcg(c.bpart + (size_t)b * 5 + q);
-#pragma unroll
-    for (int q = 0; q < 5; ++q) {
-        t[q] = warp_sum(t[q]);
-        if (lane == 0) wred[warp][q] = t[q];
+    {
+        const double ws = warp_sum5(t, lane);
+        const int v = (lane >> 2) & 7;
+        if ((lane & 3) == 0 && v < 5) wred[warp][v] = ws;
     }
     __syncthreads();
+    // the sums over the warps (value q in lane q, the warps in order), then the two
+    // square roots in lanes 1 and 2 while lane 0 divides
+    __shared__ double rtot[5], rroot[3];
+    if (warp == 0) {
+        double r = 0.0;
+        if (lane < 5)
+            for (int w = 0; w < NT / 32; ++w) r += wred[w][lane];
+        const double rj2 = __shfl_sync(0xffffffffu, r, 0), rd2 = __shfl_sync(0xffffffffu, r, 4);
+        if (lane < 5) rtot[lane] = r;
+        if (lane == 1 || lane == 2) rroot[lane] = sqrt(lane == 1 ? rj2 : rd2);
+        __syncwarp();
+    }
     if (threadIdx.x == 0) {
-        double r[5] = {0, 0, 0, 0, 0};
-        for (int w = 0; w < NT / 32; ++w)
-#pragma unroll
-            for (int q = 0; q < 5; ++q) r[q] += wred[w][q];
-        const double t_j2 = r[0], t_num = r[1], t_den = r[2], t_dl = r[3], t_d2 = r[4];
-        const double Jarc = t_den > 0 ? t_num / t_den : 0.0, dJdl = -2.0 * t_dl, Dnorm = sqrt(t_d2);
+        const double t_j2 = rtot[0], t_num = rtot[1], t_den = rtot[2], t_dl = rtot[3];
+        const double Jarc = t_den > 0 ? t_num / t_den : 0.0, dJdl = -2.0 * t_dl, Dnorm = rroot[2];
         int active = 1;
         if (write) {
             sc->J2 = t_j2;
@@ -232,7 +269,7 @@ __device__ __forceinline__ int rows_finish(const CurveDev &c, int mode, int nblk
             sc->f2_minus = f2m;
         }
         if (mode == ROWS_STEP) {
-            const double J = sqrt(t_j2);
+            const double J = rroot[1];
             const double crit = conv == 0 ? Jarc : (conv == 1 ? J : (Dnorm > 0 ? J / Dnorm : J));
             int done = 0, bad = 0;
             if (!isfinite(t_j2) || !isfinite(Jarc)) {
@@ -412,34 +449,45 @@ __device__ __forceinline__ void rows_body(const CurveDev &c, int mode, int blk, 
             s0[q] = warp_sum(s0[q]);
             s1[q] = warp_sum(s1[q]);
         }
-        if (lane == 0) {
-            // per-section norms |q_m|^2 = L sum_j c_j |q^_j|^2 (FP64 from here on)
-            const double L = c.L, lamd = lamd0, al = fabs(lamd);
-            double v[5] = {0, 0, 0, 0, 0};
-            const int ms[2] = {m0, m1};
-            const bool ins[2] = {in0, in1};
-            // per-section terms in the storage type; their sum over sections in FP64
-            const T Lt = (T)L, alt = (T)al, l2 = (T)(lamd * lamd);
-            for (int q = 0; q < 2; ++q) {
-                if (q == 1 && !has1) break;
-                const T *sq = q ? s1 : s0;
-                const T nr = Lt * sq[0], nd = Lt * sq[1], ndr = Lt * sq[2];
-                double *rs = c.rowsc + (size_t)ms[q] * 4;
-                rs[0] = ins[q] ? (double)nr : (double)(Lt * sq[3]);
-                rs[1] = (double)nd;
-                rs[2] = (double)ndr;
-                rs[3] = (double)(Lt * sq[4]);
-                if (ins[q]) {
-                    const T w = q ? wm1 : wm0, sd = sqrt(nd);
-                    v[0] += (double)(w * nr);                 // J^2
-                    v[1] += (double)(w * sqrt(nr) * alt * sd); // J_arc numerator
-                    v[2] += (double)(w * alt * sd);           // J_arc denominator
-                    v[3] += (double)(w * ndr);                // <d, r>_W
-                    v[4] += (double)(w * l2 * nd);            // |l d|_W^2
+        {
+            // Per-section norms |q_m|^2 = L sum_j c_j |q^_j|^2.  The five section
+            // terms are formed in the storage type, one per lane (lanes 5 q + k for
+            // section q, term k), the four FP64 row sums in lanes 16 + 4 q + k; one
+            // FP64 conversion for the warp, the two sections' terms summed in FP64.
+            // (GB300 issues a warp's FP64 instruction at a small fraction of the
+            // FP32 rate whatever the active lanes, so the lanes share the work.)
+            const double lamd = lamd0;
+            const T Lt = (T)c.L, alt = (T)fabs(lamd), l2 = (T)(lamd * lamd);
+            const bool is_term = lane < 10, is_row = lane >= 16 && lane < 24;
+            const int q = is_term ? lane / 5 : (is_row ? (lane - 16) >> 2 : 0);
+            const int k = is_term ? lane % 5 : (lane - 16) & 3;
+            T sv[5];
+#pragma unroll
+            for (int i = 0; i < 5; ++i) sv[i] = q ? s1[i] : s0[i];
+            const bool ins = q ? in1 : in0, has = q ? has1 : true;
+            const T nr = Lt * sv[0], nd = Lt * sv[1], ndr = Lt * sv[2];
+            T val = T(0);
+            if (is_term && ins) {
+                const T w = q ? wm1 : wm0, sd = sqrt(nd);
+                switch (k) {
+                case 0: val = w * nr; break;                    // J^2
+                case 1: val = w * sqrt(nr) * alt * sd; break;   // J_arc numerator
+                case 2: val = w * alt * sd; break;              // J_arc denominator
+                case 3: val = w * ndr; break;                   // <d, r>_W
+                default: val = w * l2 * nd; break;              // |l d|_W^2
+                }
+            } else if (is_row) {
+                switch (k) {
+                case 0: val = ins ? nr : Lt * sv[3]; break;
+                case 1: val = nd; break;
+                case 2: val = ndr; break;
+                default: val = Lt * sv[4]; break;
                 }
             }
-#pragma unroll
-            for (int q = 0; q < 5; ++q) wpart[warp][q] = v[q];
+            const double dv = (double)val;
+            const double d1 = __shfl_down_sync(0xffffffffu, dv, 5);
+            if (lane < 5) wpart[warp][lane] = dv + d1;
+            if (is_row && has) c.rowsc[(size_t)(q ? m1 : m0) * 4 + k] = dv;
         }
     } else if (lane == 0) {
 #pragma unroll
