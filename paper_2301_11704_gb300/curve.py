@@ -39,9 +39,15 @@ class KSCurve:
     Row 0 is s = +inf (u_plus), row ns-1 is s = -inf (u_minus).
     symmetry: 1 holds every section odd, 2 holds it L/2-periodic, 3 both (the
     symmetric subspaces the descent preserves, Sec. V.B).
-    launch: "auto" / "kernels" run descent steps as three kernels per step,
-    "persistent" runs many steps of a dense-form curve in one cooperative kernel
-    (same results; slower on GB300 at the sizes measured).
+    s_transform: how D_t is applied along s (same results to rounding): "auto"
+    (the form measured fastest for the size), "dense", "dense_tc" (FP32, tensor
+    cores), "fft" (one CTA per mode; four-step above its limit), "fft4" (four-step
+    FFT, three launches), "fft4c" (four-step FFT, one clustered launch); the form
+    in use is in `s_form`, the FFT length in `fft_length`.
+    launch: "auto" / "kernels" run descent steps as kernels per phase (row phase
+    and the two contractions; one launch for both contractions in the clustered
+    form), "persistent" runs many steps of a dense-form curve in one cooperative
+    kernel (same results; slower on GB300 at the sizes measured).
     """
 
     def __init__(self, L: float, nx: int, ns: int, S: float, u_plus, u_minus=None, *, s0: float = 0.0,
