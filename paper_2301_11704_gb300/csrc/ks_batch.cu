@@ -130,6 +130,16 @@ ks_status build_items(ks_batch *b)
     return KS_OK;
 }
 
+// The FFT items of one transform length: the one-CTA FFT form, or from F = 4096
+// on its four-step variant (register line transforms).
+static cudaError_t launch_fft_group(const ks_batch *b, const Group &g, int mode, int discrete, cudaStream_t st)
+{
+    const int2 *items = (const int2 *)(b->items_dev + g.off);
+    if (g.key >= ks::F4_FMIN)
+        return ks::launch_f4b_batch(b->prec, g.key, b->cv_dev, items, g.count, mode, discrete, 1, st);
+    return ks::launch_sconv_batch(b->prec, g.key, b->cv_dev, items, g.count, mode, discrete, 1, st);
+}
+
 ks_status launch_step(ks_batch *b, cudaStream_t st)
 {
     cudaError_t e = cudaSuccess;
@@ -142,17 +152,13 @@ ks_status launch_step(ks_batch *b, cudaStream_t st)
             e = ks::launch_dt_batch(b->prec, g.key, b->cv_dev, (const int4 *)(b->items_dev + g.off), g.count,
                                     ks::GM_UPDATE, b->discrete, 1, st);
     for (const Group &g : b->ffts)
-        if (e == cudaSuccess)
-            e = ks::launch_sconv_batch(b->prec, g.key, b->cv_dev, (const int2 *)(b->items_dev + g.off), g.count,
-                                       ks::GM_UPDATE, b->discrete, 1, st);
+        if (e == cudaSuccess) e = launch_fft_group(b, g, ks::GM_UPDATE, b->discrete, st);
     for (const Group &g : b->dts)
         if (e == cudaSuccess)
             e = ks::launch_dt_batch(b->prec, g.key, b->cv_dev, (const int4 *)(b->items_dev + g.off), g.count,
                                     ks::GM_STORE, 0, 1, st);
     for (const Group &g : b->ffts)
-        if (e == cudaSuccess)
-            e = ks::launch_sconv_batch(b->prec, g.key, b->cv_dev, (const int2 *)(b->items_dev + g.off), g.count,
-                                       ks::GM_STORE, 0, 1, st);
+        if (e == cudaSuccess) e = launch_fft_group(b, g, ks::GM_STORE, 0, st);
     if (e != cudaSuccess) return ks::report_error(KS_ECUDA, "batched step launch: %s", cudaGetErrorString(e));
     return KS_OK;
 }

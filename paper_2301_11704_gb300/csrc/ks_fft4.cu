@@ -21,6 +21,8 @@
 //          increment and the FP64 |G|^2 with its last-CTA sum).
 #include <cmath>
 
+#include <type_traits>
+
 #include <cooperative_groups.h>
 
 #include "ks_device.cuh"
@@ -892,6 +894,182 @@ __global__ void __launch_bounds__(F4_THREADS) k_f4c(CurveDev c, int mode, int di
     }
 }
 
+// ---- the one-CTA-per-mode form (batched curves): one CTA holds a mode's whole
+// F1 x F2 array in shared memory, rows r of k1 (scrambled) by columns n2, with a
+// row stride F2 + 1 so that the column accesses of a warp (32 consecutive rows)
+// fall in distinct banks; the three passes of the four-step form with the same
+// register line transforms and tables, separated by CTA barriers; the epilogue
+// and the per-curve last-CTA FP64 |G|^2 of the one-CTA FFT form.
+template <typename T, int F1, int F2>
+struct F4B {
+    static constexpr int BS = F2 + 1;
+    static constexpr size_t BYTES = ((size_t)F1 + F2 + 16 + (size_t)F1 * BS) * sizeof(cpx<T>);
+};
+
+template <typename T, int F1, int F2>
+__device__ __forceinline__ void f4b_body(const CurveDev &c, int mode, int discrete, int gate, int jm, int nmodes)
+{
+    using V2 = typename V2of<T>::type;
+    constexpr int R1 = F1 / 32, R2 = F2 / 32, BS = F4B<T, F1, F2>::BS, F = F1 * F2;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    cpx<T> *tw1 = (cpx<T> *)smem_raw, *tw2 = tw1 + F1, *w32 = tw2 + F2, *B = w32 + 16;
+    __shared__ double red[F4_THREADS];
+    __shared__ int am_last;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const cpx<T> *ftw = (const cpx<T> *)c.ftw, *chat = (const cpx<T> *)c.chat;
+    load_line_twiddles<T, F2>(tw2, w32, ftw, F);
+    for (int t = threadIdx.x; t < F1; t += F4_THREADS) tw1[t] = ftw[(size_t)((t >> 5) * (t & 31)) * (F / F1)];
+    DevScalars *sc = c.sc;
+    pdl_wait();
+    if (gate && !sc->active) return;
+    const double lam_d = sc->lambda, dtau_d = sc->dtau;
+    const int P = c.P, N = c.nx, ns = c.ns;
+    const T *X = (const T *)(mode == GM_STORE ? c.U : c.R);
+    const T *colscale = (const T *)(discrete ? c.sw : c.tau);
+    const T *rowscale = (const T *)(discrete ? c.twr : c.sig);
+    const T s = discrete ? T(-1) : T(1);
+    const int ca = 2 * jm, cb = 2 * jm + 1;
+    const bool oka = col_allowed(ca, c.sym), okb = col_allowed(cb, c.sym) && jm != 0;
+    __syncthreads();   // twiddles
+
+    // pass 1: lines n2, FFT over n1, times W_F^(n2 k1), into column n2 of B
+    for (int n2 = warp; n2 < F2; n2 += F4W) {
+        V2 xv[R1];
+        T cs[R1];
+        cpx<T> t1[R1];
+#pragma unroll
+        for (int a = 0; a < R1; ++a) {
+            const int k = F2 * (lane + 32 * a) + n2;
+            int m = -1;
+            T f = T(1);
+            if (k == 0) { m = 0; f = T(1) + s; }
+            else if (k < P) { m = k; f = s; }
+            else if (k == P) { m = P; f = T(1) + s; }
+            else if (k < 2 * P) { m = 2 * P - k; }
+            if (f == T(0)) m = -1;
+            cs[a] = T(0);
+            xv[a] = V2{T(0), T(0)};
+            if (m >= 0) {
+                cs[a] = f * colscale[m];
+                xv[a] = *reinterpret_cast<const V2 *>(X + (size_t)m * N + ca);
+            }
+            t1[a] = ftw[F + (size_t)n2 * F1 + 32 * a + lane];
+        }
+        cpx<T> v[R1];
+#pragma unroll
+        for (int a = 0; a < R1; ++a) v[a] = {oka ? cs[a] * xv[a].x : T(0), okb ? cs[a] * xv[a].y : T(0)};
+        reg_fft_fwd<T, R1>(v, tw1, w32, lane);
+#pragma unroll
+        for (int a = 0; a < R1; ++a) B[(32 * a + lane) * BS + n2] = cmul(v[a], t1[a]);
+    }
+    __syncthreads();
+
+    // pass 2: rows r: FFT over n2, kernel spectrum, IFFT, times W_F^(-n2 k1), in place
+    for (int r = warp; r < F1; r += F4W) {
+        cpx<T> *row = B + (size_t)r * BS;
+        const cpx<T> *ch = chat + (size_t)r * F2, *t2 = ftw + 2 * (size_t)F + (size_t)r * F2;
+        cpx<T> v[R2], chv[R2], t2v[R2];
+#pragma unroll
+        for (int a = 0; a < R2; ++a) {
+            chv[a] = ch[32 * a + lane];
+            t2v[a] = t2[lane + 32 * a];
+            v[a] = row[lane + 32 * a];
+        }
+        reg_fft_fwd<T, R2>(v, tw2, w32, lane);
+#pragma unroll
+        for (int a = 0; a < R2; ++a) v[a] = cmul(v[a], chv[a]);
+        reg_fft_inv<T, R2>(v, tw2, w32, lane);
+#pragma unroll
+        for (int a = 0; a < R2; ++a) row[lane + 32 * a] = cmul(v[a], cconj(t2v[a]));
+    }
+    __syncthreads();
+
+    // pass 3: lines n2, IFFT over k1, epilogue on the sections j = F2 n1 + n2 < N_s
+    T *Dout = (T *)c.D, *U = (T *)c.U, *G = (T *)c.G;
+    const T *Ah = (const T *)c.A;
+    const T pr = ((const T *)c.prec_imex)[jm];
+    const T lam = (T)lam_d, dtau = (T)dtau_d;
+    const double cw = (jm == 0) ? 1.0 : 2.0;
+    double partsum = 0.0;
+    for (int n2 = warp; n2 < F2; n2 += F4W) {
+        cpx<T> v[R1];
+#pragma unroll
+        for (int a = 0; a < R1; ++a) v[a] = B[(32 * a + lane) * BS + n2];
+        // the epilogue operands of this line's sections, issued before the transform
+        T rs[R1];
+        double wj[R1];
+        V2 av[R1], uv[R1];
+#pragma unroll
+        for (int a = 0; a < R1; ++a) {
+            const int j = F2 * (lane + 32 * a) + n2;
+            rs[a] = rowscale[j < ns ? j : 0];
+            wj[a] = 0.0;
+            if (mode != GM_STORE && j > 0 && j < P) {
+                wj[a] = c.w[j];
+                av[a] = *reinterpret_cast<const V2 *>(Ah + (size_t)j * N + ca);
+                if (mode == GM_UPDATE) uv[a] = *reinterpret_cast<const V2 *>(U + (size_t)j * N + ca);
+            }
+        }
+        reg_fft_inv<T, R1>(v, tw1, w32, lane);
+#pragma unroll
+        for (int a = 0; a < R1; ++a) {
+            const int j = F2 * (lane + 32 * a) + n2;
+            if (j >= ns) break;
+            const cpx<T> yv = {rs[a] * v[a].x, rs[a] * v[a].y};
+            const size_t o = (size_t)j * N + ca;
+            if (mode == GM_STORE) {
+                *reinterpret_cast<V2 *>(Dout + o) = V2{oka ? yv.x : T(0), okb ? yv.y : T(0)};
+                continue;
+            }
+            const bool interior = (j > 0 && j < P);
+            T ga = 0, gb = 0;
+            if (interior) {
+                if (oka) ga = -(av[a].x + (discrete ? -lam * yv.x : lam * yv.x));
+                if (okb) gb = -(av[a].y + (discrete ? -lam * yv.y : lam * yv.y));
+                partsum += wj[a] * cw * ((double)ga * (double)ga + (double)gb * (double)gb);
+            }
+            if (mode == GM_UPDATE) {
+                if (interior) *reinterpret_cast<V2 *>(U + o) = V2{uv[a].x + dtau * pr * ga, uv[a].y + dtau * pr * gb};
+            } else {
+                *reinterpret_cast<V2 *>(G + o) = V2{ga, gb};
+            }
+        }
+    }
+    if (mode == GM_STORE) return;
+
+    // ---- FP64 |G|^2 of the curve: per-mode partial, the curve's last CTA sums them
+    partsum = block_sum<F4_THREADS>(partsum, red);
+    if (threadIdx.x == 0) c.tile[jm] = partsum;
+    if (!last_cta_arrive(&sc->cnt_gemm, (unsigned)nmodes, am_last)) return;
+    double tt = 0.0;
+    for (int b2 = threadIdx.x; b2 < nmodes; b2 += F4_THREADS) tt += __ldcg(c.tile + b2);
+    tt = block_sum<F4_THREADS>(tt, red);
+    if (threadIdx.x == 0) {
+        sc->G2 = c.L * tt;
+        if (mode == GM_UPDATE) {
+            sc->step += 1;
+            sc->tau += sc->dtau;
+            sc->lambda = sc->lambda_next;
+        }
+        sc->cnt_gemm = 0;
+    }
+}
+
+template <typename T, int F1, int F2>
+__global__ void __launch_bounds__(F4_THREADS) k_f4b(CurveDev c, int mode, int discrete, int gate)
+{
+    f4b_body<T, F1, F2>(c, mode, discrete, gate, blockIdx.x, gridDim.x);
+}
+
+template <typename T, int F1, int F2>
+__global__ void __launch_bounds__(F4_THREADS) k_f4b_batch(const CurveDev *cv, const int2 *items, int mode,
+                                                          int discrete, int gate)
+{
+    const int2 it = items[blockIdx.x];
+    const CurveDev &c = cv[it.x];
+    f4b_body<T, F1, F2>(c, mode, discrete, gate, it.y, c.nx / 2);
+}
+
 // ---- set-up: the twiddles W_F^k (storage type) and the kernel spectrum
 // FFT(c_F)/F in the [k1][k2] order of the passes, by the forward half of the same
 // decomposition in FP64: c_F[t] = cot(pi t / 2P) for 0 <= t <= P, c_F[F - t] =
@@ -1068,6 +1246,55 @@ cudaError_t launch_f4(const CurveDev &c, int mode, int discrete, int gate, cudaS
                                           : f4c_dispatch<float, 1>(c, mode, discrete, gate, st);
     }
     return c.prec ? f4_dispatch<float>(c, mode, discrete, gate, st) : f4_dispatch<double>(c, mode, discrete, gate, st);
+}
+
+// The one-CTA-per-mode form exists for the lengths a batched curve can have
+// (the one-CTA FFT form's range from F = 4096: 4096 and 8192 in FP32, 4096 in FP64).
+template <typename T, typename Fn>
+static cudaError_t f4b_dispatch(int F, Fn &&fn)
+{
+    if (F == 4096) return fn(std::integral_constant<int, 64>(), std::integral_constant<int, 64>());
+    if constexpr (sizeof(T) == 4)
+        if (F == 8192) return fn(std::integral_constant<int, 128>(), std::integral_constant<int, 64>());
+    return cudaErrorInvalidValue;
+}
+
+template <typename T>
+static cudaError_t f4b_run(const CurveDev &c, int mode, int discrete, int gate, cudaStream_t st)
+{
+    return f4b_dispatch<T>(c.F, [&](auto f1, auto f2) {
+        constexpr int F1 = decltype(f1)::value, F2 = decltype(f2)::value;
+        const size_t sm = F4B<T, F1, F2>::BYTES;
+        cudaError_t e = set_smem(k_f4b<T, F1, F2>, sm);
+        if (e != cudaSuccess) return e;
+        return launch_pdl(k_f4b<T, F1, F2>, dim3(c.nx / 2), sm, st, c, mode, discrete, gate);
+    });
+}
+
+cudaError_t launch_f4b(const CurveDev &c, int mode, int discrete, int gate, cudaStream_t st)
+{
+    return c.prec ? f4b_run<float>(c, mode, discrete, gate, st) : f4b_run<double>(c, mode, discrete, gate, st);
+}
+
+template <typename T>
+static cudaError_t f4b_batch_run(int F, const CurveDev *cv, const int2 *items, int nitems, int mode, int discrete,
+                                 int gate, cudaStream_t st)
+{
+    return f4b_dispatch<T>(F, [&](auto f1, auto f2) {
+        constexpr int F1 = decltype(f1)::value, F2 = decltype(f2)::value;
+        const size_t sm = F4B<T, F1, F2>::BYTES;
+        cudaError_t e = set_smem(k_f4b_batch<T, F1, F2>, sm);
+        if (e != cudaSuccess) return e;
+        return launch_pdl(k_f4b_batch<T, F1, F2>, dim3(nitems), sm, st, cv, items, mode, discrete, gate);
+    });
+}
+
+cudaError_t launch_f4b_batch(int prec, int F, const CurveDev *cv, const int2 *items, int nitems, int mode,
+                             int discrete, int gate, cudaStream_t st)
+{
+    if (nitems <= 0) return cudaSuccess;
+    return prec ? f4b_batch_run<float>(F, cv, items, nitems, mode, discrete, gate, st)
+                : f4b_batch_run<double>(F, cv, items, nitems, mode, discrete, gate, st);
 }
 
 template <typename T, int F1, int F2>

@@ -179,6 +179,7 @@ struct Layout {
     int tc, tc_bn, tc_tiles_r, tc_tiles_c, tc_ksplit, tc_kchunk;   // tensor-core form (tc = 1)
     int f4, F1, F2;                    // four-step FFT form (f4 = 1): F = F1 F2
     int f4c;                           // its clustered one-launch variant: cluster size (0: three passes)
+    int f4b;                           // its one-CTA-per-mode variant (batched curves; F1 F2 in shared memory)
 };
 
 struct CurveDev {
@@ -197,6 +198,7 @@ struct CurveDev {
     int tc, tc_bn, tc_tiles_r, tc_tiles_c, tc_ksplit, tc_kchunk;   // tensor-core form (tc = 1)
     int f4, F1, F2;                    // four-step FFT form (f4 = 1): F = F1 F2
     int f4c;                           // its clustered one-launch variant: cluster size (0: three passes)
+    int f4b;                           // its one-CTA-per-mode variant (batched curves; F1 F2 in shared memory)
     int F;                 // FFT length of the s-contraction (0: dense form)
     void *chat, *ftw;      // FFT form: kernel spectrum / F and twiddles (complex, storage type);
                            // four-step form: spectrum stored [k1][k2] for k = k1 + F1 k2 (both
@@ -261,6 +263,11 @@ cudaError_t launch_dt_tc(const CurveDev &c, int mode, int discrete, int gate, cu
 // the s-contraction in the modes of launch_dt.
 cudaError_t launch_setup_f4(const CurveDev &c, cudaStream_t st);
 cudaError_t launch_f4(const CurveDev &c, int mode, int discrete, int gate, cudaStream_t st);
+// The one-CTA-per-mode four-step form: over the modes of one curve, or over the
+// (curve, mode) items of a batch whose curves share F.
+cudaError_t launch_f4b(const CurveDev &c, int mode, int discrete, int gate, cudaStream_t st);
+cudaError_t launch_f4b_batch(int prec, int F, const CurveDev *cv, const int2 *items, int nitems, int mode,
+                             int discrete, int gate, cudaStream_t st);
 
 // Persistent step (ks_step.cu): nsteps descent steps of a dense-form curve
 // (c.part set) in one cooperative launch; stops early with the curve's gates.

@@ -44,7 +44,16 @@ Layout make_layout(int ns, int nx, int prec, int allow_split, int bn, int s_tran
     // s_transform 0 (auto): a single curve (allow_split) takes the measured rule,
     // batched curves the one-CTA FFT form wherever it fits
     int form = SF_DENSE;
-    if (!allow_split) form = (s_transform == 0 || s_transform == 2) && fft_size(ns, prec) ? SF_FFT1 : SF_DENSE;
+    // batched curves: the FFT form with one CTA per mode wherever it fits, its
+    // four-step variant (register line transforms) from F = 4096 on
+    bool batched_f4 = false;
+    if (!allow_split) {
+        form = (s_transform == 0 || s_transform == 2) && fft_size(ns, prec) ? SF_FFT1 : SF_DENSE;
+        if (form == SF_FFT1 && fft_size(ns, prec) >= F4_FMIN) {
+            form = SF_FFT4;
+            batched_f4 = true;
+        }
+    }
     else if (s_transform == 0) form = auto_form(ns, nx, prec);
     else if (s_transform == 2) form = fft_size(ns, prec) ? SF_FFT1 : (fft4_size(ns, prec) ? SF_FFT4 : SF_DENSE);
     else if (s_transform == 4) form = fft4_size(ns, prec, 1) ? SF_FFT4 : SF_DENSE;
@@ -55,6 +64,7 @@ Layout make_layout(int ns, int nx, int prec, int allow_split, int bn, int s_tran
         l.f4 = 1;
         f4_split(l.F, l.F1, l.F2);
         l.f4c = (form == SF_FFT4C && f4c_fits(prec, l.F1, l.F2)) ? F4C_CS : 0;
+        l.f4b = batched_f4 ? 1 : 0;
     }
     size_t field = al256((size_t)ns * nx * b);
     // tiling and split of the s-contraction
@@ -126,7 +136,9 @@ Layout make_layout(int ns, int nx, int prec, int allow_split, int bn, int s_tran
     l.off_sc = off; off += al256(sizeof(DevScalars));
     l.off_chat = off; off += l.F ? al256((size_t)l.F * 2 * b) : 0;
     l.off_ftw = off; off += l.F ? al256((size_t)l.F * (l.f4 ? 3 : 1) * 2 * b) : 0;   // four-step: + step twiddles
-    l.off_f4s = off; off += l.f4 ? al256((size_t)(nx / 2) * l.F * 2 * b) : 0;
+    // the three-launch form's scratch (also the FP64 set-up scratch, 32 F bytes);
+    // the one-CTA-per-mode variant needs the set-up's only
+    l.off_f4s = off; off += l.f4 ? al256(l.f4b ? (size_t)32 * l.F : (size_t)(nx / 2) * l.F * 2 * b) : 0;
     l.total = off;
     return l;
 }
@@ -175,6 +187,7 @@ CurveDev bind_layout(const ks_params *p, const Layout &l, void *base)
     d.F1 = l.F1;
     d.F2 = l.F2;
     d.f4c = l.f4c;
+    d.f4b = l.f4b;
     d.cot = b + l.off_cot;
     d.sig = b + l.off_sig;
     d.tau = b + l.off_tau;
@@ -1156,6 +1169,7 @@ cudaError_t launch_sconv_batch(int prec, int F_max, const CurveDev *cv, const in
 
 cudaError_t launch_dt(const CurveDev &c, int mode, int discrete, int gate, cudaStream_t st)
 {
+    if (c.f4b) return launch_f4b(c, mode, discrete, gate, st);
     if (c.f4) return launch_f4(c, mode, discrete, gate, st);
     if (c.F > 0) return c.prec ? launch_sconv_t<float>(c, mode, discrete, gate, st)
                                : launch_sconv_t<double>(c, mode, discrete, gate, st);

@@ -105,3 +105,55 @@ def test_batch_workload_256_curves_fp32():
     assert np.all(np.isfinite(out["J"])) and np.all(out["steps"] == 64)
     assert np.median(out["J"] / j0) < 1.0
     b.close()
+
+
+def _four_step_specs(sizes):
+    """Curves of the batch recipe with the given N (their stored end points) and N_s."""
+    base = gen.workload(3)
+    out, used = [], set()
+    for N, Ns in sizes:
+        i = next(i for i, s in enumerate(base) if s.N == N and i not in used)
+        used.add(i)
+        out.append(gen.CurveSpec(3, i, base[i].L, N, Ns, gen.mapping_scale(Ns), dtau=0.002, steps=0))
+    return out
+
+
+def test_batch_four_step_items_match_independent_curves_fp32():
+    """Curves whose transform length reaches 4096 or 8192 run the batch's
+    one-CTA-per-mode four-step form; each tracks its own single-curve run."""
+    specs = _four_step_specs([(32, 700), (64, 1500), (128, 2100), (32, 1200)])
+    ins = [_inputs(s) for s in specs]
+    b = KSBatch(specs, [i[0] for i in ins], [i[1] for i in ins], precision="fp32", conv="jarc")
+    b.init_trial(np.array([i[2] for i in ins]), [i[3] for i in ins])
+    out = b.descend(20)
+    assert np.all(out["steps"] == 20)
+    for k, s in enumerate(specs):
+        up, um, amps, vp = ins[k]
+        c = KSCurve(s.L, s.N, s.Ns, s.S, up, um, dtau=s.dtau, precision="fp32")
+        assert c.fft_length in (4096, 8192)
+        c.init_trial(0.0, None, amps, vp)
+        ref = c.descend(20)
+        xb = b.get_state(k).double().cpu().numpy()
+        xc = c.get_state().double().cpu().numpy()
+        assert np.abs(xb - xc).max() <= 2e-5 * np.abs(xc).max(), (k, s)
+        assert abs(out["J"][k] - ref["J"]) <= 2e-5 * ref["J"]
+        c.close()
+    b.close()
+
+
+def test_batch_four_step_items_match_the_oracle_fp64():
+    """FP64 batch curves with F = 4096 (the one-CTA-per-mode four-step form) against
+    the oracle's descent."""
+    specs = _four_step_specs([(32, 700), (64, 1200)])
+    ins = [_inputs(s) for s in specs]
+    b = KSBatch(specs, [i[0] for i in ins], [i[1] for i in ins], precision="fp64", conv="jarc")
+    b.init_trial(np.array([i[2] for i in ins]), [i[3] for i in ins])
+    out = b.descend(10)
+    for k, s in enumerate(specs):
+        up, um, amps, vp = ins[k]
+        U = oracle.curve_init(s.M, s.S, up, um, amps=amps, vp=vp)
+        Uo, _, sco, _ = oracle.curve_descend(U, s.L, s.S, 10, dtau=s.dtau)
+        xo = oracle.curve_physical(Uo)
+        assert np.abs(b.get_state(k).cpu().numpy() - xo).max() <= 1e-10 * np.abs(xo).max()
+        assert abs(out["J_arc"][k] - sco["J_arc"]) <= 1e-10 * sco["J_arc"]
+    b.close()
