@@ -130,12 +130,12 @@ ks_status build_items(ks_batch *b)
     return KS_OK;
 }
 
-// The FFT items of one transform length: the one-CTA FFT form, or from F = 4096
+// The FFT items of one transform length: the one-CTA FFT form, or from F = 1024
 // on its four-step variant (register line transforms).
 static cudaError_t launch_fft_group(const ks_batch *b, const Group &g, int mode, int discrete, cudaStream_t st)
 {
     const int2 *items = (const int2 *)(b->items_dev + g.off);
-    if (g.key >= ks::F4_FMIN)
+    if (g.key >= ks::F4B_FMIN)
         return ks::launch_f4b_batch(b->prec, g.key, b->cv_dev, items, g.count, mode, discrete, 1, st);
     return ks::launch_sconv_batch(b->prec, g.key, b->cv_dev, items, g.count, mode, discrete, 1, st);
 }

@@ -152,14 +152,14 @@ __device__ __forceinline__ void lane_swap(cpx<T> &v0, cpx<T> &v1, bool up, int m
 template <typename T, int R>
 __device__ __forceinline__ void reg_fft_fwd(cpx<T> (&v)[R], const cpx<T> *twl, const cpx<T> *w32, int lane)
 {
-    static_assert(R % 2 == 0, "register pairs");
+    static_assert(R == 1 || R % 2 == 0, "one value per lane or register pairs");
     reg_dft<T, R>(v, false);
 #pragma unroll
     for (int a = 1; a < R; ++a) v[a] = cmul(v[a], twl[a * 32 + lane]);
 #pragma unroll
     for (int m = 16; m >= 1; m >>= 1) {
         const bool up = (lane & m) != 0;
-        if constexpr (sizeof(T) == 8) {
+        if constexpr (sizeof(T) == 8 && R % 2 == 0) {
             const cpx<T> w = w32[(lane & (m - 1)) * (16 / m)];   // W_2m^(position within the half)
 #pragma unroll
             for (int a = 0; a < R; a += 2) {
@@ -184,11 +184,11 @@ __device__ __forceinline__ void reg_fft_fwd(cpx<T> (&v)[R], const cpx<T> *twl, c
 template <typename T, int R>
 __device__ __forceinline__ void reg_fft_inv(cpx<T> (&v)[R], const cpx<T> *twl, const cpx<T> *w32, int lane)
 {
-    static_assert(R % 2 == 0, "register pairs");
+    static_assert(R == 1 || R % 2 == 0, "one value per lane or register pairs");
 #pragma unroll
     for (int m = 1; m <= 16; m <<= 1) {
         const bool up = (lane & m) != 0;
-        if constexpr (sizeof(T) == 8) {
+        if constexpr (sizeof(T) == 8 && R % 2 == 0) {
             const cpx<T> w = cconj(w32[(lane & (m - 1)) * (16 / m)]);
 #pragma unroll
             for (int a = 0; a < R; a += 2) {
@@ -1249,10 +1249,12 @@ cudaError_t launch_f4(const CurveDev &c, int mode, int discrete, int gate, cudaS
 }
 
 // The one-CTA-per-mode form exists for the lengths a batched curve can have
-// (the one-CTA FFT form's range from F = 4096: 4096 and 8192 in FP32, 4096 in FP64).
+// (the one-CTA FFT form's range from F = 1024: up to 8192 in FP32, 4096 in FP64).
 template <typename T, typename Fn>
 static cudaError_t f4b_dispatch(int F, Fn &&fn)
 {
+    if (F == 1024) return fn(std::integral_constant<int, 32>(), std::integral_constant<int, 32>());
+    if (F == 2048) return fn(std::integral_constant<int, 64>(), std::integral_constant<int, 32>());
     if (F == 4096) return fn(std::integral_constant<int, 64>(), std::integral_constant<int, 64>());
     if constexpr (sizeof(T) == 4)
         if (F == 8192) return fn(std::integral_constant<int, 128>(), std::integral_constant<int, 64>());
@@ -1314,6 +1316,8 @@ static cudaError_t setup_run(const CurveDev &c, cudaStream_t st)
 template <typename T>
 static cudaError_t setup_dispatch(const CurveDev &c, cudaStream_t st)
 {
+    if (c.F1 == 32 && c.F2 == 32) return setup_run<T, 32, 32>(c, st);
+    if (c.F1 == 64 && c.F2 == 32) return setup_run<T, 64, 32>(c, st);
     if (c.F1 == 64 && c.F2 == 64) return setup_run<T, 64, 64>(c, st);
     if (c.F1 == 128 && c.F2 == 64) return setup_run<T, 128, 64>(c, st);
     if (c.F1 == 128 && c.F2 == 128) return setup_run<T, 128, 128>(c, st);

@@ -47,6 +47,7 @@ inline int fft_size(int ns, int prec)
 // buffer in between; up to F4_FMAX.
 constexpr int F4_FMAX = 65536;
 constexpr int F4_FMIN = 4096;             // 64 x 64
+constexpr int F4B_FMIN = 1024;            // 32 x 32: the one-CTA-per-mode variant of batched curves
 constexpr int F4_THREADS = 256;           // 8 warps, one line each
 constexpr int F4C_CS = 8;                 // clustered four-step form: CTAs per cluster (portable size)
 constexpr size_t F4C_SMEM_MAX = 224 * 1024;   // its dynamic shared memory per CTA (of 227 KB)

@@ -45,11 +45,11 @@ Layout make_layout(int ns, int nx, int prec, int allow_split, int bn, int s_tran
     // batched curves the one-CTA FFT form wherever it fits
     int form = SF_DENSE;
     // batched curves: the FFT form with one CTA per mode wherever it fits, its
-    // four-step variant (register line transforms) from F = 4096 on
+    // four-step variant (register line transforms) from F = 1024 on
     bool batched_f4 = false;
     if (!allow_split) {
         form = (s_transform == 0 || s_transform == 2) && fft_size(ns, prec) ? SF_FFT1 : SF_DENSE;
-        if (form == SF_FFT1 && fft_size(ns, prec) >= F4_FMIN) {
+        if (form == SF_FFT1 && fft_size(ns, prec) >= F4B_FMIN) {
             form = SF_FFT4;
             batched_f4 = true;
         }
@@ -60,7 +60,7 @@ Layout make_layout(int ns, int nx, int prec, int allow_split, int bn, int s_tran
     else if (s_transform == 5) form = fft4_size(ns, prec, 1) ? SF_FFT4C : SF_DENSE;
     if (form == SF_FFT1) l.F = fft_size(ns, prec);
     if (form == SF_FFT4 || form == SF_FFT4C) {   // the four-step form
-        l.F = fft4_size(ns, prec, 1);
+        l.F = batched_f4 ? fft_size(ns, prec) : fft4_size(ns, prec, 1);
         l.f4 = 1;
         f4_split(l.F, l.F1, l.F2);
         l.f4c = (form == SF_FFT4C && f4c_fits(prec, l.F1, l.F2)) ? F4C_CS : 0;
