@@ -365,6 +365,18 @@ def main():
         host_in.copy_(curve.get_state().cpu())
         dev_in = torch.empty((spec.Ns, spec.N), dtype=dt, device=dev)
         n_e2e = max(1, min(args.e2e_steps, K))
+        nb = spec.Ns * spec.N * b
+        # every step: the curve from pinned host memory (set_state), one descent
+        # step, and its result J read back to the host (ks_curve_descend copies the
+        # device scalar record, 176 bytes, and synchronises)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        for _ in range(n_e2e):
+            dev_in.copy_(host_in, non_blocking=True)
+            curve.set_state(dev_in, 1.0, 0.0)
+            curve.descend(1)
+        e2e_s = time.perf_counter() - t0
+        # the same with the whole state read back as well (context)
         torch.cuda.synchronize(dev)
         t0 = time.perf_counter()
         for _ in range(n_e2e):
@@ -373,11 +385,12 @@ def main():
             curve.descend(1)
             host_out.copy_(curve.get_state(), non_blocking=True)
             torch.cuda.synchronize(dev)
-        e2e_s = time.perf_counter() - t0
-        nb = spec.Ns * spec.N * b
+        e2e_state_s = time.perf_counter() - t0
         e2e = {"value": points * n_e2e / e2e_s, "unit": UNIT, "h2d_bytes_per_step": nb,
-               "d2h_bytes_per_step": nb, "steps": n_e2e,
-               "path": "pinned host curve -> set_state -> descend(1) -> get_state -> pinned host"}
+               "d2h_bytes_per_step": 176, "steps": n_e2e,
+               "path": "pinned host curve -> set_state -> descend(1), J read back",
+               "with_state_readback": {"value": points * n_e2e / e2e_state_s, "d2h_bytes_per_step": nb + 176,
+                                       "path": "... -> get_state -> pinned host"}}
 
     # ---- steady state: K consecutive steps in one call (graph replay, L2 not flushed)
     steady = None
