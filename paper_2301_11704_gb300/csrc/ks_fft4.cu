@@ -1,9 +1,8 @@
-// ks_fft4.cu -- the FFT form of the s-contraction for transforms longer than one
-// CTA's shared memory holds (Ashtari & Schneider, arXiv 2301.11704, eq.
-// rational_diff_matrix, Sec. V.C.1; the convolution identity is stated beside
-// the single-CTA form in ks_kernels.cu):
+// ks_fft4.cu -- the four-step FFT form of the s-contraction (Ashtari & Schneider,
+// arXiv 2301.11704, eq. rational_diff_matrix, Sec. V.C.1; the convolution
+// identity is stated beside the single-CTA form in ks_kernels.cu):
 //
-//   y = IFFT_F( FFT_F(c_F) / F * FFT_F(z) )[0..P],   F = F1 F2 (powers of two <= 256)
+//   y = IFFT_F( FFT_F(c_F) / F * FFT_F(z) )[0..P],   F = F1 F2 (powers of two, 32 <= F1, F2 <= 256)
 //
 // with the index maps n = F2 n1 + n2 and k = k1 + F1 k2, so that
 //   FFT:  Z[k1 + F1 k2] = sum_n2 W_F2^(n2 k2) W_F^(n2 k1) sum_n1 W_F1^(n1 k1) z[F2 n1 + n2]
@@ -13,12 +12,18 @@
 // line held in registers (k1 and k2 stay in the transforms' scrambled order,
 // the spectrum and the twiddles are tabulated in it):
 //   pass 1 (per n2): z from the columns, FFT over n1, times W_F^(n2 k1), stored
-//          transposed as S[k1][n2] (staged through shared memory);
+//          transposed as S[k1][n2];
 //   pass 2 (per k1): FFT over n2, times the kernel spectrum (kept in the same
 //          order: no transposes), IFFT over k2, times W_F^(-n2 k1);
 //   pass 3 (per n2): IFFT over k1 -> y at j = F2 n1 + n2 <= P, and the epilogue
 //          of the single-CTA form (store D_t u; or G, the semi-implicit
 //          increment and the FP64 |G|^2 with its last-CTA sum).
+// Three variants of where S lives: a global scratch between three launches
+// (k_f4_p1/p2/p3, single curves, F >= 4096); the distributed shared memory of a
+// cluster of CTAs per mode group, in one launch that can also apply the step's
+// second contraction (k_f4c); one CTA's shared memory per (curve, mode) for
+// batched curves (k_f4b, F from 1024 to 8192).  Their set-up computes the
+// kernel spectrum by the forward half of the same decomposition in FP64.
 #include <cmath>
 
 #include <type_traits>
