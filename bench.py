@@ -439,11 +439,28 @@ def main():
             cl.init_trial(0.0, None, ampl, vpl)
             kl = max(3, min(50, K))
             msl, _ = timed_steps(cl, kl, 3)
-            large.append({"workload": "L=%g N_x=%d N_s=%d FP32" % (sp.L, sp.N, sp.Ns),
-                          "value": sp.M * kl / (sum(msl) / 1e3), "unit": UNIT, "ms_per_step": sum(msl) / kl,
-                          "steps": kl, "s_transform": "%s%s" % (cl.s_form, (", F=%d" % cl.fft_length) if cl.fft_length
-                                                                else "")})
+            entry = {"workload": "L=%g N_x=%d N_s=%d FP32" % (sp.L, sp.N, sp.Ns),
+                     "value": sp.M * kl / (sum(msl) / 1e3), "unit": UNIT, "ms_per_step": sum(msl) / kl,
+                     "steps": kl, "s_transform": "%s%s" % (cl.s_form, (", F=%d" % cl.fft_length) if cl.fft_length
+                                                           else "")}
             cl.close()
+            if cfg == 4:
+                # the mixed-precision workload's error against the plain FP64 GPU path:
+                # J and J_arc of the trial curve, J and the curve after ten steps
+                res = {}
+                for prec in ("fp64", "fp32"):
+                    ce = KSCurve(sp.L, sp.N, sp.Ns, sp.S, upl, uml, s0=sp.s0, dtau=sp.dtau, precision=prec,
+                                 device=dev)
+                    ce.init_trial(0.0, None, ampl, vpl)
+                    j2, ja = ce.cost()
+                    o = ce.descend(10)
+                    res[prec] = (j2, ja, o["J"], ce.get_state().double())
+                    ce.close()
+                (j2d, jad, jd, ud), (j2s, jas, js, us) = res["fp64"], res["fp32"]
+                entry["vs_fp64_gpu_path"] = {"J2_rel": abs(j2s - j2d) / j2d, "J_arc_rel": abs(jas - jad) / jad,
+                                             "J_after_10_steps_rel": abs(js - jd) / jd,
+                                             "u_after_10_steps_rel_2": float(((us - ud).norm() / ud.norm()).item())}
+            large.append(entry)
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
