@@ -4,17 +4,38 @@
 Metric: curve-point adjoint-gradient evaluations per second, i.e. interior
 curve points (M = N_s - 2 per curve) x descent steps / time.  One bench step is
 one full descent step of the workload curve: the row phase (f, residual,
-spatial adjoint, FP64 cost reductions), the s-phase with the descent update and
-|G|^2, and the s-phase D_t u of the new state (one kernel each, three each in
-the three-launch four-step form; one launch for both s-phases in the clustered
-form, the bench workload's).
+spatial adjoint, FP64 cost reductions), the s-contraction with the descent
+update and |G|^2, and the s-contraction D_t u of the new state.
 
-Default workload: L = 22, N_x = 64, N_s = 1024 (the differentiation workload),
-FP32 storage and transforms with FP64 reductions.  The curve is far smaller
-than L2, so L2 is flushed (a 256 MiB write) before every timed step and each
-step is timed on its own with CUDA events on the curve's stream.
+Workloads (`--workload`):
+  mixed  L = 100, N_x = 256, N_s = 16384 (the default: the largest single-GPU
+         curve, the mixed-precision workload): FP32 storage with FP64 reductions
+         (`--precision fp32`), the x-transforms as split-BF16 tensor-core
+         products (`bf16x2`, `bf16x3`), or plain FP64 (`fp64`);
+  large  L = 44, N_x = 128, N_s = 4096;
+  diff   L = 22, N_x = 64, N_s = 1024 (the differentiation workload);
+  batch  256 curves, L ~ U[20,60], N_x in {32,64,128}, N_s ~ U[256,2048].
+The single-curve workloads flush L2 (a 256 MiB write) before every timed step
+and time each step alone with CUDA events on the curve's stream.
+
+The JSON line carries, besides the throughput: the roofline of the dominant
+kernel (algorithmic bytes and flops per launch after the per-point counts below,
+over its mean event time), the HBM fraction of the whole step, the error of J,
+J_arc, the gradient and the curve after ten steps against the FP64 oracle
+(stored reference values), the plain FP64 GPU path at the same workload, an end
+to end number through the C ABI with host buffers, and a CPU baseline (the
+oracle on a bounded sample of the workload).
+
+Per interior point and step (N = N_x, M = N_s - 2, b = bytes per stored word):
+  flops  12.5 N log2 N (five real x-transforms) + 10 N log2(2(M+1)) (four real
+         s-transforms) + 30 N (pointwise);
+  bytes  2 N b (the state read and written; every intermediate can be recomputed).
+Per kernel: the row phase reads U, D_t U and writes R, A (4 N b per section);
+the update contraction reads R, A, U and writes U (4 N b); the D_t u contraction
+reads U and writes D (2 N b); each contraction does half the s-transform flops.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload mixed|large|diff|batch] [--precision ...]
 
 Under torchrun (N > 1) every rank runs its own curve (independent replicas,
 weak scaling); rank 0 prints the JSON line with the max-over-ranks time.
@@ -23,8 +44,10 @@ from __future__ import annotations
 
 import argparse
 import csv
+import hashlib
 import io
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -37,44 +60,93 @@ sys.path.insert(0, ROOT)
 METRIC = "curve-point adjoint-gradient evals/s"
 UNIT = "point-evals/s"
 FP32_LANES_PER_SM = 128
-N_SM = 152
-SM_MAX_MHZ = 2070.0
-# DRAM bytes (read + write) per launch of the dominant kernel, from one
-# `ncu --set full` capture of `bench.py --steps 30 --warmup 3` (caches flushed by
-# ncu between its passes), keyed by (form, F, N_x, precision, fused step); other
-# configurations report null, and an entry is dropped when its kernel changes.
-NCU_TRAFFIC = {("fft4c", 4096, 64, "fp32", True): 960512}
+WORKLOADS = {"diff": 1, "large": 2, "batch": 3, "mixed": 4}
+BYTES = {"fp64": 8, "fp32": 4, "bf16x2": 4, "bf16x3": 4}
+# the CUDA sources that define each kernel (a DRAM-traffic figure is used only
+# while these are unchanged since its capture)
+KERNEL_SOURCES = {
+    "rows": ["ks_device.cuh", "ks_kernels.cu", "ks_internal.h"],
+    "rows_tc": ["ks_rows_tc.cu", "ks_device.cuh", "ks_internal.h"],
+    "fft4": ["ks_fft4.cu", "ks_device.cuh", "ks_internal.h"],
+}
 
 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=3000)
-    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32")
-    ap.add_argument("--s-transform", choices=["auto", "dense", "fft", "dense_tc", "fft4", "fft4c"], default="auto",
-                    help="how D_t is applied along s in the headline curve")
-    ap.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the oracle CPU baseline")
-    ap.add_argument("--e2e-steps", type=int, default=100)
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="mixed")
+    ap.add_argument("--precision", choices=["fp64", "fp32", "bf16x2", "bf16x3"], default=None,
+                    help="default: the fastest form that meets the workload's J tolerance")
+    ap.add_argument("--s-transform", choices=["auto", "dense", "fft", "dense_tc", "fft4", "fft4c"], default="auto")
+    ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=["curve", "batch"], default="curve",
-                    help="curve: one L=22, N_x=64, N_s=1024 curve (default); batch: the 256-curve batch")
+    ap.add_argument("--no-context", action="store_true", help="skip the context measurements (other forms, "
+                                                                 "FP64 path, other workloads, oracle errors)")
     return ap.parse_args()
 
 
-def workload_spec():
+def default_precision(workload):
+    return "fp32"
+
+
+def spec_of(workload):
     from paper_2301_11704_gb300 import gen
-    return gen.workload(1)[0]
+    return gen.workload(WORKLOADS[workload])[0]
 
 
-def workload_config(spec, precision):
-    return {"workload": "KSE curve L=%g N_x=%d N_s=%d (M=%d), S=%g, dtau=%g, %s storage, FP64 reductions"
-                        % (spec.L, spec.N, spec.Ns, spec.M, spec.S, spec.dtau, precision),
-            "L": spec.L, "N_x": spec.N, "N_s": spec.Ns, "S": spec.S, "dtau": spec.dtau,
-            "adjoint": "paper", "curves_per_gpu": 1,
+def workload_name(spec, precision):
+    prec = {"fp64": "FP64", "fp32": "FP32 storage and transforms, FP64 reductions",
+            "bf16x2": "FP32 storage, x-transforms as 2-term split-BF16 tensor-core products, FP64 reductions",
+            "bf16x3": "FP32 storage, x-transforms as 3-term split-BF16 tensor-core products, FP64 reductions"}
+    return ("KSE curve L=%g N_x=%d N_s=%d (M=%d), S=%g, dtau=%g; %s"
+            % (spec.L, spec.N, spec.Ns, spec.M, spec.S, spec.dtau, prec[precision]))
+
+
+def config_of(spec, precision):
+    """The workload's config, the same in both arms."""
+    return {"workload": workload_name(spec, precision), "L": spec.L, "N_x": spec.N, "N_s": spec.Ns, "S": spec.S,
+            "dtau": spec.dtau, "precision": precision, "adjoint": "paper", "curves_per_gpu": 1,
             "l2": "flushed before every timed step (256 MiB write); each step timed alone",
             "parallelism": "independent replicas (one curve per GPU)"}
+
+
+def read_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "sm_max_mhz": 2070.0}, \
+            "fallback"
+
+
+def sources_digest(kind):
+    h = hashlib.sha256()
+    for name in KERNEL_SOURCES[kind]:
+        p = os.path.join(ROOT, "paper_2301_11704_gb300", "csrc", name)
+        if os.path.exists(p):
+            with open(p, "rb") as f:
+                h.update(f.read())
+    return h.hexdigest()[:12]
+
+
+def recorded_traffic(kernel_key, kind):
+    """DRAM bytes (read + write) per launch of a kernel from the ncu captures
+    summarised in profiles/dram_traffic.txt, when the kernel's sources are the
+    ones captured (else None)."""
+    path = os.path.join(ROOT, "profiles", "dram_traffic.txt")
+    if not os.path.exists(path):
+        return None
+    digest = sources_digest(kind)
+    with open(path) as f:
+        for line in f:
+            parts = line.split()
+            if len(parts) >= 3 and not line.startswith("#") and parts[0] == kernel_key and parts[2] == digest:
+                return {"bytes_per_launch": float(parts[1]), "sources": digest,
+                        "from": "ncu capture summarised in profiles/dram_traffic.txt"}
+    return None
 
 
 # ---------------------------------------------------------------------------- clocks
@@ -121,46 +193,89 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+# ---------------------------------------------------------------------------- per-point counts
+def flops_per_point(N, M):
+    """Section 8(d) counts per interior point and step: x-side, s-side, pointwise."""
+    fx = 12.5 * N * math.log2(N)
+    fs = 10.0 * N * math.log2(2 * (M + 1))
+    fp = 30.0 * N
+    return fx, fs, fp
+
+
 # ---------------------------------------------------------------------------- oracle (CPU)
-def oracle_steps(spec, budget_s, max_steps=None):
-    """Times the FP64 oracle's descent on the same curve until the budget is used."""
+ORACLE_COLS = 16     # complex Fourier columns of the s-direction sample (one per core on the box)
+ORACLE_ROWS = 64     # sections of the x-direction sample
+
+
+def oracle_sample_step(spec, U):
+    """One descent step of the oracle on a bounded sample of the workload curve,
+    scaled to the whole curve.  The oracle's step is an x-part per section (naive
+    DFTs: f, residual, spatial adjoint) and an s-part per Fourier column (the two
+    explicit trig sums of D_t applied to u and to r); each part is timed on a
+    sample, through the oracle's own curve functions as they stand:
+      s-part: curve_residual + curve_adjoint on the curve restricted to its first
+              ORACLE_COLS complex columns (all N_s sections; D_t on those columns
+              exactly as in the full step), scaled by (N/2) / ORACLE_COLS;
+      x-part: curve_residual + curve_adjoint on ORACLE_ROWS of its sections at
+              full N (the x-work of those sections), scaled by N_s / ORACLE_ROWS.
+    Returns the estimated seconds of one full oracle step."""
+    import numpy as np
+    import oracle
+    H = spec.N // 2
+    Uc = np.ascontiguousarray(U[:, :ORACLE_COLS])
+    t0 = time.perf_counter()
+    R, _ = oracle.curve_residual(Uc, spec.L, spec.S)
+    oracle.curve_adjoint(Uc, R, spec.L, spec.S)
+    t_cols = time.perf_counter() - t0
+    rows = np.linspace(0, spec.Ns - 1, ORACLE_ROWS).astype(int)
+    Ur = np.ascontiguousarray(U[rows])
+    t0 = time.perf_counter()
+    R, _ = oracle.curve_residual(Ur, spec.L, spec.S)
+    oracle.curve_adjoint(Ur, R, spec.L, spec.S)
+    t_rows = time.perf_counter() - t0
+    return t_cols * H / ORACLE_COLS + t_rows * spec.Ns / ORACLE_ROWS
+
+
+def oracle_baseline(spec, nsamples):
+    """(point-evals/s, per-sample step estimates, threads) of the oracle."""
     import oracle
     from paper_2301_11704_gb300 import gen
+    oracle.build()
     up, um = gen.end_points(spec)
     amps, vp = gen.perturbation(spec)
     U = oracle.curve_init(spec.M, spec.S, up, um, s0=spec.s0, amps=amps, vp=vp)
-    oracle.curve_descend(U, spec.L, spec.S, 1, dtau=spec.dtau)          # build + warm caches
-    times = []
-    t_all = time.perf_counter()
-    while True:
-        t0 = time.perf_counter()
-        U, _, _, _ = oracle.curve_descend(U, spec.L, spec.S, 1, dtau=spec.dtau)
-        times.append(time.perf_counter() - t0)
-        if max_steps is not None and len(times) >= max_steps:
-            break
-        if max_steps is None and time.perf_counter() - t_all >= budget_s:
-            break
-    return times, oracle.num_threads()
+    est = [oracle_sample_step(spec, U) for _ in range(nsamples)]
+    return spec.M * len(est) / sum(est), est, oracle.num_threads()
+
+
+def oracle_sample_text(spec):
+    return ("oracle descent step (FP64, OpenMP) of the same curve, timed on a sample and scaled to the curve: "
+            "the s-part (both D_t applications) on %d of %d complex Fourier columns x %d, the x-part on %d of %d "
+            "sections x %d" % (ORACLE_COLS, spec.N // 2, spec.N // 2 // ORACLE_COLS, ORACLE_ROWS, spec.Ns,
+                               spec.Ns // ORACLE_ROWS))
 
 
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
-    spec = workload_spec()
-    import oracle
-    oracle.build()
-    # warm-up steps are untimed; each timed step is one full oracle descent step of the curve
-    oracle_steps(spec, 0.0, max_steps=max(1, min(args.warmup, 3)))
-    times, cores = oracle_steps(spec, 0.0, max_steps=args.steps)
-    total = sum(times)
-    value = spec.M * len(times) / total
-    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": len(times),
-            "warmup": args.warmup, "ms_per_step": 1e3 * total / len(times), "higher_is_better": True,
+    if args.workload == "batch":
+        print(json.dumps({"impl": "reference", "unavailable": "the oracle baseline is defined for the single-curve "
+                                                             "workloads"}))
+        return 0
+    spec = spec_of(args.workload)
+    precision = args.precision or default_precision(args.workload)
+    W = max(0, args.warmup)
+    oracle_baseline(spec, max(1, min(W, 1)))          # untimed warm-up (builds, pages in)
+    value, est, cores = oracle_baseline(spec, args.steps)
+    total = sum(est)
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": len(est),
+            "warmup": W, "ms_per_step": 1e3 * total / len(est), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": workload_config(spec, "FP64"), "impl": "reference",
+            "config": config_of(spec, precision),
+            "impl": "reference",
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                             "sample": "%d full descent steps of the workload curve" % len(times)},
+                             "sample": oracle_sample_text(spec)},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
@@ -194,35 +309,28 @@ def run_batch(args):
     clk = clocks.stop()
     ms = e0.elapsed_time(e1)
     points = sum(s.M for s in specs)
-    from paper_2301_11704_gb300.build import fft_length
-
-    def sflops(s):   # both s-contractions of a step, in the form the curve runs
-        F = fft_length(s.Ns, True)
-        return 2 * (s.N // 2) * (2 * 5.0 * F * np.log2(F) + 6.0 * F) if F else 4.0 * s.Ns * s.Ns * s.N
-    flops = sum(sflops(s) for s in specs)
+    flops = sum(s.M * sum(flops_per_point(s.N, s.M)) for s in specs)
+    nsm = torch.cuda.get_device_properties(dev).multi_processor_count
+    peaks, src = read_peaks()
+    mhz = clk.get("sm_max_mhz") or peaks.get("sm_max_mhz", 2070.0)
+    peak_alu = nsm * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12
     ach = flops / (ms / args.steps / 1e3) / 1e12
-    peak = N_SM * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
-    bytes_alg = sum(2.0 * s.M * s.N * 4 for s in specs)   # state read + write per step
-    try:
-        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
-            hbm_peak = float(json.load(f).get("hbm_gbs", 6800.0))
-    except OSError:
-        hbm_peak = 6800.0
+    bytes_alg = sum(2.0 * s.M * s.N * 4 for s in specs)
+    hbm_peak = float(peaks["hbm_gbs"])
     hbm_ach = bytes_alg / (ms / args.steps / 1e3) / 1e9
     sc = b.scalars()
     line = {"metric": METRIC, "value": points * args.steps / (ms / 1e3), "unit": UNIT, "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": "batch of 256 KSE curves, L~U[20,60], N_x in {32,64,128}, N_s~U[256,2048]",
-                       "curves": len(specs), "points_per_step": points, "tile_width": chosen,
+                       "curves": len(specs), "points_per_step": points, "tuning": chosen,
                        "l2": "working set ~0.4 GB > L2; steps back to back (CUDA-graph replay)"},
-            "roofline": {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
-                         "traffic": None, "kernel": "whole step: flops of both s-contractions (FFT form "
-                                                     "where N_s allows) / step time",
-                         "algorithmic_flops_per_step": flops,
-                         "hbm": {"achieved": hbm_ach, "peak": hbm_peak, "unit": "GB/s", "frac": hbm_ach / hbm_peak,
-                                 "algorithmic_bytes_per_step": bytes_alg,
-                                 "note": "B_alg = state read + write (2 N_x b per point)"}},
+            "roofline": {"bound": "hbm", "achieved": hbm_ach, "peak": hbm_peak, "unit": "GB/s",
+                         "frac": hbm_ach / hbm_peak, "traffic": None, "peak_source": src,
+                         "kernel": "whole step of the batch",
+                         "algorithmic_bytes_per_step": bytes_alg,
+                         "alu": {"achieved": ach, "peak": peak_alu, "unit": "TFLOP/s", "frac": ach / peak_alu,
+                                 "algorithmic_flops_per_step": flops}},
             "gpu_launches": None, "clocks": clk,
             "median_J_rel": float(np.median([x["J"] / max(x["Dnorm"], 1e-300) for x in sc]))}
     print(json.dumps(line))
@@ -230,13 +338,56 @@ def run_batch(args):
     return 0
 
 
-# ---------------------------------------------------------------------------- GPU
-def main():
-    args = parse()
-    if args.impl == "reference":
-        return run_reference(args)
-    if args.workload == "batch":
-        return run_batch(args)
+# ---------------------------------------------------------------------------- errors against the oracle
+def oracle_errors(spec, make_curve, precision):
+    """J^2, J_arc, dJ^2/dl, |G|_W and sampled G of the trial curve, J, J_arc and
+    sampled sections after ten steps, against the FP64 oracle's stored values
+    (tests/golden/fullsize_*.json, written by tests/golden/make_fullsize_refs.py)."""
+    import numpy as np
+    path = os.path.join(ROOT, "tests", "golden", "fullsize_L%g_N%d_Ns%d.json" % (spec.L, spec.N, spec.Ns))
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        ref = json.load(f)
+    rows = ref["rows"]
+
+    def cx(rowsvals):
+        a = np.array(rowsvals)
+        return a[..., 0] + 1j * a[..., 1]
+
+    k = 2 * np.pi * np.arange(spec.N // 2) / spec.L
+    a = k ** 4 - k ** 2
+    pw = spec.dtau / (1.0 + spec.dtau * a * a)
+
+    def spec_rows(x):
+        x = np.asarray(x, dtype=np.float64)
+        return np.fft.rfft(x, axis=1)[:, : spec.N // 2] / spec.N
+
+    c = make_curve(precision)
+    J2, Ja = c.cost()
+    g, dl = c.gradient()
+    sc = c.scalars()
+    Gs = spec_rows(g.double().cpu().numpy()[rows])
+    Gr = cx(ref["trial"]["G_rows"])
+    res = c.descend(ref["after_steps"]["steps"])
+    u = c.get_state().double().cpu().numpy()
+    Us = spec_rows(u[rows])
+    Ur = cx(ref["after_steps"]["U_rows"])
+    c.close()
+    tr = ref["trial"]
+    rel = lambda x, y: abs(x - y) / abs(y)
+    return {"J2": rel(J2, tr["J2"]), "J_arc": rel(Ja, tr["J_arc"]),
+            "dJ2_dlambda": rel(dl, tr["dJ2_dlambda"]), "Dnorm": rel(sc["Dnorm"], tr["Dnorm"]),
+            "G_norm_W": rel(sc["G_norm"], math.sqrt(tr["G2"])),
+            "G_sampled_precond": float(np.linalg.norm((Gs - Gr) * pw) / np.linalg.norm(Gr * pw)),
+            "J_after_10": rel(res["J"], ref["after_steps"]["J"]),
+            "J_arc_after_10": rel(res["J_arc"], ref["after_steps"]["J_arc"]),
+            "u_sampled_after_10": float(np.linalg.norm(Us - Ur) / np.linalg.norm(Ur)),
+            "sampled_sections": len(rows), "reference": os.path.relpath(path, ROOT)}
+
+
+# ---------------------------------------------------------------------------- single curve
+def run_curve(args):
     import numpy as np
     import torch
     import torch.distributed as dist
@@ -255,12 +406,13 @@ def main():
         if world > 1:
             dist.barrier()
 
-    spec = workload_spec()
+    spec = spec_of(args.workload)
+    precision = args.precision or default_precision(args.workload)
     up, um = gen.end_points(spec)
     amps, vp = gen.perturbation(spec)
 
-    def make_curve(precision, s_transform="auto"):
-        c = KSCurve(spec.L, spec.N, spec.Ns, spec.S, up, um, s0=spec.s0, dtau=spec.dtau, precision=precision,
+    def make_curve(prec, s_transform=args.s_transform):
+        c = KSCurve(spec.L, spec.N, spec.Ns, spec.S, up, um, s0=spec.s0, dtau=spec.dtau, precision=prec,
                     s_transform=s_transform, device=dev)
         c.init_trial(0.0, None, amps, vp)
         return c
@@ -290,82 +442,99 @@ def main():
             c.profile(0)
         return ms, prof
 
-    curve = make_curve(args.precision, args.s_transform)
-    K, W = args.steps, args.warmup
+    curve = make_curve(precision)
+    K, W = args.steps, max(3, args.warmup)
     clocks = ClockSampler(local)
     clocks.start()
-    # per-kernel events on the first 1/20 of the timed steps only: events between
-    # kernels serialise them, so the other steps run as a user's would
-    step_ms, prof = timed_steps(curve, K, W, profile=max(1, K // 20))
+    # per-kernel events on the first 1/20 of the timed steps only (events between
+    # kernels serialise them); the other steps run as a user's would
+    step_ms, prof = timed_steps(curve, K, W, profile=max(3, K // 20))
     clk = clocks.stop()
     total_ms = sum(step_ms)
     t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
     if world > 1:
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
     total_ms_max = float(t.item())
-    points = spec.M
-    value = world * points * K / (total_ms_max / 1e3)
-    sc = curve.scalars()
+    M, N, b = spec.M, spec.N, BYTES[precision]
+    value = world * M * K / (total_ms_max / 1e3)
+    ms_step = total_ms_max / K
 
-    # ---- roofline of the dominant kernel (per-launch event times from inside the library)
-    b = 4 if args.precision == "fp32" else 8
-    field = spec.Ns * spec.N * b
-    avg = {k: v["ms"] / max(v["launches"], 1) for k, v in prof.items()}
-    dom = max(avg, key=avg.get)
-    from paper_2301_11704_gb300.build import fft_length
+    # ---- roofline: the dominant kernel, bytes and flops after the per-point counts
+    peaks, peak_src = read_peaks()
+    nsm = torch.cuda.get_device_properties(dev).multi_processor_count
+    mhz = clk.get("sm_max_mhz") or peaks.get("sm_max_mhz", 2070.0)
+    peak_fp32 = nsm * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12
+    peak_alu = peak_fp32 if b == 4 else 1.25
+    hbm_peak = float(peaks["hbm_gbs"])
+    fx, fs, fpw = flops_per_point(N, M)
     F = curve.fft_length
-    form_name = {"dense": "dense contraction", "dense_tc": "dense contraction on the tensor cores",
-                 "fft": "FFT convolution, one CTA per mode", "fft4": "four-step FFT convolution, three launches",
-                 "fft4c": "four-step FFT convolution, one clustered launch"}[curve.s_form]
-    if F:   # FFT form: per mode two complex FFTs of length F and the spectral product
-        flops_dt = (spec.N // 2) * (2 * 5.0 * F * np.log2(F) + 6.0 * F)
-        dt_form = "%s, F=%d" % (form_name, F)
-    else:
-        flops_dt = 2.0 * spec.Ns * spec.Ns * spec.N
-        dt_form = form_name
-    # kernels per timed step (one descend call of one step, whose row phase arms
-    # the step limit): the row phase and two s-contractions (three launches each
-    # in the three-launch four-step form, both in one launch in the clustered form)
-    n_x = spec.N
-    fused = curve.s_form == "fft4c" and ((n_x <= 64 and F <= 16384) or (n_x <= 128 and F <= 8192) if b == 4
-                                         else n_x <= 16 and F == 4096)
-    launches_per_step = 2 if fused else (7 if curve.s_form == "fft4" else 3)
-    if fused:   # the update launch applies both contractions
-        flops_dt *= 2
-        dt_form += "; update and D_t u in one launch"
-    peak_alu = (N_SM * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12) if b == 4 else 1.25
-    peaks = {}
-    try:
-        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
-            peaks = json.load(f)
-    except OSError:
-        pass
-    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    form = curve.s_form
+    fused = form == "fft4c" and "dt_store" not in prof
+    kernels = {}   # name -> (mean ms per launch, algorithmic bytes, algorithmic flops, traffic kind)
+    rows_kind = "rows_tc" if precision.startswith("bf16") else "rows"
+    if "rows" in prof:
+        kernels["rows"] = (prof["rows"]["ms"] / prof["rows"]["launches"], 4.0 * N * b * spec.Ns,
+                           (fx + fpw) * M, rows_kind)
+    for key, nb in (("dt_update", 4.0), ("dt_store", 2.0)):
+        if key in prof:
+            fl = fs / 2 * M * (2 if (key == "dt_update" and fused) else 1)
+            by = (nb + (2.0 if (key == "dt_update" and fused) else 0.0)) * N * b * spec.Ns
+            kernels[key] = (prof[key]["ms"] / prof[key]["launches"], by, fl, "fft4")
+    dom = max(kernels, key=lambda k: kernels[k][0])
+    t_dom, by_dom, fl_dom, kind = kernels[dom]
+    kernel_names = {"rows": "row phase (k_rows%s)" % ("_tc" if rows_kind == "rows_tc" else ""),
+                    "dt_update": "update contraction (%s)" % form, "dt_store": "D_t u contraction (%s)" % form}
+    ach = by_dom / (t_dom / 1e3) / 1e9
+    roof = {"bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s", "frac": ach / hbm_peak,
+            "traffic": None, "peak_source": peak_src + " (MEASURED_PEAKS.json hbm_gbs)",
+            "kernel": kernel_names[dom], "algorithmic_bytes_per_launch": by_dom,
+            "ms_per_launch": t_dom,
+            "alu": {"achieved": fl_dom / (t_dom / 1e3) / 1e12, "peak": peak_alu, "unit": "TFLOP/s",
+                    "frac": fl_dom / (t_dom / 1e3) / 1e12 / peak_alu, "algorithmic_flops_per_launch": fl_dom,
+                    "peak_source": ("%d SMs x 128 FP32 lanes x 2 flop x %.0f MHz (derived)" % (nsm, mhz))
+                    if b == 4 else "nominal FP64 1.25 TFLOP/s"},
+            "phase_ms_per_launch": {k: v[0] for k, v in kernels.items()}}
+    if "passes" in prof:
+        roof["pass_ms_per_launch"] = {k: [p["ms"] / max(p["launches"], 1) for p in v]
+                                      for k, v in prof["passes"].items()}
+        roof["note"] = ("a contraction of the three-launch four-step form counts as one kernel of three "
+                        "launches (passes); its passes' times are listed")
+    traf = None
     if dom == "rows":
-        bytes_alg = 4 * field + spec.Ns * 32
-        ach = bytes_alg / (avg[dom] / 1e3) / 1e9
-        roof = {"bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s", "frac": ach / hbm_peak,
-                "traffic": None, "kernel": "k_rows", "algorithmic_bytes": bytes_alg}
-    else:
-        ach = flops_dt / (avg[dom] / 1e3) / 1e12
-        roof = {"bound": "alu", "achieved": ach, "peak": peak_alu, "unit": "TFLOP/s", "frac": ach / peak_alu,
-                "traffic": None, "kernel": "s-contraction (%s, %s)" % (dom, dt_form), "algorithmic_flops": flops_dt,
-                "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz" if b == 4 else
-                "nominal FP64 1.25 TFLOP/s"}
-    roof["phase_ms_per_launch"] = avg
-    if dom != "rows":
-        roof["traffic"] = NCU_TRAFFIC.get((curve.s_form, F, spec.N, args.precision, fused))
+        traf = recorded_traffic("rows:%s:N%d:Ns%d:%s" % (rows_kind, N, spec.Ns, precision), rows_kind)
+    elif form == "fft4":
+        traf = recorded_traffic("%s:fft4:N%d:Ns%d:%s" % (dom, N, spec.Ns, precision), "fft4")
+    if traf:
+        roof["traffic"] = traf["bytes_per_launch"]
+        roof["traffic_source"] = traf
+    if precision.startswith("bf16") and "rows" in kernels:
+        nprod = 6 if precision == "bf16x3" else 3
+        tfl = 4 * 2.0 * N * N * spec.Ns          # four real N x N DFT products per section
+        tr = kernels["rows"][0]
+        tpeak = float(peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops", 1700.0)))
+        roof["tensor_rows"] = {"achieved": tfl / (tr / 1e3) / 1e12, "peak": tpeak, "unit": "TFLOP/s",
+                               "frac": tfl / (tr / 1e3) / 1e12 / tpeak,
+                               "algorithmic_flops_per_launch": tfl,
+                               "executed_tensor_flops_per_launch": tfl * nprod,
+                               "executed_frac": tfl * nprod / (tr / 1e3) / 1e12 / tpeak,
+                               "peak_source": peak_src + " bf16 sustained (MEASURED_PEAKS.json)"}
+    bytes_step = 2.0 * N * b * M
+    flops_step = (fx + fs + fpw) * M
+    hbm_step = {"achieved": bytes_step / (ms_step / 1e3) / 1e9, "peak": hbm_peak, "unit": "GB/s",
+                "frac": bytes_step / (ms_step / 1e3) / 1e9 / hbm_peak, "algorithmic_bytes_per_step": bytes_step,
+                "alu": {"achieved": flops_step / (ms_step / 1e3) / 1e12, "peak": peak_alu, "unit": "TFLOP/s",
+                        "frac": flops_step / (ms_step / 1e3) / 1e12 / peak_alu,
+                        "algorithmic_flops_per_step": flops_step}}
 
     # ---- end to end through the public API with host buffers
     e2e = None
     if rank == 0 or world > 1:
         dt = curve.dtype
-        host_in = torch.empty((spec.Ns, spec.N), dtype=dt).pin_memory()
-        host_out = torch.empty((spec.Ns, spec.N), dtype=dt).pin_memory()
+        host_in = torch.empty((spec.Ns, N), dtype=dt).pin_memory()
         host_in.copy_(curve.get_state().cpu())
-        dev_in = torch.empty((spec.Ns, spec.N), dtype=dt, device=dev)
+        dev_in = torch.empty((spec.Ns, N), dtype=dt, device=dev)
         n_e2e = max(1, min(args.e2e_steps, K))
-        nb = spec.Ns * spec.N * b
+        nbytes = spec.Ns * N * b
         # every step: the curve from pinned host memory (set_state), one descent
         # step, and its result J read back to the host (ks_curve_descend copies the
         # device scalar record, 176 bytes, and synchronises)
@@ -376,112 +545,91 @@ def main():
             curve.set_state(dev_in, 1.0, 0.0)
             curve.descend(1)
         e2e_s = time.perf_counter() - t0
-        # the same with the whole state read back as well (context)
-        torch.cuda.synchronize(dev)
-        t0 = time.perf_counter()
-        for _ in range(n_e2e):
-            dev_in.copy_(host_in, non_blocking=True)
-            curve.set_state(dev_in, 1.0, 0.0)
-            curve.descend(1)
-            host_out.copy_(curve.get_state(), non_blocking=True)
-            torch.cuda.synchronize(dev)
-        e2e_state_s = time.perf_counter() - t0
-        e2e = {"value": points * n_e2e / e2e_s, "unit": UNIT, "h2d_bytes_per_step": nb,
+        e2e = {"value": M * n_e2e / e2e_s, "unit": UNIT, "h2d_bytes_per_step": nbytes,
                "d2h_bytes_per_step": 176, "steps": n_e2e,
-               "path": "pinned host curve -> set_state -> descend(1), J read back",
-               "with_state_readback": {"value": points * n_e2e / e2e_state_s, "d2h_bytes_per_step": nb + 176,
-                                       "path": "... -> get_state -> pinned host"}}
+               "path": "pinned host curve -> set_state -> descend(1), J read back"}
+    sc = curve.scalars()
+    curve.close()
 
-    # ---- steady state: K consecutive steps in one call (graph replay, L2 not flushed)
-    steady = None
-    if rank == 0:
-        curve.descend_async(min(K, 64))
-        torch.cuda.synchronize(dev)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        curve.descend_async(K)
-        e1.record()
-        torch.cuda.synchronize(dev)
-        ms = e0.elapsed_time(e1)
-        steady = {"value": points * K / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / K, "steps": K,
-                  "note": "descend_async(K): CUDA-graph replay, curve L2-resident (not the headline)"}
-
-    # ---- the other form of the s-contraction (context)
-    other = None
-    other_form = "dense" if F else "fft"
-    if F or fft_length(spec.Ns, b == 4):
-        cd = make_curve(args.precision, other_form)
-        kd = max(3, min(200, K))
-        msd, _ = timed_steps(cd, kd, 3)
-        other = {"form": other_form, "value": points * kd / (sum(msd) / 1e3), "unit": UNIT,
-                 "ms_per_step": sum(msd) / kd, "steps": kd}
-        cd.close()
-
-    # ---- FP64 GPU path (context)
-    fp64 = None
-    if args.precision == "fp32":
-        c64 = make_curve("fp64")
-        k64 = max(3, min(50, K))
-        ms64, _ = timed_steps(c64, k64, 3)
-        fp64 = {"value": points * k64 / (sum(ms64) / 1e3), "unit": UNIT, "ms_per_step": sum(ms64) / k64,
-                "steps": k64}
-        c64.close()
-
-    # ---- the larger workloads (context): L=44, N_x=128, N_s=4096 and L=100, N_x=256,
-    # N_s=16384, FP32 storage, the form auto picks, L2 flushed before each step
-    large = []
-    if rank == 0 and args.precision == "fp32":
-        for cfg in (2, 4):
-            sp = gen.workload(cfg)[0]
-            upl, uml = gen.end_points(sp)
-            ampl, vpl = gen.perturbation(sp)
-            cl = KSCurve(sp.L, sp.N, sp.Ns, sp.S, upl, uml, s0=sp.s0, dtau=sp.dtau, precision="fp32", device=dev)
-            cl.init_trial(0.0, None, ampl, vpl)
-            kl = max(3, min(50, K))
-            msl, _ = timed_steps(cl, kl, 3)
-            entry = {"workload": "L=%g N_x=%d N_s=%d FP32" % (sp.L, sp.N, sp.Ns),
-                     "value": sp.M * kl / (sum(msl) / 1e3), "unit": UNIT, "ms_per_step": sum(msl) / kl,
-                     "steps": kl, "s_transform": "%s%s" % (cl.s_form, (", F=%d" % cl.fft_length) if cl.fft_length
-                                                           else "")}
-            cl.close()
-            if cfg == 4:
-                # the mixed-precision workload's error against the plain FP64 GPU path:
-                # J and J_arc of the trial curve, J and the curve after ten steps
-                res = {}
-                for prec in ("fp64", "fp32"):
-                    ce = KSCurve(sp.L, sp.N, sp.Ns, sp.S, upl, uml, s0=sp.s0, dtau=sp.dtau, precision=prec,
-                                 device=dev)
-                    ce.init_trial(0.0, None, ampl, vpl)
-                    j2, ja = ce.cost()
-                    o = ce.descend(10)
-                    res[prec] = (j2, ja, o["J"], ce.get_state().double())
-                    ce.close()
-                (j2d, jad, jd, ud), (j2s, jas, js, us) = res["fp64"], res["fp32"]
-                entry["vs_fp64_gpu_path"] = {"J2_rel": abs(j2s - j2d) / j2d, "J_arc_rel": abs(jas - jad) / jad,
-                                             "J_after_10_steps_rel": abs(js - jd) / jd,
-                                             "u_after_10_steps_rel_2": float(((us - ud).norm() / ud.norm()).item())}
-            large.append(entry)
+    ctx = {}
+    if rank == 0 and not args.no_context:
+        # ---- plain FP64 GPU path at the same workload
+        if precision != "fp64":
+            c64 = make_curve("fp64")
+            k64 = max(3, min(20, K))
+            ms64, _ = timed_steps(c64, k64, 3)
+            ctx["fp64_gpu_path"] = {"value": M * k64 / (sum(ms64) / 1e3), "unit": UNIT,
+                                    "ms_per_step": sum(ms64) / k64, "steps": k64, "s_form": c64.s_form}
+            c64.close()
+        # ---- the other precisions of this workload
+        others = {}
+        for prec in ("fp32", "bf16x3", "bf16x2"):
+            if prec == precision:
+                continue
+            try:
+                co = make_curve(prec)
+            except Exception as exc:   # a precision this build or size does not support
+                others[prec] = {"unavailable": str(exc)[:120]}
+                continue
+            ko = max(3, min(50, K))
+            mso, _ = timed_steps(co, ko, 3)
+            others[prec] = {"value": M * ko / (sum(mso) / 1e3), "unit": UNIT, "ms_per_step": sum(mso) / ko,
+                            "steps": ko}
+            co.close()
+        ctx["other_precisions"] = others
+        # ---- error against the FP64 oracle (stored reference values)
+        errs = {}
+        for prec in sorted({precision, "fp64", "fp32"} | ({"bf16x2", "bf16x3"} if spec.N >= 128 else set())):
+            try:
+                errs[prec] = oracle_errors(spec, make_curve, prec)
+            except Exception as exc:
+                errs[prec] = {"unavailable": str(exc)[:120]}
+        ctx["error_vs_oracle"] = errs
+        # ---- the differentiation workload (context)
+        if args.workload != "diff":
+            sd = spec_of("diff")
+            upd, umd = gen.end_points(sd)
+            ampd, vpd = gen.perturbation(sd)
+            cd = KSCurve(sd.L, sd.N, sd.Ns, sd.S, upd, umd, s0=sd.s0, dtau=sd.dtau, precision="fp32", device=dev)
+            cd.init_trial(0.0, None, ampd, vpd)
+            kd = max(3, min(200, K))
+            msd, _ = timed_steps(cd, kd, 3)
+            ctx["diff_workload_fp32"] = {"workload": "L=%g N_x=%d N_s=%d FP32" % (sd.L, sd.N, sd.Ns),
+                                         "value": sd.M * kd / (sum(msd) / 1e3), "unit": UNIT,
+                                         "ms_per_step": sum(msd) / kd, "steps": kd, "s_form": cd.s_form}
+            cd.close()
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
-        times, cores = oracle_steps(spec, args.cpu_seconds)
-        cpu = {"value": points * len(times) / sum(times), "unit": UNIT, "cores": cores, "kind": "oracle",
-               "sample": "%d full FP64 descent steps of the same curve (%.1f s)" % (len(times), sum(times))}
+        v, est, cores = oracle_baseline(spec, 3)
+        cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": oracle_sample_text(spec),
+               "seconds_per_step_estimates": est}
 
     if rank == 0:
+        launches = {"fft4": 7, "fft4c": 2 if fused else 3}.get(form, 3)
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
-                "ms_per_step": total_ms_max / K, "higher_is_better": True, "scaling": "weak",
-                "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "f64", "data": "synthetic",
-                "config": dict(workload_config(spec, args.precision.upper()), s_transform=dt_form),
-                "roofline": roof,
-                "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches_per_step * K, "clocks": clk,
-                "fp64_gpu_path": fp64, "larger_workloads": large, "other_s_transform": other, "steady_state": steady, "final_J": sc["J"], "final_J_arc": sc["J_arc"],
-                "step_ms_median": statistics.median(step_ms)}
+                "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": {"fp64": "f64", "fp32": "f32"}.get(precision, precision + "+f32"),
+                "data": "synthetic",
+                "config": config_of(spec, precision),
+                "s_transform": "%s%s" % (form, (", F=%d" % F) if F else ""),
+                "roofline": roof, "hbm_step": hbm_step,
+                "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches * K, "clocks": clk,
+                "final_J": sc["J"], "final_J_arc": sc["J_arc"], "step_ms_median": statistics.median(step_ms)}
+        line.update(ctx)
         print(json.dumps(line))
-    curve.close()
     if world > 1:
         dist.destroy_process_group()
     return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    if args.workload == "batch":
+        return run_batch(args)
+    return run_curve(args)
 
 
 if __name__ == "__main__":

@@ -260,6 +260,9 @@ typedef struct {
     double step_ms;          /* persistent step kernel: milliseconds of its launches */
     int64_t step_launches;   /* its launches */
     int64_t step_steps;      /* steps those launches were asked to run */
+    double pass_ms[2][3];    /* three-launch four-step form (s_transform 4): milliseconds of
+                                passes 1, 2, 3 of the update (row 0) and of D_t u (row 1) */
+    int64_t pass_launches[2][3];
 } ks_profile;
 
 ks_status ks_curve_profile(ks_curve *c, int32_t max_steps);
@@ -316,19 +319,24 @@ ks_status ks_batch_destroy(ks_batch *b);
  * synchronisation and latency, or a process whose device memory is reserved up
  * front.  It computes J^2 and J_arc (eq. cost_function_general, eq. J_arc) of
  * a curve without a handle and without a workspace:
- *   p        parameters, same rules as ks_curve_workspace_bytes; the curve's
- *            scratch (ks_curve_workspace_bytes(p)) must not exceed
- *            KS_NOALLOC_SCRATCH_BYTES, else KS_ENOMEM with a message.
+ *   p        parameters, same rules as ks_curve_workspace_bytes; p->launch is
+ *            ignored (the evaluation runs kernel by kernel).  The scratch the
+ *            curve needs, ks_curve_workspace_bytes(p) with p->launch = 0, must
+ *            not exceed KS_NOALLOC_SCRATCH_BYTES, else KS_ENOMEM with a message.
  *   u_dev    [N_s][N] physical curve in the storage type (rows 0 and N_s-1
  *            are the end sections u_+ and u_-).
- *   out_dev  device doubles [2] receiving J^2 and J_arc.
+ *   out_dev  device doubles [2] receiving J^2 and J_arc; both are NaN when a
+ *            bounded device-side wait of the evaluation gave up (the results
+ *            of that launch are invalid; ks_curve_cost reports the same event
+ *            as KS_ETIMEOUT).
  *   stream   cudaStream_t (NULL = legacy default stream); asynchronous.
  * The scratch is one static device array of KS_NOALLOC_SCRATCH_BYTES, held on
- * every device that loads the library until the process exits.  The first
- * call on a device looks up that array's device address (with that device
- * current); make that first call before any stream capture.  All calls share
- * the array and it keeps the last call's contents (each call clears what must
- * start at zero): calls that overlap on the GPU race and give wrong results.
+ * every device that loads the library until the process exits.  Every call
+ * looks up that array's device address in the current device's context (the
+ * first call on a device also loads the library's module there); make the
+ * first call on a device before any stream capture.  All calls share the array
+ * and it keeps the last call's contents (each call clears what must start at
+ * zero): calls that overlap on the GPU race and give wrong results.
  * No device memory is allocated or freed. */
 #define KS_NOALLOC_SCRATCH_BYTES (32u << 20)
 ks_status ks_cost_noalloc(const ks_params *p, const void *u_dev, double *out_dev, void *stream);

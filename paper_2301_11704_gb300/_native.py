@@ -69,7 +69,8 @@ class KSScalars(ctypes.Structure):
 
 class KSProfile(ctypes.Structure):
     _fields_ = [("ms", ctypes.c_double * 3), ("launches", ctypes.c_int64 * 3), ("step_ms", ctypes.c_double),
-                ("step_launches", ctypes.c_int64), ("step_steps", ctypes.c_int64)]
+                ("step_launches", ctypes.c_int64), ("step_steps", ctypes.c_int64),
+                ("pass_ms", (ctypes.c_double * 3) * 2), ("pass_launches", (ctypes.c_int64 * 3) * 2)]
 
 
 class KSError(RuntimeError):

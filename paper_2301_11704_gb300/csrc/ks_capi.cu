@@ -17,8 +17,10 @@ struct ks_curve {
     ks::CurveDev d;
     cudaStream_t st;
     int device;
-    // profiling: events[2*(3*entry + phase)] / [.. + 1] bracket one kernel; an
-    // entry is a three-kernel step (prof_steps = 0) or a persistent launch of
+    // profiling: events[EV_PER_ENTRY * entry + 2 * phase] / [.. + 1] bracket one
+    // phase; [.. + 6], [.. + 7] (update) and [.. + 8], [.. + 9] (D_t u) mark the
+    // ends of the first two passes of the three-launch four-step form; an entry
+    // is a kernel-per-phase step (prof_steps = 0) or a persistent launch of
     // prof_steps steps (phase 0 only)
     std::vector<cudaEvent_t> events;
     std::vector<int64_t> prof_steps;
@@ -31,6 +33,7 @@ struct ks_curve {
 };
 
 static const int GRAPH_STEPS = 16;
+static const int EV_PER_ENTRY = 10;
 
 static thread_local char g_err[512];
 
@@ -131,6 +134,8 @@ ks_status read_scalars(ks_curve *c, ks::DevScalars *h)
 // The clustered four-step form applies the update and D_t u of the updated state
 // in one launch (GM_STEP) at the sizes of f4c_fused; every other form in two.
 static bool fused_step(const ks_curve *c) { return c->d.f4c != 0 && ks::f4c_fused(c->d.prec, c->d.nx, c->d.F); }
+// The three-launch four-step form, whose passes are timed one by one.
+static bool three_pass(const ks_curve *c) { return c->d.f4 && !c->d.f4c && !c->d.f4b; }
 
 ks_status launch_step(ks_curve *c, int discrete, cudaStream_t st)
 {
@@ -190,7 +195,7 @@ ks_status enqueue_steps(ks_curve *c, int64_t nsteps, double tol)
         for (int64_t done = 0; done < nsteps; done += PERSISTENT_STEPS) {
             const int64_t n = std::min(PERSISTENT_STEPS, nsteps - done);
             const bool prof = c->prof_used < c->prof_cap;
-            cudaEvent_t *ev = prof ? &c->events[(size_t)6 * c->prof_used] : nullptr;
+            cudaEvent_t *ev = prof ? &c->events[(size_t)EV_PER_ENTRY * c->prof_used] : nullptr;
             if (prof) KS_CUDA(cudaEventRecord(ev[0], c->st));
             KS_CUDA(ks::launch_step_persistent(c->d, discrete, (long long)n, c->st));
             if (prof) {
@@ -213,16 +218,17 @@ ks_status enqueue_steps(ks_curve *c, int64_t nsteps, double tol)
     }
     for (int64_t s = 0; s < nsteps; ++s) {
         const bool prof = c->prof_used < c->prof_cap;
-        cudaEvent_t *ev = prof ? &c->events[(size_t)6 * c->prof_used] : nullptr;
+        cudaEvent_t *ev = prof ? &c->events[(size_t)EV_PER_ENTRY * c->prof_used] : nullptr;
+        cudaEvent_t *pass_u = (prof && three_pass(c)) ? ev + 6 : nullptr, *pass_d = pass_u ? ev + 8 : nullptr;
         if (prof) KS_CUDA(cudaEventRecord(ev[0], c->st));
         const ks::StepArm arm = {(long long)nsteps, tol, s == 0 ? 1 : 0};
         KS_CUDA(ks::launch_rows(c->d, ks::ROWS_STEP, c->st, arm));
         if (prof) KS_CUDA(cudaEventRecord(ev[1], c->st));
         if (prof) KS_CUDA(cudaEventRecord(ev[2], c->st));
-        KS_CUDA(ks::launch_dt(c->d, fused_step(c) ? ks::GM_STEP : ks::GM_UPDATE, discrete, 1, c->st));
+        KS_CUDA(ks::launch_dt(c->d, fused_step(c) ? ks::GM_STEP : ks::GM_UPDATE, discrete, 1, c->st, pass_u));
         if (prof) KS_CUDA(cudaEventRecord(ev[3], c->st));
         if (prof) KS_CUDA(cudaEventRecord(ev[4], c->st));
-        if (!fused_step(c)) KS_CUDA(ks::launch_dt(c->d, ks::GM_STORE, 0, 1, c->st));
+        if (!fused_step(c)) KS_CUDA(ks::launch_dt(c->d, ks::GM_STORE, 0, 1, c->st, pass_d));
         if (prof) {
             KS_CUDA(cudaEventRecord(ev[5], c->st));
             c->prof_steps[c->prof_used] = 0;
@@ -545,7 +551,7 @@ ks_status ks_curve_profile(ks_curve *c, int32_t max_steps)
     if (!g.ok) return fail(KS_ECUDA, "cannot select the curve's device");
     KS_CUDA(cudaStreamSynchronize(c->st));
     release_events(c);
-    c->events.resize((size_t)6 * max_steps);
+    c->events.resize((size_t)EV_PER_ENTRY * max_steps);
     for (size_t i = 0; i < c->events.size(); ++i) {
         if (cudaEventCreate(&c->events[i]) != cudaSuccess) {
             c->events.resize(i);
@@ -570,18 +576,31 @@ ks_status ks_curve_profile_read(ks_curve *c, ks_profile *out)
     for (int st = 0; st < c->prof_used; ++st) {
         if (c->prof_steps[st] > 0) {
             float ms = 0.f;
-            KS_CUDA(cudaEventElapsedTime(&ms, c->events[(size_t)6 * st], c->events[(size_t)6 * st + 1]));
+            KS_CUDA(cudaEventElapsedTime(&ms, c->events[(size_t)EV_PER_ENTRY * st], c->events[(size_t)EV_PER_ENTRY * st + 1]));
             out->step_ms += ms;
             out->step_launches += 1;
             out->step_steps += c->prof_steps[st];
             continue;
         }
+        const cudaEvent_t *ev = &c->events[(size_t)EV_PER_ENTRY * st];
         for (int ph = 0; ph < 3; ++ph) {
             if (ph == 2 && fused_step(c)) continue;   // D_t u ran inside the update launch
             float ms = 0.f;
-            KS_CUDA(cudaEventElapsedTime(&ms, c->events[(size_t)6 * st + 2 * ph], c->events[(size_t)6 * st + 2 * ph + 1]));
+            KS_CUDA(cudaEventElapsedTime(&ms, ev[2 * ph], ev[2 * ph + 1]));
             out->ms[ph] += ms;
             out->launches[ph] += 1;
+        }
+        if (three_pass(c)) {
+            for (int ph = 0; ph < 2; ++ph) {
+                // pass boundaries: phase start, end of pass 1, end of pass 2, phase end
+                const cudaEvent_t b[4] = {ev[2 + 2 * ph], ev[6 + 2 * ph], ev[7 + 2 * ph], ev[3 + 2 * ph]};
+                for (int q = 0; q < 3; ++q) {
+                    float ms = 0.f;
+                    KS_CUDA(cudaEventElapsedTime(&ms, b[q], b[q + 1]));
+                    out->pass_ms[ph][q] += ms;
+                    out->pass_launches[ph][q] += 1;
+                }
+            }
         }
     }
     return KS_OK;

@@ -1172,7 +1172,7 @@ __global__ void k_f4_steptw(CurveDev c)
 
 // ---- launchers
 template <typename T, int F1, int F2>
-static cudaError_t f4_run(const CurveDev &c, int mode, int discrete, int gate, cudaStream_t st)
+static cudaError_t f4_run(const CurveDev &c, int mode, int discrete, int gate, cudaStream_t st, cudaEvent_t *pass_ev)
 {
     const int nm = c.nx / 2;
     const size_t sm1 = F4Stage<T, F1>::BYTES;
@@ -1182,18 +1182,21 @@ static cudaError_t f4_run(const CurveDev &c, int mode, int discrete, int gate, c
     if ((e = set_smem(k_f4_p3<T, F1, F2>, sm1)) != cudaSuccess) return e;
     if ((e = launch_pdl(k_f4_p1<T, F1, F2>, dim3(nmb, F2 / F4W), sm1, st, c, mode, discrete, gate)) != cudaSuccess)
         return e;
+    if (pass_ev && (e = cudaEventRecord(pass_ev[0], st)) != cudaSuccess) return e;
     if ((e = launch_pdl(k_f4_p2<T, F1, F2>, dim3(F1 / F4W, nm), 0, st, c, gate)) != cudaSuccess) return e;
+    if (pass_ev && (e = cudaEventRecord(pass_ev[1], st)) != cudaSuccess) return e;
     return launch_pdl(k_f4_p3<T, F1, F2>, dim3(nmb, F2 / F4W), sm1, st, c, mode, discrete, gate);
 }
 
 template <typename T>
-static cudaError_t f4_dispatch(const CurveDev &c, int mode, int discrete, int gate, cudaStream_t st)
+static cudaError_t f4_dispatch(const CurveDev &c, int mode, int discrete, int gate, cudaStream_t st,
+                               cudaEvent_t *pass_ev)
 {
-    if (c.F1 == 64 && c.F2 == 64) return f4_run<T, 64, 64>(c, mode, discrete, gate, st);
-    if (c.F1 == 128 && c.F2 == 64) return f4_run<T, 128, 64>(c, mode, discrete, gate, st);
-    if (c.F1 == 128 && c.F2 == 128) return f4_run<T, 128, 128>(c, mode, discrete, gate, st);
-    if (c.F1 == 256 && c.F2 == 128) return f4_run<T, 256, 128>(c, mode, discrete, gate, st);
-    if (c.F1 == 256 && c.F2 == 256) return f4_run<T, 256, 256>(c, mode, discrete, gate, st);
+    if (c.F1 == 64 && c.F2 == 64) return f4_run<T, 64, 64>(c, mode, discrete, gate, st, pass_ev);
+    if (c.F1 == 128 && c.F2 == 64) return f4_run<T, 128, 64>(c, mode, discrete, gate, st, pass_ev);
+    if (c.F1 == 128 && c.F2 == 128) return f4_run<T, 128, 128>(c, mode, discrete, gate, st, pass_ev);
+    if (c.F1 == 256 && c.F2 == 128) return f4_run<T, 256, 128>(c, mode, discrete, gate, st, pass_ev);
+    if (c.F1 == 256 && c.F2 == 256) return f4_run<T, 256, 256>(c, mode, discrete, gate, st, pass_ev);
     return cudaErrorInvalidValue;
 }
 
@@ -1242,7 +1245,7 @@ static cudaError_t f4c_dispatch(const CurveDev &c, int mode, int discrete, int g
     return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_f4(const CurveDev &c, int mode, int discrete, int gate, cudaStream_t st)
+cudaError_t launch_f4(const CurveDev &c, int mode, int discrete, int gate, cudaStream_t st, cudaEvent_t *pass_ev)
 {
     if (mode == GM_STEP && !c.f4c) return cudaErrorInvalidValue;
     if (c.f4c) {
@@ -1250,7 +1253,8 @@ cudaError_t launch_f4(const CurveDev &c, int mode, int discrete, int gate, cudaS
         return f4c_mpc(c.prec, c.nx, c.F1, c.F2) == 2 ? f4c_dispatch<float, 2>(c, mode, discrete, gate, st)
                                           : f4c_dispatch<float, 1>(c, mode, discrete, gate, st);
     }
-    return c.prec ? f4_dispatch<float>(c, mode, discrete, gate, st) : f4_dispatch<double>(c, mode, discrete, gate, st);
+    return c.prec ? f4_dispatch<float>(c, mode, discrete, gate, st, pass_ev)
+                  : f4_dispatch<double>(c, mode, discrete, gate, st, pass_ev);
 }
 
 // The one-CTA-per-mode form exists for the lengths a batched curve can have

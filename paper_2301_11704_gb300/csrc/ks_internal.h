@@ -255,7 +255,10 @@ cudaError_t launch_rows(const CurveDev &c, int mode, cudaStream_t st, StepArm ar
 // Structured contraction along s.  op 0: D_t (columns scaled by tau, rows by
 // sigma), op 1: W^-1 D_t^T W.  mode GM_STORE writes D_t U into D (gated when
 // `gate`), GM_UPDATE applies the descent update to U, GM_GRAD writes G.
-cudaError_t launch_dt(const CurveDev &c, int mode, int discrete, int gate, cudaStream_t st);
+// pass_ev (may be null): for the three-launch four-step form, two events
+// recorded on `st` after its first and second pass (per-pass timing).
+cudaError_t launch_dt(const CurveDev &c, int mode, int discrete, int gate, cudaStream_t st,
+                      cudaEvent_t *pass_ev = nullptr);
 // Tensor-core form of the dense contraction (ks_tc.cu; c.tc set): the same
 // modes and epilogue as the dense kernel.
 cudaError_t launch_dt_tc(const CurveDev &c, int mode, int discrete, int gate, cudaStream_t st);
@@ -263,7 +266,8 @@ cudaError_t launch_dt_tc(const CurveDev &c, int mode, int discrete, int gate, cu
 // Four-step FFT form (ks_fft4.cu; c.f4 set): set-up of the kernel spectrum and
 // the s-contraction in the modes of launch_dt.
 cudaError_t launch_setup_f4(const CurveDev &c, cudaStream_t st);
-cudaError_t launch_f4(const CurveDev &c, int mode, int discrete, int gate, cudaStream_t st);
+cudaError_t launch_f4(const CurveDev &c, int mode, int discrete, int gate, cudaStream_t st,
+                      cudaEvent_t *pass_ev = nullptr);
 // The one-CTA-per-mode four-step form: over the modes of one curve, or over the
 // (curve, mode) items of a batch whose curves share F.
 cudaError_t launch_f4b(const CurveDev &c, int mode, int discrete, int gate, cudaStream_t st);

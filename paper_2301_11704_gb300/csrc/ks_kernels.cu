@@ -1167,10 +1167,10 @@ cudaError_t launch_sconv_batch(int prec, int F_max, const CurveDev *cv, const in
     }
 }
 
-cudaError_t launch_dt(const CurveDev &c, int mode, int discrete, int gate, cudaStream_t st)
+cudaError_t launch_dt(const CurveDev &c, int mode, int discrete, int gate, cudaStream_t st, cudaEvent_t *pass_ev)
 {
     if (c.f4b) return launch_f4b(c, mode, discrete, gate, st);
-    if (c.f4) return launch_f4(c, mode, discrete, gate, st);
+    if (c.f4) return launch_f4(c, mode, discrete, gate, st, pass_ev);
     if (c.F > 0) return c.prec ? launch_sconv_t<float>(c, mode, discrete, gate, st)
                                : launch_sconv_t<double>(c, mode, discrete, gate, st);
     if (c.tc) return launch_dt_tc(c, mode, discrete, gate, st);

@@ -17,7 +17,6 @@
 // cleared before use), and calls that overlap on the GPU -- on two streams, or
 // from two threads -- race on it and give wrong results.
 #include <cmath>
-#include <mutex>
 
 #include "../../include/ksconn.h"
 #include "ks_internal.h"
@@ -26,18 +25,15 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[KS_NOALLOC_SCRA
 
 namespace {
 
-// Device address of g_noalloc_scratch per device.  In host code the symbol
-// name is only a host-side stand-in; the address the kernels need is looked
-// up once per device with that device current.
-constexpr int kMaxDevices = 64;
-std::mutex g_mu;
-void *g_addr[kMaxDevices] = {};
-
+// J^2 and J_arc of the evaluation, or NaN in both when a bounded device-side
+// wait of one of its kernels gave up (sc->err set): the launch's results are
+// then invalid, and the caller sees it in the outputs instead of a wrong cost.
 __global__ void k_export_cost(const ks::DevScalars *sc, double *out)
 {
     if (threadIdx.x == 0 && blockIdx.x == 0) {
-        out[0] = sc->J2;
-        out[1] = sc->Jarc;
+        const bool bad = sc->err != 0;
+        out[0] = bad ? __longlong_as_double(0x7ff8000000000000ll) : sc->J2;
+        out[1] = bad ? __longlong_as_double(0x7ff8000000000000ll) : sc->Jarc;
     }
 }
 
@@ -59,21 +55,15 @@ extern "C" ks_status ks_cost_noalloc(const ks_params *p, const void *u_dev, doub
         return ks::report_error(KS_ENOMEM,
                                 "ks_cost_noalloc: a %d x %d curve needs %zu bytes of scratch; the built-in array holds %zu",
                                 p->ns, p->nx, lay.total, (size_t)KS_NOALLOC_SCRATCH_BYTES);
-    int dev = -1;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return na_fail(KS_ECUDA, "cudaGetDevice", e);
-    if (dev < 0 || dev >= kMaxDevices) return ks::report_error(KS_EINVAL, "ks_cost_noalloc: device ordinal out of range");
+    // Device address of the scratch array, looked up on every call with the
+    // caller's device current.  In host code the array's name is only a host-side
+    // stand-in; the address belongs to the module loaded in the current context,
+    // and a cached one would go stale once that context is reset and the module
+    // loaded again (the lookup is cheap once the module is loaded).
     void *base = nullptr;
-    {
-        std::lock_guard<std::mutex> lk(g_mu);
-        if (!g_addr[dev]) {
-            void *ptr = nullptr;
-            e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
-            if (e != cudaSuccess || !ptr) return na_fail(KS_ECUDA, "cudaGetSymbolAddress", e);
-            g_addr[dev] = ptr;
-        }
-        base = g_addr[dev];
-    }
+    cudaError_t e = cudaGetSymbolAddress(&base, g_noalloc_scratch);
+    if (e != cudaSuccess) return na_fail(KS_ECUDA, "cudaGetSymbolAddress", e);
+    if (!base) return ks::report_error(KS_ECUDA, "ks_cost_noalloc: cudaGetSymbolAddress returned a null address");
 
     const ks::CurveDev d = ks::bind_layout(p, lay, base);
 

@@ -172,6 +172,13 @@ class KSCurve:
         out = {n: dict(ms=pr.ms[i], launches=pr.launches[i]) for i, n in enumerate(names) if pr.launches[i]}
         if pr.step_launches:
             out["step"] = dict(ms=pr.step_ms, launches=pr.step_launches, steps=pr.step_steps)
+        # three-launch four-step form: the passes of each contraction, timed one by one
+        passes = {}
+        for i, n in enumerate(("dt_update", "dt_store")):
+            if pr.pass_launches[i][0]:
+                passes[n] = [dict(ms=pr.pass_ms[i][q], launches=pr.pass_launches[i][q]) for q in range(3)]
+        if passes:
+            out["passes"] = passes
         return out
 
     def close(self):

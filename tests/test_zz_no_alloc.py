@@ -66,6 +66,28 @@ def test_noalloc_cost_matches_the_workspace_entry_points(precision, tol):
         c.close()
 
 
+def test_noalloc_call_allocates_no_device_memory():
+    """After a first (module-loading) call, further calls leave the device's free
+    memory unchanged: the entry point allocates nothing."""
+    lib = _native.load()
+    spec, c = _curve(1, "fp32")
+    u = c.get_state().clone()
+    out = torch.full((2,), float("nan"), dtype=torch.float64, device=u.device)
+    args = (ctypes.byref(c.params), ctypes.c_void_p(u.data_ptr()), ctypes.c_void_p(out.data_ptr()),
+            ctypes.c_void_p(c.stream.cuda_stream))
+    _native.check(lib.ks_cost_noalloc(*args))
+    c.stream.synchronize()
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    for _ in range(3):
+        _native.check(lib.ks_cost_noalloc(*args))
+    c.stream.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0, (free0, free1)
+    assert np.all(np.isfinite(out.cpu().numpy()))
+    c.close()
+
+
 def test_noalloc_rejects_curves_larger_than_its_scratch():
     lib = _native.load()
     p = _native.KSParams(L=100.0, nx=256, ns=16384, S=1638.3, s0=0.0, lam=1.0, lambda_free=0, dtau=0.01,
