@@ -25,7 +25,7 @@
  *    memory itself: every buffer it uses lives in the caller's workspace.
  *    Host pointers ("_host" or scalar outputs) are ordinary host memory.
  *  - Physical curve arrays are row-major [N_s][N] in the storage type of the
- *    curve (double for KS_FP64, float for KS_FP32); row m is section s_m,
+ *    curve (double for KS_FP64, float for the others); row m is section s_m,
  *    row 0 is s = +inf (u_+), row N_s-1 is s = -inf (u_-); column n is x_n = n L / N.
  *  - Work is issued on the caller's CUDA stream (cudaStream_t passed as void*;
  *    NULL = legacy default stream).  Functions that return host scalars
@@ -54,7 +54,19 @@ typedef enum {
     KS_ENOTIMPL = 8
 } ks_status;
 
-typedef enum { KS_FP64 = 0, KS_FP32 = 1 } ks_precision;
+/* Arithmetic of the curve's fields and transforms; J, J_arc, dJ^2/dlambda,
+ * |G|, the lambda update and the convergence test are FP64 in every precision.
+ * KS_FP64:   FP64 storage and transforms.
+ * KS_FP32:   FP32 storage, FP32 transforms (FFTs in x and s).
+ * KS_BF16X2, KS_BF16X3: FP32 storage; the x-transforms of every section (one
+ *            forward or backward DFT per section, Sec. V.C.1: four per row phase)
+ *            as dense products with the N x N DFT matrices on the tensor cores,
+ *            each FP32 operand split into two (BF16X2, about 2^-17 relative) or
+ *            three (BF16X3, about FP32 rounding) BF16 parts with FP32
+ *            accumulation; the s-transforms as in KS_FP32.  N must be 64, 128
+ *            or 256; single curves only (batches take KS_FP64 or KS_FP32); the
+ *            persistent launch form (launch = 1) does not apply. */
+typedef enum { KS_FP64 = 0, KS_FP32 = 1, KS_BF16X2 = 2, KS_BF16X3 = 3 } ks_precision;
 
 /* s-term of the adjoint (eq. KSE_G).
  * KS_ADJ_PAPER:    +lambda D_t r, the continuous adjoint discretised, as published.
@@ -340,6 +352,18 @@ ks_status ks_batch_destroy(ks_batch *b);
  * No device memory is allocated or freed. */
 #define KS_NOALLOC_SCRATCH_BYTES (32u << 20)
 ks_status ks_cost_noalloc(const ks_params *p, const void *u_dev, double *out_dev, void *stream);
+
+/* Test hook for the failure path of the device-side bounded waits; the paper has
+ * no counterpart.  The kernels that wait on an mbarrier (the split-BF16 row
+ * phase, the FFT form with one CTA per mode, the tensor-core contraction) spin
+ * at most `cycles` clock cycles in their first wait of a launch (0 restores the
+ * default, about 2^31 cycles; a negative value makes that wait give up at once).
+ * A wait that gives up sets the curve's error word, lets the copies and
+ * products already in flight finish (with the default bound), frees its tensor
+ * memory and returns; every later call that reads the curve's scalars returns
+ * KS_ETIMEOUT until ks_curve_init_trial re-initialises the curve (which also
+ * restores the default bound).  Asynchronous. */
+ks_status ks_curve_debug_wait_limit(ks_curve *c, int64_t cycles);
 
 /* Releases the handle (host memory only; the workspace stays the caller's). */
 ks_status ks_curve_destroy(ks_curve *c);

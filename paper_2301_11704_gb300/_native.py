@@ -13,7 +13,7 @@ from . import build as _build
 KS_OK, KS_EINVAL, KS_ENOMEM, KS_ECUDA, KS_ETIMEOUT, KS_ENONFINITE, KS_ENOTCONV, KS_ENOTEQUILIBRIUM, KS_ENOTIMPL = range(9)
 STATUS_NAMES = {0: "KS_OK", 1: "KS_EINVAL", 2: "KS_ENOMEM", 3: "KS_ECUDA", 4: "KS_ETIMEOUT",
                 5: "KS_ENONFINITE", 6: "KS_ENOTCONV", 7: "KS_ENOTEQUILIBRIUM", 8: "KS_ENOTIMPL"}
-KS_FP64, KS_FP32 = 0, 1
+KS_FP64, KS_FP32, KS_BF16X2, KS_BF16X3 = 0, 1, 2, 3
 KS_ADJ_PAPER, KS_ADJ_DISCRETE = 0, 1
 KS_CONV_JARC, KS_CONV_J, KS_CONV_JREL = 0, 1, 2
 
@@ -22,7 +22,7 @@ EXPORTS = [
     "ks_last_error", "ks_version", "ks_curve_workspace_bytes", "ks_curve_fft_length", "ks_curve_s_form", "ks_curve_create", "ks_curve_set_stream",
     "ks_curve_init_trial", "ks_curve_residual", "ks_curve_cost", "ks_curve_gradient", "ks_curve_descend",
     "ks_curve_descend_async", "ks_curve_scalars", "ks_curve_get_state", "ks_curve_set_state", "ks_curve_profile",
-    "ks_curve_profile_read", "ks_curve_destroy", "ks_cost_noalloc",
+    "ks_curve_profile_read", "ks_curve_debug_wait_limit", "ks_curve_destroy", "ks_cost_noalloc",
     "ks_batch_workspace_bytes", "ks_batch_create", "ks_batch_init_trial", "ks_batch_descend",
     "ks_batch_descend_async", "ks_batch_scalars", "ks_batch_get_state", "ks_batch_autotune", "ks_batch_destroy",
 ]
@@ -117,6 +117,7 @@ def load(build_if_missing: bool = True):
         "ks_curve_set_state": (i32, [p, p, d, d]),
         "ks_curve_profile": (i32, [p, i32]),
         "ks_curve_profile_read": (i32, [p, ctypes.POINTER(KSProfile)]),
+        "ks_curve_debug_wait_limit": (i32, [p, i64]),
         "ks_curve_destroy": (i32, [p]),
         "ks_cost_noalloc": (i32, [ctypes.POINTER(KSParams), p, p, p]),
         "ks_batch_workspace_bytes": (sz, [i32, ctypes.POINTER(KSParams)]),

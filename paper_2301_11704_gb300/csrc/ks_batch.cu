@@ -68,6 +68,8 @@ ks_status validate_batch(int nb, const ks_params *p)
         if (s != KS_OK) return s;
         if (p[i].precision != p[0].precision)
             return ks::report_error(KS_EINVAL, "all curves of a batch must have the same precision");
+        if (ks::xtc_of(p[i].precision))
+            return ks::report_error(KS_EINVAL, "batches run the FFT row phase: precision must be KS_FP64 or KS_FP32");
         if (p[i].adjoint != p[0].adjoint)
             return ks::report_error(KS_EINVAL, "all curves of a batch must have the same adjoint mode");
     }
@@ -245,7 +247,7 @@ size_t ks_batch_workspace_bytes(int32_t nb, const ks_params *params)
     header_sizes(nb, params, &cvb, &itb);
     size_t total = cvb + itb;
     for (int i = 0; i < nb; ++i)
-        total += ks::make_layout(params[i].ns, params[i].nx, params[i].precision == KS_FP32, 0, 0, params[i].s_transform).total;
+        total += ks::make_layout(params[i].ns, params[i].nx, ks::storage32(params[i].precision), 0, 0, params[i].s_transform).total;
     return total;
 }
 
@@ -264,7 +266,7 @@ ks_status ks_batch_create(int32_t nb, const ks_params *params, const double *u_p
     ks_batch *b = new (std::nothrow) ks_batch();
     if (!b) return ks::report_error(KS_ENOMEM, "host allocation of the batch handle failed");
     b->nb = nb;
-    b->prec = params[0].precision == KS_FP32 ? 1 : 0;
+    b->prec = ks::storage32(params[0].precision);
     b->discrete = params[0].adjoint == KS_ADJ_DISCRETE;
     b->st = (cudaStream_t)stream;
     cudaGetDevice(&b->device);

@@ -84,26 +84,29 @@ ks_status validate(const ks_params *p)
     if (!(p->dtau > 0) || !std::isfinite(p->dtau)) return fail(KS_EINVAL, "dtau must be finite and > 0 (got %g)", p->dtau);
     if (!(p->dtau_lambda >= 0) || !std::isfinite(p->dtau_lambda)) return fail(KS_EINVAL, "dtau_lambda must be finite and >= 0");
     if (p->lambda_free != 0 && p->lambda_free != 1) return fail(KS_EINVAL, "lambda_free must be 0 or 1");
-    if (p->precision != KS_FP64 && p->precision != KS_FP32) return fail(KS_EINVAL, "precision must be KS_FP64 or KS_FP32");
+    if (p->precision < KS_FP64 || p->precision > KS_BF16X3)
+        return fail(KS_EINVAL, "precision must be KS_FP64, KS_FP32, KS_BF16X2 or KS_BF16X3");
+    if (ks::xtc_of(p->precision) && p->nx != 64 && p->nx != 128 && p->nx != 256)
+        return fail(KS_EINVAL, "split-BF16 x-transforms need nx in {64, 128, 256} (got %d)", p->nx);
     if (p->adjoint != KS_ADJ_PAPER && p->adjoint != KS_ADJ_DISCRETE) return fail(KS_EINVAL, "adjoint must be KS_ADJ_PAPER or KS_ADJ_DISCRETE");
     if (p->conv < KS_CONV_JARC || p->conv > KS_CONV_JREL) return fail(KS_EINVAL, "conv must be a ks_conv value");
     if (p->check_ends != 0 && p->check_ends != 1) return fail(KS_EINVAL, "check_ends must be 0 or 1");
     if (p->symmetry < 0 || p->symmetry > 3) return fail(KS_EINVAL, "symmetry must be in [0, 3]");
     if (p->s_transform < 0 || p->s_transform > 5) return fail(KS_EINVAL, "s_transform must be in [0, 5]");
-    if ((p->s_transform == 4 || p->s_transform == 5) && ks::fft4_size(p->ns, p->precision == KS_FP32, 1) == 0)
+    if ((p->s_transform == 4 || p->s_transform == 5) && ks::fft4_size(p->ns, ks::storage32(p->precision), 1) == 0)
         return fail(KS_EINVAL, "s_transform = four-step FFT needs %d <= 3 (N_s - 1) <= %d (rounded up to a power of two)",
                     ks::F4_FMIN / 2 + 1, ks::F4_FMAX);
     if (p->s_transform == 5) {
         int F1 = 0, F2 = 0;
-        ks::f4_split(ks::fft4_size(p->ns, p->precision == KS_FP32, 1), F1, F2);
-        if (!ks::f4c_fits(p->precision == KS_FP32, F1, F2))
+        ks::f4_split(ks::fft4_size(p->ns, ks::storage32(p->precision), 1), F1, F2);
+        if (!ks::f4c_fits(ks::storage32(p->precision), F1, F2))
             return fail(KS_EINVAL, "s_transform = clustered four-step FFT holds F <= 32768 in FP64 (N_s <= 10923)");
     }
-    if (p->s_transform == 3 && p->precision != KS_FP32)
+    if (p->s_transform == 3 && !ks::storage32(p->precision))
         return fail(KS_EINVAL, "s_transform = tensor cores needs FP32 storage");
     if (p->launch < 0 || p->launch > 1) return fail(KS_EINVAL, "launch must be 0 or 1");
-    if (p->s_transform == 2 && ks::fft_size(p->ns, p->precision == KS_FP32) == 0 &&
-        ks::fft4_size(p->ns, p->precision == KS_FP32) == 0)
+    if (p->s_transform == 2 && ks::fft_size(p->ns, ks::storage32(p->precision)) == 0 &&
+        ks::fft4_size(p->ns, ks::storage32(p->precision)) == 0)
         return fail(KS_EINVAL, "s_transform = FFT supports N_s <= %d", ks::F4_FMAX / 3 + 1);
     return KS_OK;
 }
@@ -273,19 +276,19 @@ int32_t ks_version(void) { return (1 << 16) | 0; }
 size_t ks_curve_workspace_bytes(const ks_params *p)
 {
     if (validate(p) != KS_OK) return 0;
-    return ks::make_layout(p->ns, p->nx, p->precision == KS_FP32, 1, 0, p->s_transform, p->launch == 1).total;
+    return ks::curve_layout(p, p->launch == 1).total;
 }
 
 int32_t ks_curve_fft_length(const ks_params *p)
 {
     if (validate(p) != KS_OK) return -1;
-    return ks::make_layout(p->ns, p->nx, p->precision == KS_FP32, 1, 0, p->s_transform).F;
+    return ks::curve_layout(p, 0).F;
 }
 
 int32_t ks_curve_s_form(const ks_params *p)
 {
     if (validate(p) != KS_OK) return -1;
-    const ks::Layout l = ks::make_layout(p->ns, p->nx, p->precision == KS_FP32, 1, 0, p->s_transform);
+    const ks::Layout l = ks::curve_layout(p, 0);
     if (l.f4) return l.f4c ? 5 : 4;
     if (l.F) return 2;
     return l.tc ? 3 : 1;
@@ -306,7 +309,7 @@ ks_status ks_curve_create(const ks_params *p, const double *u_plus_host, const d
     for (int n = 0; n < p->nx; ++n)
         if (!std::isfinite(u_plus_host[n]) || !std::isfinite(u_minus_host[n]))
             return fail(KS_EINVAL, "u_plus/u_minus contain non-finite values");
-    ks::Layout lay = ks::make_layout(p->ns, p->nx, p->precision == KS_FP32, 1, 0, p->s_transform, p->launch == 1);
+    ks::Layout lay = ks::curve_layout(p, p->launch == 1);
     if (workspace_bytes < lay.total)
         return fail(KS_ENOMEM, "workspace has %zu bytes, %zu needed", workspace_bytes, lay.total);
 
@@ -603,6 +606,16 @@ ks_status ks_curve_profile_read(ks_curve *c, ks_profile *out)
             }
         }
     }
+    return KS_OK;
+}
+
+ks_status ks_curve_debug_wait_limit(ks_curve *c, int64_t cycles)
+{
+    ks_status s = check_handle(c);
+    if (s != KS_OK) return s;
+    DeviceGuard g(c->device);
+    if (!g.ok) return fail(KS_ECUDA, "cannot select the curve's device");
+    KS_CUDA(ks::launch_set_wait_cycles(c->d, (long long)cycles, c->st));
     return KS_OK;
 }
 

@@ -308,7 +308,10 @@ __global__ void __launch_bounds__(F4_THREADS) k_f4_p1(CurveDev c, int mode, int 
             const int k = F2 * (threadIdx.x / F4W + 32 * (i0 + h)) + n2_0 + tn;
             int m = -1;
             T f = T(1);
-            if (k == 0) { m = 0; f = T(1) + s; }
+            if (c.f4h) {   // Toeplitz-Hankel form: the column itself, z[k] = x_k for k <= P
+                if (k <= P) m = k;
+            }
+            else if (k == 0) { m = 0; f = T(1) + s; }
             else if (k < P) { m = k; f = s; }
             else if (k == P) { m = P; f = T(1) + s; }
             else if (k < 2 * P) { m = 2 * P - k; }
@@ -379,6 +382,98 @@ __global__ void __launch_bounds__(F4_THREADS) k_f4_p2(CurveDev c, int gate)
     reg_fft_inv<T, R>(v, twl, w32, lane);
 #pragma unroll
     for (int a = 0; a < R; ++a) S[lane + 32 * a] = cmul(v[a], cconj(t2[lane + 32 * a]));   // W_F^(-n2 k1)
+}
+
+// ---- pass 2 of the Toeplitz-Hankel form (c.f4h): D_t = sigma (H + s T) with
+// H_jm = cot[(j + m) mod 2P], T_jm = cot[(j - m) mod 2P], applied to the column
+// z (z_m, m <= P) as
+//   y = IFFT(s T^ Z + H^ Z(-k)),   T^ = FFT(cot at lags [-P, P]) / F,
+//                                  H^ = FFT(cot at lags [0, 2P]) / F,
+// where Z(-k) = FFT of z reversed: index -k of the same transform.  With
+// k = k1 + F1 k2, -k is row F1 - k1 at k2' = F2 - 1 - k2 (k1 > 0) or row 0 at
+// (F2 - k2) mod F2 (k1 = 0).  A warp takes rows k1 and F1 - k1 together (rows 0
+// and F1/2 alone): FFT over n2 of both, the products, IFFT, W_F^(-n2 k1).  In
+// the transforms' scrambled order (k2 = a + R brev5(l) in register a of lane l)
+// the partner of (a, l) is (R - 1 - a, 31 - l): a register reversal and a
+// shuffle across 31 lanes; in row 0, (R - a, 31 - l) for a > 0 and lane
+// brev5(32 - brev5(l)) for a = 0.
+template <typename T, int F1, int F2>
+__global__ void __launch_bounds__(F4_THREADS) k_f4h_p2(CurveDev c, int discrete, int gate)
+{
+    constexpr int R = F2 / 32, R1 = F1 / 32, NIT = F1 / 2 + 1;
+    static_assert(R >= 2, "lines of at least 64 points");
+    __shared__ cpx<T> twl[F2], w32[16];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, jm = blockIdx.y, F = F1 * F2;
+    const int it = blockIdx.x * F4W + warp;
+    const bool valid = it < NIT, pair = it > 0 && it < F1 / 2;
+    const int ka = it, kb = F1 - it;
+    const int ra = valid ? (ka % R1) * 32 + brev5(ka / R1) : 0, rb = pair ? (kb % R1) * 32 + brev5(kb / R1) : 0;
+    const cpx<T> *ftw = (const cpx<T> *)c.ftw, *chat = (const cpx<T> *)c.chat;
+    load_line_twiddles<T, F2>(twl, w32, ftw, F);
+    // the spectra (set-up tables) before the programmatic wait; in FP64 those of
+    // the second row only where they are used (register pressure)
+    constexpr bool early_b = sizeof(T) == 4;
+    cpx<T> ta[R], ha[R], tb[R], hb[R];
+    auto load_spec = [&](int r, cpx<T> (&t)[R], cpx<T> (&h)[R]) {
+#pragma unroll
+        for (int a = 0; a < R; ++a) {
+            t[a] = chat[(size_t)r * F2 + a * 32 + lane];
+            h[a] = chat[F + (size_t)r * F2 + a * 32 + lane];
+        }
+    };
+    if (valid) load_spec(ra, ta, ha);
+    if (early_b && pair) load_spec(rb, tb, hb);
+    pdl_wait();
+    if (gate && !c.sc->active) return;
+    const T sg = discrete ? T(-1) : T(1);
+    cpx<T> *Sa = (cpx<T> *)c.f4s + (size_t)jm * F + (size_t)ra * F2, *Sb = (cpx<T> *)c.f4s + (size_t)jm * F + (size_t)rb * F2;
+    cpx<T> va[R], vb[R];
+    if (valid) {
+#pragma unroll
+        for (int a = 0; a < R; ++a) {
+            va[a] = Sa[lane + 32 * a];
+            if (pair) vb[a] = Sb[lane + 32 * a];
+        }
+    }
+    __syncthreads();   // twiddles
+    if (!valid) return;
+    reg_fft_fwd<T, R>(va, twl, w32, lane);
+    if (pair) reg_fft_fwd<T, R>(vb, twl, w32, lane);
+    cpx<T> pa[R], pb[R];   // Z(-k) at each position of rows a and b
+    if (pair) {
+#pragma unroll
+        for (int a = 0; a < R; ++a) {
+            pa[a] = cshfl(vb[R - 1 - a], 31);
+            pb[a] = cshfl(va[R - 1 - a], 31);
+        }
+    } else if (ka == F1 / 2) {
+#pragma unroll
+        for (int a = 0; a < R; ++a) pa[a] = cshfl(va[R - 1 - a], 31);
+    } else {   // row 0
+        const int src = brev5((32 - brev5(lane)) & 31);
+        pa[0] = {__shfl_sync(0xffffffffu, va[0].x, src), __shfl_sync(0xffffffffu, va[0].y, src)};
+#pragma unroll
+        for (int a = 1; a < R; ++a) pa[a] = cshfl(va[R - a], 31);
+    }
+    const cpx<T> *t2a = ftw + 2 * (size_t)F + (size_t)ra * F2, *t2b = ftw + 2 * (size_t)F + (size_t)rb * F2;
+#pragma unroll
+    for (int a = 0; a < R; ++a) {
+        const cpx<T> y = cmul(ta[a], va[a]);
+        va[a] = cadd(cpx<T>{sg * y.x, sg * y.y}, cmul(ha[a], pa[a]));
+    }
+    reg_fft_inv<T, R>(va, twl, w32, lane);
+#pragma unroll
+    for (int a = 0; a < R; ++a) Sa[lane + 32 * a] = cmul(va[a], cconj(t2a[lane + 32 * a]));
+    if (!pair) return;
+    if (!early_b) load_spec(rb, tb, hb);
+#pragma unroll
+    for (int a = 0; a < R; ++a) {
+        const cpx<T> y = cmul(tb[a], vb[a]);
+        vb[a] = cadd(cpx<T>{sg * y.x, sg * y.y}, cmul(hb[a], pb[a]));
+    }
+    reg_fft_inv<T, R>(vb, twl, w32, lane);
+#pragma unroll
+    for (int a = 0; a < R; ++a) Sb[lane + 32 * a] = cmul(vb[a], cconj(t2b[lane + 32 * a]));
 }
 
 // ---- pass 3: lines over k1 (length F1), one per (n2, mode): IFFT and the epilogue
@@ -947,7 +1042,10 @@ __device__ __forceinline__ void f4b_body(const CurveDev &c, int mode, int discre
             const int k = F2 * (lane + 32 * a) + n2;
             int m = -1;
             T f = T(1);
-            if (k == 0) { m = 0; f = T(1) + s; }
+            if (c.f4h) {   // Toeplitz-Hankel form: the column itself
+                if (k <= P) m = k;
+            }
+            else if (k == 0) { m = 0; f = T(1) + s; }
             else if (k < P) { m = k; f = s; }
             else if (k == P) { m = P; f = T(1) + s; }
             else if (k < 2 * P) { m = 2 * P - k; }
@@ -969,8 +1067,56 @@ __device__ __forceinline__ void f4b_body(const CurveDev &c, int mode, int discre
     }
     __syncthreads();
 
+    // pass 2 of the Toeplitz-Hankel form: rows k1 and F1 - k1 together (0 and F1/2
+    // alone), as in k_f4h_p2 but on the shared array
+    if (c.f4h) {
+        for (int it = warp; it <= F1 / 2; it += F4W) {
+            const bool pair = it > 0 && it < F1 / 2;
+            const int ka = it, kb = F1 - it;
+            const int ra = (ka % R1) * 32 + brev5(ka / R1), rb = pair ? (kb % R1) * 32 + brev5(kb / R1) : 0;
+            cpx<T> *rowa = B + (size_t)ra * BS, *rowb = B + (size_t)rb * BS;
+            cpx<T> va[R2], vb[R2], pa[R2], pb[R2];
+#pragma unroll
+            for (int a = 0; a < R2; ++a) {
+                va[a] = rowa[lane + 32 * a];
+                if (pair) vb[a] = rowb[lane + 32 * a];
+            }
+            reg_fft_fwd<T, R2>(va, tw2, w32, lane);
+            if (pair) reg_fft_fwd<T, R2>(vb, tw2, w32, lane);
+            if (pair) {
+#pragma unroll
+                for (int a = 0; a < R2; ++a) {
+                    pa[a] = cshfl(vb[R2 - 1 - a], 31);
+                    pb[a] = cshfl(va[R2 - 1 - a], 31);
+                }
+            } else if (ka == F1 / 2) {
+#pragma unroll
+                for (int a = 0; a < R2; ++a) pa[a] = cshfl(va[R2 - 1 - a], 31);
+            } else {   // row 0
+                const int src = brev5((32 - brev5(lane)) & 31);
+                pa[0] = {__shfl_sync(0xffffffffu, va[0].x, src), __shfl_sync(0xffffffffu, va[0].y, src)};
+#pragma unroll
+                for (int a = 1; a < R2; ++a) pa[a] = cshfl(va[R2 - a], 31);
+            }
+            // Y = s T^ Z + H^ Z(-k), IFFT, W_F^(-n2 k1), back into the row
+            auto finish = [&](int r, cpx<T> *row, cpx<T> (&v)[R2], const cpx<T> (&p)[R2]) {
+                const cpx<T> *ct = chat + (size_t)r * F2, *chh = chat + F + (size_t)r * F2;
+                const cpx<T> *t2 = ftw + 2 * (size_t)F + (size_t)r * F2;
+#pragma unroll
+                for (int a = 0; a < R2; ++a) {
+                    const cpx<T> y = cmul(ct[32 * a + lane], v[a]);
+                    v[a] = cadd(cpx<T>{s * y.x, s * y.y}, cmul(chh[32 * a + lane], p[a]));
+                }
+                reg_fft_inv<T, R2>(v, tw2, w32, lane);
+#pragma unroll
+                for (int a = 0; a < R2; ++a) row[lane + 32 * a] = cmul(v[a], cconj(t2[lane + 32 * a]));
+            };
+            finish(ra, rowa, va, pa);
+            if (pair) finish(rb, rowb, vb, pb);
+        }
+    }
     // pass 2: rows r: FFT over n2, kernel spectrum, IFFT, times W_F^(-n2 k1), in place
-    for (int r = warp; r < F1; r += F4W) {
+    for (int r = warp; r < F1 && !c.f4h; r += F4W) {
         cpx<T> *row = B + (size_t)r * BS;
         const cpx<T> *ch = chat + (size_t)r * F2, *t2 = ftw + 2 * (size_t)F + (size_t)r * F2;
         cpx<T> v[R2], chv[R2], t2v[R2];
@@ -1092,6 +1238,24 @@ __device__ __forceinline__ double cot_kernel(int n, int F, int P)
     return cs / sn;
 }
 
+// the Toeplitz-Hankel form's two sequences (kind 1: cot at lags [-P, P], lag l
+// at n = l mod F; kind 2: cot at lags [0, 2P]); kind 0 the extended one above
+__device__ __forceinline__ double th_kernel(int n, int F, int P, int kind)
+{
+    if (kind == 0) return cot_kernel(n, F, P);
+    int u = -1;
+    if (kind == 1) {
+        if (n <= P) u = n;
+        else if (n >= F - P) u = n - F + 2 * P;
+    } else if (n <= 2 * P) {
+        u = n == 2 * P ? 0 : n;
+    }
+    if (u <= 0) return 0.0;
+    double sn, cs;
+    sincospi((double)u / (double)(2 * P), &sn, &cs);
+    return cs / sn;
+}
+
 __global__ void k_f4_twiddles(CurveDev c)
 {
     const int F = c.F;
@@ -1105,7 +1269,7 @@ __global__ void k_f4_twiddles(CurveDev c)
 
 // pass A (per n2): FFT over n1 of c_F[F2 n1 + n2], times W_F^(n2 k1) -> S64[k1][n2]
 template <int F1, int F2>
-__global__ void __launch_bounds__(F4_THREADS) k_f4_specA(CurveDev c)
+__global__ void __launch_bounds__(F4_THREADS) k_f4_specA(CurveDev c, int kind)
 {
     using Sm = F4Smem<double, F1, F1>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -1116,7 +1280,7 @@ __global__ void __launch_bounds__(F4_THREADS) k_f4_specA(CurveDev c)
     cpx<double> *S = (cpx<double> *)c.f4s + F;
     for (int t = threadIdx.x; t < F1 / 2; t += F4_THREADS) tw[t] = w64[t * F2];
     cpx<double> *x = buf + (size_t)warp * 2 * F1, *y = x + F1;
-    for (int n1 = lane; n1 < F1; n1 += 32) x[n1] = {cot_kernel(F2 * n1 + n2, F, c.P), 0.0};
+    for (int n1 = lane; n1 < F1; n1 += 32) x[n1] = {th_kernel(F2 * n1 + n2, F, c.P, kind), 0.0};
     __syncthreads();
     cpx<double> *Y = warp_fft<double, F1>(x, y, tw, false, lane);
     for (int k1 = lane; k1 < F1; k1 += 32) stage[(size_t)warp * (F1 + 1) + k1] = cmul(Y[k1], w64[n2 * k1]);
@@ -1130,7 +1294,7 @@ __global__ void __launch_bounds__(F4_THREADS) k_f4_specA(CurveDev c)
 // pass B (per k1): FFT over n2 -> spectrum / F in the storage type, both indices
 // in the scrambled order of the passes; the plain twiddle table W_F^p
 template <typename T, int F1, int F2>
-__global__ void __launch_bounds__(F4_THREADS) k_f4_specB(CurveDev c)
+__global__ void __launch_bounds__(F4_THREADS) k_f4_specB(CurveDev c, int half)
 {
     using Sm = F4Smem<double, F2, F2>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -1145,7 +1309,8 @@ __global__ void __launch_bounds__(F4_THREADS) k_f4_specB(CurveDev c)
     __syncthreads();
     cpx<double> *Z = warp_fft<double, F2>(x, y, tw, false, lane);
     constexpr int R1 = F1 / 32, R2 = F2 / 32;
-    cpx<T> *chat = (cpx<T> *)c.chat + (size_t)((k1 % R1) * 32 + brev5(k1 / R1)) * F2, *ftw = (cpx<T> *)c.ftw;
+    cpx<T> *chat = (cpx<T> *)c.chat + (size_t)half * F + (size_t)((k1 % R1) * 32 + brev5(k1 / R1)) * F2;
+    cpx<T> *ftw = (cpx<T> *)c.ftw;
     for (int k2 = lane; k2 < F2; k2 += 32)
         chat[(k2 % R2) * 32 + brev5(k2 / R2)] = {(T)(Z[k2].x / F), (T)(Z[k2].y / F)};
     for (int p = k1 * F2 + lane; p < (k1 + 1) * F2; p += 32) ftw[p] = {(T)w64[p].x, (T)w64[p].y};
@@ -1183,7 +1348,9 @@ static cudaError_t f4_run(const CurveDev &c, int mode, int discrete, int gate, c
     if ((e = launch_pdl(k_f4_p1<T, F1, F2>, dim3(nmb, F2 / F4W), sm1, st, c, mode, discrete, gate)) != cudaSuccess)
         return e;
     if (pass_ev && (e = cudaEventRecord(pass_ev[0], st)) != cudaSuccess) return e;
-    if ((e = launch_pdl(k_f4_p2<T, F1, F2>, dim3(F1 / F4W, nm), 0, st, c, gate)) != cudaSuccess) return e;
+    if (c.f4h) e = launch_pdl(k_f4h_p2<T, F1, F2>, dim3((F1 / 2 + 1 + F4W - 1) / F4W, nm), 0, st, c, discrete, gate);
+    else e = launch_pdl(k_f4_p2<T, F1, F2>, dim3(F1 / F4W, nm), 0, st, c, gate);
+    if (e != cudaSuccess) return e;
     if (pass_ev && (e = cudaEventRecord(pass_ev[1], st)) != cudaSuccess) return e;
     return launch_pdl(k_f4_p3<T, F1, F2>, dim3(nmb, F2 / F4W), sm1, st, c, mode, discrete, gate);
 }
@@ -1316,8 +1483,11 @@ static cudaError_t setup_run(const CurveDev &c, cudaStream_t st)
     if ((e = set_smem(k_f4_specA<F1, F2>, smA)) != cudaSuccess) return e;
     if ((e = set_smem(k_f4_specB<T, F1, F2>, smB)) != cudaSuccess) return e;
     k_f4_twiddles<<<(c.F + 255) / 256, 256, 0, st>>>(c);
-    k_f4_specA<F1, F2><<<F2 / F4W, F4_THREADS, smA, st>>>(c);
-    k_f4_specB<T, F1, F2><<<F1 / F4W, F4_THREADS, smB, st>>>(c);
+    // one spectrum (the extended sequence), or the Toeplitz then the Hankel one
+    for (int half = 0; half < (c.f4h ? 2 : 1); ++half) {
+        k_f4_specA<F1, F2><<<F2 / F4W, F4_THREADS, smA, st>>>(c, c.f4h ? 1 + half : 0);
+        k_f4_specB<T, F1, F2><<<F1 / F4W, F4_THREADS, smB, st>>>(c, half);
+    }
     k_f4_steptw<T, F1, F2><<<(c.F + 255) / 256, 256, 0, st>>>(c);
     return cudaGetLastError();
 }

@@ -92,6 +92,19 @@ inline int fft4_size(int ns, int prec, int any = 0)
     return (F >= lo && F <= F4_FMAX) ? F : 0;
 }
 
+// Length of the three-launch four-step form for a single curve.  D_t is applied
+// there as two convolutions of the column z_m (m <= P, not its symmetric
+// extension): a Toeplitz part with lags in [-P, P] and a Hankel part with lags
+// in [0, 2P], so a power of two F >= 2P + 1 suffices (F >= 3P for the extended
+// sequence of the other FFT forms): F in [fmin, F4_FMAX], 0 outside.  The
+// batched one-CTA-per-mode variant uses the same split from F4B_FMIN on.
+inline int fft4h_size(int ns, int fmin = F4_FMIN)
+{
+    int F = fmin;
+    while (F < 2 * (ns - 1) + 1) F <<= 1;
+    return F <= F4_FMAX ? F : 0;
+}
+
 // Form of the s-contraction: dense, FFT with one CTA per mode, four-step FFT in
 // three launches, four-step FFT in one clustered launch.
 enum SForm { SF_DENSE = 0, SF_FFT1 = 1, SF_FFT4 = 2, SF_FFT4C = 3 };
@@ -128,6 +141,11 @@ inline bool tc_preferred(int ns, int nx)
     return nx >= 32 && (ns >= 8192 || (nx >= 128 && ns >= 4096));
 }
 
+// Storage in FP32 (KS_FP32 and the split-BF16 forms) rather than FP64.
+inline int storage32(int precision) { return precision != KS_FP64 ? 1 : 0; }
+// Parts of the split-BF16 x-transforms on the tensor cores (0: FFT row phase).
+inline int xtc_of(int precision) { return precision == KS_BF16X3 ? 3 : (precision == KS_BF16X2 ? 2 : 0); }
+
 // Sections handled per CTA by the row (x-direction) kernels: two rows per warp,
 // packed into one complex FFT.
 constexpr int ROWS_WARPS = 4;
@@ -154,9 +172,16 @@ struct DevScalars {
     int done, active, status, conv;
     int lambda_free;
     int err;                            // nonzero: a bounded wait in a kernel gave up (launch invalid)
+    long long wait_cycles;              // bound of the first mbarrier wait of a kernel (0: about 2^31
+                                        // cycles; < 0: give up at once, a test of the error path)
     unsigned int cnt_rows, cnt_gemm;    // arrival counters of the last-CTA reductions
     unsigned long long bar;             // arrivals at the persistent step's grid barriers
 };
+
+// Cycles a kernel's first bounded wait may spin for this curve (the waits that
+// follow a failed one, which wait for copies still in flight, keep the full bound).
+constexpr long long WAIT_CYCLES = 1ll << 31;
+__host__ __device__ inline long long wait_bound(const DevScalars &s) { return s.wait_cycles ? s.wait_cycles : WAIT_CYCLES; }
 
 // Gates of the kernels of one descent step:
 //   rows kernel:   skip when done or step >= limit (clears `active`)
@@ -181,6 +206,9 @@ struct Layout {
     int f4, F1, F2;                    // four-step FFT form (f4 = 1): F = F1 F2
     int f4c;                           // its clustered one-launch variant: cluster size (0: three passes)
     int f4b;                           // its one-CTA-per-mode variant (batched curves; F1 F2 in shared memory)
+    int f4h;                           // the three-launch form on the Toeplitz and Hankel parts (F >= 2P + 1)
+    int xtc;                           // split-BF16 tensor-core row phase: parts per operand (0: FFT row phase)
+    size_t off_xdft;                   // its DFT matrices, split into BF16 parts
 };
 
 struct CurveDev {
@@ -200,6 +228,10 @@ struct CurveDev {
     int f4, F1, F2;                    // four-step FFT form (f4 = 1): F = F1 F2
     int f4c;                           // its clustered one-launch variant: cluster size (0: three passes)
     int f4b;                           // its one-CTA-per-mode variant (batched curves; F1 F2 in shared memory)
+    int f4h;                           // the three-launch form on the Toeplitz and Hankel parts: the
+                                       // spectra of both ([k1][k2] each, Toeplitz first) in chat
+    int xtc;               // split-BF16 tensor-core row phase: parts per operand (2 or 3; 0: FFT row phase)
+    void *xdft;            // its DFT matrices C (inverse) and E (forward), three BF16 parts, operand layout
     int F;                 // FFT length of the s-contraction (0: dense form)
     void *chat, *ftw;      // FFT form: kernel spectrum / F and twiddles (complex, storage type);
                            // four-step form: spectrum stored [k1][k2] for k = k1 + F1 k2 (both
@@ -215,7 +247,14 @@ struct CurveDev {
 // allow_split = 0 lays a curve out without split contractions (batched curves
 // get their parallelism from the batch); bn = 0 picks the column tile width.
 Layout make_layout(int ns, int nx, int prec, int allow_split = 1, int bn = 0, int s_transform = 0,
-                   int persistent = 0);
+                   int persistent = 0, int xtc = 0);
+// Layout of a single curve with parameters p (persistent: room for the
+// persistent step's partials when p asks for that launch form).
+inline Layout curve_layout(const ks_params *p, int persistent)
+{
+    const int xtc = xtc_of(p->precision);   // the persistent step has its own (FFT) row phase
+    return make_layout(p->ns, p->nx, storage32(p->precision), 1, 0, p->s_transform, persistent && !xtc, xtc);
+}
 // Pointers of a curve whose workspace starts at `base` (256-byte aligned).
 CurveDev bind_layout(const ks_params *p, const Layout &l, void *base);
 
@@ -231,6 +270,7 @@ cudaError_t launch_scalars_init(const CurveDev &c, double lambda, int lambda_fre
                                 double dtau_lambda, int conv, cudaStream_t st);
 cudaError_t launch_set_limit(const CurveDev &c, long long nsteps, double tol, cudaStream_t st);
 cudaError_t launch_set_lambda_tau(const CurveDev &c, double lambda, double tau, cudaStream_t st);
+cudaError_t launch_set_wait_cycles(const CurveDev &c, long long cycles, cudaStream_t st);
 // Trial curve (eq. KSE_initial_curve) into the FP64 scratch X.
 cudaError_t launch_trial(const CurveDev &c, double a, int has_v, int npert, cudaStream_t st);
 // X = (double) in  (a physical curve in the storage type)
@@ -273,6 +313,12 @@ cudaError_t launch_f4(const CurveDev &c, int mode, int discrete, int gate, cudaS
 cudaError_t launch_f4b(const CurveDev &c, int mode, int discrete, int gate, cudaStream_t st);
 cudaError_t launch_f4b_batch(int prec, int F, const CurveDev *cv, const int2 *items, int nitems, int mode,
                              int discrete, int gate, cudaStream_t st);
+
+// Split-BF16 tensor-core row phase (ks_rows_tc.cu; c.xtc set): bytes of its DFT
+// matrices, their set-up, and the row phase with the modes of launch_rows.
+size_t xdft_bytes(int nx);
+cudaError_t launch_setup_xdft(const CurveDev &c, cudaStream_t st);
+cudaError_t launch_rows_tc(const CurveDev &c, int mode, cudaStream_t st, StepArm arm);
 
 // Persistent step (ks_step.cu): nsteps descent steps of a dense-form curve
 // (c.part set) in one cooperative launch; stops early with the curve's gates.

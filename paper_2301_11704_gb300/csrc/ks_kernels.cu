@@ -37,7 +37,7 @@ namespace ks {
 // ---------------------------------------------------------------------------
 static size_t al256(size_t x) { return (x + 255) & ~size_t(255); }
 
-Layout make_layout(int ns, int nx, int prec, int allow_split, int bn, int s_transform, int persistent)
+Layout make_layout(int ns, int nx, int prec, int allow_split, int bn, int s_transform, int persistent, int xtc)
 {
     Layout l{};
     size_t b = prec ? 4 : 8;
@@ -59,9 +59,13 @@ Layout make_layout(int ns, int nx, int prec, int allow_split, int bn, int s_tran
     else if (s_transform == 4) form = fft4_size(ns, prec, 1) ? SF_FFT4 : SF_DENSE;
     else if (s_transform == 5) form = fft4_size(ns, prec, 1) ? SF_FFT4C : SF_DENSE;
     if (form == SF_FFT1) l.F = fft_size(ns, prec);
+    // the three-launch form of a single curve and the batched one-CTA-per-mode
+    // form: Toeplitz and Hankel parts, F >= 2P + 1
+    const bool f4h = form == SF_FFT4 && fft4h_size(ns, batched_f4 ? F4B_FMIN : F4_FMIN) > 0;
     if (form == SF_FFT4 || form == SF_FFT4C) {   // the four-step form
-        l.F = batched_f4 ? fft_size(ns, prec) : fft4_size(ns, prec, 1);
+        l.F = f4h ? fft4h_size(ns, batched_f4 ? F4B_FMIN : F4_FMIN) : fft4_size(ns, prec, 1);
         l.f4 = 1;
+        l.f4h = f4h ? 1 : 0;
         f4_split(l.F, l.F1, l.F2);
         l.f4c = (form == SF_FFT4C && f4c_fits(prec, l.F1, l.F2)) ? F4C_CS : 0;
         l.f4b = batched_f4 ? 1 : 0;
@@ -134,11 +138,14 @@ Layout make_layout(int ns, int nx, int prec, int allow_split, int bn, int s_tran
     l.off_ends = off; off += al256((size_t)2 * nx * 8);
     l.off_pert = off; off += al256((size_t)(nx + MAX_PERT + MAX_PERT * nx) * 8);
     l.off_sc = off; off += al256(sizeof(DevScalars));
-    l.off_chat = off; off += l.F ? al256((size_t)l.F * 2 * b) : 0;
+    l.off_chat = off; off += l.F ? al256((size_t)l.F * 2 * b * (l.f4h ? 2 : 1)) : 0;
     l.off_ftw = off; off += l.F ? al256((size_t)l.F * (l.f4 ? 3 : 1) * 2 * b) : 0;   // four-step: + step twiddles
     // the three-launch form's scratch (also the FP64 set-up scratch, 32 F bytes);
     // the one-CTA-per-mode variant needs the set-up's only
     l.off_f4s = off; off += l.f4 ? al256(l.f4b ? (size_t)32 * l.F : (size_t)(nx / 2) * l.F * 2 * b) : 0;
+    // the split-BF16 row phase's DFT matrices
+    l.xtc = xtc;
+    l.off_xdft = off; off += xtc ? al256(xdft_bytes(nx)) : 0;
     l.total = off;
     return l;
 }
@@ -150,7 +157,7 @@ CurveDev bind_layout(const ks_params *p, const Layout &l, void *base)
     d.ns = p->ns;
     d.nx = p->nx;
     d.P = p->ns - 1;
-    d.prec = p->precision == KS_FP32 ? 1 : 0;
+    d.prec = storage32(p->precision);
     d.sym = p->symmetry;
     d.L = p->L;
     d.S = p->S;
@@ -188,6 +195,9 @@ CurveDev bind_layout(const ks_params *p, const Layout &l, void *base)
     d.F2 = l.F2;
     d.f4c = l.f4c;
     d.f4b = l.f4b;
+    d.f4h = l.f4h;
+    d.xtc = l.xtc;
+    d.xdft = l.xtc ? (void *)(b + l.off_xdft) : nullptr;
     d.cot = b + l.off_cot;
     d.sig = b + l.off_sig;
     d.tau = b + l.off_tau;
@@ -269,6 +279,11 @@ __global__ void k_scalars_init(DevScalars *sc, unsigned *tcnt, int ntiles, doubl
         z.limit = 0;
         *sc = z;
     }
+}
+
+__global__ void k_set_wait_cycles(DevScalars *sc, long long cycles)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) sc->wait_cycles = cycles;
 }
 
 __global__ void k_set_limit(DevScalars *sc, long long nsteps, double tol)
@@ -701,12 +716,14 @@ __device__ __forceinline__ bool mbar_test(unsigned long long *bar, unsigned pari
     return ok != 0;
 }
 
-// Bounded wait for phase `parity`; false when the bound ran out.
-__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned parity)
+// Bounded wait for phase `parity`; false when the bound ran out (a negative
+// bound gives up at once: the error path's test).
+__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned parity, long long bound = WAIT_CYCLES)
 {
+    if (bound < 0) return false;
     const long long t0 = clock64();
     while (!mbar_test(bar, parity))
-        if (clock64() - t0 > (1ll << 31)) return false;
+        if (clock64() - t0 > bound) return false;
     return true;
 }
 
@@ -823,6 +840,7 @@ __device__ __forceinline__ void sconv_body(const CurveDev &c, int mode, int disc
     pdl_wait();
     const int g_active = sc->active;
     const double lam_d = sc->lambda, dtau_d = sc->dtau;
+    const long long wb = wait_bound(*sc);
     if (gate && !g_active) {
         // the thread that armed the barrier keeps the CTA alive until the copy has landed
         if (bulk && t == 0 && !mbar_wait(&bar, 0)) {
@@ -873,7 +891,7 @@ __device__ __forceinline__ void sconv_body(const CurveDev &c, int mode, int disc
         }
     }
     __syncthreads();   // z complete; the barrier's initialisation visible to every thread
-    if (bulk && !mbar_wait(&bar, 0)) {
+    if (bulk && !mbar_wait(&bar, 0, wb)) {
         atomicExch(&sc->err, 1);
         mbar_wait(&bar, 0);   // the copy may still be writing this CTA's shared memory
     }
@@ -1056,6 +1074,7 @@ cudaError_t launch_setup(const CurveDev &c, double dtau, cudaStream_t st)
     if (c.prec) k_setup<float><<<grid, 256, 0, st>>>(c, dtau);
     else k_setup<double><<<grid, 256, 0, st>>>(c, dtau);
     cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess && c.xtc) e = launch_setup_xdft(c, st);
     if (e != cudaSuccess || c.F == 0) return e;
     if (c.f4) return launch_setup_f4(c, st);
     const int g2 = (c.F + 255) / 256;
@@ -1075,6 +1094,12 @@ cudaError_t launch_scalars_init(const CurveDev &c, double lambda, int lambda_fre
 {
     k_scalars_init<<<1, 256, 0, st>>>(c.sc, c.tcnt, c.tiles_r * c.tiles_c, lambda, lambda_free, dtau, dtau_lambda,
                                       conv);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_set_wait_cycles(const CurveDev &c, long long cycles, cudaStream_t st)
+{
+    k_set_wait_cycles<<<1, 32, 0, st>>>(c.sc, cycles);
     return cudaGetLastError();
 }
 
@@ -1130,6 +1155,7 @@ cudaError_t launch_row_inv(const CurveDev &c, const void *spec, void *phys, int 
 
 cudaError_t launch_rows(const CurveDev &c, int mode, cudaStream_t st, StepArm arm)
 {
+    if (c.xtc) return launch_rows_tc(c, mode, st, arm);
     return c.prec ? rows_t<float>(c, mode, st, arm) : rows_t<double>(c, mode, st, arm);
 }
 

@@ -50,7 +50,7 @@ extern "C" ks_status ks_cost_noalloc(const ks_params *p, const void *u_dev, doub
         return ks::report_error(KS_EINVAL, "ks_cost_noalloc: p, u_dev and out_dev are required");
     ks_status s = ks::check_params(p);
     if (s != KS_OK) return s;
-    const ks::Layout lay = ks::make_layout(p->ns, p->nx, p->precision == KS_FP32, 1, 0, p->s_transform);
+    const ks::Layout lay = ks::curve_layout(p, 0);
     if (lay.total > (size_t)KS_NOALLOC_SCRATCH_BYTES)
         return ks::report_error(KS_ENOMEM,
                                 "ks_cost_noalloc: a %d x %d curve needs %zu bytes of scratch; the built-in array holds %zu",

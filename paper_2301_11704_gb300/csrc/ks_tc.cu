@@ -29,30 +29,11 @@
 #include <cooperative_groups.h>
 
 #include "ks_device.cuh"
+#include "ks_tcgen05.cuh"
 
 namespace ks {
 
 namespace tc {
-
-__device__ __forceinline__ unsigned su32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
-
-// Shared-memory matrix descriptor: start address, leading and stride byte
-// offsets (16-byte units), descriptor version 1, no swizzle.
-__device__ __forceinline__ unsigned long long sdesc(const void *p, unsigned lbo, unsigned sbo)
-{
-    unsigned long long d = (unsigned long long)((su32(p) & 0x3FFFF) >> 4);
-    d |= (unsigned long long)((lbo >> 4) & 0x3FFF) << 16;
-    d |= (unsigned long long)((sbo >> 4) & 0x3FFF) << 32;
-    d |= 1ull << 46;
-    return d;
-}
-
-// Instruction descriptor of kind::tf32: FP32 accumulator, TF32 A and B, both
-// K-major, N and M.
-__host__ __device__ constexpr unsigned idesc_tf32(int M, int N)
-{
-    return (1u << 4) | (2u << 7) | (2u << 10) | ((unsigned)(N >> 3) << 17) | ((unsigned)(M >> 4) << 24);
-}
 
 __device__ __forceinline__ float tf32(float x)
 {
@@ -69,55 +50,6 @@ __device__ __forceinline__ void split3(float x, float &x0, float &x1, float &x2)
     const float r = x - x0;
     x1 = tf32(r);
     x2 = tf32(r - x1);
-}
-
-__device__ __forceinline__ void mma(unsigned tmem, unsigned long long a, unsigned long long b, unsigned idesc, int acc)
-{
-    asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-                 "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
-                 "l"(a), "l"(b), "r"(idesc), "r"(acc)
-                 : "memory");
-}
-
-__device__ __forceinline__ void commit(unsigned long long *bar)
-{
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su32(bar))
-                 : "memory");
-}
-
-__device__ __forceinline__ bool bar_test(unsigned long long *bar, unsigned parity)
-{
-    unsigned ok;
-    asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
-                 : "=r"(ok)
-                 : "r"(su32(bar)), "r"(parity)
-                 : "memory");
-    return ok != 0;
-}
-
-// Bounded wait (about a second of clock cycles); false when it gave up.
-__device__ __forceinline__ bool bar_wait(unsigned long long *bar, unsigned parity)
-{
-    const long long t0 = clock64();
-    while (!bar_test(bar, parity))
-        if (clock64() - t0 > (1ll << 31)) return false;
-    return true;
-}
-
-__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-
-// 16 consecutive accumulator columns of this thread's TMEM lane.
-__device__ __forceinline__ void ld16(unsigned taddr, float (&v)[16])
-{
-    unsigned r[16];
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-                   "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-                 : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
 }  // namespace tc
@@ -157,6 +89,7 @@ __global__ void __launch_bounds__(TC_THREADS) k_dt_tc(CurveDev c, int mode, int 
     pdl_wait();
     const int g_active = sc->active;
     const double lam_d = sc->lambda, dtau_d = sc->dtau;
+    const long long wb = wait_bound(*sc);
     if (gate && !g_active) return;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -245,7 +178,10 @@ __global__ void __launch_bounds__(TC_THREADS) k_dt_tc(CurveDev c, int mode, int 
     for (int s = 0; s < nst; ++s) {
         const int buf = s & 1;
         if (s >= 2) {   // stage s-2 has been multiplied: its operands and accumulator are free
-            if (!tc::bar_wait(&mbar[buf], ((s - 2) >> 1) & 1)) ok = false;
+            if (!tc::bar_wait(&mbar[buf], ((s - 2) >> 1) & 1, ok ? wb : -1)) {
+                ok = false;
+                tc::bar_wait(&mbar[buf], ((s - 2) >> 1) & 1);   // its products still read this stage
+            }
             tc::fence_after();
             add_stage(buf);
         }
@@ -310,19 +246,19 @@ __global__ void __launch_bounds__(TC_THREADS) k_dt_tc(CurveDev c, int mode, int 
                 const unsigned long long b1 = tc::sdesc(B1 + 256 * s8, 128, Cfg::SBO);
                 const unsigned long long b2 = tc::sdesc(B2 + 256 * s8, 128, Cfg::SBO);
                 const unsigned d = tmem + buf * Cfg::MMA_N;
-                tc::mma(d, a0, b2, IDESC, s8 > 0 ? 1 : 0);
-                tc::mma(d, a1, b1, IDESC, 1);
-                tc::mma(d, a2, b0, IDESC, 1);
-                tc::mma(d, a0, b1, IDESC, 1);
-                tc::mma(d, a1, b0, IDESC, 1);
-                tc::mma(d, a0, b0, IDESC, 1);
+                tc::mma_tf32(d, a0, b2, IDESC, s8 > 0 ? 1 : 0);
+                tc::mma_tf32(d, a1, b1, IDESC, 1);
+                tc::mma_tf32(d, a2, b0, IDESC, 1);
+                tc::mma_tf32(d, a0, b1, IDESC, 1);
+                tc::mma_tf32(d, a1, b0, IDESC, 1);
+                tc::mma_tf32(d, a0, b0, IDESC, 1);
             }
             tc::commit(&mbar[buf]);
         }
     }
     // the last two stages (a commit tracks every earlier MMA of the issuing thread)
     for (int s = nst >= 2 ? nst - 2 : 0; s < nst; ++s) {
-        if (!tc::bar_wait(&mbar[s & 1], (s >> 1) & 1)) {
+        if (!tc::bar_wait(&mbar[s & 1], (s >> 1) & 1, ok ? wb : -1)) {
             ok = false;
             tc::bar_wait(&mbar[s & 1], (s >> 1) & 1);
         }

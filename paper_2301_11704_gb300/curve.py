@@ -14,7 +14,8 @@ import torch
 from . import _native
 from ._native import KSParams, KSScalars, check, dptr
 
-_PREC = {"fp64": _native.KS_FP64, "fp32": _native.KS_FP32}
+_PREC = {"fp64": _native.KS_FP64, "fp32": _native.KS_FP32, "bf16x2": _native.KS_BF16X2,
+         "bf16x3": _native.KS_BF16X3}
 _ADJ = {"paper": _native.KS_ADJ_PAPER, "discrete": _native.KS_ADJ_DISCRETE}
 _CONV = {"jarc": _native.KS_CONV_JARC, "j": _native.KS_CONV_J, "jrel": _native.KS_CONV_JREL}
 _STR = {"auto": 0, "dense": 1, "fft": 2, "dense_tc": 3, "fft4": 4, "fft4c": 5}
@@ -180,6 +181,12 @@ class KSCurve:
         if passes:
             out["passes"] = passes
         return out
+
+    def debug_wait_limit(self, cycles: int):
+        """Bound (clock cycles) of each kernel's first device-side mbarrier wait
+        (0: the default; < 0: give up at once).  A test hook for the KS_ETIMEOUT
+        path; ks_curve_init_trial restores the default."""
+        check(self.lib.ks_curve_debug_wait_limit(self._live(), int(cycles)))
 
     def close(self):
         if getattr(self, "handle", None) is not None:

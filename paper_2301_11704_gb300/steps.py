@@ -18,7 +18,7 @@ def main(argv=None):
     ap.add_argument("--cfg", type=int, default=1, choices=[0, 1, 2, 4])
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=2)
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64", "bf16x2", "bf16x3"])
     ap.add_argument("--s-transform", default="auto", choices=["auto", "dense", "fft", "dense_tc", "fft4", "fft4c"])
     ap.add_argument("--phases", action="store_true",
                     help="after the timed steps, time the phases of --steps more steps (rows, the two contractions)")

@@ -57,7 +57,7 @@ def test_workspace_size_scales_with_the_curve(lib):
 
 
 @pytest.mark.parametrize("bad", [dict(nx=24), dict(nx=4), dict(nx=512), dict(ns=2), dict(L=0.0), dict(S=-1.0),
-                                 dict(dtau=0.0), dict(precision=7), dict(adjoint=3), dict(conv=9),
+                                 dict(dtau=0.0), dict(precision=7), dict(precision=4), dict(precision=2, nx=32), dict(precision=3, nx=16), dict(adjoint=3), dict(conv=9),
                                  dict(symmetry=4), dict(s_transform=6), dict(s_transform=4, ns=500), dict(s_transform=5, ns=500), dict(s_transform=5, ns=12000, precision=0), dict(s_transform=3, precision=0), dict(launch=2), dict(L=float("nan"))])
 def test_invalid_parameters_are_rejected_on_the_host(lib, bad):
     p = _params(**bad)
@@ -93,16 +93,17 @@ def test_null_handle_is_rejected(lib):
     (dict(precision=1, nx=64, ns=600), 0, 1),                # FP32 below N_s = 684: dense
     (dict(precision=1, nx=64, ns=1024), 4096, 5),            # FP32 from N_s = 684: clustered four-step
     (dict(precision=1, nx=64, ns=5462), 16384, 5),           # N_x <= 64 up to F = 16384
-    (dict(precision=1, nx=64, ns=5463), 32768, 4),
+    (dict(precision=1, nx=64, ns=5463), 16384, 4),           # three-launch: F >= 2P + 1
     (dict(precision=1, nx=128, ns=2731), 8192, 5),           # N_x = 128 up to F = 8192
-    (dict(precision=1, nx=128, ns=2732), 16384, 4),
+    (dict(precision=1, nx=128, ns=2732), 8192, 4),
     (dict(precision=1, nx=256, ns=700), 4096, 4),            # N_x = 256: three-launch four-step
-    (dict(precision=1, nx=256, ns=16384), 65536, 4),
+    (dict(precision=1, nx=256, ns=16384), 32768, 4),
+    (dict(precision=1, nx=256, ns=16385), 65536, 4),         # 2P + 1 = 32769
     (dict(precision=1, nx=64, ns=30000), 0, 3),              # above the four-step limit: tensor-core dense
     (dict(precision=0, nx=16, ns=1366), 4096, 5),            # FP64 clustered at F = 4096, N_x <= 16
     (dict(precision=0, nx=32, ns=1024), 4096, 4),            # FP64 N_s >= 684: four-step
     (dict(precision=0, nx=256, ns=1024), 4096, 2),           # FP64 N_x = 256: one CTA per mode while it fits
-    (dict(precision=0, nx=256, ns=2048), 8192, 4),
+    (dict(precision=0, nx=256, ns=2048), 4096, 4),
     (dict(precision=0, nx=64, ns=600), 2048, 2),             # FP64 below N_s = 684, N_x >= 64: one-CTA FFT
     (dict(precision=0, nx=32, ns=600), 0, 1),                # FP64, N_x = 32, small: dense
     (dict(precision=0, nx=32, ns=128), 512, 2),              # FP64, N_s <= 128
@@ -115,3 +116,21 @@ def test_null_handle_is_rejected(lib):
 def test_s_transform_rule(lib, kw, F, form):
     assert lib.ks_curve_fft_length(ctypes.byref(_params(**kw))) == F
     assert lib.ks_curve_s_form(ctypes.byref(_params(**kw))) == form
+
+
+@pytest.mark.parametrize("prec", [2, 3])
+@pytest.mark.parametrize("nx", [64, 128, 256])
+def test_split_bf16_workspace_holds_the_dft_matrices(lib, prec, nx):
+    """Split-BF16 x-transforms: FP32 storage plus the two N x N DFT matrices in
+    three BF16 parts (12 N^2 bytes); same s-form as FP32."""
+    ws32 = lib.ks_curve_workspace_bytes(ctypes.byref(_params(precision=1, nx=nx, ns=1024)))
+    wsb = lib.ks_curve_workspace_bytes(ctypes.byref(_params(precision=prec, nx=nx, ns=1024)))
+    assert wsb - ws32 == ((12 * nx * nx + 255) // 256) * 256
+    assert lib.ks_curve_s_form(ctypes.byref(_params(precision=prec, nx=nx, ns=1024))) == \
+        lib.ks_curve_s_form(ctypes.byref(_params(precision=1, nx=nx, ns=1024)))
+
+
+def test_split_bf16_batches_are_rejected(lib):
+    ps = (KSParams * 2)(_params(precision=3, nx=64), _params(precision=3, nx=64))
+    assert lib.ks_batch_workspace_bytes(2, ps) == 0
+    assert b"batch" in lib.ks_last_error()

@@ -1,5 +1,7 @@
 """The four-step FFT form of the s-contraction (transforms longer than one CTA
-holds: F = F1 F2 with warp-level line transforms and a scratch pass in between)
+holds: F = F1 F2 with warp-level line transforms and a scratch pass in between;
+the three-launch form on the Toeplitz and Hankel parts of D_t with F >= 2P + 1,
+the clustered one on the extended sequence with F >= 3P)
 against the FP64 oracle and against the dense contraction on the same inputs:
 every pair (F1, F2) the library uses, both adjoints, the descent, ragged N_s and
 the symmetric subspace.
@@ -38,13 +40,14 @@ def _curve(N, Ns, L, seed, fp32=False):
 @pytest.mark.parametrize("form", ["fft", "fft4c"])
 @pytest.mark.parametrize("adjoint", ["paper", "discrete"])
 def test_four_step_fp64_matches_oracle(adjoint, form):
-    """N_s = 1500 in FP64: F = 8192 = 128 x 64 (above the single-CTA FP64 limit);
-    the three-launch form and the clustered one-launch form."""
+    """N_s = 1500 in FP64 (above the single-CTA FP64 limit): the three-launch form
+    on the Toeplitz and Hankel parts (F = 4096 = 64 x 64 >= 2P + 1) and the
+    clustered one-launch form on the extended sequence (F = 8192 = 128 x 64 >= 3P)."""
     N, Ns, L = 32, 1500, 22.0
     S = 0.1 * (Ns - 1)
     X = _curve(N, Ns, L, 11)
     c = KSCurve(L, N, Ns, S, X[0], X[-1], u_init=torch.from_numpy(X), adjoint=adjoint, s_transform=form)
-    assert c.fft_length == 8192
+    assert c.fft_length == (4096 if form == "fft" else 8192)
     U = oracle.curve_spectral(X)
     spec = gen.CurveSpec(0, 0, L, N, Ns, S)
     mode = oracle.DISCRETE if adjoint == "discrete" else oracle.PAPER
@@ -87,9 +90,13 @@ def test_fused_step_fp64_matches_oracle(adjoint):
 
 
 @pytest.mark.parametrize("precision,N,Ns,F,form", [
-    ("fp32", 64, 3000, 16384, "fft"),     # 128 x 128
-    ("fp32", 32, 7001, 32768, "fft"),     # 256 x 128, ragged
-    ("fp32", 16, 12345, 65536, "fft"),    # 256 x 256, ragged
+    # the three-launch form (Toeplitz and Hankel parts, F >= 2P + 1): every (F1, F2)
+    ("fp32", 64, 3000, 8192, "fft"),      # 128 x 64
+    ("fp32", 64, 6000, 16384, "fft"),     # 128 x 128
+    ("fp32", 32, 7001, 16384, "fft"),     # ragged
+    ("fp32", 16, 12345, 32768, "fft"),    # 256 x 128, ragged
+    ("fp32", 16, 20000, 65536, "fft"),    # 256 x 256
+    ("fp32", 256, 16384, 32768, "fft4"),  # the largest workload's form
     ("fp64", 128, 2500, 8192, "fft"),     # 128 x 64
     ("fp64", 64, 5000, 16384, "fft"),
     ("fp32", 64, 1024, 4096, "fft4"),     # 64 x 64, where one CTA would also hold it
@@ -125,13 +132,15 @@ def test_four_step_matches_dense(precision, N, Ns, F, form):
     cd.close()
 
 
-def test_four_step_fp32_matches_oracle():
-    """F = 65536 = 256 x 256 in FP32 against the FP64 oracle on the same (FP32) curve."""
-    N, Ns = 16, 12345
+@pytest.mark.parametrize("Ns,F,form", [(20000, 65536, "fft"), (12345, 65536, "fft4c")])
+def test_four_step_fp32_matches_oracle(Ns, F, form):
+    """F = 65536 = 256 x 256 in FP32 against the FP64 oracle on the same (FP32)
+    curve: the three-launch form (Toeplitz and Hankel parts) and the clustered one."""
+    N = 16
     L, S = 22.0 + N / 16.0, 0.1 * (Ns - 1)
     X = _curve(N, Ns, L, N + Ns, fp32=True)
-    c = KSCurve(L, N, Ns, S, X[0], X[-1], u_init=torch.from_numpy(X).float(), precision="fp32", s_transform="fft")
-    assert c.fft_length == 65536
+    c = KSCurve(L, N, Ns, S, X[0], X[-1], u_init=torch.from_numpy(X).float(), precision="fp32", s_transform=form)
+    assert c.fft_length == F
     U = oracle.curve_spectral(X)
     R, D = oracle.curve_residual(U, L, S, 1.0)
     sc = oracle.curve_scalars(R, D, L, S, 1.0)
@@ -154,7 +163,7 @@ def test_four_step_holds_the_symmetric_subspace(sym, form):
         X += 0.2 * np.outer(np.sin(2 * th), np.sin(2 * np.pi * x / L))
     c = KSCurve(L, N, Ns, 0.1 * (Ns - 1), X[0], X[-1], u_init=torch.from_numpy(X), dtau=1e-3, symmetry=sym,
                 s_transform=form)
-    assert c.fft_length == 16384
+    assert c.fft_length == (8192 if form == "fft" else 16384)
     c.descend(20)
     U = np.fft.rfft(c.get_state().cpu().numpy(), axis=1)
     assert np.abs(U.real).max() <= 1e-12 * np.abs(U).max()
