@@ -562,12 +562,13 @@ __global__ void __launch_bounds__(F4_THREADS) k_f4_p3(CurveDev c, int mode, int 
             }
             T g[NV];
             if (j > 0 && j < P) {
+                T gg = T(0);   // this row's sum over the sector in the storage type, one FP64 term per row
 #pragma unroll
                 for (int q = 0; q < NV; ++q) {
                     g[q] = sector_col_ok(jm0, q, sym) ? -(av[h][q] + (discrete ? -lam * y[q] : lam * y[q])) : T(0);
-                    const double cw = (jm0 + q / 2 == 0) ? 1.0 : 2.0;
-                    partsum += wv[h] * cw * ((double)g[q] * (double)g[q]);
+                    gg += ((jm0 + q / 2 == 0) ? T(1) : T(2)) * g[q] * g[q];
                 }
+                partsum += wv[h] * (double)gg;
                 if (mode == GM_UPDATE) {
 #pragma unroll
                     for (int q = 0; q < NV; ++q) uv[h][q] += dtau * prec[q / 2] * g[q];
@@ -945,12 +946,13 @@ __global__ void __launch_bounds__(F4_THREADS) k_f4c(CurveDev c, int mode, int di
                 }
                 T g[NV];
                 if (j > 0 && j < P) {
+                    T gg = T(0);   // the row's sum over the sector in the storage type, one FP64 term per row
 #pragma unroll
                     for (int q = 0; q < NV; ++q) {
                         g[q] = sector_col_ok(jm0, q, sym) ? -(av[h][q] + (cdisc ? -lam * yv[q] : lam * yv[q])) : T(0);
-                        const double cw = (jm0 + q / 2 == 0) ? 1.0 : 2.0;
-                        partsum += wv[h] * cw * ((double)g[q] * (double)g[q]);
+                        gg += ((jm0 + q / 2 == 0) ? T(1) : T(2)) * g[q] * g[q];
                     }
+                    partsum += wv[h] * (double)gg;
                     if (cmode == GM_UPDATE) {
 #pragma unroll
                         for (int q = 0; q < NV; ++q) uv[h][q] += dtau * prec[q / 2] * g[q];
@@ -1177,7 +1179,7 @@ __device__ __forceinline__ void f4b_body(const CurveDev &c, int mode, int discre
             if (interior) {
                 if (oka) ga = -(av[a].x + (discrete ? -lam * yv.x : lam * yv.x));
                 if (okb) gb = -(av[a].y + (discrete ? -lam * yv.y : lam * yv.y));
-                partsum += wj[a] * cw * ((double)ga * (double)ga + (double)gb * (double)gb);
+                partsum += wj[a] * cw * (double)(ga * ga + gb * gb);
             }
             if (mode == GM_UPDATE) {
                 if (interior) *reinterpret_cast<V2 *>(U + o) = V2{uv[a].x + dtau * pr * ga, uv[a].y + dtau * pr * gb};

@@ -941,7 +941,7 @@ __device__ __forceinline__ void sconv_body(const CurveDev &c, int mode, int disc
         if (interior) {
             if (oka) ga = -(av[i].x + (discrete ? -lam * yv.x : lam * yv.x));
             if (okb) gb = -(av[i].y + (discrete ? -lam * yv.y : lam * yv.y));
-            partsum += wj[i] * cw * ((double)ga * (double)ga + (double)gb * (double)gb);
+            partsum += wj[i] * cw * (double)(ga * ga + gb * gb);
         }
         if (mode == GM_UPDATE) {
             if (interior)

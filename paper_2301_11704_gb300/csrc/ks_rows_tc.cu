@@ -51,7 +51,8 @@ namespace ks {
 namespace {
 
 constexpr int XT_M = 128;          // sections per CTA: MMA M, TMEM lanes
-constexpr int XT_THREADS = 256;    // two threads per section, one per half of each chunk
+constexpr int XT_PROD = 256;       // operand and epilogue threads: two per section, one per half of each chunk
+constexpr int XT_THREADS = XT_PROD + 32;   // and one warp that issues the bulk copies and the products
 constexpr int XT_KC = 32;          // K per pipeline chunk
 constexpr int XT_HV = XT_KC / 2;   // values of a chunk per thread
 constexpr int XT_PARTS = 3;        // parts stored per DFT-matrix chunk
@@ -125,13 +126,36 @@ __device__ __forceinline__ void st_half(float *p, const float (&v)[XT_HV])
         reinterpret_cast<float4 *>(p)[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
 }
 
-// XT_HV accumulator columns of this thread's lane (warp-collective: the warp
-// reconverges first)
-__device__ __forceinline__ void tld(unsigned taddr, float (&v)[XT_HV])
+// XT_HV accumulator columns of this thread's lane, in two steps: tld_issue starts
+// the load (warp-collective: the warp reconverges first), tld_wait waits for every
+// load this thread started and ties the registers to that wait, so that no read
+// of them is scheduled before it.
+__device__ __forceinline__ void tld_issue(unsigned taddr, unsigned (&r)[XT_HV])
 {
     __syncwarp();
-    tc::ld16(taddr, v);
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                   "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+                 : "r"(taddr));
 }
+
+__device__ __forceinline__ void tld_wait(unsigned (&r)[XT_HV])
+{
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
+                   "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]), "+r"(r[15])
+                 :
+                 : "memory");
+}
+
+__device__ __forceinline__ void tld_wait(unsigned (&r)[XT_HV], unsigned (&r2)[XT_HV])
+{
+    tld_wait(r);
+    asm volatile("" : "+r"(r2[0]), "+r"(r2[1]), "+r"(r2[2]), "+r"(r2[3]), "+r"(r2[4]), "+r"(r2[5]), "+r"(r2[6]),
+                 "+r"(r2[7]), "+r"(r2[8]), "+r"(r2[9]), "+r"(r2[10]), "+r"(r2[11]), "+r"(r2[12]), "+r"(r2[13]),
+                 "+r"(r2[14]), "+r"(r2[15]));
+}
+
 
 __device__ __forceinline__ void tst(unsigned taddr, const float (&v)[XT_HV])
 {
@@ -143,24 +167,28 @@ template <int N, int NP>
 __global__ void __launch_bounds__(XT_THREADS, 1) k_rows_tc(CurveDev c, int mode, StepArm arm)
 {
     using Cfg = XtCfg<N, NP>;
-    constexpr int H = N / 2;
+    constexpr int H = N / 2, NW = XT_THREADS / 32;
     extern __shared__ __align__(1024) unsigned char smem_x[];
     unsigned char *As = smem_x;                                        // [2][NP][A_PART]
     unsigned char *Bs = smem_x + XT_ASTAGES * Cfg::A_STAGE;           // [3][NP][B_PART]
-    __shared__ __align__(8) unsigned long long full_b[XT_BSTAGES], mma_done[XT_BSTAGES];
+    // full_b: a DFT-matrix chunk has landed; a_full: an operand chunk is written
+    // (XT_PROD arrivals); mma_done: the products of a chunk are complete (commit)
+    __shared__ __align__(8) unsigned long long full_b[XT_BSTAGES], mma_done[XT_BSTAGES], a_full[XT_ASTAGES];
     __shared__ unsigned tmem_slot;
+    __shared__ int sbad;   // a bounded wait gave up: no more copies or products are issued
     __shared__ float tk[H], ta[H];
     __shared__ float hsum[XT_M][5];
-    __shared__ double wpart[XT_THREADS / 32][5];
+    __shared__ double wpart[NW][5];
     __shared__ int am_last;
     DevScalars *sc = c.sc;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    // section row r (TMEM lane 32 (warp % 4) + lane) and column half h of every chunk
-    const int r = 32 * (warp & 3) + lane, h = warp >> 2, co = h * XT_HV;
+    const bool issuer = warp == XT_PROD / 32;
+    // producers: section row r (TMEM lane 32 (warp % 4) + lane), column half h of every chunk
+    const int r = 32 * (warp & 3) + lane, h = (warp >> 2) & 1, co = h * XT_HV;
     const int blk = blockIdx.x, nblk = gridDim.x;
     const int ns = c.ns, P = c.P;
     const int m = blk * XT_M + r;
-    const bool has = m < ns, in = has && m > 0 && m < P;
+    const bool has = !issuer && m < ns, in = has && m > 0 && m < P;
     const float *U = (const float *)c.U, *D = (const float *)c.D;
     float *R = (float *)c.R, *A = (float *)c.A;
     const unsigned char *xdft = (const unsigned char *)c.xdft;
@@ -198,61 +226,41 @@ __global__ void __launch_bounds__(XT_THREADS, 1) k_rows_tc(CurveDev c, int mode,
             tc::bar_init(&full_b[i], 1);
             tc::bar_init(&mma_done[i], 1);
         }
+        for (int i = 0; i < XT_ASTAGES; ++i) tc::bar_init(&a_full[i], XT_PROD);
+        sbad = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     tc::fence_before();
     __syncthreads();
     tc::fence_after();
     const unsigned tmem = tmem_slot;
-    // this thread's TMEM lane, at its column half
-    const unsigned lane_base = tmem + ((unsigned)(32 * (warp & 3)) << 16) + (unsigned)co;
-    constexpr unsigned IDESC = tc::idesc_bf16(XT_M, N);
-    const float lam = (float)lamd;
-    const size_t ro = (size_t)(has ? m : 0) * N + co;
-    const float *Urow = U + ro, *Drow = D + ro;
-    float *Rrow = R + ro, *Arow = A + ro;
+    volatile int *vbad = &sbad;
+    float s[5] = {0.f, 0.f, 0.f, 0.f, 0.f};   // row sums |r|^2, |d|^2, <d,r>, |u|^2, |f|^2 (Parseval weights)
 
-    // chunk q of the stream: product q / NCH (C, E, C, E), K-chunk q % NCH
-    int issued_b = -1, waited_b = -1;   // thread 0: the last chunk whose B copy was issued / seen complete
-    auto issue_b = [&](int q) {
-        const int X = (q / Cfg::NCH) & 1, cch = q % Cfg::NCH, sb = q % XT_BSTAGES;
-        tc::bulk_g2s(Bs + sb * Cfg::B_STAGE, xdft + (size_t)((X * Cfg::NCH + cch) * XT_PARTS) * Cfg::B_PART,
-                     (unsigned)Cfg::B_STAGE, &full_b[sb]);
-        issued_b = q;
-    };
-    bool bad = false;   // CTA-uniform: a bounded wait gave up
-    if (tid == 0) issue_b(0);
-
-    // one product.  `fetch(cch, buf)` loads what chunk cch of this thread's half
-    // row needs (issued one chunk ahead, so that its latency overlaps the previous
-    // chunk), `produce(cch, buf, v)` turns it into the operand values.
-    int q = 0;
-    auto product = [&](int g, auto &&fetch, auto &&produce) {
-        const unsigned dcol = tmem + (g == 0 ? 0u : (unsigned)N);
-        float cur[XT_HV], nxt[XT_HV];
-        fetch(0, cur);
-#pragma unroll 1
-        for (int cch = 0; cch < Cfg::NCH; ++cch, ++q) {
-            const int sa = q & 1, sb = q % XT_BSTAGES;
-            if (cch + 1 < Cfg::NCH) fetch(cch + 1, nxt);
-            if (q >= 2 && !bad && !tc::bar_wait(&mma_done[(q - 2) % XT_BSTAGES], ((q - 2) / XT_BSTAGES) & 1, wb))
-                bad = true;
-            if (tid == 0 && !bad && q + 1 < Cfg::QTOT) issue_b(q + 1);
-            float v[XT_HV];
-            produce(cch, cur, v);
-            if (!has) {
-#pragma unroll
-                for (int i = 0; i < XT_HV; ++i) v[i] = 0.f;
-            }
-            put_split<NP>(As + sa * Cfg::A_STAGE, Cfg::A_PART, r, h, v);
-            tc::fence_async_smem();
-            tc::fence_before();
-            bad = __syncthreads_or(bad) != 0;
-            tc::fence_after();
-            if (tid == 0) {
-                bool okb = !bad && tc::bar_wait(&full_b[sb], (q / XT_BSTAGES) & 1, wb);
-                if (okb) {
+    if (issuer) {
+        // ---- the chunk stream: product q / NCH (C, E, C, E), K-chunk q % NCH.  One
+        // thread: bulk copy of each DFT-matrix chunk two ahead, the products of each
+        // chunk once its operand chunk and matrix chunk are in, a commit per chunk.
+        if (lane == 0) {
+            constexpr unsigned IDESC = tc::idesc_bf16(XT_M, N);
+            auto issue_b = [&](int q) {
+                const int X = (q / Cfg::NCH) & 1, cch = q % Cfg::NCH, sb = q % XT_BSTAGES;
+                tc::bulk_g2s(Bs + sb * Cfg::B_STAGE, xdft + (size_t)((X * Cfg::NCH + cch) * XT_PARTS) * Cfg::B_PART,
+                             (unsigned)Cfg::B_STAGE, &full_b[sb]);
+            };
+            bool ok = true;
+            int issued_b = 1, waited_b = -1;
+            issue_b(0);
+            issue_b(1);
+            for (int q = 0; q < Cfg::QTOT; ++q) {
+                const int g = q / Cfg::NCH, cch = q % Cfg::NCH, sa = q & 1, sb = q % XT_BSTAGES;
+                ok = ok && !*vbad;
+                if (ok && !tc::bar_wait(&a_full[sa], (q >> 1) & 1, wb)) ok = false;
+                if (ok && !tc::bar_wait(&full_b[sb], (q / XT_BSTAGES) & 1, wb)) ok = false;
+                if (ok) {
                     waited_b = q;
+                    tc::fence_after();
+                    const unsigned dcol = tmem + (g == 0 ? 0u : (unsigned)N);
                     const unsigned char *a0 = As + sa * Cfg::A_STAGE, *b0 = Bs + sb * Cfg::B_STAGE;
 #pragma unroll
                     for (int s = 0; s < XT_KC / 16; ++s) {
@@ -268,160 +276,252 @@ __global__ void __launch_bounds__(XT_THREADS, 1) k_rows_tc(CurveDev c, int mode,
                             tc::mma_f16(dcol, ad, bd, IDESC, (cch > 0 || s > 0 || t > 0) ? 1 : 0);
                         }
                     }
-                } else {
+                } else if (!*vbad) {
+                    *vbad = 1;
                     atomicExch(&sc->err, 4);
                 }
                 tc::commit(&mma_done[sb]);   // also when nothing was issued: keeps the phases in step
+                // matrix chunk q + 2 into the stage of chunk q - 1, once its products are done
+                if (ok && q + 2 < Cfg::QTOT) {
+                    if (q >= 1 && !tc::bar_wait(&mma_done[(q - 1) % XT_BSTAGES], ((q - 1) / XT_BSTAGES) & 1, wb)) {
+                        ok = false;
+                        *vbad = 1;
+                        atomicExch(&sc->err, 4);
+                    } else {
+                        issue_b(q + 2);
+                        issued_b = q + 2;
+                    }
+                }
             }
-#pragma unroll
-            for (int i = 0; i < XT_HV; ++i) cur[i] = nxt[i];
+            // copies that may still be landing (after a wait gave up), and the last products
+            for (int qq = waited_b + 1; qq <= issued_b; ++qq) tc::bar_wait(&full_b[qq % XT_BSTAGES], (qq / XT_BSTAGES) & 1);
+            tc::bar_wait(&mma_done[(Cfg::QTOT - 1) % XT_BSTAGES], ((Cfg::QTOT - 1) / XT_BSTAGES) & 1);
         }
-        // the product is complete once its last chunk's mbarrier has fired
-        const int ql = q - 1;
-        if (!bad && !tc::bar_wait(&mma_done[ql % XT_BSTAGES], (ql / XT_BSTAGES) & 1, wb)) bad = true;
-        bad = __syncthreads_or(bad) != 0;
-        tc::fence_after();
-    };
-    // between an epilogue's TMEM reads and the next product's writes to them
-    auto epilogue_done = [&]() {
-        tc::fence_before();
-        __syncthreads();
-        tc::fence_after();
-    };
-    auto fetch_row = [&](const float *row) {
-        return [row, has](int cch, float (&b)[XT_HV]) {
-            if (has) ld_half(row + cch * XT_KC, b);
-            else {
-#pragma unroll
-                for (int i = 0; i < XT_HV; ++i) b[i] = 0.f;
+        __syncwarp();
+    } else {
+        // ---- producers: operand chunks, and the pointwise work between the products
+        const unsigned lane_base = tmem + ((unsigned)(32 * (warp & 3)) << 16) + (unsigned)co;
+        const float lam = (float)lamd;
+        const size_t ro = (size_t)(has ? m : 0) * N + co;
+        const float *Urow = U + ro, *Drow = D + ro;
+        float *Rrow = R + ro, *Arow = A + ro;
+        auto fail = [&]() {
+            if (!*vbad) {
+                *vbad = 1;
+                atomicExch(&sc->err, 4);
             }
         };
-    };
-    auto fetch_t0 = [&](int cch, float (&b)[XT_HV]) { tld(lane_base + cch * XT_KC, b); };
-    // first mode of this thread's half of chunk cch
-    auto mode0 = [&](int cch) { return cch * (XT_KC / 2) + h * (XT_HV / 2); };
 
-    // ---- G1: u = uh C
-    product(0, fetch_row(Urow), [&](int cch, const float (&b)[XT_HV], float (&v)[XT_HV]) {
+        // one product.  `fetch(cch, buf)` starts loading what chunk cch of this
+        // thread's half row needs, one chunk ahead; `ready(buf)` completes it;
+        // `produce(cch, buf, v)` turns it into operand values.
+        // Chunks are taken in pairs with two buffers (b0 for even chunks, b1 for odd
+        // ones): a buffer whose TMEM load is in flight is never read or copied
+        // before `ready` has waited for it.
+        int q = 0;
+        auto product = [&](auto &&fetch, auto &&ready, auto &&produce) {
+            auto chunk = [&](int cch, unsigned (&b)[XT_HV]) {
+                const int sa = q & 1;
+                // the operand stage of chunk q - 2 is free once its products are done
+                if (q >= 2 && !*vbad && !tc::bar_wait(&mma_done[(q - 2) % XT_BSTAGES], ((q - 2) / XT_BSTAGES) & 1, wb))
+                    fail();
+                float v[XT_HV];
+                produce(cch, b, v);
+                if (!has) {
 #pragma unroll
-        for (int i = 0; i < XT_HV; ++i) v[i] = b[i];
-        if (cch == 0 && h == 0) v[1] = 0.f;
-    });
-    // ---- G2: wh = (u u) E
-    product(1, fetch_t0, [&](int, const float (&b)[XT_HV], float (&v)[XT_HV]) {
-#pragma unroll
-        for (int i = 0; i < XT_HV; ++i) v[i] = b[i] * b[i];
-    });
-    // ---- f^, r^ = f^ - l d^, row sums; r^ out (u^, d^ of the next chunk in flight)
-    float s[5] = {0.f, 0.f, 0.f, 0.f, 0.f};   // |r|^2, |d|^2, <d,r>, |u|^2, |f|^2 (Parseval weights)
-    {
-        auto fu = fetch_row(Urow), fd = fetch_row(Drow);
-        float u[XT_HV], d[XT_HV], un[XT_HV], dn[XT_HV];
-        fu(0, u);
-        fd(0, d);
+                    for (int i = 0; i < XT_HV; ++i) v[i] = 0.f;
+                }
+                put_split<NP>(As + sa * Cfg::A_STAGE, Cfg::A_PART, r, h, v);
+                tc::fence_async_smem();   // the generic writes, before the products read them
+                tc::fence_before();       // and this thread's TMEM reads, before later products write
+                asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::su32(&a_full[sa])) : "memory");
+                ++q;
+            };
+            static_assert(Cfg::NCH % 2 == 0, "chunks are taken in pairs");
+            unsigned b0[XT_HV], b1[XT_HV];
+            fetch(0, b0);
 #pragma unroll 1
-        for (int cch = 0; cch < Cfg::NCH; ++cch) {
-            if (cch + 1 < Cfg::NCH) {
-                fu(cch + 1, un);
-                fd(cch + 1, dn);
+            for (int cch = 0; cch < Cfg::NCH; cch += 2) {
+                ready(b0);
+                fetch(cch + 1, b1);
+                chunk(cch, b0);
+                ready(b1);
+                if (cch + 2 < Cfg::NCH) fetch(cch + 2, b0);
+                chunk(cch + 1, b1);
             }
-            float w[XT_HV], rv[XT_HV];
-            tld(lane_base + N + cch * XT_KC, w);
-            const int j0 = mode0(cch);
+            // the product is complete once its last chunk's mbarrier has fired
+            const int ql = q - 1;
+            if (!*vbad && !tc::bar_wait(&mma_done[ql % XT_BSTAGES], (ql / XT_BSTAGES) & 1, wb)) fail();
+            tc::fence_after();
+        };
+        auto fetch_row = [&](const float *row) {
+            return [row, has = has](int cch, unsigned (&b)[XT_HV]) {
+                float t[XT_HV];
+                if (has) ld_half(row + cch * XT_KC, t);
+                else {
 #pragma unroll
-            for (int i = 0; i < XT_HV / 2; ++i) {
-                const int j = j0 + i;
-                const float k = tk[j], a = ta[j], hk = 0.5f * k;
-                const float ur = u[2 * i], ui = j == 0 ? 0.f : u[2 * i + 1];
-                const float dr = d[2 * i], di = j == 0 ? 0.f : d[2 * i + 1];
-                const float fr = hk * w[2 * i + 1] - a * ur, fi = j == 0 ? 0.f : -hk * w[2 * i] - a * ui;
-                cpx<float> rr = {0.f, 0.f};
-                if (in) rr = project(cpx<float>{fr - lam * dr, fi - lam * di}, j, c.sym);
-                if (j == 0) rr.y = 0.f;
-                rv[2 * i] = rr.x;
-                rv[2 * i + 1] = rr.y;
-                const float cw = j == 0 ? 1.f : 2.f;
-                s[0] += cw * (rr.x * rr.x + rr.y * rr.y);
-                s[1] += cw * (dr * dr + di * di);
-                s[2] += cw * (dr * rr.x + di * rr.y);
-                s[3] += cw * (ur * ur + ui * ui);
-                s[4] += cw * (fr * fr + fi * fi);
-            }
-            if (has) st_half(Rrow + cch * XT_KC, rv);
+                    for (int i = 0; i < XT_HV; ++i) t[i] = 0.f;
+                }
+#pragma unroll
+                for (int i = 0; i < XT_HV; ++i) b[i] = __float_as_uint(t[i]);
+            };
+        };
+        auto no_wait = [](unsigned (&)[XT_HV]) {};
+        auto fetch_t0 = [&](int cch, unsigned (&b)[XT_HV]) { tld_issue(lane_base + cch * XT_KC, b); };
+        auto wait_t = [](unsigned (&b)[XT_HV]) { tld_wait(b); };
+        // first mode of this thread's half of chunk cch
+        auto mode0 = [&](int cch) { return cch * (XT_KC / 2) + h * (XT_HV / 2); };
+
+        // ---- G1: u = uh C
+        product(fetch_row(Urow), no_wait, [&](int cch, const unsigned (&b)[XT_HV], float (&v)[XT_HV]) {
+#pragma unroll
+            for (int i = 0; i < XT_HV; ++i) v[i] = __uint_as_float(b[i]);
+            if (cch == 0 && h == 0) v[1] = 0.f;
+        });
+        // ---- G2: wh = (u u) E
+        product(fetch_t0, wait_t, [&](int, const unsigned (&b)[XT_HV], float (&v)[XT_HV]) {
 #pragma unroll
             for (int i = 0; i < XT_HV; ++i) {
-                u[i] = un[i];
-                d[i] = dn[i];
+                const float x = __uint_as_float(b[i]);
+                v[i] = x * x;
+            }
+        });
+        // ---- f^, r^ = f^ - l d^, row sums; r^ out (the next chunk's u^, d^ and
+        // accumulator columns in flight)
+        {
+            auto fu = fetch_row(Urow), fd = fetch_row(Drow);
+            auto step = [&](int cch, const unsigned (&u)[XT_HV], const unsigned (&d)[XT_HV], const unsigned (&wr)[XT_HV]) {
+                float rv[XT_HV];
+                const int j0 = mode0(cch);
+#pragma unroll
+                for (int i = 0; i < XT_HV / 2; ++i) {
+                    const int j = j0 + i;
+                    const float k = tk[j], a = ta[j], hk = 0.5f * k;
+                    const float wre = __uint_as_float(wr[2 * i]), wim = __uint_as_float(wr[2 * i + 1]);
+                    const float ur = __uint_as_float(u[2 * i]), ui = j == 0 ? 0.f : __uint_as_float(u[2 * i + 1]);
+                    const float dr = __uint_as_float(d[2 * i]), di = j == 0 ? 0.f : __uint_as_float(d[2 * i + 1]);
+                    const float fr = hk * wim - a * ur, fi = j == 0 ? 0.f : -hk * wre - a * ui;
+                    cpx<float> rr = {0.f, 0.f};
+                    if (in) rr = project(cpx<float>{fr - lam * dr, fi - lam * di}, j, c.sym);
+                    if (j == 0) rr.y = 0.f;
+                    rv[2 * i] = rr.x;
+                    rv[2 * i + 1] = rr.y;
+                    const float cw = j == 0 ? 1.f : 2.f;
+                    s[0] += cw * (rr.x * rr.x + rr.y * rr.y);
+                    s[1] += cw * (dr * dr + di * di);
+                    s[2] += cw * (dr * rr.x + di * rr.y);
+                    s[3] += cw * (ur * ur + ui * ui);
+                    s[4] += cw * (fr * fr + fi * fi);
+                }
+                if (has) st_half(Rrow + cch * XT_KC, rv);
+            };
+            unsigned u0[XT_HV], d0[XT_HV], w0[XT_HV], u1[XT_HV], d1[XT_HV], w1[XT_HV];
+            fu(0, u0);
+            fd(0, d0);
+            tld_issue(lane_base + N, w0);
+#pragma unroll 1
+            for (int cch = 0; cch < Cfg::NCH; cch += 2) {
+                tld_wait(w0);
+                fu(cch + 1, u1);
+                fd(cch + 1, d1);
+                tld_issue(lane_base + N + (cch + 1) * XT_KC, w1);
+                step(cch, u0, d0, w0);
+                tld_wait(w1);
+                if (cch + 2 < Cfg::NCH) {
+                    fu(cch + 2, u0);
+                    fd(cch + 2, d0);
+                    tld_issue(lane_base + N + (cch + 2) * XT_KC, w0);
+                }
+                step(cch + 1, u1, d1, w1);
             }
         }
-    }
-    if (h == 1) {
+        if (h == 1) {
 #pragma unroll
-        for (int k = 0; k < 5; ++k) hsum[r][k] = s[k];
-    }
-    epilogue_done();   // also publishes the upper halves' sums
-    // ---- G3: r_x = (i k r^) C   (r^ as just written by this thread)
-    product(2, fetch_row(Rrow), [&](int cch, const float (&rv)[XT_HV], float (&v)[XT_HV]) {
-        const int j0 = mode0(cch);
-#pragma unroll
-        for (int i = 0; i < XT_HV / 2; ++i) {
-            const float k = tk[j0 + i];
-            v[2 * i] = -k * rv[2 * i + 1];
-            v[2 * i + 1] = k * rv[2 * i];
+            for (int k = 0; k < 5; ++k) hsum[r][k] = s[k];
         }
-    });
-    // ---- y = u r_x into T0
-#pragma unroll 1
-    for (int cch = 0; cch < Cfg::NCH; ++cch) {
-        float u[XT_HV], rx[XT_HV];
-        tld(lane_base + cch * XT_KC, u);
-        tld(lane_base + N + cch * XT_KC, rx);
-#pragma unroll
-        for (int i = 0; i < XT_HV; ++i) u[i] *= rx[i];
-        tst(lane_base + cch * XT_KC, u);
-    }
-    tc::wait_st();
-    epilogue_done();
-    // ---- G4: p^ = y E
-    product(3, fetch_t0, [&](int, const float (&b)[XT_HV], float (&v)[XT_HV]) {
-#pragma unroll
-        for (int i = 0; i < XT_HV; ++i) v[i] = b[i];
-    });
-    // ---- A^ = p^ - a_j r^ (r^ of the next chunk in flight)
-    {
-        auto fr = fetch_row(Rrow);
-        float rv[XT_HV], rn[XT_HV];
-        fr(0, rv);
-#pragma unroll 1
-        for (int cch = 0; cch < Cfg::NCH; ++cch) {
-            if (cch + 1 < Cfg::NCH) fr(cch + 1, rn);
-            float ph[XT_HV];
-            tld(lane_base + N + cch * XT_KC, ph);
+        // ---- G3: r_x = (i k r^) C   (r^ as just written by this thread)
+        product(fetch_row(Rrow), no_wait, [&](int cch, const unsigned (&rb)[XT_HV], float (&v)[XT_HV]) {
             const int j0 = mode0(cch);
 #pragma unroll
             for (int i = 0; i < XT_HV / 2; ++i) {
-                const int j = j0 + i;
-                const float a = ta[j];
-                cpx<float> av = project(cpx<float>{ph[2 * i] - a * rv[2 * i], ph[2 * i + 1] - a * rv[2 * i + 1]}, j, c.sym);
-                if (j == 0) av.y = 0.f;
-                ph[2 * i] = av.x;
-                ph[2 * i + 1] = av.y;
+                const float k = tk[j0 + i];
+                v[2 * i] = -k * __uint_as_float(rb[2 * i + 1]);
+                v[2 * i + 1] = k * __uint_as_float(rb[2 * i]);
             }
-            if (has) st_half(Arow + cch * XT_KC, ph);
+        });
+        // ---- y = u r_x into T0 (the next chunk's columns in flight)
+        {
+            auto step = [&](int cch, const unsigned (&ua)[XT_HV], const unsigned (&xa)[XT_HV]) {
+                float y[XT_HV];
 #pragma unroll
-            for (int i = 0; i < XT_HV; ++i) rv[i] = rn[i];
+                for (int i = 0; i < XT_HV; ++i) y[i] = __uint_as_float(ua[i]) * __uint_as_float(xa[i]);
+                tst(lane_base + cch * XT_KC, y);
+            };
+            unsigned u0[XT_HV], x0[XT_HV], u1[XT_HV], x1[XT_HV];
+            tld_issue(lane_base, u0);
+            tld_issue(lane_base + N, x0);
+#pragma unroll 1
+            for (int cch = 0; cch < Cfg::NCH; cch += 2) {
+                tld_wait(u0, x0);
+                tld_issue(lane_base + (cch + 1) * XT_KC, u1);
+                tld_issue(lane_base + N + (cch + 1) * XT_KC, x1);
+                step(cch, u0, x0);
+                tld_wait(u1, x1);
+                if (cch + 2 < Cfg::NCH) {
+                    tld_issue(lane_base + (cch + 2) * XT_KC, u0);
+                    tld_issue(lane_base + N + (cch + 2) * XT_KC, x0);
+                }
+                step(cch + 1, u1, x1);
+            }
+            tc::wait_st();
         }
+        // ---- G4: p^ = y E
+        product(fetch_t0, wait_t, [&](int, const unsigned (&b)[XT_HV], float (&v)[XT_HV]) {
+#pragma unroll
+            for (int i = 0; i < XT_HV; ++i) v[i] = __uint_as_float(b[i]);
+        });
+        // ---- A^ = p^ - a_j r^ (the next chunk's r^ and columns in flight)
+        {
+            auto fr = fetch_row(Rrow);
+            auto step = [&](int cch, const unsigned (&rb)[XT_HV], const unsigned (&pr)[XT_HV]) {
+                float ph[XT_HV];
+                const int j0 = mode0(cch);
+#pragma unroll
+                for (int i = 0; i < XT_HV / 2; ++i) {
+                    const int j = j0 + i;
+                    const float a = ta[j];
+                    cpx<float> av = project(cpx<float>{__uint_as_float(pr[2 * i]) - a * __uint_as_float(rb[2 * i]),
+                                                       __uint_as_float(pr[2 * i + 1]) - a * __uint_as_float(rb[2 * i + 1])},
+                                            j, c.sym);
+                    if (j == 0) av.y = 0.f;
+                    ph[2 * i] = av.x;
+                    ph[2 * i + 1] = av.y;
+                }
+                if (has) st_half(Arow + cch * XT_KC, ph);
+            };
+            unsigned r0[XT_HV], p0[XT_HV], r1[XT_HV], p1[XT_HV];
+            fr(0, r0);
+            tld_issue(lane_base + N, p0);
+#pragma unroll 1
+            for (int cch = 0; cch < Cfg::NCH; cch += 2) {
+                tld_wait(p0);
+                fr(cch + 1, r1);
+                tld_issue(lane_base + N + (cch + 1) * XT_KC, p1);
+                step(cch, r0, p0);
+                tld_wait(p1);
+                if (cch + 2 < Cfg::NCH) {
+                    fr(cch + 2, r0);
+                    tld_issue(lane_base + N + (cch + 2) * XT_KC, p0);
+                }
+                step(cch + 1, r1, p1);
+            }
+        }
+        tc::fence_before();
     }
 
-    // ---- drain (only after a wait gave up: copies may still be landing), free TMEM
-    tc::fence_before();
+    // ---- every product is done and every TMEM access complete: free TMEM
     __syncthreads();
-    if (bad && tid == 0) {
-        for (int qq = waited_b + 1; qq <= issued_b; ++qq) tc::bar_wait(&full_b[qq % XT_BSTAGES], (qq / XT_BSTAGES) & 1);
-        tc::bar_wait(&mma_done[(Cfg::QTOT - 1) % XT_BSTAGES], ((Cfg::QTOT - 1) / XT_BSTAGES) & 1);
-        atomicExch(&sc->err, 4);
-    }
-    __syncthreads();
+    tc::fence_after();
     if (warp == 0)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(Cfg::TMEM_COLS) : "memory");
 
@@ -456,7 +556,7 @@ __global__ void __launch_bounds__(XT_THREADS, 1) k_rows_tc(CurveDev c, int mode,
     if (tid < 5) {
         double tt = 0.0;
 #pragma unroll
-        for (int w = 0; w < XT_THREADS / 32; ++w) tt += wpart[w][tid];
+        for (int w = 0; w < NW; ++w) tt += wpart[w][tid];
         c.bpart[(size_t)blk * 5 + tid] = tt;
     }
     // ---- last CTA: the FP64 reduction over the CTAs' partial sums

@@ -99,10 +99,12 @@ def test_gradient_matches_the_oracle(setup, precision, tol, gtol):
     u = torch.tensor(X[1:-1], dtype=dt, device="cuda", requires_grad=True)
     lam = torch.tensor(1.0, dtype=torch.float64, device="cuda", requires_grad=True)
     J2 = cost(u, lam)
-    assert abs(J2.item() - sc["J2"]) <= tol * sc["J2"]
     J2.backward()
-    assert _precond_rel(u.grad.double().cpu().numpy(), G, w, spec) < gtol
-    assert abs(lam.grad.item() - sc["dJ2_dlambda"]) <= tol * abs(sc["dJ2_dlambda"])
+    ej = abs(J2.item() - sc["J2"]) / sc["J2"]
+    eg = _precond_rel(u.grad.double().cpu().numpy(), G, w, spec)
+    el = abs(lam.grad.item() - sc["dJ2_dlambda"]) / abs(sc["dJ2_dlambda"])
+    print("AUTOGRAD %s: J2=%.3e grad=%.3e dJdl=%.3e" % (precision, ej, eg, el))
+    assert ej <= tol and eg < gtol and el <= tol
     cost.curve.close()
 
 
