@@ -311,6 +311,24 @@ def run_batch(args):
     torch.cuda.synchronize(dev)
     clk = clocks.stop()
     ms = e0.elapsed_time(e1)
+    fp64 = None
+    if not args.no_context:
+        # the same batch in FP64 (storage, transforms and reductions), tuned and timed alike
+        b64 = KSBatch(specs, [i[0][0] for i in ins], [i[0][1] for i in ins], precision="fp64", conv="jrel",
+                      device=dev)
+        b64.init_trial(np.array([i[1][0] for i in ins]), [i[1][1] for i in ins])
+        t64 = b64.autotune(8)
+        b64.descend_async(args.warmup)
+        torch.cuda.synchronize(dev)
+        e0.record()
+        b64.descend_async(args.steps)
+        e1.record()
+        torch.cuda.synchronize(dev)
+        ms64 = e0.elapsed_time(e1)
+        b64.close()
+        fp64 = {"ms_per_step": ms64 / args.steps, "value": sum(s.M for s in specs) * args.steps / (ms64 / 1e3),
+                "unit": UNIT, "fp32_speedup": ms64 / ms,
+                "tuning": {k: (v if k != "splits" else {str(a): b2 for a, b2 in v.items()}) for k, v in t64.items()}}
     points = sum(s.M for s in specs)
     flops = sum(s.M * sum(flops_per_point(s.N, s.M)) for s in specs)
     nsm = torch.cuda.get_device_properties(dev).multi_processor_count
@@ -326,7 +344,7 @@ def run_batch(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": "batch of 256 KSE curves, L~U[20,60], N_x in {32,64,128}, N_s~U[256,2048]",
-                       "curves": len(specs), "points_per_step": points, "tuning": chosen,
+                       "curves": len(specs), "points_per_step": points, "tuning": {k: (v if k != "splits" else {str(a): b2 for a, b2 in v.items()}) for k, v in chosen.items()},
                        "l2": "working set ~0.4 GB > L2; steps back to back (CUDA-graph replay)"},
             "roofline": {"bound": "hbm", "achieved": hbm_ach, "peak": hbm_peak, "unit": "GB/s",
                          "frac": hbm_ach / hbm_peak, "traffic": None, "peak_source": src,
@@ -335,7 +353,8 @@ def run_batch(args):
                          "alu": {"achieved": ach, "peak": peak_alu, "unit": "TFLOP/s", "frac": ach / peak_alu,
                                  "algorithmic_flops_per_step": flops}},
             "gpu_launches": None, "clocks": clk,
-            "median_J_rel": float(np.median([x["J"] / max(x["Dnorm"], 1e-300) for x in sc]))}
+            "median_J_rel": float(np.median([x["J"] / max(x["Dnorm"], 1e-300) for x in sc])),
+            "fp64_batch": fp64}
     print(json.dumps(line))
     b.close()
     return 0

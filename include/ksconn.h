@@ -317,10 +317,29 @@ ks_status ks_batch_scalars(ks_batch *b, ks_scalars *out);
 /* Physical state of curve i, [N_s,i][N_i] in the storage type.  Asynchronous. */
 ks_status ks_batch_get_state(ks_batch *b, int32_t i, void *u_dev);
 
-/* Times `steps` descent steps of the batch for each candidate s-phase tile width
- * (64 or 32 columns per CTA for curves with N >= 64) and keeps the faster one
- * (*chosen, may be NULL).  The timed steps are real descent steps.  Synchronises. */
+/* Tunes the batch's launch shapes by timing `steps` real descent steps of every
+ * curve per candidate (the timed steps count in each curve's step counter and
+ * tau), one knob after the other, keeping the fastest:
+ *   1. sections per CTA of the row phase: 8 or 16;
+ *   2. for each transform length F of the four-step curves (the batched FFT form
+ *      from F = 1024 on), the split F = F1 F2 of its line transforms: 32 x 32;
+ *      64 x 32 or 32 x 64; 64 x 64, 128 x 32 or 32 x 128; 128 x 64 (the kernel
+ *      spectrum and twiddles are recomputed for the split);
+ *   3. for dense-form curves with N >= 64, the s-phase tile width: 64 or 32 columns.
+ * *chosen (may be NULL) receives the sections per row CTA; ks_batch_get_tuning
+ * reports every choice.  Synchronises. */
 ks_status ks_batch_autotune(ks_batch *b, int32_t steps, int32_t *chosen);
+
+typedef struct {
+    int32_t row_sections;   /* sections per row-phase CTA */
+    int32_t dense_tile;     /* s-phase tile width of dense-form curves (0: per-curve default) */
+    int32_t nlen;           /* transform lengths of the four-step curves (at most 8 listed) */
+    int32_t F[8], F1[8];    /* each length F and its split F = F1 (F / F1) */
+    double ms_per_step;     /* a batch step with these choices, as the autotuner timed it (0 before) */
+} ks_batch_tuning;
+
+/* The batch's current launch-shape choices (defaults before ks_batch_autotune). */
+ks_status ks_batch_get_tuning(ks_batch *b, ks_batch_tuning *out);
 
 ks_status ks_batch_destroy(ks_batch *b);
 

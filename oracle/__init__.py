@@ -69,7 +69,8 @@ def _load():
             "ko_curve_adjoint": (None, [i, i, d, d, d, i, p, p, p, p]),
             "ko_curve_scalars": (None, [i, i, d, d, d, p, p, p, p]),
             "ko_curve_norm2_W": (d, [i, i, d, d, p]),
-            "ko_curve_descend": (l, [i, i, d, d, d, i, d, d, i, l, d, i, p, p, p]),
+            "ko_curve_descend": (l, [i, i, d, d, d, i, d, d, i, i, l, d, i, p, p, p]),
+            "ko_implicit_update": (None, [i, i, d, d, d, d, p, p]),
             "ko_curve_init": (None, [i, i, d, d, p, p, d, p, i, p, p, p]),
             "ko_newton_odd": (i, [i, d, p, i, d, p]),
             "ko_jacobian_zero_mean": (None, [i, d, p, p]),
@@ -258,9 +259,14 @@ def curve_norm2_W(X, L, S):
 CONV_JARC, CONV_J, CONV_JREL = 0, 1, 2
 
 
+IMEX_X, IMPLICIT = 0, 1
+
+
 def curve_descend(U, L, S, nsteps, dtau=0.01, lam=1.0, lambda_free=False, dtau_lambda=0.0,
-                  mode=PAPER, tol=0.0, conv=CONV_JARC, history=False):
-    """Runs the descent in place on a copy of U.
+                  mode=PAPER, tol=0.0, conv=CONV_JARC, history=False, scheme=IMEX_X):
+    """Runs the descent in place on a copy of U.  scheme IMEX_X takes only the
+    diagonal -a_j^2 u term of G implicitly; IMPLICIT every linear term
+    (lambda^2 Dt~^2 - a_j^2) u, by a dense LU solve per spatial mode.
 
     Returns (U_final, steps_done, scalars dict, history array [steps+1, 6] or None).
     """
@@ -269,11 +275,21 @@ def curve_descend(U, L, S, nsteps, dtau=0.01, lam=1.0, lambda_free=False, dtau_l
     hist = np.zeros((nsteps + 1, 6)) if history else None
     out = np.zeros(5)
     steps = _load().ko_curve_descend(M, N, L, S, lam, int(bool(lambda_free)), dtau, dtau_lambda,
-                                     mode, int(nsteps), tol, conv, _ptr(U), _ptr(hist), _ptr(out))
+                                     mode, int(scheme), int(nsteps), tol, conv, _ptr(U), _ptr(hist), _ptr(out))
     sc = dict(J=out[0], J_arc=out[1], dJ2_dlambda=out[2], G=out[3], lam=out[4])
     if hist is not None:
         hist = hist[: steps + 1]
     return U, int(steps), sc, hist
+
+
+def implicit_update(U, G, L, S, dtau, lam=1.0):
+    """One full-linear-implicit increment of the interior rows of a copy of U:
+    (I (1 + dtau a_j^2) - dtau lam^2 Dt~^2) delta_j = dtau G_j, U + delta."""
+    U, M, N = _curve(U)
+    U = U.copy()
+    G = _c(G, np.complex128)
+    _load().ko_implicit_update(M, N, L, S, dtau, lam, _ptr(G), _ptr(U))
+    return U
 
 
 def curve_init(M, S, up, um, s0=0.0, a=0.0, v=None, amps=None, vp=None):

@@ -528,15 +528,144 @@ double ko_curve_norm2_W(int M, int N, double L, double S, const cplx *X)
 }
 
 /* ------------------------------------------------------------------------ */
+/* Full-linear-implicit stepping (Sec. V.C.3)                                */
+/* ------------------------------------------------------------------------ */
+/*
+ * The paper steps the descent by semi-implicit forward Euler, treating the
+ * terms of G that are linear in u implicitly.  On the interior rows the linear
+ * part of the paper's G (eq. KSE_G with r of eq. KSE_residual) is
+ *     Lin_j u = (lambda^2 Dt~^2 - a_j^2) u,    a_j = k_j^4 - k_j^2,
+ * per spatial mode j, where Dt~ is the interior block (rows and columns
+ * 1..M) of the matrix of eq. rational_diff_matrix: the end rows of u are
+ * fixed and r's end rows are zero.  The step
+ *     (I - dtau Lin_j) u_new = u + dtau (G(u) - Lin_j u)
+ * is taken in its equivalent increment form
+ *     (I (1 + dtau a_j^2) - dtau lambda^2 Dt~^2) delta_j = dtau G_j,
+ *     u_new = u + delta,
+ * by an LU factorisation with partial pivoting of each mode's M x M matrix
+ * (factored once per (dtau, lambda)).  With the discrete adjoint the same
+ * operator is applied to its G.
+ */
+typedef struct {
+    int M, H;
+    double L, dtau, lambda;
+    double *D2;   /* Dt~^2, M x M row-major */
+    double *F;    /* H LU factors, M x M each */
+    int *piv;     /* H x M row interchanges */
+} implicit_ops;
+
+static implicit_ops *implicit_new(int M, int H, double L, double S)
+{
+    int P = M + 1;
+    implicit_ops *im = calloc(1, sizeof(implicit_ops));
+    im->M = M; im->H = H; im->L = L; im->dtau = -1.0; im->lambda = 0.0;
+    double *Dfull = malloc(sizeof(double) * (size_t)(P + 1) * (P + 1));
+    ko_dt_matrix(M, S, Dfull);
+    im->D2 = calloc((size_t)M * M, sizeof(double));
+#pragma omp parallel for schedule(static)
+    for (int i = 0; i < M; ++i)
+        for (int k = 0; k < M; ++k) {
+            double acc = 0.0;
+            for (int l = 0; l < M; ++l)
+                acc += Dfull[(long)(i + 1) * (P + 1) + (l + 1)] * Dfull[(long)(l + 1) * (P + 1) + (k + 1)];
+            im->D2[(long)i * M + k] = acc;
+        }
+    free(Dfull);
+    im->F = malloc(sizeof(double) * (size_t)H * M * M);
+    im->piv = malloc(sizeof(int) * (size_t)H * M);
+    return im;
+}
+
+static void implicit_free(implicit_ops *im)
+{
+    if (!im) return;
+    free(im->D2); free(im->F); free(im->piv); free(im);
+}
+
+/* Gaussian elimination with partial pivoting, in place: the multipliers below
+ * the diagonal, U on and above it, piv[c] the row swapped into row c. */
+static void lu_factor(int n, double *A, int *piv)
+{
+    for (int c = 0; c < n; ++c) {
+        int p = c;
+        for (int r = c + 1; r < n; ++r)
+            if (fabs(A[(long)r * n + c]) > fabs(A[(long)p * n + c])) p = r;
+        piv[c] = p;
+        if (p != c)
+            for (int k = 0; k < n; ++k) {
+                double t = A[(long)c * n + k];
+                A[(long)c * n + k] = A[(long)p * n + k];
+                A[(long)p * n + k] = t;
+            }
+        for (int r = c + 1; r < n; ++r) {
+            double f = A[(long)r * n + c] / A[(long)c * n + c];
+            A[(long)r * n + c] = f;
+            for (int k = c + 1; k < n; ++k) A[(long)r * n + k] -= f * A[(long)c * n + k];
+        }
+    }
+}
+
+/* Solves with the factors of lu_factor: row interchanges, L y = b, U x = y. */
+static void lu_apply(int n, const double *A, const int *piv, double *b)
+{
+    for (int c = 0; c < n; ++c) {
+        double t = b[c]; b[c] = b[piv[c]]; b[piv[c]] = t;
+    }
+    for (int r = 0; r < n; ++r) {
+        double acc = b[r];
+        for (int c = 0; c < r; ++c) acc -= A[(long)r * n + c] * b[c];
+        b[r] = acc;
+    }
+    for (int r = n - 1; r >= 0; --r) {
+        double acc = b[r];
+        for (int k = r + 1; k < n; ++k) acc -= A[(long)r * n + k] * b[k];
+        b[r] = acc / A[(long)r * n + r];
+    }
+}
+
+static void implicit_update(implicit_ops *im, double dtau, double lambda, const cplx *G, cplx *U)
+{
+    const int M = im->M, H = im->H;
+    if (im->dtau != dtau || im->lambda != lambda) {
+#pragma omp parallel for schedule(dynamic)
+        for (int j = 0; j < H; ++j) {
+            double a = pow(kwave(j, im->L), 4) - pow(kwave(j, im->L), 2);
+            double *A = im->F + (size_t)j * M * M;
+            for (int i = 0; i < M; ++i)
+                for (int k = 0; k < M; ++k)
+                    A[(long)i * M + k] = (i == k ? 1.0 + dtau * a * a : 0.0) - dtau * lambda * lambda * im->D2[(long)i * M + k];
+            lu_factor(M, A, im->piv + (size_t)j * M);
+        }
+        im->dtau = dtau;
+        im->lambda = lambda;
+    }
+#pragma omp parallel for schedule(dynamic)
+    for (int j = 0; j < H; ++j) {
+        double *re = malloc(sizeof(double) * M), *imv = malloc(sizeof(double) * M);
+        for (int i = 0; i < M; ++i) {
+            cplx g = G[(long)(i + 1) * H + j];
+            re[i] = dtau * creal(g);
+            imv[i] = dtau * cimag(g);
+        }
+        lu_apply(M, im->F + (size_t)j * M * M, im->piv + (size_t)j * M, re);
+        lu_apply(M, im->F + (size_t)j * M * M, im->piv + (size_t)j * M, imv);
+        for (int i = 0; i < M; ++i) U[(long)(i + 1) * H + j] += re[i] + I * imv[i];
+        free(re);
+        free(imv);
+    }
+}
+
+/* ------------------------------------------------------------------------ */
 /* Descent in fictitious time (Sec. III, Sec. V.C.3)                         */
 /* ------------------------------------------------------------------------ */
 
-/* Semi-implicit forward Euler for du/dtau = G (Sec. V.C.3).  The term of G
- * that is linear in u and diagonal in Fourier space, -A^2 u with
- * A = d_xx + d_xxxx (symbol a_j = k_j^4 - k_j^2), is taken at the new level;
- * the rest of G at the old level:
+/* Semi-implicit forward Euler for du/dtau = G (Sec. V.C.3).
+ * scheme 0: the term of G that is linear in u and diagonal in Fourier space,
+ * -A^2 u with A = d_xx + d_xxxx (symbol a_j = k_j^4 - k_j^2), is taken at the
+ * new level, the rest of G at the old level:
  *   u^{n+1} = [u^n + dtau (G(u^n) + a_j^2 u^n)] / (1 + dtau a_j^2)
  * for the interior rows; the end rows stay at u_+-.
+ * scheme 1: every linear term of G at the new level (implicit_update above).
  * conv: 0 stop when J_arc < tol, 1 when J < tol, 2 when J/|lambda D_t u|_W < tol;
  * tol <= 0 never stops early.
  * hist (optional) [nsteps+1][6]: (step, tau, J, J_arc, |G|_W, lambda) of the
@@ -545,7 +674,7 @@ double ko_curve_norm2_W(int M, int N, double L, double S, const cplx *X)
  * (the cost and lambda-gradient of the returned state; |G| of the last step).
  * Returns the number of updates applied. */
 long ko_curve_descend(int M, int N, double L, double S, double lambda, int lambda_free,
-                      double dtau, double dtau_lambda, int mode, long nsteps, double tol,
+                      double dtau, double dtau_lambda, int mode, int scheme, long nsteps, double tol,
                       int conv, cplx *U, double *hist, double *out)
 {
     int P = M + 1, H = N / 2;
@@ -555,6 +684,7 @@ long ko_curve_descend(int M, int N, double L, double S, double lambda, int lambd
     cplx *G = malloc(sizeof(cplx) * sz);
     double sc[5] = {0, 0, 0, 0, 0}, gnorm = 0.0;
     long step = 0;
+    implicit_ops *im = (scheme == 1) ? implicit_new(M, H, L, S) : NULL;
     for (;;) {
         ko_curve_residual(M, N, L, S, lambda, U, R, D);
         ko_curve_scalars(M, N, L, S, lambda, R, D, NULL, sc);
@@ -568,12 +698,16 @@ long ko_curve_descend(int M, int N, double L, double S, double lambda, int lambd
         if (step >= nsteps || (tol > 0 && crit < tol)) break;
         ko_curve_adjoint(M, N, L, S, lambda, mode, U, R, G, NULL);
         gnorm = sqrt(ko_curve_norm2_W(M, N, L, S, G));
-        for (int m = 1; m <= M; ++m)
-            for (int j = 0; j < H; ++j) {
-                double a = pow(kwave(j, L), 4) - pow(kwave(j, L), 2);
-                long i = (long)m * H + j;
-                U[i] = (U[i] + dtau * (G[i] + a * a * U[i])) / (1.0 + dtau * a * a);
-            }
+        if (im) {
+            implicit_update(im, dtau, lambda, G, U);
+        } else {
+            for (int m = 1; m <= M; ++m)
+                for (int j = 0; j < H; ++j) {
+                    double a = pow(kwave(j, L), 4) - pow(kwave(j, L), 2);
+                    long i = (long)m * H + j;
+                    U[i] = (U[i] + dtau * (G[i] + a * a * U[i])) / (1.0 + dtau * a * a);
+                }
+        }
         if (lambda_free) lambda -= dtau_lambda * sc[2];
         ++step;
     }
@@ -585,7 +719,17 @@ long ko_curve_descend(int M, int N, double L, double S, double lambda, int lambd
     free(R);
     free(D);
     free(G);
+    implicit_free(im);
     return step;
+}
+
+/* One full-linear-implicit update of the interior rows, for tests of a single
+ * step: U += delta with (I (1 + dtau a_j^2) - dtau lambda^2 Dt~^2) delta_j = dtau G_j. */
+void ko_implicit_update(int M, int N, double L, double S, double dtau, double lambda, const cplx *G, cplx *U)
+{
+    implicit_ops *im = implicit_new(M, N / 2, L, S);
+    implicit_update(im, dtau, lambda, G, U);
+    implicit_free(im);
 }
 
 /* ------------------------------------------------------------------------ */

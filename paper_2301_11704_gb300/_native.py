@@ -24,7 +24,8 @@ EXPORTS = [
     "ks_curve_descend_async", "ks_curve_scalars", "ks_curve_get_state", "ks_curve_set_state", "ks_curve_profile",
     "ks_curve_profile_read", "ks_curve_debug_wait_limit", "ks_curve_destroy", "ks_cost_noalloc",
     "ks_batch_workspace_bytes", "ks_batch_create", "ks_batch_init_trial", "ks_batch_descend",
-    "ks_batch_descend_async", "ks_batch_scalars", "ks_batch_get_state", "ks_batch_autotune", "ks_batch_destroy",
+    "ks_batch_descend_async", "ks_batch_scalars", "ks_batch_get_state", "ks_batch_autotune", "ks_batch_get_tuning",
+    "ks_batch_destroy",
 ]
 
 
@@ -71,6 +72,11 @@ class KSProfile(ctypes.Structure):
     _fields_ = [("ms", ctypes.c_double * 3), ("launches", ctypes.c_int64 * 3), ("step_ms", ctypes.c_double),
                 ("step_launches", ctypes.c_int64), ("step_steps", ctypes.c_int64),
                 ("pass_ms", (ctypes.c_double * 3) * 2), ("pass_launches", (ctypes.c_int64 * 3) * 2)]
+
+
+class KSBatchTuning(ctypes.Structure):
+    _fields_ = [("row_sections", ctypes.c_int32), ("dense_tile", ctypes.c_int32), ("nlen", ctypes.c_int32),
+                ("F", ctypes.c_int32 * 8), ("F1", ctypes.c_int32 * 8), ("ms_per_step", ctypes.c_double)]
 
 
 class KSError(RuntimeError):
@@ -128,6 +134,7 @@ def load(build_if_missing: bool = True):
         "ks_batch_scalars": (i32, [p, ctypes.POINTER(KSScalars)]),
         "ks_batch_get_state": (i32, [p, i32, p]),
         "ks_batch_autotune": (i32, [p, i32, ctypes.POINTER(i32)]),
+        "ks_batch_get_tuning": (i32, [p, ctypes.POINTER(KSBatchTuning)]),
         "ks_batch_destroy": (i32, [p]),
     }
     for name, (res, args) in sigs.items():

@@ -80,10 +80,20 @@ class KSBatch:
         self.stream.synchronize()
         return out
 
-    def autotune(self, steps: int = 8) -> int:
+    def autotune(self, steps: int = 8) -> dict:
+        """Tunes the launch shapes (sections per row CTA, the four-step split of each
+        transform length, the dense tile width) on real descent steps; returns the
+        choices (see tuning())."""
         chosen = ctypes.c_int32()
         check(self.lib.ks_batch_autotune(self.handle, int(steps), ctypes.byref(chosen)))
-        return chosen.value
+        return self.tuning()
+
+    def tuning(self) -> dict:
+        t = _native.KSBatchTuning()
+        check(self.lib.ks_batch_get_tuning(self.handle, ctypes.byref(t)))
+        return dict(row_sections=t.row_sections, dense_tile=t.dense_tile,
+                    splits={int(t.F[i]): (int(t.F1[i]), int(t.F[i] // t.F1[i])) for i in range(t.nlen)},
+                    ms_per_step=t.ms_per_step)
 
     def close(self):
         if getattr(self, "handle", None) is not None:

@@ -16,9 +16,10 @@ namespace {
 const int BATCH_GRAPH_STEPS = 16;
 
 struct Group {
-    int key;              // N (rows) or tile width (s-phase)
+    int key;              // N (rows), tile width (dense s-phase) or F (FFT s-phase)
     size_t off;           // offset of the item list in the item area
     int count;
+    int sub = 0;          // FFT s-phase: F1 of the split F = F1 (F / F1)
 };
 
 }  // namespace
@@ -38,6 +39,8 @@ struct ks_batch {
     std::vector<Group> rows, dts;
     std::vector<Group> ffts;            // (curve, mode) items of the FFT-form curves, one group per F
     int tile_pref = 0;                  // 0: per-curve default, 32 or 64: forced (autotuner)
+    int row_warps = ks::ROWS_WARPS;     // warps per row-phase CTA (two sections each): 4 or 8 (autotuner)
+    float tuned_ms = 0.f;               // the autotuner's time of a step with its choice
     cudaGraphExec_t gexec = nullptr;
     cudaStream_t gstream = nullptr;
 };
@@ -81,12 +84,14 @@ ks_status build_items(ks_batch *b)
 {
     std::map<int, std::vector<int2>> rows;
     std::map<int, std::vector<int4>> dts;
-    std::map<int, std::vector<int2>> fft;   // by F: each group launched with its own shared memory
+    std::map<std::pair<int, int>, std::vector<int2>> fft;   // by (F, F1): each group launched with its own shared memory
     for (int i = 0; i < b->nb; ++i) {
         ks::CurveDev &c = b->cv[i];
+        const int rs = 2 * b->row_warps;
+        c.row_blocks = (c.ns + rs - 1) / rs;
         for (int k = 0; k < c.row_blocks; ++k) rows[c.nx].push_back(make_int2(i, k));
         if (c.F > 0) {
-            for (int jm = 0; jm < c.nx / 2; ++jm) fft[c.F].push_back(make_int2(i, jm));
+            for (int jm = 0; jm < c.nx / 2; ++jm) fft[std::make_pair(c.F, c.f4b ? c.F1 : 0)].push_back(make_int2(i, jm));
             continue;
         }
         const int bn = b->tile_pref ? (c.nx < 64 ? 32 : b->tile_pref) : (c.nx >= 64 ? 64 : 32);
@@ -115,7 +120,7 @@ ks_status build_items(ks_batch *b)
     o = al256(o);
     b->ffts.clear();
     for (auto it = fft.rbegin(); it != fft.rend(); ++it) {   // largest F (longest CTAs) first
-        b->ffts.push_back({it->first, o, (int)it->second.size()});
+        b->ffts.push_back({it->first.first, o, (int)it->second.size(), it->first.second});
         memcpy(host.data() + o, it->second.data(), it->second.size() * sizeof(int2));
         o += it->second.size() * sizeof(int2);
     }
@@ -137,8 +142,8 @@ ks_status build_items(ks_batch *b)
 static cudaError_t launch_fft_group(const ks_batch *b, const Group &g, int mode, int discrete, cudaStream_t st)
 {
     const int2 *items = (const int2 *)(b->items_dev + g.off);
-    if (g.key >= ks::F4B_FMIN)
-        return ks::launch_f4b_batch(b->prec, g.key, b->cv_dev, items, g.count, mode, discrete, 1, st);
+    if (g.sub > 0)
+        return ks::launch_f4b_batch(b->prec, g.sub, g.key / g.sub, b->cv_dev, items, g.count, mode, discrete, 1, st);
     return ks::launch_sconv_batch(b->prec, g.key, b->cv_dev, items, g.count, mode, discrete, 1, st);
 }
 
@@ -147,7 +152,7 @@ ks_status launch_step(ks_batch *b, cudaStream_t st)
     cudaError_t e = cudaSuccess;
     for (const Group &g : b->rows)
         if (e == cudaSuccess)
-            e = ks::launch_rows_batch(b->prec, g.key, b->cv_dev, (const int2 *)(b->items_dev + g.off), g.count,
+            e = ks::launch_rows_batch(b->prec, g.key, b->row_warps, b->cv_dev, (const int2 *)(b->items_dev + g.off), g.count,
                                       ks::ROWS_STEP, st);
     for (const Group &g : b->dts)
         if (e == cudaSuccess)
@@ -230,7 +235,7 @@ ks_status eval_all(ks_batch *b)
     cudaError_t e = cudaSuccess;
     for (const Group &g : b->rows)
         if (e == cudaSuccess)
-            e = ks::launch_rows_batch(b->prec, g.key, b->cv_dev, (const int2 *)(b->items_dev + g.off), g.count,
+            e = ks::launch_rows_batch(b->prec, g.key, b->row_warps, b->cv_dev, (const int2 *)(b->items_dev + g.off), g.count,
                                       ks::ROWS_EVAL, b->st);
     if (e != cudaSuccess) return ks::report_error(KS_ECUDA, "batched evaluation: %s", cudaGetErrorString(e));
     return KS_OK;
@@ -404,40 +409,104 @@ ks_status ks_batch_get_state(ks_batch *b, int32_t i, void *u_dev)
 ks_status ks_batch_autotune(ks_batch *b, int32_t steps, int32_t *chosen)
 {
     if (!b || steps <= 0) return ks::report_error(KS_EINVAL, "batch handle required and steps > 0");
-    // candidates: the s-phase tile width of curves with N >= 64 (64 or 32 columns per CTA)
-    const int cand[2] = {64, 32};
-    float best = 1e30f;
-    int best_c = 64;
-    cudaEvent_t e0, e1;
-    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        if (e0) cudaEventDestroy(e0);
         return ks::report_error(KS_ECUDA, "autotune events");
-    // the timed trial steps are real descent steps of every curve (they count in
-    // each curve's step counter and tau)
-    ks_status s = KS_OK;
-    for (int k = 0; k < 2 && s == KS_OK; ++k) {
-        b->tile_pref = cand[k];
-        s = build_items(b);
-        if (s != KS_OK) break;
-        s = enqueue(b, 2, 0.0);                                      // warm-up
-        if (s != KS_OK) break;
-        cudaEventRecord(e0, b->st);
-        s = enqueue(b, steps, 0.0);
-        cudaEventRecord(e1, b->st);
-        cudaEventSynchronize(e1);
-        float ms = 0.f;
-        cudaEventElapsedTime(&ms, e0, e1);
-        if (ms < best) {
-            best = ms;
-            best_c = cand[k];
+    }
+    // time of `steps` real descent steps of every curve with the current knobs (the
+    // trial steps count in each curve's step counter and tau)
+    auto time_steps = [&](float *ms) -> ks_status {
+        ks_status s = build_items(b);
+        if (s == KS_OK) s = enqueue(b, 2, 0.0);   // warm-up (and the graph for these items)
+        if (s != KS_OK) return s;
+        cudaError_t e = cudaEventRecord(e0, b->st);
+        if (e == cudaSuccess) {
+            s = enqueue(b, steps, 0.0);
+            if (s != KS_OK) return s;
+            e = cudaEventRecord(e1, b->st);
         }
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(ms, e0, e1);
+        if (e != cudaSuccess) return ks::report_error(KS_ECUDA, "autotune timing: %s", cudaGetErrorString(e));
+        return KS_OK;
+    };
+    // the split F = F1 (F / F1) of every four-step curve of length F, with its tables
+    auto set_split = [&](int F, int f1) -> ks_status {
+        for (int i = 0; i < b->nb; ++i) {
+            ks::CurveDev &c = b->cv[i];
+            if (!c.f4b || c.F != F || c.F1 == f1) continue;
+            c.F1 = f1;
+            c.F2 = F / f1;
+            cudaError_t e = ks::launch_setup_f4(c, b->st);
+            if (e != cudaSuccess) return ks::report_error(KS_ECUDA, "autotune set-up: %s", cudaGetErrorString(e));
+        }
+        return KS_OK;
+    };
+    ks_status s = KS_OK;
+    float best = 1e30f, ms = 0.f;
+    // knob 1: sections per row-phase CTA
+    int best_w = b->row_warps;
+    for (int w : {ks::ROWS_WARPS, 2 * ks::ROWS_WARPS}) {
+        b->row_warps = w;
+        if ((s = time_steps(&ms)) != KS_OK) break;
+        if (ms < best) { best = ms; best_w = w; }
+    }
+    b->row_warps = best_w;
+    // knob 2: the split of each length of the four-step curves
+    std::map<int, int> lens;   // F -> current F1
+    for (int i = 0; i < b->nb && s == KS_OK; ++i)
+        if (b->cv[i].f4b) lens[b->cv[i].F] = b->cv[i].F1;
+    for (auto &kv : lens) {
+        if (s != KS_OK) break;
+        int F1s[3];
+        const int n = ks::f4b_splits(kv.first, b->prec, F1s);
+        int best_f1 = kv.second;
+        for (int k = 0; k < n && s == KS_OK && n > 1; ++k) {
+            if ((s = set_split(kv.first, F1s[k])) != KS_OK) break;
+            if ((s = time_steps(&ms)) != KS_OK) break;
+            if (ms < best) { best = ms; best_f1 = F1s[k]; }
+        }
+        if (s == KS_OK) s = set_split(kv.first, best_f1);
+    }
+    // knob 3: the column tile of dense-form curves with N >= 64
+    bool dense = false;
+    for (int i = 0; i < b->nb; ++i) dense = dense || (b->cv[i].F == 0 && b->cv[i].nx >= 64);
+    if (dense && s == KS_OK) {
+        int best_t = b->tile_pref;
+        for (int t : {64, 32}) {
+            b->tile_pref = t;
+            if ((s = time_steps(&ms)) != KS_OK) break;
+            if (ms < best) { best = ms; best_t = t; }
+        }
+        b->tile_pref = best_t;
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (s != KS_OK) return s;
-    b->tile_pref = best_c;
+    b->tuned_ms = best / (float)steps;
     s = build_items(b);
-    if (chosen) *chosen = best_c;
+    if (chosen) *chosen = 2 * b->row_warps;
     return s;
+}
+
+ks_status ks_batch_get_tuning(ks_batch *b, ks_batch_tuning *out)
+{
+    if (!b || !out) return ks::report_error(KS_EINVAL, "batch handle and out are required");
+    *out = ks_batch_tuning{};
+    out->row_sections = 2 * b->row_warps;
+    out->dense_tile = b->tile_pref;
+    std::map<int, int> lens;
+    for (int i = 0; i < b->nb; ++i)
+        if (b->cv[i].f4b) lens[b->cv[i].F] = b->cv[i].F1;
+    for (auto &kv : lens) {
+        if (out->nlen >= 8) break;
+        out->F[out->nlen] = kv.first;
+        out->F1[out->nlen] = kv.second;
+        out->nlen++;
+    }
+    out->ms_per_step = b->tuned_ms;
+    return KS_OK;
 }
 
 ks_status ks_batch_destroy(ks_batch *b)

@@ -1427,22 +1427,29 @@ cudaError_t launch_f4(const CurveDev &c, int mode, int discrete, int gate, cudaS
 }
 
 // The one-CTA-per-mode form exists for the lengths a batched curve can have
-// (the one-CTA FFT form's range from F = 1024: up to 8192 in FP32, 4096 in FP64).
+// (from F = 1024 to 4096, and 8192 in FP32), each in the splits F = F1 F2 the
+// batch autotuner chooses from.
 template <typename T, typename Fn>
-static cudaError_t f4b_dispatch(int F, Fn &&fn)
+static cudaError_t f4b_dispatch(int F1, int F2, Fn &&fn)
 {
-    if (F == 1024) return fn(std::integral_constant<int, 32>(), std::integral_constant<int, 32>());
-    if (F == 2048) return fn(std::integral_constant<int, 64>(), std::integral_constant<int, 32>());
-    if (F == 4096) return fn(std::integral_constant<int, 64>(), std::integral_constant<int, 64>());
+    using I = std::integral_constant<int, 32>;
+    using J = std::integral_constant<int, 64>;
+    using K = std::integral_constant<int, 128>;
+    if (F1 == 32 && F2 == 32) return fn(I(), I());
+    if (F1 == 64 && F2 == 32) return fn(J(), I());
+    if (F1 == 32 && F2 == 64) return fn(I(), J());
+    if (F1 == 64 && F2 == 64) return fn(J(), J());
+    if (F1 == 128 && F2 == 32) return fn(K(), I());
+    if (F1 == 32 && F2 == 128) return fn(I(), K());
     if constexpr (sizeof(T) == 4)
-        if (F == 8192) return fn(std::integral_constant<int, 128>(), std::integral_constant<int, 64>());
+        if (F1 == 128 && F2 == 64) return fn(K(), J());
     return cudaErrorInvalidValue;
 }
 
 template <typename T>
 static cudaError_t f4b_run(const CurveDev &c, int mode, int discrete, int gate, cudaStream_t st)
 {
-    return f4b_dispatch<T>(c.F, [&](auto f1, auto f2) {
+    return f4b_dispatch<T>(c.F1, c.F2, [&](auto f1, auto f2) {
         constexpr int F1 = decltype(f1)::value, F2 = decltype(f2)::value;
         const size_t sm = F4B<T, F1, F2>::BYTES;
         cudaError_t e = set_smem(k_f4b<T, F1, F2>, sm);
@@ -1457,24 +1464,24 @@ cudaError_t launch_f4b(const CurveDev &c, int mode, int discrete, int gate, cuda
 }
 
 template <typename T>
-static cudaError_t f4b_batch_run(int F, const CurveDev *cv, const int2 *items, int nitems, int mode, int discrete,
-                                 int gate, cudaStream_t st)
+static cudaError_t f4b_batch_run(int F1, int F2, const CurveDev *cv, const int2 *items, int nitems, int mode,
+                                 int discrete, int gate, cudaStream_t st)
 {
-    return f4b_dispatch<T>(F, [&](auto f1, auto f2) {
-        constexpr int F1 = decltype(f1)::value, F2 = decltype(f2)::value;
-        const size_t sm = F4B<T, F1, F2>::BYTES;
-        cudaError_t e = set_smem(k_f4b_batch<T, F1, F2>, sm);
+    return f4b_dispatch<T>(F1, F2, [&](auto f1, auto f2) {
+        constexpr int G1 = decltype(f1)::value, G2 = decltype(f2)::value;
+        const size_t sm = F4B<T, G1, G2>::BYTES;
+        cudaError_t e = set_smem(k_f4b_batch<T, G1, G2>, sm);
         if (e != cudaSuccess) return e;
-        return launch_pdl(k_f4b_batch<T, F1, F2>, dim3(nitems), sm, st, cv, items, mode, discrete, gate);
+        return launch_pdl(k_f4b_batch<T, G1, G2>, dim3(nitems), sm, st, cv, items, mode, discrete, gate);
     });
 }
 
-cudaError_t launch_f4b_batch(int prec, int F, const CurveDev *cv, const int2 *items, int nitems, int mode,
+cudaError_t launch_f4b_batch(int prec, int F1, int F2, const CurveDev *cv, const int2 *items, int nitems, int mode,
                              int discrete, int gate, cudaStream_t st)
 {
     if (nitems <= 0) return cudaSuccess;
-    return prec ? f4b_batch_run<float>(F, cv, items, nitems, mode, discrete, gate, st)
-                : f4b_batch_run<double>(F, cv, items, nitems, mode, discrete, gate, st);
+    return prec ? f4b_batch_run<float>(F1, F2, cv, items, nitems, mode, discrete, gate, st)
+                : f4b_batch_run<double>(F1, F2, cv, items, nitems, mode, discrete, gate, st);
 }
 
 template <typename T, int F1, int F2>
@@ -1499,7 +1506,10 @@ static cudaError_t setup_dispatch(const CurveDev &c, cudaStream_t st)
 {
     if (c.F1 == 32 && c.F2 == 32) return setup_run<T, 32, 32>(c, st);
     if (c.F1 == 64 && c.F2 == 32) return setup_run<T, 64, 32>(c, st);
+    if (c.F1 == 32 && c.F2 == 64) return setup_run<T, 32, 64>(c, st);
     if (c.F1 == 64 && c.F2 == 64) return setup_run<T, 64, 64>(c, st);
+    if (c.F1 == 128 && c.F2 == 32) return setup_run<T, 128, 32>(c, st);
+    if (c.F1 == 32 && c.F2 == 128) return setup_run<T, 32, 128>(c, st);
     if (c.F1 == 128 && c.F2 == 64) return setup_run<T, 128, 64>(c, st);
     if (c.F1 == 128 && c.F2 == 128) return setup_run<T, 128, 128>(c, st);
     if (c.F1 == 256 && c.F2 == 128) return setup_run<T, 256, 128>(c, st);

@@ -48,6 +48,8 @@ inline int fft_size(int ns, int prec)
 constexpr int F4_FMAX = 65536;
 constexpr int F4_FMIN = 4096;             // 64 x 64
 constexpr int F4B_FMIN = 1024;            // 32 x 32: the one-CTA-per-mode variant of batched curves
+constexpr int F4B_FMAX_F32 = 8192;        // 128 x 64
+constexpr int F4B_FMAX_F64 = 4096;        // 64 x 64
 constexpr int F4_THREADS = 256;           // 8 warps, one line each
 constexpr int F4C_CS = 8;                 // clustered four-step form: CTAs per cluster (portable size)
 constexpr size_t F4C_SMEM_MAX = 224 * 1024;   // its dynamic shared memory per CTA (of 227 KB)
@@ -311,8 +313,24 @@ cudaError_t launch_f4(const CurveDev &c, int mode, int discrete, int gate, cudaS
 // The one-CTA-per-mode four-step form: over the modes of one curve, or over the
 // (curve, mode) items of a batch whose curves share F.
 cudaError_t launch_f4b(const CurveDev &c, int mode, int discrete, int gate, cudaStream_t st);
-cudaError_t launch_f4b_batch(int prec, int F, const CurveDev *cv, const int2 *items, int nitems, int mode,
+cudaError_t launch_f4b_batch(int prec, int F1, int F2, const CurveDev *cv, const int2 *items, int nitems, int mode,
                              int discrete, int gate, cudaStream_t st);
+// The splits F = F1 F2 the one-CTA-per-mode four-step form runs a length in (the
+// first is the default of f4_split).
+inline int f4b_splits(int F, int prec, int (&F1s)[3])
+{
+    int n = 0;
+    int d1 = 0, d2 = 0;
+    f4_split(F, d1, d2);
+    F1s[n++] = d1;
+    for (int f1 = 32; f1 <= 128; f1 <<= 1) {
+        const int f2 = F / f1;
+        if (f1 == d1 || f2 < 32 || f2 > 128 || f1 * f2 != F) continue;
+        if (F == 8192 && !(prec && f1 == 128)) continue;   // F = 8192: 128 x 64, FP32 only
+        if (n < 3) F1s[n++] = f1;
+    }
+    return n;
+}
 
 // Split-BF16 tensor-core row phase (ks_rows_tc.cu; c.xtc set): bytes of its DFT
 // matrices, their set-up, and the row phase with the modes of launch_rows.
@@ -325,7 +343,9 @@ cudaError_t launch_rows_tc(const CurveDev &c, int mode, cudaStream_t st, StepArm
 cudaError_t launch_step_persistent(const CurveDev &c, int discrete, long long nsteps, cudaStream_t st);
 
 // ---- batched launches over (curve, block) work items; cv is a device array of curves
-cudaError_t launch_rows_batch(int prec, int N, const CurveDev *cv, const int2 *items, int nitems, int mode,
+// warps: 4 or 8 per CTA (2 sections per warp); the items' blocks and each curve's
+// row_blocks must use the same width.
+cudaError_t launch_rows_batch(int prec, int N, int warps, const CurveDev *cv, const int2 *items, int nitems, int mode,
                               cudaStream_t st);
 cudaError_t launch_dt_batch(int prec, int bn, const CurveDev *cv, const int4 *items, int nitems, int mode,
                             int discrete, int gate, cudaStream_t st);

@@ -46,13 +46,15 @@ Layout make_layout(int ns, int nx, int prec, int allow_split, int bn, int s_tran
     int form = SF_DENSE;
     // batched curves: the FFT form with one CTA per mode wherever it fits, its
     // four-step variant (register line transforms) from F = 1024 on
+    // (F >= 2P + 1 there, so FP64 curves up to N_s = 2048 fit its 4096 points)
     bool batched_f4 = false;
-    if (!allow_split) {
-        form = (s_transform == 0 || s_transform == 2) && fft_size(ns, prec) ? SF_FFT1 : SF_DENSE;
-        if (form == SF_FFT1 && fft_size(ns, prec) >= F4B_FMIN) {
+    if (!allow_split && (s_transform == 0 || s_transform == 2)) {
+        const int f1 = fft_size(ns, prec), fh = fft4h_size(ns, F4B_FMIN);
+        if (f1 && f1 < F4B_FMIN) form = SF_FFT1;
+        else if (fh && fh <= (prec ? F4B_FMAX_F32 : F4B_FMAX_F64)) {
             form = SF_FFT4;
             batched_f4 = true;
-        }
+        } else if (f1) form = SF_FFT1;
     }
     else if (s_transform == 0) form = auto_form(ns, nx, prec);
     else if (s_transform == 2) form = fft_size(ns, prec) ? SF_FFT1 : (fft4_size(ns, prec) ? SF_FFT4 : SF_DENSE);
@@ -444,12 +446,12 @@ __global__ void __launch_bounds__(ROWS_WARPS * 32) k_rows(CurveDev c, int mode, 
 
 // Batched row phase: work item (curve, row block) per CTA; every curve keeps its
 // own gates, counters and reductions.
-template <typename T, int N>
-__global__ void __launch_bounds__(ROWS_WARPS * 32) k_rows_batch(const CurveDev *cv, const int2 *items, int mode)
+template <typename T, int N, int WARPS>
+__global__ void __launch_bounds__(WARPS * 32) k_rows_batch(const CurveDev *cv, const int2 *items, int mode)
 {
     const int2 it = items[blockIdx.x];
     const CurveDev &c = cv[it.x];
-    rows_body<T, N>(c, mode, it.y, c.row_blocks, true);
+    rows_body<T, N, WARPS>(c, mode, it.y, c.row_blocks, true);
 }
 
 // ---------------------------------------------------------------------------
@@ -1206,23 +1208,28 @@ cudaError_t launch_dt(const CurveDev &c, int mode, int discrete, int gate, cudaS
                   : launch_dt_t<double, 32>(c, mode, discrete, gate, st);
 }
 
-template <typename T>
+template <typename T, int W>
 static cudaError_t rows_batch_t(int N, const CurveDev *cv, const int2 *items, int nitems, int mode, cudaStream_t st)
 {
     return dispatch_n(N, [&](auto nn) {
         constexpr int NN = decltype(nn)::value;
-        size_t sm = rows_smem<T>(NN, 3);
-        cudaError_t e = set_smem(k_rows_batch<T, NN>, sm);
+        size_t sm = rows_smem<T>(NN, 3, W);
+        cudaError_t e = set_smem(k_rows_batch<T, NN, W>, sm);
         if (e != cudaSuccess) return e;
-        return launch_step_kernel(k_rows_batch<T, NN>, dim3(nitems), dim3(ROWS_WARPS * 32), sm, st, 0, cv, items, mode);
+        return launch_step_kernel(k_rows_batch<T, NN, W>, dim3(nitems), dim3(W * 32), sm, st, 0, cv, items, mode);
     });
 }
 
-cudaError_t launch_rows_batch(int prec, int N, const CurveDev *cv, const int2 *items, int nitems, int mode,
+cudaError_t launch_rows_batch(int prec, int N, int warps, const CurveDev *cv, const int2 *items, int nitems, int mode,
                               cudaStream_t st)
 {
     if (nitems <= 0) return cudaSuccess;
-    return prec ? rows_batch_t<float>(N, cv, items, nitems, mode, st) : rows_batch_t<double>(N, cv, items, nitems, mode, st);
+    if (warps == 8)
+        return prec ? rows_batch_t<float, 8>(N, cv, items, nitems, mode, st)
+                    : rows_batch_t<double, 8>(N, cv, items, nitems, mode, st);
+    if (warps != ROWS_WARPS) return cudaErrorInvalidValue;
+    return prec ? rows_batch_t<float, ROWS_WARPS>(N, cv, items, nitems, mode, st)
+                : rows_batch_t<double, ROWS_WARPS>(N, cv, items, nitems, mode, st);
 }
 
 cudaError_t launch_dt_batch(int prec, int bn, const CurveDev *cv, const int4 *items, int nitems, int mode,

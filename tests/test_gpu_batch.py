@@ -81,10 +81,41 @@ def test_curves_stop_at_their_own_tolerance_and_autotune_keeps_results():
     out = b.descend(30, tol)
     below = first["J_arc"] < tol
     assert np.all(out["steps"][below] == 0) and np.all(out["steps"][~below] > 0)
-    chosen = b.autotune(4)
-    assert chosen in (32, 64)
+    tune = b.autotune(4)
+    assert tune["row_sections"] in (8, 16) and tune["dense_tile"] in (0, 32, 64)
     sc = b.scalars()
     assert all(np.isfinite(x["J"]) for x in sc)
+    b.close()
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-11), ("fp32", 2e-5)])
+def test_autotuned_four_step_batch_matches_independent_curves(precision, tol):
+    """Curves in the batched four-step form (F = 1024, 2048, 4096; N_s = 2000 is
+    the longest FP64 curve that fits it): the autotuner switches the row-phase
+    width and the split of every length (recomputing the spectra); the tuned
+    batch still equals independent curves run for the same number of steps."""
+    base = gen.workload(3)
+    specs = [gen.CurveSpec(3, i, base[i].L, base[i].N, Ns, gen.mapping_scale(Ns), dtau=0.002, steps=0)
+             for i, Ns in zip((4, 6, 7, 9, 11), (400, 700, 1100, 1300, 2000))]
+    ins = [_inputs(s) for s in specs]
+    b = KSBatch(specs, [i[0] for i in ins], [i[1] for i in ins], precision=precision, conv="jarc")
+    b.init_trial(np.array([i[2] for i in ins]), [i[3] for i in ins])
+    tune = b.autotune(3)
+    print("batch tuning:", tune)
+    assert set(tune["splits"]) == {1024, 2048, 4096}
+    assert all(f1 * f2 == F for F, (f1, f2) in tune["splits"].items())
+    out = b.descend(10)
+    steps = [x["step"] for x in b.scalars()]
+    for k, s in enumerate(specs):
+        up, um, amps, vp = ins[k]
+        c = KSCurve(s.L, s.N, s.Ns, s.S, up, um, dtau=s.dtau, precision=precision)
+        c.init_trial(0.0, None, amps, vp)
+        ref = c.descend(steps[k])
+        xb = b.get_state(k).double().cpu().numpy()
+        xc = c.get_state().double().cpu().numpy()
+        assert np.abs(xb - xc).max() <= tol * np.abs(xc).max(), (k, s.Ns)
+        assert abs(out["J"][k] - ref["J"]) <= tol * ref["J"]
+        c.close()
     b.close()
 
 
