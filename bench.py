@@ -408,6 +408,52 @@ def oracle_errors(spec, make_curve, precision):
             "sampled_sections": len(rows), "reference": os.path.relpath(path, ROOT)}
 
 
+# ---------------------------------------------------------------------------- implicit stepping
+def implicit_context(dev, timed_steps, K, dtau=0.5):
+    """The L=44, N_x=128, N_s=4096 curve in FP32 stepped with every linear term of
+    G implicit (eigenbases of the even and odd parts of the interior D_t^2) at a
+    dtau 25x the IMEX limit, beside the IMEX scheme at the workload's dtau:
+    device time per step, fictitious time per second, and the increment's two
+    products against the FP32 CUDA-core peak."""
+    from paper_2301_11704_gb300 import gen
+    from paper_2301_11704_gb300.curve import KSCurve
+    sl = spec_of("large")
+    up, um = gen.end_points(sl)
+    amps, vp = gen.perturbation(sl)
+    out = {"workload": "L=%g N_x=%d N_s=%d FP32" % (sl.L, sl.N, sl.Ns)}
+    for scheme, dt in (("imex", sl.dtau), ("implicit", dtau)):
+        t0 = time.perf_counter()
+        c = KSCurve(sl.L, sl.N, sl.Ns, sl.S, up, um, s0=sl.s0, dtau=dt, precision="fp32", scheme=scheme, device=dev)
+        setup_s = time.perf_counter() - t0
+        c.init_trial(0.0, None, amps, vp)
+        ms, prof = timed_steps(c, K, 3, profile=K)
+        sc = c.scalars()
+        c.close()
+        step = sum(ms) / K
+        rec = {"dtau": dt, "ms_per_step": step, "tau_per_s": dt / (step / 1e3), "create_s": setup_s,
+               "J_after": sc["J"], "steps": K, "phases_ms": {k: v["ms"] / v["launches"] for k, v in prof.items()
+                                                             if isinstance(v, dict) and v.get("launches")}}
+        if scheme == "implicit" and "implicit" in prof:
+            M = sl.Ns - 2
+            ne, no = (M + 1) // 2, M // 2
+            flops = 2 * 2.0 * (ne * ne + no * no) * sl.N
+            t = prof["implicit"]["ms"] / prof["implicit"]["launches"]
+            peaks, _ = read_peaks()
+            nsm = torch_sm_count(dev)
+            peak = nsm * FP32_LANES_PER_SM * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+            rec["products"] = {"ms": t, "flops": flops, "achieved_tflops": flops / (t / 1e3) / 1e12,
+                               "peak_tflops": peak, "frac": flops / (t / 1e3) / 1e12 / peak,
+                               "bound": "alu (FP32 CUDA cores)"}
+        out[scheme] = rec
+    out["tau_rate_ratio"] = out["implicit"]["tau_per_s"] / out["imex"]["tau_per_s"]
+    return out
+
+
+def torch_sm_count(dev):
+    import torch
+    return torch.cuda.get_device_properties(dev).multi_processor_count
+
+
 # ---------------------------------------------------------------------------- single curve
 def run_curve(args):
     import numpy as np
@@ -620,6 +666,11 @@ def run_curve(args):
                                          "value": sd.M * kd / (sum(msd) / 1e3), "unit": UNIT,
                                          "ms_per_step": sum(msd) / kd, "steps": kd, "s_form": cd.s_form}
             cd.close()
+        # ---- full-linear-implicit stepping (Sec. V.C.3) on the single large curve
+        try:
+            ctx["implicit_scheme"] = implicit_context(dev, timed_steps, max(3, min(50, K)))
+        except Exception as exc:
+            ctx["implicit_scheme"] = {"unavailable": str(exc)[:160]}
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:

@@ -81,6 +81,22 @@ typedef enum { KS_ADJ_PAPER = 0, KS_ADJ_DISCRETE = 1 } ks_adjoint;
  * KS_CONV_JREL: J / |lambda D_t u|_W (scale-free; the FP32 criterion). */
 typedef enum { KS_CONV_JARC = 0, KS_CONV_J = 1, KS_CONV_JREL = 2 } ks_conv;
 
+/* Time stepping of the descent du/dtau = G, semi-implicit forward Euler
+ * (Sec. V.C.3: the terms of G linear in u at the new level, the rest at the old).
+ * KS_SCHEME_IMEX: the diagonal term -a_j^2 u (a_j = k_j^4 - k_j^2):
+ *   u += dtau G / (1 + dtau a_j^2); stable while dtau rho(lambda^2 D_t^2) < 2.
+ * KS_SCHEME_IMPLICIT: every linear term, (lambda^2 D~^2 - a_j^2) u with D~ the
+ *   interior block of D_t (eq. rational_diff_matrix):
+ *   (I (1 + dtau a_j^2) - dtau lambda^2 D~^2) delta_j = dtau G_j, u += delta,
+ *   applied as V (dtau / (1 + dtau (a_j^2 - lambda^2 mu))) V^-1 in the
+ *   eigenbases of D~^2 restricted to its even and odd parts under s -> -s
+ *   (computed once at create, in FP64, by cuSOLVER's nonsymmetric eigensolver,
+ *   which the library opens at run time: create fails with KS_ECUDA if it is
+ *   missing, KS_EINVAL if an eigenvalue is complex or positive).  Single
+ *   curves, launch = 0, N_s <= 16384; the set-up temporarily allocates device
+ *   memory of about 5 (N_s / 2)^2 doubles besides the workspace. */
+typedef enum { KS_SCHEME_IMEX = 0, KS_SCHEME_IMPLICIT = 1 } ks_scheme;
+
 typedef struct {
     double L;            /* domain length, > 0 (Sec. V: x in [0, L)) */
     int32_t nx;          /* N: Fourier modes = grid points per section; power of two, 8..256 */
@@ -131,6 +147,9 @@ typedef struct {
                             grid-wide barriers between the phases of a step (dense form
                             only, else as 0; measured slower than 0 on GB300).
                             Batches ignore it. */
+    int32_t scheme;      /* ks_scheme (time stepping); the workspace grows by
+                            2 (ceil(M/2)^2 + floor(M/2)^2) storage words + 8 M bytes for
+                            KS_SCHEME_IMPLICIT */
 } ks_params;
 
 /* Scalars of the state most recently evaluated (cost, gradient or descent). */
@@ -275,6 +294,9 @@ typedef struct {
     double pass_ms[2][3];    /* three-launch four-step form (s_transform 4): milliseconds of
                                 passes 1, 2, 3 of the update (row 0) and of D_t u (row 1) */
     int64_t pass_launches[2][3];
+    double impl_ms;          /* KS_SCHEME_IMPLICIT: milliseconds of the increment's two
+                                products (part of phase 1) */
+    int64_t impl_launches;   /* steps they were timed for */
 } ks_profile;
 
 ks_status ks_curve_profile(ks_curve *c, int32_t max_steps);

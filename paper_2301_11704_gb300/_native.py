@@ -16,6 +16,7 @@ STATUS_NAMES = {0: "KS_OK", 1: "KS_EINVAL", 2: "KS_ENOMEM", 3: "KS_ECUDA", 4: "K
 KS_FP64, KS_FP32, KS_BF16X2, KS_BF16X3 = 0, 1, 2, 3
 KS_ADJ_PAPER, KS_ADJ_DISCRETE = 0, 1
 KS_CONV_JARC, KS_CONV_J, KS_CONV_JREL = 0, 1, 2
+KS_SCHEME_IMEX, KS_SCHEME_IMPLICIT = 0, 1
 
 # Every symbol include/ksconn.h declares.
 EXPORTS = [
@@ -47,6 +48,7 @@ class KSParams(ctypes.Structure):
         ("symmetry", ctypes.c_int32),
         ("s_transform", ctypes.c_int32),
         ("launch", ctypes.c_int32),
+        ("scheme", ctypes.c_int32),
     ]
 
 
@@ -71,7 +73,8 @@ class KSScalars(ctypes.Structure):
 class KSProfile(ctypes.Structure):
     _fields_ = [("ms", ctypes.c_double * 3), ("launches", ctypes.c_int64 * 3), ("step_ms", ctypes.c_double),
                 ("step_launches", ctypes.c_int64), ("step_steps", ctypes.c_int64),
-                ("pass_ms", (ctypes.c_double * 3) * 2), ("pass_launches", (ctypes.c_int64 * 3) * 2)]
+                ("pass_ms", (ctypes.c_double * 3) * 2), ("pass_launches", (ctypes.c_int64 * 3) * 2),
+                ("impl_ms", ctypes.c_double), ("impl_launches", ctypes.c_int64)]
 
 
 class KSBatchTuning(ctypes.Structure):

@@ -75,6 +75,8 @@ ks_status validate_batch(int nb, const ks_params *p)
             return ks::report_error(KS_EINVAL, "batches run the FFT row phase: precision must be KS_FP64 or KS_FP32");
         if (p[i].adjoint != p[0].adjoint)
             return ks::report_error(KS_EINVAL, "all curves of a batch must have the same adjoint mode");
+        if (p[i].scheme != KS_SCHEME_IMEX)
+            return ks::report_error(KS_EINVAL, "batches step with KS_SCHEME_IMEX");
     }
     return KS_OK;
 }

@@ -33,7 +33,7 @@ struct ks_curve {
 };
 
 static const int GRAPH_STEPS = 16;
-static const int EV_PER_ENTRY = 10;
+static const int EV_PER_ENTRY = 12;
 
 static thread_local char g_err[512];
 
@@ -105,6 +105,10 @@ ks_status validate(const ks_params *p)
     if (p->s_transform == 3 && !ks::storage32(p->precision))
         return fail(KS_EINVAL, "s_transform = tensor cores needs FP32 storage");
     if (p->launch < 0 || p->launch > 1) return fail(KS_EINVAL, "launch must be 0 or 1");
+    if (p->scheme != KS_SCHEME_IMEX && p->scheme != KS_SCHEME_IMPLICIT)
+        return fail(KS_EINVAL, "scheme must be KS_SCHEME_IMEX or KS_SCHEME_IMPLICIT");
+    if (p->scheme == KS_SCHEME_IMPLICIT && (p->launch != 0 || p->ns < 4 || p->ns > 16384))
+        return fail(KS_EINVAL, "implicit stepping needs launch = 0 and 4 <= N_s <= 16384");
     if (p->s_transform == 2 && ks::fft_size(p->ns, ks::storage32(p->precision)) == 0 &&
         ks::fft4_size(p->ns, ks::storage32(p->precision)) == 0)
         return fail(KS_EINVAL, "s_transform = FFT supports N_s <= %d", ks::F4_FMAX / 3 + 1);
@@ -136,19 +140,36 @@ ks_status read_scalars(ks_curve *c, ks::DevScalars *h)
 
 // The clustered four-step form applies the update and D_t u of the updated state
 // in one launch (GM_STEP) at the sizes of f4c_fused; every other form in two.
-static bool fused_step(const ks_curve *c) { return c->d.f4c != 0 && ks::f4c_fused(c->d.prec, c->d.nx, c->d.F); }
+static bool fused_step(const ks_curve *c)
+{
+    return c->d.f4c != 0 && !c->d.impl && ks::f4c_fused(c->d.prec, c->d.nx, c->d.F);
+}
+
+// The update of one step: the update contraction (G and |G|^2), and for the
+// implicit scheme the two products of its increment.
+// impl_ev (may be null): two events bracketing the implicit products.
+static ks_status launch_update(ks_curve *c, int discrete, cudaStream_t st, cudaEvent_t *pass_ev,
+                               cudaEvent_t *impl_ev = nullptr)
+{
+    if (!c->d.impl) {
+        KS_CUDA(ks::launch_dt(c->d, fused_step(c) ? ks::GM_STEP : ks::GM_UPDATE, discrete, 1, st, pass_ev));
+        return KS_OK;
+    }
+    KS_CUDA(ks::launch_dt(c->d, ks::GM_GRAD, discrete, 1, st, pass_ev));
+    if (impl_ev) KS_CUDA(cudaEventRecord(impl_ev[0], st));
+    KS_CUDA(ks::launch_implicit_update(c->d, 1, st));
+    if (impl_ev) KS_CUDA(cudaEventRecord(impl_ev[1], st));
+    return KS_OK;
+}
 // The three-launch four-step form, whose passes are timed one by one.
 static bool three_pass(const ks_curve *c) { return c->d.f4 && !c->d.f4c && !c->d.f4b; }
 
 ks_status launch_step(ks_curve *c, int discrete, cudaStream_t st)
 {
     KS_CUDA(ks::launch_rows(c->d, ks::ROWS_STEP, st));
-    if (fused_step(c)) {
-        KS_CUDA(ks::launch_dt(c->d, ks::GM_STEP, discrete, 1, st));
-        return KS_OK;
-    }
-    KS_CUDA(ks::launch_dt(c->d, ks::GM_UPDATE, discrete, 1, st));
-    KS_CUDA(ks::launch_dt(c->d, ks::GM_STORE, 0, 1, st));
+    ks_status s = launch_update(c, discrete, st, nullptr);
+    if (s != KS_OK) return s;
+    if (!fused_step(c)) KS_CUDA(ks::launch_dt(c->d, ks::GM_STORE, 0, 1, st));
     return KS_OK;
 }
 
@@ -228,7 +249,8 @@ ks_status enqueue_steps(ks_curve *c, int64_t nsteps, double tol)
         KS_CUDA(ks::launch_rows(c->d, ks::ROWS_STEP, c->st, arm));
         if (prof) KS_CUDA(cudaEventRecord(ev[1], c->st));
         if (prof) KS_CUDA(cudaEventRecord(ev[2], c->st));
-        KS_CUDA(ks::launch_dt(c->d, fused_step(c) ? ks::GM_STEP : ks::GM_UPDATE, discrete, 1, c->st, pass_u));
+        ks_status us = launch_update(c, discrete, c->st, pass_u, (prof && c->d.impl) ? ev + 10 : nullptr);
+        if (us != KS_OK) return us;
         if (prof) KS_CUDA(cudaEventRecord(ev[3], c->st));
         if (prof) KS_CUDA(cudaEventRecord(ev[4], c->st));
         if (!fused_step(c)) KS_CUDA(ks::launch_dt(c->d, ks::GM_STORE, 0, 1, c->st, pass_d));
@@ -350,6 +372,7 @@ ks_status ks_curve_create(const ks_params *p, const double *u_plus_host, const d
             r = fail(KS_ECUDA, "set-up kernels failed: %s", cudaGetErrorString(e));
             break;
         }
+        if ((r = ks::setup_implicit(c->d, c->st)) != KS_OK) break;
         ks::DevScalars h;
         r = read_scalars(c, &h);
         if (r != KS_OK) break;
@@ -593,10 +616,18 @@ ks_status ks_curve_profile_read(ks_curve *c, ks_profile *out)
             out->ms[ph] += ms;
             out->launches[ph] += 1;
         }
+        if (c->d.impl) {
+            float ms = 0.f;
+            KS_CUDA(cudaEventElapsedTime(&ms, ev[10], ev[11]));
+            out->impl_ms += ms;
+            out->impl_launches += 1;
+        }
         if (three_pass(c)) {
             for (int ph = 0; ph < 2; ++ph) {
                 // pass boundaries: phase start, end of pass 1, end of pass 2, phase end
-                const cudaEvent_t b[4] = {ev[2 + 2 * ph], ev[6 + 2 * ph], ev[7 + 2 * ph], ev[3 + 2 * ph]};
+                // (for the update of the implicit scheme: the start of its products)
+                const cudaEvent_t b[4] = {ev[2 + 2 * ph], ev[6 + 2 * ph], ev[7 + 2 * ph],
+                                          (ph == 0 && c->d.impl) ? ev[10] : ev[3 + 2 * ph]};
                 for (int q = 0; q < 3; ++q) {
                     float ms = 0.f;
                     KS_CUDA(cudaEventElapsedTime(&ms, b[q], b[q + 1]));

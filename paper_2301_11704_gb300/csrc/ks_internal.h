@@ -211,6 +211,8 @@ struct Layout {
     int f4h;                           // the three-launch form on the Toeplitz and Hankel parts (F >= 2P + 1)
     int xtc;                           // split-BF16 tensor-core row phase: parts per operand (0: FFT row phase)
     size_t off_xdft;                   // its DFT matrices, split into BF16 parts
+    int impl;                          // full-linear-implicit stepping: its eigenbases (0: IMEX)
+    size_t off_iv, off_ivi, off_imu;   // V (even block, then odd), V^-1 likewise, eigenvalues (FP64)
 };
 
 struct CurveDev {
@@ -234,6 +236,11 @@ struct CurveDev {
                                        // spectra of both ([k1][k2] each, Toeplitz first) in chat
     int xtc;               // split-BF16 tensor-core row phase: parts per operand (2 or 3; 0: FFT row phase)
     void *xdft;            // its DFT matrices C (inverse) and E (forward), three BF16 parts, operand layout
+    int impl;              // full-linear-implicit stepping (Sec. V.C.3): the eigenbases of the
+                           // interior D_t^2 in its even and odd parts under s -> -s
+    int ine, ino;          // their sizes: ceil(M/2), floor(M/2)
+    void *iv, *ivi;        // V_e [ine][ine] then V_o [ino][ino], row-major (storage type); V^-1 alike
+    double *imu;           // eigenvalues: ine of the even part, then ino of the odd part
     int F;                 // FFT length of the s-contraction (0: dense form)
     void *chat, *ftw;      // FFT form: kernel spectrum / F and twiddles (complex, storage type);
                            // four-step form: spectrum stored [k1][k2] for k = k1 + F1 k2 (both
@@ -249,13 +256,14 @@ struct CurveDev {
 // allow_split = 0 lays a curve out without split contractions (batched curves
 // get their parallelism from the batch); bn = 0 picks the column tile width.
 Layout make_layout(int ns, int nx, int prec, int allow_split = 1, int bn = 0, int s_transform = 0,
-                   int persistent = 0, int xtc = 0);
+                   int persistent = 0, int xtc = 0, int impl = 0);
 // Layout of a single curve with parameters p (persistent: room for the
 // persistent step's partials when p asks for that launch form).
 inline Layout curve_layout(const ks_params *p, int persistent)
 {
     const int xtc = xtc_of(p->precision);   // the persistent step has its own (FFT) row phase
-    return make_layout(p->ns, p->nx, storage32(p->precision), 1, 0, p->s_transform, persistent && !xtc, xtc);
+    return make_layout(p->ns, p->nx, storage32(p->precision), 1, 0, p->s_transform, persistent && !xtc, xtc,
+                       p->scheme == KS_SCHEME_IMPLICIT);
 }
 // Pointers of a curve whose workspace starts at `base` (256-byte aligned).
 CurveDev bind_layout(const ks_params *p, const Layout &l, void *base);
@@ -336,6 +344,17 @@ inline int f4b_splits(int F, int prec, int (&F1s)[3])
 // matrices, their set-up, and the row phase with the modes of launch_rows.
 size_t xdft_bytes(int nx);
 cudaError_t launch_setup_xdft(const CurveDev &c, cudaStream_t st);
+
+// ---- full-linear-implicit stepping (ks_implicit.cu)
+// Bytes of the eigenbases of a curve with N_s sections in the storage type.
+size_t implicit_bytes(int ns, int prec);
+// One-time set-up: eigendecomposition of the interior D_t^2 (FP64, cuSOLVER,
+// opened at run time), stored in the curve's workspace.  Synchronous.
+ks_status setup_implicit(const CurveDev &c, cudaStream_t st);
+// The increment of one step from G (written by the GM_GRAD contraction):
+// U += V (dtau / (1 + dtau (a_j^2 - lambda^2 mu))) V^-1 G per parity, then the
+// step's bookkeeping (step, tau, lambda); gated like the contractions.
+cudaError_t launch_implicit_update(const CurveDev &c, int gate, cudaStream_t st);
 cudaError_t launch_rows_tc(const CurveDev &c, int mode, cudaStream_t st, StepArm arm);
 
 // Persistent step (ks_step.cu): nsteps descent steps of a dense-form curve

@@ -37,7 +37,8 @@ namespace ks {
 // ---------------------------------------------------------------------------
 static size_t al256(size_t x) { return (x + 255) & ~size_t(255); }
 
-Layout make_layout(int ns, int nx, int prec, int allow_split, int bn, int s_transform, int persistent, int xtc)
+Layout make_layout(int ns, int nx, int prec, int allow_split, int bn, int s_transform, int persistent, int xtc,
+                   int impl)
 {
     Layout l{};
     size_t b = prec ? 4 : 8;
@@ -148,6 +149,12 @@ Layout make_layout(int ns, int nx, int prec, int allow_split, int bn, int s_tran
     // the split-BF16 row phase's DFT matrices
     l.xtc = xtc;
     l.off_xdft = off; off += xtc ? al256(xdft_bytes(nx)) : 0;
+    // the implicit step's eigenbases (V and V^-1 of both parts) and eigenvalues
+    l.impl = impl;
+    const size_t ne = (size_t)(ns - 1) / 2, no = (size_t)(ns - 2) / 2;   // ceil(M/2), floor(M/2)
+    l.off_iv = off; off += impl ? al256((ne * ne + no * no) * b) : 0;
+    l.off_ivi = off; off += impl ? al256((ne * ne + no * no) * b) : 0;
+    l.off_imu = off; off += impl ? al256((ne + no) * 8) : 0;
     l.total = off;
     return l;
 }
@@ -200,6 +207,12 @@ CurveDev bind_layout(const ks_params *p, const Layout &l, void *base)
     d.f4h = l.f4h;
     d.xtc = l.xtc;
     d.xdft = l.xtc ? (void *)(b + l.off_xdft) : nullptr;
+    d.impl = l.impl;
+    d.ine = (p->ns - 1) / 2;
+    d.ino = (p->ns - 2) / 2;
+    d.iv = l.impl ? (void *)(b + l.off_iv) : nullptr;
+    d.ivi = l.impl ? (void *)(b + l.off_ivi) : nullptr;
+    d.imu = l.impl ? (double *)(b + l.off_imu) : nullptr;
     d.cot = b + l.off_cot;
     d.sig = b + l.off_sig;
     d.tau = b + l.off_tau;

@@ -21,6 +21,7 @@ _CONV = {"jarc": _native.KS_CONV_JARC, "j": _native.KS_CONV_J, "jrel": _native.K
 _STR = {"auto": 0, "dense": 1, "fft": 2, "dense_tc": 3, "fft4": 4, "fft4c": 5}
 _FORM_NAME = {1: "dense", 2: "fft", 3: "dense_tc", 4: "fft4", 5: "fft4c"}
 _LAUNCH = {"auto": 0, "kernels": 0, "persistent": 1}
+_SCHEME = {"imex": _native.KS_SCHEME_IMEX, "implicit": _native.KS_SCHEME_IMPLICIT}
 
 
 def _f64(a, n=None):
@@ -49,13 +50,17 @@ class KSCurve:
     and the two contractions; one launch for both contractions in the clustered
     form), "persistent" runs many steps of a dense-form curve in one cooperative
     kernel (same results; slower on GB300 at the sizes measured).
+    scheme: "imex" takes only the diagonal term -a_j^2 u of G implicitly (stable
+    while dtau rho(lambda^2 D_t^2) < 2); "implicit" every linear term of G,
+    (lambda^2 D~^2 - a_j^2) u, through the eigenbases of the interior D_t^2 set
+    up once at creation (Sec. V.C.3), which allows far larger dtau.
     """
 
     def __init__(self, L: float, nx: int, ns: int, S: float, u_plus, u_minus=None, *, s0: float = 0.0,
                  lam: float = 1.0, lambda_free: bool = False, dtau: float = 0.01, dtau_lambda: float = 0.0,
                  precision: str = "fp64", adjoint: str = "paper", conv: str = "jarc", u_init=None,
                  check_ends: bool = False, symmetry: int = 0, s_transform: str = "auto", launch: str = "auto",
-                 device=None, stream: Optional[torch.cuda.Stream] = None):
+                 scheme: str = "imex", device=None, stream: Optional[torch.cuda.Stream] = None):
         self.lib = _native.load()
         self.device = torch.device(device if device is not None else "cuda")
         self.dtype = torch.float64 if precision == "fp64" else torch.float32
@@ -64,7 +69,7 @@ class KSCurve:
                                dtau=dtau, dtau_lambda=dtau_lambda, precision=_PREC[precision],
                                adjoint=_ADJ[adjoint], conv=_CONV[conv], check_ends=int(bool(check_ends)),
                                symmetry=int(symmetry), s_transform=_STR[s_transform],
-                               launch=_LAUNCH[launch])
+                               launch=_LAUNCH[launch], scheme=_SCHEME[scheme])
         nbytes = self.lib.ks_curve_workspace_bytes(ctypes.byref(self.params))
         if nbytes == 0:
             raise _native.KSError(_native.KS_EINVAL, self.lib.ks_last_error().decode())
@@ -180,6 +185,8 @@ class KSCurve:
                 passes[n] = [dict(ms=pr.pass_ms[i][q], launches=pr.pass_launches[i][q]) for q in range(3)]
         if passes:
             out["passes"] = passes
+        if pr.impl_launches:
+            out["implicit"] = dict(ms=pr.impl_ms, launches=pr.impl_launches)
         return out
 
     def debug_wait_limit(self, cycles: int):

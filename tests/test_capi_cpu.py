@@ -134,3 +134,34 @@ def test_split_bf16_batches_are_rejected(lib):
     ps = (KSParams * 2)(_params(precision=3, nx=64), _params(precision=3, nx=64))
     assert lib.ks_batch_workspace_bytes(2, ps) == 0
     assert b"batch" in lib.ks_last_error()
+
+
+@pytest.mark.parametrize("bad", [dict(scheme=2), dict(scheme=-1), dict(scheme=1, launch=1), dict(scheme=1, ns=3),
+                                 dict(scheme=1, ns=16385, nx=64)])
+def test_invalid_implicit_parameters_are_rejected(lib, bad):
+    p = _params(**bad)
+    assert lib.ks_curve_workspace_bytes(ctypes.byref(p)) == 0
+    assert lib.ks_last_error()
+
+
+@pytest.mark.parametrize("prec,b", [(0, 8), (1, 4), (2, 4)])
+@pytest.mark.parametrize("ns", [129, 130, 1000])
+def test_implicit_workspace_holds_the_eigenbases(lib, prec, b, ns):
+    """Full-linear-implicit stepping: V and V^-1 of the even (ceil(M/2) square) and
+    odd (floor(M/2) square) parts of D~^2 in the storage type, their eigenvalues
+    in FP64; same s-form as the IMEX scheme."""
+    nx = 64
+    imex = lib.ks_curve_workspace_bytes(ctypes.byref(_params(precision=prec, nx=nx, ns=ns)))
+    impl = lib.ks_curve_workspace_bytes(ctypes.byref(_params(precision=prec, nx=nx, ns=ns, scheme=1)))
+    M = ns - 2
+    ne, no = (M + 1) // 2, M // 2
+    al = lambda x: (x + 255) // 256 * 256
+    assert impl - imex == 2 * al((ne * ne + no * no) * b) + al(M * 8)
+    assert lib.ks_curve_s_form(ctypes.byref(_params(precision=prec, nx=nx, ns=ns, scheme=1))) == \
+        lib.ks_curve_s_form(ctypes.byref(_params(precision=prec, nx=nx, ns=ns)))
+
+
+def test_implicit_batches_are_rejected(lib):
+    ps = (KSParams * 2)(_params(scheme=1), _params(scheme=1))
+    assert lib.ks_batch_workspace_bytes(2, ps) == 0
+    assert b"IMEX" in lib.ks_last_error()
