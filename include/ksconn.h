@@ -148,8 +148,8 @@ typedef struct {
                             only, else as 0; measured slower than 0 on GB300).
                             Batches ignore it. */
     int32_t scheme;      /* ks_scheme (time stepping); the workspace grows by
-                            2 (ceil(M/2)^2 + floor(M/2)^2) storage words + 8 M bytes for
-                            KS_SCHEME_IMPLICIT */
+                            2 (ceil(M/2)^2 + floor(M/2)^2) + 16 M N storage words + 8 M bytes
+                            for KS_SCHEME_IMPLICIT */
 } ks_params;
 
 /* Scalars of the state most recently evaluated (cost, gradient or descent). */

@@ -15,14 +15,18 @@ _PREC = {"fp64": _native.KS_FP64, "fp32": _native.KS_FP32}
 _ADJ = {"paper": _native.KS_ADJ_PAPER, "discrete": _native.KS_ADJ_DISCRETE}
 _CONV = {"jarc": _native.KS_CONV_JARC, "j": _native.KS_CONV_J, "jrel": _native.KS_CONV_JREL}
 _STR = {"auto": 0, "dense": 1, "fft": 2}
+_SCHEME = {"imex": _native.KS_SCHEME_IMEX, "implicit": _native.KS_SCHEME_IMPLICIT}
 
 
 class KSBatch:
     """specs: sequence of objects with L, N, Ns, S, s0, dtau (e.g. gen.CurveSpec);
-    u_plus / u_minus: per-curve physical end sections."""
+    u_plus / u_minus: per-curve physical end sections.  scheme "implicit" steps
+    every curve with all linear terms of G implicit (its eigenbases are set up
+    at creation, in parallel host threads); dtau, when given, replaces every
+    spec's dtau."""
 
     def __init__(self, specs: Sequence, u_plus, u_minus, *, precision="fp32", adjoint="paper", conv="jrel",
-                 s_transform="auto", device=None, stream=None):
+                 s_transform="auto", scheme="imex", dtau=None, device=None, stream=None):
         self.lib = _native.load()
         self.device = torch.device(device if device is not None else "cuda")
         self.dtype = torch.float64 if precision == "fp64" else torch.float32
@@ -31,9 +35,9 @@ class KSBatch:
         arr = (KSParams * self.nb)()
         for i, s in enumerate(self.specs):
             arr[i] = KSParams(L=s.L, nx=s.N, ns=s.Ns, S=s.S, s0=getattr(s, "s0", 0.0), lam=1.0, lambda_free=0,
-                              dtau=s.dtau, dtau_lambda=0.0, precision=_PREC[precision], adjoint=_ADJ[adjoint],
-                              conv=_CONV[conv], check_ends=0, symmetry=0, s_transform=_STR[s_transform],
-                              launch=0)
+                              dtau=s.dtau if dtau is None else dtau, dtau_lambda=0.0, precision=_PREC[precision],
+                              adjoint=_ADJ[adjoint], conv=_CONV[conv], check_ends=0, symmetry=0,
+                              s_transform=_STR[s_transform], launch=0, scheme=_SCHEME[scheme])
         self.params = arr
         nbytes = self.lib.ks_batch_workspace_bytes(self.nb, arr)
         if nbytes == 0:

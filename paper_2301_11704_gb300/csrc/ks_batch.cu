@@ -2,10 +2,13 @@
 // together: every phase of a step is one launch over the work items (curve,
 // block) of all curves, captured once into a CUDA graph and replayed.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <map>
 #include <new>
+#include <string>
+#include <thread>
 #include <vector>
 
 #include "../../include/ksconn.h"
@@ -38,6 +41,8 @@ struct ks_batch {
     size_t items_cap = 0;
     std::vector<Group> rows, dts;
     std::vector<Group> ffts;            // (curve, mode) items of the FFT-form curves, one group per F
+    int impl = 0;                       // full-linear-implicit stepping
+    Group imp_prod{}, imp_fin{};        // its items: the two products, the finishing pass
     int tile_pref = 0;                  // 0: per-curve default, 32 or 64: forced (autotuner)
     int row_warps = ks::ROWS_WARPS;     // warps per row-phase CTA (two sections each): 4 or 8 (autotuner)
     float tuned_ms = 0.f;               // the autotuner's time of a step with its choice
@@ -52,14 +57,17 @@ size_t al256(size_t x) { return (x + 255) & ~size_t(255); }
 // Bytes of the batch header: curve array and the largest item lists.
 void header_sizes(int nb, const ks_params *p, size_t *cv_bytes, size_t *items_bytes)
 {
-    size_t rows = 0, tiles = 0, modes = 0;
+    size_t rows = 0, tiles = 0, modes = 0, imp = 0;
     for (int i = 0; i < nb; ++i) {
         rows += (p[i].ns + ks::ROWS_PER_CTA - 1) / ks::ROWS_PER_CTA;
         tiles += (size_t)((p[i].ns + ks::DT_BM - 1) / ks::DT_BM) * ((p[i].nx + 31) / 32);
         modes += p[i].nx / 2;
+        if (p[i].scheme == KS_SCHEME_IMPLICIT)   // the increment's products (<= 2 per tile) and finishing pass (<= 8)
+            imp += 2 * (size_t)((p[i].nx + 63) / 64) * ((p[i].ns - 1) / 2 / 128 + 1) + 8;
     }
     *cv_bytes = al256((size_t)nb * sizeof(ks::CurveDev));
-    *items_bytes = al256(rows * sizeof(int2)) + al256(tiles * sizeof(int4)) + al256(modes * sizeof(int2));
+    *items_bytes = al256(rows * sizeof(int2)) + al256(tiles * sizeof(int4)) + al256(modes * sizeof(int2)) +
+                   al256(imp * sizeof(int4));
 }
 
 ks_status validate_batch(int nb, const ks_params *p)
@@ -75,8 +83,8 @@ ks_status validate_batch(int nb, const ks_params *p)
             return ks::report_error(KS_EINVAL, "batches run the FFT row phase: precision must be KS_FP64 or KS_FP32");
         if (p[i].adjoint != p[0].adjoint)
             return ks::report_error(KS_EINVAL, "all curves of a batch must have the same adjoint mode");
-        if (p[i].scheme != KS_SCHEME_IMEX)
-            return ks::report_error(KS_EINVAL, "batches step with KS_SCHEME_IMEX");
+        if (p[i].scheme != p[0].scheme)
+            return ks::report_error(KS_EINVAL, "all curves of a batch must have the same scheme");
     }
     return KS_OK;
 }
@@ -126,6 +134,21 @@ ks_status build_items(ks_batch *b)
         memcpy(host.data() + o, it->second.data(), it->second.size() * sizeof(int2));
         o += it->second.size() * sizeof(int2);
     }
+    if (b->impl) {
+        std::vector<int4> prod, fin;
+        for (int i = 0; i < b->nb; ++i) ks::implicit_batch_items(b->cv[i], i, prod, fin);
+        o = al256(o);
+        b->imp_prod = {0, o, (int)prod.size()};
+        if (o + (prod.size() + fin.size()) * sizeof(int4) <= itb) {
+            memcpy(host.data() + o, prod.data(), prod.size() * sizeof(int4));
+            o += prod.size() * sizeof(int4);
+            b->imp_fin = {0, o, (int)fin.size()};
+            memcpy(host.data() + o, fin.data(), fin.size() * sizeof(int4));
+            o += fin.size() * sizeof(int4);
+        } else {
+            o = itb + 1;
+        }
+    }
     if (o > itb) return ks::report_error(KS_ENOMEM, "batch item lists exceed their reserved space");
     cudaError_t e = cudaMemcpyAsync(b->items_dev, host.data(), o, cudaMemcpyHostToDevice, b->st);
     if (e == cudaSuccess)
@@ -156,12 +179,18 @@ ks_status launch_step(ks_batch *b, cudaStream_t st)
         if (e == cudaSuccess)
             e = ks::launch_rows_batch(b->prec, g.key, b->row_warps, b->cv_dev, (const int2 *)(b->items_dev + g.off), g.count,
                                       ks::ROWS_STEP, st);
+    // the update contraction; for the implicit scheme it writes G, whose increment follows
+    const int um = b->impl ? ks::GM_GRAD : ks::GM_UPDATE;
     for (const Group &g : b->dts)
         if (e == cudaSuccess)
             e = ks::launch_dt_batch(b->prec, g.key, b->cv_dev, (const int4 *)(b->items_dev + g.off), g.count,
-                                    ks::GM_UPDATE, b->discrete, 1, st);
+                                    um, b->discrete, 1, st);
     for (const Group &g : b->ffts)
-        if (e == cudaSuccess) e = launch_fft_group(b, g, ks::GM_UPDATE, b->discrete, st);
+        if (e == cudaSuccess) e = launch_fft_group(b, g, um, b->discrete, st);
+    if (b->impl && e == cudaSuccess)
+        e = ks::launch_implicit_batch(b->prec, b->cv_dev, (const int4 *)(b->items_dev + b->imp_prod.off),
+                                      b->imp_prod.count, (const int4 *)(b->items_dev + b->imp_fin.off),
+                                      b->imp_fin.count, st);
     for (const Group &g : b->dts)
         if (e == cudaSuccess)
             e = ks::launch_dt_batch(b->prec, g.key, b->cv_dev, (const int4 *)(b->items_dev + g.off), g.count,
@@ -243,6 +272,43 @@ ks_status eval_all(ks_batch *b)
     return KS_OK;
 }
 
+// The implicit scheme's set-up of every curve (eigendecompositions), spread
+// over host threads with a stream each after the batch stream's set-up work.
+ks_status setup_implicit_all(ks_batch *b)
+{
+    cudaError_t e = cudaStreamSynchronize(b->st);
+    if (e != cudaSuccess) return ks::report_error(KS_ECUDA, "batch set-up: %s", cudaGetErrorString(e));
+    const int nt = std::max(1, std::min(8, b->nb));
+    std::vector<ks_status> st(nt, KS_OK);
+    std::vector<std::string> msg(nt);
+    std::atomic<int> next{0};
+    auto work = [&](int t) {
+        if (cudaSetDevice(b->device) != cudaSuccess) {
+            st[t] = KS_ECUDA;
+            msg[t] = "cannot select the batch's device";
+            return;
+        }
+        cudaStream_t s = nullptr;
+        if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
+            st[t] = KS_ECUDA;
+            msg[t] = "stream creation";
+            return;
+        }
+        for (int i = next++; i < b->nb && st[t] == KS_OK; i = next++) {
+            st[t] = ks::setup_implicit(b->cv[i], s);
+            if (st[t] != KS_OK) msg[t] = "curve " + std::to_string(i) + ": " + ks_last_error();
+        }
+        cudaStreamDestroy(s);
+    };
+    std::vector<std::thread> th;
+    for (int t = 1; t < nt; ++t) th.emplace_back(work, t);
+    work(0);
+    for (auto &x : th) x.join();
+    for (int t = 0; t < nt; ++t)
+        if (st[t] != KS_OK) return ks::report_error(st[t], "implicit set-up, %s", msg[t].c_str());
+    return KS_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -254,7 +320,8 @@ size_t ks_batch_workspace_bytes(int32_t nb, const ks_params *params)
     header_sizes(nb, params, &cvb, &itb);
     size_t total = cvb + itb;
     for (int i = 0; i < nb; ++i)
-        total += ks::make_layout(params[i].ns, params[i].nx, ks::storage32(params[i].precision), 0, 0, params[i].s_transform).total;
+        total += ks::make_layout(params[i].ns, params[i].nx, ks::storage32(params[i].precision), 0, 0,
+                                 params[i].s_transform, 0, 0, params[i].scheme == KS_SCHEME_IMPLICIT).total;
     return total;
 }
 
@@ -275,6 +342,7 @@ ks_status ks_batch_create(int32_t nb, const ks_params *params, const double *u_p
     b->nb = nb;
     b->prec = ks::storage32(params[0].precision);
     b->discrete = params[0].adjoint == KS_ADJ_DISCRETE;
+    b->impl = params[0].scheme == KS_SCHEME_IMPLICIT;
     b->st = (cudaStream_t)stream;
     cudaGetDevice(&b->device);
     b->p.assign(params, params + nb);
@@ -288,7 +356,8 @@ ks_status ks_batch_create(int32_t nb, const ks_params *params, const double *u_p
     b->cv.resize(nb);
     size_t xoff = 0;
     for (int i = 0; i < nb; ++i) {
-        const ks::Layout l = ks::make_layout(params[i].ns, params[i].nx, b->prec, 0, 0, params[i].s_transform);
+        const ks::Layout l = ks::make_layout(params[i].ns, params[i].nx, b->prec, 0, 0, params[i].s_transform, 0, 0,
+                                             params[i].scheme == KS_SCHEME_IMPLICIT);
         b->off.push_back(o);
         b->cv[i] = ks::bind_layout(&params[i], l, base + o);
         o += l.total;
@@ -311,6 +380,7 @@ ks_status ks_batch_create(int32_t nb, const ks_params *params, const double *u_p
         if (e != cudaSuccess) s = ks::report_error(KS_ECUDA, "batch set-up of curve %d: %s", i, cudaGetErrorString(e));
         xoff += c.nx;
     }
+    if (s == KS_OK && b->impl) s = setup_implicit_all(b);
     if (s == KS_OK) s = build_items(b);
     if (s != KS_OK) {
         delete b;

@@ -32,6 +32,7 @@
 #include <cusolverDn.h>   // types and constants only; the functions are looked up at run time
 #include <dlfcn.h>
 
+#include <algorithm>
 #include <cmath>
 #include <mutex>
 #include <vector>
@@ -186,18 +187,21 @@ static const Solver &solver()
     return s;
 }
 
-// Device buffers of the set-up, released on every path out.
+// Device buffers of the set-up (stream-ordered, so set-ups on several streams
+// do not synchronise the device), released on every path out.
 struct DevBufs {
+    cudaStream_t st;
     std::vector<void *> p;
+    explicit DevBufs(cudaStream_t s) : st(s) {}
     ~DevBufs()
     {
-        for (void *q : p) cudaFree(q);
+        for (void *q : p) cudaFreeAsync(q, st);
     }
     template <typename T>
     T *get(size_t count)
     {
         void *q = nullptr;
-        if (cudaMalloc(&q, count * sizeof(T) + 16) != cudaSuccess) return nullptr;
+        if (cudaMallocAsync(&q, count * sizeof(T) + 16, st) != cudaSuccess) return nullptr;
         p.push_back(q);
         return (T *)q;
     }
@@ -222,7 +226,7 @@ static ks_status eig_block(SolverHandle &sh, cudaStream_t st, int n, double *B, 
 {
     if (n == 0) return KS_OK;
     const Solver &s = sh.s;
-    DevBufs mem;
+    DevBufs mem(st);
     double *VR = mem.get<double>((size_t)n * n), *W = mem.get<double>(2 * (size_t)n);
     double *X = mem.get<double>((size_t)n * n);
     int64_t *piv = mem.get<int64_t>(n);
@@ -288,7 +292,7 @@ static ks_status setup_implicit_t(const CurveDev &c, cudaStream_t st)
     const Solver &s = solver();
     if (!s.ok) return report_error(KS_ECUDA, "implicit stepping needs cuSOLVER: %s", s.why);
     const int M = c.ns - 2, ne = c.ine, no = c.ino;
-    DevBufs mem;
+    DevBufs mem(st);
     double *Doe = mem.get<double>((size_t)no * ne + 1), *Deo = mem.get<double>((size_t)ne * no + 1);
     double *B = mem.get<double>((size_t)ne * ne + 1);
     if (!Doe || !Deo || !B) return report_error(KS_ECUDA, "implicit set-up: device memory");
@@ -309,6 +313,7 @@ static ks_status setup_implicit_t(const CurveDev &c, cudaStream_t st)
         if (cudaGetLastError() != cudaSuccess) return report_error(KS_ECUDA, "implicit set-up: block products");
         r = eig_block<T>(sh, st, no, B, c.imu + ne, V + (size_t)ne * ne, Vi + (size_t)ne * ne);
     }
+    if (r == KS_OK && cudaStreamSynchronize(st) != cudaSuccess) r = report_error(KS_ECUDA, "implicit set-up");
     return r;
 }
 
@@ -321,165 +326,270 @@ ks_status setup_implicit(const CurveDev &c, cudaStream_t st)
 // ---------------------------------------------------------------------------
 // Per step
 // ---------------------------------------------------------------------------
-constexpr int IM_BM = 64, IM_BK = 16, IM_THREADS = 256;
+// Three launches, all gated like the contractions:
+//   k_imp_fwd:    partial products over K chunks ("splits", so that the grid
+//                 fills the GPU) of V_p^-1 (Q_p^T G), folding G into the
+//                 bases on load, each partial scaled by the implicit factor
+//                 dtau / (1 + dtau (a_j^2 - lambda^2 mu)) (linear, so the sum
+//                 of the scaled partials is the scaled sum);
+//   k_imp_back:   partial products of V_p with Y_p = the sum of those partials
+//                 (summed on load, in split order);
+//   k_imp_finish: the sum of the back partials in split order, unfolded into
+//                 U's update, and the step's bookkeeping in the last CTA.
+// The products are register-tiled on the CUDA cores: 128 x 64 outputs per CTA,
+// 8 x 4 per thread, K in steps of 16 through shared memory.
+constexpr int IM_BM = 128, IM_BN = 64, IM_BK = 16, IM_THREADS = 256, IM_TM = 8, IM_TN = 4;
 
-template <typename T, int BN>
+template <typename T>
 struct ImSmem {
-    T As[IM_BM][IM_BK + 1];
-    __align__(16) T Bs[IM_BK][BN];
+    __align__(16) T As[IM_BK][IM_BM];
+    __align__(16) T Bs[IM_BK][IM_BN];
 };
 
-// acc[i][l] += sum_k A[r0 + 4 ty + i][k] * B(k, c0 + TN tx + l) for k < kdim;
-// A row-major with nrows rows and kdim columns, B(k, col) from `loadb`.
-template <typename T, int BN, typename LoadB>
-__device__ __forceinline__ void im_product(ImSmem<T, BN> &sm, const T *A, int nrows, int kdim, int r0, int c0, int ncols,
-                                           LoadB loadb, T (&acc)[4][BN / 16])
+// acc[i][l] += sum_{k in [kb, ke)} A[r0 + 8 ty + i][k] B(k, c0 + 4 tx + l);
+// A row-major (nrows x lda), B(k, col) from `loadb` (called for k < ke, col < ncols).
+template <typename T, typename LoadB>
+__device__ __forceinline__ void im_tile(ImSmem<T> &sm, const T *A, int nrows, int lda, int r0, int kb, int ke, int c0,
+                                        int ncols, LoadB loadb, T (&acc)[IM_TM][IM_TN])
 {
-    constexpr int TN = BN / 16, AL = IM_BM * IM_BK / IM_THREADS, BL = IM_BK * BN / IM_THREADS;
+    constexpr int AL = IM_BM * IM_BK / IM_THREADS, BL = IM_BK * IM_BN / IM_THREADS;
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    const int ar = tid >> 1, ak = (tid & 1) * AL;   // A: a row and 8 consecutive k per thread
     T ra[AL], rb[BL];
     auto fetch = [&](int k0) {
+        const bool rok = r0 + ar < nrows;
+        const T *arow = A + (size_t)(r0 + ar) * lda;
 #pragma unroll
         for (int q = 0; q < AL; ++q) {
-            const int e = tid + q * IM_THREADS, r = e / IM_BK, k = k0 + e % IM_BK;
-            ra[q] = (r0 + r < nrows && k < kdim) ? A[(size_t)(r0 + r) * kdim + k] : T(0);
+            const int k = k0 + ak + q;
+            ra[q] = (rok && k < ke) ? arow[k] : T(0);
         }
 #pragma unroll
         for (int q = 0; q < BL; ++q) {
-            const int e = tid + q * IM_THREADS, k = k0 + e / BN, col = c0 + e % BN;
-            rb[q] = (k < kdim && col < ncols) ? loadb(k, col) : T(0);
+            const int e = tid + q * IM_THREADS, k = k0 + e / IM_BN, col = c0 + e % IM_BN;
+            rb[q] = (k < ke && col < ncols) ? loadb(k, col) : T(0);
         }
     };
-    fetch(0);
-    for (int k0 = 0; k0 < kdim; k0 += IM_BK) {
+    if (kb >= ke) return;
+    fetch(kb);
+    for (int k0 = kb; k0 < ke; k0 += IM_BK) {
         __syncthreads();
 #pragma unroll
-        for (int q = 0; q < AL; ++q) {
-            const int e = tid + q * IM_THREADS;
-            sm.As[e / IM_BK][e % IM_BK] = ra[q];
-        }
+        for (int q = 0; q < AL; ++q) sm.As[ak + q][ar] = ra[q];
 #pragma unroll
         for (int q = 0; q < BL; ++q) {
             const int e = tid + q * IM_THREADS;
-            sm.Bs[e / BN][e % BN] = rb[q];
+            sm.Bs[e / IM_BN][e % IM_BN] = rb[q];
         }
         __syncthreads();
-        if (k0 + IM_BK < kdim) fetch(k0 + IM_BK);
+        if (k0 + IM_BK < ke) fetch(k0 + IM_BK);
 #pragma unroll
         for (int kk = 0; kk < IM_BK; ++kk) {
-            T a[4], b[TN];
+            T a[IM_TM], b[IM_TN];
 #pragma unroll
-            for (int i = 0; i < 4; ++i) a[i] = sm.As[4 * ty + i][kk];
+            for (int i = 0; i < IM_TM; ++i) a[i] = sm.As[kk][IM_TM * ty + i];
 #pragma unroll
-            for (int l = 0; l < TN; ++l) b[l] = sm.Bs[kk][TN * tx + l];
+            for (int l = 0; l < IM_TN; ++l) b[l] = sm.Bs[kk][IM_TN * tx + l];
 #pragma unroll
-            for (int i = 0; i < 4; ++i)
+            for (int i = 0; i < IM_TM; ++i)
 #pragma unroll
-                for (int l = 0; l < TN; ++l) acc[i][l] += a[i] * b[l];
+                for (int l = 0; l < IM_TN; ++l) acc[i][l] += a[i] * b[l];
         }
     }
 }
 
-// Y_p = diag(dtau / (1 + dtau (a_j^2 - lambda^2 mu_p))) V_p^-1 Q_p^T G into the
-// D_t u buffer (free between the update contraction and the next D_t u): rows
-// [0, ne) even, [ne, M) odd.  blockIdx.z = parity.
-template <typename T, int BN>
-__global__ void __launch_bounds__(IM_THREADS) k_imp_fwd(CurveDev c, int gate)
+// The K chunk of split s of a length-n contraction over `splits` chunks.
+__device__ __forceinline__ void im_chunk(int n, int splits, int s, int &kb, int &ke)
 {
-    __shared__ ImSmem<T, BN> sm;
-    pdl_wait();
+    int kc = (n + splits - 1) / splits;
+    kc = (kc + IM_BK - 1) / IM_BK * IM_BK;
+    kb = min(n, s * kc);
+    ke = min(n, kb + kc);
+}
+
+// Pf[s] rows [0, ne) even, [ne, M) odd: the scaled partial of split s.
+// Block (bx, by, bz): column tile, row tile, parity * splits + split.
+template <typename T>
+__device__ __forceinline__ void imp_fwd_body(ImSmem<T> &sm, const CurveDev &c, int bx, int by, int bz, int splits)
+{
     DevScalars *sc = c.sc;
-    if (gate && !sc->active) return;
-    const int p = blockIdx.z, M = c.ns - 2, h = M / 2, N = c.nx, ne = c.ine;
-    const int np = p ? c.ino : ne;
-    const int r0 = blockIdx.y * IM_BM, c0 = blockIdx.x * BN;
+    const int p = bz / splits, sp = bz % splits;
+    const int M = c.ns - 2, h = M / 2, N = c.nx, ne = c.ine, np = p ? c.ino : ne;
+    const int r0 = by * IM_BM, c0 = bx * IM_BN;
     if (r0 >= np) return;
+    int kb, ke;
+    im_chunk(np, splits, sp, kb, ke);
     const T *G = (const T *)c.G;
     const T r2 = T(0.70710678118654752440);
     const T *A = (const T *)c.ivi + (p ? (size_t)ne * ne : 0);
-    constexpr int TN = BN / 16;
-    T acc[4][TN];
+    T acc[IM_TM][IM_TN];
 #pragma unroll
-    for (int i = 0; i < 4; ++i)
+    for (int i = 0; i < IM_TM; ++i)
 #pragma unroll
-        for (int l = 0; l < TN; ++l) acc[i][l] = T(0);
+        for (int l = 0; l < IM_TN; ++l) acc[i][l] = T(0);
     if (p == 0)
-        im_product<T, BN>(sm, A, np, np, r0, c0, N, [&](int k, int col) -> T {
+        im_tile<T>(sm, A, np, np, r0, kb, ke, c0, N, [&](int k, int col) -> T {
             return k < h ? r2 * (G[(size_t)(1 + k) * N + col] + G[(size_t)(M - k) * N + col]) : G[(size_t)(1 + h) * N + col];
         }, acc);
     else
-        im_product<T, BN>(sm, A, np, np, r0, c0, N, [&](int k, int col) -> T {
+        im_tile<T>(sm, A, np, np, r0, kb, ke, c0, N, [&](int k, int col) -> T {
             return r2 * (G[(size_t)(1 + k) * N + col] - G[(size_t)(M - k) * N + col]);
         }, acc);
-    const double lam = sc->lambda, dtau = sc->dtau;
+    const T lam = (T)sc->lambda, dtau = (T)sc->dtau, tl = T(2.0 * M_PI / c.L);
     const double *mu = c.imu + (p ? ne : 0);
-    T *Y = (T *)c.D + (p ? (size_t)ne * N : 0);
+    T *out = (T *)c.isc + (size_t)sp * M * N + (p ? (size_t)ne * N : 0);
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        const int r = r0 + 4 * ty + i;
+    for (int i = 0; i < IM_TM; ++i) {
+        const int r = r0 + IM_TM * ty + i;
         if (r >= np) continue;
-        const double lm = lam * lam * mu[r];
+        const T lm = lam * lam * (T)mu[r];
 #pragma unroll
-        for (int l = 0; l < TN; ++l) {
-            const int col = c0 + TN * tx + l;
+        for (int l = 0; l < IM_TN; ++l) {
+            const int col = c0 + IM_TN * tx + l;
             if (col >= N) continue;
-            const double kw = 2.0 * M_PI * (double)(col >> 1) / c.L, a = kw * kw * kw * kw - kw * kw;
-            Y[(size_t)r * N + col] = (T)(dtau / (1.0 + dtau * (a * a - lm)) * (double)acc[i][l]);
+            const T kw = tl * (T)(col >> 1), a = kw * kw * kw * kw - kw * kw;
+            out[(size_t)r * N + col] = dtau / (T(1) + dtau * (a * a - lm)) * acc[i][l];
         }
     }
 }
 
-// U += Q (V_e Y_e, V_o Y_o), then the step's bookkeeping in the last CTA.
-template <typename T, int BN>
-__global__ void __launch_bounds__(IM_THREADS) k_imp_back(CurveDev c, int gate)
+// Pb[s] (after the c.isplits forward partials) rows [0, ne) even, [ne, M) odd:
+// partial of split s of V_p Y_p.
+template <typename T>
+__device__ __forceinline__ void imp_back_body(ImSmem<T> &sm, const CurveDev &c, int bx, int by, int bz, int splits_f,
+                                              int splits)
 {
-    __shared__ ImSmem<T, BN> sm;
-    __shared__ int am_last;
-    pdl_wait();
-    DevScalars *sc = c.sc;
-    if (gate && !sc->active) return;
-    const int M = c.ns - 2, h = M / 2, N = c.nx, ne = c.ine, no = c.ino;
-    const int r0 = blockIdx.y * IM_BM, c0 = blockIdx.x * BN;
-    const T *Y = (const T *)c.D;
-    const T *V = (const T *)c.iv;
-    constexpr int TN = BN / 16;
-    T ae[4][TN], ao[4][TN];
+    const int p = bz / splits, sp = bz % splits;
+    const int M = c.ns - 2, N = c.nx, ne = c.ine, np = p ? c.ino : ne;
+    const int r0 = by * IM_BM, c0 = bx * IM_BN;
+    if (r0 >= np) return;
+    int kb, ke;
+    im_chunk(np, splits, sp, kb, ke);
+    const size_t off = p ? (size_t)ne * N : 0, stride = (size_t)M * N;
+    const T *Pf = (const T *)c.isc;
+    const T *A = (const T *)c.iv + (p ? (size_t)ne * ne : 0);
+    T acc[IM_TM][IM_TN];
 #pragma unroll
-    for (int i = 0; i < 4; ++i)
+    for (int i = 0; i < IM_TM; ++i)
 #pragma unroll
-        for (int l = 0; l < TN; ++l) ae[i][l] = ao[i][l] = T(0);
-    im_product<T, BN>(sm, V, ne, ne, r0, c0, N, [&](int k, int col) -> T { return Y[(size_t)k * N + col]; }, ae);
-    if (no > 0)
-        im_product<T, BN>(sm, V + (size_t)ne * ne, no, no, r0, c0, N,
-                          [&](int k, int col) -> T { return Y[(size_t)(ne + k) * N + col]; }, ao);
-    T *U = (T *)c.U;
-    const T r2 = T(0.70710678118654752440);
+        for (int l = 0; l < IM_TN; ++l) acc[i][l] = T(0);
+    im_tile<T>(sm, A, np, np, r0, kb, ke, c0, N, [&](int k, int col) -> T {
+        const T *y = Pf + off + (size_t)k * N + col;
+        T t = y[0];
+        for (int q = 1; q < splits_f; ++q) t += y[q * stride];
+        return t;
+    }, acc);
+    T *out = (T *)c.isc + (size_t)(c.isplits + sp) * stride + off;
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        const int a = r0 + 4 * ty + i;
-        if (a >= ne) continue;
+    for (int i = 0; i < IM_TM; ++i) {
+        const int r = r0 + IM_TM * ty + i;
+        if (r >= np) continue;
 #pragma unroll
-        for (int l = 0; l < TN; ++l) {
-            const int col = c0 + TN * tx + l;
-            if (col >= N || !col_allowed(col, c.sym)) continue;
-            if (a < h) {
-                U[(size_t)(1 + a) * N + col] += r2 * (ae[i][l] + ao[i][l]);
-                U[(size_t)(M - a) * N + col] += r2 * (ae[i][l] - ao[i][l]);
-            } else {
-                U[(size_t)(1 + h) * N + col] += ae[i][l];
-            }
+        for (int l = 0; l < IM_TN; ++l) {
+            const int col = c0 + IM_TN * tx + l;
+            if (col < N) out[(size_t)r * N + col] = acc[i][l];
         }
     }
-    const unsigned nb = gridDim.x * gridDim.y;
-    if (!last_cta_arrive(&sc->cnt_gemm, nb, am_last)) return;
+}
+
+// U += Q (delta_e, delta_o), delta_p the split sums of the back partials; the
+// step's bookkeeping in the last of the curve's nbx finishing CTAs.
+template <typename T>
+__device__ __forceinline__ void imp_finish_body(const CurveDev &c, int bx, int nbx, int splits, int &am_last)
+{
+    DevScalars *sc = c.sc;
+    const int M = c.ns - 2, h = M / 2, N = c.nx, ne = c.ine;
+    const size_t stride = (size_t)M * N;
+    const T *Pb = (const T *)c.isc + (size_t)c.isplits * stride;
+    T *U = (T *)c.U;
+    const T r2 = T(0.70710678118654752440);
+    const long total = (long)ne * N;
+    for (long e = bx * (long)IM_THREADS + threadIdx.x; e < total; e += (long)nbx * IM_THREADS) {
+        const int a = (int)(e / N), col = (int)(e % N);
+        if (!col_allowed(col, c.sym)) continue;
+        T de = T(0), dd = T(0);
+        for (int q = 0; q < splits; ++q) {
+            de += Pb[q * stride + (size_t)a * N + col];
+            if (a < h) dd += Pb[q * stride + (size_t)(ne + a) * N + col];
+        }
+        if (a < h) {
+            U[(size_t)(1 + a) * N + col] += r2 * (de + dd);
+            U[(size_t)(M - a) * N + col] += r2 * (de - dd);
+        } else {
+            U[(size_t)(1 + h) * N + col] += de;
+        }
+    }
+    if (!last_cta_arrive(&sc->cnt_gemm, (unsigned)nbx, am_last)) return;
     if (threadIdx.x == 0) {
         sc->step += 1;
         sc->tau += sc->dtau;
         sc->lambda = sc->lambda_next;
         sc->cnt_gemm = 0;
     }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(IM_THREADS) k_imp_fwd(CurveDev c, int splits, int gate)
+{
+    __shared__ ImSmem<T> sm;
+    pdl_wait();
+    if (gate && !c.sc->active) return;
+    imp_fwd_body<T>(sm, c, blockIdx.x, blockIdx.y, blockIdx.z, splits);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(IM_THREADS) k_imp_back(CurveDev c, int splits, int gate)
+{
+    __shared__ ImSmem<T> sm;
+    pdl_wait();
+    if (gate && !c.sc->active) return;
+    imp_back_body<T>(sm, c, blockIdx.x, blockIdx.y, blockIdx.z, splits, splits);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(IM_THREADS) k_imp_finish(CurveDev c, int splits, int gate)
+{
+    __shared__ int am_last;
+    pdl_wait();
+    if (gate && !c.sc->active) return;
+    imp_finish_body<T>(c, blockIdx.x, gridDim.x, splits, am_last);
+}
+
+// Batched curves (one K chunk each): items (curve, bx, by, parity) of the two
+// products, (curve, bx, nbx, 0) of the finishing pass.
+template <typename T>
+__global__ void __launch_bounds__(IM_THREADS) k_imp_fwd_batch(const CurveDev *cv, const int4 *items)
+{
+    __shared__ ImSmem<T> sm;
+    pdl_wait();
+    const int4 it = items[blockIdx.x];
+    const CurveDev &c = cv[it.x];
+    if (!c.sc->active) return;
+    imp_fwd_body<T>(sm, c, it.y, it.z, it.w, 1);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(IM_THREADS) k_imp_back_batch(const CurveDev *cv, const int4 *items)
+{
+    __shared__ ImSmem<T> sm;
+    pdl_wait();
+    const int4 it = items[blockIdx.x];
+    const CurveDev &c = cv[it.x];
+    if (!c.sc->active) return;
+    imp_back_body<T>(sm, c, it.y, it.z, it.w, 1, 1);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(IM_THREADS) k_imp_finish_batch(const CurveDev *cv, const int4 *items)
+{
+    __shared__ int am_last;
+    pdl_wait();
+    const int4 it = items[blockIdx.x];
+    const CurveDev &c = cv[it.x];
+    if (!c.sc->active) return;
+    imp_finish_body<T>(c, it.y, it.z, 1, am_last);
 }
 
 template <typename K, typename... Args>
@@ -498,22 +608,67 @@ static cudaError_t imp_launch(K kern, dim3 grid, cudaStream_t st, Args... args)
     return e != cudaSuccess ? e : cudaGetLastError();
 }
 
-template <typename T, int BN>
+// K splits that bring the product's grid to about two CTAs per SM.
+static int imp_splits(const CurveDev &c)
+{
+    const int tiles = ((c.nx + IM_BN - 1) / IM_BN) * ((c.ine + IM_BM - 1) / IM_BM) * 2;
+    int s = (2 * 152 + tiles - 1) / tiles;
+    const int smax = std::max(1, c.ino / (4 * IM_BK));   // chunks of at least 64
+    return std::max(1, std::min(std::min(s, c.isplits), smax));
+}
+
+size_t implicit_scratch_bytes(int ns, int nx, int prec, int splits)
+{
+    return 2 * (size_t)splits * (size_t)(ns - 2) * nx * (prec ? 4 : 8);
+}
+
+void implicit_batch_items(const CurveDev &c, int curve, std::vector<int4> &prod, std::vector<int4> &fin)
+{
+    const int gx = (c.nx + IM_BN - 1) / IM_BN, gy = (c.ine + IM_BM - 1) / IM_BM;
+    for (int p = 0; p < 2; ++p)
+        for (int by = 0; by < gy; ++by) {
+            if (by * IM_BM >= (p ? c.ino : c.ine)) continue;
+            for (int bx = 0; bx < gx; ++bx) prod.push_back(make_int4(curve, bx, by, p));
+        }
+    const long total = (long)c.ine * c.nx;
+    const int nbx = (int)std::min<long>(8, (total + IM_THREADS - 1) / IM_THREADS);
+    for (int bx = 0; bx < nbx; ++bx) fin.push_back(make_int4(curve, bx, nbx, 0));
+}
+
+template <typename T>
 static cudaError_t implicit_t(const CurveDev &c, int gate, cudaStream_t st)
 {
-    const int gx = (c.nx + BN - 1) / BN, gy = (c.ine + IM_BM - 1) / IM_BM;
-    cudaError_t e = imp_launch(k_imp_fwd<T, BN>, dim3(gx, gy, 2), st, c, gate);
+    const int sp = imp_splits(c);
+    const int gx = (c.nx + IM_BN - 1) / IM_BN, gy = (c.ine + IM_BM - 1) / IM_BM;
+    cudaError_t e = imp_launch(k_imp_fwd<T>, dim3(gx, gy, 2 * sp), st, c, sp, gate);
+    if (e == cudaSuccess) e = imp_launch(k_imp_back<T>, dim3(gx, gy, 2 * sp), st, c, sp, gate);
     if (e != cudaSuccess) return e;
-    return imp_launch(k_imp_back<T, BN>, dim3(gx, gy), st, c, gate);
+    const long total = (long)c.ine * c.nx;
+    const int gf = (int)std::min<long>(4 * 152, (total + IM_THREADS - 1) / IM_THREADS);
+    return imp_launch(k_imp_finish<T>, dim3(gf), st, c, sp, gate);
 }
 
 cudaError_t launch_implicit_update(const CurveDev &c, int gate, cudaStream_t st)
 {
     if (!c.impl) return cudaErrorInvalidValue;
-    // narrow column tiles where the grid would not fill the GPU
-    const bool narrow = c.nx <= 32 || (c.nx / 64) * ((c.ine + IM_BM - 1) / IM_BM) < 2 * 152;
-    if (c.prec) return narrow ? implicit_t<float, 32>(c, gate, st) : implicit_t<float, 64>(c, gate, st);
-    return narrow ? implicit_t<double, 32>(c, gate, st) : implicit_t<double, 64>(c, gate, st);
+    return c.prec ? implicit_t<float>(c, gate, st) : implicit_t<double>(c, gate, st);
+}
+
+cudaError_t launch_implicit_batch(int prec, const CurveDev *cv, const int4 *prod, int nprod, const int4 *fin, int nfin,
+                                  cudaStream_t st)
+{
+    if (nprod <= 0) return cudaSuccess;
+    cudaError_t e;
+    if (prec) {
+        e = imp_launch(k_imp_fwd_batch<float>, dim3(nprod), st, cv, prod);
+        if (e == cudaSuccess) e = imp_launch(k_imp_back_batch<float>, dim3(nprod), st, cv, prod);
+        if (e == cudaSuccess) e = imp_launch(k_imp_finish_batch<float>, dim3(nfin), st, cv, fin);
+    } else {
+        e = imp_launch(k_imp_fwd_batch<double>, dim3(nprod), st, cv, prod);
+        if (e == cudaSuccess) e = imp_launch(k_imp_back_batch<double>, dim3(nprod), st, cv, prod);
+        if (e == cudaSuccess) e = imp_launch(k_imp_finish_batch<double>, dim3(nfin), st, cv, fin);
+    }
+    return e;
 }
 
 }  // namespace ks

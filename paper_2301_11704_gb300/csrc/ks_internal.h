@@ -4,6 +4,7 @@
 
 #include <cstddef>
 #include <cstdint>
+#include <vector>
 
 #include <cuda_runtime.h>
 
@@ -213,6 +214,8 @@ struct Layout {
     size_t off_xdft;                   // its DFT matrices, split into BF16 parts
     int impl;                          // full-linear-implicit stepping: its eigenbases (0: IMEX)
     size_t off_iv, off_ivi, off_imu;   // V (even block, then odd), V^-1 likewise, eigenvalues (FP64)
+    size_t off_isc;                    // the split partials of its two products
+    int isplits;                       // K chunks they hold
 };
 
 struct CurveDev {
@@ -241,6 +244,8 @@ struct CurveDev {
     int ine, ino;          // their sizes: ceil(M/2), floor(M/2)
     void *iv, *ivi;        // V_e [ine][ine] then V_o [ino][ino], row-major (storage type); V^-1 alike
     double *imu;           // eigenvalues: ine of the even part, then ino of the odd part
+    void *isc;             // split partials of the increment's products: 2 isplits [M][N]
+    int isplits;           // K chunks those partials hold (IMP_SPLIT_MAX; 1 for batched curves)
     int F;                 // FFT length of the s-contraction (0: dense form)
     void *chat, *ftw;      // FFT form: kernel spectrum / F and twiddles (complex, storage type);
                            // four-step form: spectrum stored [k1][k2] for k = k1 + F1 k2 (both
@@ -346,8 +351,17 @@ size_t xdft_bytes(int nx);
 cudaError_t launch_setup_xdft(const CurveDev &c, cudaStream_t st);
 
 // ---- full-linear-implicit stepping (ks_implicit.cu)
-// Bytes of the eigenbases of a curve with N_s sections in the storage type.
+// Bytes of the eigenbases of a curve with N_s sections in the storage type, and
+// of the split partials of the increment's two products (at most IMP_SPLIT_MAX
+// K chunks each).
+constexpr int IMP_SPLIT_MAX = 8;
 size_t implicit_bytes(int ns, int prec);
+size_t implicit_scratch_bytes(int ns, int nx, int prec, int splits);
+// Work items of a batched curve's increment: (curve, bx, by, parity) of each
+// product, (curve, bx, nbx, 0) of the finishing pass.
+void implicit_batch_items(const CurveDev &c, int curve, std::vector<int4> &prod, std::vector<int4> &fin);
+cudaError_t launch_implicit_batch(int prec, const CurveDev *cv, const int4 *prod, int nprod, const int4 *fin, int nfin,
+                                  cudaStream_t st);
 // One-time set-up: eigendecomposition of the interior D_t^2 (FP64, cuSOLVER,
 // opened at run time), stored in the curve's workspace.  Synchronous.
 ks_status setup_implicit(const CurveDev &c, cudaStream_t st);

@@ -155,6 +155,8 @@ Layout make_layout(int ns, int nx, int prec, int allow_split, int bn, int s_tran
     l.off_iv = off; off += impl ? al256((ne * ne + no * no) * b) : 0;
     l.off_ivi = off; off += impl ? al256((ne * ne + no * no) * b) : 0;
     l.off_imu = off; off += impl ? al256((ne + no) * 8) : 0;
+    l.isplits = allow_split ? IMP_SPLIT_MAX : 1;
+    l.off_isc = off; off += impl ? al256(implicit_scratch_bytes(ns, nx, prec, l.isplits)) : 0;
     l.total = off;
     return l;
 }
@@ -213,6 +215,8 @@ CurveDev bind_layout(const ks_params *p, const Layout &l, void *base)
     d.iv = l.impl ? (void *)(b + l.off_iv) : nullptr;
     d.ivi = l.impl ? (void *)(b + l.off_ivi) : nullptr;
     d.imu = l.impl ? (double *)(b + l.off_imu) : nullptr;
+    d.isc = l.impl ? (void *)(b + l.off_isc) : nullptr;
+    d.isplits = l.isplits;
     d.cot = b + l.off_cot;
     d.sig = b + l.off_sig;
     d.tau = b + l.off_tau;

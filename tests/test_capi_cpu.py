@@ -149,19 +149,23 @@ def test_invalid_implicit_parameters_are_rejected(lib, bad):
 def test_implicit_workspace_holds_the_eigenbases(lib, prec, b, ns):
     """Full-linear-implicit stepping: V and V^-1 of the even (ceil(M/2) square) and
     odd (floor(M/2) square) parts of D~^2 in the storage type, their eigenvalues
-    in FP64; same s-form as the IMEX scheme."""
+    in FP64, and the split partials of the two products (2 x 8 x M x N); same
+    s-form as the IMEX scheme."""
     nx = 64
     imex = lib.ks_curve_workspace_bytes(ctypes.byref(_params(precision=prec, nx=nx, ns=ns)))
     impl = lib.ks_curve_workspace_bytes(ctypes.byref(_params(precision=prec, nx=nx, ns=ns, scheme=1)))
     M = ns - 2
     ne, no = (M + 1) // 2, M // 2
     al = lambda x: (x + 255) // 256 * 256
-    assert impl - imex == 2 * al((ne * ne + no * no) * b) + al(M * 8)
+    assert impl - imex == 2 * al((ne * ne + no * no) * b) + al(M * 8) + al(2 * 8 * M * nx * b)
     assert lib.ks_curve_s_form(ctypes.byref(_params(precision=prec, nx=nx, ns=ns, scheme=1))) == \
         lib.ks_curve_s_form(ctypes.byref(_params(precision=prec, nx=nx, ns=ns)))
 
 
-def test_implicit_batches_are_rejected(lib):
-    ps = (KSParams * 2)(_params(scheme=1), _params(scheme=1))
+def test_batches_with_mixed_schemes_are_rejected(lib):
+    ps = (KSParams * 2)(_params(scheme=1), _params(scheme=0))
     assert lib.ks_batch_workspace_bytes(2, ps) == 0
-    assert b"IMEX" in lib.ks_last_error()
+    assert b"scheme" in lib.ks_last_error()
+    ok = (KSParams * 2)(_params(scheme=1), _params(scheme=1, ns=200))
+    plain = (KSParams * 2)(_params(), _params(ns=200))
+    assert lib.ks_batch_workspace_bytes(2, ok) > lib.ks_batch_workspace_bytes(2, plain) > 0

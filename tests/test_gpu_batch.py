@@ -187,3 +187,33 @@ def test_batch_four_step_items_match_the_oracle_fp64():
         assert np.abs(b.get_state(k).cpu().numpy() - xo).max() <= 1e-10 * np.abs(xo).max()
         assert abs(out["J_arc"][k] - sco["J_arc"]) <= 1e-10 * sco["J_arc"]
     b.close()
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-11), ("fp32", 2e-5)])
+def test_implicit_batch_matches_independent_curves(precision, tol):
+    """Full-linear-implicit stepping in a batch (its eigenbases set up in parallel
+    host threads; one K chunk per product) at dtau = 0.2, far beyond the IMEX
+    limit of every curve: each curve equals its single-curve implicit run, and
+    the FP64 curves the oracle's implicit descent."""
+    base = gen.workload(3)
+    specs = [gen.CurveSpec(3, i, base[i].L, base[i].N, Ns, gen.mapping_scale(Ns), dtau=0.2, steps=0)
+             for i, Ns in zip((0, 1, 2, 3, 5, 6, 9), (19, 130, 65, 200, 400, 1100, 1300))]
+    ins = [_inputs(s) for s in specs]
+    b = KSBatch(specs, [i[0] for i in ins], [i[1] for i in ins], precision=precision, conv="jarc", scheme="implicit")
+    b.init_trial(np.array([i[2] for i in ins]), [i[3] for i in ins])
+    out = b.descend(20)
+    for k, s in enumerate(specs):
+        up, um, amps, vp = ins[k]
+        c = KSCurve(s.L, s.N, s.Ns, s.S, up, um, dtau=s.dtau, precision=precision, scheme="implicit")
+        c.init_trial(0.0, None, amps, vp)
+        ref = c.descend(20)
+        xb = b.get_state(k).double().cpu().numpy()
+        xc = c.get_state().double().cpu().numpy()
+        assert np.abs(xb - xc).max() <= tol * np.abs(xc).max(), (k, s.Ns)
+        assert abs(out["J"][k] - ref["J"]) <= tol * ref["J"]
+        c.close()
+        if precision == "fp64" and s.Ns <= 200:
+            U = oracle.curve_init(s.M, s.S, up, um, amps=amps, vp=vp)
+            Uo, _, sco, _ = oracle.curve_descend(U, s.L, s.S, 20, dtau=s.dtau, scheme=oracle.IMPLICIT)
+            assert np.abs(xb - oracle.curve_physical(Uo)).max() <= 1e-10 * np.abs(xb).max()
+    b.close()
