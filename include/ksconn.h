@@ -21,8 +21,10 @@
  *    thread; outputs are then unspecified, and the curve stays usable unless
  *    the status is KS_ECUDA (a failed CUDA call; the CUDA context may be lost).
  *  - Device pointers ("_dev") point to memory of the current CUDA device,
- *    allocated by the caller.  The library never allocates or frees device
- *    memory itself: every buffer it uses lives in the caller's workspace.
+ *    allocated by the caller.  Every buffer the library uses lives in the
+ *    caller's workspace; the one exception is the one-time set-up of
+ *    KS_SCHEME_IMPLICIT (ks_curve_create / ks_batch_create), whose eigensolver
+ *    allocates and frees temporary device memory before create returns.
  *    Host pointers ("_host" or scalar outputs) are ordinary host memory.
  *  - Physical curve arrays are row-major [N_s][N] in the storage type of the
  *    curve (double for KS_FP64, float for the others); row m is section s_m,

@@ -35,7 +35,7 @@ def main(argv=None):
 
     specs = gen.workload(args.cfg)
     eps = np.finfo(np.float32 if args.precision == "fp32" else np.float64).eps
-    tol = args.tol if args.tol is not None else max(1e-8, 8 * eps)
+    tol = float(args.tol if args.tol is not None else max(1e-8, 8 * eps))
     ins = [(gen.end_points(s), gen.perturbation(s)) for s in specs]
     t0 = time.perf_counter()
     b = KSBatch(specs, [i[0][0] for i in ins], [i[0][1] for i in ins], precision=args.precision, conv="jrel",
@@ -61,22 +61,26 @@ def main(argv=None):
             if x["converged"] and done_at[k] is None:
                 done_at[k] = int(x["step"])
         bad = sum(1 for x in sc if x["status"] != 0)
+        fin = jr[np.isfinite(jr)]
         print(json.dumps({"steps": steps, "wall_s": round(time.perf_counter() - t0, 1), "gpu_s": round(gpu_ms / 1e3, 2),
                           "converged": sum(d is not None for d in done_at), "nonfinite": bad,
-                          "J_rel_quantiles": [float(np.quantile(jr, q)) for q in (0, 0.25, 0.5, 0.75, 1.0)]}),
+                          "J_rel_quantiles_finite": [float(np.quantile(fin, q)) for q in (0, 0.1, 0.25, 0.5, 0.75, 0.9, 1.0)]
+                          if fin.size else None}),
               flush=True)
         if all(d is not None or x["status"] != 0 for d, x in zip(done_at, sc)):
             break
     sc = b.scalars()
     b.close()
-    recs = [{"curve": k, "L": s.L, "N_x": s.N, "N_s": s.Ns, "converged_at_step": done_at[k],
-             "step": int(x["step"]), "tau": x["tau"], "J_rel": x["J"] / max(x["Dnorm"], 1e-300), "J_arc": x["J_arc"],
-             "G_norm": x["G_norm"], "status": int(x["status"])} for k, (s, x) in enumerate(zip(specs, sc))]
+    recs = [{"curve": k, "L": float(s.L), "N_x": int(s.N), "N_s": int(s.Ns), "converged_at_step": done_at[k],
+             "step": int(x["step"]), "tau": float(x["tau"]), "J_rel": float(x["J"] / max(x["Dnorm"], 1e-300)),
+             "J_arc": float(x["J_arc"]), "G_norm": float(x["G_norm"]), "status": int(x["status"])}
+            for k, (s, x) in enumerate(zip(specs, sc))]
     conv = [r["converged_at_step"] for r in recs if r["converged_at_step"] is not None]
     print(json.dumps({"cfg": args.cfg, "precision": args.precision, "scheme": args.scheme, "dtau": args.dtau,
                       "tol": tol, "setup_s": round(setup_s, 2), "steps_run": steps, "gpu_s": round(gpu_ms / 1e3, 2),
                       "ms_per_step": gpu_ms / max(1, steps), "converged": len(conv),
                       "steps_to_converge_quantiles": [int(np.quantile(conv, q)) for q in (0, 0.5, 1.0)] if conv else None,
+                      "nonfinite": [r["curve"] for r in recs if r["status"] != 0],
                       "curves": recs}))
     return 0
 

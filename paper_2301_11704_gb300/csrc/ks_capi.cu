@@ -147,12 +147,17 @@ static bool fused_step(const ks_curve *c)
 
 // The update of one step: the update contraction (G and |G|^2), and for the
 // implicit scheme the two products of its increment.
+// D_t u of the updated state in a step: its first pass already ran inside the
+// update when the form chains them.
+static int store_mode(const ks_curve *c) { return ks::f4h_chained(c->d) ? ks::GM_STORE_P23 : ks::GM_STORE; }
+
 // impl_ev (may be null): two events bracketing the implicit products.
 static ks_status launch_update(ks_curve *c, int discrete, cudaStream_t st, cudaEvent_t *pass_ev,
                                cudaEvent_t *impl_ev = nullptr)
 {
     if (!c->d.impl) {
-        KS_CUDA(ks::launch_dt(c->d, fused_step(c) ? ks::GM_STEP : ks::GM_UPDATE, discrete, 1, st, pass_ev));
+        const int um = fused_step(c) ? ks::GM_STEP : (ks::f4h_chained(c->d) ? ks::GM_UPDATE_F : ks::GM_UPDATE);
+        KS_CUDA(ks::launch_dt(c->d, um, discrete, 1, st, pass_ev));
         return KS_OK;
     }
     KS_CUDA(ks::launch_dt(c->d, ks::GM_GRAD, discrete, 1, st, pass_ev));
@@ -169,7 +174,7 @@ ks_status launch_step(ks_curve *c, int discrete, cudaStream_t st)
     KS_CUDA(ks::launch_rows(c->d, ks::ROWS_STEP, st));
     ks_status s = launch_update(c, discrete, st, nullptr);
     if (s != KS_OK) return s;
-    if (!fused_step(c)) KS_CUDA(ks::launch_dt(c->d, ks::GM_STORE, 0, 1, st));
+    if (!fused_step(c)) KS_CUDA(ks::launch_dt(c->d, store_mode(c), 0, 1, st));
     return KS_OK;
 }
 
@@ -253,7 +258,7 @@ ks_status enqueue_steps(ks_curve *c, int64_t nsteps, double tol)
         if (us != KS_OK) return us;
         if (prof) KS_CUDA(cudaEventRecord(ev[3], c->st));
         if (prof) KS_CUDA(cudaEventRecord(ev[4], c->st));
-        if (!fused_step(c)) KS_CUDA(ks::launch_dt(c->d, ks::GM_STORE, 0, 1, c->st, pass_d));
+        if (!fused_step(c)) KS_CUDA(ks::launch_dt(c->d, store_mode(c), 0, 1, c->st, pass_d));
         if (prof) {
             KS_CUDA(cudaEventRecord(ev[5], c->st));
             c->prof_steps[c->prof_used] = 0;

@@ -480,6 +480,9 @@ __global__ void __launch_bounds__(F4_THREADS) k_f4h_p2(CurveDev c, int discrete,
 template <typename T, int F1, int F2>
 __global__ void __launch_bounds__(F4_THREADS) k_f4_p3(CurveDev c, int mode, int discrete, int gate)
 {
+    // GM_UPDATE_F: the update, then pass 1 of D_t u of the updated columns
+    const bool chain = mode == GM_UPDATE_F;
+    if (chain) mode = GM_UPDATE;
     using Sec = F4Sector<T>;
     using St = F4Stage<T, F1>;
     constexpr int R = F1 / 32, LS = St::LS, TS = St::TS, MPC = Sec::MPC, NV = Sec::NV;
@@ -541,6 +544,8 @@ __global__ void __launch_bounds__(F4_THREADS) k_f4_p3(CurveDev c, int mode, int 
                 ld_sector(Ah + o, av[h]);
                 if (mode == GM_UPDATE) ld_sector(U + o, uv[h]);
                 wv[h] = c.w[j];
+            } else if (chain && (j == 0 || j == P)) {
+                ld_sector(U + (size_t)j * N + 2 * jm0, uv[h]);   // the end rows, for the chained pass 1
             }
         }
         if (jv[0] >= ns) break;
@@ -579,6 +584,46 @@ __global__ void __launch_bounds__(F4_THREADS) k_f4_p3(CurveDev c, int mode, int 
                 for (int q = 0; q < NV; ++q) g[q] = T(0);
             }
             if (mode == GM_GRAD) st_sector(G + o, g);
+            if (chain) {   // z_j = tau_j u_j of the updated column, at the position the epilogue just read
+                const T cs = ((const T *)c.tau)[j];
+#pragma unroll
+                for (int q = 0; q < MPC; ++q)
+                    tile[q * TS + tn * LS + n1] = {sector_col_ok(jm0, 2 * q, sym) ? cs * uv[h][2 * q] : T(0),
+                                                   sector_col_ok(jm0, 2 * q + 1, sym) ? cs * uv[h][2 * q + 1] : T(0)};
+            }
+        }
+    }
+    if (chain) {
+        // pass 1 of D_t u (Toeplitz-Hankel form: z_k = tau_k u_k for k <= P, zero above):
+        // the rows past the curve, then FFT over n1, step twiddles, into the scratch
+        // locations this CTA read (no other CTA reads them)
+#pragma unroll
+        for (int i = 0; i < R; ++i) {
+            const int n1 = threadIdx.x / F4W + 32 * i;
+            if (F2 * n1 + n2_0 + tn >= ns)
+#pragma unroll
+                for (int q = 0; q < MPC; ++q) tile[q * TS + tn * LS + n1] = {T(0), T(0)};
+        }
+        const cpx<T> *t1 = (const cpx<T> *)c.ftw + F + (size_t)(n2_0 + warp) * F1;
+        cpx<T> tw1[R];
+#pragma unroll
+        for (int a = 0; a < R; ++a) tw1[a] = t1[a * 32 + lane];
+        __syncthreads();
+        for (int q = 0; q < MPC; ++q) {
+            cpx<T> *line = tile + q * TS + warp * LS;
+            cpx<T> v[R];
+#pragma unroll
+            for (int a = 0; a < R; ++a) v[a] = line[lane + 32 * a];
+            __syncwarp();
+            reg_fft_fwd<T, R>(v, twl, w32, lane);
+#pragma unroll
+            for (int a = 0; a < R; ++a) line[a * 32 + lane] = cmul(v[a], tw1[a]);
+        }
+        __syncthreads();
+        cpx<T> *So = (cpx<T> *)c.f4s;
+        for (int e = threadIdx.x; e < MPC * F1 * F4W; e += F4_THREADS) {
+            const int w = e % F4W, r = (e / F4W) % F1, q = e / (F4W * F1);
+            So[((size_t)(jm0 + q) * F1 + r) * F2 + n2_0 + w] = tile[q * TS + w * LS + r];
         }
     }
     if (mode == GM_STORE) return;
@@ -1347,7 +1392,10 @@ static cudaError_t f4_run(const CurveDev &c, int mode, int discrete, int gate, c
     cudaError_t e;
     if ((e = set_smem(k_f4_p1<T, F1, F2>, sm1)) != cudaSuccess) return e;
     if ((e = set_smem(k_f4_p3<T, F1, F2>, sm1)) != cudaSuccess) return e;
-    if ((e = launch_pdl(k_f4_p1<T, F1, F2>, dim3(nmb, F2 / F4W), sm1, st, c, mode, discrete, gate)) != cudaSuccess)
+    // GM_STORE_P23: pass 1 ran inside the preceding update's pass 3
+    if (mode == GM_STORE_P23) mode = GM_STORE;
+    else if ((e = launch_pdl(k_f4_p1<T, F1, F2>, dim3(nmb, F2 / F4W), sm1, st, c, mode == GM_UPDATE_F ? GM_UPDATE : mode,
+                             discrete, gate)) != cudaSuccess)
         return e;
     if (pass_ev && (e = cudaEventRecord(pass_ev[0], st)) != cudaSuccess) return e;
     if (c.f4h) e = launch_pdl(k_f4h_p2<T, F1, F2>, dim3((F1 / 2 + 1 + F4W - 1) / F4W, nm), 0, st, c, discrete, gate);
@@ -1417,6 +1465,7 @@ static cudaError_t f4c_dispatch(const CurveDev &c, int mode, int discrete, int g
 cudaError_t launch_f4(const CurveDev &c, int mode, int discrete, int gate, cudaStream_t st, cudaEvent_t *pass_ev)
 {
     if (mode == GM_STEP && !c.f4c) return cudaErrorInvalidValue;
+    if ((mode == GM_UPDATE_F || mode == GM_STORE_P23) && !f4h_chained(c)) return cudaErrorInvalidValue;
     if (c.f4c) {
         if (!c.prec) return f4c_dispatch<double, 1>(c, mode, discrete, gate, st);
         return f4c_mpc(c.prec, c.nx, c.F1, c.F2) == 2 ? f4c_dispatch<float, 2>(c, mode, discrete, gate, st)

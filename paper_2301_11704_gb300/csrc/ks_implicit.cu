@@ -326,14 +326,14 @@ ks_status setup_implicit(const CurveDev &c, cudaStream_t st)
 // ---------------------------------------------------------------------------
 // Per step
 // ---------------------------------------------------------------------------
-// Three launches, all gated like the contractions:
+// Up to four launches, all gated like the contractions:
 //   k_imp_fwd:    partial products over K chunks ("splits", so that the grid
 //                 fills the GPU) of V_p^-1 (Q_p^T G), folding G into the
 //                 bases on load, each partial scaled by the implicit factor
 //                 dtau / (1 + dtau (a_j^2 - lambda^2 mu)) (linear, so the sum
 //                 of the scaled partials is the scaled sum);
-//   k_imp_back:   partial products of V_p with Y_p = the sum of those partials
-//                 (summed on load, in split order);
+//   k_imp_sum:    Y_p = the sum of those partials in split order (when split);
+//   k_imp_back:   partial products of V_p with Y_p;
 //   k_imp_finish: the sum of the back partials in split order, unfolded into
 //                 U's update, and the step's bookkeeping in the last CTA.
 // The products are register-tiled on the CUDA cores: 128 x 64 outputs per CTA,
@@ -530,6 +530,22 @@ __device__ __forceinline__ void imp_finish_body(const CurveDev &c, int bx, int n
     }
 }
 
+// Y = the split sum of the forward partials, in split order, into split 0's slot
+// (the back product then reads one value per element instead of `splits`).
+template <typename T>
+__global__ void __launch_bounds__(IM_THREADS) k_imp_sum(CurveDev c, int splits, int gate)
+{
+    pdl_wait();
+    if (gate && !c.sc->active) return;
+    const size_t stride = (size_t)(c.ns - 2) * c.nx;
+    T *Pf = (T *)c.isc;
+    for (size_t e = blockIdx.x * (size_t)IM_THREADS + threadIdx.x; e < stride; e += (size_t)gridDim.x * IM_THREADS) {
+        T t = Pf[e];
+        for (int q = 1; q < splits; ++q) t += Pf[q * stride + e];
+        Pf[e] = t;
+    }
+}
+
 template <typename T>
 __global__ void __launch_bounds__(IM_THREADS) k_imp_fwd(CurveDev c, int splits, int gate)
 {
@@ -545,7 +561,7 @@ __global__ void __launch_bounds__(IM_THREADS) k_imp_back(CurveDev c, int splits,
     __shared__ ImSmem<T> sm;
     pdl_wait();
     if (gate && !c.sc->active) return;
-    imp_back_body<T>(sm, c, blockIdx.x, blockIdx.y, blockIdx.z, splits, splits);
+    imp_back_body<T>(sm, c, blockIdx.x, blockIdx.y, blockIdx.z, 1, splits);   // forward partials summed
 }
 
 template <typename T>
@@ -641,9 +657,12 @@ static cudaError_t implicit_t(const CurveDev &c, int gate, cudaStream_t st)
     const int sp = imp_splits(c);
     const int gx = (c.nx + IM_BN - 1) / IM_BN, gy = (c.ine + IM_BM - 1) / IM_BM;
     cudaError_t e = imp_launch(k_imp_fwd<T>, dim3(gx, gy, 2 * sp), st, c, sp, gate);
+    const long total = (long)c.ine * c.nx;
+    if (e == cudaSuccess && sp > 1)
+        e = imp_launch(k_imp_sum<T>, dim3((int)std::min<long>(4 * 152, (2 * total + IM_THREADS - 1) / IM_THREADS)), st,
+                       c, sp, gate);
     if (e == cudaSuccess) e = imp_launch(k_imp_back<T>, dim3(gx, gy, 2 * sp), st, c, sp, gate);
     if (e != cudaSuccess) return e;
-    const long total = (long)c.ine * c.nx;
     const int gf = (int)std::min<long>(4 * 152, (total + IM_THREADS - 1) / IM_THREADS);
     return imp_launch(k_imp_finish<T>, dim3(gf), st, c, sp, gate);
 }

@@ -192,7 +192,11 @@ __host__ __device__ inline long long wait_bound(const DevScalars &s) { return s.
 enum RowsMode { ROWS_STEP = 0, ROWS_EVAL = 1 };
 // GM_STEP (clustered four-step form only): GM_UPDATE, then GM_STORE of the
 // updated state in the same launch.
-enum GemmMode { GM_STORE = 0, GM_UPDATE = 1, GM_GRAD = 2, GM_STEP = 3 };
+// The three-launch four-step form on the Toeplitz and Hankel parts (single
+// curves, f4h) chains a step's two contractions: GM_UPDATE_F is GM_UPDATE whose
+// third pass also runs the first pass of D_t u of the updated columns (the same
+// CTA lines and scratch locations), GM_STORE_P23 the rest of that D_t u.
+enum GemmMode { GM_STORE = 0, GM_UPDATE = 1, GM_GRAD = 2, GM_STEP = 3, GM_UPDATE_F = 4, GM_STORE_P23 = 5 };
 
 // Offsets into the caller's workspace.
 struct Layout {
@@ -257,6 +261,9 @@ struct CurveDev {
     double *ends, *pert;
     DevScalars *sc;
 };
+
+// A curve whose step chains its two contractions (GM_UPDATE_F, GM_STORE_P23).
+inline bool f4h_chained(const CurveDev &c) { return c.f4 && c.f4h && !c.f4c && !c.f4b && !c.impl; }
 
 // allow_split = 0 lays a curve out without split contractions (batched curves
 // get their parallelism from the batch); bn = 0 picks the column tile width.

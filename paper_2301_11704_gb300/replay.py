@@ -4,6 +4,10 @@ modes, s0 = 0, dtau = 0.01, the trial curve of eq. KSE_initial_curve with a = 0,
 and the descent run until J_arc < 1e-12 (eq. J_arc).
 
     python -m paper_2301_11704_gb300.replay E1-E2 [--precision fp64] [--max-tau 20000]
+    python -m paper_2301_11704_gb300.replay E1-E2 --M 300 --scheme implicit --dtau 0.2 --tol 0
+
+(the second: the floor of J_arc at M = 300 with the full-linear-implicit step,
+for the spectral convergence of J_arc,min in M, Fig. spectral_accuracy)
 
 The end-point equilibria E1, E2, E3 are stored input data (Newton solutions of
 the discretised KSE in the odd subspace; their unstable eigenvalues reproduce
@@ -78,30 +82,37 @@ def default_symmetry(orbit: str) -> int:
 
 
 def run(orbit: str, precision: str = "fp64", tol: float = 1e-12, max_tau: float = 2.0e4,
-        record_every: int = 1000, device=None, log=None, symmetry=None, save=None):
+        record_every: int = 1000, device=None, log=None, symmetry=None, save=None, M=None, S=None,
+        dtau=DTAU_PAPER, scheme="imex", s_transform="auto"):
     """Descends the trial curve of `orbit` until J_arc < tol or tau >= max_tau.
+    M and S default to the orbit's row of Table tab:parameters; scheme
+    "implicit" takes every linear term of G implicitly (the fixed points are
+    those of the paper's scheme; dtau can be far larger).
 
     Returns a dict with the settings, the (tau, J, J_arc) history every
     `record_every` steps, and the final state's cost."""
     from .curve import KSCurve
-    M, S = ORBITS[orbit]
+    M0, S0 = ORBITS[orbit]
+    M = M0 if M is None else int(M)
+    S = S0 if S is None else float(S)
     um, up = end_points(orbit)
     sym = default_symmetry(orbit) if symmetry is None else int(symmetry)
-    c = KSCurve(L_PAPER, N_PAPER, M + 2, S, up, um, s0=0.0, dtau=DTAU_PAPER, precision=precision,
-                adjoint="paper", conv="jarc", check_ends=True, symmetry=sym, device=device)
+    c = KSCurve(L_PAPER, N_PAPER, M + 2, S, up, um, s0=0.0, dtau=dtau, precision=precision,
+                adjoint="paper", conv="jarc", check_ends=True, symmetry=sym, device=device, scheme=scheme,
+                s_transform=s_transform)
     J2, Ja = c.cost()
     hist = [(0.0, float(np.sqrt(J2)), float(Ja))]
     t0 = time.perf_counter()
-    max_steps = int(round(max_tau / DTAU_PAPER))
+    max_steps = int(round(max_tau / dtau))
     steps = 0
     converged = False
     while steps < max_steps:
         n = min(record_every, max_steps - steps)
         out = c.descend(n, tol)
         steps += out["steps"]
-        hist.append((steps * DTAU_PAPER, out["J"], out["J_arc"]))
+        hist.append((steps * dtau, out["J"], out["J_arc"]))
         if log is not None and len(hist) % 50 == 0:
-            print(json.dumps({"orbit": orbit, "tau": steps * DTAU_PAPER, "J": out["J"], "J_arc": out["J_arc"]}),
+            print(json.dumps({"orbit": orbit, "tau": steps * dtau, "J": out["J"], "J_arc": out["J_arc"]}),
                   file=log, flush=True)
         if out["steps"] < n or out["J_arc"] < tol:
             converged = out["J_arc"] < tol
@@ -112,10 +123,10 @@ def run(orbit: str, precision: str = "fp64", tol: float = 1e-12, max_tau: float 
     if save:
         np.save(save, c.get_state().double().cpu().numpy())
     c.close()
-    return dict(orbit=orbit, M=M, S=S, N=N_PAPER, L=L_PAPER, dtau=DTAU_PAPER, precision=precision, tol=tol,
-                symmetry=sym,
-                steps=steps, tau=steps * DTAU_PAPER, J=hist[-1][1], J_arc=hist[-1][2], converged=converged,
-                seconds=wall, history=hist)
+    return dict(orbit=orbit, M=M, S=S, N=N_PAPER, L=L_PAPER, dtau=dtau, scheme=scheme, s_transform=s_transform,
+                precision=precision, tol=tol, symmetry=sym,
+                steps=steps, tau=steps * dtau, J=hist[-1][1], J_arc=hist[-1][2],
+                J_arc_min=min(h[2] for h in hist), converged=converged, seconds=wall, history=hist)
 
 
 def main(argv=None):
@@ -128,9 +139,15 @@ def main(argv=None):
     ap.add_argument("--history", action="store_true", help="print the full history")
     ap.add_argument("--symmetry", type=int, default=None, help="0 none, 1 odd, 3 odd and L/2-periodic")
     ap.add_argument("--save", default=None, help="write the final physical curve to this .npy file")
+    ap.add_argument("--M", type=int, default=None, help="interior sections (default: Table tab:parameters)")
+    ap.add_argument("--S", type=float, default=None, help="map scale (default: Table tab:parameters)")
+    ap.add_argument("--dtau", type=float, default=DTAU_PAPER)
+    ap.add_argument("--scheme", default="imex", choices=["imex", "implicit"])
+    ap.add_argument("--s-transform", default="auto", choices=["auto", "dense", "fft", "fft4", "fft4c"])
     args = ap.parse_args(argv)
     res = run(args.orbit, args.precision, args.tol, args.max_tau, args.record_every, log=sys.stderr,
-              symmetry=args.symmetry, save=args.save)
+              symmetry=args.symmetry, save=args.save, M=args.M, S=args.S, dtau=args.dtau, scheme=args.scheme,
+              s_transform=args.s_transform)
     if not args.history:
         h = res["history"]
         res["history"] = h[:: max(1, len(h) // 40)] + [h[-1]]
