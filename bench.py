@@ -449,6 +449,30 @@ def implicit_context(dev, timed_steps, K, dtau=0.5):
     return out
 
 
+def symmetric_context(dev, timed_steps, K):
+    """The L=44, N_x=128, N_s=4096 curve in FP32 held in the odd subspace
+    (symmetry = 1: real parts of every section's coefficients zero, Sec. V.B)
+    beside the general run: the three-launch four-step form then transforms the
+    imaginary columns of two modes as one sequence."""
+    from paper_2301_11704_gb300 import gen
+    from paper_2301_11704_gb300.curve import KSCurve
+    sl = spec_of("large")
+    up, um = gen.end_points(sl)
+    amps, vp = gen.perturbation(sl)
+    out = {"workload": "L=%g N_x=%d N_s=%d FP32" % (sl.L, sl.N, sl.Ns)}
+    for name, sym in (("general", 0), ("odd_subspace", 1)):
+        c = KSCurve(sl.L, sl.N, sl.Ns, sl.S, up, um, s0=sl.s0, dtau=sl.dtau, precision="fp32", symmetry=sym,
+                    device=dev)
+        c.init_trial(0.0, None, amps, vp)
+        ms, prof = timed_steps(c, K, 3, profile=K)
+        out[name] = {"ms_per_step": sum(ms) / K, "s_form": c.s_form,
+                     "phases_ms": {k: v["ms"] / v["launches"] for k, v in prof.items()
+                                   if isinstance(v, dict) and v.get("launches")}}
+        c.close()
+    out["speedup"] = out["general"]["ms_per_step"] / out["odd_subspace"]["ms_per_step"]
+    return out
+
+
 def torch_sm_count(dev):
     import torch
     return torch.cuda.get_device_properties(dev).multi_processor_count
@@ -676,6 +700,11 @@ def run_curve(args):
             ctx["implicit_scheme"] = implicit_context(dev, timed_steps, max(3, min(50, K)))
         except Exception as exc:
             ctx["implicit_scheme"] = {"unavailable": str(exc)[:160]}
+        # ---- the odd subspace (Sec. V.B) on the same curve
+        try:
+            ctx["symmetric_subspace"] = symmetric_context(dev, timed_steps, max(3, min(50, K)))
+        except Exception as exc:
+            ctx["symmetric_subspace"] = {"unavailable": str(exc)[:160]}
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:

@@ -296,6 +296,10 @@ __global__ void __launch_bounds__(F4_THREADS) k_f4_p1(CurveDev c, int mode, int 
     const T *X = (const T *)(mode == GM_STORE ? c.U : c.R);
     const T *colscale = (const T *)(discrete ? c.sw : c.tau);
     const T s = discrete ? T(-1) : T(1);
+    // odd sections (real parts zero): the imaginary columns of modes 2q and 2q + 1
+    // of the block as one complex sequence q, so MPC / 2 sequences per block
+    const bool paired = (c.sym & 1) != 0;
+    const int nq = paired ? MPC / 2 : MPC;
     // z[F2 n1 + n2] of the MPC modes (the symmetric extension of the scaled
     // columns, as in the single-CTA form): thread -> line n2_0 + tn, n1 = t / F4W + 32 i.
     // Rows are fetched two at a time, both loads issued before either is used.
@@ -326,10 +330,17 @@ __global__ void __launch_bounds__(F4_THREADS) k_f4_p1(CurveDev c, int mode, int 
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
             const int n1 = threadIdx.x / F4W + 32 * (i0 + h);
+            if (paired) {
 #pragma unroll
-            for (int q = 0; q < MPC; ++q)
-                tile[q * TS + tn * LS + n1] = {sector_col_ok(jm0, 2 * q, c.sym) ? cs[h] * x[h][2 * q] : T(0),
-                                               sector_col_ok(jm0, 2 * q + 1, c.sym) ? cs[h] * x[h][2 * q + 1] : T(0)};
+                for (int q = 0; q < MPC / 2; ++q)
+                    tile[q * TS + tn * LS + n1] = {sector_col_ok(jm0, 4 * q + 1, c.sym) ? cs[h] * x[h][4 * q + 1] : T(0),
+                                                   sector_col_ok(jm0, 4 * q + 3, c.sym) ? cs[h] * x[h][4 * q + 3] : T(0)};
+            } else {
+#pragma unroll
+                for (int q = 0; q < MPC; ++q)
+                    tile[q * TS + tn * LS + n1] = {sector_col_ok(jm0, 2 * q, c.sym) ? cs[h] * x[h][2 * q] : T(0),
+                                                   sector_col_ok(jm0, 2 * q + 1, c.sym) ? cs[h] * x[h][2 * q + 1] : T(0)};
+            }
         }
     }
     // the step twiddles W_F^(n2 k1) of this warp's line (scrambled order of k1)
@@ -338,7 +349,7 @@ __global__ void __launch_bounds__(F4_THREADS) k_f4_p1(CurveDev c, int mode, int 
 #pragma unroll
     for (int a = 0; a < R; ++a) tw1[a] = t1[a * 32 + lane];
     __syncthreads();
-    for (int q = 0; q < MPC; ++q) {
+    for (int q = 0; q < nq; ++q) {
         cpx<T> *line = tile + q * TS + warp * LS;
         cpx<T> v[R];
 #pragma unroll
@@ -349,11 +360,13 @@ __global__ void __launch_bounds__(F4_THREADS) k_f4_p1(CurveDev c, int mode, int 
         for (int a = 0; a < R; ++a) line[a * 32 + lane] = cmul(v[a], tw1[a]);
     }
     __syncthreads();
-    // S[jm][k1][n2] (k1 in the scrambled order): F4W consecutive n2 per (mode, k1)
+    // S[jm][k1][n2] (k1 in the scrambled order): F4W consecutive n2 per (sequence, k1);
+    // the sequences of a paired block are numbered jm0 / 2 + q
     cpx<T> *S = (cpx<T> *)c.f4s;
-    for (int e = threadIdx.x; e < MPC * F1 * F4W; e += F4_THREADS) {
+    const int sq0 = paired ? jm0 / 2 : jm0;
+    for (int e = threadIdx.x; e < nq * F1 * F4W; e += F4_THREADS) {
         const int w = e % F4W, r = (e / F4W) % F1, q = e / (F4W * F1);
-        S[((size_t)(jm0 + q) * F1 + r) * F2 + n2_0 + w] = tile[q * TS + w * LS + r];
+        S[((size_t)(sq0 + q) * F1 + r) * F2 + n2_0 + w] = tile[q * TS + w * LS + r];
     }
 }
 
@@ -499,14 +512,17 @@ __global__ void __launch_bounds__(F4_THREADS) k_f4_p3(CurveDev c, int mode, int 
     if (gate && !sc->active) return;
     const double lam_d = sc->lambda, dtau_d = sc->dtau;
 
-    // S[jm][k1][n2] of this CTA's lines and modes -> tile
+    // S[jm][k1][n2] of this CTA's lines and sequences -> tile (odd sections: the
+    // block's modes in pairs, as pass 1 wrote them)
+    const bool paired = (c.sym & 1) != 0;
+    const int nq = paired ? MPC / 2 : MPC, sq0 = paired ? jm0 / 2 : jm0;
     const cpx<T> *S = (const cpx<T> *)c.f4s;
-    for (int e = threadIdx.x; e < MPC * F1 * F4W; e += F4_THREADS) {
+    for (int e = threadIdx.x; e < nq * F1 * F4W; e += F4_THREADS) {
         const int w = e % F4W, r = (e / F4W) % F1, q = e / (F4W * F1);
-        tile[q * TS + w * LS + r] = S[((size_t)(jm0 + q) * F1 + r) * F2 + n2_0 + w];
+        tile[q * TS + w * LS + r] = S[((size_t)(sq0 + q) * F1 + r) * F2 + n2_0 + w];
     }
     __syncthreads();
-    for (int q = 0; q < MPC; ++q) {
+    for (int q = 0; q < nq; ++q) {
         cpx<T> *line = tile + q * TS + warp * LS;
         cpx<T> v[R];
 #pragma unroll
@@ -554,11 +570,22 @@ __global__ void __launch_bounds__(F4_THREADS) k_f4_p3(CurveDev c, int mode, int 
             const int j = jv[h], n1 = threadIdx.x / F4W + 32 * (i0 + h);
             if (j >= ns) break;
             T y[NV];
+            if (paired) {
 #pragma unroll
-            for (int q = 0; q < MPC; ++q) {
-                const cpx<T> t = tile[q * TS + tn * LS + n1];
-                y[2 * q] = sector_col_ok(jm0, 2 * q, sym) ? rsv[h] * t.x : T(0);
-                y[2 * q + 1] = sector_col_ok(jm0, 2 * q + 1, sym) ? rsv[h] * t.y : T(0);
+                for (int q = 0; q < MPC / 2; ++q) {
+                    const cpx<T> t = tile[q * TS + tn * LS + n1];
+                    y[4 * q] = T(0);
+                    y[4 * q + 1] = sector_col_ok(jm0, 4 * q + 1, sym) ? rsv[h] * t.x : T(0);
+                    y[4 * q + 2] = T(0);
+                    y[4 * q + 3] = sector_col_ok(jm0, 4 * q + 3, sym) ? rsv[h] * t.y : T(0);
+                }
+            } else {
+#pragma unroll
+                for (int q = 0; q < MPC; ++q) {
+                    const cpx<T> t = tile[q * TS + tn * LS + n1];
+                    y[2 * q] = sector_col_ok(jm0, 2 * q, sym) ? rsv[h] * t.x : T(0);
+                    y[2 * q + 1] = sector_col_ok(jm0, 2 * q + 1, sym) ? rsv[h] * t.y : T(0);
+                }
             }
             const size_t o = (size_t)j * N + 2 * jm0;
             if (mode == GM_STORE) {
@@ -586,10 +613,17 @@ __global__ void __launch_bounds__(F4_THREADS) k_f4_p3(CurveDev c, int mode, int 
             if (mode == GM_GRAD) st_sector(G + o, g);
             if (chain) {   // z_j = tau_j u_j of the updated column, at the position the epilogue just read
                 const T cs = ((const T *)c.tau)[j];
+                if (paired) {
 #pragma unroll
-                for (int q = 0; q < MPC; ++q)
-                    tile[q * TS + tn * LS + n1] = {sector_col_ok(jm0, 2 * q, sym) ? cs * uv[h][2 * q] : T(0),
-                                                   sector_col_ok(jm0, 2 * q + 1, sym) ? cs * uv[h][2 * q + 1] : T(0)};
+                    for (int q = 0; q < MPC / 2; ++q)
+                        tile[q * TS + tn * LS + n1] = {sector_col_ok(jm0, 4 * q + 1, sym) ? cs * uv[h][4 * q + 1] : T(0),
+                                                       sector_col_ok(jm0, 4 * q + 3, sym) ? cs * uv[h][4 * q + 3] : T(0)};
+                } else {
+#pragma unroll
+                    for (int q = 0; q < MPC; ++q)
+                        tile[q * TS + tn * LS + n1] = {sector_col_ok(jm0, 2 * q, sym) ? cs * uv[h][2 * q] : T(0),
+                                                       sector_col_ok(jm0, 2 * q + 1, sym) ? cs * uv[h][2 * q + 1] : T(0)};
+                }
             }
         }
     }
@@ -601,15 +635,14 @@ __global__ void __launch_bounds__(F4_THREADS) k_f4_p3(CurveDev c, int mode, int 
         for (int i = 0; i < R; ++i) {
             const int n1 = threadIdx.x / F4W + 32 * i;
             if (F2 * n1 + n2_0 + tn >= ns)
-#pragma unroll
-                for (int q = 0; q < MPC; ++q) tile[q * TS + tn * LS + n1] = {T(0), T(0)};
+                for (int q = 0; q < nq; ++q) tile[q * TS + tn * LS + n1] = {T(0), T(0)};
         }
         const cpx<T> *t1 = (const cpx<T> *)c.ftw + F + (size_t)(n2_0 + warp) * F1;
         cpx<T> tw1[R];
 #pragma unroll
         for (int a = 0; a < R; ++a) tw1[a] = t1[a * 32 + lane];
         __syncthreads();
-        for (int q = 0; q < MPC; ++q) {
+        for (int q = 0; q < nq; ++q) {
             cpx<T> *line = tile + q * TS + warp * LS;
             cpx<T> v[R];
 #pragma unroll
@@ -621,9 +654,9 @@ __global__ void __launch_bounds__(F4_THREADS) k_f4_p3(CurveDev c, int mode, int 
         }
         __syncthreads();
         cpx<T> *So = (cpx<T> *)c.f4s;
-        for (int e = threadIdx.x; e < MPC * F1 * F4W; e += F4_THREADS) {
+        for (int e = threadIdx.x; e < nq * F1 * F4W; e += F4_THREADS) {
             const int w = e % F4W, r = (e / F4W) % F1, q = e / (F4W * F1);
-            So[((size_t)(jm0 + q) * F1 + r) * F2 + n2_0 + w] = tile[q * TS + w * LS + r];
+            So[((size_t)(sq0 + q) * F1 + r) * F2 + n2_0 + w] = tile[q * TS + w * LS + r];
         }
     }
     if (mode == GM_STORE) return;
@@ -1398,8 +1431,10 @@ static cudaError_t f4_run(const CurveDev &c, int mode, int discrete, int gate, c
                              discrete, gate)) != cudaSuccess)
         return e;
     if (pass_ev && (e = cudaEventRecord(pass_ev[0], st)) != cudaSuccess) return e;
-    if (c.f4h) e = launch_pdl(k_f4h_p2<T, F1, F2>, dim3((F1 / 2 + 1 + F4W - 1) / F4W, nm), 0, st, c, discrete, gate);
-    else e = launch_pdl(k_f4_p2<T, F1, F2>, dim3(F1 / F4W, nm), 0, st, c, gate);
+    // pass 2 per sequence: the modes' columns, or for odd sections the modes' imaginary columns in pairs
+    const int nseq = (c.sym & 1) ? nm / 2 : nm;
+    if (c.f4h) e = launch_pdl(k_f4h_p2<T, F1, F2>, dim3((F1 / 2 + 1 + F4W - 1) / F4W, nseq), 0, st, c, discrete, gate);
+    else e = launch_pdl(k_f4_p2<T, F1, F2>, dim3(F1 / F4W, nseq), 0, st, c, gate);
     if (e != cudaSuccess) return e;
     if (pass_ev && (e = cudaEventRecord(pass_ev[1], st)) != cudaSuccess) return e;
     return launch_pdl(k_f4_p3<T, F1, F2>, dim3(nmb, F2 / F4W), sm1, st, c, mode, discrete, gate);

@@ -83,9 +83,8 @@ def test_gradient_matches_finite_differences(setup):
 
 
 # J within 1e-5 in FP32; the FP32 gradient, compared in the preconditioned norm,
-# within 5e-5 (about 400 FP32 ulps: its floor depends on the contraction form,
-# 3e-6 to 2e-5 measured at this size for the SIMT, FFT and tensor-core forms)
-@pytest.mark.parametrize("precision,tol,gtol", [("fp64", 1e-10, 1e-10), ("fp32", 1e-5, 5e-5)])
+# within 1.5e-5: twice the 7.4e-6 measured for the form this size runs in
+@pytest.mark.parametrize("precision,tol,gtol", [("fp64", 1e-10, 1e-10), ("fp32", 1e-5, 1.5e-5)])
 def test_gradient_matches_the_oracle(setup, precision, tol, gtol):
     spec, up, um, U, X = setup
     dt = torch.float64 if precision == "fp64" else torch.float32
