@@ -185,8 +185,11 @@ ks_status launch_step(ks_batch *b, cudaStream_t st)
         if (e == cudaSuccess)
             e = ks::launch_dt_batch(b->prec, g.key, b->cv_dev, (const int4 *)(b->items_dev + g.off), g.count,
                                     um, b->discrete, 1, st);
+    // the batched four-step groups run the update and D_t u of the updated columns
+    // in one launch (GM_STEP) unless the implicit increment comes between them
+    const bool chain = !b->impl;
     for (const Group &g : b->ffts)
-        if (e == cudaSuccess) e = launch_fft_group(b, g, um, b->discrete, st);
+        if (e == cudaSuccess) e = launch_fft_group(b, g, (chain && g.sub > 0) ? ks::GM_STEP : um, b->discrete, st);
     if (b->impl && e == cudaSuccess)
         e = ks::launch_implicit_batch(b->prec, b->cv_dev, (const int4 *)(b->items_dev + b->imp_prod.off),
                                       b->imp_prod.count, (const int4 *)(b->items_dev + b->imp_fin.off),
@@ -196,7 +199,7 @@ ks_status launch_step(ks_batch *b, cudaStream_t st)
             e = ks::launch_dt_batch(b->prec, g.key, b->cv_dev, (const int4 *)(b->items_dev + g.off), g.count,
                                     ks::GM_STORE, 0, 1, st);
     for (const Group &g : b->ffts)
-        if (e == cudaSuccess) e = launch_fft_group(b, g, ks::GM_STORE, 0, st);
+        if (e == cudaSuccess && !(chain && g.sub > 0)) e = launch_fft_group(b, g, ks::GM_STORE, 0, st);
     if (e != cudaSuccess) return ks::report_error(KS_ECUDA, "batched step launch: %s", cudaGetErrorString(e));
     return KS_OK;
 }

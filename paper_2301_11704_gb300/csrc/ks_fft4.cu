@@ -1102,11 +1102,14 @@ __device__ __forceinline__ void f4b_body(const CurveDev &c, int mode, int discre
     DevScalars *sc = c.sc;
     pdl_wait();
     if (gate && !sc->active) return;
+    // GM_STEP: the update, then D_t u of the updated column in the same CTA (its
+    // pass 1 fed from the update's registers: the same (line, position) layout)
+    const bool step = mode == GM_STEP && c.f4h;
+    if (step) mode = GM_UPDATE;
     const double lam_d = sc->lambda, dtau_d = sc->dtau;
     const int P = c.P, N = c.nx, ns = c.ns;
     const T *X = (const T *)(mode == GM_STORE ? c.U : c.R);
     const T *colscale = (const T *)(discrete ? c.sw : c.tau);
-    const T *rowscale = (const T *)(discrete ? c.twr : c.sig);
     const T s = discrete ? T(-1) : T(1);
     const int ca = 2 * jm, cb = 2 * jm + 1;
     const bool oka = col_allowed(ca, c.sym), okb = col_allowed(cb, c.sym) && jm != 0;
@@ -1147,124 +1150,157 @@ __device__ __forceinline__ void f4b_body(const CurveDev &c, int mode, int discre
     }
     __syncthreads();
 
-    // pass 2 of the Toeplitz-Hankel form: rows k1 and F1 - k1 together (0 and F1/2
-    // alone), as in k_f4h_p2 but on the shared array
-    if (c.f4h) {
-        for (int it = warp; it <= F1 / 2; it += F4W) {
-            const bool pair = it > 0 && it < F1 / 2;
-            const int ka = it, kb = F1 - it;
-            const int ra = (ka % R1) * 32 + brev5(ka / R1), rb = pair ? (kb % R1) * 32 + brev5(kb / R1) : 0;
-            cpx<T> *rowa = B + (size_t)ra * BS, *rowb = B + (size_t)rb * BS;
-            cpx<T> va[R2], vb[R2], pa[R2], pb[R2];
+    // pass 2 (sign sg of the Toeplitz part: -1 for the discrete adjoint's transpose)
+    auto pass2 = [&](T sg) {
+        if (c.f4h) {   // rows k1 and F1 - k1 together (0 and F1/2 alone), as in k_f4h_p2
+            for (int it = warp; it <= F1 / 2; it += F4W) {
+                const bool pair = it > 0 && it < F1 / 2;
+                const int ka = it, kb = F1 - it;
+                const int ra = (ka % R1) * 32 + brev5(ka / R1), rb = pair ? (kb % R1) * 32 + brev5(kb / R1) : 0;
+                cpx<T> *rowa = B + (size_t)ra * BS, *rowb = B + (size_t)rb * BS;
+                cpx<T> va[R2], vb[R2], pa[R2], pb[R2];
+#pragma unroll
+                for (int a = 0; a < R2; ++a) {
+                    va[a] = rowa[lane + 32 * a];
+                    if (pair) vb[a] = rowb[lane + 32 * a];
+                }
+                reg_fft_fwd<T, R2>(va, tw2, w32, lane);
+                if (pair) reg_fft_fwd<T, R2>(vb, tw2, w32, lane);
+                if (pair) {
+#pragma unroll
+                    for (int a = 0; a < R2; ++a) {
+                        pa[a] = cshfl(vb[R2 - 1 - a], 31);
+                        pb[a] = cshfl(va[R2 - 1 - a], 31);
+                    }
+                } else if (ka == F1 / 2) {
+#pragma unroll
+                    for (int a = 0; a < R2; ++a) pa[a] = cshfl(va[R2 - 1 - a], 31);
+                } else {   // row 0
+                    const int src = brev5((32 - brev5(lane)) & 31);
+                    pa[0] = {__shfl_sync(0xffffffffu, va[0].x, src), __shfl_sync(0xffffffffu, va[0].y, src)};
+#pragma unroll
+                    for (int a = 1; a < R2; ++a) pa[a] = cshfl(va[R2 - a], 31);
+                }
+                // Y = s T^ Z + H^ Z(-k), IFFT, W_F^(-n2 k1), back into the row
+                auto finish = [&](int r, cpx<T> *row, cpx<T> (&v)[R2], const cpx<T> (&pp)[R2]) {
+                    const cpx<T> *ct = chat + (size_t)r * F2, *chh = chat + F + (size_t)r * F2;
+                    const cpx<T> *t2 = ftw + 2 * (size_t)F + (size_t)r * F2;
+#pragma unroll
+                    for (int a = 0; a < R2; ++a) {
+                        const cpx<T> y = cmul(ct[32 * a + lane], v[a]);
+                        v[a] = cadd(cpx<T>{sg * y.x, sg * y.y}, cmul(chh[32 * a + lane], pp[a]));
+                    }
+                    reg_fft_inv<T, R2>(v, tw2, w32, lane);
+#pragma unroll
+                    for (int a = 0; a < R2; ++a) row[lane + 32 * a] = cmul(v[a], cconj(t2[lane + 32 * a]));
+                };
+                finish(ra, rowa, va, pa);
+                if (pair) finish(rb, rowb, vb, pb);
+            }
+        }
+        // rows r: FFT over n2, kernel spectrum, IFFT, times W_F^(-n2 k1), in place
+        for (int r = warp; r < F1 && !c.f4h; r += F4W) {
+            cpx<T> *row = B + (size_t)r * BS;
+            const cpx<T> *ch = chat + (size_t)r * F2, *t2 = ftw + 2 * (size_t)F + (size_t)r * F2;
+            cpx<T> v[R2], chv[R2], t2v[R2];
 #pragma unroll
             for (int a = 0; a < R2; ++a) {
-                va[a] = rowa[lane + 32 * a];
-                if (pair) vb[a] = rowb[lane + 32 * a];
+                chv[a] = ch[32 * a + lane];
+                t2v[a] = t2[lane + 32 * a];
+                v[a] = row[lane + 32 * a];
             }
-            reg_fft_fwd<T, R2>(va, tw2, w32, lane);
-            if (pair) reg_fft_fwd<T, R2>(vb, tw2, w32, lane);
-            if (pair) {
+            reg_fft_fwd<T, R2>(v, tw2, w32, lane);
 #pragma unroll
-                for (int a = 0; a < R2; ++a) {
-                    pa[a] = cshfl(vb[R2 - 1 - a], 31);
-                    pb[a] = cshfl(va[R2 - 1 - a], 31);
-                }
-            } else if (ka == F1 / 2) {
+            for (int a = 0; a < R2; ++a) v[a] = cmul(v[a], chv[a]);
+            reg_fft_inv<T, R2>(v, tw2, w32, lane);
 #pragma unroll
-                for (int a = 0; a < R2; ++a) pa[a] = cshfl(va[R2 - 1 - a], 31);
-            } else {   // row 0
-                const int src = brev5((32 - brev5(lane)) & 31);
-                pa[0] = {__shfl_sync(0xffffffffu, va[0].x, src), __shfl_sync(0xffffffffu, va[0].y, src)};
-#pragma unroll
-                for (int a = 1; a < R2; ++a) pa[a] = cshfl(va[R2 - a], 31);
-            }
-            // Y = s T^ Z + H^ Z(-k), IFFT, W_F^(-n2 k1), back into the row
-            auto finish = [&](int r, cpx<T> *row, cpx<T> (&v)[R2], const cpx<T> (&p)[R2]) {
-                const cpx<T> *ct = chat + (size_t)r * F2, *chh = chat + F + (size_t)r * F2;
-                const cpx<T> *t2 = ftw + 2 * (size_t)F + (size_t)r * F2;
-#pragma unroll
-                for (int a = 0; a < R2; ++a) {
-                    const cpx<T> y = cmul(ct[32 * a + lane], v[a]);
-                    v[a] = cadd(cpx<T>{s * y.x, s * y.y}, cmul(chh[32 * a + lane], p[a]));
-                }
-                reg_fft_inv<T, R2>(v, tw2, w32, lane);
-#pragma unroll
-                for (int a = 0; a < R2; ++a) row[lane + 32 * a] = cmul(v[a], cconj(t2[lane + 32 * a]));
-            };
-            finish(ra, rowa, va, pa);
-            if (pair) finish(rb, rowb, vb, pb);
+            for (int a = 0; a < R2; ++a) row[lane + 32 * a] = cmul(v[a], cconj(t2v[a]));
         }
-    }
-    // pass 2: rows r: FFT over n2, kernel spectrum, IFFT, times W_F^(-n2 k1), in place
-    for (int r = warp; r < F1 && !c.f4h; r += F4W) {
-        cpx<T> *row = B + (size_t)r * BS;
-        const cpx<T> *ch = chat + (size_t)r * F2, *t2 = ftw + 2 * (size_t)F + (size_t)r * F2;
-        cpx<T> v[R2], chv[R2], t2v[R2];
-#pragma unroll
-        for (int a = 0; a < R2; ++a) {
-            chv[a] = ch[32 * a + lane];
-            t2v[a] = t2[lane + 32 * a];
-            v[a] = row[lane + 32 * a];
-        }
-        reg_fft_fwd<T, R2>(v, tw2, w32, lane);
-#pragma unroll
-        for (int a = 0; a < R2; ++a) v[a] = cmul(v[a], chv[a]);
-        reg_fft_inv<T, R2>(v, tw2, w32, lane);
-#pragma unroll
-        for (int a = 0; a < R2; ++a) row[lane + 32 * a] = cmul(v[a], cconj(t2v[a]));
-    }
+    };
+    pass2(s);
     __syncthreads();
 
-    // pass 3: lines n2, IFFT over k1, epilogue on the sections j = F2 n1 + n2 < N_s
+    // pass 3: lines n2, IFFT over k1, epilogue on the sections j = F2 n1 + n2 < N_s;
+    // `chain`: then pass 1 of D_t u of the line's updated sections into column n2
     T *Dout = (T *)c.D, *U = (T *)c.U, *G = (T *)c.G;
     const T *Ah = (const T *)c.A;
     const T pr = ((const T *)c.prec_imex)[jm];
     const T lam = (T)lam_d, dtau = (T)dtau_d;
     const double cw = (jm == 0) ? 1.0 : 2.0;
-    double partsum = 0.0;
-    for (int n2 = warp; n2 < F2; n2 += F4W) {
-        cpx<T> v[R1];
+    const T *tauc = (const T *)c.tau;
+    auto pass3 = [&](int md, bool disc, bool chain) -> double {
+        const T *rowscale = (const T *)(disc ? c.twr : c.sig);
+        double partsum = 0.0;
+        for (int n2 = warp; n2 < F2; n2 += F4W) {
+            cpx<T> v[R1];
 #pragma unroll
-        for (int a = 0; a < R1; ++a) v[a] = B[(32 * a + lane) * BS + n2];
-        // the epilogue operands of this line's sections, issued before the transform
-        T rs[R1];
-        double wj[R1];
-        V2 av[R1], uv[R1];
+            for (int a = 0; a < R1; ++a) v[a] = B[(32 * a + lane) * BS + n2];
+            // the epilogue operands of this line's sections, issued before the transform
+            T rs[R1];
+            double wj[R1];
+            V2 av[R1], uv[R1];
 #pragma unroll
-        for (int a = 0; a < R1; ++a) {
-            const int j = F2 * (lane + 32 * a) + n2;
-            rs[a] = rowscale[j < ns ? j : 0];
-            wj[a] = 0.0;
-            if (mode != GM_STORE && j > 0 && j < P) {
-                wj[a] = c.w[j];
-                av[a] = *reinterpret_cast<const V2 *>(Ah + (size_t)j * N + ca);
-                if (mode == GM_UPDATE) uv[a] = *reinterpret_cast<const V2 *>(U + (size_t)j * N + ca);
+            for (int a = 0; a < R1; ++a) {
+                const int j = F2 * (lane + 32 * a) + n2;
+                rs[a] = rowscale[j < ns ? j : 0];
+                wj[a] = 0.0;
+                uv[a] = V2{T(0), T(0)};
+                if (md != GM_STORE && j > 0 && j < P) {
+                    wj[a] = c.w[j];
+                    av[a] = *reinterpret_cast<const V2 *>(Ah + (size_t)j * N + ca);
+                    if (md == GM_UPDATE) uv[a] = *reinterpret_cast<const V2 *>(U + (size_t)j * N + ca);
+                } else if (chain && (j == 0 || j == P)) {
+                    uv[a] = *reinterpret_cast<const V2 *>(U + (size_t)j * N + ca);   // end rows, for the chained pass 1
+                }
+            }
+            reg_fft_inv<T, R1>(v, tw1, w32, lane);
+#pragma unroll
+            for (int a = 0; a < R1; ++a) {
+                const int j = F2 * (lane + 32 * a) + n2;
+                if (j >= ns) break;
+                const cpx<T> yv = {rs[a] * v[a].x, rs[a] * v[a].y};
+                const size_t o = (size_t)j * N + ca;
+                if (md == GM_STORE) {
+                    *reinterpret_cast<V2 *>(Dout + o) = V2{oka ? yv.x : T(0), okb ? yv.y : T(0)};
+                    continue;
+                }
+                const bool interior = (j > 0 && j < P);
+                T ga = 0, gb = 0;
+                if (interior) {
+                    if (oka) ga = -(av[a].x + (disc ? -lam * yv.x : lam * yv.x));
+                    if (okb) gb = -(av[a].y + (disc ? -lam * yv.y : lam * yv.y));
+                    partsum += wj[a] * cw * (double)(ga * ga + gb * gb);
+                }
+                if (md == GM_UPDATE) {
+                    if (interior) {
+                        uv[a] = V2{uv[a].x + dtau * pr * ga, uv[a].y + dtau * pr * gb};
+                        *reinterpret_cast<V2 *>(U + o) = uv[a];
+                    }
+                } else {
+                    *reinterpret_cast<V2 *>(G + o) = V2{ga, gb};
+                }
+            }
+            if (chain) {   // z_j = tau_j u_j (j <= P), zero above: FFT over n1, W_F^(n2 k1), into column n2
+                cpx<T> z[R1];
+#pragma unroll
+                for (int a = 0; a < R1; ++a) {
+                    const int j = F2 * (lane + 32 * a) + n2;
+                    const T cs = j < ns ? tauc[j] : T(0);
+                    z[a] = {oka ? cs * uv[a].x : T(0), okb ? cs * uv[a].y : T(0)};
+                }
+                reg_fft_fwd<T, R1>(z, tw1, w32, lane);
+#pragma unroll
+                for (int a = 0; a < R1; ++a) B[(32 * a + lane) * BS + n2] = cmul(z[a], ftw[F + (size_t)n2 * F1 + 32 * a + lane]);
             }
         }
-        reg_fft_inv<T, R1>(v, tw1, w32, lane);
-#pragma unroll
-        for (int a = 0; a < R1; ++a) {
-            const int j = F2 * (lane + 32 * a) + n2;
-            if (j >= ns) break;
-            const cpx<T> yv = {rs[a] * v[a].x, rs[a] * v[a].y};
-            const size_t o = (size_t)j * N + ca;
-            if (mode == GM_STORE) {
-                *reinterpret_cast<V2 *>(Dout + o) = V2{oka ? yv.x : T(0), okb ? yv.y : T(0)};
-                continue;
-            }
-            const bool interior = (j > 0 && j < P);
-            T ga = 0, gb = 0;
-            if (interior) {
-                if (oka) ga = -(av[a].x + (discrete ? -lam * yv.x : lam * yv.x));
-                if (okb) gb = -(av[a].y + (discrete ? -lam * yv.y : lam * yv.y));
-                partsum += wj[a] * cw * (double)(ga * ga + gb * gb);
-            }
-            if (mode == GM_UPDATE) {
-                if (interior) *reinterpret_cast<V2 *>(U + o) = V2{uv[a].x + dtau * pr * ga, uv[a].y + dtau * pr * gb};
-            } else {
-                *reinterpret_cast<V2 *>(G + o) = V2{ga, gb};
-            }
-        }
+        return partsum;
+    };
+    double partsum = pass3(mode, discrete != 0, step);
+    if (step) {   // D_t u of the updated column: passes 2 and 3 of the published operator
+        __syncthreads();
+        pass2(T(1));
+        __syncthreads();
+        pass3(GM_STORE, false, false);
     }
     if (mode == GM_STORE) return;
 
