@@ -1328,8 +1328,10 @@ __global__ void __launch_bounds__(F4_THREADS) k_f4b(CurveDev c, int mode, int di
     f4b_body<T, F1, F2>(c, mode, discrete, gate, blockIdx.x, gridDim.x);
 }
 
+// Four CTAs per SM: the register cap this sets (64) measured 9% faster on the
+// 256-curve batch step than the compiler's own choice (up to 105 registers).
 template <typename T, int F1, int F2>
-__global__ void __launch_bounds__(F4_THREADS) k_f4b_batch(const CurveDev *cv, const int2 *items, int mode,
+__global__ void __launch_bounds__(F4_THREADS, 4) k_f4b_batch(const CurveDev *cv, const int2 *items, int mode,
                                                           int discrete, int gate)
 {
     const int2 it = items[blockIdx.x];

@@ -313,6 +313,8 @@ static ks_status setup_implicit_t(const CurveDev &c, cudaStream_t st)
         if (cudaGetLastError() != cudaSuccess) return report_error(KS_ECUDA, "implicit set-up: block products");
         r = eig_block<T>(sh, st, no, B, c.imu + ne, V + (size_t)ne * ne, Vi + (size_t)ne * ne);
     }
+    if (r == KS_OK && c.ivtc && launch_setup_implicit_tc(c, st) != cudaSuccess)
+        r = report_error(KS_ECUDA, "implicit set-up: tensor-core operands");
     if (r == KS_OK && cudaStreamSynchronize(st) != cudaSuccess) r = report_error(KS_ECUDA, "implicit set-up");
     return r;
 }
@@ -651,9 +653,27 @@ void implicit_batch_items(const CurveDev &c, int curve, std::vector<int4> &prod,
     for (int bx = 0; bx < nbx; ++bx) fin.push_back(make_int4(curve, bx, nbx, 0));
 }
 
+// The tensor-core products (FP32 storage, N >= 32): K split so that the grid of
+// 128-row tiles of both parities holds about two CTAs per SM.
+static cudaError_t implicit_tc_run(const CurveDev &c, int gate, cudaStream_t st)
+{
+    const int tiles = ((c.ine + 127) / 128) * 2, nk = (c.ino + 31) / 32;
+    const int sp = std::max(1, std::min(std::min((2 * 152 + tiles - 1) / tiles, c.isplits), std::max(1, nk / 2)));
+    cudaError_t e = launch_implicit_tc(c, sp, gate, st, 0);
+    const long total = (long)c.ine * c.nx;
+    if (e == cudaSuccess && sp > 1)
+        e = imp_launch(k_imp_sum<float>, dim3((int)std::min<long>(4 * 152, (2 * total + IM_THREADS - 1) / IM_THREADS)), st,
+                       c, sp, gate);
+    if (e == cudaSuccess) e = launch_implicit_tc(c, sp, gate, st, 1);
+    if (e != cudaSuccess) return e;
+    const int gf = (int)std::min<long>(4 * 152, (total + IM_THREADS - 1) / IM_THREADS);
+    return imp_launch(k_imp_finish<float>, dim3(gf), st, c, sp, gate);
+}
+
 template <typename T>
 static cudaError_t implicit_t(const CurveDev &c, int gate, cudaStream_t st)
 {
+    if (sizeof(T) == 4 && c.ivtc) return implicit_tc_run(c, gate, st);
     const int sp = imp_splits(c);
     const int gx = (c.nx + IM_BN - 1) / IM_BN, gy = (c.ine + IM_BM - 1) / IM_BM;
     cudaError_t e = imp_launch(k_imp_fwd<T>, dim3(gx, gy, 2 * sp), st, c, sp, gate);

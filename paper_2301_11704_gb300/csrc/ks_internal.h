@@ -219,6 +219,8 @@ struct Layout {
     int impl;                          // full-linear-implicit stepping: its eigenbases (0: IMEX)
     size_t off_iv, off_ivi, off_imu;   // V (even block, then odd), V^-1 likewise, eigenvalues (FP64)
     size_t off_isc;                    // the split partials of its two products
+    size_t off_ivtc;                   // V^-1 and V as tensor-core operands
+    int ivtc;                          // 1: that region exists (single curves, FP32 storage, N >= 32)
     int isplits;                       // K chunks they hold
 };
 
@@ -249,6 +251,7 @@ struct CurveDev {
     void *iv, *ivi;        // V_e [ine][ine] then V_o [ino][ino], row-major (storage type); V^-1 alike
     double *imu;           // eigenvalues: ine of the even part, then ino of the odd part
     void *isc;             // split partials of the increment's products: 2 isplits [M][N]
+    void *ivtc;            // V^-1 and V as split-BF16 tensor-core operands (FP32 storage, N >= 32; else null)
     int isplits;           // K chunks those partials hold (IMP_SPLIT_MAX; 1 for batched curves)
     int F;                 // FFT length of the s-contraction (0: dense form)
     void *chat, *ftw;      // FFT form: kernel spectrum / F and twiddles (complex, storage type);
@@ -369,6 +372,12 @@ size_t implicit_scratch_bytes(int ns, int nx, int prec, int splits);
 void implicit_batch_items(const CurveDev &c, int curve, std::vector<int4> &prod, std::vector<int4> &fin);
 cudaError_t launch_implicit_batch(int prec, const CurveDev *cv, const int4 *prod, int nprod, const int4 *fin, int nfin,
                                   cudaStream_t st);
+// ks_implicit_tc.cu: the two products on the tensor cores (single curves, FP32
+// storage, N >= 32): operand bytes, their set-up, and one product (which = 0:
+// forward, 1: back) writing the split partials.
+size_t implicit_tc_bytes(int ns);
+cudaError_t launch_setup_implicit_tc(const CurveDev &c, cudaStream_t st);
+cudaError_t launch_implicit_tc(const CurveDev &c, int splits, int gate, cudaStream_t st, int which);
 // One-time set-up: eigendecomposition of the interior D_t^2 (FP64, cuSOLVER,
 // opened at run time), stored in the curve's workspace.  Synchronous.
 ks_status setup_implicit(const CurveDev &c, cudaStream_t st);

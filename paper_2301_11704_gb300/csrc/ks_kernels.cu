@@ -157,6 +157,8 @@ Layout make_layout(int ns, int nx, int prec, int allow_split, int bn, int s_tran
     l.off_imu = off; off += impl ? al256((ne + no) * 8) : 0;
     l.isplits = allow_split ? IMP_SPLIT_MAX : 1;
     l.off_isc = off; off += impl ? al256(implicit_scratch_bytes(ns, nx, prec, l.isplits)) : 0;
+    l.ivtc = (impl && prec && allow_split && nx >= 32) ? 1 : 0;
+    l.off_ivtc = off; off += l.ivtc ? al256(implicit_tc_bytes(ns)) : 0;
     l.total = off;
     return l;
 }
@@ -217,6 +219,7 @@ CurveDev bind_layout(const ks_params *p, const Layout &l, void *base)
     d.imu = l.impl ? (double *)(b + l.off_imu) : nullptr;
     d.isc = l.impl ? (void *)(b + l.off_isc) : nullptr;
     d.isplits = l.isplits;
+    d.ivtc = l.ivtc ? (void *)(b + l.off_ivtc) : nullptr;
     d.cot = b + l.off_cot;
     d.sig = b + l.off_sig;
     d.tau = b + l.off_tau;

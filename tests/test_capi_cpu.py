@@ -149,15 +149,18 @@ def test_invalid_implicit_parameters_are_rejected(lib, bad):
 def test_implicit_workspace_holds_the_eigenbases(lib, prec, b, ns):
     """Full-linear-implicit stepping: V and V^-1 of the even (ceil(M/2) square) and
     odd (floor(M/2) square) parts of D~^2 in the storage type, their eigenvalues
-    in FP64, and the split partials of the two products (2 x 8 x M x N); same
-    s-form as the IMEX scheme."""
+    in FP64, the split partials of the two products (2 x 8 x M x N), and in FP32
+    storage V^-1 and V as split-BF16 tensor-core operands (two parts, padded to
+    128-row tiles and 32-wide K chunks); same s-form as the IMEX scheme."""
     nx = 64
     imex = lib.ks_curve_workspace_bytes(ctypes.byref(_params(precision=prec, nx=nx, ns=ns)))
     impl = lib.ks_curve_workspace_bytes(ctypes.byref(_params(precision=prec, nx=nx, ns=ns, scheme=1)))
     M = ns - 2
     ne, no = (M + 1) // 2, M // 2
     al = lambda x: (x + 255) // 256 * 256
-    assert impl - imex == 2 * al((ne * ne + no * no) * b) + al(M * 8) + al(2 * 8 * M * nx * b)
+    blk = lambda n: ((n + 127) // 128) * ((n + 31) // 32) * 2 * (128 * 32 * 2)   # tensor-core operand blocks
+    tc = al(2 * (blk(ne) + blk(no))) if b == 4 else 0
+    assert impl - imex == 2 * al((ne * ne + no * no) * b) + al(M * 8) + al(2 * 8 * M * nx * b) + tc
     assert lib.ks_curve_s_form(ctypes.byref(_params(precision=prec, nx=nx, ns=ns, scheme=1))) == \
         lib.ks_curve_s_form(ctypes.byref(_params(precision=prec, nx=nx, ns=ns)))
 

@@ -15,13 +15,14 @@ from paper_2301_11704_gb300.curve import KSCurve
 pytestmark = pytest.mark.gpu
 
 
-def _curve(N, Ns, precision, s_transform="auto"):
+def _curve(N, Ns, precision, s_transform="auto", scheme="imex"):
     L = 22.0 + N / 16.0
     spec = gen.CurveSpec(0, 0, L, N, Ns, 0.1 * (Ns - 1))
     up = np.zeros(N)
     amps = np.full(4, 0.1)
     vp = gen.perturbation_fields(N, L, 11, 4)
-    c = KSCurve(L, N, Ns, spec.S, up, np.zeros(N), dtau=1e-3, precision=precision, s_transform=s_transform)
+    c = KSCurve(L, N, Ns, spec.S, up, np.zeros(N), dtau=1e-3, precision=precision, s_transform=s_transform,
+                scheme=scheme)
     c.init_trial(0.0, None, amps, vp)
     return c, (amps, vp)
 
@@ -45,15 +46,16 @@ def test_nonfinite_state_stops_the_descent(precision):
     c.close()
 
 
-@pytest.mark.parametrize("precision,s_transform,N,Ns,call", [
-    ("bf16x3", "auto", 128, 257, "cost"),        # the split-BF16 row phase (tcgen05, bulk copies)
-    ("bf16x2", "auto", 256, 130, "cost"),
-    ("fp64", "fft", 32, 128, "descend"),         # the FFT form with one CTA per mode (bulk-copied twiddles)
-    ("fp32", "dense_tc", 64, 256, "descend"),    # the tensor-core s-contraction
+@pytest.mark.parametrize("precision,s_transform,N,Ns,call,scheme", [
+    ("bf16x3", "auto", 128, 257, "cost", "imex"),        # the split-BF16 row phase (tcgen05, bulk copies)
+    ("bf16x2", "auto", 256, 130, "cost", "imex"),
+    ("fp64", "fft", 32, 128, "descend", "imex"),         # the FFT form with one CTA per mode (bulk-copied twiddles)
+    ("fp32", "dense_tc", 64, 256, "descend", "imex"),    # the tensor-core s-contraction
+    ("fp32", "dense", 64, 300, "descend", "implicit"),   # the implicit increment's tensor-core products
 ])
-def test_expired_device_wait_reports_timeout(precision, s_transform, N, Ns, call):
-    c, (amps, vp) = _curve(N, Ns, precision, s_transform)
-    ref, _ = _curve(N, Ns, precision, s_transform)
+def test_expired_device_wait_reports_timeout(precision, s_transform, N, Ns, call, scheme):
+    c, (amps, vp) = _curve(N, Ns, precision, s_transform, scheme)
+    ref, _ = _curve(N, Ns, precision, s_transform, scheme)
     J2_ref = ref.cost()[0]
     out_ref = ref.descend(1)
     ref.close()
