@@ -408,6 +408,25 @@ def oracle_errors(spec, make_curve, precision):
             "sampled_sections": len(rows), "reference": os.path.relpath(path, ROOT)}
 
 
+# ---------------------------------------------------------------------------- across ranks
+def reduce_max_ms(total_ms, world, device):
+    """The slowest rank's timed milliseconds (max over the ranks; every rank gets
+    the same value).  One process per GPU; a single process returns its own."""
+    if world <= 1:
+        return float(total_ms)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(total_ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(world, points_per_step, steps, total_ms_max):
+    """Whole-job curve-point evaluations per second: every rank steps its own
+    replica of the workload (weak scaling), timed by the slowest rank."""
+    return world * points_per_step * steps / (total_ms_max / 1e3)
+
+
 # ---------------------------------------------------------------------------- implicit stepping
 def implicit_context(dev, timed_steps, K, dtau=0.5):
     """The L=44, N_x=128, N_s=4096 curve in FP32 stepped with every linear term of
@@ -548,12 +567,9 @@ def run_curve(args):
     step_ms, prof = timed_steps(curve, K, W, profile=max(3, K // 20))
     clk = clocks.stop()
     total_ms = sum(step_ms)
-    t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    total_ms_max = float(t.item())
+    total_ms_max = reduce_max_ms(total_ms, world, dev)
     M, N, b = spec.M, spec.N, BYTES[precision]
-    value = world * M * K / (total_ms_max / 1e3)
+    value = job_throughput(world, M, K, total_ms_max)
     ms_step = total_ms_max / K
 
     # ---- roofline: the dominant kernel, bytes and flops after the per-point counts
