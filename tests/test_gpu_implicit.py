@@ -125,3 +125,26 @@ def test_implicit_descent_is_stable_far_beyond_imex_limit():
     _, _, sco, _ = oracle.curve_descend(U, L, S, 200, dtau=dtau, mode=oracle.DISCRETE, scheme=oracle.IMPLICIT)
     assert abs(J[-1] - sco["J"]) < 1e-9 * sco["J"]
     c.close()
+
+
+def test_implicit_full_size_fp32_tensor_cores_match_fp64():
+    """The L = 44, N_x = 128, N_s = 4096 workload curve as the bench times it
+    (FP32 storage: the increment's products on the tensor cores, K split over
+    CTAs) against the FP64 implicit path on the CUDA cores (itself held to the
+    oracle at 1e-13 above), five steps at dtau = 0.5."""
+    from paper_2301_11704_gb300 import gen
+    sp = gen.workload(2)[0]
+    up, um = gen.end_points(sp)
+    amps, vp = gen.perturbation(sp)
+    out = {}
+    for prec in ("fp32", "fp64"):
+        c = KSCurve(sp.L, sp.N, sp.Ns, sp.S, up, um, dtau=0.5, precision=prec, scheme="implicit")
+        c.init_trial(0.0, None, amps, vp)
+        r = c.descend(5)
+        out[prec] = (c.get_state().double().cpu().numpy(), r["J"])
+        c.close()
+    (x32, j32), (x64, j64) = out["fp32"], out["fp64"]
+    e_u = float(np.linalg.norm(x32 - x64) / np.linalg.norm(x64))
+    e_j = abs(j32 - j64) / j64
+    print("IMPLICIT full size fp32 vs fp64: u %.2e J %.2e" % (e_u, e_j))
+    assert e_u < 1e-5 and e_j < 1e-5
