@@ -170,14 +170,44 @@ __global__ void __launch_bounds__(IT_THREADS, 1) k_imp_tc(CurveDev c, int splits
     const float *G = (const float *)c.G;
     const float *Y = (const float *)c.isc + (p ? (size_t)ne * Nn : 0);
     const float r2 = 0.70710678118654752440f;
-    // the B value (k, col): folded G (forward) or Y (back), zero past the block
-    auto bval = [&](int k, int col) -> float {
-        if (k >= np) return 0.f;
-        if (!FWD) return Y[(size_t)k * Nn + col];
-        if (p == 0)
-            return k < h ? r2 * (G[(size_t)(1 + k) * Nn + col] + G[(size_t)(M - k) * Nn + col]) : G[(size_t)(1 + h) * Nn + col];
-        return r2 * (G[(size_t)(1 + k) * Nn + col] - G[(size_t)(M - k) * Nn + col]);
+    // B chunk q: units (col, k-block of 8) of 8 values, UPT per thread.  `fetch`
+    // issues every load of a chunk at once (rows and predicates computed first,
+    // no branch between the loads), one chunk ahead of `produce`, which folds,
+    // splits and writes the operand stage.
+    constexpr int UNITS = N * (IT_KC / 8), UPT = (UNITS + IT_THREADS - 1) / IT_THREADS;
+    const float *Bsrc = FWD ? G : Y;
+    auto fetch = [&](int q, float (&xa)[UPT][8], float (&xb)[UPT][8]) {
+#pragma unroll
+        for (int j = 0; j < UPT; ++j) {
+            const int u = tid + j * IT_THREADS, col = u % N, kb = u / N, k0 = q * IT_KC + 8 * kb;
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+                const int k = k0 + e;
+                const bool v = u < UNITS && k < np;
+                const int ra = FWD ? 1 + k : k;
+                const int rb = (p == 0 && k >= h) ? ra : M - k;   // the mirror row (odd M: the middle alone)
+                xa[j][e] = v ? Bsrc[(size_t)ra * Nn + col] : 0.f;
+                xb[j][e] = (FWD && v) ? G[(size_t)rb * Nn + col] : 0.f;
+            }
+        }
     };
+    auto produce = [&](int q, unsigned char *bst, const float (&xa)[UPT][8], const float (&xb)[UPT][8]) {
+#pragma unroll
+        for (int j = 0; j < UPT; ++j) {
+            const int u = tid + j * IT_THREADS, col = u % N, kb = u / N, k0 = q * IT_KC + 8 * kb;
+            if (u >= UNITS) continue;
+            float x[8];
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+                if (!FWD) x[e] = xa[j][e];
+                else if (p == 0) x[e] = (k0 + e < h) ? r2 * (xa[j][e] + xb[j][e]) : xa[j][e];
+                else x[e] = r2 * (xa[j][e] - xb[j][e]);
+            }
+            it_put8(bst, Cfg::B_PART, col, 8 * kb, x);
+        }
+    };
+    float ca[UPT][8], cb[UPT][8];
+    if (q1 > q0) fetch(q0, ca, cb);
     constexpr unsigned IDESC = tc::idesc_bf16(IT_M, N);
     int copied = 0, landed = 0;   // thread 0: chunks whose A copy was issued / waited for
     if (tid == 0 && q1 > q0) {     // the first chunk's A block; each later one a chunk ahead
@@ -198,15 +228,18 @@ __global__ void __launch_bounds__(IT_THREADS, 1) k_imp_tc(CurveDev c, int splits
                 copied = i + 2;
             }
         }
-        // B chunk: units (col, k-block of 8), 8 values each
+        // B chunk: the next chunk's loads in flight while this one is written
         unsigned char *bst = Bs + st * Cfg::B_STAGE;
-        for (int u = tid; u < N * (IT_KC / 8); u += IT_THREADS) {
-            const int col = u % N, kb = u / N, k0 = q * IT_KC + 8 * kb;
-            float x[8];
+        float na[UPT][8], nb[UPT][8];
+        if (q + 1 < q1) fetch(q + 1, na, nb);
+        produce(q, bst, ca, cb);
 #pragma unroll
-            for (int e = 0; e < 8; ++e) x[e] = bval(k0 + e, col);
-            it_put8(bst, Cfg::B_PART, col, 8 * kb, x);
-        }
+        for (int j = 0; j < UPT; ++j)
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+                ca[j][e] = na[j][e];
+                cb[j][e] = nb[j][e];
+            }
         tc::fence_async_smem();
         asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::su32(&b_full[st])) : "memory");
         if (tid == 0) {
@@ -262,16 +295,19 @@ __global__ void __launch_bounds__(IT_THREADS, 1) k_imp_tc(CurveDev c, int splits
         float v[16];
         tc::ld16(tmem + ((unsigned)(32 * (warp & 3)) << 16) + (unsigned)c0, v);
         if (!ok) continue;
+        float y[16];
 #pragma unroll
         for (int e = 0; e < 16; ++e) {
             const int col = c0 + e;
-            float y = nq > 0 ? v[e] : 0.f;
+            y[e] = nq > 0 ? v[e] : 0.f;
             if (FWD) {
                 const float kw = tl * (float)(col >> 1), a = kw * kw * kw * kw - kw * kw;
-                y *= dtau / (1.f + dtau * (a * a - lm));
+                y[e] *= dtau / (1.f + dtau * (a * a - lm));
             }
-            out[col] = y;
         }
+#pragma unroll
+        for (int e = 0; e < 16; e += 4)
+            *reinterpret_cast<float4 *>(out + c0 + e) = make_float4(y[e], y[e + 1], y[e + 2], y[e + 3]);
     }
     tc::fence_before();
     __syncthreads();
