@@ -1117,11 +1117,10 @@ __device__ __forceinline__ void f4b_body(const CurveDev &c, int mode, int discre
     const bool oka = col_allowed(ca, c.sym), okb = col_allowed(cb, c.sym) && jm != 0;
     __syncthreads();   // twiddles
 
-    // pass 1: lines n2, FFT over n1, times W_F^(n2 k1), into column n2 of B
-    for (int n2 = warp; n2 < F2; n2 += F4W) {
-        V2 xv[R1];
-        T cs[R1];
-        cpx<T> t1[R1];
+    // pass 1: lines n2, FFT over n1, times W_F^(n2 k1), into column n2 of B.  A
+    // line's column values are loaded during the previous line's transform (the
+    // rows and scales first, then every load of the line at once).
+    auto load_line = [&](int n2, V2 (&xv)[R1], T (&cs)[R1]) {
 #pragma unroll
         for (int a = 0; a < R1; ++a) {
             const int k = F2 * (lane + 32 * a) + n2;
@@ -1135,20 +1134,33 @@ __device__ __forceinline__ void f4b_body(const CurveDev &c, int mode, int discre
             else if (k == P) { m = P; f = T(1) + s; }
             else if (k < 2 * P) { m = 2 * P - k; }
             if (f == T(0)) m = -1;
-            cs[a] = T(0);
-            xv[a] = V2{T(0), T(0)};
-            if (m >= 0) {
-                cs[a] = f * colscale[m];
-                xv[a] = *reinterpret_cast<const V2 *>(X + (size_t)m * N + ca);
-            }
-            t1[a] = ftw[F + (size_t)n2 * F1 + 32 * a + lane];
+            const int mm = m >= 0 ? m : 0;
+            cs[a] = m >= 0 ? f * colscale[mm] : T(0);
+            const V2 x = *reinterpret_cast<const V2 *>(X + (size_t)mm * N + ca);
+            xv[a] = m >= 0 ? x : V2{T(0), T(0)};
         }
+    };
+    V2 xv[R1];
+    T cs[R1];
+    if (warp < F2) load_line(warp, xv, cs);
+    for (int n2 = warp; n2 < F2; n2 += F4W) {
+        V2 nxv[R1];
+        T ncs[R1];
+        if (n2 + F4W < F2) load_line(n2 + F4W, nxv, ncs);
+        cpx<T> t1[R1];
+#pragma unroll
+        for (int a = 0; a < R1; ++a) t1[a] = ftw[F + (size_t)n2 * F1 + 32 * a + lane];
         cpx<T> v[R1];
 #pragma unroll
         for (int a = 0; a < R1; ++a) v[a] = {oka ? cs[a] * xv[a].x : T(0), okb ? cs[a] * xv[a].y : T(0)};
         reg_fft_fwd<T, R1>(v, tw1, w32, lane);
 #pragma unroll
         for (int a = 0; a < R1; ++a) B[(32 * a + lane) * BS + n2] = cmul(v[a], t1[a]);
+#pragma unroll
+        for (int a = 0; a < R1; ++a) {
+            xv[a] = nxv[a];
+            cs[a] = ncs[a];
+        }
     }
     __syncthreads();
 
