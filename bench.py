@@ -474,26 +474,33 @@ def implicit_context(dev, timed_steps, K, dtau=0.5):
 
 
 def symmetric_context(dev, timed_steps, K):
-    """The L=44, N_x=128, N_s=4096 curve in FP32 held in the odd subspace
-    (symmetry = 1: real parts of every section's coefficients zero, Sec. V.B)
-    beside the general run: the three-launch four-step form then transforms the
-    imaginary columns of two modes as one sequence."""
+    """Curves held in the odd subspace (Sec. V.B: real parts of every section's
+    coefficients zero) beside the general run: symmetry = 1 keeps full storage
+    (the three-launch four-step form then transforms the imaginary columns of two
+    modes as one sequence); symmetry = 5 keeps only the sine coefficients (half
+    the field bytes, half the columns of every s-contraction).  The L=44,
+    N_x=128, N_s=4096 FP32 curve and the L=22, N_x=64, N_s=1024 curve in FP32 and
+    FP64."""
     from paper_2301_11704_gb300 import gen
     from paper_2301_11704_gb300.curve import KSCurve
-    sl = spec_of("large")
-    up, um = gen.end_points(sl)
-    amps, vp = gen.perturbation(sl)
-    out = {"workload": "L=%g N_x=%d N_s=%d FP32" % (sl.L, sl.N, sl.Ns)}
-    for name, sym in (("general", 0), ("odd_subspace", 1)):
-        c = KSCurve(sl.L, sl.N, sl.Ns, sl.S, up, um, s0=sl.s0, dtau=sl.dtau, precision="fp32", symmetry=sym,
-                    device=dev)
-        c.init_trial(0.0, None, amps, vp)
-        ms, prof = timed_steps(c, K, 3, profile=K)
-        out[name] = {"ms_per_step": sum(ms) / K, "s_form": c.s_form,
-                     "phases_ms": {k: v["ms"] / v["launches"] for k, v in prof.items()
-                                   if isinstance(v, dict) and v.get("launches")}}
-        c.close()
-    out["speedup"] = out["general"]["ms_per_step"] / out["odd_subspace"]["ms_per_step"]
+    out = {}
+    for wl, prec in (("large", "fp32"), ("diff", "fp32"), ("diff", "fp64")):
+        sl = spec_of(wl)
+        up, um = gen.end_points(sl)
+        amps, vp = gen.perturbation(sl)
+        r = {}
+        for name, sym in (("general", 0), ("odd_subspace", 1), ("sine_storage", 5)):
+            c = KSCurve(sl.L, sl.N, sl.Ns, sl.S, up, um, s0=sl.s0, dtau=sl.dtau, precision=prec, symmetry=sym,
+                        device=dev)
+            c.init_trial(0.0, None, amps, vp)
+            ms, prof = timed_steps(c, K, 3, profile=K)
+            r[name] = {"ms_per_step": sum(ms) / K, "s_form": c.s_form, "workspace_bytes": c.workspace_bytes,
+                       "phases_ms": {k: v["ms"] / v["launches"] for k, v in prof.items()
+                                     if isinstance(v, dict) and v.get("launches")}}
+            c.close()
+        r["speedup_odd"] = r["general"]["ms_per_step"] / r["odd_subspace"]["ms_per_step"]
+        r["speedup_sine"] = r["general"]["ms_per_step"] / r["sine_storage"]["ms_per_step"]
+        out["L=%g N_x=%d N_s=%d %s" % (sl.L, sl.N, sl.Ns, prec.upper())] = r
     return out
 
 

@@ -99,6 +99,9 @@ typedef enum { KS_CONV_JARC = 0, KS_CONV_J = 1, KS_CONV_JREL = 2 } ks_conv;
  *   memory of about 5 (N_s / 2)^2 doubles besides the workspace. */
 typedef enum { KS_SCHEME_IMEX = 0, KS_SCHEME_IMPLICIT = 1 } ks_scheme;
 
+/* Bits of ks_params.symmetry (Sec. V.B). */
+enum { KS_SYM_ODD = 1, KS_SYM_HALF_PERIOD = 2, KS_SYM_SINE = 4 };
+
 typedef struct {
     double L;            /* domain length, > 0 (Sec. V: x in [0, L)) */
     int32_t nx;          /* N: Fourier modes = grid points per section; power of two, 8..256 */
@@ -117,7 +120,16 @@ typedef struct {
     int32_t symmetry;    /* symmetric subspace held exactly (Sec. V.B; the dynamics preserves it):
                             bit 0: every section odd, u(-x) = -u(x) (real parts of u^ zero);
                             bit 1: every section L/2-periodic (odd Fourier modes zero);
-                            0 = none.  Values above 3 are invalid. */
+                            bit 2 (KS_SYM_SINE, with bit 0 only): sine storage: every stored
+                            field keeps only Im u^_j, N_x/2 words per section instead of N_x,
+                            and every s-contraction runs on those N_x/2 columns (half the
+                            bytes and half the s-side work of bit 0 alone; same results to
+                            rounding).  Inputs and outputs of the entry points keep the
+                            physical layout.  Needs N_x >= 16, precision KS_FP64 or KS_FP32
+                            (the FFT row phase), scheme KS_SCHEME_IMEX, launch = 0 and
+                            s_transform 0, 1, 2, 4 or 5 (auto applies its rule to the
+                            N_x/2 stored columns); batches do not take it.  0 = none.
+                            Values above 7, and bit 2 without bit 0, are invalid. */
     int32_t s_transform; /* how D_t is applied along s (same result to rounding):
                             0 auto: for a single curve the form measured fastest on GB300 for its
                             size: from N_s = 684 on (FFT length >= 4096) a four-step FFT form:

@@ -17,6 +17,7 @@ KS_FP64, KS_FP32, KS_BF16X2, KS_BF16X3 = 0, 1, 2, 3
 KS_ADJ_PAPER, KS_ADJ_DISCRETE = 0, 1
 KS_CONV_JARC, KS_CONV_J, KS_CONV_JREL = 0, 1, 2
 KS_SCHEME_IMEX, KS_SCHEME_IMPLICIT = 0, 1
+KS_SYM_ODD, KS_SYM_HALF_PERIOD, KS_SYM_SINE = 1, 2, 4
 
 # Every symbol include/ksconn.h declares.
 EXPORTS = [

@@ -85,6 +85,8 @@ ks_status validate_batch(int nb, const ks_params *p)
             return ks::report_error(KS_EINVAL, "all curves of a batch must have the same adjoint mode");
         if (p[i].scheme != p[0].scheme)
             return ks::report_error(KS_EINVAL, "all curves of a batch must have the same scheme");
+        if (p[i].symmetry & KS_SYM_SINE)
+            return ks::report_error(KS_EINVAL, "batched curves keep full storage (symmetry bit 2 is for single curves)");
     }
     return KS_OK;
 }

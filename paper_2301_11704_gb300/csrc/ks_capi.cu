@@ -91,7 +91,16 @@ ks_status validate(const ks_params *p)
     if (p->adjoint != KS_ADJ_PAPER && p->adjoint != KS_ADJ_DISCRETE) return fail(KS_EINVAL, "adjoint must be KS_ADJ_PAPER or KS_ADJ_DISCRETE");
     if (p->conv < KS_CONV_JARC || p->conv > KS_CONV_JREL) return fail(KS_EINVAL, "conv must be a ks_conv value");
     if (p->check_ends != 0 && p->check_ends != 1) return fail(KS_EINVAL, "check_ends must be 0 or 1");
-    if (p->symmetry < 0 || p->symmetry > 3) return fail(KS_EINVAL, "symmetry must be in [0, 3]");
+    if (p->symmetry < 0 || p->symmetry > 7) return fail(KS_EINVAL, "symmetry must be in [0, 7]");
+    if (p->symmetry & KS_SYM_SINE) {
+        if (!(p->symmetry & KS_SYM_ODD)) return fail(KS_EINVAL, "sine storage (symmetry bit 2) needs odd sections (bit 0)");
+        if (p->nx < 16) return fail(KS_EINVAL, "sine storage needs nx >= 16 (got %d)", p->nx);
+        if (p->precision != KS_FP64 && p->precision != KS_FP32)
+            return fail(KS_EINVAL, "sine storage needs precision KS_FP64 or KS_FP32 (the FFT row phase)");
+        if (p->s_transform == 3) return fail(KS_EINVAL, "sine storage takes s_transform 0, 1, 2, 4 or 5");
+        if (p->launch != 0 || p->scheme != KS_SCHEME_IMEX)
+            return fail(KS_EINVAL, "sine storage needs launch = 0 and scheme KS_SCHEME_IMEX");
+    }
     if (p->s_transform < 0 || p->s_transform > 5) return fail(KS_EINVAL, "s_transform must be in [0, 5]");
     if ((p->s_transform == 4 || p->s_transform == 5) && ks::fft4_size(p->ns, ks::storage32(p->precision), 1) == 0)
         return fail(KS_EINVAL, "s_transform = four-step FFT needs %d <= 3 (N_s - 1) <= %d (rounded up to a power of two)",
@@ -142,7 +151,7 @@ ks_status read_scalars(ks_curve *c, ks::DevScalars *h)
 // in one launch (GM_STEP) at the sizes of f4c_fused; every other form in two.
 static bool fused_step(const ks_curve *c)
 {
-    return c->d.f4c != 0 && !c->d.impl && ks::f4c_fused(c->d.prec, c->d.nx, c->d.F);
+    return c->d.f4c != 0 && !c->d.impl && ks::f4c_fused(c->d.prec, c->d.W, c->d.F);
 }
 
 // The update of one step: the update contraction (G and |G|^2), and for the

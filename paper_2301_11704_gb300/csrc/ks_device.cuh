@@ -136,6 +136,40 @@ __device__ __forceinline__ void st2(T *p, int m, int N, int j, cpx<T> v)
     q[1] = (j == 0) ? T(0) : v.y;
 }
 
+// Columns of a stored row.  Full storage: Re and Im of mode j at columns 2j and
+// 2j + 1 (column 1, the imaginary part of the real mean, is zero).  Sine storage
+// (odd sections): Im of mode j at column j, N/2 columns (column 0, the mean's,
+// is zero).  Every s-contraction treats its columns alike; only the mode of a
+// column (its IMEX factor and norm weight) and whether the subspace keeps it
+// depend on the storage.
+__device__ __forceinline__ int col_mode(int col, int hs) { return hs ? col : col >> 1; }
+__device__ __forceinline__ bool col_live(int col, int sym, int hs)
+{
+    if (hs) return col != 0 && !((sym & 2) && (col & 1));
+    return col != 1 && col_allowed(col, sym);
+}
+// weight of a column in |q|^2 = L sum_j c_j |q^_j|^2 (c_0 = 1, c_j = 2)
+__device__ __forceinline__ int col_weight(int col, int hs) { return col_mode(col, hs) == 0 ? 1 : 2; }
+
+// Mode j of section m of a field of N-point sections in either storage (rows of N
+// words, or N/2 in sine storage, whose real parts are zero).
+template <typename T>
+__device__ __forceinline__ cpx<T> ldm(const T *p, int m, int N, int j, int hs)
+{
+    if (hs) return {T(0), j == 0 ? T(0) : p[(size_t)m * (N / 2) + j]};
+    return ld2(p, m, N, j);
+}
+
+template <typename T>
+__device__ __forceinline__ void stm(T *p, int m, int N, int j, cpx<T> v, int hs)
+{
+    if (hs) {
+        p[(size_t)m * (N / 2) + j] = (j == 0) ? T(0) : v.y;
+        return;
+    }
+    st2(p, m, N, j, v);
+}
+
 template <typename T>
 __device__ __forceinline__ T warp_sum(T v)
 {
@@ -307,7 +341,7 @@ __device__ __forceinline__ void rows_body(const CurveDev &c, int mode, int blk, 
     __shared__ double wpart[WARPS][5];
     __shared__ int am_last;
     DevScalars *sc = c.sc;
-    const int ns = c.ns, P = c.P;
+    const int ns = c.ns, P = c.P, hs = c.hs;
     const T *U = (const T *)c.U, *D = (const T *)c.D;
     T *R = (T *)c.R, *A = (T *)c.A;
     const T *kj = (const T *)c.kj, *aj = (const T *)c.aj;
@@ -346,10 +380,10 @@ __device__ __forceinline__ void rows_body(const CurveDev &c, int mode, int blk, 
     for (int i = 0; i < MPL; ++i) {
         const int j = lane + 32 * i;
         const bool ok = j < H;
-        ua[i] = (ok && has0) ? ld2(U, m0, N, j) : cpx<T>{0, 0};
-        ub[i] = (ok && has1) ? ld2(U, m1, N, j) : cpx<T>{0, 0};
-        dva[i] = (ok && has0) ? ld2(D, m0, N, j) : cpx<T>{0, 0};
-        dvb[i] = (ok && has1) ? ld2(D, m1, N, j) : cpx<T>{0, 0};
+        ua[i] = (ok && has0) ? ldm(U, m0, N, j, hs) : cpx<T>{0, 0};
+        ub[i] = (ok && has1) ? ldm(U, m1, N, j, hs) : cpx<T>{0, 0};
+        dva[i] = (ok && has0) ? ldm(D, m0, N, j, hs) : cpx<T>{0, 0};
+        dvb[i] = (ok && has1) ? ldm(D, m1, N, j, hs) : cpx<T>{0, 0};
     }
 
     if (mode == ROWS_STEP && (g_done || g_step >= g_limit)) {
@@ -436,11 +470,11 @@ __device__ __forceinline__ void rows_body(const CurveDev &c, int mode, int blk, 
                 cpx<T> pa, pb;
                 get_pair<T, N>(Pp, j, pa, pb);
                 const T a = av[i];
-                st2(R, m0, N, j, ra[i]);
-                st2(A, m0, N, j, project(cpx<T>{pa.x - a * ra[i].x, pa.y - a * ra[i].y}, j, c.sym));
+                stm(R, m0, N, j, ra[i], hs);
+                stm(A, m0, N, j, project(cpx<T>{pa.x - a * ra[i].x, pa.y - a * ra[i].y}, j, c.sym), hs);
                 if (has1) {
-                    st2(R, m1, N, j, rb[i]);
-                    st2(A, m1, N, j, project(cpx<T>{pb.x - a * rb[i].x, pb.y - a * rb[i].y}, j, c.sym));
+                    stm(R, m1, N, j, rb[i], hs);
+                    stm(A, m1, N, j, project(cpx<T>{pb.x - a * rb[i].x, pb.y - a * rb[i].y}, j, c.sym), hs);
                 }
             }
         }

@@ -232,17 +232,19 @@ __device__ __forceinline__ void load_line_twiddles(cpx<T> *twl, cpx<T> *w32, con
 // values between the row accesses, the line transforms and the scratch.  Row
 // length LS pads the line so that the column accesses (F4W lines, one or two
 // positions) fall in distinct banks: 8-byte elements pad two, 16-byte one.
-template <typename T>
+// In sine storage (HS) a CTA takes a 16-byte half sector: rows there are half as
+// long, and half sectors keep as many CTAs on the rows as full storage has.
+template <typename T, bool HS = false>
 struct F4Sector {
-    static constexpr int MPC = 32 / (2 * (int)sizeof(T));   // 4 (FP32) or 2 (FP64)
-    static constexpr int NV = 2 * MPC;                      // values of a row sector
+    static constexpr int MPC = (HS ? 16 : 32) / (2 * (int)sizeof(T));   // 4 (FP32) or 2 (FP64); halved in HS
+    static constexpr int NV = 2 * MPC;                                  // values of a row sector
 };
 
-template <typename T, int L>
+template <typename T, int L, bool HS = false>
 struct F4Stage {
     static constexpr int LS = L + (sizeof(T) == 4 ? 2 : 1);
     static constexpr int TS = F4W * LS;   // tile stride of a mode
-    static constexpr size_t BYTES = (size_t)(L + 16 + F4Sector<T>::MPC * TS) * sizeof(cpx<T>);
+    static constexpr size_t BYTES = (size_t)(L + 16 + F4Sector<T, HS>::MPC * TS) * sizeof(cpx<T>);
 };
 
 __device__ __forceinline__ void ld_sector(const float *p, float (&x)[8])
@@ -265,23 +267,41 @@ __device__ __forceinline__ void st_sector(double *p, const double (&x)[4])
     reinterpret_cast<double2 *>(p)[0] = make_double2(x[0], x[1]);
     reinterpret_cast<double2 *>(p)[1] = make_double2(x[2], x[3]);
 }
-
-// the columns 2 jm0 + i of a row sector that the subspace keeps (column 1, the
-// imaginary part of the mean, never)
-__device__ __forceinline__ bool sector_col_ok(int jm0, int i, int sym)
+// half sectors (16 bytes)
+__device__ __forceinline__ void ld_sector(const float *p, float (&x)[4])
 {
-    const int col = 2 * jm0 + i;
-    return col != 1 && col_allowed(col, sym);
+    const float4 a = *reinterpret_cast<const float4 *>(p);
+    x[0] = a.x; x[1] = a.y; x[2] = a.z; x[3] = a.w;
+}
+__device__ __forceinline__ void ld_sector(const double *p, double (&x)[2])
+{
+    const double2 a = *reinterpret_cast<const double2 *>(p);
+    x[0] = a.x; x[1] = a.y;
+}
+__device__ __forceinline__ void st_sector(float *p, const float (&x)[4])
+{
+    *reinterpret_cast<float4 *>(p) = make_float4(x[0], x[1], x[2], x[3]);
+}
+__device__ __forceinline__ void st_sector(double *p, const double (&x)[2])
+{
+    *reinterpret_cast<double2 *>(p) = make_double2(x[0], x[1]);
+}
+
+// the columns 2 jm0 + i of a row sector that the subspace keeps (in full storage
+// column 1, the imaginary part of the mean, never; in sine storage column 0)
+__device__ __forceinline__ bool sector_col_ok(int jm0, int i, int sym, int hs = 0)
+{
+    return col_live(2 * jm0 + i, sym, hs);
 }
 
 }  // namespace
 
 // ---- pass 1: lines over n1 (length F1), one per (n2, mode)
-template <typename T, int F1, int F2>
+template <typename T, int F1, int F2, bool HS = false>
 __global__ void __launch_bounds__(F4_THREADS) k_f4_p1(CurveDev c, int mode, int discrete, int gate)
 {
-    using Sec = F4Sector<T>;
-    using St = F4Stage<T, F1>;
+    using Sec = F4Sector<T, HS>;
+    using St = F4Stage<T, F1, HS>;
     constexpr int R = F1 / 32, LS = St::LS, TS = St::TS, MPC = Sec::MPC, NV = Sec::NV;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     cpx<T> *twl = (cpx<T> *)smem_raw, *w32 = twl + F1, *tile = w32 + 16;
@@ -292,13 +312,15 @@ __global__ void __launch_bounds__(F4_THREADS) k_f4_p1(CurveDev c, int mode, int 
     pdl_wait();
     if (gate && !c.sc->active) return;
 
-    const int P = c.P, N = c.nx;
+    constexpr int hs = HS ? 1 : 0;
+    const int P = c.P, N = c.W;   // N: the stored columns
     const T *X = (const T *)(mode == GM_STORE ? c.U : c.R);
     const T *colscale = (const T *)(discrete ? c.sw : c.tau);
     const T s = discrete ? T(-1) : T(1);
-    // odd sections (real parts zero): the imaginary columns of modes 2q and 2q + 1
-    // of the block as one complex sequence q, so MPC / 2 sequences per block
-    const bool paired = (c.sym & 1) != 0;
+    // odd sections in full storage (real parts zero): the imaginary columns of
+    // modes 2q and 2q + 1 of the block as one complex sequence q, so MPC / 2
+    // sequences per block (sine storage holds only those columns: no pairing)
+    const bool paired = !HS && (c.sym & 1);
     const int nq = paired ? MPC / 2 : MPC;
     // z[F2 n1 + n2] of the MPC modes (the symmetric extension of the scaled
     // columns, as in the single-CTA form): thread -> line n2_0 + tn, n1 = t / F4W + 32 i.
@@ -338,8 +360,8 @@ __global__ void __launch_bounds__(F4_THREADS) k_f4_p1(CurveDev c, int mode, int 
             } else {
 #pragma unroll
                 for (int q = 0; q < MPC; ++q)
-                    tile[q * TS + tn * LS + n1] = {sector_col_ok(jm0, 2 * q, c.sym) ? cs[h] * x[h][2 * q] : T(0),
-                                                   sector_col_ok(jm0, 2 * q + 1, c.sym) ? cs[h] * x[h][2 * q + 1] : T(0)};
+                    tile[q * TS + tn * LS + n1] = {sector_col_ok(jm0, 2 * q, c.sym, hs) ? cs[h] * x[h][2 * q] : T(0),
+                                                   sector_col_ok(jm0, 2 * q + 1, c.sym, hs) ? cs[h] * x[h][2 * q + 1] : T(0)};
             }
         }
     }
@@ -492,14 +514,14 @@ __global__ void __launch_bounds__(F4_THREADS, 3) k_f4h_p2(CurveDev c, int discre
 }
 
 // ---- pass 3: lines over k1 (length F1), one per (n2, mode): IFFT and the epilogue
-template <typename T, int F1, int F2>
+template <typename T, int F1, int F2, bool HS = false>
 __global__ void __launch_bounds__(F4_THREADS) k_f4_p3(CurveDev c, int mode, int discrete, int gate)
 {
     // GM_UPDATE_F: the update, then pass 1 of D_t u of the updated columns
     const bool chain = mode == GM_UPDATE_F;
     if (chain) mode = GM_UPDATE;
-    using Sec = F4Sector<T>;
-    using St = F4Stage<T, F1>;
+    using Sec = F4Sector<T, HS>;
+    using St = F4Stage<T, F1, HS>;
     constexpr int R = F1 / 32, LS = St::LS, TS = St::TS, MPC = Sec::MPC, NV = Sec::NV;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     cpx<T> *twl = (cpx<T> *)smem_raw, *w32 = twl + F1, *tile = w32 + 16;
@@ -514,9 +536,9 @@ __global__ void __launch_bounds__(F4_THREADS) k_f4_p3(CurveDev c, int mode, int 
     if (gate && !sc->active) return;
     const double lam_d = sc->lambda, dtau_d = sc->dtau;
 
-    // S[jm][k1][n2] of this CTA's lines and sequences -> tile (odd sections: the
-    // block's modes in pairs, as pass 1 wrote them)
-    const bool paired = (c.sym & 1) != 0;
+    // S[jm][k1][n2] of this CTA's lines and sequences -> tile (odd sections in full
+    // storage: the block's modes in pairs, as pass 1 wrote them)
+    const bool paired = !HS && (c.sym & 1);
     const int nq = paired ? MPC / 2 : MPC, sq0 = paired ? jm0 / 2 : jm0;
     const cpx<T> *S = (const cpx<T> *)c.f4s;
     for (int e = threadIdx.x; e < nq * F1 * F4W; e += F4_THREADS) {
@@ -539,11 +561,12 @@ __global__ void __launch_bounds__(F4_THREADS) k_f4_p3(CurveDev c, int mode, int 
     // epilogue over the sections j = F2 n1 + n2 < N_s: thread -> line n2_0 + tn,
     // n1 = t / F4W + 32 i; the MPC modes' columns of row j as one sector.  Two rows
     // at a time, all their loads issued before the arithmetic.
-    const int ns = c.ns, N = c.nx, P = c.P, sym = c.sym;
+    constexpr int hs = HS ? 1 : 0;
+    const int ns = c.ns, N = c.W, P = c.P, sym = c.sym;   // N: the stored columns
     const T *rowscale = (const T *)(discrete ? c.twr : c.sig);
     T *Dout = (T *)c.D, *U = (T *)c.U, *G = (T *)c.G;
     const T *Ah = (const T *)c.A;
-    const T *prec = (const T *)c.prec_imex + jm0;
+    const T *prec = (const T *)c.prec_imex;
     const T lam = (T)lam_d, dtau = (T)dtau_d;
     const int tn = threadIdx.x % F4W;
     double partsum = 0.0;
@@ -585,8 +608,8 @@ __global__ void __launch_bounds__(F4_THREADS) k_f4_p3(CurveDev c, int mode, int 
 #pragma unroll
                 for (int q = 0; q < MPC; ++q) {
                     const cpx<T> t = tile[q * TS + tn * LS + n1];
-                    y[2 * q] = sector_col_ok(jm0, 2 * q, sym) ? rsv[h] * t.x : T(0);
-                    y[2 * q + 1] = sector_col_ok(jm0, 2 * q + 1, sym) ? rsv[h] * t.y : T(0);
+                    y[2 * q] = sector_col_ok(jm0, 2 * q, sym, hs) ? rsv[h] * t.x : T(0);
+                    y[2 * q + 1] = sector_col_ok(jm0, 2 * q + 1, sym, hs) ? rsv[h] * t.y : T(0);
                 }
             }
             const size_t o = (size_t)j * N + 2 * jm0;
@@ -599,13 +622,13 @@ __global__ void __launch_bounds__(F4_THREADS) k_f4_p3(CurveDev c, int mode, int 
                 T gg = T(0);   // this row's sum over the sector in the storage type, one FP64 term per row
 #pragma unroll
                 for (int q = 0; q < NV; ++q) {
-                    g[q] = sector_col_ok(jm0, q, sym) ? -(av[h][q] + (discrete ? -lam * y[q] : lam * y[q])) : T(0);
-                    gg += ((jm0 + q / 2 == 0) ? T(1) : T(2)) * g[q] * g[q];
+                    g[q] = sector_col_ok(jm0, q, sym, hs) ? -(av[h][q] + (discrete ? -lam * y[q] : lam * y[q])) : T(0);
+                    gg += (T)col_weight(2 * jm0 + q, hs) * g[q] * g[q];
                 }
                 partsum += wv[h] * (double)gg;
                 if (mode == GM_UPDATE) {
 #pragma unroll
-                    for (int q = 0; q < NV; ++q) uv[h][q] += dtau * prec[q / 2] * g[q];
+                    for (int q = 0; q < NV; ++q) uv[h][q] += dtau * prec[col_mode(2 * jm0 + q, hs)] * g[q];
                     st_sector(U + o, uv[h]);
                 }
             } else {
@@ -623,8 +646,8 @@ __global__ void __launch_bounds__(F4_THREADS) k_f4_p3(CurveDev c, int mode, int 
                 } else {
 #pragma unroll
                     for (int q = 0; q < MPC; ++q)
-                        tile[q * TS + tn * LS + n1] = {sector_col_ok(jm0, 2 * q, sym) ? cs * uv[h][2 * q] : T(0),
-                                                       sector_col_ok(jm0, 2 * q + 1, sym) ? cs * uv[h][2 * q + 1] : T(0)};
+                        tile[q * TS + tn * LS + n1] = {sector_col_ok(jm0, 2 * q, sym, hs) ? cs * uv[h][2 * q] : T(0),
+                                                       sector_col_ok(jm0, 2 * q + 1, sym, hs) ? cs * uv[h][2 * q + 1] : T(0)};
                 }
             }
         }
@@ -777,7 +800,7 @@ __global__ void __launch_bounds__(F4_THREADS) k_f4c(CurveDev c, int mode, int di
     __shared__ double red[F4_THREADS];
     __shared__ int am_last;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, jm0 = blockIdx.y * MPC, F = F1 * F2;
-    const int P = c.P, N = c.nx, ns = c.ns, sym = c.sym;
+    const int P = c.P, N = c.W, ns = c.ns, sym = c.sym, hs = c.hs;   // N: the stored columns
     const cpx<T> *ftw = (const cpx<T> *)c.ftw;
     // the contraction being applied: GM_STEP runs the update (adjoint mode
     // `discrete`), then D_t u of the updated state (cmode, cdisc switch between them)
@@ -871,7 +894,7 @@ __global__ void __launch_bounds__(F4_THREADS) k_f4c(CurveDev c, int mode, int di
         p3_rows(j3f, a3f, u3f);
     }
     const double lam_d = sc->lambda, dtau_d = sc->dtau;
-    const T *prec = (const T *)c.prec_imex + jm0;
+    const T *prec = (const T *)c.prec_imex;
     const T lam = (T)lam_d, dtau = (T)dtau_d;
     double partsum = 0.0;
     __syncthreads();   // twiddles
@@ -910,8 +933,8 @@ __global__ void __launch_bounds__(F4_THREADS) k_f4c(CurveDev c, int mode, int di
             cpx<T> v[R1];
 #pragma unroll
             for (int a = 0; a < R1; ++a)
-                v[a] = {sector_col_ok(jm0, 2 * q, sym) ? cs[a] * x[a][2 * q] : T(0),
-                        sector_col_ok(jm0, 2 * q + 1, sym) ? cs[a] * x[a][2 * q + 1] : T(0)};
+                v[a] = {sector_col_ok(jm0, 2 * q, sym, hs) ? cs[a] * x[a][2 * q] : T(0),
+                        sector_col_ok(jm0, 2 * q + 1, sym, hs) ? cs[a] * x[a][2 * q + 1] : T(0)};
             reg_fft_fwd<T, R1>(v, tw1, w32, lane);
             cpx<T> *lt = Lt + ((size_t)q * LPC + li) * LT;
 #pragma unroll
@@ -1016,8 +1039,8 @@ __global__ void __launch_bounds__(F4_THREADS) k_f4c(CurveDev c, int mode, int di
                 T yv[NV];
 #pragma unroll
                 for (int q = 0; q < MPC; ++q) {
-                    yv[2 * q] = sector_col_ok(jm0, 2 * q, sym) ? rsv[h] * y[q][a0 + h].x : T(0);
-                    yv[2 * q + 1] = sector_col_ok(jm0, 2 * q + 1, sym) ? rsv[h] * y[q][a0 + h].y : T(0);
+                    yv[2 * q] = sector_col_ok(jm0, 2 * q, sym, hs) ? rsv[h] * y[q][a0 + h].x : T(0);
+                    yv[2 * q + 1] = sector_col_ok(jm0, 2 * q + 1, sym, hs) ? rsv[h] * y[q][a0 + h].y : T(0);
                 }
                 const size_t o = (size_t)j * N + 2 * jm0;
                 if (cmode == GM_STORE) {
@@ -1029,13 +1052,13 @@ __global__ void __launch_bounds__(F4_THREADS) k_f4c(CurveDev c, int mode, int di
                     T gg = T(0);   // the row's sum over the sector in the storage type, one FP64 term per row
 #pragma unroll
                     for (int q = 0; q < NV; ++q) {
-                        g[q] = sector_col_ok(jm0, q, sym) ? -(av[h][q] + (cdisc ? -lam * yv[q] : lam * yv[q])) : T(0);
-                        gg += ((jm0 + q / 2 == 0) ? T(1) : T(2)) * g[q] * g[q];
+                        g[q] = sector_col_ok(jm0, q, sym, hs) ? -(av[h][q] + (cdisc ? -lam * yv[q] : lam * yv[q])) : T(0);
+                        gg += (T)col_weight(2 * jm0 + q, hs) * g[q] * g[q];
                     }
                     partsum += wv[h] * (double)gg;
                     if (cmode == GM_UPDATE) {
 #pragma unroll
-                        for (int q = 0; q < NV; ++q) uv[h][q] += dtau * prec[q / 2] * g[q];
+                        for (int q = 0; q < NV; ++q) uv[h][q] += dtau * prec[col_mode(2 * jm0 + q, hs)] * g[q];
                         RV::st(U + o, uv[h]);
                     }
                 } else {
@@ -1468,40 +1491,49 @@ __global__ void k_f4_steptw(CurveDev c)
 }
 
 // ---- launchers
-template <typename T, int F1, int F2>
+template <typename T, int F1, int F2, bool HS>
 static cudaError_t f4_run(const CurveDev &c, int mode, int discrete, int gate, cudaStream_t st, cudaEvent_t *pass_ev)
 {
-    const int nm = c.nx / 2;
-    const size_t sm1 = F4Stage<T, F1>::BYTES;
-    const int nmb = c.nx / 2 / F4Sector<T>::MPC;
+    const int nm = c.W / 2;   // column pairs
+    const size_t sm1 = F4Stage<T, F1, HS>::BYTES;
+    const int nmb = c.W / 2 / F4Sector<T, HS>::MPC;
     cudaError_t e;
-    if ((e = set_smem(k_f4_p1<T, F1, F2>, sm1)) != cudaSuccess) return e;
-    if ((e = set_smem(k_f4_p3<T, F1, F2>, sm1)) != cudaSuccess) return e;
+    if ((e = set_smem(k_f4_p1<T, F1, F2, HS>, sm1)) != cudaSuccess) return e;
+    if ((e = set_smem(k_f4_p3<T, F1, F2, HS>, sm1)) != cudaSuccess) return e;
     // GM_STORE_P23: pass 1 ran inside the preceding update's pass 3
     if (mode == GM_STORE_P23) mode = GM_STORE;
-    else if ((e = launch_pdl(k_f4_p1<T, F1, F2>, dim3(nmb, F2 / F4W), sm1, st, c, mode == GM_UPDATE_F ? GM_UPDATE : mode,
-                             discrete, gate)) != cudaSuccess)
+    else if ((e = launch_pdl(k_f4_p1<T, F1, F2, HS>, dim3(nmb, F2 / F4W), sm1, st, c,
+                             mode == GM_UPDATE_F ? GM_UPDATE : mode, discrete, gate)) != cudaSuccess)
         return e;
     if (pass_ev && (e = cudaEventRecord(pass_ev[0], st)) != cudaSuccess) return e;
-    // pass 2 per sequence: the modes' columns, or for odd sections the modes' imaginary columns in pairs
-    const int nseq = (c.sym & 1) ? nm / 2 : nm;
+    // pass 2 per sequence: the column pairs, or for odd sections in full storage
+    // the modes' imaginary columns in pairs
+    const int nseq = ((c.sym & 1) && !c.hs) ? nm / 2 : nm;
     if (c.f4h) e = launch_pdl(k_f4h_p2<T, F1, F2>, dim3((F1 / 2 + 1 + F4W - 1) / F4W, nseq), 0, st, c, discrete, gate);
     else e = launch_pdl(k_f4_p2<T, F1, F2>, dim3(F1 / F4W, nseq), 0, st, c, gate);
     if (e != cudaSuccess) return e;
     if (pass_ev && (e = cudaEventRecord(pass_ev[1], st)) != cudaSuccess) return e;
-    return launch_pdl(k_f4_p3<T, F1, F2>, dim3(nmb, F2 / F4W), sm1, st, c, mode, discrete, gate);
+    return launch_pdl(k_f4_p3<T, F1, F2, HS>, dim3(nmb, F2 / F4W), sm1, st, c, mode, discrete, gate);
+}
+
+template <typename T, bool HS>
+static cudaError_t f4_dispatch_hs(const CurveDev &c, int mode, int discrete, int gate, cudaStream_t st,
+                                  cudaEvent_t *pass_ev)
+{
+    if (c.F1 == 64 && c.F2 == 64) return f4_run<T, 64, 64, HS>(c, mode, discrete, gate, st, pass_ev);
+    if (c.F1 == 128 && c.F2 == 64) return f4_run<T, 128, 64, HS>(c, mode, discrete, gate, st, pass_ev);
+    if (c.F1 == 128 && c.F2 == 128) return f4_run<T, 128, 128, HS>(c, mode, discrete, gate, st, pass_ev);
+    if (c.F1 == 256 && c.F2 == 128) return f4_run<T, 256, 128, HS>(c, mode, discrete, gate, st, pass_ev);
+    if (c.F1 == 256 && c.F2 == 256) return f4_run<T, 256, 256, HS>(c, mode, discrete, gate, st, pass_ev);
+    return cudaErrorInvalidValue;
 }
 
 template <typename T>
 static cudaError_t f4_dispatch(const CurveDev &c, int mode, int discrete, int gate, cudaStream_t st,
                                cudaEvent_t *pass_ev)
 {
-    if (c.F1 == 64 && c.F2 == 64) return f4_run<T, 64, 64>(c, mode, discrete, gate, st, pass_ev);
-    if (c.F1 == 128 && c.F2 == 64) return f4_run<T, 128, 64>(c, mode, discrete, gate, st, pass_ev);
-    if (c.F1 == 128 && c.F2 == 128) return f4_run<T, 128, 128>(c, mode, discrete, gate, st, pass_ev);
-    if (c.F1 == 256 && c.F2 == 128) return f4_run<T, 256, 128>(c, mode, discrete, gate, st, pass_ev);
-    if (c.F1 == 256 && c.F2 == 256) return f4_run<T, 256, 256>(c, mode, discrete, gate, st, pass_ev);
-    return cudaErrorInvalidValue;
+    return c.hs ? f4_dispatch_hs<T, true>(c, mode, discrete, gate, st, pass_ev)
+                : f4_dispatch_hs<T, false>(c, mode, discrete, gate, st, pass_ev);
 }
 
 template <typename T, int F1, int F2, int MPC, bool STEP>
@@ -1511,7 +1543,7 @@ static cudaError_t f4c_run(const CurveDev &c, int mode, int discrete, int gate, 
     cudaError_t e = set_smem(k_f4c<T, F1, F2, MPC, STEP>, sm);
     if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(c.f4c, c.nx / 2 / MPC);
+    cfg.gridDim = dim3(c.f4c, c.W / 2 / MPC);
     cfg.blockDim = dim3(F4_THREADS);
     cfg.dynamicSmemBytes = sm;
     cfg.stream = st;
@@ -1533,7 +1565,7 @@ template <typename T, int MPC>
 static cudaError_t f4c_dispatch(const CurveDev &c, int mode, int discrete, int gate, cudaStream_t st)
 {
     if (mode == GM_STEP) {   // the fused step exists for the sizes of f4c_fused
-        if (!f4c_fused(c.prec, c.nx, c.F)) return cudaErrorInvalidValue;
+        if (!f4c_fused(c.prec, c.W, c.F)) return cudaErrorInvalidValue;
         if (c.F1 == 64 && c.F2 == 64) return f4c_run<T, 64, 64, MPC, true>(c, mode, discrete, gate, st);
         if constexpr (sizeof(T) == 4) {
             if (c.F1 == 128 && c.F2 == 64) return f4c_run<T, 128, 64, MPC, true>(c, mode, discrete, gate, st);
@@ -1555,7 +1587,7 @@ cudaError_t launch_f4(const CurveDev &c, int mode, int discrete, int gate, cudaS
     if ((mode == GM_UPDATE_F || mode == GM_STORE_P23) && !f4h_chained(c)) return cudaErrorInvalidValue;
     if (c.f4c) {
         if (!c.prec) return f4c_dispatch<double, 1>(c, mode, discrete, gate, st);
-        return f4c_mpc(c.prec, c.nx, c.F1, c.F2) == 2 ? f4c_dispatch<float, 2>(c, mode, discrete, gate, st)
+        return f4c_mpc(c.prec, c.W, c.F1, c.F2) == 2 ? f4c_dispatch<float, 2>(c, mode, discrete, gate, st)
                                           : f4c_dispatch<float, 1>(c, mode, discrete, gate, st);
     }
     return c.prec ? f4_dispatch<float>(c, mode, discrete, gate, st, pass_ev)
@@ -1596,6 +1628,7 @@ static cudaError_t f4b_run(const CurveDev &c, int mode, int discrete, int gate, 
 
 cudaError_t launch_f4b(const CurveDev &c, int mode, int discrete, int gate, cudaStream_t st)
 {
+    if (c.hs) return cudaErrorInvalidValue;   // full rows only
     return c.prec ? f4b_run<float>(c, mode, discrete, gate, st) : f4b_run<double>(c, mode, discrete, gate, st);
 }
 

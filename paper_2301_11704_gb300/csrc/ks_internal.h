@@ -112,7 +112,8 @@ inline int fft4h_size(int ns, int fmin = F4_FMIN)
 // three launches, four-step FFT in one clustered launch.
 enum SForm { SF_DENSE = 0, SF_FFT1 = 1, SF_FFT4 = 2, SF_FFT4C = 3 };
 
-// Form that `auto` picks for a single curve: the fastest measured on GB300 (20
+// Form that `auto` picks for a single curve (nx: the contraction's columns, N_x
+// or N_x/2 in sine storage): the fastest measured on GB300 (20
 // graph-replayed steps, N_x from 8 to 256, N_s from 256 to 16384).  From
 // N_s = 684 on (F >= 4096) a four-step form wins: in FP32 the clustered one-launch
 // form up to F = 16384 at N_x <= 64 and up to F = 8192 at N_x = 128 (15-30 %
@@ -222,11 +223,15 @@ struct Layout {
     size_t off_ivtc;                   // V^-1 and V as tensor-core operands
     int ivtc;                          // 1: that region exists (single curves, FP32 storage, N >= 32)
     int isplits;                       // K chunks they hold
+    int hs;                            // sine storage (odd sections): rows of N/2 words, Im u^_j at j
+    int w;                             // stored words per section: N, or N/2 with sine storage
 };
 
 struct CurveDev {
     int ns, nx, P, prec;   // prec: 0 = double, 1 = float
-    int sym;               // symmetry bits of ks_params (coefficients held at zero)
+    int sym;               // symmetry bits 0 and 1 of ks_params (coefficients held at zero)
+    int hs;                // sine storage: every field row holds Im u^_j at column j (odd sections)
+    int W;                 // words per stored row: nx, or nx / 2 with sine storage
     double L, S, s0;
     void *U, *D, *R, *A, *G;
     void *X;               // FP64 physical scratch [N_s][N]
@@ -270,15 +275,16 @@ inline bool f4h_chained(const CurveDev &c) { return c.f4 && c.f4h && !c.f4c && !
 
 // allow_split = 0 lays a curve out without split contractions (batched curves
 // get their parallelism from the batch); bn = 0 picks the column tile width.
+// hs = 1 lays the fields out in sine storage (rows of nx / 2 words).
 Layout make_layout(int ns, int nx, int prec, int allow_split = 1, int bn = 0, int s_transform = 0,
-                   int persistent = 0, int xtc = 0, int impl = 0);
+                   int persistent = 0, int xtc = 0, int impl = 0, int hs = 0);
 // Layout of a single curve with parameters p (persistent: room for the
 // persistent step's partials when p asks for that launch form).
 inline Layout curve_layout(const ks_params *p, int persistent)
 {
     const int xtc = xtc_of(p->precision);   // the persistent step has its own (FFT) row phase
     return make_layout(p->ns, p->nx, storage32(p->precision), 1, 0, p->s_transform, persistent && !xtc, xtc,
-                       p->scheme == KS_SCHEME_IMPLICIT);
+                       p->scheme == KS_SCHEME_IMPLICIT, (p->symmetry & KS_SYM_SINE) ? 1 : 0);
 }
 // Pointers of a curve whose workspace starts at `base` (256-byte aligned).
 CurveDev bind_layout(const ks_params *p, const Layout &l, void *base);

@@ -38,10 +38,15 @@ namespace ks {
 static size_t al256(size_t x) { return (x + 255) & ~size_t(255); }
 
 Layout make_layout(int ns, int nx, int prec, int allow_split, int bn, int s_transform, int persistent, int xtc,
-                   int impl)
+                   int impl, int hs)
 {
     Layout l{};
     size_t b = prec ? 4 : 8;
+    // sine storage: every field row and every s-contraction has nx / 2 columns
+    // (the Fourier tables and the physical scratch keep nx)
+    l.hs = hs ? 1 : 0;
+    const int w = hs ? nx / 2 : nx;
+    l.w = w;
     // s_transform 0 (auto): a single curve (allow_split) takes the measured rule,
     // batched curves the one-CTA FFT form wherever it fits
     int form = SF_DENSE;
@@ -57,7 +62,7 @@ Layout make_layout(int ns, int nx, int prec, int allow_split, int bn, int s_tran
             batched_f4 = true;
         } else if (f1) form = SF_FFT1;
     }
-    else if (s_transform == 0) form = auto_form(ns, nx, prec);
+    else if (s_transform == 0) form = auto_form(ns, w, prec);   // by the contraction's columns
     else if (s_transform == 2) form = fft_size(ns, prec) ? SF_FFT1 : (fft4_size(ns, prec) ? SF_FFT4 : SF_DENSE);
     else if (s_transform == 4) form = fft4_size(ns, prec, 1) ? SF_FFT4 : SF_DENSE;
     else if (s_transform == 5) form = fft4_size(ns, prec, 1) ? SF_FFT4C : SF_DENSE;
@@ -73,14 +78,14 @@ Layout make_layout(int ns, int nx, int prec, int allow_split, int bn, int s_tran
         l.f4c = (form == SF_FFT4C && f4c_fits(prec, l.F1, l.F2)) ? F4C_CS : 0;
         l.f4b = batched_f4 ? 1 : 0;
     }
-    size_t field = al256((size_t)ns * nx * b);
-    // tiling and split of the s-contraction
-    l.bn = bn ? bn : (nx >= 64 ? 64 : 32);
+    size_t field = al256((size_t)ns * w * b);
+    // tiling and split of the s-contraction (over the w stored columns)
+    l.bn = bn ? bn : (w >= 64 ? 64 : 32);
     l.tiles_r = (ns + DT_BM - 1) / DT_BM;
-    l.tiles_c = (nx + l.bn - 1) / l.bn;
+    l.tiles_c = (w + l.bn - 1) / l.bn;
     int tiles = l.tiles_r * l.tiles_c;
-    int tiles_max = l.tiles_r * ((nx + 31) / 32);       // buffers sized for the narrowest tiles
-    if (tiles_max < nx / 2) tiles_max = nx / 2;          // the FFT form has one CTA per mode
+    int tiles_max = l.tiles_r * ((w + 31) / 32);        // buffers sized for the narrowest tiles
+    if (tiles_max < w / 2) tiles_max = w / 2;            // the FFT form has one CTA per column pair
     int ks = (allow_split && tiles < DT_TARGET_CTAS) ? DT_TARGET_CTAS / tiles : 1;
     int kmax = ns / DT_MIN_KCHUNK;
     if (ks > kmax) ks = kmax;
@@ -93,7 +98,7 @@ Layout make_layout(int ns, int nx, int prec, int allow_split, int bn, int s_tran
     l.row_blocks = (ns + ROWS_PER_CTA - 1) / ROWS_PER_CTA;
     // tensor-core form of the dense contraction: FP32 storage, single curves,
     // asked for (s_transform 3) or picked by the measured rule (auto)
-    if (prec && allow_split && l.F == 0 && (s_transform == 3 || (s_transform == 0 && tc_preferred(ns, nx)))) {
+    if (prec && allow_split && !hs && l.F == 0 && (s_transform == 3 || (s_transform == 0 && tc_preferred(ns, nx)))) {
         l.tc = 1;
         l.tc_bn = nx >= 64 ? 64 : (nx >= 32 ? 32 : 16);
         l.tc_tiles_c = (nx + l.tc_bn - 1) / l.tc_bn;
@@ -118,12 +123,12 @@ Layout make_layout(int ns, int nx, int prec, int allow_split, int bn, int s_tran
     l.off_rowsc = off; off += al256((size_t)ns * 4 * 8);
     l.off_bpart = off; off += al256((size_t)l.row_blocks * 5 * 8);
     size_t ntile = (size_t)tiles_max * DT_MAX_SPLIT;                   // either contraction form
-    if (l.f4 && ntile < (size_t)(l.F2 / 8) * (nx / 2)) ntile = (size_t)(l.F2 / 8) * (nx / 2);   // four-step CTAs
+    if (l.f4 && ntile < (size_t)(l.F2 / 8) * (w / 2)) ntile = (size_t)(l.F2 / 8) * (w / 2);   // four-step CTAs
     l.off_tile = off; off += al256(ntile * 8);
     l.off_tcnt = off; off += al256((size_t)tiles_max * 4);
     // the persistent step's split partials and per-CTA |G|^2 partials (single
     // curves in the dense form that asked for it)
-    const bool persist = persistent && allow_split && l.F == 0;
+    const bool persist = persistent && allow_split && !hs && l.F == 0;
     l.off_part = off; off += persist ? al256((size_t)l.ksplit * ns * nx * b) : 0;
     l.off_gpart = off; off += persist ? al256((size_t)PS_MAX_CTAS * 8) : 0;
     int P = ns - 1;
@@ -145,7 +150,7 @@ Layout make_layout(int ns, int nx, int prec, int allow_split, int bn, int s_tran
     l.off_ftw = off; off += l.F ? al256((size_t)l.F * (l.f4 ? 3 : 1) * 2 * b) : 0;   // four-step: + step twiddles
     // the three-launch form's scratch (also the FP64 set-up scratch, 32 F bytes);
     // the one-CTA-per-mode variant needs the set-up's only
-    l.off_f4s = off; off += l.f4 ? al256(l.f4b ? (size_t)32 * l.F : (size_t)(nx / 2) * l.F * 2 * b) : 0;
+    l.off_f4s = off; off += l.f4 ? al256(l.f4b ? (size_t)32 * l.F : (size_t)(w / 2) * l.F * 2 * b) : 0;
     // the split-BF16 row phase's DFT matrices
     l.xtc = xtc;
     l.off_xdft = off; off += xtc ? al256(xdft_bytes(nx)) : 0;
@@ -171,7 +176,9 @@ CurveDev bind_layout(const ks_params *p, const Layout &l, void *base)
     d.nx = p->nx;
     d.P = p->ns - 1;
     d.prec = storage32(p->precision);
-    d.sym = p->symmetry;
+    d.sym = p->symmetry & 3;
+    d.hs = l.hs;
+    d.W = l.w;
     d.L = p->L;
     d.S = p->S;
     d.s0 = p->s0;
@@ -418,8 +425,8 @@ __global__ void __launch_bounds__(ROWS_WARPS * 32) k_row_fwd(CurveDev c, const T
         get_pair<Tc, N>(W, j, A, B);
         A = project(A, j, c.sym);
         B = project(B, j, c.sym);
-        if (!(keep_ends && (m0 == 0 || m0 == c.P))) st2(spec, m0, N, j, cpx<To>{(To)A.x, (To)A.y});
-        if (has1 && !(keep_ends && m1 == c.P)) st2(spec, m1, N, j, cpx<To>{(To)B.x, (To)B.y});
+        if (!(keep_ends && (m0 == 0 || m0 == c.P))) stm(spec, m0, N, j, cpx<To>{(To)A.x, (To)A.y}, c.hs);
+        if (has1 && !(keep_ends && m1 == c.P)) stm(spec, m1, N, j, cpx<To>{(To)B.x, (To)B.y}, c.hs);
     }
 }
 
@@ -438,8 +445,8 @@ __global__ void __launch_bounds__(ROWS_WARPS * 32) k_row_inv(CurveDev c, const T
     if (m0 >= ns) return;
     const bool has1 = m1 < ns;
     for (int j = lane; j < H; j += 32) {
-        cpx<T> A = ld2(spec, m0, N, j);
-        cpx<T> B = has1 ? ld2(spec, m1, N, j) : cpx<T>{0, 0};
+        cpx<T> A = ldm(spec, m0, N, j, c.hs);
+        cpx<T> B = has1 ? ldm(spec, m1, N, j, c.hs) : cpx<T>{0, 0};
         put_pair<T, N>(B0, j, A, B);
     }
     if (lane == 0) B0[H] = {0, 0};
@@ -506,7 +513,7 @@ __device__ __forceinline__ void dt_body(const CurveDev &c, int mode, int discret
     const int g_active = sc->active;
     const double lam_d = sc->lambda, dtau_d = sc->dtau;
 
-    const int ns = c.ns, N = c.nx, P = c.P;
+    const int ns = c.ns, N = c.W, P = c.P, hs = c.hs;   // N: the stored columns
     const T *rowscale = (const T *)(discrete ? c.twr : c.sig);
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
     const int j0 = tile_r * BM, c0 = tile_c * BN;
@@ -558,7 +565,7 @@ __device__ __forceinline__ void dt_body(const CurveDev &c, int mode, int discret
         pS[q] = ok ? rowscale[j] : T(0);
         pA[q] = (ok && mode != GM_STORE) ? Ah[(size_t)j * N + col] : T(0);
         pU[q] = (ok && mode == GM_UPDATE) ? ((const T *)c.U)[(size_t)j * N + col] : T(0);
-        pP[q] = (ok && mode == GM_UPDATE) ? pr[col >> 1] : T(0);
+        pP[q] = (ok && mode == GM_UPDATE) ? pr[col_mode(col, hs)] : T(0);
         pW[q] = (ok && mode != GM_STORE) ? c.w[j] : 0.0;
     }
     if (gate && !g_active) return;
@@ -604,10 +611,10 @@ __device__ __forceinline__ void dt_body(const CurveDev &c, int mode, int discret
         }
         const bool interior = (j > 0 && j < P);
         T g = 0;
-        if (interior && col != 1 && col_allowed(col, c.sym)) {
+        if (interior && col_live(col, c.sym, hs)) {
             const T e = discrete ? -lam * y : lam * y;
             g = -(pA[q] + e);
-            const double cw = (col < 2) ? 1.0 : 2.0;
+            const double cw = col_weight(col, hs);
             partsum += pW[q] * cw * (double)g * (double)g;
         }
         if (mode == GM_UPDATE) {
@@ -839,7 +846,7 @@ __device__ __forceinline__ void sconv_body(const CurveDev &c, int mode, int disc
     using V2 = typename vec2<T>::type;
     constexpr int SPEC = SconvMax<T>::SPEC, EPI = SconvMax<T>::EPI, ZCH = 8;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int F = c.F, P = c.P, N = c.nx, ns = c.ns, B = SC_THREADS, t = threadIdx.x;
+    const int F = c.F, P = c.P, N = c.W, ns = c.ns, B = SC_THREADS, t = threadIdx.x;
     cpx<T> *Z = (cpx<T> *)smem_raw, *Wb = Z + F, *tw = Wb + F;   // tw: F entries
     __shared__ double red[SC_THREADS];
     __shared__ int am_last;
@@ -876,8 +883,10 @@ __device__ __forceinline__ void sconv_body(const CurveDev &c, int mode, int disc
     const T *colscale = (const T *)(discrete ? c.sw : c.tau);
     const T *rowscale = (const T *)(discrete ? c.twr : c.sig);
     const T s = discrete ? T(-1) : T(1);
+    // the CTA's column pair (a Fourier mode in full storage, two modes' imaginary
+    // parts in sine storage)
     const int ca = 2 * jm, cb = 2 * jm + 1;
-    const bool oka = col_allowed(ca, c.sym), okb = col_allowed(cb, c.sym) && jm != 0;
+    const bool oka = col_live(ca, c.sym, c.hs), okb = col_live(cb, c.sym, c.hs);
     // z of the two columns, packed as za + i zb; the (Re, Im) pair is one vector load
     for (int k0 = t; k0 < F; k0 += ZCH * B) {
         V2 xv[ZCH];
@@ -923,7 +932,7 @@ __device__ __forceinline__ void sconv_body(const CurveDev &c, int mode, int disc
     // epilogue operands of the sections j = t + i B, issued before the product
     T *Dout = (T *)c.D, *U = (T *)c.U, *G = (T *)c.G;
     const T *Ah = (const T *)c.A;
-    const T pr = ((const T *)c.prec_imex)[jm];
+    const T pra = ((const T *)c.prec_imex)[col_mode(ca, c.hs)], prb = ((const T *)c.prec_imex)[col_mode(cb, c.hs)];
     T rs[EPI];
     double wj[EPI];
     V2 av[EPI], uv[EPI];
@@ -947,7 +956,7 @@ __device__ __forceinline__ void sconv_body(const CurveDev &c, int mode, int disc
 
     // epilogue over the sections j = 0..P of the two columns
     const T lam = (T)lam_d, dtau = (T)dtau_d;
-    const double cw = (jm == 0) ? 1.0 : 2.0;
+    const double cw = col_weight(cb, c.hs);   // column a's weight where it is live
     double partsum = 0.0;
 #pragma unroll
     for (int i = 0; i < EPI; ++i) {
@@ -967,7 +976,7 @@ __device__ __forceinline__ void sconv_body(const CurveDev &c, int mode, int disc
         }
         if (mode == GM_UPDATE) {
             if (interior)
-                *reinterpret_cast<V2 *>(U + (size_t)j * N + ca) = V2{uv[i].x + dtau * pr * ga, uv[i].y + dtau * pr * gb};
+                *reinterpret_cast<V2 *>(U + (size_t)j * N + ca) = V2{uv[i].x + dtau * pra * ga, uv[i].y + dtau * prb * gb};
         } else {
             *reinterpret_cast<V2 *>(G + (size_t)j * N + ca) = V2{ga, gb};
         }
@@ -1003,7 +1012,7 @@ __global__ void __launch_bounds__(SC_THREADS) k_sconv_batch(const CurveDev *cv, 
 {
     const int2 it = items[blockIdx.x];
     const CurveDev &c = cv[it.x];
-    sconv_body<T>(c, mode, discrete, gate, it.y, c.nx / 2);
+    sconv_body<T>(c, mode, discrete, gate, it.y, c.W / 2);
 }
 
 template <typename T>
@@ -1194,7 +1203,7 @@ static cudaError_t launch_sconv_t(const CurveDev &c, int mode, int discrete, int
     const size_t sm = sconv_smem<T>(c.F);
     cudaError_t e = set_smem(k_sconv<T>, sm);
     if (e != cudaSuccess) return e;
-    return launch_step_kernel(k_sconv<T>, dim3(c.nx / 2), dim3(SC_THREADS), sm, st, 0, c, mode, discrete, gate);
+    return launch_step_kernel(k_sconv<T>, dim3(c.W / 2), dim3(SC_THREADS), sm, st, 0, c, mode, discrete, gate);
 }
 
 cudaError_t launch_sconv_batch(int prec, int F_max, const CurveDev *cv, const int2 *items, int nitems, int mode,

@@ -40,7 +40,10 @@ class KSCurve:
     curve's device in its storage dtype (float64 for "fp64", float32 for "fp32").
     Row 0 is s = +inf (u_plus), row ns-1 is s = -inf (u_minus).
     symmetry: 1 holds every section odd, 2 holds it L/2-periodic, 3 both (the
-    symmetric subspaces the descent preserves, Sec. V.B).
+    symmetric subspaces the descent preserves, Sec. V.B); adding 4 to an odd
+    value (5, 7) also stores only the sine coefficients Im u^_j (half the field
+    bytes and half the columns of every s-contraction; FP64 or FP32, nx >= 16,
+    s_transform "auto", "dense", "fft", "fft4" or "fft4c").
     s_transform: how D_t is applied along s (same results to rounding): "auto"
     (the form measured fastest for the size), "dense", "dense_tc" (FP32, tensor
     cores), "fft" (one CTA per mode; four-step above its limit), "fft4" (four-step

@@ -56,9 +56,23 @@ def test_workspace_size_scales_with_the_curve(lib):
     assert big < 16 * 16384 * 256 * 8   # fields, FP64 scratch and the four-step scratch (about 4 fields)
 
 
+def test_sine_storage_halves_the_fields(lib):
+    """Symmetry bit 2 keeps N_x/2 words per section in each of the five fields (and
+    half the four-step scratch); the FP64 physical scratch and the tables stay."""
+    for kw in (dict(), dict(precision=1, nx=64, ns=1500, s_transform=4)):
+        full = lib.ks_curve_workspace_bytes(ctypes.byref(_params(symmetry=1, **kw)))
+        sine = lib.ks_curve_workspace_bytes(ctypes.byref(_params(symmetry=5, **kw)))
+        p = _params(**kw)
+        b = 8 if p.precision == 0 else 4
+        half_field = p.ns * p.nx // 2 * b
+        assert 0 < sine < full and full - sine >= 5 * half_field - 5 * 256
+
+
 @pytest.mark.parametrize("bad", [dict(nx=24), dict(nx=4), dict(nx=512), dict(ns=2), dict(L=0.0), dict(S=-1.0),
                                  dict(dtau=0.0), dict(precision=7), dict(precision=4), dict(precision=2, nx=32), dict(precision=3, nx=16), dict(adjoint=3), dict(conv=9),
-                                 dict(symmetry=4), dict(s_transform=6), dict(s_transform=4, ns=500), dict(s_transform=5, ns=500), dict(s_transform=5, ns=12000, precision=0), dict(s_transform=3, precision=0), dict(launch=2), dict(L=float("nan"))])
+                                 dict(symmetry=4), dict(symmetry=6), dict(symmetry=8), dict(symmetry=5, nx=8),
+                                 dict(symmetry=5, precision=2, nx=64), dict(symmetry=5, precision=1, s_transform=3),
+                                 dict(symmetry=5, launch=1), dict(symmetry=5, scheme=1), dict(s_transform=6), dict(s_transform=4, ns=500), dict(s_transform=5, ns=500), dict(s_transform=5, ns=12000, precision=0), dict(s_transform=3, precision=0), dict(launch=2), dict(L=float("nan"))])
 def test_invalid_parameters_are_rejected_on_the_host(lib, bad):
     p = _params(**bad)
     assert lib.ks_curve_workspace_bytes(ctypes.byref(p)) == 0
@@ -111,6 +125,13 @@ def test_null_handle_is_rejected(lib):
     (dict(precision=1, nx=64, ns=1024, s_transform=4), 4096, 4),
     (dict(precision=1, nx=128, ns=1024, s_transform=1), 0, 1),
     (dict(precision=1, nx=128, ns=1024, s_transform=3), 0, 3),
+    (dict(precision=1, nx=64, ns=1024, symmetry=5), 4096, 5),   # sine storage: the rule on the 32 stored columns
+    (dict(precision=1, nx=256, ns=2731, symmetry=5), 8192, 5),  # 128 stored columns: clustered (full rows: three-launch)
+    (dict(precision=1, nx=256, ns=2731, symmetry=1), 8192, 4),
+    (dict(precision=0, nx=256, ns=1024, symmetry=5), 4096, 4),  # FP64, 128 columns: four-step (full rows: one CTA per mode)
+    (dict(precision=1, nx=64, ns=30000, symmetry=5), 0, 1),     # sine storage: SIMT dense, not the tensor-core form
+    (dict(precision=0, nx=64, ns=600, symmetry=7), 0, 1),       # FP64, 32 stored columns below N_s = 684: dense
+    (dict(precision=0, nx=128, ns=600, symmetry=5), 2048, 2),   # 64 stored columns: one CTA per column pair
     (dict(nx=24), -1, -1),
 ])
 def test_s_transform_rule(lib, kw, F, form):
