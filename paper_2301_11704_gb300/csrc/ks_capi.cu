@@ -30,6 +30,8 @@ struct ks_curve {
     cudaGraphExec_t gexec = nullptr;
     cudaStream_t gstream = nullptr;
     int gdiscrete = -1;
+    // tensor maps of U and D_t U for the FFT row phase's tile loads (d.rowmaps)
+    ks::RowMaps rmaps{};
 };
 
 static const int GRAPH_STEPS = 16;
@@ -361,6 +363,14 @@ ks_status ks_curve_create(const ks_params *p, const double *u_plus_host, const d
     }
     ks_status r = KS_OK;
     do {
+        if (!c->d.xtc && p->ns >= ks::ROWS_TMA_MIN_NS) {
+            const cudaError_t e = ks::make_row_maps(c->d, &c->rmaps);
+            if (e != cudaSuccess) {
+                r = fail(KS_ECUDA, "encoding the row phase's tensor maps failed: %s", cudaGetErrorString(e));
+                break;
+            }
+            c->d.rowmaps = &c->rmaps;
+        }
         const size_t nb = (size_t)p->nx * sizeof(double);
         if (cudaMemcpyAsync(c->d.ends, u_plus_host, nb, cudaMemcpyHostToDevice, c->st) != cudaSuccess ||
             cudaMemcpyAsync(c->d.ends + p->nx, u_minus_host, nb, cudaMemcpyHostToDevice, c->st) != cudaSuccess ||

@@ -9,6 +9,7 @@
 #include <utility>
 
 #include "ks_internal.h"
+#include "ks_tcgen05.cuh"
 
 namespace ks {
 
@@ -328,9 +329,22 @@ __device__ __forceinline__ int rows_finish(const CurveDev &c, int mode, int nblk
     return go;
 }
 
+// Shared-memory tiles of the row phase's TMA loads: U and D_t U rows of the CTA,
+// [2 WARPS][W] each, 128-byte aligned after the transform buffers.
+template <typename T, int N, int WARPS>
+__device__ __forceinline__ T *rows_tiles(unsigned char *smem_raw)
+{
+    const size_t off = (size_t)(N / 2 + WARPS * 3 * N) * sizeof(cpx<T>);
+    const unsigned a = tc::su32(smem_raw + off);
+    return (T *)(smem_raw + off + ((128u - (a & 127u)) & 127u));
+}
+
+// tm (single curves): U and D_t U of the CTA's sections come in as two tiles by
+// TMA (one tensor-map copy each, issued by thread 0 once the predecessor's writes
+// are visible) instead of per-lane loads; rows past the curve read as zeros.
 template <typename T, int N, int WARPS = ROWS_WARPS>
 __device__ __forceinline__ void rows_body(const CurveDev &c, int mode, int blk, int nblk, bool tail,
-                                          StepArm arm = StepArm{0, 0.0, 0})
+                                          StepArm arm = StepArm{0, 0.0, 0}, const RowMaps *tm = nullptr)
 {
     constexpr int H = N / 2;
     constexpr int MPL = (H + 31) / 32;
@@ -340,6 +354,13 @@ __device__ __forceinline__ void rows_body(const CurveDev &c, int mode, int blk, 
     cpx<T> *B0 = tw + H + warp * 3 * N, *B1 = B0 + N, *B2 = B1 + N;
     __shared__ double wpart[WARPS][5];
     __shared__ int am_last;
+    __shared__ unsigned long long tbar;
+    T *tileU = tm ? rows_tiles<T, N, WARPS>(smem_raw) : nullptr;
+    T *tileD = tm ? tileU + (size_t)2 * WARPS * c.W : nullptr;
+    if (tm && threadIdx.x == 0) {
+        tc::bar_init(&tbar, 1);
+        tc::fence_bar_init();
+    }
     DevScalars *sc = c.sc;
     const int ns = c.ns, P = c.P, hs = c.hs;
     const T *U = (const T *)c.U, *D = (const T *)c.D;
@@ -363,7 +384,14 @@ __device__ __forceinline__ void rows_body(const CurveDev &c, int mode, int blk, 
     }
     const T wm0 = has0 ? (T)c.w[m0] : T(0), wm1 = has1 ? (T)c.w[m1] : T(0);   // quadrature weights
     for (int t = threadIdx.x + blockDim.x; t < H; t += blockDim.x) tw[t] = ((const cpx<T> *)c.twid)[t];
+    if (tm) __syncthreads();   // the barrier's initialisation, before any thread waits on it
     pdl_wait();
+    if (tm && threadIdx.x == 0) {
+        const unsigned tb = (unsigned)(2 * WARPS * c.W * sizeof(T));   // the whole box, zero-filled past N_s
+        tc::expect_tx(&tbar, 2 * tb);
+        tc::tensor_g2s_2d(tileU, &tm->u, 0, blk * 2 * WARPS, &tbar);
+        tc::tensor_g2s_2d(tileD, &tm->d, 0, blk * 2 * WARPS, &tbar);
+    }
     // an armed call starts from the current step with `done` cleared; block 0
     // records the limit for the later kernels before its arrival at the
     // reduction, which orders these writes before the last CTA's
@@ -376,14 +404,28 @@ __device__ __forceinline__ void rows_body(const CurveDev &c, int mode, int blk, 
         sc->done = 0;
         sc->status = 0;
     }
+    const T *Us = U, *Ds = D;
+    int r0 = m0, r1 = m1;
+    if (tm) {
+        // every thread waits for the tiles (bounded: a wait that gives up records
+        // the error, then waits again so that no copy lands after the CTA is gone)
+        if (!tc::bar_wait(&tbar, 0, wait_bound(*sc))) {
+            atomicExch(&sc->err, 1);
+            tc::bar_wait(&tbar, 0);
+        }
+        Us = tileU;
+        Ds = tileD;
+        r0 = 2 * warp;
+        r1 = r0 + 1;
+    }
 #pragma unroll
     for (int i = 0; i < MPL; ++i) {
         const int j = lane + 32 * i;
         const bool ok = j < H;
-        ua[i] = (ok && has0) ? ldm(U, m0, N, j, hs) : cpx<T>{0, 0};
-        ub[i] = (ok && has1) ? ldm(U, m1, N, j, hs) : cpx<T>{0, 0};
-        dva[i] = (ok && has0) ? ldm(D, m0, N, j, hs) : cpx<T>{0, 0};
-        dvb[i] = (ok && has1) ? ldm(D, m1, N, j, hs) : cpx<T>{0, 0};
+        ua[i] = (ok && has0) ? ldm(Us, r0, N, j, hs) : cpx<T>{0, 0};
+        ub[i] = (ok && has1) ? ldm(Us, r1, N, j, hs) : cpx<T>{0, 0};
+        dva[i] = (ok && has0) ? ldm(Ds, r0, N, j, hs) : cpx<T>{0, 0};
+        dvb[i] = (ok && has1) ? ldm(Ds, r1, N, j, hs) : cpx<T>{0, 0};
     }
 
     if (mode == ROWS_STEP && (g_done || g_step >= g_limit)) {
@@ -678,10 +720,13 @@ struct DtContract {
 // ---------------------------------------------------------------------------
 // Launch helpers
 // ---------------------------------------------------------------------------
+// tiles: room for the TMA tiles of U and D_t U (2 warps rows of W words each,
+// 128-byte aligned) after the transform buffers
 template <typename T>
-static size_t rows_smem(int N, int bufs, int warps = ROWS_WARPS)
+static size_t rows_smem(int N, int bufs, int warps = ROWS_WARPS, int tiles_w = 0)
 {
-    return (size_t)(N / 2 + warps * bufs * N) * sizeof(cpx<T>);
+    const size_t base = (size_t)(N / 2 + warps * bufs * N) * sizeof(cpx<T>);
+    return tiles_w ? base + 128 + (size_t)2 * 2 * warps * tiles_w * sizeof(T) : base;
 }
 
 // Sets a kernel's dynamic shared-memory limit to the largest size requested so

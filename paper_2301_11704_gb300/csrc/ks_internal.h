@@ -6,6 +6,7 @@
 #include <cstdint>
 #include <vector>
 
+#include <cuda.h>   // CUtensorMap (the tensor maps are encoded through the runtime's driver entry point)
 #include <cuda_runtime.h>
 
 #include "../../include/ksconn.h"
@@ -154,6 +155,10 @@ inline int xtc_of(int precision) { return precision == KS_BF16X3 ? 3 : (precisio
 // packed into one complex FFT.
 constexpr int ROWS_WARPS = 4;
 constexpr int ROWS_PER_CTA = 2 * ROWS_WARPS;
+// Single curves from this N_s on load the row phase's tiles of U and D_t U by
+// TMA (measured on GB300: 1-2% faster row phase at N_s = 4096 and 16384; at
+// N_s = 1024, 128 CTAs, 5-8% slower than per-lane loads, which are kept there).
+constexpr int ROWS_TMA_MIN_NS = 2048;
 
 constexpr int MAX_PERT = 16;
 
@@ -227,6 +232,12 @@ struct Layout {
     int w;                             // stored words per section: N, or N/2 with sine storage
 };
 
+// Tensor maps of a single curve's fields U and D_t U for the row phase's tile
+// loads (TMA): 2D [N_s][W] in the storage type, box W x ROWS_PER_CTA.
+struct RowMaps {
+    CUtensorMap u, d;
+};
+
 struct CurveDev {
     int ns, nx, P, prec;   // prec: 0 = double, 1 = float
     int sym;               // symmetry bits 0 and 1 of ks_params (coefficients held at zero)
@@ -268,6 +279,7 @@ struct CurveDev {
     void *twid, *twid64, *kj, *aj, *prec_imex;
     double *ends, *pert;
     DevScalars *sc;
+    const RowMaps *rowmaps;   // host pointer: U and D tile maps of a single curve's row phase (else null)
 };
 
 // A curve whose step chains its two contractions (GM_UPDATE_F, GM_STORE_P23).
@@ -288,6 +300,9 @@ inline Layout curve_layout(const ks_params *p, int persistent)
 }
 // Pointers of a curve whose workspace starts at `base` (256-byte aligned).
 CurveDev bind_layout(const ks_params *p, const Layout &l, void *base);
+// Encodes the row phase's tensor maps of U and D (FFT row phase); the caller keeps
+// *m alive while c.rowmaps points to it.
+cudaError_t make_row_maps(const CurveDev &c, RowMaps *m);
 
 // ks_capi.cu: parameter rules of the entry points, and the thread-local
 // message returned by ks_last_error().

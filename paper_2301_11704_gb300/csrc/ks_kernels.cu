@@ -465,10 +465,12 @@ __global__ void __launch_bounds__(ROWS_WARPS * 32) k_row_inv(CurveDev c, const T
     }
 }
 
+// use_tm: the CTA's rows of U and D_t U come in by TMA through the tensor maps tm
 template <typename T, int N>
-__global__ void __launch_bounds__(ROWS_WARPS * 32) k_rows(CurveDev c, int mode, StepArm arm)
+__global__ void __launch_bounds__(ROWS_WARPS * 32) k_rows(CurveDev c, int mode, StepArm arm,
+                                                          const __grid_constant__ RowMaps tm, int use_tm)
 {
-    rows_body<T, N>(c, mode, blockIdx.x, gridDim.x, true, arm);
+    rows_body<T, N>(c, mode, blockIdx.x, gridDim.x, true, arm, use_tm ? &tm : nullptr);
 }
 
 // Batched row phase: work item (curve, row block) per CTA; every curve keeps its
@@ -1063,13 +1065,50 @@ static cudaError_t launch_step_kernel(void (*kern)(KArgs...), dim3 grid, dim3 bl
 template <typename T>
 static cudaError_t rows_t(const CurveDev &c, int mode, cudaStream_t st, StepArm arm)
 {
+    static const RowMaps none{};
+    const int use_tm = c.rowmaps ? 1 : 0;
+    const RowMaps &tm = c.rowmaps ? *c.rowmaps : none;
     return dispatch_n(c.nx, [&](auto nn) {
         constexpr int NN = decltype(nn)::value;
-        size_t sm = rows_smem<T>(NN, 3);
+        size_t sm = rows_smem<T>(NN, 3, ROWS_WARPS, use_tm ? c.W : 0);
         cudaError_t e = set_smem(k_rows<T, NN>, sm);
         if (e != cudaSuccess) return e;
-        return launch_step_kernel(k_rows<T, NN>, dim3(row_grid(c.ns)), dim3(ROWS_WARPS * 32), sm, st, 0, c, mode, arm);
+        return launch_step_kernel(k_rows<T, NN>, dim3(row_grid(c.ns)), dim3(ROWS_WARPS * 32), sm, st, 0, c, mode, arm,
+                                  tm, use_tm);
     });
+}
+
+// The driver's tensor-map encoder, through the runtime's entry-point query (no
+// link against the driver library).
+using EncodeTiled = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                 const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+cudaError_t make_row_maps(const CurveDev &c, RowMaps *m)
+{
+    static EncodeTiled enc = nullptr;
+    if (!enc) {
+        void *fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
+        if (e != cudaSuccess) return e;
+        if (q != cudaDriverEntryPointSuccess || !fn) return cudaErrorNotSupported;
+        enc = (EncodeTiled)fn;
+    }
+    const size_t b = c.prec ? 4 : 8;
+    const cuuint64_t dims[2] = {(cuuint64_t)c.W, (cuuint64_t)c.ns};        // columns, sections
+    const cuuint64_t strides[1] = {(cuuint64_t)(c.W * b)};                // bytes between sections
+    const cuuint32_t box[2] = {(cuuint32_t)c.W, (cuuint32_t)ROWS_PER_CTA};
+    const cuuint32_t estr[2] = {1, 1};
+    const CUtensorMapDataType dt = c.prec ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64;
+    void *src[2] = {c.U, c.D};
+    CUtensorMap *dst[2] = {&m->u, &m->d};
+    for (int i = 0; i < 2; ++i)
+        if (enc(dst[i], dt, 2, src[i], dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) !=
+            CUDA_SUCCESS)
+            return cudaErrorInvalidValue;
+    return cudaSuccess;
 }
 
 template <typename Tc, typename To>

@@ -101,6 +101,25 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned by
                  : "memory");
 }
 
+// Tiled tensor copy (TMA) of the 2D box at coordinates (x, y) of the tensor map
+// `map` (a __grid_constant__ kernel parameter) into shared memory, completing on
+// `bar` (armed for the box's bytes by expect_tx).  x * element size must be a
+// multiple of 16 bytes; elements outside the tensor are filled with zeros.
+__device__ __forceinline__ void tensor_g2s_2d(void *dst, const void *map, int x, int y, unsigned long long *bar)
+{
+    asm volatile("cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+                 ::"r"(su32(dst)), "l"(map), "r"(x), "r"(y), "r"(su32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void expect_tx(unsigned long long *bar, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(bar)), "r"(bytes) : "memory");
+}
+
+// Makes an initialised mbarrier visible to the asynchronous (TMA) proxy.
+__device__ __forceinline__ void fence_bar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+
 __device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 // Orders this thread's generic-proxy shared-memory writes before later async-proxy

@@ -202,7 +202,8 @@ def test_config1_single_evaluation(precision, tol, s_transform):
 
 
 @pytest.mark.parametrize("s_transform", ["dense", "fft"])
-@pytest.mark.parametrize("N,Ns", [(8, 3), (8, 16), (16, 37), (32, 33), (64, 65), (128, 31), (256, 20), (32, 129)])
+@pytest.mark.parametrize("N,Ns", [(8, 3), (8, 16), (16, 37), (32, 33), (64, 65), (128, 31), (256, 20), (32, 129),
+                                  (16, 2053)])   # the last: row tiles by TMA, ragged last tile
 def test_edge_shapes_fp64(N, Ns, s_transform):
     """Smallest curve (one interior section), ragged N_s (odd, not a tile multiple),
     every supported N_x, on a random smooth curve; includes 20 descent steps."""

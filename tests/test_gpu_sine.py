@@ -53,6 +53,7 @@ CASES = [  # (N_x, N_s, form): every form that takes sine storage, ragged N_s, s
     (64, 301, "fft"),       # one CTA per column pair, F = 1024
     (64, 1500, "fft4"),     # three-launch four-step, F = 4096
     (16, 1500, "fft4"),     # N_x = 16: one row sector of four FP32 column pairs
+    (32, 2100, "fft4"),     # the row phase's tiles by TMA (N_s >= 2048), ragged last tile
     (64, 1024, "fft4c"),    # clustered four-step, F = 4096
     (128, 1024, "auto"),    # FP32 clustered in both storages; FP64 three-launch
     (256, 1024, "auto"),    # FP64: one CTA per mode in full storage, four-step on the 128 stored columns
@@ -96,7 +97,7 @@ def test_sine_storage_matches_full_storage(N, Ns, form, precision, sym):
 
 
 @pytest.mark.parametrize("adjoint", ["paper", "discrete"])
-@pytest.mark.parametrize("N,Ns,form", [(32, 301, "dense"), (32, 301, "fft"), (32, 1500, "fft4")])
+@pytest.mark.parametrize("N,Ns,form", [(32, 301, "dense"), (32, 301, "fft"), (32, 1500, "fft4"), (32, 2100, "fft4")])
 def test_sine_storage_fp64_matches_oracle(N, Ns, form, adjoint):
     """FP64 sine storage against the oracle: residual, J, J_arc, the gradient and
     five descent steps (the oracle keeps full coefficients; its odd curve stays odd)."""
