@@ -283,6 +283,8 @@ ks_status ks_curve_get_state(ks_curve *c, void *u_dev, double *lambda, double *t
 
 /* Replaces the state (all rows, including the end sections) from a physical
  * [N_s][N] array in the storage type, with lambda and tau; step is reset to 0.
+ * The array is transformed in FP64 (FP32 storage: double-float arithmetic,
+ * about 44 bits) and rounded per coefficient to the storage type.
  * Asynchronous. */
 ks_status ks_curve_set_state(ks_curve *c, const void *u_dev, double lambda, double tau);
 

@@ -32,6 +32,9 @@ struct ks_curve {
     int gdiscrete = -1;
     // tensor maps of U and D_t U for the FFT row phase's tile loads (d.rowmaps)
     ks::RowMaps rmaps{};
+    // pinned host copy of the scalars at the start of a descend call (read back
+    // with the final ones, one synchronisation per call)
+    ks::DevScalars *h0 = nullptr;
 };
 
 static const int GRAPH_STEPS = 16;
@@ -363,6 +366,11 @@ ks_status ks_curve_create(const ks_params *p, const double *u_plus_host, const d
     }
     ks_status r = KS_OK;
     do {
+        if (cudaMallocHost((void **)&c->h0, sizeof(ks::DevScalars)) != cudaSuccess) {
+            c->h0 = nullptr;
+            r = fail(KS_ENOMEM, "pinned host allocation of the scalars failed");
+            break;
+        }
         if (!c->d.xtc && p->ns >= ks::ROWS_TMA_MIN_NS) {
             const cudaError_t e = ks::make_row_maps(c->d, &c->rmaps);
             if (e != cudaSuccess) {
@@ -410,7 +418,7 @@ ks_status ks_curve_create(const ks_params *p, const double *u_plus_host, const d
         }
     } while (0);
     if (r != KS_OK) {
-        delete c;
+        ks_curve_destroy(c);
         return r;
     }
     *out = c;
@@ -518,15 +526,15 @@ ks_status ks_curve_descend(ks_curve *c, int64_t nsteps, double tol, int64_t *ste
     if (!std::isfinite(tol)) return fail(KS_EINVAL, "tol must be finite");
     DeviceGuard g(c->device);
     if (!g.ok) return fail(KS_ECUDA, "cannot select the curve's device");
-    ks::DevScalars h0;
-    s = read_scalars(c, &h0);
-    if (s != KS_OK) return s;
+    // the step count at the start, copied before the steps and read after them
+    KS_CUDA(cudaMemcpyAsync(c->h0, c->d.sc, sizeof(ks::DevScalars), cudaMemcpyDeviceToHost, c->st));
     s = enqueue_steps(c, nsteps, tol);
     if (s != KS_OK) return s;
     KS_CUDA(ks::launch_rows(c->d, ks::ROWS_EVAL, c->st));
     ks::DevScalars h;
     s = read_scalars(c, &h);
     if (s != KS_OK) return s;
+    const ks::DevScalars h0 = *c->h0;
     if (steps_done) *steps_done = h.step - h0.step;
     if (J) *J = std::sqrt(h.J2);
     if (J_arc) *J_arc = h.Jarc;
@@ -584,8 +592,11 @@ ks_status ks_curve_set_state(ks_curve *c, const void *u_dev, double lambda, doub
     if (!std::isfinite(lambda) || !std::isfinite(tau)) return fail(KS_EINVAL, "lambda and tau must be finite");
     DeviceGuard g(c->device);
     if (!g.ok) return fail(KS_ECUDA, "cannot select the curve's device");
-    KS_CUDA(ks::launch_widen(c->d, u_dev, c->st));
-    KS_CUDA(ks::launch_row_fwd_x(c->d, c->d.U, 0, c->st));
+    // the forward transform straight from the input, in FP64 or, for FP32
+    // storage, double-float (the linear term of f multiplies each coefficient by
+    // a_j ~ k_j^4: a coefficient must keep its own relative precision, not that
+    // of the largest one, which an FP32 transform would give it)
+    KS_CUDA(ks::launch_row_fwd(c->d, u_dev, c->d.U, c->st));
     s = refresh_dt_u(c);
     if (s != KS_OK) return s;
     KS_CUDA(ks::launch_set_lambda_tau(c->d, lambda, tau, c->st));
@@ -682,6 +693,7 @@ ks_status ks_curve_destroy(ks_curve *c)
         release_events(c);
         if (c->gexec) cudaGraphExecDestroy(c->gexec);
         if (c->gstream) cudaStreamDestroy(c->gstream);
+        if (c->h0) cudaFreeHost(c->h0);
     }
     delete c;
     return KS_OK;

@@ -326,6 +326,11 @@ cudaError_t launch_set_ends(const CurveDev &c, cudaStream_t st);
 // spectral state = forward transform of X, computed in FP64 and rounded per
 // coefficient to the storage type
 cudaError_t launch_row_fwd_x(const CurveDev &c, void *spec, int keep_ends, cudaStream_t st);
+// spectral state = forward transform of a physical curve given in the storage
+// type: FP64 storage in FP64; FP32 storage in double-float arithmetic (about 44
+// bits on the FP32 pipes, ks_dfloat.cuh), rounded per coefficient to FP32 as the
+// FP64 transform of launch_row_fwd_x
+cudaError_t launch_row_fwd(const CurveDev &c, const void *phys, void *spec, cudaStream_t st);
 // spec -> phys; scale_mode 0: plain; 1: Euclidean gradient scaling -2 dx w_m
 // and zero end rows.
 cudaError_t launch_row_inv(const CurveDev &c, const void *spec, void *phys, int scale_mode, cudaStream_t st);

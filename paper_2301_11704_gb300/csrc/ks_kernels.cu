@@ -29,6 +29,7 @@
 #include <cooperative_groups.h>
 
 #include "ks_device.cuh"
+#include "ks_dfloat.cuh"
 
 namespace ks {
 
@@ -399,25 +400,31 @@ __global__ void k_set_ends(CurveDev c)
 // ---------------------------------------------------------------------------
 // Row transforms (physical <-> spectral), two sections per warp
 // ---------------------------------------------------------------------------
-// Physical -> spectral in the compute type Tc (the type of the physical input;
-// FP64 for the scratch X), rounded to the storage type To per coefficient.
-template <typename Tc, typename To, int N>
-__global__ void __launch_bounds__(ROWS_WARPS * 32) k_row_fwd(CurveDev c, const Tc *phys, To *spec, int keep_ends)
+// Physical (input type Ti) -> spectral in the compute type Tc, rounded to the
+// storage type To per coefficient.
+template <typename Ti, typename Tc, typename To, int N>
+__global__ void __launch_bounds__(ROWS_WARPS * 32) k_row_fwd(CurveDev c, const Ti *phys, To *spec, int keep_ends)
 {
     constexpr int H = N / 2;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     cpx<Tc> *tw = (cpx<Tc> *)smem_raw;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     cpx<Tc> *B0 = tw + H + warp * 2 * N, *B1 = B0 + N;
-    const cpx<Tc> *tsrc = (const cpx<Tc> *)(sizeof(Tc) == 8 ? c.twid64 : c.twid);
-    for (int t = threadIdx.x; t < H; t += blockDim.x) tw[t] = tsrc[t];
+    for (int t = threadIdx.x; t < H; t += blockDim.x) {
+        if constexpr (std::is_same<Tc, dfloat>::value) {   // from the FP64 table
+            const cpx<double> w = ((const cpx<double> *)c.twid64)[t];
+            tw[t] = {dfloat(w.x), dfloat(w.y)};
+        } else {
+            tw[t] = ((const cpx<Tc> *)(sizeof(Tc) == 8 ? c.twid64 : c.twid))[t];
+        }
+    }
     __syncthreads();
     const int ns = c.ns;
     const int m0 = (blockIdx.x * ROWS_WARPS + warp) * 2, m1 = m0 + 1;
     if (m0 >= ns) return;
     const bool has1 = m1 < ns;
     for (int n = lane; n < N; n += 32)
-        B0[n] = {phys[(size_t)m0 * N + n], has1 ? phys[(size_t)m1 * N + n] : Tc(0)};
+        B0[n] = {(Tc)phys[(size_t)m0 * N + n], has1 ? (Tc)phys[(size_t)m1 * N + n] : Tc(0)};
     __syncwarp();
     cpx<Tc> *W = warp_fft<Tc, N>(B0, B1, tw, false, lane);
     for (int j = lane; j < H; j += 32) {
@@ -1111,15 +1118,16 @@ cudaError_t make_row_maps(const CurveDev &c, RowMaps *m)
     return cudaSuccess;
 }
 
-template <typename Tc, typename To>
+template <typename Ti, typename Tc, typename To>
 static cudaError_t row_fwd_t(const CurveDev &c, const void *phys, void *spec, int keep_ends, cudaStream_t st)
 {
     return dispatch_n(c.nx, [&](auto nn) {
         constexpr int NN = decltype(nn)::value;
         size_t sm = rows_smem<Tc>(NN, 2);
-        cudaError_t e = set_smem(k_row_fwd<Tc, To, NN>, sm);
+        cudaError_t e = set_smem(k_row_fwd<Ti, Tc, To, NN>, sm);
         if (e != cudaSuccess) return e;
-        k_row_fwd<Tc, To, NN><<<row_grid(c.ns), ROWS_WARPS * 32, sm, st>>>(c, (const Tc *)phys, (To *)spec, keep_ends);
+        k_row_fwd<Ti, Tc, To, NN><<<row_grid(c.ns), ROWS_WARPS * 32, sm, st>>>(c, (const Ti *)phys, (To *)spec,
+                                                                               keep_ends);
         return cudaGetLastError();
     });
 }
@@ -1214,8 +1222,14 @@ cudaError_t launch_widen(const CurveDev &c, const void *in, cudaStream_t st)
 
 cudaError_t launch_row_fwd_x(const CurveDev &c, void *spec, int keep_ends, cudaStream_t st)
 {
-    return c.prec ? row_fwd_t<double, float>(c, c.X, spec, keep_ends, st)
-                  : row_fwd_t<double, double>(c, c.X, spec, keep_ends, st);
+    return c.prec ? row_fwd_t<double, double, float>(c, c.X, spec, keep_ends, st)
+                  : row_fwd_t<double, double, double>(c, c.X, spec, keep_ends, st);
+}
+
+cudaError_t launch_row_fwd(const CurveDev &c, const void *phys, void *spec, cudaStream_t st)
+{
+    return c.prec ? row_fwd_t<float, dfloat, float>(c, phys, spec, 0, st)
+                  : row_fwd_t<double, double, double>(c, phys, spec, 0, st);
 }
 
 cudaError_t launch_row_inv(const CurveDev &c, const void *spec, void *phys, int scale_mode, cudaStream_t st)

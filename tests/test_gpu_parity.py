@@ -254,6 +254,36 @@ def test_descent_is_deterministic_and_resumable(cfg0):
         x.close()
 
 
+@pytest.mark.parametrize("N,Ns,L", [(64, 1024, 22.0), (256, 600, 100.0)])
+def test_set_state_fp32_matches_the_fp64_transform(N, Ns, L):
+    """FP32 storage: set_state transforms its input in double-float arithmetic;
+    the state it makes equals, to one FP32 rounding per coefficient, the state
+    that create's FP64 transform makes of the same curve, so J (whose linear term
+    weighs each coefficient by a_j ~ k_j^4) agrees to 1e-6 relative (an FP32
+    transform in set_state put J of the autograd test's curve 3.6e-4 off)."""
+    rng = np.random.default_rng(N + Ns)
+    x = np.arange(N) * L / N
+    th = np.arange(Ns) * np.pi / (Ns - 1)
+    X = np.zeros((Ns, N))
+    for j in range(1, N // 2):   # a spectrum decaying over the whole range of modes
+        a, b = rng.standard_normal(2) * np.exp(-0.35 * j)
+        X += np.outer(0.5 + np.sin(th * (1 + j % 3)), a * np.cos(2 * np.pi * j * x / L) + b * np.sin(2 * np.pi * j * x / L))
+    X = X.astype(np.float32).astype(np.float64)
+    xt = torch.from_numpy(X).float()
+    S = 0.1 * (Ns - 1)
+    c = KSCurve(L, N, Ns, S, X[0], X[-1], u_init=xt, precision="fp32")
+    d = KSCurve(L, N, Ns, S, X[0], X[-1], precision="fp32")
+    d.set_state(xt.cuda(), 1.0, 0.0)
+    (J2c, Jac), (J2d, Jad) = c.cost(), d.cost()
+    gc, gd = c.gradient()[0].double().cpu().numpy(), d.gradient()[0].double().cpu().numpy()
+    e = dict(J2=abs(J2d - J2c) / J2c, J_arc=abs(Jad - Jac) / Jac, g=rel_2(gd, gc),
+             u=rel_max(d.get_state().double().cpu().numpy(), c.get_state().double().cpu().numpy()))
+    print("SET_STATE fp32 N=%d Ns=%d: %s" % (N, Ns, " ".join("%s=%.2e" % kv for kv in e.items())))
+    assert e["J2"] < 1e-6 and e["J_arc"] < 1e-6 and e["g"] < 1e-6 and e["u"] < 1e-6
+    c.close()
+    d.close()
+
+
 @pytest.mark.parametrize("s_transform", ["dense", "fft"])
 @pytest.mark.parametrize("sym", [1, 3])
 def test_symmetric_subspace_is_held_exactly(sym, s_transform):
