@@ -128,8 +128,9 @@ typedef struct {
                             physical layout.  Needs N_x >= 16, precision KS_FP64 or KS_FP32
                             (the FFT row phase), scheme KS_SCHEME_IMEX, launch = 0 and
                             s_transform 0, 1, 2, 4 or 5 (auto applies its rule to the
-                            N_x/2 stored columns); batches do not take it.  0 = none.
-                            Values above 7, and bit 2 without bit 0, are invalid. */
+                            N_x/2 stored columns); batched curves take it curve by curve.
+                            0 = none.  Values above 7, and bit 2 without bit 0, are
+                            invalid. */
     int32_t s_transform; /* how D_t is applied along s (same result to rounding):
                             0 auto: for a single curve the form measured fastest on GB300 for its
                             size: from N_s = 684 on (FFT length >= 4096) a four-step FFT form:

@@ -23,20 +23,22 @@ class KSBatch:
     u_plus / u_minus: per-curve physical end sections.  scheme "implicit" steps
     every curve with all linear terms of G implicit (its eigenbases are set up
     at creation, in parallel host threads); dtau, when given, replaces every
-    spec's dtau."""
+    spec's dtau.  symmetry: one value for every curve, or one per curve (the
+    subspaces of KSCurve; 5 and 7 store only the sine coefficients)."""
 
     def __init__(self, specs: Sequence, u_plus, u_minus, *, precision="fp32", adjoint="paper", conv="jrel",
-                 s_transform="auto", scheme="imex", dtau=None, device=None, stream=None):
+                 s_transform="auto", scheme="imex", dtau=None, symmetry=0, device=None, stream=None):
         self.lib = _native.load()
         self.device = torch.device(device if device is not None else "cuda")
         self.dtype = torch.float64 if precision == "fp64" else torch.float32
         self.specs = list(specs)
         self.nb = len(self.specs)
         arr = (KSParams * self.nb)()
+        syms = [int(symmetry)] * self.nb if np.ndim(symmetry) == 0 else [int(v) for v in symmetry]
         for i, s in enumerate(self.specs):
             arr[i] = KSParams(L=s.L, nx=s.N, ns=s.Ns, S=s.S, s0=getattr(s, "s0", 0.0), lam=1.0, lambda_free=0,
                               dtau=s.dtau if dtau is None else dtau, dtau_lambda=0.0, precision=_PREC[precision],
-                              adjoint=_ADJ[adjoint], conv=_CONV[conv], check_ends=0, symmetry=0,
+                              adjoint=_ADJ[adjoint], conv=_CONV[conv], check_ends=0, symmetry=syms[i],
                               s_transform=_STR[s_transform], launch=0, scheme=_SCHEME[scheme])
         self.params = arr
         nbytes = self.lib.ks_batch_workspace_bytes(self.nb, arr)

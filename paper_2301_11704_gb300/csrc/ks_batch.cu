@@ -85,8 +85,6 @@ ks_status validate_batch(int nb, const ks_params *p)
             return ks::report_error(KS_EINVAL, "all curves of a batch must have the same adjoint mode");
         if (p[i].scheme != p[0].scheme)
             return ks::report_error(KS_EINVAL, "all curves of a batch must have the same scheme");
-        if (p[i].symmetry & KS_SYM_SINE)
-            return ks::report_error(KS_EINVAL, "batched curves keep full storage (symmetry bit 2 is for single curves)");
     }
     return KS_OK;
 }
@@ -103,12 +101,13 @@ ks_status build_items(ks_batch *b)
         c.row_blocks = (c.ns + rs - 1) / rs;
         for (int k = 0; k < c.row_blocks; ++k) rows[c.nx].push_back(make_int2(i, k));
         if (c.F > 0) {
-            for (int jm = 0; jm < c.nx / 2; ++jm) fft[std::make_pair(c.F, c.f4b ? c.F1 : 0)].push_back(make_int2(i, jm));
+            for (int jm = 0; jm < c.W / 2; ++jm) fft[std::make_pair(c.F, c.f4b ? c.F1 : 0)].push_back(make_int2(i, jm));
             continue;
         }
-        const int bn = b->tile_pref ? (c.nx < 64 ? 32 : b->tile_pref) : (c.nx >= 64 ? 64 : 32);
+        // the contraction's columns: W (N_x, or N_x / 2 in sine storage)
+        const int bn = b->tile_pref ? (c.W < 64 ? 32 : b->tile_pref) : (c.W >= 64 ? 64 : 32);
         c.bn = bn;
-        c.tiles_c = (c.nx + bn - 1) / bn;
+        c.tiles_c = (c.W + bn - 1) / bn;
         for (int tr = 0; tr < c.tiles_r; ++tr)
             for (int tc = 0; tc < c.tiles_c; ++tc) dts[bn].push_back(make_int4(i, tc, tr, 0));
     }
@@ -326,7 +325,8 @@ size_t ks_batch_workspace_bytes(int32_t nb, const ks_params *params)
     size_t total = cvb + itb;
     for (int i = 0; i < nb; ++i)
         total += ks::make_layout(params[i].ns, params[i].nx, ks::storage32(params[i].precision), 0, 0,
-                                 params[i].s_transform, 0, 0, params[i].scheme == KS_SCHEME_IMPLICIT).total;
+                                 params[i].s_transform, 0, 0, params[i].scheme == KS_SCHEME_IMPLICIT,
+                                 (params[i].symmetry & KS_SYM_SINE) ? 1 : 0).total;
     return total;
 }
 
@@ -362,7 +362,8 @@ ks_status ks_batch_create(int32_t nb, const ks_params *params, const double *u_p
     size_t xoff = 0;
     for (int i = 0; i < nb; ++i) {
         const ks::Layout l = ks::make_layout(params[i].ns, params[i].nx, b->prec, 0, 0, params[i].s_transform, 0, 0,
-                                             params[i].scheme == KS_SCHEME_IMPLICIT);
+                                             params[i].scheme == KS_SCHEME_IMPLICIT,
+                                             (params[i].symmetry & KS_SYM_SINE) ? 1 : 0);
         b->off.push_back(o);
         b->cv[i] = ks::bind_layout(&params[i], l, base + o);
         o += l.total;
@@ -548,7 +549,7 @@ ks_status ks_batch_autotune(ks_batch *b, int32_t steps, int32_t *chosen)
     }
     // knob 3: the column tile of dense-form curves with N >= 64
     bool dense = false;
-    for (int i = 0; i < b->nb; ++i) dense = dense || (b->cv[i].F == 0 && b->cv[i].nx >= 64);
+    for (int i = 0; i < b->nb; ++i) dense = dense || (b->cv[i].F == 0 && b->cv[i].W >= 64);
     if (dense && s == KS_OK) {
         int best_t = b->tile_pref;
         for (int t : {64, 32}) {

@@ -1132,12 +1132,12 @@ __device__ __forceinline__ void f4b_body(const CurveDev &c, int mode, int discre
     const bool step = mode == GM_STEP && c.f4h;
     if (step) mode = GM_UPDATE;
     const double lam_d = sc->lambda, dtau_d = sc->dtau;
-    const int P = c.P, N = c.nx, ns = c.ns;
+    const int P = c.P, N = c.W, ns = c.ns;   // N: the stored columns
     const T *X = (const T *)(mode == GM_STORE ? c.U : c.R);
     const T *colscale = (const T *)(discrete ? c.sw : c.tau);
     const T s = discrete ? T(-1) : T(1);
     const int ca = 2 * jm, cb = 2 * jm + 1;
-    const bool oka = col_allowed(ca, c.sym), okb = col_allowed(cb, c.sym) && jm != 0;
+    const bool oka = col_live(ca, c.sym, c.hs), okb = col_live(cb, c.sym, c.hs);   // a column pair
     __syncthreads();   // twiddles
 
     // pass 1: lines n2, FFT over n1, times W_F^(n2 k1), into column n2 of B.  A
@@ -1261,9 +1261,9 @@ __device__ __forceinline__ void f4b_body(const CurveDev &c, int mode, int discre
     // `chain`: then pass 1 of D_t u of the line's updated sections into column n2
     T *Dout = (T *)c.D, *U = (T *)c.U, *G = (T *)c.G;
     const T *Ah = (const T *)c.A;
-    const T pr = ((const T *)c.prec_imex)[jm];
+    const T pra = ((const T *)c.prec_imex)[col_mode(ca, c.hs)], prb = ((const T *)c.prec_imex)[col_mode(cb, c.hs)];
     const T lam = (T)lam_d, dtau = (T)dtau_d;
-    const double cw = (jm == 0) ? 1.0 : 2.0;
+    const double cw = col_weight(cb, c.hs);   // column a's weight where it is live
     const T *tauc = (const T *)c.tau;
     auto pass3 = [&](int md, bool disc, bool chain) -> double {
         const T *rowscale = (const T *)(disc ? c.twr : c.sig);
@@ -1310,7 +1310,7 @@ __device__ __forceinline__ void f4b_body(const CurveDev &c, int mode, int discre
                 }
                 if (md == GM_UPDATE) {
                     if (interior) {
-                        uv[a] = V2{uv[a].x + dtau * pr * ga, uv[a].y + dtau * pr * gb};
+                        uv[a] = V2{uv[a].x + dtau * pra * ga, uv[a].y + dtau * prb * gb};
                         *reinterpret_cast<V2 *>(U + o) = uv[a];
                     }
                 } else {
@@ -1373,7 +1373,7 @@ __global__ void __launch_bounds__(F4_THREADS, 4) k_f4b_batch(const CurveDev *cv,
 {
     const int2 it = items[blockIdx.x];
     const CurveDev &c = cv[it.x];
-    f4b_body<T, F1, F2>(c, mode, discrete, gate, it.y, c.nx / 2);
+    f4b_body<T, F1, F2>(c, mode, discrete, gate, it.y, c.W / 2);
 }
 
 // ---- set-up: the twiddles W_F^k (storage type) and the kernel spectrum
@@ -1622,13 +1622,12 @@ static cudaError_t f4b_run(const CurveDev &c, int mode, int discrete, int gate, 
         const size_t sm = F4B<T, F1, F2>::BYTES;
         cudaError_t e = set_smem(k_f4b<T, F1, F2>, sm);
         if (e != cudaSuccess) return e;
-        return launch_pdl(k_f4b<T, F1, F2>, dim3(c.nx / 2), sm, st, c, mode, discrete, gate);
+        return launch_pdl(k_f4b<T, F1, F2>, dim3(c.W / 2), sm, st, c, mode, discrete, gate);
     });
 }
 
 cudaError_t launch_f4b(const CurveDev &c, int mode, int discrete, int gate, cudaStream_t st)
 {
-    if (c.hs) return cudaErrorInvalidValue;   // full rows only
     return c.prec ? f4b_run<float>(c, mode, discrete, gate, st) : f4b_run<double>(c, mode, discrete, gate, st);
 }
 

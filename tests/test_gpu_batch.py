@@ -251,3 +251,35 @@ def test_batch_converges_per_curve_to_the_papers_criterion():
         R, D = oracle.curve_residual(oracle.curve_spectral(X), 22.0, s.S)
         assert oracle.curve_scalars(R, D, 22.0, s.S)["J_arc"] < 1e-10, o
     b.close()
+
+
+@pytest.mark.parametrize("precision,tol,tol_tuned", [("fp64", 1e-12, 1e-11), ("fp32", 2e-6, 2e-5)])
+def test_sine_storage_batch_matches_full_storage(precision, tol, tol_tuned):
+    """A batch of odd curves (the workload's end points are odd; the projection
+    makes the trial curves so) in which every other curve keeps only the sine
+    coefficients (symmetry 5) against the same batch in full storage (symmetry
+    1), curve by curve, in the dense, one-CTA FFT and batched four-step forms,
+    before and after the tile autotuner (which may pick other splits for the two
+    batches: then the tolerance between s-forms)."""
+    specs = _mixed_specs() + _four_step_specs([(32, 700), (64, 1500), (128, 600)])
+    ins = [_inputs(s) for s in specs]
+    syms = [5 if k % 2 == 0 else 1 for k in range(len(specs))]
+    bh = KSBatch(specs, [i[0] for i in ins], [i[1] for i in ins], precision=precision, conv="jarc", symmetry=syms)
+    bf = KSBatch(specs, [i[0] for i in ins], [i[1] for i in ins], precision=precision, conv="jarc", symmetry=1)
+    assert bh.workspace_bytes < bf.workspace_bytes
+    for b in (bh, bf):
+        b.init_trial(np.array([i[2] for i in ins]), [i[3] for i in ins])
+    oh, of = bh.descend(20), bf.descend(20)
+    for k in range(len(specs)):
+        xh, xf = bh.get_state(k).double().cpu().numpy(), bf.get_state(k).double().cpu().numpy()
+        assert np.abs(xh - xf).max() <= tol * np.abs(xf).max(), (k, specs[k])
+        assert abs(oh["J"][k] - of["J"][k]) <= tol * of["J"][k]
+        U = np.fft.rfft(xh, axis=1)
+        assert np.abs(U.real).max() <= (1e-12 if precision == "fp64" else 1e-6) * np.abs(U).max()
+    bh.autotune(4)
+    bf.autotune(4)
+    oh, of = bh.descend(10), bf.descend(10)
+    for k in range(len(specs)):
+        assert abs(oh["J"][k] - of["J"][k]) <= tol_tuned * of["J"][k], k
+    bh.close()
+    bf.close()
