@@ -566,7 +566,9 @@ __global__ void __launch_bounds__(F4_THREADS) k_f4_p3(CurveDev c, int mode, int 
     const T *rowscale = (const T *)(discrete ? c.twr : c.sig);
     T *Dout = (T *)c.D, *U = (T *)c.U, *G = (T *)c.G;
     const T *Ah = (const T *)c.A;
-    const T *prec = (const T *)c.prec_imex;
+    // the IMEX factors of the sector's columns: full storage, mode jm0 + q / 2 of
+    // column q; sine storage, mode 2 jm0 + q
+    const T *prec = (const T *)c.prec_imex + (HS ? 2 * jm0 : jm0);
     const T lam = (T)lam_d, dtau = (T)dtau_d;
     const int tn = threadIdx.x % F4W;
     double partsum = 0.0;
@@ -623,12 +625,12 @@ __global__ void __launch_bounds__(F4_THREADS) k_f4_p3(CurveDev c, int mode, int 
 #pragma unroll
                 for (int q = 0; q < NV; ++q) {
                     g[q] = sector_col_ok(jm0, q, sym, hs) ? -(av[h][q] + (discrete ? -lam * y[q] : lam * y[q])) : T(0);
-                    gg += (T)col_weight(2 * jm0 + q, hs) * g[q] * g[q];
+                    gg += (((HS ? 2 * jm0 + q : jm0 + q / 2) == 0) ? T(1) : T(2)) * g[q] * g[q];
                 }
                 partsum += wv[h] * (double)gg;
                 if (mode == GM_UPDATE) {
 #pragma unroll
-                    for (int q = 0; q < NV; ++q) uv[h][q] += dtau * prec[col_mode(2 * jm0 + q, hs)] * g[q];
+                    for (int q = 0; q < NV; ++q) uv[h][q] += dtau * prec[HS ? q : q / 2] * g[q];
                     st_sector(U + o, uv[h]);
                 }
             } else {
@@ -801,6 +803,9 @@ __global__ void __launch_bounds__(F4_THREADS) k_f4c(CurveDev c, int mode, int di
     __shared__ int am_last;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, jm0 = blockIdx.y * MPC, F = F1 * F2;
     const int P = c.P, N = c.W, ns = c.ns, sym = c.sym, hs = c.hs;   // N: the stored columns
+    unsigned live = 0;   // bit q: column 2 jm0 + q of the sector is one the subspace keeps
+#pragma unroll
+    for (int q = 0; q < NV; ++q) live |= sector_col_ok(jm0, q, sym, hs) ? 1u << q : 0u;
     const cpx<T> *ftw = (const cpx<T> *)c.ftw;
     // the contraction being applied: GM_STEP runs the update (adjoint mode
     // `discrete`), then D_t u of the updated state (cmode, cdisc switch between them)
@@ -894,7 +899,7 @@ __global__ void __launch_bounds__(F4_THREADS) k_f4c(CurveDev c, int mode, int di
         p3_rows(j3f, a3f, u3f);
     }
     const double lam_d = sc->lambda, dtau_d = sc->dtau;
-    const T *prec = (const T *)c.prec_imex;
+    const T *prec = (const T *)c.prec_imex + (hs ? 2 * jm0 : jm0);   // the IMEX factors of the sector
     const T lam = (T)lam_d, dtau = (T)dtau_d;
     double partsum = 0.0;
     __syncthreads();   // twiddles
@@ -933,8 +938,8 @@ __global__ void __launch_bounds__(F4_THREADS) k_f4c(CurveDev c, int mode, int di
             cpx<T> v[R1];
 #pragma unroll
             for (int a = 0; a < R1; ++a)
-                v[a] = {sector_col_ok(jm0, 2 * q, sym, hs) ? cs[a] * x[a][2 * q] : T(0),
-                        sector_col_ok(jm0, 2 * q + 1, sym, hs) ? cs[a] * x[a][2 * q + 1] : T(0)};
+                v[a] = {((live >> (2 * q)) & 1u) ? cs[a] * x[a][2 * q] : T(0),
+                        ((live >> (2 * q + 1)) & 1u) ? cs[a] * x[a][2 * q + 1] : T(0)};
             reg_fft_fwd<T, R1>(v, tw1, w32, lane);
             cpx<T> *lt = Lt + ((size_t)q * LPC + li) * LT;
 #pragma unroll
@@ -1039,8 +1044,8 @@ __global__ void __launch_bounds__(F4_THREADS) k_f4c(CurveDev c, int mode, int di
                 T yv[NV];
 #pragma unroll
                 for (int q = 0; q < MPC; ++q) {
-                    yv[2 * q] = sector_col_ok(jm0, 2 * q, sym, hs) ? rsv[h] * y[q][a0 + h].x : T(0);
-                    yv[2 * q + 1] = sector_col_ok(jm0, 2 * q + 1, sym, hs) ? rsv[h] * y[q][a0 + h].y : T(0);
+                    yv[2 * q] = ((live >> (2 * q)) & 1u) ? rsv[h] * y[q][a0 + h].x : T(0);
+                    yv[2 * q + 1] = ((live >> (2 * q + 1)) & 1u) ? rsv[h] * y[q][a0 + h].y : T(0);
                 }
                 const size_t o = (size_t)j * N + 2 * jm0;
                 if (cmode == GM_STORE) {
@@ -1052,13 +1057,13 @@ __global__ void __launch_bounds__(F4_THREADS) k_f4c(CurveDev c, int mode, int di
                     T gg = T(0);   // the row's sum over the sector in the storage type, one FP64 term per row
 #pragma unroll
                     for (int q = 0; q < NV; ++q) {
-                        g[q] = sector_col_ok(jm0, q, sym, hs) ? -(av[h][q] + (cdisc ? -lam * yv[q] : lam * yv[q])) : T(0);
-                        gg += (T)col_weight(2 * jm0 + q, hs) * g[q] * g[q];
+                        g[q] = ((live >> q) & 1u) ? -(av[h][q] + (cdisc ? -lam * yv[q] : lam * yv[q])) : T(0);
+                        gg += (((hs ? 2 * jm0 + q : jm0 + q / 2) == 0) ? T(1) : T(2)) * g[q] * g[q];
                     }
                     partsum += wv[h] * (double)gg;
                     if (cmode == GM_UPDATE) {
 #pragma unroll
-                        for (int q = 0; q < NV; ++q) uv[h][q] += dtau * prec[col_mode(2 * jm0 + q, hs)] * g[q];
+                        for (int q = 0; q < NV; ++q) uv[h][q] += dtau * prec[hs ? q : q / 2] * g[q];
                         RV::st(U + o, uv[h]);
                     }
                 } else {
