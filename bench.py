@@ -657,22 +657,38 @@ def run_curve(args):
         dt = curve.dtype
         host_in = torch.empty((spec.Ns, N), dtype=dt).pin_memory()
         host_in.copy_(curve.get_state().cpu())
-        dev_in = torch.empty((spec.Ns, N), dtype=dt, device=dev)
+        dev_in = [torch.empty((spec.Ns, N), dtype=dt, device=dev) for _ in range(2)]
         n_e2e = max(1, min(args.e2e_steps, K))
         nbytes = spec.Ns * N * b
         # every step: the curve from pinned host memory (set_state), one descent
         # step, and its result J read back to the host (ks_curve_descend copies the
-        # device scalar record, 176 bytes, and synchronises)
+        # device scalar record, 176 bytes, and synchronises).  Two device buffers:
+        # the next step's copy runs on a copy stream while this step computes (the
+        # buffer it fills was last read by the step before, which has completed).
+        cur = torch.cuda.current_stream(dev)
+        cps = torch.cuda.Stream(dev)
+        copied = [torch.cuda.Event(), torch.cuda.Event()]
+
+        def h2d(k):
+            with torch.cuda.stream(cps):
+                dev_in[k % 2].copy_(host_in, non_blocking=True)
+                copied[k % 2].record(cps)
+
         torch.cuda.synchronize(dev)
         t0 = time.perf_counter()
-        for _ in range(n_e2e):
-            dev_in.copy_(host_in, non_blocking=True)
-            curve.set_state(dev_in, 1.0, 0.0)
+        h2d(0)
+        for k in range(n_e2e):
+            cur.wait_event(copied[k % 2])
+            if k + 1 < n_e2e:
+                h2d(k + 1)
+            curve.set_state(dev_in[k % 2], 1.0, 0.0)
             curve.descend(1)
+        torch.cuda.synchronize(dev)
         e2e_s = time.perf_counter() - t0
         e2e = {"value": M * n_e2e / e2e_s, "unit": UNIT, "h2d_bytes_per_step": nbytes,
                "d2h_bytes_per_step": 176, "steps": n_e2e,
-               "path": "pinned host curve -> set_state -> descend(1), J read back"}
+               "path": "pinned host curve -> set_state -> descend(1), J read back; each step's host-to-device "
+                       "copy overlaps the step before (two device buffers, a copy stream)"}
     sc = curve.scalars()
     curve.close()
 

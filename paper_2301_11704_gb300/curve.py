@@ -166,9 +166,13 @@ class KSCurve:
         return lam.value, tau.value
 
     def set_state(self, u, lam: float = 1.0, tau: float = 0.0):
+        """Asynchronous on the curve's stream (like the C call): u is read by the
+        curve's kernels; on another stream than torch's current one its memory is
+        kept from reuse until that stream has read it."""
         u = self._as_curve_tensor(u)
         check(self.lib.ks_curve_set_state(self._live(), u.data_ptr(), float(lam), float(tau)))
-        self.stream.synchronize()
+        if self.stream != torch.cuda.current_stream(self.device):
+            u.record_stream(self.stream)
 
     def profile(self, max_steps: int):
         """Start (max_steps > 0) or stop (0) per-phase event timing of descent steps."""
