@@ -5,7 +5,8 @@
 // Row m holds section s_m spectrally: N/2 complex Fourier coefficients
 // u^_{m,j}, j = 0..N/2-1, interleaved (re, im); the Nyquist coefficient is not
 // stored (held at zero) and Im u^_{m,0} = 0.  Row 0 is s = +inf, row N_s-1 is
-// s = -inf (eq. t_grid).
+// s = -inf (eq. t_grid).  Sine storage (odd sections, symmetry bit 2): rows of
+// N/2 words, Im u^_{m,j} at column j (the real parts are zero).
 //
 // One descent step is three kernels:
 //   k_rows  (x-direction, one warp per pair of sections): f(u), r = f - l D_t u,
