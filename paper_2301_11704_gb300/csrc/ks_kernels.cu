@@ -1086,8 +1086,8 @@ static cudaError_t rows_t(const CurveDev &c, int mode, cudaStream_t st, StepArm 
     });
 }
 
-// The driver's tensor-map encoder, through the runtime's entry-point query (no
-// link against the driver library).
+// cuTensorMapEncodeTiled of the CUDA driver API, obtained through the runtime's
+// entry-point query (no link against libcuda).
 using EncodeTiled = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
