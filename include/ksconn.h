@@ -220,6 +220,9 @@ int32_t ks_curve_s_form(const ks_params *p);
  *  stream       cudaStream_t for all work of this curve (may be changed with
  *               ks_curve_set_stream).
  *  out          receives the handle.
+ * The handle holds host metadata, a pinned host copy of the device scalars
+ * (cudaMallocHost, freed by ks_curve_destroy) and, for the FFT row phase from
+ * N_s = 2048 on, the tensor maps of the row phase's TMA tile loads.
  * Errors: KS_EINVAL, KS_ENOMEM, KS_ECUDA, KS_ENOTEQUILIBRIUM (check_ends = 1).
  * Synchronises the stream. */
 ks_status ks_curve_create(const ks_params *p, const double *u_plus_host, const double *u_minus_host,
