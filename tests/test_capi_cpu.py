@@ -193,3 +193,20 @@ def test_batches_with_mixed_schemes_are_rejected(lib):
     ok = (KSParams * 2)(_params(scheme=1), _params(scheme=1, ns=200))
     plain = (KSParams * 2)(_params(), _params(ns=200))
     assert lib.ks_batch_workspace_bytes(2, ok) > lib.ks_batch_workspace_bytes(2, plain) > 0
+
+
+def test_sine_storage_batches_take_half_fields(lib):
+    """A batch may mix sine and full storage curve by curve; each sine curve's five
+    fields take half the bytes (the FP64 scratch and the tables stay); the
+    implicit scheme keeps full storage."""
+    full = (KSParams * 3)(_params(symmetry=1, precision=1, nx=64, ns=700), _params(symmetry=1, ns=300),
+                          _params(symmetry=1, precision=1, nx=128, ns=1500))
+    mixed = (KSParams * 3)(_params(symmetry=5, precision=1, nx=64, ns=700), _params(symmetry=1, ns=300),
+                           _params(symmetry=5, precision=1, nx=128, ns=1500))
+    # batches take one precision: make the middle curve FP32 too
+    full[1].precision = mixed[1].precision = 1
+    bf, bm = lib.ks_batch_workspace_bytes(3, full), lib.ks_batch_workspace_bytes(3, mixed)
+    assert 0 < bm < bf
+    assert bf - bm >= 5 * (700 * 32 + 1500 * 64) * 4 - 10 * 256
+    bad = (KSParams * 2)(_params(symmetry=5, scheme=1), _params(symmetry=5, scheme=1))
+    assert lib.ks_batch_workspace_bytes(2, bad) == 0
