@@ -283,3 +283,22 @@ def test_sine_storage_batch_matches_full_storage(precision, tol, tol_tuned):
         assert abs(oh["J"][k] - of["J"][k]) <= tol_tuned * of["J"][k], k
     bh.close()
     bf.close()
+
+
+def test_sine_storage_batch_dense_form():
+    """The dense batched contraction (s_transform "dense") in sine storage against
+    full storage, FP64, curve by curve."""
+    specs = _mixed_specs()
+    ins = [_inputs(s) for s in specs]
+    out = []
+    for sym in (5, 1):
+        b = KSBatch(specs, [i[0] for i in ins], [i[1] for i in ins], precision="fp64", conv="jarc",
+                    s_transform="dense", symmetry=sym)
+        b.init_trial(np.array([i[2] for i in ins]), [i[3] for i in ins])
+        o = b.descend(15)
+        out.append((o["J"].copy(), [b.get_state(k).cpu().numpy() for k in range(len(specs))]))
+        b.close()
+    (jh, xh), (jf, xf) = out
+    for k in range(len(specs)):
+        assert np.abs(xh[k] - xf[k]).max() <= 1e-12 * np.abs(xf[k]).max(), k
+        assert abs(jh[k] - jf[k]) <= 1e-12 * jf[k], k

@@ -97,3 +97,23 @@ def test_noalloc_rejects_curves_larger_than_its_scratch():
                              None)
     assert st == _native.KS_ENOMEM
     assert b"scratch" in lib.ks_last_error()
+
+
+def test_noalloc_cost_in_sine_storage():
+    """A curve in sine storage (symmetry 5) evaluated by the allocation-free entry
+    point: the same J^2 and J_arc as its workspace curve and as full storage."""
+    lib = _native.load()
+    spec, c = _curve(1, "fp64")
+    u = c.get_state().clone()   # odd end points; the projection of both curves drops the rest
+    c.close()
+    x = u.cpu().double().numpy()
+    outs = []
+    for sym in (1, 5):
+        r = KSCurve(spec.L, spec.N, spec.Ns, spec.S, x[0], x[-1], dtau=spec.dtau, precision="fp64", u_init=u,
+                    symmetry=sym)
+        ref = r.cost()
+        got = _noalloc(lib, r, u)
+        outs.append(got)
+        assert abs(got[0] - ref[0]) <= 1e-12 * ref[0] and abs(got[1] - ref[1]) <= 1e-12 * ref[1]
+        r.close()
+    assert abs(outs[0][0] - outs[1][0]) <= 1e-12 * outs[0][0]
